@@ -1,0 +1,189 @@
+"""Pins for the oracle's compositing (Eq. 11) and loss (Eq. 12): closed-form
+single-Gaussian images, the opaque-front and early-stop rules, invariants,
+and brute vs prefilter mode."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as R
+from synth import workloads
+from synth.scene import Camera, look_at
+
+Y00 = 0.5 / math.sqrt(math.pi)
+CAM = Camera(60.0, 60.0, 32.0, 24.0, 64, 48)
+IDENT = (np.eye(3), np.zeros(3))
+
+
+def _scene(means, log_scales, logits, colors, quats=None):
+    n = len(means)
+    sh = ((np.asarray(colors, float) - 0.5) / Y00)[:, None, :]
+    if quats is None:
+        quats = [[1.0, 0, 0, 0]] * n
+    return {"means": np.asarray(means, float), "log_scales": np.asarray(log_scales, float),
+            "quats": np.asarray(quats, float), "opacity_logits": np.asarray(logits, float), "sh": sh}
+
+
+def _render(params, cam=CAM, pose=IDENT, deg=0, **kw):
+    return R.render(R.to_tensors(params), deg, cam, *pose, **kw)
+
+
+@pytest.mark.parametrize("z,s,logit", [(2.0, 0.02, 0.0), (1.0, 0.05, 1.5), (3.0, 0.01, -2.0)])
+def test_single_isotropic_gaussian_closed_form(z, s, logit):
+    """Pixel value = c * min(0.99, sigmoid(o) exp(-|u - mu|^2 / (2 sigma^2))) where
+    the 3-sigma and 1/255 rules allow, sigma^2 = (f s / z)^2 + 0.3."""
+    c = np.array([0.9, 0.4, 0.2])
+    out = _render(_scene([[0, 0, z]], [[np.log(s)] * 3], [logit], [c]))
+    sig2 = (CAM.fx * s / z) ** 2 + 0.3
+    jj, ii = np.meshgrid(np.arange(48) + 0.5, np.arange(64) + 0.5, indexing="ij")
+    r2 = (ii - 32.0) ** 2 + (jj - 24.0) ** 2
+    q = r2 / sig2
+    a = np.minimum(0.99, 1 / (1 + math.exp(-logit)) * np.exp(-0.5 * q))
+    a = np.where((q <= 9) & (a >= 1 / 255), a, 0.0)
+    np.testing.assert_allclose(out["color"].numpy(), c[:, None, None] * a[None], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(out["depth"].numpy(), z * a, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(out["alpha"].numpy(), a, rtol=1e-12, atol=1e-15)
+    # four pixels around the centre share the peak exp(-0.25 / sigma^2)
+    peak = min(0.99, 1 / (1 + math.exp(-logit)) * math.exp(-0.25 / sig2))
+    np.testing.assert_allclose(out["alpha"].numpy()[23:25, 31:33], peak, rtol=1e-12)
+
+
+def test_pixel_centre_convention():
+    """A Gaussian whose mean sits exactly on the centre of pixel (10, 7) gives
+    that pixel G = 1, i.e. alpha = min(0.99, opacity)."""
+    z = 2.0
+    x = (10.5 - CAM.cx) * z / CAM.fx
+    y = (7.5 - CAM.cy) * z / CAM.fy
+    out = _render(_scene([[x, y, z]], [[np.log(0.01)] * 3], [0.0], [[1, 1, 1]]))
+    assert abs(out["alpha"].numpy()[7, 10] - 0.5) < 1e-12
+    assert out["alpha"].numpy()[7, 10] == out["alpha"].numpy().max()
+
+
+def test_opaque_front_hides_all_but_one_percent():
+    """A front Gaussian clamped at alpha 0.99 over the whole image lets exactly
+    1% of the rest through: image = 0.99 c_front + 0.01 * (render of the rest)."""
+    rest = workloads.tiny_random(seed=5, n=60).params
+    front = _scene([[0, 0, 0.3]], [[np.log(5.0)] * 3], [20.0], [[0.2, 0.7, 0.4]])
+    both = {k: np.concatenate([front[k], np.asarray(rest[k], float)]) for k in front}
+    a = _render(both)
+    b = _render({k: np.asarray(rest[k], float) for k in front})
+    expect = 0.99 * np.array([0.2, 0.7, 0.4])[:, None, None] + 0.01 * b["color"].numpy()
+    np.testing.assert_allclose(a["color"].numpy(), expect, rtol=1e-12, atol=1e-15)
+
+
+def test_three_opaque_fronts_stop_compositing():
+    """Two alpha-0.99 layers leave T = 1e-4; the third would push T to 1e-6 <
+    1e-4, so it and everything behind contribute exactly nothing."""
+    cols = [[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]]
+    sc = _scene([[0, 0, 0.3], [0, 0, 0.4], [0, 0, 0.5], [0, 0, 0.6]], [[np.log(5.0)] * 3] * 4, [20.0] * 4, cols)
+    out = _render(sc)
+    img = out["color"].numpy()
+    np.testing.assert_allclose(img[:, 10, 10], [0.99, 0.01 * 0.99, 0.0], rtol=1e-12, atol=1e-15)
+    assert (out["n_contrib"].numpy() == 2).all()
+    np.testing.assert_allclose(out["T_final"].numpy(), 0.01 * 0.01, rtol=1e-9)
+
+
+def test_invisible_gaussian_below_alpha_min():
+    """sigmoid(logit) < 1/255 everywhere: the Gaussian never takes part."""
+    out = _render(_scene([[0, 0, 1.0]], [[np.log(0.1)] * 3], [-6.0], [[1, 1, 1]]))
+    assert float(out["alpha"].abs().max()) == 0.0
+
+
+def test_invariants_random_scene():
+    w = workloads.tiny_random(seed=11, n=300)
+    out = _render({k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES})
+    T = out["T_final"].numpy()
+    assert (T >= 0).all() and (T <= 1).all()
+    a = out["alpha"].numpy()
+    assert (a >= 0).all() and (a < 1).all()
+    cmax = out["proj"]["rgb"].detach().numpy().max()
+    assert out["color"].numpy().max() <= cmax + 1e-12
+
+
+def test_permutation_invariance():
+    w = workloads.tiny_random(seed=12, n=200)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    perm = np.random.default_rng(0).permutation(200)
+    Q = {k: v[perm] for k, v in P.items()}
+    a, b = _render(P), _render(Q)
+    np.testing.assert_allclose(a["color"].numpy(), b["color"].numpy(), rtol=0, atol=1e-15)
+
+
+def test_rigid_motion_invariance(rng):
+    """Moving the map and the camera by the same rigid motion changes nothing
+    (SH degree 3, so the view direction is exercised too)."""
+    w = workloads.tiny_random(seed=13, n=150, sh_degree=3, sh_rest_std=0.1)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    from scipy.spatial.transform import Rotation
+    G = Rotation.from_rotvec([0.3, -0.5, 0.8]).as_matrix()
+    tr = np.array([1.0, -2.0, 0.5])
+    Q = dict(P)
+    Q["means"] = P["means"] @ G.T + tr
+    # rotate each Gaussian's frame: q' = g * q
+    gq = Rotation.from_matrix(G).as_quat()[[3, 0, 1, 2]]
+    w0, x0, y0, z0 = gq
+    qs = P["quats"]
+    Q["quats"] = np.stack([
+        w0 * qs[:, 0] - x0 * qs[:, 1] - y0 * qs[:, 2] - z0 * qs[:, 3],
+        w0 * qs[:, 1] + x0 * qs[:, 0] + y0 * qs[:, 3] - z0 * qs[:, 2],
+        w0 * qs[:, 2] - x0 * qs[:, 3] + y0 * qs[:, 0] + z0 * qs[:, 1],
+        w0 * qs[:, 3] + x0 * qs[:, 2] - y0 * qs[:, 1] + z0 * qs[:, 0]], 1)
+    # SH coefficients are expressed in the world frame: rotating the world
+    # rotates the colour field, so compare the view-independent (deg-0) part
+    # with a pose moved accordingly.  T_CW' = T_CW G^-1.
+    Rc, tc = np.eye(3), np.zeros(3)
+    Rc2 = Rc @ G.T
+    tc2 = tc - Rc2 @ tr
+    P0 = dict(P, sh=P["sh"][:, :1])
+    Q0 = dict(Q, sh=Q["sh"][:, :1])
+    a = _render(P0)
+    b = _render(Q0, pose=(Rc2, tc2))
+    np.testing.assert_allclose(a["color"].numpy(), b["color"].numpy(), atol=1e-11)
+    np.testing.assert_allclose(a["depth"].numpy(), b["depth"].numpy(), atol=1e-11)
+    # translation only: the full SH colour is invariant too
+    Qt = dict(P, means=P["means"] + tr)
+    c = _render(P, deg=3)
+    d = _render(Qt, pose=(Rc, tc - tr), deg=3)
+    np.testing.assert_allclose(c["color"].numpy(), d["color"].numpy(), atol=1e-11)
+
+
+def test_brute_equals_prefilter():
+    """Dropping Gaussians with q > 9 at every pixel of a chunk changes nothing:
+    identical blend sets, values equal up to the summation order (1e-13)."""
+    w = workloads.tiny_random(seed=14, n=400, sh_degree=1, sh_rest_std=0.1)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    a = _render(P, deg=1, prefilter=False)
+    b = _render(P, deg=1, prefilter=True)
+    assert torch.equal(a["n_contrib"], b["n_contrib"])
+    for k in ("color", "depth", "alpha"):
+        np.testing.assert_allclose(a[k].numpy(), b[k].numpy(), rtol=1e-13, atol=1e-15, err_msg=k)
+
+
+def test_pixel_subset_matches_full_image(rng):
+    w = workloads.tiny_random(seed=15, n=300)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    full = _render(P)
+    pix = np.stack([rng.integers(0, 64, 50), rng.integers(0, 48, 50)], 1)
+    sub = _render(P, pixels=pix, prefilter=True)
+    np.testing.assert_allclose(sub["color"].numpy(), full["color"].numpy()[:, pix[:, 1], pix[:, 0]], rtol=1e-13)
+    np.testing.assert_allclose(sub["depth"].numpy(), full["depth"].numpy()[pix[:, 1], pix[:, 0]], rtol=1e-13)
+    np.testing.assert_array_equal(sub["n_contrib"].numpy(), full["n_contrib"].numpy()[pix[:, 1], pix[:, 0]])
+
+
+def test_loss_closed_form():
+    H, W = 4, 5
+    tgt = np.full((3, H, W), 0.5)
+    tdep = np.full((H, W), 2.0)
+    tdep[0, :] = 0.0  # invalid target depth is ignored
+    col = torch.as_tensor(tgt + 0.1)
+    dep = torch.as_tensor(tdep + 0.3)
+    L = float(R.loss_l1(col, dep, tgt, tdep))
+    assert abs(L - (0.8 * 0.1 + 0.2 * 0.3)) < 1e-12
+    _, gc, gd = R.loss_image_grads(tgt + 0.1, tdep + 0.3, tgt, tdep)
+    np.testing.assert_allclose(gc.numpy(), 0.8 / (3 * H * W))
+    expect = np.full((H, W), 0.2 / (H * W - W))
+    expect[0, :] = 0.0
+    np.testing.assert_allclose(gd.numpy(), expect)
+    _, gc0, _ = R.loss_image_grads(tgt, tdep, tgt, tdep)
+    assert float(gc0.abs().max()) == 0.0  # sign(0) = 0
