@@ -1,0 +1,345 @@
+"""Benchmark: fwd + bwd + Adam iterations of the Gaussian map optimisation
+(GSFusion's online optimisation, Sec. III-B.3) on one synthetic view at
+1200x680 with about 300k quadtree-seeded Gaussians, SH degree 3, float32.
+
+One step = gs_render_fwd + gs_loss_l1 + gs_render_bwd + gs_adam_step on the
+same view (inputs resident in HBM).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--gpus N > 1 runs N independent replicas under torchrun (one process per GPU,
+no collective on the data path); the value is the sum over replicas.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the only other place this script runs the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+Adam iterations/sec and Gaussian-pixel evals/sec at 1 GB300, % HBM roofline"
+WORKLOAD = "single_view 1200x680, ~300k quadtree-seeded Gaussians, SH degree 3, fp32, loss 0.8 L1(rgb) + 0.2 L1(depth)"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic traffic and work per launch (bytes a kernel must move at least)
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(n, deg, pairs, npx):
+    K = (deg + 1) ** 2
+    pbytes = 4 * (11 + 3 * K)  # parameters of one Gaussian
+    feat = 48                   # projected record
+    return {
+        "project_fwd": n * (pbytes + feat + 4 + 4 + 8),
+        "depth_sort": n * 4 * 8,          # 4 passes of one read + one write of (key, id)
+        "duplicate": n * 12 + pairs * 8,
+        "pair_sort": pairs * 16 * 2,      # 2 passes of (key, id) read + write
+        "ranges": pairs * 4,
+        "raster_fwd": pairs * (4 + feat) + npx * (3 * 4 + 4 + 4 + 4 + 4),
+        "loss": npx * (4 * 4 * 2 + 4 * 4),
+        "raster_bwd": pairs * (4 + feat) + npx * (4 + 4 + 16) + n * 48,
+        "project_bwd": n * (pbytes + 48 + pbytes * 2),
+        "adam": n * (11 + 3 * K) * 4 * 7,  # read p, g, m, v; write p, m, v
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region (median SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import Context, GaussianModel, Trainer
+    from synth import workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    abi.load()
+    w = workloads.single_view()
+    v = w.views[0]
+    H, W = v.cam.height, v.cam.width
+    ctx = Context(local_rank)
+    model = GaussianModel(w.params, device=dev)
+    tr = Trainer(model, v.cam, v.pose.R, v.pose.t, ctx=ctx, device=local_rank)
+    trgb = torch.as_tensor(v.target_rgb, device=dev)
+    tdep = torch.as_tensor(v.target_depth, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        tr.step(trgb, tdep)
+    torch.cuda.synchronize(dev)
+
+    # counts per iteration (pairs, evals) from one counted iteration
+    abi.gs_set_eval_counting(ctx.handle, True)
+    tr.step(trgb, tdep)
+    st = ctx.stats()
+    abi.gs_set_eval_counting(ctx.handle, False)
+    pairs, e_blend, e_tiled = st["n_pairs"], st["evals_blended"], st["evals_tiled"]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # timed region: K steps, events on the launch stream, per-stage events inside the library
+    launches0 = ctx.stats()["kernel_launches"]
+    abi.gs_set_profiling(ctx.handle, True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tr.step(trgb, tdep)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    stages = abi.gs_profile_read(ctx.handle)
+    abi.gs_set_profiling(ctx.handle, False)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    loss_end = float(tr.loss)
+
+    # end to end through the public API with host buffers: per step, H2D of
+    # the target RGB-D frame from pinned memory and D2H of the loss
+    h_rgb = torch.from_numpy(v.target_rgb).pin_memory()
+    h_dep = torch.from_numpy(v.target_depth).pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+    d_rgb = torch.empty_like(trgb)
+    d_dep = torch.empty_like(tdep)
+    barrier()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    t_host0 = time.perf_counter()
+    f0.record(stream)
+    for _ in range(args.steps):
+        d_rgb.copy_(h_rgb, non_blocking=True)
+        d_dep.copy_(h_dep, non_blocking=True)
+        loss = tr.step(d_rgb, d_dep)
+        h_loss.copy_(loss, non_blocking=True)
+    f1.record(stream)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    e2e_host_s = time.perf_counter() - t_host0
+    h2d = h_rgb.numel() * 4 + h_dep.numel() * 4
+
+    times = torch.tensor([ms_total, e2e_ms], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    ms_total, e2e_ms = float(times[0]), float(times[1])
+
+    # roofline of the dominant kernel (per launch, CUDA events over the timed region)
+    npx = H * W
+    alg = algorithmic_bytes(w.n, w.sh_degree, pairs, npx)
+    per_stage = {k: {"ms_per_launch": (ms / c if c else 0.0), "launches": c, "share": None}
+                 for k, (ms, c) in stages.items()}
+    tot_stage = sum(ms for ms, _ in stages.values())
+    for k, (ms, c) in stages.items():
+        per_stage[k]["share"] = ms / tot_stage if tot_stage else None
+    dom = max(stages, key=lambda k: stages[k][0])
+    hbm_peak, peak_kind = load_peaks()
+    dom_ms = per_stage[dom]["ms_per_launch"]
+    achieved = alg[dom] / (dom_ms * 1e-3) / 1e9 if dom_ms else 0.0
+    traffic = load_traffic(dom)
+    it_s = world * args.steps / (ms_total * 1e-3)
+    b_alg_iter = sum(alg.values())
+    out = {
+        "metric": METRIC, "value": it_s, "unit": "it/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": w.n, "width": W, "height": H, "sh_degree": w.sh_degree,
+                   "tile": "16x16", "pairs": pairs, "parallelism": f"replicas{world}",
+                   "l2": "no flush: per-step working set (params, grads, Adam moments, pairs, images) > 129 MB L2"},
+        "gaussian_pixel_evals_per_s": e_blend * it_s, "evals_blended_per_iter": e_blend,
+        "evals_tiled_per_iter": e_tiled,
+        "hbm_roofline_frac_iteration": b_alg_iter * it_s / world / (hbm_peak * 1e9),
+        "alg_bytes_per_iter": b_alg_iter,
+        "roofline": {"kernel": dom, "bound": "alu" if dom.startswith("raster") else "hbm",
+                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms},
+        "stages": per_stage,
+        "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "it/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 4, "host_wall_s": e2e_host_s},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "loss_end": loss_end,
+    }
+    return out
+
+
+def load_traffic(kernel):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, if
+    one exists for the current kernels (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get(kernel)
+    return None
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, n_pix, seed=0):
+    """Time the FP64 oracle: projection + forward + backward over n_pix random
+    pixels (prefilter mode) and the Adam update of all parameters; extrapolate
+    the per-pixel part to the full image.  Returns (seconds per iteration,
+    description)."""
+    import numpy as np
+    import torch
+
+    from oracle import adam as oadam
+    from oracle import render as R
+
+    v = w.views[0]
+    H, W = v.cam.height, v.cam.width
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, W, n_pix), rng.integers(0, H, n_pix)], 1)
+    wc = rng.standard_normal((3, n_pix))
+    wd = rng.standard_normal(n_pix)
+    Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
+    t0 = time.perf_counter()
+    P = R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
+    R.project(P, w.sh_degree, v.cam, Rm, t)
+    t_proj = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    R.weighted_pixel_gradients(w.params, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
+    t_pix = time.perf_counter() - t1
+    cfg = oadam.AdamCfg()
+    flat = oadam.flatten(w.params)
+    g = rng.standard_normal(flat.size)
+    lr = oadam.lr_per_element(w.n, w.sh_degree, cfg)
+    t2 = time.perf_counter()
+    oadam.adam_step(flat, g, np.zeros_like(flat), np.zeros_like(flat), 1, lr, cfg)
+    t_adam = time.perf_counter() - t2
+    per_pixel = max(t_pix - t_proj, 0.0) / n_pix
+    t_iter = t_proj + per_pixel * H * W + t_adam
+    desc = (f"oracle fwd+bwd on {n_pix} random pixels of the {W}x{H} view ({t_pix:.1f} s incl. a {t_proj:.1f} s "
+            f"projection of all {w.n} Gaussians), per-pixel time extrapolated to {H * W} pixels, plus one "
+            f"float64 Adam step over all parameters ({t_adam:.2f} s)")
+    return t_iter, desc, torch.get_num_threads()
+
+
+def run_reference(args):
+    from synth import workloads
+    w = workloads.single_view()
+    times = []
+    desc, cores = "", 0
+    for i in range(args.warmup + args.steps):
+        t_iter, desc, cores = oracle_sample(w, args.ref_pixels, seed=i)
+        if i >= args.warmup:
+            times.append(t_iter)
+    value = 1.0 / statistics.mean(times)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": w.n},
+        "cpu_baseline": {"value": value, "unit": "it/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-pixels", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            from synth import workloads
+            t_iter, desc, cores = oracle_sample(workloads.single_view(), args.ref_pixels)
+            out["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "it/s", "cores": cores, "kind": "oracle",
+                                   "sample": desc}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * gsplat.h -- C ABI of the GB300 (sm_103a) differentiable 3D Gaussian
+ * splatting hot path of GSFusion (arXiv 2408.12677): the tile-based
+ * rasterizer forward and backward pass and the Adam update of the Gaussian
+ * parameters (Sec. III-B.3 "Online Optimization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All array pointers are DEVICE pointers on the context's device, owned by
+ *   the caller, unless a comment says "host".  Float arrays are IEEE float32,
+ *   contiguous, row-major.  Images are planar: colour [3, H, W], depth, alpha
+ *   [H, W].
+ * - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *   default stream) except where noted.  Inputs must stay valid and
+ *   unmodified until the stream reaches the call.
+ * - Every function returns a gs_status; nothing is thrown across the ABI.
+ *   gs_last_error(ctx) gives a human-readable message for the last failure on
+ *   that context.  Argument checks happen on the host before any GPU work:
+ *   a call that returns GS_ERR_INVALID_ARG has enqueued nothing.
+ * - A context is bound to one device and is not thread-safe; use one context
+ *   per host thread.  It owns the scratch memory of the path (projected
+ *   features, sort buffers, per-tile ranges, per-pixel state); grow-on-demand
+ *   allocations use cudaMalloc.
+ * - Camera model (Eq. 4): a point p_w maps to p_c = R p_w + t (the viewmat is
+ *   the world-to-camera transform T_CW = T_WC^{-1}, R row-major) and projects
+ *   to (fx x/z + cx, fy y/z + cy); pixel (i, j) has its centre at
+ *   (i + 0.5, j + 0.5).  Camera x right, y down, z forward.
+ * - Gaussian parameters (Eq. 1-2 and Sec. III-A.2), N Gaussians, SH degree
+ *   d in {0, 1, 2, 3}, K = (d + 1)^2 coefficients per colour channel:
+ *     means [N, 3], log_scales [N, 3] (S = diag(exp(log_s))),
+ *     quats [N, 4] (w, x, y, z; normalised inside), opacity_logits [N]
+ *     (opacity = sigmoid), sh [N, K, 3] (real SH basis with the
+ *     Condon-Shortley phase, colour = max(0, 0.5 + sum_k Y_k(dir) sh_k),
+ *     dir = unit vector from the camera centre to the mean).
+ *   The flat layout used by gs_adam_step is these five arrays back to back
+ *   in that order: N * (11 + 3K) floats.
+ */
+#ifndef GSPLAT_H
+#define GSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GSPLAT_ABI_VERSION 1
+
+typedef struct CUstream_st *gs_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* bad pointer, size or configuration; nothing enqueued */
+  GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in gs_last_error) */
+  GS_ERR_CAPACITY = 3,    /* (tile, Gaussian) pairs exceeded the reserved capacity in no-sync mode */
+  GS_ERR_NONFINITE = 4,   /* reserved: non-finite inputs detected */
+  GS_ERR_BOUNDS = 5,      /* reserved: device-side bounds check failed */
+  GS_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait gave up */
+  GS_ERR_OOM = 7,         /* cudaMalloc of context scratch failed */
+  GS_ERR_STATE = 8        /* gs_render_bwd without a matching gs_render_fwd on this context */
+} gs_status;
+
+typedef struct {
+  float fx, fy, cx, cy;   /* pinhole intrinsics in pixels */
+  int32_t width, height;  /* image size in pixels, each in [1, 65535 * tile size] */
+} gs_camera;
+
+typedef struct {
+  float R[9]; /* world-to-camera rotation, row-major */
+  float t[3]; /* world-to-camera translation */
+} gs_viewmat;
+
+typedef struct {
+  const float *means, *log_scales, *quats, *opacity_logits, *sh; /* device, see layout above */
+  int64_t n;          /* number of Gaussians, 0 <= n < 2^31 */
+  int32_t sh_degree;  /* 0..3 */
+} gs_gaussians;
+
+typedef struct {
+  float *means, *log_scales, *quats, *opacity_logits, *sh; /* device; gradients are ACCUMULATED (+=) */
+} gs_grads;
+
+typedef struct {
+  int32_t tile_w, tile_h; /* 16x16, 8x32 or 32x8 */
+  int32_t batch;          /* Gaussians staged in shared memory per step: 256 */
+  float bg[3];            /* background colour added with the final transmittance */
+  float near_z;           /* cull Gaussians with camera z <= near_z (0.2) */
+  float alpha_max;        /* opacity clamp (0.99) */
+  float alpha_min;        /* skip contributions below this alpha (1/255) */
+  float t_eps;            /* stop before the Gaussian that would push T below this (1e-4) */
+  float dilation;         /* added to the 2D covariance diagonal, px^2 (0.3) */
+} gs_raster_cfg;
+
+typedef struct {
+  float lr_means, lr_log_scales, lr_quats, lr_opacity, lr_sh_dc, lr_sh_rest;
+  float beta1, beta2, eps;
+  int32_t zero_grads; /* 1: gs_adam_step writes 0 to every gradient it consumed */
+} gs_adam_cfg;
+
+typedef struct {
+  int64_t n_pairs;          /* (tile, Gaussian) pairs of the last forward pass (-1 in no-sync mode) */
+  int64_t pair_capacity;    /* pairs the context can hold without growing */
+  int64_t kernel_launches;  /* kernels this context has launched since creation */
+  int64_t n_tiles;          /* tiles of the last forward pass */
+  int64_t evals_blended;    /* (pixel, Gaussian) pairs blended, summed over forward passes since the last reset */
+  int64_t evals_tiled;      /* (pixel, list entry) visits of the forward raster loop, same period */
+} gs_stats;
+
+/* Stages timed by the optional profiler (CUDA events on the launch stream). */
+typedef enum {
+  GS_STAGE_PROJECT_FWD = 0,
+  GS_STAGE_DEPTH_SORT,
+  GS_STAGE_DUPLICATE,
+  GS_STAGE_PAIR_SORT,
+  GS_STAGE_RANGES,
+  GS_STAGE_RASTER_FWD,
+  GS_STAGE_LOSS,
+  GS_STAGE_RASTER_BWD,
+  GS_STAGE_PROJECT_BWD,
+  GS_STAGE_ADAM,
+  GS_NUM_STAGES
+} gs_stage;
+
+typedef struct gs_ctx gs_ctx;
+
+/* Create a context on CUDA device `device`.  `pair_capacity` pre-sizes the
+ * (tile, Gaussian) pair buffers (0 = grow on demand).  *ctx receives the
+ * handle.  Sync mode is on: each forward pass reads the pair count back to
+ * the host once and grows the pair buffers as needed. */
+gs_status gs_ctx_create(gs_ctx **ctx, int device, int64_t pair_capacity);
+
+/* Free the context and all scratch it owns.  Synchronises its device. */
+gs_status gs_ctx_destroy(gs_ctx *ctx);
+
+/* Last error message of this context ("" if none).  Owned by the context. */
+const char *gs_last_error(const gs_ctx *ctx);
+
+/* Pre-size scratch for up to n Gaussians, width*height pixels and n_pairs
+ * pairs (each 0 = leave as is), e.g. before capturing a CUDA graph. */
+gs_status gs_ctx_reserve(gs_ctx *ctx, int64_t n_gaussians, int64_t n_pixels, int64_t n_pairs);
+
+/* sync = 1 (default): the forward pass reads the pair count to the host and
+ * grows buffers.  sync = 0: no host synchronisation inside the forward pass
+ * (stream-capturable); pairs beyond the reserved capacity are dropped and
+ * the next gs_render_fwd / gs_sync_status reports GS_ERR_CAPACITY. */
+gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
+
+/* Synchronise the stream, then report GS_ERR_CAPACITY if a no-sync forward
+ * pass overflowed the pair buffers (and clear the flag). */
+gs_status gs_sync_status(gs_ctx *ctx, gs_stream_t stream);
+
+/* Counters of this context (host struct).  The two eval counters live on the
+ * device: this call synchronises the device when counting is on. */
+gs_status gs_get_stats(gs_ctx *ctx, gs_stats *out);
+
+/* counting = 1 makes every forward pass add its blended and visited
+ * (pixel, Gaussian) counts to two device counters (one atomic per CTA);
+ * also zeroes them.  Off by default. */
+gs_status gs_set_eval_counting(gs_ctx *ctx, int counting);
+
+/* profiling = 1: record a CUDA event pair around every stage launched on the
+ * call's stream and accumulate the elapsed times; also clears the totals.
+ * gs_profile_read synchronises the device and returns, per gs_stage, the
+ * summed milliseconds and the number of timed launches (host arrays of
+ * GS_NUM_STAGES). */
+gs_status gs_set_profiling(gs_ctx *ctx, int profiling);
+gs_status gs_profile_read(gs_ctx *ctx, double *ms, int64_t *count);
+
+/* Default configurations (host structs): 16x16 tiles, batch 256, bg 0,
+ * near 0.2, alpha in [1/255, 0.99], T_eps 1e-4, dilation 0.3; Adam
+ * beta = (0.9, 0.999), eps 1e-15, lr means 1.6e-4, log-scales 5e-3,
+ * quats 1e-3, opacity 5e-2, SH DC 2.5e-3, SH rest 1.25e-4, zero_grads 0. */
+gs_status gs_raster_cfg_default(gs_raster_cfg *cfg);
+gs_status gs_adam_cfg_default(gs_adam_cfg *cfg);
+
+/* Forward pass (Eq. 2-5 projection, tile binning with per-tile depth sort,
+ * Eq. 11 front-to-back compositing; Sec. III-B.3).  Writes colour [3, H, W],
+ * depth [H, W] (sum z_i w_i, camera z of the means) and alpha [H, W]
+ * (1 - final transmittance).  Any of the three outputs may be NULL.  Keeps
+ * the per-pixel final transmittance and last-contributor index, the
+ * projected features and the sorted per-tile lists in the context for
+ * gs_render_bwd; they stay valid until the next forward call on the context. */
+gs_status gs_render_fwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam,
+                        const gs_viewmat *view, const gs_raster_cfg *cfg,
+                        float *color, float *depth, float *alpha, gs_stream_t stream);
+
+/* Backward pass of the most recent gs_render_fwd on this context (same g,
+ * cam, view, cfg; GS_ERR_STATE otherwise).  Walks every tile list back to
+ * front from the stored last contributor, recomputing transmittance from the
+ * stored final T.  dL_dcolor [3, H, W] and dL_ddepth [H, W] are required,
+ * dL_dalpha [H, W] may be NULL.  Gradients w.r.t. every parameter array are
+ * ADDED to `grads` (the caller zeroes them).  dL_dpose (device float[6],
+ * nullable) receives += the gradient w.r.t. xi = (rho, phi) of the left
+ * perturbation T_CW(xi) = exp(xi^) T_CW at xi = 0. */
+gs_status gs_render_bwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam,
+                        const gs_viewmat *view, const gs_raster_cfg *cfg,
+                        const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,
+                        const gs_grads *grads, float *dL_dpose, gs_stream_t stream);
+
+/* Photometric loss (Eq. 12) plus a depth term:
+ *   L = w_color * mean over 3HW of |color - target_rgb|
+ *     + w_depth * mean over pixels with target_depth > 0 of |depth - target_depth|.
+ * Writes L to loss (device float[1]) and dL/dcolor, dL/ddepth (sign(0) = 0). */
+gs_status gs_loss_l1(gs_ctx *ctx, const gs_camera *cam, const float *color, const float *depth,
+                     const float *target_rgb, const float *target_depth, float w_color, float w_depth,
+                     float *loss, float *dL_dcolor, float *dL_ddepth, gs_stream_t stream);
+
+/* One dense Adam step over the flat parameter buffer (layout above):
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= lr_group * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * The paper optimises "using the gradient descent method" (Sec. III-B.3);
+ * Adam is the optimiser used here.  step >= 1.  params, m, v updated in
+ * place; grads read, and cleared to 0 when cfg->zero_grads is 1 (ready for
+ * the next accumulating gs_render_bwd). */
+gs_status gs_adam_step(gs_ctx *ctx, float *params, float *grads, float *m, float *v,
+                       int64_t n, int32_t sh_degree, const gs_adam_cfg *cfg, int64_t step,
+                       gs_stream_t stream);
+
+/* The tile-binning stage on its own (Sec. III-B.3: tiles, per-tile depth
+ * order), for exact checks: per Gaussian mean2d [n, 2], support half-extents
+ * extent [n, 2] (a Gaussian takes part iff both are > 0) and depth [n] (> 0).
+ * With tw, th powers of two, TX = ceil(W / tw), TY = ceil(H / th) and float32
+ * arithmetic, a Gaussian covers tiles [x0, x1) x [y0, y1),
+ *   x0 = clamp(floor((mx - ex) / tw), 0, TX), x1 = clamp(floor((mx + ex) / tw) + 1, 0, TX).
+ * Outputs: keys [P] = (tile << 32) | bits(depth), ids [P] sorted by key with
+ * ties in index order, ranges [TX * TY, 2] = [first, last + 1) per tile
+ * ((0, 0) if empty), *n_pairs (host) = P.  Returns GS_ERR_CAPACITY (and sets
+ * *n_pairs) if P > pair_capacity (keys/ids then untouched).  Synchronises. */
+gs_status gs_bin_tiles(gs_ctx *ctx, int64_t n, const float *mean2d, const float *extent,
+                       const float *depth, int32_t width, int32_t height, int32_t tile_w, int32_t tile_h,
+                       uint64_t *keys, uint32_t *ids, uint32_t *ranges, int64_t pair_capacity,
+                       int64_t *n_pairs, gs_stream_t stream);
+
+/* Copy the last forward pass's projected per-Gaussian quantities to caller
+ * buffers (each nullable): mean2d [n, 2] (high part of a double-float),
+ * cov2d [n, 3] (a, b, c of the dilated 2D covariance [[a, b], [b, c]]),
+ * depth [n], rgb [n, 3], opacity [n], tiles [n] (int32 tiles touched; 0 =
+ * culled).  For parity checks of the projection step. */
+gs_status gs_get_projection(gs_ctx *ctx, float *mean2d, float *cov2d, float *depth, float *rgb,
+                            float *opacity, int32_t *tiles, gs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSPLAT_H */

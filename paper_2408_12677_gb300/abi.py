@@ -1,0 +1,290 @@
+"""ctypes binding of libgsplat (include/gsplat.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch CUDA tensors (or plain ints / floats) where the C function takes device
+pointers.  No computation happens in Python: every step of the path runs in
+the library's kernels.  Loading fails loudly when libgsplat.so is missing;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsplat.so")
+
+GS_OK = 0
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_NONFINITE",
+                5: "GS_ERR_BOUNDS", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_OOM", 8: "GS_ERR_STATE"}
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gs_viewmat(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3)]
+
+
+class gs_gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+
+
+class gs_grads(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class gs_raster_cfg(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32), ("bg", C.c_float * 3),
+                ("near_z", C.c_float), ("alpha_max", C.c_float), ("alpha_min", C.c_float), ("t_eps", C.c_float),
+                ("dilation", C.c_float)]
+
+
+class gs_adam_cfg(C.Structure):
+    _fields_ = [("lr_means", C.c_float), ("lr_log_scales", C.c_float), ("lr_quats", C.c_float),
+                ("lr_opacity", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("zero_grads", C.c_int32)]
+
+
+class gs_stats(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("pair_capacity", C.c_int64), ("kernel_launches", C.c_int64),
+                ("n_tiles", C.c_int64), ("evals_blended", C.c_int64), ("evals_tiled", C.c_int64)]
+
+
+STAGES = ("project_fwd", "depth_sort", "duplicate", "pair_sort", "ranges", "raster_fwd", "loss", "raster_bwd",
+          "project_bwd", "adam")
+
+
+P = C.c_void_p
+EXPORTS = {
+    "gs_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int64]),
+    "gs_ctx_destroy": (C.c_int, [P]),
+    "gs_last_error": (C.c_char_p, [P]),
+    "gs_ctx_reserve": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
+    "gs_ctx_set_sync": (C.c_int, [P, C.c_int]),
+    "gs_sync_status": (C.c_int, [P, P]),
+    "gs_get_stats": (C.c_int, [P, C.POINTER(gs_stats)]),
+    "gs_raster_cfg_default": (C.c_int, [C.POINTER(gs_raster_cfg)]),
+    "gs_adam_cfg_default": (C.c_int, [C.POINTER(gs_adam_cfg)]),
+    "gs_render_fwd": (C.c_int, [P, C.POINTER(gs_gaussians), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                                C.POINTER(gs_raster_cfg), P, P, P, P]),
+    "gs_render_bwd": (C.c_int, [P, C.POINTER(gs_gaussians), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                                C.POINTER(gs_raster_cfg), P, P, P, C.POINTER(gs_grads), P, P]),
+    "gs_loss_l1": (C.c_int, [P, C.POINTER(gs_camera), P, P, P, P, C.c_float, C.c_float, P, P, P, P]),
+    "gs_adam_step": (C.c_int, [P, P, P, P, P, C.c_int64, C.c_int32, C.POINTER(gs_adam_cfg), C.c_int64, P]),
+    "gs_bin_tiles": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int64,
+                               C.POINTER(C.c_int64), P]),
+    "gs_get_projection": (C.c_int, [P, P, P, P, P, P, P, P]),
+    "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
+    "gs_set_profiling": (C.c_int, [P, C.c_int]),
+    "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libgsplat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgsplat.so not found at {path}; run __graft_entry__.build() first")
+        lib = C.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _f32(t, name):
+    if t is not None and t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    return _ptr(t)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(ctx, status: int, where: str):
+    if status != GS_OK:
+        msg = load().gs_last_error(ctx).decode() if ctx else ""
+        raise GsError(status, where, msg)
+
+
+# ---------------------------------------------------------------------------
+# struct builders
+# ---------------------------------------------------------------------------
+def make_camera(fx, fy, cx, cy, width, height) -> gs_camera:
+    return gs_camera(float(fx), float(fy), float(cx), float(cy), int(width), int(height))
+
+
+def make_viewmat(R, t) -> gs_viewmat:
+    v = gs_viewmat()
+    Rf = [float(x) for x in torch.as_tensor(R).reshape(-1).tolist()]
+    tf = [float(x) for x in torch.as_tensor(t).reshape(-1).tolist()]
+    v.R = (C.c_float * 9)(*Rf)
+    v.t = (C.c_float * 3)(*tf)
+    return v
+
+
+def raster_cfg(**overrides) -> gs_raster_cfg:
+    c = gs_raster_cfg()
+    load().gs_raster_cfg_default(C.byref(c))
+    for k, v in overrides.items():
+        if k == "bg":
+            c.bg = (C.c_float * 3)(*[float(x) for x in v])
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def adam_cfg(**overrides) -> gs_adam_cfg:
+    c = gs_adam_cfg()
+    load().gs_adam_cfg_default(C.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def make_gaussians(means, log_scales, quats, opacity_logits, sh, sh_degree: int) -> gs_gaussians:
+    n = means.shape[0]
+    return gs_gaussians(_f32(means, "means"), _f32(log_scales, "log_scales"), _f32(quats, "quats"),
+                        _f32(opacity_logits, "opacity_logits"), _f32(sh, "sh"), int(n), int(sh_degree))
+
+
+def make_grads(means, log_scales, quats, opacity_logits, sh) -> gs_grads:
+    return gs_grads(_f32(means, "means"), _f32(log_scales, "log_scales"), _f32(quats, "quats"),
+                    _f32(opacity_logits, "opacity_logits"), _f32(sh, "sh"))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def gs_ctx_create(device: int = 0, pair_capacity: int = 0) -> int:
+    h = C.c_void_p()
+    st = load().gs_ctx_create(C.byref(h), int(device), int(pair_capacity))
+    _check(None, st, "gs_ctx_create")
+    return h.value
+
+
+def gs_ctx_destroy(ctx: int) -> None:
+    _check(None, load().gs_ctx_destroy(ctx), "gs_ctx_destroy")
+
+
+def gs_last_error(ctx: int) -> str:
+    return load().gs_last_error(ctx).decode()
+
+
+def gs_ctx_reserve(ctx, n_gaussians=0, n_pixels=0, n_pairs=0):
+    _check(ctx, load().gs_ctx_reserve(ctx, int(n_gaussians), int(n_pixels), int(n_pairs)), "gs_ctx_reserve")
+
+
+def gs_ctx_set_sync(ctx, sync: bool):
+    _check(ctx, load().gs_ctx_set_sync(ctx, int(bool(sync))), "gs_ctx_set_sync")
+
+
+def gs_sync_status(ctx, stream=None):
+    _check(ctx, load().gs_sync_status(ctx, _stream(stream)), "gs_sync_status")
+
+
+def gs_get_stats(ctx) -> dict:
+    s = gs_stats()
+    _check(ctx, load().gs_get_stats(ctx, C.byref(s)), "gs_get_stats")
+    return {k: getattr(s, k) for k, _ in gs_stats._fields_}
+
+
+def gs_set_eval_counting(ctx, counting: bool):
+    _check(ctx, load().gs_set_eval_counting(ctx, int(bool(counting))), "gs_set_eval_counting")
+
+
+def gs_set_profiling(ctx, profiling: bool):
+    _check(ctx, load().gs_set_profiling(ctx, int(bool(profiling))), "gs_set_profiling")
+
+
+def gs_profile_read(ctx) -> dict:
+    """{stage: (total ms, launches)} since profiling was switched on / last read."""
+    ms = (C.c_double * len(STAGES))()
+    cnt = (C.c_int64 * len(STAGES))()
+    _check(ctx, load().gs_profile_read(ctx, ms, cnt), "gs_profile_read")
+    return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
+
+
+def gs_render_fwd(ctx, gaussians: gs_gaussians, cam: gs_camera, view: gs_viewmat, cfg: gs_raster_cfg,
+                  color=None, depth=None, alpha=None, stream=None):
+    st = load().gs_render_fwd(ctx, C.byref(gaussians), C.byref(cam), C.byref(view), C.byref(cfg),
+                              _f32(color, "color"), _f32(depth, "depth"), _f32(alpha, "alpha"), _stream(stream))
+    _check(ctx, st, "gs_render_fwd")
+
+
+def gs_render_bwd(ctx, gaussians, cam, view, cfg, dL_dcolor, dL_ddepth, dL_dalpha, grads: gs_grads,
+                  dL_dpose=None, stream=None):
+    st = load().gs_render_bwd(ctx, C.byref(gaussians), C.byref(cam), C.byref(view), C.byref(cfg),
+                              _f32(dL_dcolor, "dL_dcolor"), _f32(dL_ddepth, "dL_ddepth"),
+                              _f32(dL_dalpha, "dL_dalpha"), C.byref(grads), _f32(dL_dpose, "dL_dpose"),
+                              _stream(stream))
+    _check(ctx, st, "gs_render_bwd")
+
+
+def gs_loss_l1(ctx, cam, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor, dL_ddepth,
+               stream=None):
+    st = load().gs_loss_l1(ctx, C.byref(cam), _f32(color, "color"), _f32(depth, "depth"),
+                           _f32(target_rgb, "target_rgb"), _f32(target_depth, "target_depth"), float(w_color),
+                           float(w_depth), _f32(loss, "loss"), _f32(dL_dcolor, "dL_dcolor"),
+                           _f32(dL_ddepth, "dL_ddepth"), _stream(stream))
+    _check(ctx, st, "gs_loss_l1")
+
+
+def gs_adam_step(ctx, params, grads, m, v, n: int, sh_degree: int, cfg: gs_adam_cfg, step: int, stream=None):
+    st = load().gs_adam_step(ctx, _f32(params, "params"), _f32(grads, "grads"), _f32(m, "m"), _f32(v, "v"), int(n),
+                             int(sh_degree), C.byref(cfg), int(step), _stream(stream))
+    _check(ctx, st, "gs_adam_step")
+
+
+def gs_bin_tiles(ctx, mean2d, extent, depth, width, height, tile_w, tile_h, keys, ids, ranges, stream=None) -> int:
+    n = mean2d.shape[0]
+    cap = 0 if keys is None else keys.numel()
+    npairs = C.c_int64(0)
+    st = load().gs_bin_tiles(ctx, int(n), _f32(mean2d, "mean2d"), _f32(extent, "extent"), _f32(depth, "depth"),
+                             int(width), int(height), int(tile_w), int(tile_h), _ptr(keys), _ptr(ids), _ptr(ranges),
+                             int(cap), C.byref(npairs), _stream(stream))
+    if st == 3:  # capacity: report the size needed
+        return -int(npairs.value) - 1
+    _check(ctx, st, "gs_bin_tiles")
+    return int(npairs.value)
+
+
+def gs_get_projection(ctx, mean2d=None, cov2d=None, depth=None, rgb=None, opacity=None, tiles=None, stream=None):
+    st = load().gs_get_projection(ctx, _f32(mean2d, "mean2d"), _f32(cov2d, "cov2d"), _f32(depth, "depth"),
+                                  _f32(rgb, "rgb"), _f32(opacity, "opacity"), _ptr(tiles), _stream(stream))
+    _check(ctx, st, "gs_get_projection")

@@ -1,0 +1,777 @@
+// C ABI of libgsplat: context and scratch management, argument checks and
+// the orchestration of the projection, binning, raster, loss and Adam
+// kernels.  See include/gsplat.h for the contract of every entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gsplat.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace gs;
+
+struct gs_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  bool sync = true;
+  int64_t launches = 0;
+
+  // per-Gaussian scratch
+  int64_t cap_n = 0;
+  float4* feat = nullptr;
+  uint32_t* zkey = nullptr;  // per-Gaussian depth key (float32 bits of z)
+  uint32_t* dkey[2] = {nullptr, nullptr};
+  uint32_t* dval[2] = {nullptr, nullptr};
+  uint32_t* tiles = nullptr;
+  ushort4* rects = nullptr;
+  float4* g2d = nullptr;
+  uint32_t* dup_sums = nullptr;
+  float* pose_partials = nullptr;
+  // per-pair scratch
+  int64_t cap_p = 0;
+  uint32_t* pk[2] = {nullptr, nullptr};
+  uint32_t* pv[2] = {nullptr, nullptr};
+  // radix histograms
+  uint32_t* hist = nullptr;
+  int hist_blocks = 0;
+  // per-tile / per-pixel scratch
+  int64_t cap_t = 0;
+  uint2* ranges = nullptr;
+  int64_t cap_px = 0;
+  float* T_final = nullptr;
+  int32_t* last = nullptr;
+  float* loss_partials = nullptr;
+  // device scalars and their host mirror
+  uint32_t* d_npairs = nullptr;
+  unsigned long long* d_npairs_full = nullptr;
+  uint32_t* d_overflow = nullptr;
+  unsigned long long* h_pinned = nullptr;
+  // eval counters (blended, visited) and per-stage event profiling
+  bool counting = false;
+  unsigned long long* d_evals = nullptr;
+  bool profiling = false;
+  struct Ev {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> evs;
+  size_t ev_used = 0;
+
+  // state of the last forward pass
+  bool have_state = false;
+  int64_t st_n = 0;
+  int st_w = 0, st_h = 0, st_tw = 0, st_th = 0, st_tx = 0, st_ty = 0;
+  int64_t st_pairs = 0;
+  int st_pair_buf = 0;
+  int st_sh = 0;
+};
+
+namespace {
+
+// Records a CUDA event pair around the launches of one stage when profiling.
+struct StageTimer {
+  gs_ctx* c;
+  cudaStream_t s;
+  size_t idx = (size_t)-1;
+  StageTimer(gs_ctx* ctx, int stage, cudaStream_t stream) : c(ctx), s(stream) {
+    if (!c->profiling) return;
+    if (c->ev_used == c->evs.size()) {
+      gs_ctx::Ev e{stage, nullptr, nullptr};
+      if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
+      c->evs.push_back(e);
+    }
+    idx = c->ev_used++;
+    c->evs[idx].stage = stage;
+    cudaEventRecord(c->evs[idx].a, s);
+  }
+  ~StageTimer() {
+    if (idx != (size_t)-1) cudaEventRecord(c->evs[idx].b, s);
+  }
+};
+
+gs_status fail(gs_ctx* c, gs_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+gs_status cuda_fail(gs_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GS_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+#define GS_CHECK_LAUNCH(ctx, where)                           \
+  do {                                                        \
+    cudaError_t e_ = cudaGetLastError();                      \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);   \
+  } while (0)
+
+template <class T>
+cudaError_t regrow(T** p, int64_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count <= 0) return cudaSuccess;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+}
+
+int64_t grow_target(int64_t need, int64_t have) { return std::max<int64_t>(need + need / 4 + 1024, have); }
+
+gs_status ensure_n(gs_ctx* c, int64_t n) {
+  if (n <= c->cap_n) return GS_OK;
+  const int64_t cap = grow_target(n, c->cap_n);
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  GS_CUDA(c, regrow(&c->feat, 3 * cap));
+  GS_CUDA(c, regrow(&c->zkey, cap));
+  for (int k = 0; k < 2; ++k) {
+    GS_CUDA(c, regrow(&c->dkey[k], cap));
+    GS_CUDA(c, regrow(&c->dval[k], cap));
+  }
+  GS_CUDA(c, regrow(&c->tiles, cap));
+  GS_CUDA(c, regrow(&c->rects, cap));
+  GS_CUDA(c, regrow(&c->g2d, 3 * cap));
+  GS_CUDA(c, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
+  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((int64_t)project_bwd_blocks((int)cap) + 1)));
+  c->cap_n = cap;
+  c->have_state = false;
+  return GS_OK;
+}
+
+gs_status ensure_pairs(gs_ctx* c, int64_t p) {
+  if (p <= c->cap_p) return GS_OK;
+  if (p > 0xFFFFFFF0ll) return fail(c, GS_ERR_CAPACITY, "more than 2^32 - 16 (tile, Gaussian) pairs");
+  const int64_t cap = std::min<int64_t>(grow_target(p, c->cap_p), 0xFFFFFFF0ll);
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  for (int k = 0; k < 2; ++k) {
+    GS_CUDA(c, regrow(&c->pk[k], cap));
+    GS_CUDA(c, regrow(&c->pv[k], cap));
+  }
+  c->cap_p = cap;
+  c->have_state = false;
+  return GS_OK;
+}
+
+gs_status ensure_tiles(gs_ctx* c, int64_t t) {
+  if (t <= c->cap_t) return GS_OK;
+  GS_CUDA(c, cudaDeviceSynchronize());
+  const int64_t cap = grow_target(t, c->cap_t);
+  GS_CUDA(c, regrow(&c->ranges, cap));
+  c->cap_t = cap;
+  c->have_state = false;
+  return GS_OK;
+}
+
+gs_status ensure_px(gs_ctx* c, int64_t npx) {
+  if (npx <= c->cap_px) return GS_OK;
+  GS_CUDA(c, cudaDeviceSynchronize());
+  const int64_t cap = grow_target(npx, c->cap_px);
+  GS_CUDA(c, regrow(&c->T_final, cap));
+  GS_CUDA(c, regrow(&c->last, cap));
+  GS_CUDA(c, regrow(&c->loss_partials, 3 * (int64_t)loss_blocks((int)cap) + 4));
+  c->cap_px = cap;
+  c->have_state = false;
+  return GS_OK;
+}
+
+int bits_for(int64_t n) {
+  int b = 0;
+  while (b < 40 && (int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+gs_status check_cam(gs_ctx* c, const gs_camera* cam) {
+  if (!cam) return fail(c, GS_ERR_INVALID_ARG, "camera is NULL");
+  if (cam->width < 1 || cam->height < 1) return fail(c, GS_ERR_INVALID_ARG, "camera width/height must be >= 1");
+  if ((int64_t)cam->width * cam->height > (int64_t)1 << 30)
+    return fail(c, GS_ERR_INVALID_ARG, "image larger than 2^30 pixels");
+  if (!finite_pos(cam->fx) || !finite_pos(cam->fy) || !std::isfinite(cam->cx) || !std::isfinite(cam->cy))
+    return fail(c, GS_ERR_INVALID_ARG, "camera intrinsics must be finite with fx, fy > 0");
+  return GS_OK;
+}
+
+gs_status check_cfg(gs_ctx* c, const gs_raster_cfg* cfg) {
+  if (!cfg) return fail(c, GS_ERR_INVALID_ARG, "raster cfg is NULL");
+  if (!raster_shape_supported(cfg->tile_w, cfg->tile_h))
+    return fail(c, GS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x32 or 32x8");
+  if (cfg->batch != 256) return fail(c, GS_ERR_INVALID_ARG, "batch must be 256");
+  if (!(cfg->alpha_max > 0.f && cfg->alpha_max < 1.f) || !(cfg->alpha_min > 0.f && cfg->alpha_min < cfg->alpha_max) ||
+      !(cfg->t_eps > 0.f && cfg->t_eps < 1.f) || !(cfg->dilation >= 0.f) || !std::isfinite(cfg->near_z))
+    return fail(c, GS_ERR_INVALID_ARG, "raster thresholds out of range");
+  return GS_OK;
+}
+
+gs_status check_gauss(gs_ctx* c, const gs_gaussians* g) {
+  if (!g) return fail(c, GS_ERR_INVALID_ARG, "gaussians is NULL");
+  if (g->n < 0 || g->n >= ((int64_t)1 << 31)) return fail(c, GS_ERR_INVALID_ARG, "n out of range");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return fail(c, GS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return fail(c, GS_ERR_INVALID_ARG, "a Gaussian parameter pointer is NULL");
+  return GS_OK;
+}
+
+CamView make_camview(const gs_camera* cam, const gs_viewmat* v) {
+  CamView cv;
+  cv.fx = cam->fx;
+  cv.fy = cam->fy;
+  cv.cx = cam->cx;
+  cv.cy = cam->cy;
+  cv.width = cam->width;
+  cv.height = cam->height;
+  for (int k = 0; k < 9; ++k) cv.R[k] = v->R[k];
+  for (int k = 0; k < 3; ++k) cv.t[k] = v->t[k];
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (int r = 0; r < 3; ++r) s += (double)v->R[3 * r + c] * (double)v->t[r];
+    cv.C[c] = (float)(-s);
+  }
+  return cv;
+}
+
+gs_status ensure_hist(gs_ctx* c) {
+  const int want = 4 * std::max(c->num_sms, 1);
+  if (c->hist && c->hist_blocks >= want) return GS_OK;
+  GS_CUDA(c, regrow(&c->hist, (int64_t)256 * want));
+  c->hist_blocks = want;
+  return GS_OK;
+}
+
+// Depth sort of n Gaussians (keys in zkey, ids implicit), duplication into
+// pairs, pair sort by tile, tile ranges.  On success c->st_pairs / st_pair_buf
+// describe the sorted pair list.
+gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
+  const int64_t T = (int64_t)tiles_x * tiles_y;
+  if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
+  SortBuffers sb;
+  sb.keys[0] = c->dkey[0];
+  sb.keys[1] = c->dkey[1];
+  sb.vals[0] = c->dval[0];
+  sb.vals[1] = c->dval[1];
+  sb.hist = c->hist;
+  sb.max_blocks = c->hist_blocks;
+  int dcur;
+  {
+    StageTimer t(c, GS_STAGE_DEPTH_SORT, s);
+    dcur = radix_sort_pairs(sb, c->zkey, nullptr, (uint32_t)n, nullptr, 32, c->num_sms, s, &c->launches);
+  }
+  const uint32_t* sorted_ids = dcur >= 0 ? c->dval[dcur] : c->dval[0];
+
+  DupArgs da;
+  da.n = n;
+  da.sorted_ids = sorted_ids;
+  da.tiles_touched = c->tiles;
+  da.rects = c->rects;
+  da.tiles_x = tiles_x;
+  da.block_sums = c->dup_sums;
+  da.n_pairs = c->d_npairs;
+  da.n_pairs_full = c->d_npairs_full;
+  da.tile_keys = nullptr;
+  da.vals = nullptr;
+  da.capacity = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFF0ll);
+  da.overflow = c->d_overflow;
+  // phase 1: counts and scan
+  {
+    StageTimer t(c, GS_STAGE_DUPLICATE, s);
+    launch_dup_count_scan(da, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "duplicate count/scan");
+  int64_t P = -1;
+  if (c->sync) {
+    GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_npairs_full, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    P = (int64_t)*c->h_pinned;
+    gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
+    if (st != GS_OK) return st;
+    da.capacity = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFF0ll);
+  } else if (c->cap_p == 0) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode needs reserved pair capacity (gs_ctx_reserve)");
+  }
+  da.tile_keys = c->pk[0];
+  da.vals = c->pv[0];
+  {
+    StageTimer t(c, GS_STAGE_DUPLICATE, s);
+    launch_dup_write(da, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "duplicate write");
+
+  SortBuffers pb;
+  pb.keys[0] = c->pk[0];
+  pb.keys[1] = c->pk[1];
+  pb.vals[0] = c->pv[0];
+  pb.vals[1] = c->pv[1];
+  pb.hist = c->hist;
+  pb.max_blocks = c->hist_blocks;
+  const uint32_t n_max = c->sync ? (uint32_t)P : (uint32_t)c->cap_p;
+  const uint32_t* n_dev = c->sync ? nullptr : c->d_npairs;
+  int pcur;
+  {
+    StageTimer t(c, GS_STAGE_PAIR_SORT, s);
+    pcur = radix_sort_pairs(pb, c->pk[0], c->pv[0], n_max, n_dev, bits_for(T), c->num_sms, s, &c->launches);
+  }
+  {
+    StageTimer t(c, GS_STAGE_RANGES, s);
+    launch_tile_ranges(c->pk[pcur], n_dev, n_max, c->ranges, (int)T, c->num_sms, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "pair sort / ranges");
+  c->st_pairs = c->sync ? P : -1;
+  c->st_pair_buf = pcur;
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_raster_cfg_default(gs_raster_cfg* cfg) {
+  if (!cfg) return GS_ERR_INVALID_ARG;
+  cfg->tile_w = 16;
+  cfg->tile_h = 16;
+  cfg->batch = 256;
+  cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
+  cfg->near_z = 0.2f;
+  cfg->alpha_max = 0.99f;
+  cfg->alpha_min = 1.f / 255.f;
+  cfg->t_eps = 1e-4f;
+  cfg->dilation = 0.3f;
+  return GS_OK;
+}
+
+gs_status gs_adam_cfg_default(gs_adam_cfg* cfg) {
+  if (!cfg) return GS_ERR_INVALID_ARG;
+  cfg->lr_means = 1.6e-4f;
+  cfg->lr_log_scales = 5e-3f;
+  cfg->lr_quats = 1e-3f;
+  cfg->lr_opacity = 5e-2f;
+  cfg->lr_sh_dc = 2.5e-3f;
+  cfg->lr_sh_rest = 1.25e-4f;
+  cfg->beta1 = 0.9f;
+  cfg->beta2 = 0.999f;
+  cfg->eps = 1e-15f;
+  cfg->zero_grads = 0;
+  return GS_OK;
+}
+
+gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
+  if (!out) return GS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device < 0 || pair_capacity < 0) return GS_ERR_INVALID_ARG;
+  gs_ctx* c = new gs_ctx();
+  c->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_npairs, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_npairs_full, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_overflow, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_evals, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_overflow, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 4 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    gs_ctx_destroy(c);
+    return e == cudaErrorMemoryAllocation ? GS_ERR_OOM : GS_ERR_CUDA;
+  }
+  if (ensure_hist(c) != GS_OK || (pair_capacity > 0 && ensure_pairs(c, pair_capacity) != GS_OK)) {
+    gs_ctx_destroy(c);
+    return GS_ERR_OOM;
+  }
+  *out = c;
+  return GS_OK;
+}
+
+gs_status gs_ctx_destroy(gs_ctx* c) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  cudaFree(c->feat);
+  cudaFree(c->zkey);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(c->dkey[k]);
+    cudaFree(c->dval[k]);
+    cudaFree(c->pk[k]);
+    cudaFree(c->pv[k]);
+  }
+  cudaFree(c->tiles);
+  cudaFree(c->rects);
+  cudaFree(c->g2d);
+  cudaFree(c->dup_sums);
+  cudaFree(c->pose_partials);
+  cudaFree(c->hist);
+  cudaFree(c->ranges);
+  cudaFree(c->T_final);
+  cudaFree(c->last);
+  cudaFree(c->loss_partials);
+  cudaFree(c->d_npairs);
+  cudaFree(c->d_npairs_full);
+  cudaFree(c->d_overflow);
+  cudaFree(c->d_evals);
+  for (auto& ev : c->evs) {
+    cudaEventDestroy(ev.a);
+    cudaEventDestroy(ev.b);
+  }
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return GS_OK;
+}
+
+const char* gs_last_error(const gs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gs_status gs_ctx_reserve(gs_ctx* c, int64_t n_gaussians, int64_t n_pixels, int64_t n_pairs) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (n_gaussians < 0 || n_pixels < 0 || n_pairs < 0) return fail(c, GS_ERR_INVALID_ARG, "negative reserve size");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  gs_status s = GS_OK;
+  if (n_gaussians > 0 && (s = ensure_n(c, n_gaussians)) != GS_OK) return s;
+  if (n_pixels > 0 && (s = ensure_px(c, n_pixels)) != GS_OK) return s;
+  if (n_pixels > 0 && (s = ensure_tiles(c, (n_pixels + 63) / 64 + 1024)) != GS_OK) return s;
+  if (n_pairs > 0 && (s = ensure_pairs(c, n_pairs)) != GS_OK) return s;
+  return GS_OK;
+}
+
+gs_status gs_ctx_set_sync(gs_ctx* c, int sync) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->sync = sync != 0;
+  return GS_OK;
+}
+
+gs_status gs_sync_status(gs_ctx* c, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned + 1, c->d_overflow, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned + 2, c->d_npairs_full, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  const uint32_t ov = (uint32_t)(c->h_pinned[1] & 0xFFFFFFFFull);
+  if (ov) {
+    GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    c->have_state = false;
+    return fail(c, GS_ERR_CAPACITY, "pair buffer overflow: needed " + std::to_string(c->h_pinned[2]) + " pairs");
+  }
+  return GS_OK;
+}
+
+gs_status gs_get_stats(gs_ctx* c, gs_stats* out) {
+  if (!c || !out) return GS_ERR_INVALID_ARG;
+  out->n_pairs = c->st_pairs;
+  out->pair_capacity = c->cap_p;
+  out->kernel_launches = c->launches;
+  out->n_tiles = (int64_t)c->st_tx * c->st_ty;
+  out->evals_blended = 0;
+  out->evals_tiled = 0;
+  if (c->counting) {
+    unsigned long long h[2] = {0, 0};
+    GS_CUDA(c, cudaSetDevice(c->device));
+    GS_CUDA(c, cudaDeviceSynchronize());
+    GS_CUDA(c, cudaMemcpy(h, c->d_evals, sizeof(h), cudaMemcpyDeviceToHost));
+    out->evals_blended = (int64_t)h[0];
+    out->evals_tiled = (int64_t)h[1];
+  }
+  return GS_OK;
+}
+
+gs_status gs_set_eval_counting(gs_ctx* c, int counting) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  GS_CUDA(c, cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long)));
+  c->counting = counting != 0;
+  return GS_OK;
+}
+
+gs_status gs_set_profiling(gs_ctx* c, int profiling) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  c->ev_used = 0;
+  c->profiling = profiling != 0;
+  return GS_OK;
+}
+
+gs_status gs_profile_read(gs_ctx* c, double* ms, int64_t* count) {
+  if (!c || !ms || !count) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  for (int k = 0; k < GS_NUM_STAGES; ++k) {
+    ms[k] = 0.0;
+    count[k] = 0;
+  }
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    float t = 0.f;
+    GS_CUDA(c, cudaEventElapsedTime(&t, c->evs[i].a, c->evs[i].b));
+    ms[c->evs[i].stage] += t;
+    count[c->evs[i].stage] += 1;
+  }
+  c->ev_used = 0;
+  return GS_OK;
+}
+
+gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, float* color, float* depth, float* alpha, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_gauss(c, g)) != GS_OK || (st = check_cam(c, cam)) != GS_OK || (st = check_cfg(c, cfg)) != GS_OK)
+    return st;
+  if (!view) return fail(c, GS_ERR_INVALID_ARG, "viewmat is NULL");
+  const int tiles_x = (cam->width + cfg->tile_w - 1) / cfg->tile_w;
+  const int tiles_y = (cam->height + cfg->tile_h - 1) / cfg->tile_h;
+  if (tiles_x > 65535 || tiles_y > 65535) return fail(c, GS_ERR_INVALID_ARG, "too many tiles per axis");
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const int n = (int)g->n;
+  const int64_t npx = (int64_t)cam->width * cam->height;
+  const int64_t T = (int64_t)tiles_x * tiles_y;
+  if (c->sync) {
+    if ((st = ensure_n(c, std::max(n, 1))) != GS_OK || (st = ensure_px(c, npx)) != GS_OK ||
+        (st = ensure_tiles(c, T)) != GS_OK)
+      return st;
+  } else if (n > c->cap_n || npx > c->cap_px || T > c->cap_t) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve Gaussians/pixels first (gs_ctx_reserve)");
+  }
+  c->have_state = false;
+
+  ProjectArgs pa;
+  pa.n = n;
+  pa.means = g->means;
+  pa.log_scales = g->log_scales;
+  pa.quats = g->quats;
+  pa.logits = g->opacity_logits;
+  pa.sh = g->sh;
+  pa.sh_degree = g->sh_degree;
+  pa.cv = make_camview(cam, view);
+  pa.near_z = cfg->near_z;
+  pa.dilation = cfg->dilation;
+  pa.alpha_min = cfg->alpha_min;
+  pa.tile_w = cfg->tile_w;
+  pa.tile_h = cfg->tile_h;
+  pa.tiles_x = tiles_x;
+  pa.tiles_y = tiles_y;
+  {
+    StageTimer t(c, GS_STAGE_PROJECT_FWD, s);
+    launch_project_fwd(pa, c->feat, c->zkey, c->tiles, c->rects, s);
+  }
+  if (n > 0) c->launches += 1;
+  GS_CHECK_LAUNCH(c, "project_fwd");
+
+  if ((st = bin_and_sort(c, n, tiles_x, tiles_y, s)) != GS_OK) return st;
+
+  RasterArgs ra;
+  ra.width = cam->width;
+  ra.height = cam->height;
+  ra.tile_w = cfg->tile_w;
+  ra.tile_h = cfg->tile_h;
+  ra.tiles_x = tiles_x;
+  ra.tiles_y = tiles_y;
+  for (int k = 0; k < 3; ++k) ra.bg[k] = cfg->bg[k];
+  ra.alpha_max = cfg->alpha_max;
+  ra.alpha_min = cfg->alpha_min;
+  ra.t_eps = cfg->t_eps;
+  ra.ranges = c->ranges;
+  ra.ids = c->pv[c->st_pair_buf];
+  ra.feat = c->feat;
+  {
+    StageTimer t(c, GS_STAGE_RASTER_FWD, s);
+    launch_raster_fwd(ra, color, depth, alpha, c->T_final, c->last, c->counting ? c->d_evals : nullptr, s);
+  }
+  c->launches += 1;
+  GS_CHECK_LAUNCH(c, "raster_fwd");
+
+  c->have_state = true;
+  c->st_n = n;
+  c->st_w = cam->width;
+  c->st_h = cam->height;
+  c->st_tw = cfg->tile_w;
+  c->st_th = cfg->tile_h;
+  c->st_tx = tiles_x;
+  c->st_ty = tiles_y;
+  c->st_sh = g->sh_degree;
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
+                        const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_gauss(c, g)) != GS_OK || (st = check_cam(c, cam)) != GS_OK || (st = check_cfg(c, cfg)) != GS_OK)
+    return st;
+  if (!view || !grads) return fail(c, GS_ERR_INVALID_ARG, "viewmat or grads is NULL");
+  if (!dL_dcolor || !dL_ddepth) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
+  if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
+    return fail(c, GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+  if (!c->have_state || c->st_n != g->n || c->st_w != cam->width || c->st_h != cam->height ||
+      c->st_tw != cfg->tile_w || c->st_th != cfg->tile_h || c->st_sh != g->sh_degree)
+    return fail(c, GS_ERR_STATE, "gs_render_bwd needs the matching gs_render_fwd on this context");
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const int n = (int)g->n;
+  if (n == 0) return GS_OK;
+  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)n, s));
+
+  RasterArgs ra;
+  ra.width = cam->width;
+  ra.height = cam->height;
+  ra.tile_w = cfg->tile_w;
+  ra.tile_h = cfg->tile_h;
+  ra.tiles_x = c->st_tx;
+  ra.tiles_y = c->st_ty;
+  for (int k = 0; k < 3; ++k) ra.bg[k] = cfg->bg[k];
+  ra.alpha_max = cfg->alpha_max;
+  ra.alpha_min = cfg->alpha_min;
+  ra.t_eps = cfg->t_eps;
+  ra.ranges = c->ranges;
+  ra.ids = c->pv[c->st_pair_buf];
+  ra.feat = c->feat;
+  {
+    StageTimer t(c, GS_STAGE_RASTER_BWD, s);
+    launch_raster_bwd(ra, c->T_final, c->last, dL_dcolor, dL_ddepth, dL_dalpha, c->g2d, s);
+  }
+  c->launches += 1;
+  GS_CHECK_LAUNCH(c, "raster_bwd");
+
+  ProjectArgs pa;
+  pa.n = n;
+  pa.means = g->means;
+  pa.log_scales = g->log_scales;
+  pa.quats = g->quats;
+  pa.logits = g->opacity_logits;
+  pa.sh = g->sh;
+  pa.sh_degree = g->sh_degree;
+  pa.cv = make_camview(cam, view);
+  pa.near_z = cfg->near_z;
+  pa.dilation = cfg->dilation;
+  pa.alpha_min = cfg->alpha_min;
+  pa.tile_w = cfg->tile_w;
+  pa.tile_h = cfg->tile_h;
+  pa.tiles_x = c->st_tx;
+  pa.tiles_y = c->st_ty;
+  {
+    StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
+    const int nb = launch_project_bwd(pa, c->g2d, grads->means, grads->log_scales, grads->quats,
+                                      grads->opacity_logits, grads->sh, c->pose_partials, s);
+    c->launches += 1;
+    if (dL_dpose) {
+      launch_pose_reduce(c->pose_partials, nb, dL_dpose, s);
+      c->launches += 1;
+    }
+  }
+  GS_CHECK_LAUNCH(c, "project_bwd");
+  return GS_OK;
+}
+
+gs_status gs_loss_l1(gs_ctx* c, const gs_camera* cam, const float* color, const float* depth,
+                     const float* target_rgb, const float* target_depth, float w_color, float w_depth, float* loss,
+                     float* dL_dcolor, float* dL_ddepth, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_cam(c, cam)) != GS_OK) return st;
+  if (!color || !depth || !target_rgb || !target_depth || !loss || !dL_dcolor || !dL_ddepth)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_loss_l1: NULL pointer");
+  if (!std::isfinite(w_color) || !std::isfinite(w_depth)) return fail(c, GS_ERR_INVALID_ARG, "non-finite weight");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const int64_t npx = (int64_t)cam->width * cam->height;
+  if (c->sync) {
+    if ((st = ensure_px(c, npx)) != GS_OK) return st;
+  } else if (npx > c->cap_px) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve pixels first");
+  }
+  {
+    StageTimer t(c, GS_STAGE_LOSS, (cudaStream_t)stream);
+    launch_loss(cam->height, cam->width, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
+                dL_ddepth, c->loss_partials, (cudaStream_t)stream, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "loss");
+  return GS_OK;
+}
+
+gs_status gs_adam_step(gs_ctx* c, float* params, float* grads, float* m, float* v, int64_t n,
+                       int32_t sh_degree, const gs_adam_cfg* cfg, int64_t step, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!cfg || step < 1 || n < 0 || sh_degree < 0 || sh_degree > 3)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: bad cfg, step, n or sh_degree");
+  if (n > 0 && (!params || !grads || !m || !v)) return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: NULL pointer");
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
+    return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: betas must be in [0, 1), eps >= 0");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
+  const float lr[6] = {cfg->lr_means, cfg->lr_log_scales, cfg->lr_quats, cfg->lr_opacity, cfg->lr_sh_dc, cfg->lr_sh_rest};
+  {
+    StageTimer t(c, GS_STAGE_ADAM, (cudaStream_t)stream);
+    launch_adam(params, grads, m, v, n, sh_degree, lr, cfg->beta1, cfg->beta2, cfg->eps, (float)(1.0 / bc1),
+                (float)(1.0 / std::sqrt(bc2)), cfg->zero_grads != 0, (cudaStream_t)stream);
+  }
+  if (n > 0) c->launches += 1;
+  GS_CHECK_LAUNCH(c, "adam");
+  return GS_OK;
+}
+
+gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* extent, const float* depth,
+                       int32_t width, int32_t height, int32_t tile_w, int32_t tile_h, uint64_t* keys, uint32_t* ids,
+                       uint32_t* ranges, int64_t pair_capacity, int64_t* n_pairs, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (n < 0 || n >= ((int64_t)1 << 31) || width < 1 || height < 1 || !n_pairs || pair_capacity < 0)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: bad sizes");
+  if (!raster_shape_supported(tile_w, tile_h)) return fail(c, GS_ERR_INVALID_ARG, "unsupported tile shape");
+  if (n > 0 && (!mean2d || !extent || !depth)) return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: NULL input");
+  if (!ranges) return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: NULL ranges");
+  const int tiles_x = (width + tile_w - 1) / tile_w, tiles_y = (height + tile_h - 1) / tile_h;
+  if (tiles_x > 65535 || tiles_y > 65535) return fail(c, GS_ERR_INVALID_ARG, "too many tiles per axis");
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const bool was_sync = c->sync;
+  c->sync = true;
+  gs_status st;
+  const int64_t T = (int64_t)tiles_x * tiles_y;
+  if ((st = ensure_n(c, std::max<int64_t>(n, 1))) != GS_OK || (st = ensure_tiles(c, T)) != GS_OK) {
+    c->sync = was_sync;
+    return st;
+  }
+  c->have_state = false;
+  launch_bin_prepare((int)n, mean2d, extent, depth, tile_w, tile_h, tiles_x, tiles_y, c->zkey, c->tiles, c->rects,
+                     s);
+  if (n > 0) c->launches += 1;
+  st = bin_and_sort(c, (int)n, tiles_x, tiles_y, s);
+  c->sync = was_sync;
+  if (st != GS_OK) return st;
+  const int64_t P = c->st_pairs;
+  *n_pairs = P;
+  GS_CUDA(c, cudaMemcpyAsync(ranges, c->ranges, sizeof(uint2) * (size_t)T, cudaMemcpyDeviceToDevice, s));
+  if (P > pair_capacity) {
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    return fail(c, GS_ERR_CAPACITY, "gs_bin_tiles: output capacity too small");
+  }
+  if (P > 0) {
+    if (!keys || !ids) return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: NULL keys/ids");
+    launch_export_keys(c->pk[c->st_pair_buf], c->pv[c->st_pair_buf], c->zkey, (uint32_t)P, keys, ids, s);
+    c->launches += 1;
+  }
+  GS_CHECK_LAUNCH(c, "bin export");
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  return GS_OK;
+}
+
+gs_status gs_get_projection(gs_ctx* c, float* mean2d, float* cov2d, float* depth, float* rgb, float* opacity,
+                            int32_t* tiles, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!c->have_state) return fail(c, GS_ERR_STATE, "no forward pass on this context");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  launch_export_projection((int)c->st_n, c->feat, c->tiles, mean2d, cov2d, depth, rgb, opacity, tiles,
+                           (cudaStream_t)stream);
+  if (c->st_n > 0) c->launches += 1;
+  GS_CHECK_LAUNCH(c, "export projection");
+  return GS_OK;
+}
+
+}  // extern "C"

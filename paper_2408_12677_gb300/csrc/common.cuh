@@ -1,0 +1,212 @@
+// Shared device helpers of the GB300 Gaussian-splatting path: constants,
+// the projected-feature layout, double-float arithmetic, the real SH basis
+// and the per-pixel evaluation used by both raster passes.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// Projected feature record, 3 x float4 = 48 B per Gaussian (written by the
+// projection kernel, gathered by the raster kernels):
+//   f0 = {mu_x_hi, mu_y_hi, mu_x_lo, mu_y_lo}   double-float pixel mean
+//   f1 = {i0, k, i1, log2(opacity)}             factored inverse covariance
+//   f2 = {r, g, b, z}                           decoded colour, camera depth
+// The 2D Gaussian exponent is evaluated as
+//   q' = (i0 dx)^2 + (i1 (dy - k dx))^2 = 0.5 log2(e) * (u - mu)^T Sigma^-1 (u - mu)
+// with i0 = S / sqrt(a), k = b / a, i1 = S sqrt(a / det), S^2 = 0.5 log2(e),
+// for the dilated covariance [[a, b], [b, c]] (Eq. 5).  This is a Cholesky
+// factorisation of the conic: a sum of two squares, so q' keeps full float32
+// relative accuracy even for very elongated splats, where the usual
+// a dx^2 + 2 b dx dy + c dy^2 form cancels.  exp(-q/2) becomes 2^(-q').
+// ---------------------------------------------------------------------------
+constexpr float kS2 = 0.8493218002880191f;        // sqrt(0.5 * log2(e))
+constexpr float kHalfLog2e = 0.7213475204444817f;  // 0.5 * log2(e)
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Real SH basis constants (Condon-Shortley phase), from
+//   Y_{l,+-m} = sqrt(2 - [m==0]) K_l^m (-1)^m (d^m P_l / dz^m)(z) {Re,Im}(x + i y)^m,
+//   K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), with the Legendre derivative
+//   factors folded in.
+constexpr float kSH0 = 0.28209479177387814f;   // K_0^0
+constexpr float kSH1 = 0.4886025119029199f;    // sqrt(3 / (4 pi))
+constexpr float kSH20 = 0.31539156525252005f;  // K_2^0 / 2          * (3z^2 - 1)
+constexpr float kSH21 = 1.0925484305920792f;   // 3 sqrt(2) K_2^1     * z {x, y}
+constexpr float kSH22 = 0.5462742152960396f;   // 3 sqrt(2) K_2^2     * (x^2 - y^2), 2xy
+constexpr float kSH30 = 0.3731763325901154f;   // K_3^0 / 2          * (5z^3 - 3z)
+constexpr float kSH31 = 0.4570457994644658f;   // 1.5 sqrt(2) K_3^1   * (5z^2 - 1) {x, y}
+constexpr float kSH32 = 1.4453057213202773f;   // 15 sqrt(2) K_3^2    * z (x^2 - y^2), 2xyz
+constexpr float kSH33 = 0.5900435899266436f;   // 15 sqrt(2) K_3^3    * (x^3 - 3xy^2), (3x^2y - y^3)
+
+struct RasterParams {
+  int width, height, tile_w, tile_h, tiles_x, tiles_y;
+  float bg[3];
+  float alpha_max;
+  float log2_alpha_min;  // log2(alpha_min)
+  float qmax_s;          // 9 * 0.5 log2(e): the 3-sigma bound on q'
+  float t_eps;
+};
+
+// ---------------------------------------------------------------------------
+// double-float helpers (error-free transformations, no contraction)
+// ---------------------------------------------------------------------------
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), s.lo);
+  return df_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  df p = df_two_prod(a.hi, b);
+  return df_fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_add(a, df_mul_f(b, -q1));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return df_fast_two_sum(q1, q2);
+}
+// sum_j W[j] * p[j] + t, exactly rounded to double-float
+__device__ __forceinline__ df df_dot3_plus(float w0, float w1, float w2, float p0, float p1, float p2, float t) {
+  df acc = df_two_prod(w0, p0);
+  acc = df_add(acc, df_two_prod(w1, p1));
+  acc = df_add(acc, df_two_prod(w2, p2));
+  return df_add(acc, df{t, 0.f});
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// real SH basis up to degree 3 (16 values) and its gradient w.r.t. the
+// (unnormalised-treated) direction components
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float* Y) {
+  Y[0] = kSH0;
+  if (deg < 1) return;
+  Y[1] = -kSH1 * y;
+  Y[2] = kSH1 * z;
+  Y[3] = -kSH1 * x;
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = 2.f * kSH22 * x * y;
+  Y[5] = -kSH21 * y * z;
+  Y[6] = kSH20 * (3.f * zz - 1.f);
+  Y[7] = -kSH21 * x * z;
+  Y[8] = kSH22 * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kSH33 * (3.f * xx * y - yy * y);
+  Y[10] = 2.f * kSH32 * x * y * z;
+  Y[11] = -kSH31 * y * (5.f * zz - 1.f);
+  Y[12] = kSH30 * (5.f * zz * z - 3.f * z);
+  Y[13] = -kSH31 * x * (5.f * zz - 1.f);
+  Y[14] = kSH32 * z * (xx - yy);
+  Y[15] = -kSH33 * (xx * x - 3.f * x * yy);
+}
+
+// d/d(x, y, z) of sum_k c_k Y_k(x, y, z) for per-basis weights c[k]
+__device__ __forceinline__ void sh_basis_vjp(int deg, float x, float y, float z, const float* c, float& gx,
+                                             float& gy, float& gz) {
+  gx = gy = gz = 0.f;
+  if (deg < 1) return;
+  gy += -kSH1 * c[1];
+  gz += kSH1 * c[2];
+  gx += -kSH1 * c[3];
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  gx += 2.f * kSH22 * y * c[4];
+  gy += 2.f * kSH22 * x * c[4];
+  gy += -kSH21 * z * c[5];
+  gz += -kSH21 * y * c[5];
+  gz += kSH20 * 6.f * z * c[6];
+  gx += -kSH21 * z * c[7];
+  gz += -kSH21 * x * c[7];
+  gx += kSH22 * 2.f * x * c[8];
+  gy += -kSH22 * 2.f * y * c[8];
+  if (deg < 3) return;
+  gx += -kSH33 * 6.f * x * y * c[9];
+  gy += -kSH33 * (3.f * xx - 3.f * yy) * c[9];
+  gx += 2.f * kSH32 * y * z * c[10];
+  gy += 2.f * kSH32 * x * z * c[10];
+  gz += 2.f * kSH32 * x * y * c[10];
+  gy += -kSH31 * (5.f * zz - 1.f) * c[11];
+  gz += -kSH31 * y * 10.f * z * c[11];
+  gz += kSH30 * (15.f * zz - 3.f) * c[12];
+  gx += -kSH31 * (5.f * zz - 1.f) * c[13];
+  gz += -kSH31 * x * 10.f * z * c[13];
+  gx += kSH32 * z * 2.f * x * c[14];
+  gy += -kSH32 * z * 2.f * y * c[14];
+  gz += kSH32 * (xx - yy) * c[14];
+  gx += -kSH33 * (3.f * xx - 3.f * yy) * c[15];
+  gy += kSH33 * 6.f * x * y * c[15];
+}
+
+// ---------------------------------------------------------------------------
+// tile rectangle of a support box (integer contract, float32 arithmetic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_rect(float mx, float my, float ex, float ey, float inv_tw, float inv_th,
+                                          int tiles_x, int tiles_y, int& x0, int& y0, int& x1, int& y1) {
+  if (!(ex > 0.f && ey > 0.f)) {
+    x0 = y0 = x1 = y1 = 0;
+    return;
+  }
+  float lx = floorf(__fmul_rn(__fsub_rn(mx, ex), inv_tw));
+  float hx = __fadd_rn(floorf(__fmul_rn(__fadd_rn(mx, ex), inv_tw)), 1.f);
+  float ly = floorf(__fmul_rn(__fsub_rn(my, ey), inv_th));
+  float hy = __fadd_rn(floorf(__fmul_rn(__fadd_rn(my, ey), inv_th)), 1.f);
+  float TX = (float)tiles_x, TY = (float)tiles_y;
+  x0 = (int)fminf(fmaxf(lx, 0.f), TX);
+  x1 = (int)fminf(fmaxf(hx, 0.f), TX);
+  y0 = (int)fminf(fmaxf(ly, 0.f), TY);
+  y1 = (int)fminf(fmaxf(hy, 0.f), TY);
+  if (x1 <= x0 || y1 <= y0) x0 = y0 = x1 = y1 = 0;
+}
+
+// ---------------------------------------------------------------------------
+// per-pixel evaluation shared by the forward and backward raster kernels;
+// the skip decisions must be bit-identical in both, hence explicit rounding
+// intrinsics (no contraction differences between the two call sites).
+// a = {mu_local_x, mu_local_y, i0, k}, i1, log2o
+// ---------------------------------------------------------------------------
+struct PixEval {
+  float dx, dy, t0, w, t1, araw;
+};
+
+__device__ __forceinline__ bool eval_splat(float4 a, float i1, float log2o, float plx, float ply, float qmax_s,
+                                           float log2_amin, PixEval& e) {
+  e.dx = __fsub_rn(plx, a.x);
+  e.dy = __fsub_rn(ply, a.y);
+  e.t0 = __fmul_rn(a.z, e.dx);
+  e.w = __fmaf_rn(-a.w, e.dx, e.dy);
+  e.t1 = __fmul_rn(i1, e.w);
+  float q = __fmaf_rn(e.t0, e.t0, __fmul_rn(e.t1, e.t1));
+  if (q > qmax_s) return false;
+  float ex = __fsub_rn(log2o, q);
+  if (ex < log2_amin) return false;
+  e.araw = ex2_approx(ex);
+  return true;
+}
+
+}  // namespace gs

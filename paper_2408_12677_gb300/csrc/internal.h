@@ -1,0 +1,105 @@
+// Host-side launchers shared between the translation units of libgsplat.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+struct CamView {
+  float fx, fy, cx, cy;
+  int width, height;
+  float R[9], t[3];
+  float C[3];  // camera centre in the world frame, -R^T t
+};
+
+struct ProjectArgs {
+  int n;
+  const float *means, *log_scales, *quats, *logits, *sh;
+  int sh_degree;
+  CamView cv;
+  float near_z, dilation, alpha_min;
+  int tile_w, tile_h, tiles_x, tiles_y;
+};
+
+// projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
+void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key, uint32_t* tiles_touched,
+                        ushort4* rects, cudaStream_t s);
+// binning-only front end: rects/keys from given mean2d / extent / depth
+void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
+                        int tiles_x, int tiles_y, uint32_t* depth_key, uint32_t* tiles_touched, ushort4* rects,
+                        cudaStream_t s);
+// g2d [n, 12] -> parameter gradients (+=) and per-block pose partials
+int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales,
+                       float* g_quats, float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s);
+void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s);
+int project_bwd_blocks(int n);
+
+// Stable radix sort of (u32 key, u32 value) pairs on the low `bits` bits.
+// The first pass reads (in_k, in_v) -- in_v == nullptr means value = index --
+// and later passes ping-pong between the two buffers of `b`.  If in_k is
+// b.keys[0] the sort runs in place.  Returns the index (0 or 1) of the buffer
+// holding the result, or -1 if no pass ran and the input is the result.
+// n is read from n_dev when non-null (grid sized from n_max).
+struct SortBuffers {
+  uint32_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;   // scratch, >= 256 * max_blocks
+  int max_blocks;
+};
+int radix_sort_pairs(SortBuffers& b, const uint32_t* in_k, const uint32_t* in_v, uint32_t n_max,
+                     const uint32_t* n_dev, int bits, int num_sms, cudaStream_t s, int64_t* launches);
+
+// pair generation: per depth-sorted Gaussian, its tiles in row-major order
+struct DupArgs {
+  int n;
+  const uint32_t* sorted_ids;
+  const uint32_t* tiles_touched;
+  const ushort4* rects;
+  int tiles_x;
+  uint32_t* block_sums;  // scratch >= dup_blocks(n) + 1
+  uint32_t* n_pairs;     // device total (clamped to capacity for the kernels)
+  unsigned long long* n_pairs_full;  // device total before clamping
+  uint32_t* tile_keys;
+  uint32_t* vals;
+  uint32_t capacity;
+  uint32_t* overflow;
+};
+int dup_blocks(int n);
+void launch_dup_count_scan(const DupArgs& a, cudaStream_t s, int64_t* launches);
+void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches);
+
+void launch_tile_ranges(const uint32_t* sorted_tiles, const uint32_t* n_dev, uint32_t n_max, uint2* ranges,
+                        int n_tiles, int num_sms, cudaStream_t s, int64_t* launches);
+
+// raster passes
+struct RasterArgs {
+  int width, height, tile_w, tile_h, tiles_x, tiles_y;
+  float bg[3];
+  float alpha_max, alpha_min, t_eps;
+  const uint2* ranges;
+  const uint32_t* ids;
+  const float4* feat;
+};
+bool raster_shape_supported(int tw, int th);
+void launch_raster_fwd(const RasterArgs& a, float* color, float* depth, float* alpha, float* T_final,
+                       int32_t* last, unsigned long long* counters, cudaStream_t s);
+void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, const float* dL_dcolor,
+                       const float* dL_ddepth, const float* dL_dalpha, float4* g2d, cudaStream_t s);
+
+// loss and optimiser
+int loss_blocks(int npix);
+void launch_loss(int H, int W, const float* color, const float* depth, const float* trgb, const float* tdep,
+                 float w_color, float w_depth, float* loss, float* dLdc, float* dLdd, float* partials,
+                 cudaStream_t s, int64_t* launches);
+void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],
+                 float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero_grads,
+                 cudaStream_t s);
+
+// debug/introspection
+void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, float* mean2d, float* cov2d,
+                              float* depth, float* rgb, float* opacity, int32_t* tiles_out, cudaStream_t s);
+void launch_export_keys(const uint32_t* sorted_tiles, const uint32_t* sorted_ids, const uint32_t* depth_key_by_id,
+                        uint32_t P, uint64_t* keys, uint32_t* ids, cudaStream_t s);
+
+}  // namespace gs

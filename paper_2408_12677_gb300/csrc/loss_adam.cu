@@ -1,0 +1,239 @@
+// L1 photometric + depth loss with image gradients (Eq. 12 plus a depth
+// term), the dense Adam update over the flat parameter buffer, and small
+// export helpers.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kLossThreads = 256;
+constexpr int kLossItems = 8;  // pixels per thread
+
+__device__ __forceinline__ float sgn(float x) { return (float)((x > 0.f) - (x < 0.f)); }
+
+// Pass 1: per pixel |residuals| and sign gradients; per-block partial sums
+// (|colour residual| sum, |depth residual| sum over valid pixels, valid count).
+__global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(
+    int npix, const float* __restrict__ color, const float* __restrict__ depth, const float* __restrict__ trgb,
+    const float* __restrict__ tdep, float gscale_c, float* __restrict__ dLdc, float* __restrict__ dLdd,
+    float* __restrict__ partials) {
+  float sc = 0.f, sd = 0.f, nv = 0.f;
+  const int base = blockIdx.x * kLossThreads * kLossItems + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kLossItems; ++j) {
+    const int p = base + j * kLossThreads;
+    if (p >= npix) break;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float r = color[(size_t)c * npix + p] - trgb[(size_t)c * npix + p];
+      sc += fabsf(r);
+      dLdc[(size_t)c * npix + p] = gscale_c * sgn(r);
+    }
+    const float td = tdep[p];
+    const bool valid = td > 0.f;
+    const float rd = depth[p] - td;
+    sd += valid ? fabsf(rd) : 0.f;
+    nv += valid ? 1.f : 0.f;
+    dLdd[p] = valid ? sgn(rd) : 0.f;
+  }
+  __shared__ float red[3][kLossThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    sc += __shfl_xor_sync(0xFFFFFFFFu, sc, off);
+    sd += __shfl_xor_sync(0xFFFFFFFFu, sd, off);
+    nv += __shfl_xor_sync(0xFFFFFFFFu, nv, off);
+  }
+  if (lane == 0) {
+    red[0][wid] = sc;
+    red[1][wid] = sd;
+    red[2][wid] = nv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float s = 0.f;
+    for (int w = 0; w < kLossThreads / 32; ++w) s += red[threadIdx.x][w];
+    partials[3 * blockIdx.x + threadIdx.x] = s;
+  }
+}
+
+// Pass 2 (one block): fixed-order reduction of the partials -> loss and the
+// depth-gradient scale w_depth / n_valid (stored in scale[0]).
+__global__ void loss_finalize_kernel(const float* __restrict__ partials, int nblocks, int npix, float w_color,
+                                     float w_depth, float* __restrict__ loss, float* __restrict__ scale) {
+  __shared__ double red[3][32];
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < 3; ++k) a[k] += (double)partials[3 * b + k];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 3; ++k) {
+    double v = a[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0) red[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+      for (int k = 0; k < 3; ++k) s[k] += red[k][w];
+    const double nv = s[2] > 0.0 ? s[2] : 1.0;
+    loss[0] = (float)(w_color * s[0] / (3.0 * npix) + w_depth * s[1] / nv);
+    scale[0] = (float)(w_depth / nv);
+  }
+}
+
+__global__ void scale_kernel(int n, float* __restrict__ x, const float* __restrict__ scale) {
+  const float s = scale[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] *= s;
+}
+
+// ---------------------------------------------------------------------------
+// Adam
+// ---------------------------------------------------------------------------
+struct AdamGroups {
+  int64_t e_means, e_scales, e_quats, e_opac;  // group ends (exclusive) in floats
+  int sh_stride;                              // 3 K
+  float lr[6];
+};
+
+__device__ __forceinline__ float adam_lr(const AdamGroups& g, int64_t i) {
+  if (i < g.e_means) return g.lr[0];
+  if (i < g.e_scales) return g.lr[1];
+  if (i < g.e_quats) return g.lr[2];
+  if (i < g.e_opac) return g.lr[3];
+  return ((i - g.e_opac) % g.sh_stride) < 3 ? g.lr[4] : g.lr[5];
+}
+
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                         float eps, float ss, float isb2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  p -= lr * ss * m / (sqrtf(v) * isb2 + eps);
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(int64_t total, float4* __restrict__ p4, float4* __restrict__ g4,
+                                                   float4* __restrict__ m4, float4* __restrict__ v4, AdamGroups grp,
+                                                   float b1, float b2, float eps, float ss, float isb2, bool zero) {
+  const int64_t nvec = total >> 2;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nvec; q += (int64_t)gridDim.x * blockDim.x) {
+    float4 p = p4[q], g = g4[q], m = m4[q], v = v4[q];
+    const int64_t i = q << 2;
+    adam_one(p.x, g.x, m.x, v.x, adam_lr(grp, i), b1, b2, eps, ss, isb2);
+    adam_one(p.y, g.y, m.y, v.y, adam_lr(grp, i + 1), b1, b2, eps, ss, isb2);
+    adam_one(p.z, g.z, m.z, v.z, adam_lr(grp, i + 2), b1, b2, eps, ss, isb2);
+    adam_one(p.w, g.w, m.w, v.w, adam_lr(grp, i + 3), b1, b2, eps, ss, isb2);
+    p4[q] = p;
+    m4[q] = m;
+    v4[q] = v;
+    if (zero) g4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__global__ void adam_tail_kernel(int64_t start, int64_t total, float* __restrict__ p, float* __restrict__ g,
+                                 float* __restrict__ m, float* __restrict__ v, AdamGroups grp, float b1, float b2,
+                                 float eps, float ss, float isb2, bool zero) {
+  const int64_t i = start + threadIdx.x;
+  if (i < total) {
+    adam_one(p[i], g[i], m[i], v[i], adam_lr(grp, i), b1, b2, eps, ss, isb2);
+    if (zero) g[i] = 0.f;
+  }
+}
+
+__global__ void adam_scalar_kernel(int64_t total, float* __restrict__ p, float* __restrict__ g,
+                                   float* __restrict__ m, float* __restrict__ v, AdamGroups grp, float b1, float b2,
+                                   float eps, float ss, float isb2, bool zero) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    adam_one(p[i], g[i], m[i], v[i], adam_lr(grp, i), b1, b2, eps, ss, isb2);
+    if (zero) g[i] = 0.f;
+  }
+}
+
+__global__ void export_projection_kernel(int n, const float4* __restrict__ feat, const uint32_t* __restrict__ tiles,
+                                         float* mean2d, float* cov2d, float* depth, float* rgb, float* opacity,
+                                         int32_t* tiles_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 f0 = feat[3 * i], f1 = feat[3 * i + 1], f2 = feat[3 * i + 2];
+  if (mean2d) {
+    mean2d[2 * i] = f0.x + f0.z;
+    mean2d[2 * i + 1] = f0.y + f0.w;
+  }
+  if (cov2d) {
+    // i0 = S/sqrt(a), k = b/a, i1 = S sqrt(a/det): a = S^2/i0^2, b = k a, c = (det + b^2)/a
+    const float S2sq = kS2 * kS2;
+    const float a = f1.x != 0.f ? S2sq / (f1.x * f1.x) : 0.f;
+    const float b = f1.y * a;
+    const float det = f1.z != 0.f ? S2sq * a / (f1.z * f1.z) : 0.f;
+    cov2d[3 * i] = a;
+    cov2d[3 * i + 1] = b;
+    cov2d[3 * i + 2] = a != 0.f ? (det + b * b) / a : 0.f;
+  }
+  if (depth) depth[i] = f2.w;
+  if (rgb) {
+    rgb[3 * i] = f2.x;
+    rgb[3 * i + 1] = f2.y;
+    rgb[3 * i + 2] = f2.z;
+  }
+  if (opacity) opacity[i] = exp2f(f1.w);
+  if (tiles_out) tiles_out[i] = (int32_t)tiles[i];
+}
+
+}  // namespace
+
+int loss_blocks(int npix) { return (npix + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems); }
+
+void launch_loss(int H, int W, const float* color, const float* depth, const float* trgb, const float* tdep,
+                 float w_color, float w_depth, float* loss, float* dLdc, float* dLdd, float* partials,
+                 cudaStream_t s, int64_t* launches) {
+  const int npix = H * W;
+  const int nb = loss_blocks(npix);
+  float* scale = partials + 3 * nb;
+  loss_partials_kernel<<<nb, kLossThreads, 0, s>>>(npix, color, depth, trgb, tdep, w_color / (3.f * (float)npix),
+                                                   dLdc, dLdd, partials);
+  loss_finalize_kernel<<<1, 1024, 0, s>>>(partials, nb, npix, w_color, w_depth, loss, scale);
+  scale_kernel<<<std::min(1024, (npix + 255) / 256), 256, 0, s>>>(npix, dLdd, scale);
+  if (launches) *launches += 3;
+}
+
+void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],
+                 float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero,
+                 cudaStream_t s) {
+  const int K = (sh_degree + 1) * (sh_degree + 1);
+  AdamGroups grp;
+  grp.e_means = 3 * n_gauss;
+  grp.e_scales = 6 * n_gauss;
+  grp.e_quats = 10 * n_gauss;
+  grp.e_opac = 11 * n_gauss;
+  grp.sh_stride = 3 * K;
+  for (int k = 0; k < 6; ++k) grp.lr[k] = lr[k];
+  const int64_t total = n_gauss * (11 + 3 * K);
+  if (total == 0) return;
+  const bool aligned = ((((uintptr_t)p) | ((uintptr_t)g) | ((uintptr_t)m) | ((uintptr_t)v)) & 15) == 0;
+  if (aligned) {
+    const int64_t nvec = total >> 2;
+    if (nvec > 0) {
+      int64_t blocks = std::min<int64_t>((nvec + 255) / 256, 152 * 16);
+      adam_kernel<<<(int)blocks, 256, 0, s>>>(total, (float4*)p, (float4*)g, (float4*)m, (float4*)v, grp, beta1,
+                                              beta2, eps, step_size_scale, inv_sqrt_bc2, zero);
+    }
+    if (total & 3)
+      adam_tail_kernel<<<1, 4, 0, s>>>(nvec << 2, total, p, g, m, v, grp, beta1, beta2, eps, step_size_scale,
+                                       inv_sqrt_bc2, zero);
+  } else {
+    int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    adam_scalar_kernel<<<(int)blocks, 256, 0, s>>>(total, p, g, m, v, grp, beta1, beta2, eps, step_size_scale,
+                                                   inv_sqrt_bc2, zero);
+  }
+}
+
+void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, float* mean2d, float* cov2d,
+                              float* depth, float* rgb, float* opacity, int32_t* tiles_out, cudaStream_t s) {
+  if (n <= 0) return;
+  export_projection_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, feat, tiles, mean2d, cov2d, depth, rgb, opacity,
+                                                           tiles_out);
+}
+
+}  // namespace gs

@@ -1,0 +1,389 @@
+// Projection of 3D Gaussians to 2D splats (Eq. 2-5) and its backward pass,
+// including the gradient w.r.t. the camera pose.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gs {
+
+namespace {
+
+__device__ __forceinline__ void quat_rotmat(float w, float x, float y, float z, float R[3][3]) {
+  R[0][0] = 1.f - 2.f * (y * y + z * z);
+  R[0][1] = 2.f * (x * y - w * z);
+  R[0][2] = 2.f * (x * z + w * y);
+  R[1][0] = 2.f * (x * y + w * z);
+  R[1][1] = 1.f - 2.f * (x * x + z * z);
+  R[1][2] = 2.f * (y * z - w * x);
+  R[2][0] = 2.f * (x * z - w * y);
+  R[2][1] = 2.f * (y * z + w * x);
+  R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Everything of the forward projection that the backward pass needs again,
+// in float32.
+struct Geo {
+  float x, y, z, rz;
+  float xt, yt;      // clamped J positions x~, y~
+  bool cx_, cy_;     // clamp active
+  float qn[4], qlen;
+  float Rq[3][3];
+  float s[3];
+  float B[3][3];     // Rq diag(s)
+  float A[3][3];     // W B
+  float j00, j02, j11, j12;
+  float m0[3], m1[3];
+  float a, b, c, det;
+  float i0, k, i1;
+};
+
+__device__ __forceinline__ void geometry(const CamView& cv, float dilation, float px, float py, float pz,
+                                         const float* q4, const float* ls, float x, float y, float z, Geo& g) {
+  g.x = x;
+  g.y = y;
+  g.z = z;
+  g.rz = 1.f / z;
+  const float limx = 1.3f * (float)cv.width / (2.f * cv.fx);
+  const float limy = 1.3f * (float)cv.height / (2.f * cv.fy);
+  float xr = x * g.rz, yr = y * g.rz;
+  g.cx_ = (xr < -limx) || (xr > limx);
+  g.cy_ = (yr < -limy) || (yr > limy);
+  g.xt = fminf(fmaxf(xr, -limx), limx) * z;
+  g.yt = fminf(fmaxf(yr, -limy), limy) * z;
+  float qq = q4[0] * q4[0] + q4[1] * q4[1] + q4[2] * q4[2] + q4[3] * q4[3];
+  float inv = rsqrtf(qq);
+  g.qlen = qq * inv;
+  for (int j = 0; j < 4; ++j) g.qn[j] = q4[j] * inv;
+  quat_rotmat(g.qn[0], g.qn[1], g.qn[2], g.qn[3], g.Rq);
+  for (int j = 0; j < 3; ++j) g.s[j] = expf(ls[j]);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) g.B[r][c] = g.Rq[r][c] * g.s[c];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      g.A[r][c] = cv.R[3 * r + 0] * g.B[0][c] + cv.R[3 * r + 1] * g.B[1][c] + cv.R[3 * r + 2] * g.B[2][c];
+  g.j00 = cv.fx * g.rz;
+  g.j02 = -cv.fx * g.xt * g.rz * g.rz;
+  g.j11 = cv.fy * g.rz;
+  g.j12 = -cv.fy * g.yt * g.rz * g.rz;
+  for (int c = 0; c < 3; ++c) {
+    g.m0[c] = g.j00 * g.A[0][c] + g.j02 * g.A[2][c];
+    g.m1[c] = g.j11 * g.A[1][c] + g.j12 * g.A[2][c];
+  }
+  float n0 = g.m0[0] * g.m0[0] + g.m0[1] * g.m0[1] + g.m0[2] * g.m0[2];
+  float n1 = g.m1[0] * g.m1[0] + g.m1[1] * g.m1[1] + g.m1[2] * g.m1[2];
+  g.a = n0 + dilation;
+  g.c = n1 + dilation;
+  g.b = g.m0[0] * g.m1[0] + g.m0[1] * g.m1[1] + g.m0[2] * g.m1[2];
+  // det of the dilated covariance without cancellation (Lagrange identity):
+  // |m0 x m1|^2 + dil (|m0|^2 + |m1|^2) + dil^2, where
+  // m0 x m1 = det(A) A^-1 (j0 x j1) = diag(s1 s2, s0 s2, s0 s1) Rq^T W^T (fx fy / z^3)(x~, y~, z)
+  float v[3];
+  for (int r = 0; r < 3; ++r) v[r] = cv.R[r] * g.xt + cv.R[3 + r] * g.yt + cv.R[6 + r] * z;  // W^T (x~, y~, z)
+  float u[3];
+  for (int c = 0; c < 3; ++c) u[c] = g.Rq[0][c] * v[0] + g.Rq[1][c] * v[1] + g.Rq[2][c] * v[2];
+  float f = cv.fx * cv.fy * g.rz * g.rz * g.rz;
+  float c0 = g.s[1] * g.s[2] * u[0] * f, c1 = g.s[0] * g.s[2] * u[1] * f, c2 = g.s[0] * g.s[1] * u[2] * f;
+  g.det = c0 * c0 + c1 * c1 + c2 * c2 + dilation * (n0 + n1) + dilation * dilation;
+  g.i0 = kS2 * rsqrtf(g.a);
+  g.k = g.b / g.a;
+  g.i1 = kS2 * sqrtf(g.a / g.det);
+}
+
+__global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a, float4* __restrict__ feat,
+                                                          uint32_t* __restrict__ depth_key,
+                                                          uint32_t* __restrict__ tiles_touched,
+                                                          ushort4* __restrict__ rects) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const CamView& cv = a.cv;
+  const float px = a.means[3 * i], py = a.means[3 * i + 1], pz = a.means[3 * i + 2];
+  // camera-space position and pixel mean in double-float (the float32 error of
+  // W p + t alone would move mu by ~1e-3 px at 1-2 m)
+  df Z = df_dot3_plus(cv.R[6], cv.R[7], cv.R[8], px, py, pz, cv.t[2]);
+  const float z = Z.hi;
+  if (!(z > a.near_z)) {
+    depth_key[i] = 0xFFFFFFFFu;
+    tiles_touched[i] = 0;
+    rects[i] = make_ushort4(0, 0, 0, 0);
+    feat[3 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    feat[3 * i + 1] = make_float4(0.f, 0.f, 0.f, -1e30f);
+    feat[3 * i + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  df X = df_dot3_plus(cv.R[0], cv.R[1], cv.R[2], px, py, pz, cv.t[0]);
+  df Y = df_dot3_plus(cv.R[3], cv.R[4], cv.R[5], px, py, pz, cv.t[1]);
+  df mux = df_add(df_mul_f(df_div(X, Z), cv.fx), df{cv.cx, 0.f});
+  df muy = df_add(df_mul_f(df_div(Y, Z), cv.fy), df{cv.cy, 0.f});
+
+  float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+  float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+  Geo g;
+  geometry(cv, a.dilation, px, py, pz, q4, ls, X.hi, Y.hi, z, g);
+
+  const float logit = a.logits[i];
+  const float o = 1.f / (1.f + expf(-logit));
+  const float log2o = log2f(o);
+  // support of the blend test: q <= min(9, 2 ln(o / alpha_min)), widened a
+  // little so that float32 rounding of the per-pixel test stays inside
+  float Q = fminf(9.f, 2.f * logf(o / a.alpha_min));
+  int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+  if (Q > 0.f && g.det > 0.f) {
+    float Qw = Q * 1.0001f + 1e-4f;
+    float ex = sqrtf(Qw * g.a) * 1.00001f + 1e-3f;
+    float ey = sqrtf(Qw * (g.b * g.b + g.det) / g.a) * 1.00001f + 1e-3f;
+    tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x, a.tiles_y, x0, y0,
+              x1, y1);
+  }
+  tiles_touched[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  rects[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+  depth_key[i] = __float_as_uint(z);
+
+  // view-dependent colour
+  const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+  float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
+  float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+  float Yb[16];
+  sh_basis(a.sh_degree, dx * inv, dy * inv, dz * inv, Yb);
+  const float* shp = a.sh + (size_t)i * K * 3;
+  float rgb[3] = {0.5f, 0.5f, 0.5f};
+  for (int k = 0; k < K; ++k) {
+    rgb[0] += Yb[k] * shp[3 * k];
+    rgb[1] += Yb[k] * shp[3 * k + 1];
+    rgb[2] += Yb[k] * shp[3 * k + 2];
+  }
+  feat[3 * i] = make_float4(mux.hi, muy.hi, mux.lo, muy.lo);
+  feat[3 * i + 1] = make_float4(g.i0, g.k, g.i1, log2o);
+  feat[3 * i + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
+}
+
+__global__ void bin_prepare_kernel(int n, const float* __restrict__ mean2d, const float* __restrict__ extent,
+                                   const float* __restrict__ depth, float inv_tw, float inv_th, int tiles_x,
+                                   int tiles_y, uint32_t* __restrict__ depth_key, uint32_t* __restrict__ tiles,
+                                   ushort4* __restrict__ rects) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x0, y0, x1, y1;
+  tile_rect(mean2d[2 * i], mean2d[2 * i + 1], extent[2 * i], extent[2 * i + 1], inv_tw, inv_th, tiles_x, tiles_y,
+            x0, y0, x1, y1);
+  tiles[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  rects[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+  depth_key[i] = __float_as_uint(depth[i]);
+}
+
+constexpr int kBwdThreads = 128;
+
+__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a, const float4* __restrict__ g2d,
+                                                                  float* __restrict__ gm, float* __restrict__ gls,
+                                                                  float* __restrict__ gq, float* __restrict__ glog,
+                                                                  float* __restrict__ gsh,
+                                                                  float* __restrict__ pose_partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const CamView& cv = a.cv;
+  if (i < a.n) {
+    float4 G0 = g2d[3 * i], G1 = g2d[3 * i + 1], G2 = g2d[3 * i + 2];
+    bool any = (G0.x != 0.f) | (G0.y != 0.f) | (G0.z != 0.f) | (G0.w != 0.f) | (G1.x != 0.f) | (G1.y != 0.f) |
+               (G1.z != 0.f) | (G2.x != 0.f) | (G2.y != 0.f) | (G2.z != 0.f);
+    if (any) {
+      const float p[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+      float pc[3];
+      for (int r = 0; r < 3; ++r) pc[r] = cv.R[3 * r] * p[0] + cv.R[3 * r + 1] * p[1] + cv.R[3 * r + 2] * p[2] + cv.t[r];
+      float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+      float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+      Geo g;
+      geometry(cv, a.dilation, p[0], p[1], p[2], q4, ls, pc[0], pc[1], pc[2], g);
+      const float gmx = G0.x, gmy = G0.y, gi0 = G0.z, gk = G0.w, gi1 = G1.x, go = G1.y, gdep = G1.z;
+
+      // opacity
+      const float o = 1.f / (1.f + expf(-a.logits[i]));
+      glog[i] += go * o * (1.f - o);
+
+      // colour: SH coefficients and view direction
+      const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
+      float dv[3] = {p[0] - cv.C[0], p[1] - cv.C[1], p[2] - cv.C[2]};
+      float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+      float d[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+      float Yb[16];
+      sh_basis(a.sh_degree, d[0], d[1], d[2], Yb);
+      const float* shp = a.sh + (size_t)i * K * 3;
+      float raw[3] = {0.5f, 0.5f, 0.5f};
+      for (int k = 0; k < K; ++k)
+        for (int c = 0; c < 3; ++c) raw[c] += Yb[k] * shp[3 * k + c];
+      float graw[3] = {raw[0] > 0.f ? G2.x : 0.f, raw[1] > 0.f ? G2.y : 0.f, raw[2] > 0.f ? G2.z : 0.f};
+      float cw[16];
+      float* gshp = gsh + (size_t)i * K * 3;
+      for (int k = 0; k < K; ++k) {
+        gshp[3 * k] += Yb[k] * graw[0];
+        gshp[3 * k + 1] += Yb[k] * graw[1];
+        gshp[3 * k + 2] += Yb[k] * graw[2];
+        cw[k] = shp[3 * k] * graw[0] + shp[3 * k + 1] * graw[1] + shp[3 * k + 2] * graw[2];
+      }
+      float gd[3];
+      sh_basis_vjp(a.sh_degree, d[0], d[1], d[2], cw, gd[0], gd[1], gd[2]);
+      float dd = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
+      float gv[3] = {(gd[0] - d[0] * dd) * inv, (gd[1] - d[1] * dd) * inv, (gd[2] - d[2] * dd) * inv};
+      float gp[3] = {gv[0], gv[1], gv[2]};
+      float gC[3] = {-gv[0], -gv[1], -gv[2]};
+
+      // (i0, k, i1) -> dilated covariance entries (a, b, c)
+      const float ga = -gi0 * g.i0 / (2.f * g.a) - gk * g.k / g.a - gi1 * g.i1 * g.b * g.b / (2.f * g.a * g.det);
+      const float gb = gk / g.a + gi1 * g.i1 * g.b / g.det;
+      const float gc = -gi1 * g.i1 * g.a / (2.f * g.det);
+      // covariance = M M^T + dil I, rows m0, m1 of M = J A
+      float Gm0[3], Gm1[3];
+      for (int c = 0; c < 3; ++c) {
+        Gm0[c] = 2.f * ga * g.m0[c] + gb * g.m1[c];
+        Gm1[c] = gb * g.m0[c] + 2.f * gc * g.m1[c];
+      }
+      float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
+      for (int c = 0; c < 3; ++c) {
+        gj00 += Gm0[c] * g.A[0][c];
+        gj02 += Gm0[c] * g.A[2][c];
+        gj11 += Gm1[c] * g.A[1][c];
+        gj12 += Gm1[c] * g.A[2][c];
+      }
+      float GA[3][3];
+      for (int c = 0; c < 3; ++c) {
+        GA[0][c] = g.j00 * Gm0[c];
+        GA[1][c] = g.j11 * Gm1[c];
+        GA[2][c] = g.j02 * Gm0[c] + g.j12 * Gm1[c];
+      }
+      // J and the mean -> camera-space position
+      const float rz = g.rz, rz2 = rz * rz, rz3 = rz2 * rz;
+      float gpc[3] = {0.f, 0.f, 0.f};
+      gpc[2] += -cv.fx * rz2 * gj00 - cv.fy * rz2 * gj11;
+      if (!g.cx_) {
+        gpc[0] += -cv.fx * rz2 * gj02;
+        gpc[2] += 2.f * cv.fx * g.x * rz3 * gj02;
+      } else {
+        gpc[2] += cv.fx * g.xt * rz3 * gj02;
+      }
+      if (!g.cy_) {
+        gpc[1] += -cv.fy * rz2 * gj12;
+        gpc[2] += 2.f * cv.fy * g.y * rz3 * gj12;
+      } else {
+        gpc[2] += cv.fy * g.yt * rz3 * gj12;
+      }
+      gpc[0] += gmx * cv.fx * rz;
+      gpc[1] += gmy * cv.fy * rz;
+      gpc[2] += -(gmx * cv.fx * g.x + gmy * cv.fy * g.y) * rz2 + gdep;
+
+      // A = W B, B = Rq diag(s)
+      float GW[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) GW[r][c] = GA[r][0] * g.B[c][0] + GA[r][1] * g.B[c][1] + GA[r][2] * g.B[c][2];
+      float GB[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          GB[r][c] = cv.R[r] * GA[0][c] + cv.R[3 + r] * GA[1][c] + cv.R[6 + r] * GA[2][c];
+      float GR[3][3];
+      for (int c = 0; c < 3; ++c) {
+        float gs_ = 0.f;
+        for (int r = 0; r < 3; ++r) {
+          GR[r][c] = GB[r][c] * g.s[c];
+          gs_ += GB[r][c] * g.Rq[r][c];
+        }
+        gls[3 * i + c] += gs_ * g.s[c];
+      }
+      // rotation matrix -> normalised quaternion -> raw quaternion
+      const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+      float gqn[4];
+      gqn[0] = 2.f * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
+      gqn[1] = 2.f * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.f * x * GR[1][1] - w * GR[1][2] +
+                      z * GR[2][0] + w * GR[2][1] - 2.f * x * GR[2][2]);
+      gqn[2] = 2.f * (-2.f * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] -
+                      w * GR[2][0] + z * GR[2][1] - 2.f * y * GR[2][2]);
+      gqn[3] = 2.f * (-2.f * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.f * z * GR[1][1] +
+                      y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
+      float dq = g.qn[0] * gqn[0] + g.qn[1] * gqn[1] + g.qn[2] * gqn[2] + g.qn[3] * gqn[3];
+      for (int j = 0; j < 4; ++j) gq[4 * i + j] += (gqn[j] - g.qn[j] * dq) / g.qlen;
+
+      // p_c = W p + t
+      for (int c = 0; c < 3; ++c) gp[c] += cv.R[c] * gpc[0] + cv.R[3 + c] * gpc[1] + cv.R[6 + c] * gpc[2];
+      for (int c = 0; c < 3; ++c) gm[3 * i + c] += gp[c];
+
+      // pose: total dL/dW and dL/dt of this Gaussian, then the left-perturbation twist
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) GW[r][c] += gpc[r] * p[c] - cv.t[r] * gC[c];
+      float gt[3];
+      for (int r = 0; r < 3; ++r)
+        gt[r] = gpc[r] - (cv.R[3 * r] * gC[0] + cv.R[3 * r + 1] * gC[1] + cv.R[3 * r + 2] * gC[2]);
+      float Am[3][3];  // GW W^T
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          Am[r][c] = GW[r][0] * cv.R[3 * c] + GW[r][1] * cv.R[3 * c + 1] + GW[r][2] * cv.R[3 * c + 2];
+      pose[0] = gt[0];
+      pose[1] = gt[1];
+      pose[2] = gt[2];
+      pose[3] = Am[2][1] - Am[1][2] + (cv.t[1] * gt[2] - cv.t[2] * gt[1]);
+      pose[4] = Am[0][2] - Am[2][0] + (cv.t[2] * gt[0] - cv.t[0] * gt[2]);
+      pose[5] = Am[1][0] - Am[0][1] + (cv.t[0] * gt[1] - cv.t[1] * gt[0]);
+    }
+  }
+  // deterministic per-block partial sums of the pose gradient
+  __shared__ float red[kBwdThreads / 32][6];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k) {
+    float v = pose[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float s = 0.f;
+    for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w][threadIdx.x];
+    pose_partials[6 * blockIdx.x + threadIdx.x] = s;
+  }
+}
+
+__global__ void pose_reduce_kernel(const float* __restrict__ partials, int nblocks, float* __restrict__ out) {
+  __shared__ float red[32][6];
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < 6; ++k) acc[k] += partials[6 * b + k];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 6; ++k) {
+    float v = acc[k];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][threadIdx.x];
+    out[threadIdx.x] += s;
+  }
+}
+
+}  // namespace
+
+void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key, uint32_t* tiles_touched,
+                        ushort4* rects, cudaStream_t s) {
+  if (a.n <= 0) return;
+  project_fwd_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a, feat, depth_key, tiles_touched, rects);
+}
+
+void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
+                        int tiles_x, int tiles_y, uint32_t* depth_key, uint32_t* tiles_touched, ushort4* rects,
+                        cudaStream_t s) {
+  if (n <= 0) return;
+  bin_prepare_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, mean2d, extent, depth, 1.f / (float)tile_w,
+                                                     1.f / (float)tile_h, tiles_x, tiles_y, depth_key,
+                                                     tiles_touched, rects);
+}
+
+int project_bwd_blocks(int n) { return n > 0 ? (n + kBwdThreads - 1) / kBwdThreads : 0; }
+
+int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales, float* g_quats,
+                       float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s) {
+  int nb = project_bwd_blocks(a.n);
+  if (nb == 0) return 0;
+  project_bwd_kernel<<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh,
+                                               pose_partials);
+  return nb;
+}
+
+void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s) {
+  pose_reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, dL_dpose);
+}
+
+}  // namespace gs

@@ -1,0 +1,325 @@
+// Tile binning (Sec. III-B.3: screen tiles, per-tile depth order):
+//   1. LSD radix sort of the Gaussians by the float32 bit pattern of their
+//      camera depth (z > 0, so the bits order like the values),
+//   2. duplication: each depth-sorted Gaussian writes one (tile, id) pair per
+//      covered tile, at offsets from an exclusive scan of the tile counts,
+//   3. stable LSD radix sort of the pairs by tile id only (ceil(log2 T) bits),
+//   4. per-tile [start, end) ranges.
+// Sorting depth once over N Gaussians and then only the tile bits over the P
+// pairs gives the same (tile, depth, id) order as one 64-bit key sort over P
+// at a fraction of the passes over the pair array.
+//
+// The radix sort is reduce-then-scan with a fixed grid: each block owns a
+// contiguous chunk; an upsweep builds per-block digit histograms, one block
+// scans them digit-major, and a downsweep ranks every item stably (warp
+// match + per-warp digit counts) and scatters it.  No block ever waits on
+// another block.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ uint32_t read_n(const uint32_t* n_dev, uint32_t n_host) {
+  return n_dev ? *n_dev : n_host;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t* __restrict__ keys,
+                                                              const uint32_t* n_dev, uint32_t n_host, int shift,
+                                                              uint32_t mask, uint32_t* __restrict__ ghist, int G) {
+  __shared__ uint32_t h[kRadix];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t n = read_n(n_dev, n_host);
+  const uint32_t chunk = (n + G - 1) / G;
+  const uint64_t beg64 = (uint64_t)blockIdx.x * chunk;
+  const uint32_t beg = (uint32_t)(beg64 < n ? beg64 : (uint64_t)n);
+  const uint32_t end = (uint32_t)(beg64 + chunk < n ? beg64 + chunk : (uint64_t)n);
+  for (uint32_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+  __syncthreads();
+  ghist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of len uint32 counts in place, one block
+__global__ void __launch_bounds__(kScanThreads) scan_exclusive_single(uint32_t* __restrict__ data, int len) {
+  __shared__ uint32_t s[kScanThreads];
+  const int per = (len + kScanThreads - 1) / kScanThreads;
+  const int beg = min(len, (int)threadIdx.x * per), end = min(len, beg + per);
+  uint32_t sum = 0;
+  for (int i = beg; i < end; ++i) sum += data[i];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    uint32_t v = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = s[threadIdx.x] - sum;
+  for (int i = beg; i < end; ++i) {
+    uint32_t v = data[i];
+    data[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_downsweep(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, int shift, uint32_t mask,
+    const uint32_t* __restrict__ ghist, int G) {
+  __shared__ uint32_t s_off[kRadix];
+  __shared__ uint32_t s_wc[kSortWarps][kRadix];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_off[tid] = ghist[tid * G + blockIdx.x];
+  for (int w = 0; w < kSortWarps; ++w) s_wc[w][tid] = 0;
+  const uint32_t n = read_n(n_dev, n_host);
+  const uint32_t chunk = (n + G - 1) / G;
+  const uint64_t beg64 = (uint64_t)blockIdx.x * chunk;
+  const uint32_t beg = (uint32_t)(beg64 < n ? beg64 : (uint64_t)n);
+  const uint32_t end = (uint32_t)(beg64 + chunk < n ? beg64 + chunk : (uint64_t)n);
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  __syncthreads();
+  for (uint32_t base = beg; base < end; base += kSortThreads) {
+    const uint32_t i = base + tid;
+    const bool valid = i < end;
+    uint32_t k = 0, v = 0, d = 0xFFFFFFFFu;
+    if (valid) {
+      k = kin[i];
+      v = vin ? vin[i] : i;
+      d = (k >> shift) & mask;
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+    __syncthreads();
+    {
+      uint32_t run = s_off[tid];
+#pragma unroll
+      for (int w = 0; w < kSortWarps; ++w) {
+        uint32_t c = s_wc[w][tid];
+        s_wc[w][tid] = run;
+        run += c;
+      }
+      s_off[tid] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      const uint32_t pos = s_wc[warp][d] + rank;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) s_wc[w][tid] = 0;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// duplication
+// ---------------------------------------------------------------------------
+constexpr int kDupThreads = 256;
+constexpr int kDupItems = 4;  // per thread, consecutive
+constexpr int kDupChunk = kDupThreads * kDupItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_w[kDupThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kDupThreads / 32 ? s_w[lane] : 0u;
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < kDupThreads / 32) s_w[lane] = w;
+  }
+  __syncthreads();
+  uint32_t warp_prefix = warp > 0 ? s_w[warp - 1] : 0u;
+  *total = s_w[kDupThreads / 32 - 1];
+  __syncthreads();
+  return warp_prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kDupThreads) dup_count_kernel(int n, const uint32_t* __restrict__ sorted_ids,
+                                                                const uint32_t* __restrict__ tiles,
+                                                                uint32_t* __restrict__ block_sums) {
+  const int base = blockIdx.x * kDupChunk + threadIdx.x * kDupItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kDupItems; ++j)
+    if (base + j < n) s += tiles[sorted_ids[base + j]];
+  uint32_t total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// exclusive scan of the block sums (one block), total to n_pairs
+__global__ void __launch_bounds__(kScanThreads) dup_scan_kernel(uint32_t* __restrict__ sums, int len,
+                                                                uint32_t capacity, uint32_t* __restrict__ n_pairs,
+                                                                unsigned long long* __restrict__ n_full) {
+  __shared__ unsigned long long s[kScanThreads];
+  const int per = (len + kScanThreads - 1) / kScanThreads;
+  const int beg = min(len, (int)threadIdx.x * per), end = min(len, beg + per);
+  unsigned long long sum = 0;
+  for (int i = beg; i < end; ++i) sum += sums[i];
+  s[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    unsigned long long v = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = s[threadIdx.x] - sum;
+  for (int i = beg; i < end; ++i) {
+    unsigned long long v = sums[i];
+    sums[i] = (uint32_t)(run < 0xFFFFFFFFull ? run : 0xFFFFFFFFull);
+    run += v;
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    unsigned long long tot = s[kScanThreads - 1];
+    *n_full = tot;
+    *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
+  }
+}
+
+__global__ void __launch_bounds__(kDupThreads) dup_write_kernel(
+    int n, const uint32_t* __restrict__ sorted_ids, const uint32_t* __restrict__ tiles,
+    const ushort4* __restrict__ rects, int tiles_x, const uint32_t* __restrict__ block_offsets,
+    uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals, uint32_t capacity, uint32_t* overflow) {
+  const int base = blockIdx.x * kDupChunk + threadIdx.x * kDupItems;
+  uint32_t cnt[kDupItems];
+  uint32_t id[kDupItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kDupItems; ++j) {
+    id[j] = base + j < n ? sorted_ids[base + j] : 0u;
+    cnt[j] = base + j < n ? tiles[id[j]] : 0u;
+    s += cnt[j];
+  }
+  uint32_t total;
+  uint64_t off = (uint64_t)block_offsets[blockIdx.x] + block_exclusive_scan(s, &total);
+  bool over = false;
+#pragma unroll
+  for (int j = 0; j < kDupItems; ++j) {
+    if (cnt[j] == 0) continue;
+    const ushort4 r = rects[id[j]];
+    for (int ty = r.y; ty < r.w; ++ty)
+      for (int tx = r.x; tx < r.z; ++tx) {
+        if (off < capacity) {
+          tile_keys[off] = (uint32_t)(ty * tiles_x + tx);
+          vals[off] = id[j];
+        } else {
+          over = true;
+        }
+        ++off;
+      }
+  }
+  if (over) atomicOr(overflow, 1u);
+}
+
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* n_dev, uint32_t n_host,
+                                   uint2* __restrict__ ranges) {
+  const uint32_t n = read_n(n_dev, n_host);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t k = keys[i];
+    if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+    if (i + 1 == n || keys[i + 1] != k) ranges[k].y = i + 1;
+  }
+}
+
+__global__ void export_keys_kernel(const uint32_t* __restrict__ tiles, const uint32_t* __restrict__ ids,
+                                   const uint32_t* __restrict__ depth_key, uint32_t P, uint64_t* __restrict__ keys,
+                                   uint32_t* __restrict__ ids_out) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+    const uint32_t g = ids[i];
+    keys[i] = ((uint64_t)tiles[i] << 32) | (uint64_t)depth_key[g];
+    ids_out[i] = g;
+  }
+}
+
+int sort_blocks(uint32_t n, int num_sms, int max_blocks) {
+  // about 8 rounds of 256 items per block at least; at most a few per SM
+  int g = (int)std::min<uint64_t>(((uint64_t)n + 2047) / 2048, (uint64_t)std::max(1, 4 * num_sms));
+  return std::max(1, std::min(g, max_blocks));
+}
+
+}  // namespace
+
+int radix_sort_pairs(SortBuffers& b, const uint32_t* in_k, const uint32_t* in_v, uint32_t n_max,
+                     const uint32_t* n_dev, int bits, int num_sms, cudaStream_t s, int64_t* launches) {
+  const bool in_place = in_k == b.keys[0];
+  if (n_max == 0 || bits <= 0) return in_place ? 0 : -1;
+  const int G = sort_blocks(n_max, num_sms, b.max_blocks);
+  const uint32_t* ck = in_k;
+  const uint32_t* cv = in_v;
+  int out = in_place ? 1 : 0, last = -1;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const int nb = std::min(8, bits - shift);
+    const uint32_t mask = (1u << nb) - 1u;
+    radix_upsweep<<<G, kSortThreads, 0, s>>>(ck, n_dev, n_max, shift, mask, b.hist, G);
+    scan_exclusive_single<<<1, kScanThreads, 0, s>>>(b.hist, kRadix * G);
+    radix_downsweep<<<G, kSortThreads, 0, s>>>(ck, cv, b.keys[out], b.vals[out], n_dev, n_max, shift, mask, b.hist, G);
+    if (launches) *launches += 3;
+    ck = b.keys[out];
+    cv = b.vals[out];
+    last = out;
+    out ^= 1;
+  }
+  return last;
+}
+
+int dup_blocks(int n) { return (n + kDupChunk - 1) / kDupChunk; }
+
+void launch_dup_count_scan(const DupArgs& a, cudaStream_t s, int64_t* launches) {
+  const int nb = dup_blocks(a.n);
+  if (nb == 0) {
+    cudaMemsetAsync(a.n_pairs, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(a.n_pairs_full, 0, sizeof(unsigned long long), s);
+    return;
+  }
+  dup_count_kernel<<<nb, kDupThreads, 0, s>>>(a.n, a.sorted_ids, a.tiles_touched, a.block_sums);
+  dup_scan_kernel<<<1, kScanThreads, 0, s>>>(a.block_sums, nb, a.capacity, a.n_pairs, a.n_pairs_full);
+  if (launches) *launches += 2;
+}
+
+void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches) {
+  const int nb = dup_blocks(a.n);
+  if (nb == 0) return;
+  dup_write_kernel<<<nb, kDupThreads, 0, s>>>(a.n, a.sorted_ids, a.tiles_touched, a.rects, a.tiles_x,
+                                              a.block_sums, a.tile_keys, a.vals, a.capacity, a.overflow);
+  if (launches) *launches += 1;
+}
+
+void launch_tile_ranges(const uint32_t* sorted_tiles, const uint32_t* n_dev, uint32_t n_max, uint2* ranges,
+                        int n_tiles, int num_sms, cudaStream_t s, int64_t* launches) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, s);
+  if (n_max == 0) return;
+  int g = (int)std::min<uint64_t>(((uint64_t)n_max + 255) / 256, (uint64_t)(8 * num_sms));
+  tile_ranges_kernel<<<std::max(g, 1), 256, 0, s>>>(sorted_tiles, n_dev, n_max, ranges);
+  if (launches) *launches += 1;
+}
+
+void launch_export_keys(const uint32_t* sorted_tiles, const uint32_t* sorted_ids, const uint32_t* depth_key_by_id,
+                        uint32_t P, uint64_t* keys, uint32_t* ids, cudaStream_t s) {
+  if (P == 0) return;
+  int g = (int)std::min<uint32_t>((P + 255) / 256, 1024u);
+  export_keys_kernel<<<g, 256, 0, s>>>(sorted_tiles, sorted_ids, depth_key_by_id, P, keys, ids);
+}
+
+}  // namespace gs

@@ -1,0 +1,191 @@
+"""PyTorch-facing layer over the C ABI: device memory, streams, autograd.
+
+* ``GaussianModel``   one flat float32 CUDA buffer holding the parameters in
+                      the ABI's flat layout (means | log_scales | quats |
+                      opacity_logits | sh), its gradient buffer and the Adam
+                      moments, with per-array views.
+* ``Trainer``         one optimisation iteration of GSFusion's online
+                      optimisation (Sec. III-B.3) through the ABI:
+                      gs_render_fwd -> gs_loss_l1 -> gs_render_bwd -> gs_adam_step.
+* ``render``          a torch.autograd.Function around gs_render_fwd /
+                      gs_render_bwd (gradients for every parameter array and,
+                      through a zero pose twist, the camera pose).
+
+PyTorch is used for allocation and stream handles only; every arithmetic step
+runs in libgsplat's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import abi
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def n_sh(deg: int) -> int:
+    return (deg + 1) ** 2
+
+
+def flat_sizes(n: int, deg: int):
+    K = n_sh(deg)
+    return [3 * n, 3 * n, 4 * n, n, 3 * K * n]
+
+
+def _views(flat: torch.Tensor, n: int, deg: int) -> dict:
+    K = n_sh(deg)
+    shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, K, 3)]
+    out, off = {}, 0
+    for name, size, shape in zip(PARAM_NAMES, flat_sizes(n, deg), shapes):
+        out[name] = flat[off:off + size].view(shape)
+        off += size
+    return out
+
+
+class GaussianModel:
+    """Gaussian map in one flat buffer (plus gradient and Adam moments)."""
+
+    def __init__(self, params: dict, device="cuda"):
+        deg = int(params["sh_degree"])
+        n = int(np.asarray(params["means"]).shape[0])
+        self.n, self.sh_degree = n, deg
+        total = sum(flat_sizes(n, deg))
+        host = np.concatenate([np.asarray(params[k], np.float32).ravel() for k in PARAM_NAMES]) if n else \
+            np.zeros(0, np.float32)
+        assert host.size == total
+        self.flat = torch.from_numpy(host).to(device)
+        self.grad = torch.zeros_like(self.flat)
+        self.m = torch.zeros_like(self.flat)
+        self.v = torch.zeros_like(self.flat)
+        self.p = _views(self.flat, n, deg)
+        self.g = _views(self.grad, n, deg)
+
+    def gaussians(self) -> abi.gs_gaussians:
+        p = self.p
+        return abi.make_gaussians(p["means"], p["log_scales"], p["quats"], p["opacity_logits"], p["sh"],
+                                  self.sh_degree)
+
+    def grads(self) -> abi.gs_grads:
+        g = self.g
+        return abi.make_grads(g["means"], g["log_scales"], g["quats"], g["opacity_logits"], g["sh"])
+
+    def numpy_params(self) -> dict:
+        out = {k: v.detach().cpu().numpy().copy() for k, v in self.p.items()}
+        out["sh_degree"] = self.sh_degree
+        return out
+
+
+def camera_struct(cam) -> abi.gs_camera:
+    return abi.make_camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+
+
+class Context:
+    """Owns one gs_ctx handle."""
+
+    def __init__(self, device: int = 0, pair_capacity: int = 0):
+        self.handle = abi.gs_ctx_create(device, pair_capacity)
+
+    def close(self):
+        if self.handle:
+            abi.gs_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        return abi.gs_get_stats(self.handle)
+
+
+class Trainer:
+    """One view, one map: fwd + L1 loss + bwd + Adam per ``step``."""
+
+    def __init__(self, model: GaussianModel, cam, R, t, raster_cfg=None, adam_cfg=None, w_color=0.8, w_depth=0.2,
+                 ctx: Context | None = None, device: int = 0):
+        self.model = model
+        self.ctx = ctx or Context(device)
+        self.cam = camera_struct(cam)
+        self.view = abi.make_viewmat(R, t)
+        self.rcfg = raster_cfg or abi.raster_cfg()
+        self.acfg = adam_cfg or abi.adam_cfg(zero_grads=1)
+        self.w_color, self.w_depth = float(w_color), float(w_depth)
+        H, W = cam.height, cam.width
+        dev = model.flat.device
+        self.color = torch.empty((3, H, W), device=dev)
+        self.depth = torch.empty((H, W), device=dev)
+        self.alpha = torch.empty((H, W), device=dev)
+        self.dLdc = torch.empty((3, H, W), device=dev)
+        self.dLdd = torch.empty((H, W), device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.step_count = 0
+        self._g = model.gaussians()
+        self._gr = model.grads()
+
+    def forward(self, stream=None):
+        abi.gs_render_fwd(self.ctx.handle, self._g, self.cam, self.view, self.rcfg, self.color, self.depth,
+                          self.alpha, stream)
+
+    def step(self, target_rgb: torch.Tensor, target_depth: torch.Tensor, stream=None):
+        """One iteration; the loss of the rendered image stays on the device in
+        ``self.loss``.  Gradients are cleared by the Adam kernel."""
+        h = self.ctx.handle
+        self.forward(stream)
+        abi.gs_loss_l1(h, self.cam, self.color, self.depth, target_rgb, target_depth, self.w_color, self.w_depth,
+                       self.loss, self.dLdc, self.dLdd, stream)
+        abi.gs_render_bwd(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, self._gr, None,
+                          stream)
+        self.step_count += 1
+        m = self.model
+        abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
+        return self.loss
+
+
+class _Render(torch.autograd.Function):
+    @staticmethod
+    def forward(actx, means, log_scales, quats, opacity_logits, sh, pose_xi, meta):
+        ctx, cam, view, rcfg, deg = meta
+        g = abi.make_gaussians(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                               opacity_logits.contiguous(), sh.contiguous(), deg)
+        H, W = cam.height, cam.width
+        color = torch.empty((3, H, W), device=means.device)
+        depth = torch.empty((H, W), device=means.device)
+        alpha = torch.empty((H, W), device=means.device)
+        abi.gs_render_fwd(ctx.handle, g, cam, view, rcfg, color, depth, alpha)
+        actx.meta = meta
+        actx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
+        actx.pose_device = pose_xi.device if pose_xi is not None else None
+        return color, depth, alpha
+
+    @staticmethod
+    def backward(actx, gc, gd, ga):
+        ctx, cam, view, rcfg, deg = actx.meta
+        means, log_scales, quats, opacity_logits, sh = actx.saved_tensors
+        g = abi.make_gaussians(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
+                               opacity_logits.contiguous(), sh.contiguous(), deg)
+        grads = [torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh)]
+        gp = torch.zeros(6, device=means.device)
+        zero = torch.zeros((cam.height, cam.width), device=means.device)
+        gc = gc.contiguous() if gc is not None else torch.zeros((3, cam.height, cam.width), device=means.device)
+        gd = gd.contiguous() if gd is not None else zero
+        ga = ga.contiguous() if ga is not None else None
+        abi.gs_render_bwd(ctx.handle, g, cam, view, rcfg, gc, gd, ga, abi.make_grads(*grads), gp)
+        pose_grad = gp.to(actx.pose_device) if actx.pose_device is not None else None
+        return (*grads, pose_grad, None)
+
+
+def render(ctx: Context, params: dict, sh_degree: int, cam, R, t, raster_cfg=None, pose_xi=None):
+    """Differentiable render of (colour [3, H, W], depth [H, W], alpha [H, W]).
+
+    ``params`` maps the five parameter names to CUDA float32 tensors.  If
+    ``pose_xi`` (a zero 6-vector with requires_grad) is given, its gradient is
+    dL/dxi of the left perturbation exp(xi^) T_CW at xi = 0."""
+    cam_s = camera_struct(cam)
+    view = abi.make_viewmat(R, t)
+    rcfg = raster_cfg or abi.raster_cfg()
+    meta = (ctx, cam_s, view, rcfg, int(sh_degree))
+    return _Render.apply(params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
+                         params["sh"], pose_xi, meta)

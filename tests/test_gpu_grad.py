@@ -1,0 +1,108 @@
+"""Backward pass on the GPU vs the oracle's autograd gradients (and, for the
+autograd Function, vs central differences of the GPU forward).
+
+Gradient tolerance: per parameter array ||g - o|| / ||o|| <= 1e-3 and
+element-wise |g - o| <= 1e-3 |o| + 1e-4 max|o|, with a small budget for
+elements touched by a float32/float64 decision flip."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as R
+from synth import workloads
+from synth.scene import Camera, Pose, look_at
+from tests._util import compare, ensure_built, gpu_backward, gpu_render, to_gpu_model
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ensure_built()
+    from paper_2408_12677_gb300.torch_api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _all_pixels(cam):
+    jj, ii = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    return np.stack([ii.ravel(), jj.ravel()], 1)
+
+
+def _check_grads(ctx, P, deg, cam, pose, seed, with_alpha=True, **cfg):
+    rng = np.random.default_rng(seed)
+    H, W = cam.height, cam.width
+    wc = rng.standard_normal((3, H, W)).astype(np.float32)
+    wd = rng.standard_normal((H, W)).astype(np.float32)
+    wa = rng.standard_normal((H, W)).astype(np.float32) if with_alpha else None
+    model = to_gpu_model(P)
+    gpu_render(ctx, model, cam, pose, **cfg)
+    g = gpu_backward(ctx, model, cam, pose, wc, wd, wa, **cfg)
+    og, _ = R.weighted_pixel_gradients(P, deg, cam, pose.R.astype(np.float64), pose.t.astype(np.float64),
+                                       _all_pixels(cam), wc.reshape(3, -1).astype(np.float64),
+                                       wd.reshape(-1).astype(np.float64),
+                                       None if wa is None else wa.reshape(-1).astype(np.float64), prefilter=True)
+    budget = max(2, int(0.002 * P["means"].shape[0]))
+    for k in NAMES + ("pose",):
+        ref = og[k].detach().numpy()
+        scale = np.abs(ref).max() if ref.size else 0.0
+        compare(k, g[k], ref, 1e-3, 1e-4 * scale + 1e-12, 1e-3, budget if k != "pose" else 0)
+
+
+def test_tiny_random_gradients(ctx):
+    w = workloads.tiny_random(seed=1000)
+    _check_grads(ctx, w.params, 0, w.views[0].cam, w.views[0].pose, 1)
+
+
+@pytest.mark.parametrize("tile", [(8, 32), (32, 8)])
+def test_gradients_sh3_posed(ctx, tile):
+    cam = Camera(80.0, 75.0, 40.0, 30.0, 84, 60)
+    pose = look_at([0.1, 0.2, -0.1], [0.7, 3.0, 0.2])
+    P = workloads.random_gaussians(np.random.default_rng(5), 700, cam, pose, 3, log_scale_range=(-3.5, -1.5),
+                                   sh_rest_std=0.15)
+    _check_grads(ctx, P, 3, cam, pose, 2, tile_w=tile[0], tile_h=tile[1])
+
+
+def test_gradients_without_alpha_upstream(ctx):
+    w = workloads.tiny_random(seed=1001, n=300, sh_degree=1, sh_rest_std=0.2)
+    _check_grads(ctx, w.params, 1, w.views[0].cam, w.views[0].pose, 3, with_alpha=False)
+
+
+def test_autograd_function_matches_abi_and_fd(ctx):
+    from paper_2408_12677_gb300.torch_api import render
+    cam = Camera(40.0, 40.0, 20.0, 16.0, 40, 32)
+    pose = look_at([0.0, 0.0, 0.0], [0.2, 3.0, 0.1])
+    P = workloads.random_gaussians(np.random.default_rng(11), 60, cam, pose, 3, z_range=(1.0, 2.5),
+                                   log_scale_range=(-2.6, -1.8), sh_rest_std=0.1)
+    T = {k: torch.tensor(np.asarray(P[k], np.float32), device="cuda", requires_grad=True) for k in NAMES}
+    xi = torch.zeros(6, requires_grad=True)
+    rng = np.random.default_rng(4)
+    wc = torch.tensor(rng.standard_normal((3, 32, 40)), dtype=torch.float32, device="cuda")
+    wd = torch.tensor(rng.standard_normal((32, 40)), dtype=torch.float32, device="cuda")
+    col, dep, alp = render(ctx, T, 3, cam, pose.R, pose.t, pose_xi=xi)
+    obj = (col * wc).sum() + (dep * wd).sum()
+    obj.backward()
+    og, _ = R.weighted_pixel_gradients(P, 3, cam, pose.R.astype(np.float64), pose.t.astype(np.float64),
+                                       _all_pixels(cam), wc.cpu().numpy().reshape(3, -1).astype(np.float64),
+                                       wd.cpu().numpy().reshape(-1).astype(np.float64), None)
+    for k in NAMES:
+        ref = og[k].detach().numpy()
+        compare(k, T[k].grad.cpu().numpy(), ref, 1e-3, 1e-4 * np.abs(ref).max(), 1e-3, 2)
+    compare("pose", xi.grad.numpy(), og["pose"].numpy(), 1e-3, 1e-4 * np.abs(og["pose"].numpy()).max(), 1e-3)
+    # central differences of the float32 GPU forward on a few large gradient entries
+    for k in ("means", "log_scales", "opacity_logits", "sh"):
+        g = T[k].grad.reshape(-1)
+        i = int(torch.argmax(g.abs()))
+        h = 2e-3
+        vals = []
+        for s in (1.0, -1.0):
+            with torch.no_grad():
+                T2 = {kk: vv.detach().clone() for kk, vv in T.items()}
+                T2[k].reshape(-1)[i] += s * h
+                c2, d2, _ = render(ctx, T2, 3, cam, pose.R, pose.t)
+                vals.append(float((c2 * wc).sum() + (d2 * wd).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - float(g[i])) <= 3e-2 * abs(float(g[i])) + 1e-3, (k, fd, float(g[i]))

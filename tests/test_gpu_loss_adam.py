@@ -1,0 +1,75 @@
+"""Loss kernel and Adam kernel vs the oracle, on identical inputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adam as oadam
+from oracle import render as R
+from synth.scene import Camera
+from tests._util import compare, ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ensure_built()
+    from paper_2408_12677_gb300.torch_api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("H,W", [(48, 64), (70, 100), (680, 1200)])
+def test_loss_l1(ctx, H, W):
+    from paper_2408_12677_gb300 import abi
+    rng = np.random.default_rng(H)
+    col = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    dep = rng.uniform(0.5, 4, (H, W)).astype(np.float32)
+    trgb = rng.uniform(0, 1, (3, H, W)).astype(np.float32)
+    tdep = rng.uniform(0.5, 4, (H, W)).astype(np.float32)
+    tdep[rng.uniform(0, 1, (H, W)) < 0.1] = 0.0
+    trgb[0, 0, :5] = col[0, 0, :5]  # exact zeros of the residual: sign(0) = 0
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    gc = torch.empty((3, H, W), device="cuda")
+    gd = torch.empty((H, W), device="cuda")
+    cam = abi.make_camera(1, 1, 0, 0, W, H)
+    abi.gs_loss_l1(ctx.handle, cam, t(col), t(dep), t(trgb), t(tdep), 0.8, 0.2, loss, gc, gd)
+    L, rc, rd = R.loss_image_grads(col, dep, trgb, tdep)
+    assert abs(float(loss) - float(L)) <= 1e-5 * abs(float(L))
+    np.testing.assert_allclose(gc.cpu().numpy(), rc.numpy(), rtol=1e-6, atol=0)
+    np.testing.assert_allclose(gd.cpu().numpy(), rd.numpy(), rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("n,deg", [(1000, 3), (777, 0), (5, 2)])
+def test_adam_matches_oracle_over_steps(ctx, n, deg):
+    from paper_2408_12677_gb300 import abi
+    cfg = oadam.AdamCfg(lr_means=1e-3, eps=1e-8)
+    rng = np.random.default_rng(n)
+    size = oadam.flat_size(n, deg)
+    p0 = rng.standard_normal(size).astype(np.float32)
+    p = torch.tensor(p0, device="cuda")
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    acfg = abi.adam_cfg(lr_means=cfg.lr_means, lr_log_scales=cfg.lr_log_scales, lr_quats=cfg.lr_quats,
+                        lr_opacity=cfg.lr_opacity, lr_sh_dc=cfg.lr_sh_dc, lr_sh_rest=cfg.lr_sh_rest, eps=cfg.eps)
+    rp, rm, rv = p0.astype(np.float64), np.zeros(size), np.zeros(size)
+    lr = oadam.lr_per_element(n, deg, cfg)
+    for step in range(1, 6):
+        g = (rng.standard_normal(size) * rng.uniform(0.1, 10, size)).astype(np.float32)
+        gt = torch.tensor(g, device="cuda")
+        # feed the oracle the GPU's own float32 state so each step compares one update
+        rp, rm, rv = p.cpu().numpy().astype(np.float64), m.cpu().numpy().astype(np.float64), \
+            v.cpu().numpy().astype(np.float64)
+        abi.gs_adam_step(ctx.handle, p, gt, m, v, n, deg, acfg, step)
+        rp, rm, rv = oadam.adam_step(rp, g, rm, rv, step, lr, cfg)
+        torch.cuda.synchronize()
+        compare("p", p.cpu().numpy(), rp, 1e-6, 1e-7, 1e-7)
+        compare("m", m.cpu().numpy(), rm, 1e-5, 1e-7, 1e-6)
+        compare("v", v.cpu().numpy(), rv, 1e-5, 1e-7, 1e-6)
+    # zero_grads clears the consumed gradient
+    gt = torch.ones(size, device="cuda")
+    abi.gs_adam_step(ctx.handle, p, gt, m, v, n, deg, abi.adam_cfg(zero_grads=1), 6)
+    torch.cuda.synchronize()
+    assert float(gt.abs().max()) == 0.0
