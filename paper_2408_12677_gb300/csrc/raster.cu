@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
           v[9] = w * dC2;
           v[6] = w * dD;
           const float cdot = c.x * dC0 + c.y * dC1 + c.z * dC2 + bb.z * dD;
-          const float g_alpha = Ti * cdot - (U + dA_T) * inv1m;
+          // d/d alpha_i: colour/depth T_i c_i - (sum behind)/(1 - alpha_i); alpha image + T_final/(1 - alpha_i)
+          const float g_alpha = Ti * cdot - (U - dA_T) * inv1m;
           U = fmaf(w, cdot, U);
           T = Ti;
           if (e.araw <= rp.alpha_max) {

@@ -56,9 +56,8 @@ def test_sparse_upstream_gradient_matches_oracle(setup):
     g = gpu_backward(ctx, model, v.cam, v.pose, wc_img, wd_img, None)
     og, _ = R.weighted_pixel_gradients(w.params, 3, v.cam, v.pose.R.astype(np.float64), v.pose.t.astype(np.float64),
                                        pix, wc.astype(np.float64), wd.astype(np.float64), None, prefilter=True)
-    for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "pose"):
-        ref = og[k].detach().numpy()
-        compare(k, g[k], ref, 1e-3, 1e-4 * np.abs(ref).max(), 1e-3, 0 if k == "pose" else 20)
+    from tests.test_gpu_grad import check_grad_arrays
+    check_grad_arrays(g, og, 20)
 
 
 def test_training_iterations_reduce_loss(setup):

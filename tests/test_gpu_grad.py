@@ -2,8 +2,12 @@
 autograd Function, vs central differences of the GPU forward).
 
 Gradient tolerance: per parameter array ||g - o|| / ||o|| <= 1e-3 and
-element-wise |g - o| <= 1e-3 |o| + 1e-4 max|o|, with a small budget for
-elements touched by a float32/float64 decision flip."""
+element-wise |g - o| <= 1e-3 |o| + 1e-4 max|o| + 1e-6 G, with G the largest
+gradient entry over all parameter arrays (float32 cancellation floor: e.g. the
+quaternion gradient of an isotropic Gaussian is exactly 0 but sums float32
+terms of size ~G), and a small budget for elements touched by a
+float32/float64 decision flip.  Arrays whose exact gradient is 0 are checked
+against the floor only."""
 import numpy as np
 import pytest
 import torch
@@ -46,10 +50,19 @@ def _check_grads(ctx, P, deg, cam, pose, seed, with_alpha=True, **cfg):
                                        wd.reshape(-1).astype(np.float64),
                                        None if wa is None else wa.reshape(-1).astype(np.float64), prefilter=True)
     budget = max(2, int(0.002 * P["means"].shape[0]))
-    for k in NAMES + ("pose",):
+    check_grad_arrays(g, og, budget)
+
+
+def check_grad_arrays(g, og, budget, names=NAMES + ("pose",)):
+    G = max(float(np.abs(og[k].detach().numpy()).max(initial=0.0)) for k in NAMES)
+    for k in names:
         ref = og[k].detach().numpy()
-        scale = np.abs(ref).max() if ref.size else 0.0
-        compare(k, g[k], ref, 1e-3, 1e-4 * scale + 1e-12, 1e-3, budget if k != "pose" else 0)
+        scale = np.abs(ref).max(initial=0.0)
+        floor = 1e-4 * scale + 1e-6 * G + 1e-12
+        if scale <= 1e-6 * G:  # exact gradient is (numerically) zero
+            assert np.abs(g[k]).max(initial=0.0) <= 1e-5 * G, (k, np.abs(g[k]).max())
+            continue
+        compare(k, g[k], ref, 1e-3, floor, 1e-3, budget if k != "pose" else 0)
 
 
 def test_tiny_random_gradients(ctx):
@@ -88,10 +101,9 @@ def test_autograd_function_matches_abi_and_fd(ctx):
     og, _ = R.weighted_pixel_gradients(P, 3, cam, pose.R.astype(np.float64), pose.t.astype(np.float64),
                                        _all_pixels(cam), wc.cpu().numpy().reshape(3, -1).astype(np.float64),
                                        wd.cpu().numpy().reshape(-1).astype(np.float64), None)
-    for k in NAMES:
-        ref = og[k].detach().numpy()
-        compare(k, T[k].grad.cpu().numpy(), ref, 1e-3, 1e-4 * np.abs(ref).max(), 1e-3, 2)
-    compare("pose", xi.grad.numpy(), og["pose"].numpy(), 1e-3, 1e-4 * np.abs(og["pose"].numpy()).max(), 1e-3)
+    got = {k: T[k].grad.cpu().numpy() for k in NAMES}
+    got["pose"] = xi.grad.numpy()
+    check_grad_arrays(got, og, 2)
     # central differences of the float32 GPU forward on a few large gradient entries
     for k in ("means", "log_scales", "opacity_logits", "sh"):
         g = T[k].grad.reshape(-1)

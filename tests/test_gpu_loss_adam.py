@@ -45,7 +45,11 @@ def test_loss_l1(ctx, H, W):
 @pytest.mark.parametrize("n,deg", [(1000, 3), (777, 0), (5, 2)])
 def test_adam_matches_oracle_over_steps(ctx, n, deg):
     from paper_2408_12677_gb300 import abi
-    cfg = oadam.AdamCfg(lr_means=1e-3, eps=1e-8)
+    # the ABI takes float32 hyper-parameters: give the oracle the same values
+    f32 = lambda x: float(np.float32(x))
+    cfg = oadam.AdamCfg(lr_means=f32(1e-3), lr_log_scales=f32(5e-3), lr_quats=f32(1e-3), lr_opacity=f32(5e-2),
+                        lr_sh_dc=f32(2.5e-3), lr_sh_rest=f32(1.25e-4), beta1=f32(0.9), beta2=f32(0.999),
+                        eps=f32(1e-8))
     rng = np.random.default_rng(n)
     size = oadam.flat_size(n, deg)
     p0 = rng.standard_normal(size).astype(np.float32)
