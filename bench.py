@@ -190,11 +190,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_host_s = time.perf_counter() - t_host0
     h2d = h_rgb.numel() * 4 + h_dep.numel() * 4
 
-    times = torch.tensor([ms_total, e2e_ms], dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    ms_total, e2e_ms = float(times[0]), float(times[1])
+    ms_total, e2e_ms = max_over_ranks([ms_total, e2e_ms], world)
 
     # roofline of the dominant kernel (per launch, CUDA events over the timed region)
     npx = H * W
@@ -209,7 +205,7 @@ def run_ours(args, rank, world, local_rank):
     dom_ms = per_stage[dom]["ms_per_launch"]
     achieved = alg[dom] / (dom_ms * 1e-3) / 1e9 if dom_ms else 0.0
     traffic = load_traffic(dom)
-    it_s = world * args.steps / (ms_total * 1e-3)
+    it_s = whole_job_rate(args.steps, world, ms_total)
     b_alg_iter = sum(alg.values())
     out = {
         "metric": METRIC, "value": it_s, "unit": "it/s", "n_gpus": world, "steps": args.steps,
@@ -227,13 +223,28 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg[dom], "ms_per_launch": dom_ms},
         "stages": per_stage,
-        "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "it/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_rate(args.steps, world, e2e_ms), "unit": "it/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4, "host_wall_s": e2e_host_s},
         "gpu_launches": launches,
         "clocks": clk,
         "loss_end": loss_end,
     }
     return out
+
+
+def max_over_ranks(values, world):
+    """Element-wise maximum of per-rank timings (gloo/NCCL all-reduce)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_rate(steps, world, max_ms):
+    """Iterations per second of the whole job: every rank ran ``steps``."""
+    return world * steps / (max_ms * 1e-3)
 
 
 def load_traffic(kernel):
