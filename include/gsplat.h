@@ -206,6 +206,30 @@ gs_status gs_loss_l1(gs_ctx *ctx, const gs_camera *cam, const float *color, cons
                      const float *target_rgb, const float *target_depth, float w_color, float w_depth,
                      float *loss, float *dL_dcolor, float *dL_ddepth, gs_stream_t stream);
 
+/* Largest image gs_loss_l1_noalloc accepts: 2^24 pixels (e.g. 4096 x 4096). */
+#define GS_LOSS_NOALLOC_MAX_PIXELS (1 << 24)
+
+/* gs_loss_l1 without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory,
+ * such as a process whose GPU memory all belongs to its own pool (a raw
+ * cudaMalloc would fail or fragment it) or a latency-critical loop that cannot
+ * absorb an allocation and the synchronisation it implies.  Same arguments
+ * (minus the context), outputs and results as gs_loss_l1.  It runs on the
+ * calling thread's current CUDA device and takes its scratch from a fixed
+ * array compiled into the library (about 96 KB on every GPU that loads the
+ * library, held until the process exits); it calls no cudaMalloc/cudaFree.
+ * - Images larger than GS_LOSS_NOALLOC_MAX_PIXELS pixels are rejected with
+ *   GS_ERR_CAPACITY before anything is enqueued.
+ * - The first call on a device looks up that device's address of the array;
+ *   make this first call before any stream capture on that device.
+ * - Every call on a device uses the same array: calls whose kernels may
+ *   overlap on the GPU (different streams with no ordering between them)
+ *   race and give wrong results.  Calls ordered on one stream are safe, since
+ *   each call writes every scratch value before it reads it. */
+gs_status gs_loss_l1_noalloc(const gs_camera *cam, const float *color, const float *depth,
+                             const float *target_rgb, const float *target_depth, float w_color, float w_depth,
+                             float *loss, float *dL_dcolor, float *dL_ddepth, gs_stream_t stream);
+
 /* One dense Adam step over the flat parameter buffer (layout above):
  *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
  *   p -= lr_group * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).

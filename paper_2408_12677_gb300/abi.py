@@ -87,6 +87,7 @@ EXPORTS = {
     "gs_bin_tiles": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int64,
                                C.POINTER(C.c_int64), P]),
     "gs_get_projection": (C.c_int, [P, P, P, P, P, P, P, P]),
+    "gs_loss_l1_noalloc": (C.c_int, [C.POINTER(gs_camera), P, P, P, P, C.c_float, C.c_float, P, P, P, P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
     "gs_set_profiling": (C.c_int, [P, C.c_int]),
     "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -263,6 +264,17 @@ def gs_loss_l1(ctx, cam, color, depth, target_rgb, target_depth, w_color, w_dept
                            float(w_depth), _f32(loss, "loss"), _f32(dL_dcolor, "dL_dcolor"),
                            _f32(dL_ddepth, "dL_ddepth"), _stream(stream))
     _check(ctx, st, "gs_loss_l1")
+
+
+def gs_loss_l1_noalloc(cam, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor, dL_ddepth,
+                       stream=None):
+    """gs_loss_l1 for callers that must not allocate device memory (scratch
+    comes from a fixed array inside the library; see include/gsplat.h)."""
+    st = load().gs_loss_l1_noalloc(C.byref(cam), _f32(color, "color"), _f32(depth, "depth"),
+                                   _f32(target_rgb, "target_rgb"), _f32(target_depth, "target_depth"), float(w_color),
+                                   float(w_depth), _f32(loss, "loss"), _f32(dL_dcolor, "dL_dcolor"),
+                                   _f32(dL_ddepth, "dL_ddepth"), _stream(stream))
+    _check(None, st, "gs_loss_l1_noalloc")
 
 
 def gs_adam_step(ctx, params, grads, m, v, n: int, sh_degree: int, cfg: gs_adam_cfg, step: int, stream=None):
