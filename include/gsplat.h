@@ -198,6 +198,20 @@ gs_status gs_render_bwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam
                         const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,
                         const gs_grads *grads, float *dL_dpose, gs_stream_t stream);
 
+/* One single-view optimisation iteration's backward half (Sec. III-B.3:
+ * each iteration optimises the map on one frame): the backward pass of the
+ * most recent gs_render_fwd fused with the Adam step.  Computes exactly
+ * gs_render_bwd into zeroed gradients followed by gs_adam_step, but never
+ * writes the parameter gradients: each Gaussian's gradient is applied by the
+ * thread that computes it.  `params` is the flat parameter buffer (layout
+ * above) that `g` must point into; m, v are the Adam moments (same layout);
+ * step >= 1.  cfg->zero_grads is ignored.  dL_dpose as in gs_render_bwd. */
+gs_status gs_render_bwd_adam(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam,
+                             const gs_viewmat *view, const gs_raster_cfg *cfg,
+                             const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,
+                             float *params, float *m, float *v, const gs_adam_cfg *adam, int64_t step,
+                             float *dL_dpose, gs_stream_t stream);
+
 /* Photometric loss (Eq. 12) plus a depth term:
  *   L = w_color * mean over 3HW of |color - target_rgb|
  *     + w_depth * mean over pixels with target_depth > 0 of |depth - target_depth|.

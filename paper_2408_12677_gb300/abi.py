@@ -82,6 +82,9 @@ EXPORTS = {
                                 C.POINTER(gs_raster_cfg), P, P, P, P]),
     "gs_render_bwd": (C.c_int, [P, C.POINTER(gs_gaussians), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                                 C.POINTER(gs_raster_cfg), P, P, P, C.POINTER(gs_grads), P, P]),
+    "gs_render_bwd_adam": (C.c_int, [P, C.POINTER(gs_gaussians), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                                     C.POINTER(gs_raster_cfg), P, P, P, P, P, P, C.POINTER(gs_adam_cfg), C.c_int64,
+                                     P, P]),
     "gs_loss_l1": (C.c_int, [P, C.POINTER(gs_camera), P, P, P, P, C.c_float, C.c_float, P, P, P, P]),
     "gs_adam_step": (C.c_int, [P, P, P, P, P, C.c_int64, C.c_int32, C.POINTER(gs_adam_cfg), C.c_int64, P]),
     "gs_bin_tiles": (C.c_int, [P, C.c_int64, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P, C.c_int64,
@@ -255,6 +258,15 @@ def gs_render_bwd(ctx, gaussians, cam, view, cfg, dL_dcolor, dL_ddepth, dL_dalph
                               _f32(dL_dalpha, "dL_dalpha"), C.byref(grads), _f32(dL_dpose, "dL_dpose"),
                               _stream(stream))
     _check(ctx, st, "gs_render_bwd")
+
+
+def gs_render_bwd_adam(ctx, gaussians, cam, view, cfg, dL_dcolor, dL_ddepth, dL_dalpha, params, m, v,
+                       adam: gs_adam_cfg, step: int, dL_dpose=None, stream=None):
+    st = load().gs_render_bwd_adam(ctx, C.byref(gaussians), C.byref(cam), C.byref(view), C.byref(cfg),
+                                   _f32(dL_dcolor, "dL_dcolor"), _f32(dL_ddepth, "dL_ddepth"),
+                                   _f32(dL_dalpha, "dL_dalpha"), _f32(params, "params"), _f32(m, "m"), _f32(v, "v"),
+                                   C.byref(adam), int(step), _f32(dL_dpose, "dL_dpose"), _stream(stream))
+    _check(ctx, st, "gs_render_bwd_adam")
 
 
 def gs_loss_l1(ctx, cam, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor, dL_ddepth,

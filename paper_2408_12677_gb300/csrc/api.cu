@@ -243,7 +243,7 @@ CamView make_camview(const gs_camera* cam, const gs_viewmat* v) {
 gs_status ensure_hist(gs_ctx* c) {
   const int want = 4 * std::max(c->num_sms, 1);
   if (c->hist && c->hist_blocks >= want) return GS_OK;
-  GS_CUDA(c, regrow(&c->hist, (int64_t)256 * want));
+  GS_CUDA(c, regrow(&c->hist, (int64_t)256 * (want + 1)));
   c->hist_blocks = want;
   return GS_OK;
 }
@@ -599,26 +599,25 @@ gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
   return GS_OK;
 }
 
-gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                        const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
-                        const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
-  if (!c) return GS_ERR_INVALID_ARG;
+namespace {
+
+gs_status check_bwd_common(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                           const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth) {
   gs_status st;
   if ((st = check_gauss(c, g)) != GS_OK || (st = check_cam(c, cam)) != GS_OK || (st = check_cfg(c, cfg)) != GS_OK)
     return st;
-  if (!view || !grads) return fail(c, GS_ERR_INVALID_ARG, "viewmat or grads is NULL");
+  if (!view) return fail(c, GS_ERR_INVALID_ARG, "viewmat is NULL");
   if (!dL_dcolor || !dL_ddepth) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
-  if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
-    return fail(c, GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
   if (!c->have_state || c->st_n != g->n || c->st_w != cam->width || c->st_h != cam->height ||
       c->st_tw != cfg->tile_w || c->st_th != cfg->tile_h || c->st_sh != g->sh_degree)
-    return fail(c, GS_ERR_STATE, "gs_render_bwd needs the matching gs_render_fwd on this context");
-  cudaStream_t s = (cudaStream_t)stream;
-  GS_CUDA(c, cudaSetDevice(c->device));
-  const int n = (int)g->n;
-  if (n == 0) return GS_OK;
-  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)n, s));
+    return fail(c, GS_ERR_STATE, "the backward pass needs the matching gs_render_fwd on this context");
+  return GS_OK;
+}
 
+// raster backward into the context's per-Gaussian gradient records
+gs_status raster_backward(gs_ctx* c, const gs_camera* cam, const gs_raster_cfg* cfg, const float* dL_dcolor,
+                          const float* dL_ddepth, const float* dL_dalpha, int n, cudaStream_t s) {
+  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)n, s));
   RasterArgs ra;
   ra.width = cam->width;
   ra.height = cam->height;
@@ -639,9 +638,13 @@ gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
   }
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_bwd");
+  return GS_OK;
+}
 
+ProjectArgs project_args(const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                         const gs_raster_cfg* cfg, int tiles_x, int tiles_y) {
   ProjectArgs pa;
-  pa.n = n;
+  pa.n = (int)g->n;
   pa.means = g->means;
   pa.log_scales = g->log_scales;
   pa.quats = g->quats;
@@ -654,8 +657,84 @@ gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
   pa.alpha_min = cfg->alpha_min;
   pa.tile_w = cfg->tile_w;
   pa.tile_h = cfg->tile_h;
-  pa.tiles_x = c->st_tx;
-  pa.tiles_y = c->st_ty;
+  pa.tiles_x = tiles_x;
+  pa.tiles_y = tiles_y;
+  return pa;
+}
+
+gs_status check_adam(gs_ctx* c, const gs_adam_cfg* cfg, int64_t step) {
+  if (!cfg || step < 1) return fail(c, GS_ERR_INVALID_ARG, "Adam: bad cfg or step");
+  if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
+    return fail(c, GS_ERR_INVALID_ARG, "Adam: betas must be in [0, 1), eps >= 0");
+  return GS_OK;
+}
+
+AdamArgs adam_args(const gs_adam_cfg* cfg, int64_t step) {
+  AdamArgs ad;
+  ad.lr[0] = cfg->lr_means;
+  ad.lr[1] = cfg->lr_log_scales;
+  ad.lr[2] = cfg->lr_quats;
+  ad.lr[3] = cfg->lr_opacity;
+  ad.lr[4] = cfg->lr_sh_dc;
+  ad.lr[5] = cfg->lr_sh_rest;
+  ad.beta1 = cfg->beta1;
+  ad.beta2 = cfg->beta2;
+  ad.eps = cfg->eps;
+  const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
+  const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
+  ad.step_scale = (float)(1.0 / bc1);
+  ad.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+  return ad;
+}
+
+}  // namespace
+
+gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                             const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
+                             const float* dL_dalpha, float* params, float* m, float* v, const gs_adam_cfg* adam,
+                             int64_t step, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_bwd_common(c, g, cam, view, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
+  if ((st = check_adam(c, adam, step)) != GS_OK) return st;
+  const int64_t n = g->n;
+  if (n > 0 && (!params || !m || !v)) return fail(c, GS_ERR_INVALID_ARG, "params, m and v are required");
+  if (n > 0 && (g->means != params || g->log_scales != params + 3 * n || g->quats != params + 6 * n ||
+                g->opacity_logits != params + 10 * n || g->sh != params + 11 * n))
+    return fail(c, GS_ERR_INVALID_ARG, "the Gaussian arrays must be the flat parameter buffer's blocks");
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  if (n == 0) return GS_OK;
+  if ((st = raster_backward(c, cam, cfg, dL_dcolor, dL_ddepth, dL_dalpha, (int)n, s)) != GS_OK) return st;
+  const ProjectArgs pa = project_args(g, cam, view, cfg, c->st_tx, c->st_ty);
+  {
+    StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
+    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, adam_args(adam, step), c->pose_partials, s);
+    c->launches += 1;
+    if (dL_dpose) {
+      launch_pose_reduce(c->pose_partials, nb, dL_dpose, s);
+      c->launches += 1;
+    }
+  }
+  GS_CHECK_LAUNCH(c, "project_bwd_adam");
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
+                        const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_bwd_common(c, g, cam, view, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
+  if (!grads) return fail(c, GS_ERR_INVALID_ARG, "grads is NULL");
+  if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
+    return fail(c, GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const int n = (int)g->n;
+  if (n == 0) return GS_OK;
+  if ((st = raster_backward(c, cam, cfg, dL_dcolor, dL_ddepth, dL_dalpha, n, s)) != GS_OK) return st;
+  const ProjectArgs pa = project_args(g, cam, view, cfg, c->st_tx, c->st_ty);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
     const int nb = launch_project_bwd(pa, c->g2d, grads->means, grads->log_scales, grads->quats,

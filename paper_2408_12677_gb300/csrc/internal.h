@@ -33,6 +33,17 @@ void launch_bin_prepare(int n, const float* mean2d, const float* extent, const f
 int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales,
                        float* g_quats, float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s);
 void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s);
+
+// Adam hyper-parameters as the kernels use them
+struct AdamArgs {
+  float lr[6];  // means, log-scales, quaternions, opacity, SH DC, SH rest
+  float beta1, beta2, eps;
+  float step_scale;    // 1 / (1 - beta1^t)
+  float inv_sqrt_bc2;  // 1 / sqrt(1 - beta2^t)
+};
+// fused projection backward + Adam over the flat buffer (one view, one step)
+int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
+                            const AdamArgs& ad, float* pose_partials, cudaStream_t s);
 int project_bwd_blocks(int n);
 
 // Stable radix sort of (u32 key, u32 value) pairs on the low `bits` bits.
@@ -44,7 +55,7 @@ int project_bwd_blocks(int n);
 struct SortBuffers {
   uint32_t* keys[2];
   uint32_t* vals[2];
-  uint32_t* hist;   // scratch, >= 256 * max_blocks
+  uint32_t* hist;   // scratch, >= 256 * (max_blocks + 1): per-block digit counts, then digit totals
   int max_blocks;
 };
 int radix_sort_pairs(SortBuffers& b, const uint32_t* in_k, const uint32_t* in_v, uint32_t n_max,

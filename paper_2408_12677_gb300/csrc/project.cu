@@ -171,159 +171,177 @@ __global__ void bin_prepare_kernel(int n, const float* __restrict__ mean2d, cons
 
 constexpr int kBwdThreads = 128;
 
-__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a, const float4* __restrict__ g2d,
-                                                                  float* __restrict__ gm, float* __restrict__ gls,
-                                                                  float* __restrict__ gq, float* __restrict__ glog,
-                                                                  float* __restrict__ gsh,
-                                                                  float* __restrict__ pose_partials) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const CamView& cv = a.cv;
-  if (i < a.n) {
-    float4 G0 = g2d[3 * i], G1 = g2d[3 * i + 1], G2 = g2d[3 * i + 2];
-    bool any = (G0.x != 0.f) | (G0.y != 0.f) | (G0.z != 0.f) | (G0.w != 0.f) | (G1.x != 0.f) | (G1.y != 0.f) |
-               (G1.z != 0.f) | (G2.x != 0.f) | (G2.y != 0.f) | (G2.z != 0.f);
-    if (any) {
-      const float p[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-      float pc[3];
-      for (int r = 0; r < 3; ++r) pc[r] = cv.R[3 * r] * p[0] + cv.R[3 * r + 1] * p[1] + cv.R[3 * r + 2] * p[2] + cv.t[r];
-      float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
-      float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
-      Geo g;
-      geometry(cv, a.dilation, p[0], p[1], p[2], q4, ls, pc[0], pc[1], pc[2], g);
-      const float gmx = G0.x, gmy = G0.y, gi0 = G0.z, gk = G0.w, gi1 = G1.x, go = G1.y, gdep = G1.z;
+// Gradient of one Gaussian's parameters from its projected-feature gradient
+// record G0..G2 (mu 2, factor 3 | opacity, depth | rgb 3), plus its share of
+// the pose-twist gradient.  SH gradients are returned in factored form: the
+// gradient of coefficient (k, c) is Y[k] * graw[c].
+template <int D>
+struct GaussGrad {
+  float gm[3], gls[3], gq[4], glogit;
+  float Y[16], graw[3];
+  float pose[6];
+};
 
-      // opacity
-      const float o = 1.f / (1.f + expf(-a.logits[i]));
-      glog[i] += go * o * (1.f - o);
+template <int D>
+__device__ __forceinline__ void gaussian_grad(const CamView& cv, float dilation, const float (&p)[3],
+                                              const float (&q4)[4], const float (&ls)[3], float logit,
+                                              const float* __restrict__ shp, float4 G0, float4 G1, float4 G2,
+                                              GaussGrad<D>& out) {
+  constexpr int K = (D + 1) * (D + 1);
+  float pc[3];
+  for (int r = 0; r < 3; ++r) pc[r] = cv.R[3 * r] * p[0] + cv.R[3 * r + 1] * p[1] + cv.R[3 * r + 2] * p[2] + cv.t[r];
+  Geo g;
+  geometry(cv, dilation, p[0], p[1], p[2], q4, ls, pc[0], pc[1], pc[2], g);
+  const float gmx = G0.x, gmy = G0.y, gi0 = G0.z, gk = G0.w, gi1 = G1.x, go = G1.y, gdep = G1.z;
 
-      // colour: SH coefficients and view direction
-      const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
-      float dv[3] = {p[0] - cv.C[0], p[1] - cv.C[1], p[2] - cv.C[2]};
-      float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
-      float d[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
-      float Yb[16];
-      sh_basis(a.sh_degree, d[0], d[1], d[2], Yb);
-      const float* shp = a.sh + (size_t)i * K * 3;
-      float raw[3] = {0.5f, 0.5f, 0.5f};
-      for (int k = 0; k < K; ++k)
-        for (int c = 0; c < 3; ++c) raw[c] += Yb[k] * shp[3 * k + c];
-      float graw[3] = {raw[0] > 0.f ? G2.x : 0.f, raw[1] > 0.f ? G2.y : 0.f, raw[2] > 0.f ? G2.z : 0.f};
-      float cw[16];
-      float* gshp = gsh + (size_t)i * K * 3;
-      for (int k = 0; k < K; ++k) {
-        gshp[3 * k] += Yb[k] * graw[0];
-        gshp[3 * k + 1] += Yb[k] * graw[1];
-        gshp[3 * k + 2] += Yb[k] * graw[2];
-        cw[k] = shp[3 * k] * graw[0] + shp[3 * k + 1] * graw[1] + shp[3 * k + 2] * graw[2];
-      }
-      float gd[3];
-      sh_basis_vjp(a.sh_degree, d[0], d[1], d[2], cw, gd[0], gd[1], gd[2]);
-      float dd = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
-      float gv[3] = {(gd[0] - d[0] * dd) * inv, (gd[1] - d[1] * dd) * inv, (gd[2] - d[2] * dd) * inv};
-      float gp[3] = {gv[0], gv[1], gv[2]};
-      float gC[3] = {-gv[0], -gv[1], -gv[2]};
+  // opacity
+  const float o = 1.f / (1.f + expf(-logit));
+  out.glogit = go * o * (1.f - o);
 
-      // (i0, k, i1) -> dilated covariance entries (a, b, c)
-      const float ga = -gi0 * g.i0 / (2.f * g.a) - gk * g.k / g.a - gi1 * g.i1 * g.b * g.b / (2.f * g.a * g.det);
-      const float gb = gk / g.a + gi1 * g.i1 * g.b / g.det;
-      const float gc = -gi1 * g.i1 * g.a / (2.f * g.det);
-      // covariance = M M^T + dil I, rows m0, m1 of M = J A
-      float Gm0[3], Gm1[3];
-      for (int c = 0; c < 3; ++c) {
-        Gm0[c] = 2.f * ga * g.m0[c] + gb * g.m1[c];
-        Gm1[c] = gb * g.m0[c] + 2.f * gc * g.m1[c];
-      }
-      float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
-      for (int c = 0; c < 3; ++c) {
-        gj00 += Gm0[c] * g.A[0][c];
-        gj02 += Gm0[c] * g.A[2][c];
-        gj11 += Gm1[c] * g.A[1][c];
-        gj12 += Gm1[c] * g.A[2][c];
-      }
-      float GA[3][3];
-      for (int c = 0; c < 3; ++c) {
-        GA[0][c] = g.j00 * Gm0[c];
-        GA[1][c] = g.j11 * Gm1[c];
-        GA[2][c] = g.j02 * Gm0[c] + g.j12 * Gm1[c];
-      }
-      // J and the mean -> camera-space position
-      const float rz = g.rz, rz2 = rz * rz, rz3 = rz2 * rz;
-      float gpc[3] = {0.f, 0.f, 0.f};
-      gpc[2] += -cv.fx * rz2 * gj00 - cv.fy * rz2 * gj11;
-      if (!g.cx_) {
-        gpc[0] += -cv.fx * rz2 * gj02;
-        gpc[2] += 2.f * cv.fx * g.x * rz3 * gj02;
-      } else {
-        gpc[2] += cv.fx * g.xt * rz3 * gj02;
-      }
-      if (!g.cy_) {
-        gpc[1] += -cv.fy * rz2 * gj12;
-        gpc[2] += 2.f * cv.fy * g.y * rz3 * gj12;
-      } else {
-        gpc[2] += cv.fy * g.yt * rz3 * gj12;
-      }
-      gpc[0] += gmx * cv.fx * rz;
-      gpc[1] += gmy * cv.fy * rz;
-      gpc[2] += -(gmx * cv.fx * g.x + gmy * cv.fy * g.y) * rz2 + gdep;
+  // colour: SH coefficients and view direction
+  float dv[3] = {p[0] - cv.C[0], p[1] - cv.C[1], p[2] - cv.C[2]};
+  const float inv = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  const float d[3] = {dv[0] * inv, dv[1] * inv, dv[2] * inv};
+  sh_basis(D, d[0], d[1], d[2], out.Y);
+  float raw[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) raw[c] += out.Y[k] * shp[3 * k + c];
+  out.graw[0] = raw[0] > 0.f ? G2.x : 0.f;
+  out.graw[1] = raw[1] > 0.f ? G2.y : 0.f;
+  out.graw[2] = raw[2] > 0.f ? G2.z : 0.f;
+  float cw[16];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    cw[k] = shp[3 * k] * out.graw[0] + shp[3 * k + 1] * out.graw[1] + shp[3 * k + 2] * out.graw[2];
+  float gd[3];
+  sh_basis_vjp(D, d[0], d[1], d[2], cw, gd[0], gd[1], gd[2]);
+  const float dd = d[0] * gd[0] + d[1] * gd[1] + d[2] * gd[2];
+  const float gv[3] = {(gd[0] - d[0] * dd) * inv, (gd[1] - d[1] * dd) * inv, (gd[2] - d[2] * dd) * inv};
+  float gp[3] = {gv[0], gv[1], gv[2]};
+  const float gC[3] = {-gv[0], -gv[1], -gv[2]};
 
-      // A = W B, B = Rq diag(s)
-      float GW[3][3];
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) GW[r][c] = GA[r][0] * g.B[c][0] + GA[r][1] * g.B[c][1] + GA[r][2] * g.B[c][2];
-      float GB[3][3];
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-          GB[r][c] = cv.R[r] * GA[0][c] + cv.R[3 + r] * GA[1][c] + cv.R[6 + r] * GA[2][c];
-      float GR[3][3];
-      for (int c = 0; c < 3; ++c) {
-        float gs_ = 0.f;
-        for (int r = 0; r < 3; ++r) {
-          GR[r][c] = GB[r][c] * g.s[c];
-          gs_ += GB[r][c] * g.Rq[r][c];
-        }
-        gls[3 * i + c] += gs_ * g.s[c];
-      }
-      // rotation matrix -> normalised quaternion -> raw quaternion
-      const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
-      float gqn[4];
-      gqn[0] = 2.f * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
-      gqn[1] = 2.f * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.f * x * GR[1][1] - w * GR[1][2] +
-                      z * GR[2][0] + w * GR[2][1] - 2.f * x * GR[2][2]);
-      gqn[2] = 2.f * (-2.f * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] -
-                      w * GR[2][0] + z * GR[2][1] - 2.f * y * GR[2][2]);
-      gqn[3] = 2.f * (-2.f * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.f * z * GR[1][1] +
-                      y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
-      float dq = g.qn[0] * gqn[0] + g.qn[1] * gqn[1] + g.qn[2] * gqn[2] + g.qn[3] * gqn[3];
-      for (int j = 0; j < 4; ++j) gq[4 * i + j] += (gqn[j] - g.qn[j] * dq) / g.qlen;
-
-      // p_c = W p + t
-      for (int c = 0; c < 3; ++c) gp[c] += cv.R[c] * gpc[0] + cv.R[3 + c] * gpc[1] + cv.R[6 + c] * gpc[2];
-      for (int c = 0; c < 3; ++c) gm[3 * i + c] += gp[c];
-
-      // pose: total dL/dW and dL/dt of this Gaussian, then the left-perturbation twist
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) GW[r][c] += gpc[r] * p[c] - cv.t[r] * gC[c];
-      float gt[3];
-      for (int r = 0; r < 3; ++r)
-        gt[r] = gpc[r] - (cv.R[3 * r] * gC[0] + cv.R[3 * r + 1] * gC[1] + cv.R[3 * r + 2] * gC[2]);
-      float Am[3][3];  // GW W^T
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-          Am[r][c] = GW[r][0] * cv.R[3 * c] + GW[r][1] * cv.R[3 * c + 1] + GW[r][2] * cv.R[3 * c + 2];
-      pose[0] = gt[0];
-      pose[1] = gt[1];
-      pose[2] = gt[2];
-      pose[3] = Am[2][1] - Am[1][2] + (cv.t[1] * gt[2] - cv.t[2] * gt[1]);
-      pose[4] = Am[0][2] - Am[2][0] + (cv.t[2] * gt[0] - cv.t[0] * gt[2]);
-      pose[5] = Am[1][0] - Am[0][1] + (cv.t[0] * gt[1] - cv.t[1] * gt[0]);
-    }
+  // (i0, k, i1) -> dilated covariance entries (a, b, c)
+  const float ga = -gi0 * g.i0 / (2.f * g.a) - gk * g.k / g.a - gi1 * g.i1 * g.b * g.b / (2.f * g.a * g.det);
+  const float gb = gk / g.a + gi1 * g.i1 * g.b / g.det;
+  const float gc = -gi1 * g.i1 * g.a / (2.f * g.det);
+  // covariance = M M^T + dil I, rows m0, m1 of M = J A
+  float Gm0[3], Gm1[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Gm0[c] = 2.f * ga * g.m0[c] + gb * g.m1[c];
+    Gm1[c] = gb * g.m0[c] + 2.f * gc * g.m1[c];
   }
-  // deterministic per-block partial sums of the pose gradient
+  float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    gj00 += Gm0[c] * g.A[0][c];
+    gj02 += Gm0[c] * g.A[2][c];
+    gj11 += Gm1[c] * g.A[1][c];
+    gj12 += Gm1[c] * g.A[2][c];
+  }
+  float GA[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    GA[0][c] = g.j00 * Gm0[c];
+    GA[1][c] = g.j11 * Gm1[c];
+    GA[2][c] = g.j02 * Gm0[c] + g.j12 * Gm1[c];
+  }
+  // J and the mean -> camera-space position
+  const float rz = g.rz, rz2 = rz * rz, rz3 = rz2 * rz;
+  float gpc[3] = {0.f, 0.f, 0.f};
+  gpc[2] += -cv.fx * rz2 * gj00 - cv.fy * rz2 * gj11;
+  if (!g.cx_) {
+    gpc[0] += -cv.fx * rz2 * gj02;
+    gpc[2] += 2.f * cv.fx * g.x * rz3 * gj02;
+  } else {
+    gpc[2] += cv.fx * g.xt * rz3 * gj02;
+  }
+  if (!g.cy_) {
+    gpc[1] += -cv.fy * rz2 * gj12;
+    gpc[2] += 2.f * cv.fy * g.y * rz3 * gj12;
+  } else {
+    gpc[2] += cv.fy * g.yt * rz3 * gj12;
+  }
+  gpc[0] += gmx * cv.fx * rz;
+  gpc[1] += gmy * cv.fy * rz;
+  gpc[2] += -(gmx * cv.fx * g.x + gmy * cv.fy * g.y) * rz2 + gdep;
+
+  // A = W B, B = Rq diag(s)
+  float GW[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) GW[r][c] = GA[r][0] * g.B[c][0] + GA[r][1] * g.B[c][1] + GA[r][2] * g.B[c][2];
+  float GR[3][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float gs_ = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float GBrc = cv.R[r] * GA[0][c] + cv.R[3 + r] * GA[1][c] + cv.R[6 + r] * GA[2][c];  // (W^T GA)[r][c]
+      GR[r][c] = GBrc * g.s[c];
+      gs_ += GBrc * g.Rq[r][c];
+    }
+    out.gls[c] = gs_ * g.s[c];
+  }
+  // rotation matrix -> normalised quaternion -> raw quaternion
+  const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+  float gqn[4];
+  gqn[0] = 2.f * (-z * GR[0][1] + y * GR[0][2] + z * GR[1][0] - x * GR[1][2] - y * GR[2][0] + x * GR[2][1]);
+  gqn[1] = 2.f * (y * GR[0][1] + z * GR[0][2] + y * GR[1][0] - 2.f * x * GR[1][1] - w * GR[1][2] + z * GR[2][0] +
+                  w * GR[2][1] - 2.f * x * GR[2][2]);
+  gqn[2] = 2.f * (-2.f * y * GR[0][0] + x * GR[0][1] + w * GR[0][2] + x * GR[1][0] + z * GR[1][2] - w * GR[2][0] +
+                  z * GR[2][1] - 2.f * y * GR[2][2]);
+  gqn[3] = 2.f * (-2.f * z * GR[0][0] - w * GR[0][1] + x * GR[0][2] + w * GR[1][0] - 2.f * z * GR[1][1] +
+                  y * GR[1][2] + x * GR[2][0] + y * GR[2][1]);
+  const float dq = g.qn[0] * gqn[0] + g.qn[1] * gqn[1] + g.qn[2] * gqn[2] + g.qn[3] * gqn[3];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out.gq[j] = (gqn[j] - g.qn[j] * dq) / g.qlen;
+
+  // p_c = W p + t
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gp[c] += cv.R[c] * gpc[0] + cv.R[3 + c] * gpc[1] + cv.R[6 + c] * gpc[2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out.gm[c] = gp[c];
+
+  // pose: total dL/dW and dL/dt of this Gaussian, then the left-perturbation twist
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) GW[r][c] += gpc[r] * p[c] - cv.t[r] * gC[c];
+  float gt[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    gt[r] = gpc[r] - (cv.R[3 * r] * gC[0] + cv.R[3 * r + 1] * gC[1] + cv.R[3 * r + 2] * gC[2]);
+  float Am[3][3];  // GW W^T
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Am[r][c] = GW[r][0] * cv.R[3 * c] + GW[r][1] * cv.R[3 * c + 1] + GW[r][2] * cv.R[3 * c + 2];
+  out.pose[0] = gt[0];
+  out.pose[1] = gt[1];
+  out.pose[2] = gt[2];
+  out.pose[3] = Am[2][1] - Am[1][2] + (cv.t[1] * gt[2] - cv.t[2] * gt[1]);
+  out.pose[4] = Am[0][2] - Am[2][0] + (cv.t[2] * gt[0] - cv.t[0] * gt[2]);
+  out.pose[5] = Am[1][0] - Am[0][1] + (cv.t[0] * gt[1] - cv.t[1] * gt[0]);
+}
+
+__device__ __forceinline__ bool nonzero_record(const float4& G0, const float4& G1, const float4& G2) {
+  return (G0.x != 0.f) | (G0.y != 0.f) | (G0.z != 0.f) | (G0.w != 0.f) | (G1.x != 0.f) | (G1.y != 0.f) |
+         (G1.z != 0.f) | (G2.x != 0.f) | (G2.y != 0.f) | (G2.z != 0.f);
+}
+
+// deterministic per-block partial sums of the pose gradient
+__device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float* __restrict__ pose_partials) {
   __shared__ float red[kBwdThreads / 32][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
   for (int k = 0; k < 6; ++k) {
     float v = pose[k];
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (lane == 0) red[wid][k] = v;
   }
@@ -333,6 +351,165 @@ __global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a,
     for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w][threadIdx.x];
     pose_partials[6 * blockIdx.x + threadIdx.x] = s;
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a, const float4* __restrict__ g2d,
+                                                                  float* __restrict__ gm, float* __restrict__ gls,
+                                                                  float* __restrict__ gq, float* __restrict__ glog,
+                                                                  float* __restrict__ gsh,
+                                                                  float* __restrict__ pose_partials) {
+  constexpr int K = (D + 1) * (D + 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (i < a.n) {
+    const float4 G0 = g2d[3 * (size_t)i], G1 = g2d[3 * (size_t)i + 1], G2 = g2d[3 * (size_t)i + 2];
+    if (nonzero_record(G0, G1, G2)) {
+      const float p[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+      const float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+      const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+      GaussGrad<D> gg;
+      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, a.logits[i], a.sh + (size_t)i * K * 3, G0, G1, G2, gg);
+      glog[i] += gg.glogit;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gm[3 * i + c] += gg.gm[c];
+        gls[3 * i + c] += gg.gls[c];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gq[4 * i + j] += gg.gq[j];
+      float* gshp = gsh + (size_t)i * K * 3;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gshp[3 * k + c] += gg.Y[k] * gg.graw[c];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
+    }
+  }
+  block_pose_partial(pose, pose_partials);
+}
+
+__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& ad) {
+  m = ad.beta1 * m + (1.f - ad.beta1) * g;
+  v = ad.beta2 * v + (1.f - ad.beta2) * g * g;
+  p -= lr * ad.step_scale * m / (sqrtf(v) * ad.inv_sqrt_bc2 + ad.eps);
+}
+
+// Backward of the projection fused with the Adam step, for one optimisation
+// iteration on one view.  A block owns 128 consecutive Gaussians:
+//   1. its slice of every parameter array (contiguous in the flat buffer) and
+//      its gradient records are loaded into shared memory with coalesced loads;
+//   2. one thread per Gaussian turns the record into parameter gradients,
+//      kept in shared memory (SH gradients in factored form Y_k * graw_c);
+//   3. coalesced sweeps over the block's slices apply Adam to every float.
+// No gradient buffer is written or read.
+constexpr int kFusedThreads = 128;
+
+template <int D>
+__global__ void __launch_bounds__(kFusedThreads, 4) project_bwd_adam_kernel(ProjectArgs a,
+                                                                            const float4* __restrict__ g2d,
+                                                                            float* __restrict__ P,
+                                                                            float* __restrict__ M,
+                                                                            float* __restrict__ V, AdamArgs ad,
+                                                                            float* __restrict__ pose_partials) {
+  constexpr int K = (D + 1) * (D + 1);
+  constexpr int NS = 3 * K;                        // SH floats per Gaussian
+  constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
+  constexpr int B = kFusedThreads;
+  __shared__ float s_p[B * 11];       // means (3B) | log-scales (3B) | quats (4B) | logits (B), block order
+  __shared__ float s_g[B * 11];       // gradients, same layout
+  __shared__ float s_sh[B * RS];
+  __shared__ float s_Y[B][K + 1];
+  __shared__ float s_graw[B][4];
+  const int64_t N = a.n;
+  const int base = blockIdx.x * B;
+  const int cnt = min(B, a.n - base);
+  const int t = threadIdx.x;
+  // global start of each slice and its offset in s_p / s_g
+  const int64_t g0[4] = {3 * (int64_t)base, 3 * N + 3 * (int64_t)base, 6 * N + 4 * (int64_t)base, 10 * N + base};
+  const int so[4] = {0, 3 * B, 6 * B, 10 * B};
+  const int len[4] = {3 * cnt, 3 * cnt, 4 * cnt, cnt};
+  const int64_t gsh = 11 * N + (int64_t)base * NS;
+
+  // 1. stage parameters (coalesced) and the gradient records
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    for (int e = t; e < len[r]; e += B) s_p[so[r] + e] = P[g0[r] + e];
+  for (int e = t; e < cnt * NS; e += B) {
+    const int gi = e / NS;
+    s_sh[gi * RS + (e - gi * NS)] = P[gsh + e];
+  }
+  float4 G0 = make_float4(0.f, 0.f, 0.f, 0.f), G1 = G0, G2 = G0;
+  if (t < cnt) {
+    const int64_t i = base + t;
+    G0 = g2d[3 * i];
+    G1 = g2d[3 * i + 1];
+    G2 = g2d[3 * i + 2];
+  }
+  __syncthreads();
+
+  // 2. per-Gaussian gradients
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (t < cnt) {
+    GaussGrad<D> gg;
+    if (nonzero_record(G0, G1, G2)) {
+      const float p[3] = {s_p[3 * t], s_p[3 * t + 1], s_p[3 * t + 2]};
+      const float ls[3] = {s_p[3 * B + 3 * t], s_p[3 * B + 3 * t + 1], s_p[3 * B + 3 * t + 2]};
+      const float q4[4] = {s_p[6 * B + 4 * t], s_p[6 * B + 4 * t + 1], s_p[6 * B + 4 * t + 2],
+                           s_p[6 * B + 4 * t + 3]};
+      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, s_p[10 * B + t], s_sh + t * RS, G0, G1, G2, gg);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) gg.gm[c] = gg.gls[c] = gg.graw[c] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) gg.gq[j] = 0.f;
+      gg.glogit = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) gg.Y[k] = 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s_g[3 * t + c] = gg.gm[c];
+      s_g[3 * B + 3 * t + c] = gg.gls[c];
+      s_graw[t][c] = gg.graw[c];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s_g[6 * B + 4 * t + j] = gg.gq[j];
+    s_g[10 * B + t] = gg.glogit;
+#pragma unroll
+    for (int k = 0; k < K; ++k) s_Y[t][k] = gg.Y[k];
+  }
+  __syncthreads();
+
+  // 3. Adam sweeps (dense: zero gradients still update the moments)
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float lr = ad.lr[r];
+#pragma unroll 4
+    for (int e = t; e < len[r]; e += B) {
+      const int64_t f = g0[r] + e;
+      float p = s_p[so[r] + e], m = M[f], v = V[f];
+      adam_update(p, s_g[so[r] + e], m, v, lr, ad);
+      P[f] = p;
+      M[f] = m;
+      V[f] = v;
+    }
+  }
+#pragma unroll 4
+  for (int e = t; e < cnt * NS; e += B) {
+    const int gi = e / NS, rr = e - gi * NS;
+    const int k = rr / 3, c = rr - 3 * k;
+    const int64_t f = gsh + e;
+    float p = s_sh[gi * RS + rr], m = M[f], v = V[f];
+    adam_update(p, s_Y[gi][k] * s_graw[gi][c], m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
+    P[f] = p;
+    M[f] = m;
+    V[f] = v;
+  }
+  block_pose_partial(pose, pose_partials);
 }
 
 __global__ void pose_reduce_kernel(const float* __restrict__ partials, int nblocks, float* __restrict__ out) {
@@ -375,10 +552,28 @@ int project_bwd_blocks(int n) { return n > 0 ? (n + kBwdThreads - 1) / kBwdThrea
 
 int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales, float* g_quats,
                        float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s) {
-  int nb = project_bwd_blocks(a.n);
+  const int nb = project_bwd_blocks(a.n);
   if (nb == 0) return 0;
-  project_bwd_kernel<<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh,
-                                               pose_partials);
+  switch (a.sh_degree) {
+    case 0: project_bwd_kernel<0><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    case 1: project_bwd_kernel<1><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    case 2: project_bwd_kernel<2><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    default: project_bwd_kernel<3><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+  }
+  return nb;
+}
+
+int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
+                            const AdamArgs& ad, float* pose_partials, cudaStream_t s) {
+  static_assert(kFusedThreads == kBwdThreads, "pose partial buffer is sized for kBwdThreads blocks");
+  const int nb = project_bwd_blocks(a.n);
+  if (nb == 0) return 0;
+  switch (a.sh_degree) {
+    case 0: project_bwd_adam_kernel<0><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
+    case 1: project_bwd_adam_kernel<1><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
+    case 2: project_bwd_adam_kernel<2><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
+    default: project_bwd_adam_kernel<3><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
+  }
   return nb;
 }
 

@@ -48,37 +48,63 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t* __
   ghist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of len uint32 counts in place, one block
-__global__ void __launch_bounds__(kScanThreads) scan_exclusive_single(uint32_t* __restrict__ data, int len) {
-  __shared__ uint32_t s[kScanThreads];
-  const int per = (len + kScanThreads - 1) / kScanThreads;
-  const int beg = min(len, (int)threadIdx.x * per), end = min(len, beg + per);
-  uint32_t sum = 0;
-  for (int i = beg; i < end; ++i) sum += data[i];
-  s[threadIdx.x] = sum;
-  __syncthreads();
-  for (int off = 1; off < kScanThreads; off <<= 1) {
-    uint32_t v = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0u;
-    __syncthreads();
-    s[threadIdx.x] += v;
-    __syncthreads();
+// exclusive scan of a value per thread over a 256-thread block; *total gets the sum
+__device__ __forceinline__ uint32_t block256_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t s_w[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
   }
-  uint32_t run = s[threadIdx.x] - sum;
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < 8 ? s_w[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+      if (lane >= off) w += y;
+    }
+    if (lane < 8) s_w[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t prefix = warp > 0 ? s_w[warp - 1] : 0u;
+  *total = s_w[7];
+  __syncthreads();
+  return prefix + x - v;
+}
+
+// Row scan of the digit-major histogram: block d turns hist[d][0..G) into its
+// exclusive prefix over blocks and writes the digit total to totals[d].
+__global__ void __launch_bounds__(kSortThreads) radix_rowscan(uint32_t* __restrict__ ghist, int G,
+                                                              uint32_t* __restrict__ totals) {
+  uint32_t* row = ghist + (size_t)blockIdx.x * G;
+  const int per = (G + kSortThreads - 1) / kSortThreads;
+  const int beg = min(G, (int)threadIdx.x * per), end = min(G, beg + per);
+  uint32_t sum = 0;
+  for (int i = beg; i < end; ++i) sum += row[i];
+  uint32_t total;
+  uint32_t run = block256_exclusive_scan(sum, &total);
   for (int i = beg; i < end; ++i) {
-    uint32_t v = data[i];
-    data[i] = run;
+    const uint32_t v = row[i];
+    row[i] = run;
     run += v;
   }
+  if (threadIdx.x == 0) totals[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kSortThreads) radix_downsweep(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const uint32_t* n_dev, uint32_t n_host, int shift, uint32_t mask,
-    const uint32_t* __restrict__ ghist, int G) {
+    const uint32_t* __restrict__ ghist, const uint32_t* __restrict__ totals, int G) {
   __shared__ uint32_t s_off[kRadix];
   __shared__ uint32_t s_wc[kSortWarps][kRadix];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  s_off[tid] = ghist[tid * G + blockIdx.x];
+  uint32_t all;
+  const uint32_t digit_base = block256_exclusive_scan(totals[tid], &all);
+  s_off[tid] = digit_base + ghist[tid * G + blockIdx.x];
   for (int w = 0; w < kSortWarps; ++w) s_wc[w][tid] = 0;
   const uint32_t n = read_n(n_dev, n_host);
   const uint32_t chunk = (n + G - 1) / G;
@@ -131,28 +157,8 @@ constexpr int kDupItems = 4;  // per thread, consecutive
 constexpr int kDupChunk = kDupThreads * kDupItems;
 
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t s_w[kDupThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t x = v;
-  for (int off = 1; off < 32; off <<= 1) {
-    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-    if (lane >= off) x += y;
-  }
-  if (lane == 31) s_w[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < kDupThreads / 32 ? s_w[lane] : 0u;
-    for (int off = 1; off < 32; off <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, off);
-      if (lane >= off) w += y;
-    }
-    if (lane < kDupThreads / 32) s_w[lane] = w;
-  }
-  __syncthreads();
-  uint32_t warp_prefix = warp > 0 ? s_w[warp - 1] : 0u;
-  *total = s_w[kDupThreads / 32 - 1];
-  __syncthreads();
-  return warp_prefix + x - v;
+  static_assert(kDupThreads == 256, "block scan is written for 256 threads");
+  return block256_exclusive_scan(v, total);
 }
 
 __global__ void __launch_bounds__(kDupThreads) dup_count_kernel(int n, const uint32_t* __restrict__ sorted_ids,
@@ -254,8 +260,8 @@ __global__ void export_keys_kernel(const uint32_t* __restrict__ tiles, const uin
 }
 
 int sort_blocks(uint32_t n, int num_sms, int max_blocks) {
-  // about 8 rounds of 256 items per block at least; at most a few per SM
-  int g = (int)std::min<uint64_t>(((uint64_t)n + 2047) / 2048, (uint64_t)std::max(1, 4 * num_sms));
+  // at least 16 rounds of 256 items per block; at most two blocks per SM
+  int g = (int)std::min<uint64_t>(((uint64_t)n + 4095) / 4096, (uint64_t)std::max(1, 2 * num_sms));
   return std::max(1, std::min(g, max_blocks));
 }
 
@@ -273,8 +279,9 @@ int radix_sort_pairs(SortBuffers& b, const uint32_t* in_k, const uint32_t* in_v,
     const int nb = std::min(8, bits - shift);
     const uint32_t mask = (1u << nb) - 1u;
     radix_upsweep<<<G, kSortThreads, 0, s>>>(ck, n_dev, n_max, shift, mask, b.hist, G);
-    scan_exclusive_single<<<1, kScanThreads, 0, s>>>(b.hist, kRadix * G);
-    radix_downsweep<<<G, kSortThreads, 0, s>>>(ck, cv, b.keys[out], b.vals[out], n_dev, n_max, shift, mask, b.hist, G);
+    radix_rowscan<<<kRadix, kSortThreads, 0, s>>>(b.hist, G, b.hist + (size_t)kRadix * G);
+    radix_downsweep<<<G, kSortThreads, 0, s>>>(ck, cv, b.keys[out], b.vals[out], n_dev, n_max, shift, mask, b.hist,
+                                               b.hist + (size_t)kRadix * G, G);
     if (launches) *launches += 3;
     ck = b.keys[out];
     cv = b.vals[out];

@@ -102,10 +102,15 @@ class Context:
 
 
 class Trainer:
-    """One view, one map: fwd + L1 loss + bwd + Adam per ``step``."""
+    """One view, one map: fwd + L1 loss + bwd + Adam per ``step``.
+
+    ``fused`` (default) runs the backward pass and the Adam step as
+    gs_render_bwd_adam (no gradient buffer); otherwise gs_render_bwd into the
+    model's gradient buffer followed by gs_adam_step (which clears it)."""
 
     def __init__(self, model: GaussianModel, cam, R, t, raster_cfg=None, adam_cfg=None, w_color=0.8, w_depth=0.2,
-                 ctx: Context | None = None, device: int = 0):
+                 ctx: Context | None = None, device: int = 0, fused: bool = True):
+        self.fused = fused
         self.model = model
         self.ctx = ctx or Context(device)
         self.cam = camera_struct(cam)
@@ -136,11 +141,15 @@ class Trainer:
         self.forward(stream)
         abi.gs_loss_l1(h, self.cam, self.color, self.depth, target_rgb, target_depth, self.w_color, self.w_depth,
                        self.loss, self.dLdc, self.dLdd, stream)
-        abi.gs_render_bwd(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, self._gr, None,
-                          stream)
         self.step_count += 1
         m = self.model
-        abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
+        if self.fused:
+            abi.gs_render_bwd_adam(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, m.flat, m.m,
+                                   m.v, self.acfg, self.step_count, None, stream)
+        else:
+            abi.gs_render_bwd(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, self._gr, None,
+                              stream)
+            abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
         return self.loss
 
 

@@ -77,3 +77,38 @@ def test_adam_matches_oracle_over_steps(ctx, n, deg):
     abi.gs_adam_step(ctx.handle, p, gt, m, v, n, deg, abi.adam_cfg(zero_grads=1), 6)
     torch.cuda.synchronize()
     assert float(gt.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("deg,seed", [(0, 1), (3, 2)])
+def test_fused_backward_adam_matches_unfused(ctx, deg, seed):
+    """gs_render_bwd_adam == gs_render_bwd into zeroed gradients + gs_adam_step,
+    over three consecutive iterations (so the moments are non-trivial)."""
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import GaussianModel, camera_struct
+    from synth import workloads
+    from synth.scene import Camera, look_at
+    cam = Camera(80.0, 75.0, 40.0, 30.0, 84, 60)
+    pose = look_at([0.1, 0.2, -0.1], [0.7, 3.0, 0.2])
+    P = workloads.random_gaussians(np.random.default_rng(seed), 700, cam, pose, deg, log_scale_range=(-3.5, -1.5),
+                                   sh_rest_std=0.15)
+    rng = np.random.default_rng(seed + 10)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+    wc, wd, wa = t(rng.standard_normal((3, 60, 84))), t(rng.standard_normal((60, 84))), t(rng.standard_normal((60, 84)))
+    A = GaussianModel(P)
+    B = GaussianModel(P)
+    camS, view, rcfg = camera_struct(cam), abi.make_viewmat(pose.R, pose.t), abi.raster_cfg()
+    acfg = abi.adam_cfg(zero_grads=1)
+    for step in range(1, 4):
+        pa, pb = torch.zeros(6, device="cuda"), torch.zeros(6, device="cuda")
+        abi.gs_render_fwd(ctx.handle, A.gaussians(), camS, view, rcfg)
+        abi.gs_render_bwd(ctx.handle, A.gaussians(), camS, view, rcfg, wc, wd, wa, A.grads(), pa)
+        abi.gs_adam_step(ctx.handle, A.flat, A.grad, A.m, A.v, A.n, deg, acfg, step)
+        abi.gs_render_fwd(ctx.handle, B.gaussians(), camS, view, rcfg)
+        abi.gs_render_bwd_adam(ctx.handle, B.gaussians(), camS, view, rcfg, wc, wd, wa, B.flat, B.m, B.v, acfg, step,
+                               pb)
+        torch.cuda.synchronize()
+        for name, x, y in (("p", A.flat, B.flat), ("m", A.m, B.m), ("v", A.v, B.v)):
+            xa, ya = x.cpu().numpy(), y.cpu().numpy()
+            compare(name, ya, xa, 1e-5, 1e-6 * np.abs(xa).max() + 1e-12, 1e-5)
+        compare("pose", pb.cpu().numpy(), pa.cpu().numpy(), 1e-5, 1e-6, 1e-5)
+    assert float(B.grad.abs().max()) == 0.0  # the fused path never touches a gradient buffer
