@@ -398,48 +398,79 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 
 // Backward of the projection fused with the Adam step, for one optimisation
 // iteration on one view.  A block owns 128 consecutive Gaussians:
-//   1. its slice of every parameter array (contiguous in the flat buffer) and
-//      its gradient records are loaded into shared memory with coalesced loads;
-//   2. one thread per Gaussian turns the record into parameter gradients,
-//      kept in shared memory (SH gradients in factored form Y_k * graw_c);
-//   3. coalesced sweeps over the block's slices apply Adam to every float.
+//   1. its slices of the parameter array and of the two Adam moments (each
+//      slice contiguous in the flat layout) are copied to shared memory with
+//      cp.async, the parameters as a first group and the moments as a second,
+//      so the moment loads stay in flight during step 2;
+//   2. one thread per Gaussian turns its gradient record into parameter
+//      gradients, kept in shared memory (SH gradients in factored form
+//      Y_k * graw_c);
+//   3. coalesced sweeps apply Adam to every float and store p, m, v.
 // No gradient buffer is written or read.
 constexpr int kFusedThreads = 128;
 
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int D>
-__global__ void __launch_bounds__(kFusedThreads, 4) project_bwd_adam_kernel(ProjectArgs a,
-                                                                            const float4* __restrict__ g2d,
-                                                                            float* __restrict__ P,
-                                                                            float* __restrict__ M,
-                                                                            float* __restrict__ V, AdamArgs ad,
-                                                                            float* __restrict__ pose_partials) {
-  constexpr int K = (D + 1) * (D + 1);
-  constexpr int NS = 3 * K;                        // SH floats per Gaussian
-  constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
-  constexpr int B = kFusedThreads;
-  __shared__ float s_p[B * 11];       // means (3B) | log-scales (3B) | quats (4B) | logits (B), block order
-  __shared__ float s_g[B * 11];       // gradients, same layout
-  __shared__ float s_sh[B * RS];
-  __shared__ float s_Y[B][K + 1];
-  __shared__ float s_graw[B][4];
+struct FusedSmem {
+  static constexpr int K = (D + 1) * (D + 1);
+  static constexpr int NS = 3 * K;
+  static constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
+  static constexpr int B = kFusedThreads;
+  float p[B * 11], m[B * 11], v[B * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
+  float g[B * 11];                        // gradients, same layout
+  float sp[B * RS], sm[B * NS], sv[B * NS];
+  float Y[B][K + 1];
+  float graw[B][4];
+};
+
+template <int D>
+__global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(ProjectArgs a,
+                                                                         const float4* __restrict__ g2d,
+                                                                         float* __restrict__ P, float* __restrict__ M,
+                                                                         float* __restrict__ V, AdamArgs ad,
+                                                                         float* __restrict__ pose_partials) {
+  using S = FusedSmem<D>;
+  constexpr int K = S::K, NS = S::NS, RS = S::RS, B = S::B;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S& sm = *reinterpret_cast<S*>(smem_raw);
   const int64_t N = a.n;
   const int base = blockIdx.x * B;
   const int cnt = min(B, a.n - base);
   const int t = threadIdx.x;
-  // global start of each slice and its offset in s_p / s_g
   const int64_t g0[4] = {3 * (int64_t)base, 3 * N + 3 * (int64_t)base, 6 * N + 4 * (int64_t)base, 10 * N + base};
   const int so[4] = {0, 3 * B, 6 * B, 10 * B};
   const int len[4] = {3 * cnt, 3 * cnt, 4 * cnt, cnt};
   const int64_t gsh = 11 * N + (int64_t)base * NS;
 
-  // 1. stage parameters (coalesced) and the gradient records
+  // 1. asynchronous staging: parameters (group 0), then Adam moments (group 1)
 #pragma unroll
   for (int r = 0; r < 4; ++r)
-    for (int e = t; e < len[r]; e += B) s_p[so[r] + e] = P[g0[r] + e];
+    for (int e = t; e < len[r]; e += B) cp_async4(&sm.p[so[r] + e], P + g0[r] + e);
   for (int e = t; e < cnt * NS; e += B) {
     const int gi = e / NS;
-    s_sh[gi * RS + (e - gi * NS)] = P[gsh + e];
+    cp_async4(&sm.sp[gi * RS + (e - gi * NS)], P + gsh + e);
   }
+  cp_async_commit();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    for (int e = t; e < len[r]; e += B) {
+      cp_async4(&sm.m[so[r] + e], M + g0[r] + e);
+      cp_async4(&sm.v[so[r] + e], V + g0[r] + e);
+    }
+  for (int e = t; e < cnt * NS; e += B) {
+    cp_async4(&sm.sm[e], M + gsh + e);
+    cp_async4(&sm.sv[e], V + gsh + e);
+  }
+  cp_async_commit();
   float4 G0 = make_float4(0.f, 0.f, 0.f, 0.f), G1 = G0, G2 = G0;
   if (t < cnt) {
     const int64_t i = base + t;
@@ -447,6 +478,7 @@ __global__ void __launch_bounds__(kFusedThreads, 4) project_bwd_adam_kernel(Proj
     G1 = g2d[3 * i + 1];
     G2 = g2d[3 * i + 2];
   }
+  cp_async_wait<1>();
   __syncthreads();
 
   // 2. per-Gaussian gradients
@@ -454,11 +486,11 @@ __global__ void __launch_bounds__(kFusedThreads, 4) project_bwd_adam_kernel(Proj
   if (t < cnt) {
     GaussGrad<D> gg;
     if (nonzero_record(G0, G1, G2)) {
-      const float p[3] = {s_p[3 * t], s_p[3 * t + 1], s_p[3 * t + 2]};
-      const float ls[3] = {s_p[3 * B + 3 * t], s_p[3 * B + 3 * t + 1], s_p[3 * B + 3 * t + 2]};
-      const float q4[4] = {s_p[6 * B + 4 * t], s_p[6 * B + 4 * t + 1], s_p[6 * B + 4 * t + 2],
-                           s_p[6 * B + 4 * t + 3]};
-      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, s_p[10 * B + t], s_sh + t * RS, G0, G1, G2, gg);
+      const float p[3] = {sm.p[3 * t], sm.p[3 * t + 1], sm.p[3 * t + 2]};
+      const float ls[3] = {sm.p[3 * B + 3 * t], sm.p[3 * B + 3 * t + 1], sm.p[3 * B + 3 * t + 2]};
+      const float q4[4] = {sm.p[6 * B + 4 * t], sm.p[6 * B + 4 * t + 1], sm.p[6 * B + 4 * t + 2],
+                           sm.p[6 * B + 4 * t + 3]};
+      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, sm.p[10 * B + t], sm.sp + t * RS, G0, G1, G2, gg);
 #pragma unroll
       for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
     } else {
@@ -472,39 +504,39 @@ __global__ void __launch_bounds__(kFusedThreads, 4) project_bwd_adam_kernel(Proj
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      s_g[3 * t + c] = gg.gm[c];
-      s_g[3 * B + 3 * t + c] = gg.gls[c];
-      s_graw[t][c] = gg.graw[c];
+      sm.g[3 * t + c] = gg.gm[c];
+      sm.g[3 * B + 3 * t + c] = gg.gls[c];
+      sm.graw[t][c] = gg.graw[c];
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) s_g[6 * B + 4 * t + j] = gg.gq[j];
-    s_g[10 * B + t] = gg.glogit;
+    for (int j = 0; j < 4; ++j) sm.g[6 * B + 4 * t + j] = gg.gq[j];
+    sm.g[10 * B + t] = gg.glogit;
 #pragma unroll
-    for (int k = 0; k < K; ++k) s_Y[t][k] = gg.Y[k];
+    for (int k = 0; k < K; ++k) sm.Y[t][k] = gg.Y[k];
   }
+  cp_async_wait<0>();
   __syncthreads();
 
   // 3. Adam sweeps (dense: zero gradients still update the moments)
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const float lr = ad.lr[r];
-#pragma unroll 4
     for (int e = t; e < len[r]; e += B) {
+      const int l = so[r] + e;
+      float p = sm.p[l], m = sm.m[l], v = sm.v[l];
+      adam_update(p, sm.g[l], m, v, lr, ad);
       const int64_t f = g0[r] + e;
-      float p = s_p[so[r] + e], m = M[f], v = V[f];
-      adam_update(p, s_g[so[r] + e], m, v, lr, ad);
       P[f] = p;
       M[f] = m;
       V[f] = v;
     }
   }
-#pragma unroll 4
   for (int e = t; e < cnt * NS; e += B) {
     const int gi = e / NS, rr = e - gi * NS;
     const int k = rr / 3, c = rr - 3 * k;
+    float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e];
+    adam_update(p, sm.Y[gi][k] * sm.graw[gi][c], m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
     const int64_t f = gsh + e;
-    float p = s_sh[gi * RS + rr], m = M[f], v = V[f];
-    adam_update(p, s_Y[gi][k] * s_graw[gi][c], m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
     P[f] = p;
     M[f] = m;
     V[f] = v;
@@ -568,12 +600,19 @@ int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* para
   static_assert(kFusedThreads == kBwdThreads, "pose partial buffer is sized for kBwdThreads blocks");
   const int nb = project_bwd_blocks(a.n);
   if (nb == 0) return 0;
+#define GS_FUSED(D_)                                                                                      \
+  do {                                                                                                    \
+    const int bytes = (int)sizeof(FusedSmem<D_>);                                                         \
+    cudaFuncSetAttribute(project_bwd_adam_kernel<D_>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
+    project_bwd_adam_kernel<D_><<<nb, kFusedThreads, bytes, s>>>(a, g2d, params, m, v, ad, pose_partials); \
+  } while (0)
   switch (a.sh_degree) {
-    case 0: project_bwd_adam_kernel<0><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
-    case 1: project_bwd_adam_kernel<1><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
-    case 2: project_bwd_adam_kernel<2><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
-    default: project_bwd_adam_kernel<3><<<nb, kFusedThreads, 0, s>>>(a, g2d, params, m, v, ad, pose_partials); break;
+    case 0: GS_FUSED(0); break;
+    case 1: GS_FUSED(1); break;
+    case 2: GS_FUSED(2); break;
+    default: GS_FUSED(3); break;
   }
+#undef GS_FUSED
   return nb;
 }
 

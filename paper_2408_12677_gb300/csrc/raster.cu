@@ -38,7 +38,7 @@ __device__ __forceinline__ void stage_entry(const float4* __restrict__ feat, uin
   const float mlx = __fadd_rn(__fsub_rn(f0.x, ox), f0.z);
   const float mly = __fadd_rn(__fsub_rn(f0.y, oy), f0.w);
   sa = make_float4(mlx, mly, f1.x, f1.y);
-  sb = make_float4(f1.z, f1.w, f2.w, ex2_approx(f1.w));
+  sb = make_float4(f1.z, f1.w, f2.w, ex2_approx(-f1.w));  // .w = 1 / opacity
   sc = make_float4(f2.x, f2.y, f2.z, 0.f);
   mask = 0;
   const float R2 = fminf(rp.qmax_s, f1.w - rp.log2_alpha_min);
@@ -70,7 +70,7 @@ __device__ __forceinline__ int build_list(const uint32_t* s_mask, int cnt, int w
   return count;
 }
 
-template <int TW, int TH>
+template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ ids,
                                                               const float4* __restrict__ feat,
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ float4 s_a[kBatch];  // mu_local.x, mu_local.y, i0, k
-  __shared__ float4 s_b[kBatch];  // i1, log2o, z, opacity
+  __shared__ float4 s_b[kBatch];  // i1, log2o, z, 1/opacity
   __shared__ float4 s_c[kBatch];  // r, g, b, -
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint8_t s_list[kThreads / 32][kBatch];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
       const float4 bb = s_b[j];
       PixEval e;
       if (!done0) {
-        ++n_visit;
+        if (COUNT) ++n_visit;
         if (eval_splat(a, bb.x, bb.y, plx, ply0, rp.qmax_s, rp.log2_alpha_min, e)) {
           const float al = fminf(rp.alpha_max, e.araw);
           const float test_T = __fmul_rn(T0, __fsub_rn(1.f, al));
@@ -133,12 +133,12 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
             D0 = fmaf(w, bb.z, D0);
             T0 = test_T;
             last0 = b + j + 1;
-            ++n_blend;
+            if (COUNT) ++n_blend;
           }
         }
       }
       if (!done1) {
-        ++n_visit;
+        if (COUNT) ++n_visit;
         if (eval_splat(a, bb.x, bb.y, plx, ply1, rp.qmax_s, rp.log2_alpha_min, e)) {
           const float al = fminf(rp.alpha_max, e.araw);
           const float test_T = __fmul_rn(T1, __fsub_rn(1.f, al));
@@ -153,13 +153,13 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
             D1 = fmaf(w, bb.z, D1);
             T1 = test_T;
             last1 = b + j + 1;
-            ++n_blend;
+            if (COUNT) ++n_blend;
           }
         }
       }
     }
   }
-  if (counters) {
+  if (COUNT) {
     unsigned long long vb = n_blend, vv = n_visit;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -198,42 +198,48 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
   }
 }
 
-// Sum v[0..15] over the warp: halving exchanges (xor 16, 8, 4, 2) leave each
-// lane with one partial sum, the last xor-1 step completes it; lane l (even)
-// then holds the total of value 8 b4 + 4 b3 + 2 b2 + b1 (b = bits of l) and
-// adds it to dst[that value] if it is one of the first `nvals`.
-__device__ __forceinline__ void warp_transpose_add(float (&v)[16], float* dst, int nvals) {
+// Sum the 10 values v[0..9] over the warp with exchanges that halve the number
+// of values each lane carries (xor 16: 10 -> 5, xor 8: 5 -> 3, xor 4: 3 -> 2,
+// xor 2: 2 -> 1) and a final xor-1 step (12 shuffles instead of 50).  The
+// even lane l then holds the total of value vidx(l) and adds it to dst.
+__device__ __forceinline__ void warp_transpose_add10(float (&v)[10], float* dst) {
   const int lane = threadIdx.x & 31;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float u[5];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const bool h = lane & 16;
-    const float send = h ? v[i] : v[i + 8];
-    const float keep = h ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 16);
+  for (int i = 0; i < 5; ++i) {  // keep v[i] (b4 = 0) or v[i + 5] (b4 = 1)
+    const float send = b4 ? v[i] : v[i + 5];
+    const float keep = b4 ? v[i + 5] : v[i];
+    u[i] = keep + __shfl_xor_sync(kFull, send, 16);
   }
+  float w3[3];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool h = lane & 8;
-    const float send = h ? v[i] : v[i + 4];
-    const float keep = h ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 8);
+  for (int i = 0; i < 3; ++i) {  // keep u[0..2] (b3 = 0) or u[3..4], 0 (b3 = 1)
+    const float hi = i < 2 ? u[i + 3] : 0.f;
+    const float send = b3 ? u[i] : hi;
+    const float keep = b3 ? hi : u[i];
+    w3[i] = keep + __shfl_xor_sync(kFull, send, 8);
   }
+  float w2[2];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool h = lane & 4;
-    const float send = h ? v[i] : v[i + 2];
-    const float keep = h ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+  for (int i = 0; i < 2; ++i) {  // keep w3[0..1] (b2 = 0) or w3[2], 0 (b2 = 1)
+    const float hi = i < 1 ? w3[i + 2] : 0.f;
+    const float send = b2 ? w3[i] : hi;
+    const float keep = b2 ? hi : w3[i];
+    w2[i] = keep + __shfl_xor_sync(kFull, send, 4);
   }
+  float x;
   {
-    const bool h = lane & 2;
-    const float send = h ? v[0] : v[1];
-    const float keep = h ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(kFull, send, 2);
+    const float send = b1 ? w2[0] : w2[1];
+    const float keep = b1 ? w2[1] : w2[0];
+    x = keep + __shfl_xor_sync(kFull, send, 2);
   }
-  v[0] += __shfl_xor_sync(kFull, v[0], 1);
-  const int f = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-  if (!(lane & 1) && f < nvals) atomicAdd(&dst[f], v[0]);
+  x += __shfl_xor_sync(kFull, x, 1);
+  // value held: 5 b4 + i3 with i3 = 3 b3 + 2 b2 + b1 among the five kept at
+  // xor 16; lanes with b2 and (b3 or b1) hold the zero pads
+  const int i3 = (b3 ? 3 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
+  const bool valid = !(b2 && (b3 || b1));
+  if (!(lane & 1) && valid) atomicAdd(&dst[(b4 ? 5 : 0) + i3], x);
 }
 
 // Back-to-front step of one pixel for one Gaussian: updates the pixel's
@@ -241,11 +247,11 @@ __device__ __forceinline__ void warp_transpose_add(float (&v)[16], float* dst, i
 // gradient record (mu 2, factor 3, opacity, z, rgb 3) to v.
 __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, const float4* s_c, int j, float plx,
                                           float ply, const RasterParams& rp, float& T, float& U, float dC0, float dC1,
-                                          float dC2, float dD, float dA_T, float (&v)[16]) {
+                                          float dC2, float dD, float dA_T, float (&v)[10]) {
   PixEval e;
   if (!eval_splat(a, bb.x, bb.y, plx, ply, rp.qmax_s, rp.log2_alpha_min, e)) return false;
   const float al = fminf(rp.alpha_max, e.araw);
-  const float inv1m = 1.f / (1.f - al);
+  const float inv1m = __frcp_rn(1.f - al);
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
   const float w = al * Ti;
   const float4 c = s_c[j];
@@ -259,7 +265,7 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
   U = fmaf(w, cdot, U);
   T = Ti;
   if (e.araw <= rp.alpha_max) {
-    v[5] += g_alpha * e.araw / bb.w;             // d alpha / d opacity = G
+    v[5] += g_alpha * e.araw * bb.w;             // d alpha / d opacity = G = alpha / opacity
     const float gq = -g_alpha * e.araw * kLn2;  // d alpha / d q' = -ln2 alpha
     // q' = t0^2 + t1^2, t0 = i0 dx, t1 = i1 (dy - k dx), dx = plx - mu_x
     const float two_t0 = 2.f * e.t0, two_t1 = 2.f * e.t1;
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ float4 s_a[kBatch];
-  __shared__ float4 s_b[kBatch];  // i1, log2o, z, opacity
+  __shared__ float4 s_b[kBatch];  // i1, log2o, z, 1/opacity
   __shared__ float4 s_c[kBatch];
   __shared__ uint32_t s_mask[kBatch];
   __shared__ uint32_t s_id[kBatch];
@@ -360,9 +366,9 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       if (idx >= wmax) continue;  // behind every pixel's last contributor in this warp
       const float4 a = s_a[j];
       const float4 bb = s_b[j];
-      float v[16];
+      float v[10];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      for (int k = 0; k < 10; ++k) v[k] = 0.f;
       bool contrib = false;
       if (idx < last0) contrib |= bwd_pixel(a, bb, s_c, j, plx, ply0, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
       if (idx < last1) contrib |= bwd_pixel(a, bb, s_c, j, plx, ply1, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
@@ -374,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
           for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[j][k], v[k]);
         }
       } else {
-        warp_transpose_add(v, s_acc[j], 10);
+        warp_transpose_add10(v, s_acc[j]);
       }
     }
     __syncthreads();
@@ -423,15 +429,19 @@ void launch_raster_fwd(const RasterArgs& a, float* color, float* depth, float* a
   const int nt = a.tiles_x * a.tiles_y;
   if (nt == 0) return;
   RasterParams rp = make_params(a);
-  if (a.tile_w == 16)
-    raster_fwd_kernel<16, 16><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, color, depth, alpha, T_final, last,
-                                                      counters);
-  else if (a.tile_w == 8)
-    raster_fwd_kernel<8, 32><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, color, depth, alpha, T_final, last,
-                                                      counters);
-  else
-    raster_fwd_kernel<32, 8><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, color, depth, alpha, T_final, last,
-                                                      counters);
+#define GS_FWD(TW_, TH_, C_)                                                                               \
+  raster_fwd_kernel<TW_, TH_, C_><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, color, depth, alpha, T_final, \
+                                                         last, counters)
+  if (counters) {
+    if (a.tile_w == 16) GS_FWD(16, 16, true);
+    else if (a.tile_w == 8) GS_FWD(8, 32, true);
+    else GS_FWD(32, 8, true);
+  } else {
+    if (a.tile_w == 16) GS_FWD(16, 16, false);
+    else if (a.tile_w == 8) GS_FWD(8, 32, false);
+    else GS_FWD(32, 8, false);
+  }
+#undef GS_FWD
 }
 
 void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, const float* dL_dcolor,

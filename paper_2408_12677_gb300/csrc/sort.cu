@@ -260,8 +260,8 @@ __global__ void export_keys_kernel(const uint32_t* __restrict__ tiles, const uin
 }
 
 int sort_blocks(uint32_t n, int num_sms, int max_blocks) {
-  // at least 16 rounds of 256 items per block; at most two blocks per SM
-  int g = (int)std::min<uint64_t>(((uint64_t)n + 4095) / 4096, (uint64_t)std::max(1, 2 * num_sms));
+  // about four rounds of 256 items per block; at most four blocks per SM
+  int g = (int)std::min<uint64_t>(((uint64_t)n + 1023) / 1024, (uint64_t)std::max(1, 4 * num_sms));
   return std::max(1, std::min(g, max_blocks));
 }
 
