@@ -146,6 +146,11 @@ gs_status gs_ctx_reserve(gs_ctx *ctx, int64_t n_gaussians, int64_t n_pixels, int
  * the next gs_render_fwd / gs_sync_status reports GS_ERR_CAPACITY. */
 gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
 
+/* Set the context's device-side Adam step counter (used by
+ * gs_render_bwd_adam with step = 0, which increments it before each use).
+ * Synchronises the device. */
+gs_status gs_ctx_set_adam_step(gs_ctx *ctx, int64_t step);
+
 /* Synchronise the stream, then report GS_ERR_CAPACITY if a no-sync forward
  * pass overflowed the pair buffers (and clear the flag). */
 gs_status gs_sync_status(gs_ctx *ctx, gs_stream_t stream);
@@ -204,8 +209,12 @@ gs_status gs_render_bwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam
  * gs_render_bwd into zeroed gradients followed by gs_adam_step, but never
  * writes the parameter gradients: each Gaussian's gradient is applied by the
  * thread that computes it.  `params` is the flat parameter buffer (layout
- * above) that `g` must point into; m, v are the Adam moments (same layout);
- * step >= 1.  cfg->zero_grads is ignored.  dL_dpose as in gs_render_bwd. */
+ * above) that `g` must point into; m, v are the Adam moments (same layout).
+ * step >= 1 is the Adam step; step = 0 instead increments the context's
+ * device-side step counter and uses it (no host value changes between
+ * calls, so a captured CUDA graph can replay the call; see
+ * gs_ctx_set_adam_step).  cfg->zero_grads is ignored.  dL_dpose as in
+ * gs_render_bwd. */
 gs_status gs_render_bwd_adam(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam,
                              const gs_viewmat *view, const gs_raster_cfg *cfg,
                              const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,

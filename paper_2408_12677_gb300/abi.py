@@ -74,6 +74,7 @@ EXPORTS = {
     "gs_last_error": (C.c_char_p, [P]),
     "gs_ctx_reserve": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
     "gs_ctx_set_sync": (C.c_int, [P, C.c_int]),
+    "gs_ctx_set_adam_step": (C.c_int, [P, C.c_int64]),
     "gs_sync_status": (C.c_int, [P, P]),
     "gs_get_stats": (C.c_int, [P, C.POINTER(gs_stats)]),
     "gs_raster_cfg_default": (C.c_int, [C.POINTER(gs_raster_cfg)]),
@@ -216,6 +217,10 @@ def gs_ctx_reserve(ctx, n_gaussians=0, n_pixels=0, n_pairs=0):
 
 def gs_ctx_set_sync(ctx, sync: bool):
     _check(ctx, load().gs_ctx_set_sync(ctx, int(bool(sync))), "gs_ctx_set_sync")
+
+
+def gs_ctx_set_adam_step(ctx, step: int):
+    _check(ctx, load().gs_ctx_set_adam_step(ctx, int(step)), "gs_ctx_set_adam_step")
 
 
 def gs_sync_status(ctx, stream=None):

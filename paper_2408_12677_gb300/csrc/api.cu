@@ -42,6 +42,11 @@ struct gs_ctx {
   // per-tile / per-pixel scratch
   int64_t cap_t = 0;
   uint2* ranges = nullptr;
+  uint32_t* tcount = nullptr;   // per-tile pair counts
+  uint32_t* toffset = nullptr;  // per-tile list offsets
+  uint32_t* tcursor = nullptr;  // per-tile scatter cursors
+  unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
+  long long* d_step = nullptr;               // device Adam step counter (step = 0 calls)
   int64_t cap_px = 0;
   float* T_final = nullptr;
   int32_t* last = nullptr;
@@ -167,6 +172,9 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   GS_CUDA(c, cudaDeviceSynchronize());
   const int64_t cap = grow_target(t, c->cap_t);
   GS_CUDA(c, regrow(&c->ranges, cap));
+  GS_CUDA(c, regrow(&c->tcount, cap));
+  GS_CUDA(c, regrow(&c->toffset, cap));
+  GS_CUDA(c, regrow(&c->tcursor, cap));
   c->cap_t = cap;
   c->have_state = false;
   return GS_OK;
@@ -248,10 +256,11 @@ gs_status ensure_hist(gs_ctx* c) {
   return GS_OK;
 }
 
-// Depth sort of n Gaussians (keys in zkey, ids implicit), duplication into
+// Radix binning (used when a tile list is longer than the per-tile sort holds):
+// depth sort of n Gaussians (keys in zkey, ids implicit), duplication into
 // pairs, pair sort by tile, tile ranges.  On success c->st_pairs / st_pair_buf
 // describe the sorted pair list.
-gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
+gs_status bin_and_sort_radix(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
   const int64_t T = (int64_t)tiles_x * tiles_y;
   if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
   SortBuffers sb;
@@ -330,6 +339,62 @@ gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t 
   return GS_OK;
 }
 
+// Counting-scatter binning with per-tile sorts: count, scan (one host read of
+// the totals in sync mode), scatter, sort.  Falls back to the radix path when
+// some tile list is longer than the per-tile sort holds.
+gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
+  const int64_t T = (int64_t)tiles_x * tiles_y;
+  if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
+  TileBinArgs tb;
+  tb.n = n;
+  tb.rects = c->rects;
+  tb.tiles = c->tiles;
+  tb.zkey = c->zkey;
+  tb.tiles_x = tiles_x;
+  tb.n_tiles = (int)T;
+  tb.num_sms = c->num_sms;
+  tb.counts = c->tcount;
+  tb.offsets = c->toffset;
+  tb.cursors = c->tcursor;
+  tb.ids = nullptr;
+  tb.ranges = c->ranges;
+  tb.capacity = c->sync ? 0xFFFFFFF0u : (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFF0ll);
+  tb.n_pairs = c->d_npairs;
+  tb.stats = c->d_binstats;
+  tb.overflow = c->d_overflow;
+  {
+    StageTimer t(c, GS_STAGE_DUPLICATE, s);
+    launch_tile_count_scan(tb, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "tile count/scan");
+  int64_t P = -1;
+  if (c->sync) {
+    GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_binstats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    P = (int64_t)c->h_pinned[0];
+    const int64_t longest = (int64_t)c->h_pinned[1];
+    if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, tiles_x, tiles_y, s);
+    gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
+    if (st != GS_OK) return st;
+    tb.capacity = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFF0ll);
+  } else if (c->cap_p == 0) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode needs reserved pair capacity (gs_ctx_reserve)");
+  }
+  tb.ids = c->pv[0];
+  {
+    StageTimer t(c, GS_STAGE_DUPLICATE, s);
+    launch_tile_scatter(tb, s, &c->launches);
+  }
+  {
+    StageTimer t(c, GS_STAGE_PAIR_SORT, s);
+    launch_tile_sort(tb, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "tile scatter/sort");
+  c->st_pairs = P;
+  c->st_pair_buf = 0;
+  return GS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -374,6 +439,10 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_npairs, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_npairs_full, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_overflow, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
+  if (e == cudaSuccess) init_project_kernels();
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_evals, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_overflow, 0, sizeof(uint32_t));
@@ -409,6 +478,11 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->pose_partials);
   cudaFree(c->hist);
   cudaFree(c->ranges);
+  cudaFree(c->tcount);
+  cudaFree(c->toffset);
+  cudaFree(c->tcursor);
+  cudaFree(c->d_binstats);
+  cudaFree(c->d_step);
   cudaFree(c->T_final);
   cudaFree(c->last);
   cudaFree(c->loss_partials);
@@ -436,6 +510,15 @@ gs_status gs_ctx_reserve(gs_ctx* c, int64_t n_gaussians, int64_t n_pixels, int64
   if (n_pixels > 0 && (s = ensure_px(c, n_pixels)) != GS_OK) return s;
   if (n_pixels > 0 && (s = ensure_tiles(c, (n_pixels + 63) / 64 + 1024)) != GS_OK) return s;
   if (n_pairs > 0 && (s = ensure_pairs(c, n_pairs)) != GS_OK) return s;
+  return GS_OK;
+}
+
+gs_status gs_ctx_set_adam_step(gs_ctx* c, int64_t step) {
+  if (!c || step < 0) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaDeviceSynchronize());
+  const long long v = (long long)step;
+  GS_CUDA(c, cudaMemcpy(c->d_step, &v, sizeof(v), cudaMemcpyHostToDevice));
   return GS_OK;
 }
 
@@ -662,8 +745,8 @@ ProjectArgs project_args(const gs_gaussians* g, const gs_camera* cam, const gs_v
   return pa;
 }
 
-gs_status check_adam(gs_ctx* c, const gs_adam_cfg* cfg, int64_t step) {
-  if (!cfg || step < 1) return fail(c, GS_ERR_INVALID_ARG, "Adam: bad cfg or step");
+gs_status check_adam(gs_ctx* c, const gs_adam_cfg* cfg, int64_t step, bool allow_device_step = false) {
+  if (!cfg || step < (allow_device_step ? 0 : 1)) return fail(c, GS_ERR_INVALID_ARG, "Adam: bad cfg or step");
   if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
     return fail(c, GS_ERR_INVALID_ARG, "Adam: betas must be in [0, 1), eps >= 0");
   return GS_OK;
@@ -680,10 +763,16 @@ AdamArgs adam_args(const gs_adam_cfg* cfg, int64_t step) {
   ad.beta1 = cfg->beta1;
   ad.beta2 = cfg->beta2;
   ad.eps = cfg->eps;
-  const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
-  const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
-  ad.step_scale = (float)(1.0 / bc1);
-  ad.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+  ad.step_dev = nullptr;
+  ad.log_beta1 = (float)std::log((double)cfg->beta1);
+  ad.log_beta2 = (float)std::log((double)cfg->beta2);
+  ad.step_scale = ad.inv_sqrt_bc2 = 1.f;
+  if (step > 0) {
+    const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
+    const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
+    ad.step_scale = (float)(1.0 / bc1);
+    ad.inv_sqrt_bc2 = (float)(1.0 / std::sqrt(bc2));
+  }
   return ad;
 }
 
@@ -696,7 +785,7 @@ gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* 
   if (!c) return GS_ERR_INVALID_ARG;
   gs_status st;
   if ((st = check_bwd_common(c, g, cam, view, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
-  if ((st = check_adam(c, adam, step)) != GS_OK) return st;
+  if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
   const int64_t n = g->n;
   if (n > 0 && (!params || !m || !v)) return fail(c, GS_ERR_INVALID_ARG, "params, m and v are required");
   if (n > 0 && (g->means != params || g->log_scales != params + 3 * n || g->quats != params + 6 * n ||
@@ -709,7 +798,13 @@ gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* 
   const ProjectArgs pa = project_args(g, cam, view, cfg, c->st_tx, c->st_ty);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
-    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, adam_args(adam, step), c->pose_partials, s);
+    AdamArgs ad = adam_args(adam, step);
+    if (step == 0) {
+      launch_step_increment(c->d_step, s);
+      c->launches += 1;
+      ad.step_dev = c->d_step;
+    }
+    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, c->pose_partials, s);
     c->launches += 1;
     if (dL_dpose) {
       launch_pose_reduce(c->pose_partials, nb, dL_dpose, s);
@@ -833,7 +928,7 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
   }
   if (P > 0) {
     if (!keys || !ids) return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: NULL keys/ids");
-    launch_export_keys(c->pk[c->st_pair_buf], c->pv[c->st_pair_buf], c->zkey, (uint32_t)P, keys, ids, s);
+    launch_export_keys_ranges(c->ranges, (int)T, c->pv[c->st_pair_buf], c->zkey, (uint32_t)P, keys, ids, s);
     c->launches += 1;
   }
   GS_CHECK_LAUNCH(c, "bin export");

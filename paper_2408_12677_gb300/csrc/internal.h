@@ -38,9 +38,15 @@ void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cud
 struct AdamArgs {
   float lr[6];  // means, log-scales, quaternions, opacity, SH DC, SH rest
   float beta1, beta2, eps;
-  float step_scale;    // 1 / (1 - beta1^t)
-  float inv_sqrt_bc2;  // 1 / sqrt(1 - beta2^t)
+  float step_scale;    // 1 / (1 - beta1^t), when step_dev is null
+  float inv_sqrt_bc2;  // 1 / sqrt(1 - beta2^t), when step_dev is null
+  const long long* step_dev;  // device step counter (bias corrections computed on the device), or null
+  float log_beta1, log_beta2;  // log(beta) for the device-side bias corrections
 };
+// device step counter: *step += 1
+void launch_step_increment(long long* step, cudaStream_t s);
+// set once per context: shared-memory limits of the fused kernel
+void init_project_kernels();
 // fused projection backward + Adam over the flat buffer (one view, one step)
 int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
                             const AdamArgs& ad, float* pose_partials, cudaStream_t s);
@@ -80,6 +86,29 @@ int dup_blocks(int n);
 void launch_dup_count_scan(const DupArgs& a, cudaStream_t s, int64_t* launches);
 void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches);
 
+// counting-scatter binning with per-tile sorts (lists of at most kTileSortCap)
+constexpr int kTileSortCap = 4096;
+struct TileBinArgs {
+  int n;                      // Gaussians
+  const ushort4* rects;       // per Gaussian tile rectangle
+  const uint32_t* tiles;      // per Gaussian tile count
+  const uint32_t* zkey;       // per Gaussian float32 depth bits
+  int tiles_x, n_tiles, num_sms;
+  uint32_t* counts;           // per tile
+  uint32_t* offsets;          // per tile
+  uint32_t* cursors;          // per tile
+  uint32_t* ids;              // per pair: Gaussian id (output, sorted per tile)
+  uint2* ranges;              // per tile (output)
+  uint32_t capacity;          // pair slots in ids
+  uint32_t* n_pairs;          // device: min(total, capacity)
+  unsigned long long* stats;  // device: [0] total pairs, [1] longest list
+  uint32_t* overflow;         // device flag: 1 = pairs over capacity, 2 = list over kTileSortCap
+};
+int tile_sort_capacity();
+void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
+void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
+void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
+
 void launch_tile_ranges(const uint32_t* sorted_tiles, const uint32_t* n_dev, uint32_t n_max, uint2* ranges,
                         int n_tiles, int num_sms, cudaStream_t s, int64_t* launches);
 
@@ -112,5 +141,9 @@ void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, 
                               float* depth, float* rgb, float* opacity, int32_t* tiles_out, cudaStream_t s);
 void launch_export_keys(const uint32_t* sorted_tiles, const uint32_t* sorted_ids, const uint32_t* depth_key_by_id,
                         uint32_t P, uint64_t* keys, uint32_t* ids, cudaStream_t s);
+// same, taking the tile of each pair from the per-tile ranges
+void launch_export_keys_ranges(const uint2* ranges, int n_tiles, const uint32_t* sorted_ids,
+                               const uint32_t* depth_key_by_id, uint32_t P, uint64_t* keys, uint32_t* ids,
+                               cudaStream_t s);
 
 }  // namespace gs

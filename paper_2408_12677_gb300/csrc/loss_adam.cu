@@ -60,28 +60,36 @@ __global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(
   }
 }
 
-// Pass 2 (one block): fixed-order reduction of the partials -> loss and the
-// depth-gradient scale w_depth / n_valid (stored in scale[0]).
-__global__ void loss_finalize_kernel(const float* __restrict__ partials, int nblocks, int npix, float w_color,
-                                     float w_depth, float* __restrict__ loss, float* __restrict__ scale) {
-  __shared__ double red[3][32];
-  double a[3] = {0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-    for (int k = 0; k < 3; ++k) a[k] += (double)partials[3 * b + k];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k = 0; k < 3; ++k) {
-    double v = a[k];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
-    if (lane == 0) red[k][wid] = v;
+// Pass 2 (one block of 256): fixed-order reduction of the partials -> loss and
+// the depth-gradient scale w_depth / n_valid (stored in scale[0]).  Each
+// thread sums a strided subset in order, then a fixed tree combines them, so
+// the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) loss_finalize_kernel(const float* __restrict__ partials, int nblocks, int npix,
+                                                            float w_color, float w_depth, float* __restrict__ loss,
+                                                            float* __restrict__ scale) {
+  __shared__ float red[3][256];
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  for (int b = threadIdx.x; b < nblocks; b += 256) {
+    a0 += partials[3 * b];
+    a1 += partials[3 * b + 1];
+    a2 += partials[3 * b + 2];
   }
+  red[0][threadIdx.x] = a0;
+  red[1][threadIdx.x] = a1;
+  red[2][threadIdx.x] = a2;
   __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w)
-      for (int k = 0; k < 3; ++k) s[k] += red[k][w];
-    const double nv = s[2] > 0.0 ? s[2] : 1.0;
-    loss[0] = (float)(w_color * s[0] / (3.0 * npix) + w_depth * s[1] / nv);
-    scale[0] = (float)(w_depth / nv);
+    const float nv = red[2][0] > 0.f ? red[2][0] : 1.f;
+    loss[0] = w_color * red[0][0] / (3.f * (float)npix) + w_depth * red[1][0] / nv;
+    scale[0] = w_depth / nv;
   }
 }
 
@@ -193,7 +201,7 @@ void launch_loss(int H, int W, const float* color, const float* depth, const flo
   float* scale = partials + 3 * nb;
   loss_partials_kernel<<<nb, kLossThreads, 0, s>>>(npix, color, depth, trgb, tdep, w_color / (3.f * (float)npix),
                                                    dLdc, dLdd, partials);
-  loss_finalize_kernel<<<1, 1024, 0, s>>>(partials, nb, npix, w_color, w_depth, loss, scale);
+  loss_finalize_kernel<<<1, 256, 0, s>>>(partials, nb, npix, w_color, w_depth, loss, scale);
   scale_kernel<<<std::min(1024, (npix + 255) / 256), 256, 0, s>>>(npix, dLdd, scale);
   if (launches) *launches += 3;
 }

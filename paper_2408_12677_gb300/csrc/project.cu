@@ -88,11 +88,26 @@ __device__ __forceinline__ void geometry(const CamView& cv, float dilation, floa
   g.i1 = kS2 * sqrtf(g.a / g.det);
 }
 
-__global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a, float4* __restrict__ feat,
-                                                          uint32_t* __restrict__ depth_key,
-                                                          uint32_t* __restrict__ tiles_touched,
-                                                          ushort4* __restrict__ rects) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int kFwdThreads = 128;
+
+template <int D>
+__global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(ProjectArgs a, float4* __restrict__ feat,
+                                                                  uint32_t* __restrict__ depth_key,
+                                                                  uint32_t* __restrict__ tiles_touched,
+                                                                  ushort4* __restrict__ rects) {
+  constexpr int K = (D + 1) * (D + 1);
+  constexpr int NS = 3 * K;
+  constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
+  __shared__ float s_sh[kFwdThreads * RS];
+  // the block's SH coefficients are contiguous: stage them with coalesced loads
+  const int base = blockIdx.x * kFwdThreads;
+  const int cnt = min(kFwdThreads, a.n - base);
+  for (int e = threadIdx.x; e < cnt * NS; e += kFwdThreads) {
+    const int gi = e / NS;
+    s_sh[gi * RS + (e - gi * NS)] = __ldg(a.sh + (size_t)base * NS + e);
+  }
+  __syncthreads();
+  const int i = base + threadIdx.x;
   if (i >= a.n) return;
   const CamView& cv = a.cv;
   const float px = a.means[3 * i], py = a.means[3 * i + 1], pz = a.means[3 * i + 2];
@@ -138,13 +153,13 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(ProjectArgs a, float4*
   depth_key[i] = __float_as_uint(z);
 
   // view-dependent colour
-  const int K = (a.sh_degree + 1) * (a.sh_degree + 1);
   float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
   float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
   float Yb[16];
-  sh_basis(a.sh_degree, dx * inv, dy * inv, dz * inv, Yb);
-  const float* shp = a.sh + (size_t)i * K * 3;
+  sh_basis(D, dx * inv, dy * inv, dz * inv, Yb);
+  const float* shp = s_sh + threadIdx.x * RS;
   float rgb[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
   for (int k = 0; k < K; ++k) {
     rgb[0] += Yb[k] * shp[3 * k];
     rgb[1] += Yb[k] * shp[3 * k + 1];
@@ -390,6 +405,17 @@ __global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a,
   block_pose_partial(pose, pose_partials);
 }
 
+// Bias corrections from the device step counter: 1 - beta^t = -expm1(t log beta),
+// accurate also for small t where 1 - powf(beta, t) would cancel.
+__device__ __forceinline__ void device_bias_corrections(AdamArgs& ad) {
+  if (!ad.step_dev) return;
+  const float t = (float)*ad.step_dev;
+  ad.step_scale = 1.f / -expm1f(t * ad.log_beta1);
+  ad.inv_sqrt_bc2 = rsqrtf(-expm1f(t * ad.log_beta2));
+}
+
+__global__ void step_increment_kernel(long long* step) { *step += 1; }
+
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& ad) {
   m = ad.beta1 * m + (1.f - ad.beta1) * g;
   v = ad.beta2 * v + (1.f - ad.beta2) * g * g;
@@ -438,6 +464,7 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(Project
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
                                                                          float* __restrict__ pose_partials) {
+  device_bias_corrections(ad);
   using S = FusedSmem<D>;
   constexpr int K = S::K, NS = S::NS, RS = S::RS, B = S::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -568,7 +595,13 @@ __global__ void pose_reduce_kernel(const float* __restrict__ partials, int nbloc
 void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key, uint32_t* tiles_touched,
                         ushort4* rects, cudaStream_t s) {
   if (a.n <= 0) return;
-  project_fwd_kernel<<<(a.n + 255) / 256, 256, 0, s>>>(a, feat, depth_key, tiles_touched, rects);
+  const int nb = (a.n + kFwdThreads - 1) / kFwdThreads;
+  switch (a.sh_degree) {
+    case 0: project_fwd_kernel<0><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
+    case 1: project_fwd_kernel<1><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
+    case 2: project_fwd_kernel<2><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
+    default: project_fwd_kernel<3><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
+  }
 }
 
 void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
@@ -601,11 +634,8 @@ int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* para
   const int nb = project_bwd_blocks(a.n);
   if (nb == 0) return 0;
 #define GS_FUSED(D_)                                                                                      \
-  do {                                                                                                    \
-    const int bytes = (int)sizeof(FusedSmem<D_>);                                                         \
-    cudaFuncSetAttribute(project_bwd_adam_kernel<D_>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); \
-    project_bwd_adam_kernel<D_><<<nb, kFusedThreads, bytes, s>>>(a, g2d, params, m, v, ad, pose_partials); \
-  } while (0)
+  project_bwd_adam_kernel<D_><<<nb, kFusedThreads, (int)sizeof(FusedSmem<D_>), s>>>(a, g2d, params, m, v, ad, \
+                                                                                   pose_partials)
   switch (a.sh_degree) {
     case 0: GS_FUSED(0); break;
     case 1: GS_FUSED(1); break;
@@ -615,6 +645,19 @@ int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* para
 #undef GS_FUSED
   return nb;
 }
+
+void init_project_kernels() {
+  cudaFuncSetAttribute(project_bwd_adam_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(FusedSmem<0>));
+  cudaFuncSetAttribute(project_bwd_adam_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(FusedSmem<1>));
+  cudaFuncSetAttribute(project_bwd_adam_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(FusedSmem<2>));
+  cudaFuncSetAttribute(project_bwd_adam_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(FusedSmem<3>));
+}
+
+void launch_step_increment(long long* step, cudaStream_t s) { step_increment_kernel<<<1, 1, 0, s>>>(step); }
 
 void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s) {
   pose_reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, dL_dpose);

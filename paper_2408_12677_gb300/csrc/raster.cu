@@ -2,16 +2,16 @@
 // transmittance) and backward (back to front from the stored last
 // contributor, transmittance recomputed from the stored final T).
 //
-// One CTA of 128 threads per tile; each warp owns an 8 x 8 pixel block, each
-// thread two pixels of it (rows y and y + 4).  The tile's depth-sorted list is
-// staged in shared memory 256 Gaussians at a time (gathered 48 B records,
-// converted to tile-local coordinates so the per-pixel offsets keep float32
-// precision); each Gaussian's support bounding box is tested against the four
-// warp blocks and every warp walks only its own compacted list.  The backward
-// pass sums each Gaussian's gradient over the warp (direct shared atomics when
-// at most two lanes contribute, else a transposed shuffle reduction), over the
-// CTA in shared memory, and adds it to global memory once per tile with
-// float4 atomics.
+// One CTA of 128 threads per tile; each warp owns an 8 x 8 pixel block of it,
+// each thread two pixels (rows y and y + 4), and the four warps run
+// independently (no block barriers).  A warp walks the tile's depth-sorted
+// list in chunks of 32 entries with the next chunk's 48 B records already in
+// flight, converts the records to tile-local coordinates (so per-pixel offsets
+// keep float32 precision), keeps the entries whose support bounding box meets
+// its block (ballot) and evaluates only those.  The backward pass sums each
+// Gaussian's gradient over the warp (per-lane atomics when at most two lanes
+// contribute, else a transposed shuffle reduction) and adds it to the
+// Gaussian's global record with one warp-wide atomic.
 #include "common.cuh"
 #include "internal.h"
 
@@ -19,55 +19,43 @@ namespace gs {
 
 namespace {
 
-constexpr int kThreads = 128;  // 4 warps, each owns an 8 x 8 pixel block, 2 pixels per thread
-constexpr int kBatch = 256;    // Gaussians staged in shared memory per step
+constexpr int kThreads = 128;  // 4 independent warps per CTA, one 8 x 8 pixel block each
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Stage one list entry: features in tile-local coordinates and the mask of
-// warps whose 8 x 8 block meets the splat's support bounding box.  The box
-// holds every pixel the per-pixel test can accept: q' <= min(qmax, log2 o -
-// log2 alpha_min) is the ellipse (i0 dx)^2 + (i1 (dy - k dx))^2 <= R2, whose
-// half-extents are sqrt(R2) / i0 and sqrt(R2) sqrt(k^2 / i0^2 + 1 / i1^2);
-// the widening covers float32 rounding of the test.
-template <int WX>
-__device__ __forceinline__ void stage_entry(const float4* __restrict__ feat, uint32_t g, float ox, float oy,
-                                            const RasterParams& rp, float4& sa, float4& sb, float4& sc,
-                                            uint32_t& mask) {
+// One list entry in tile-local coordinates:
+//   sa = {mu_x, mu_y, i0, k}, sb = {i1, log2 opacity, z, 1/opacity}, sc = {r, g, b, -}
+struct Entry {
+  float4 a, b, c;
+};
+
+__device__ __forceinline__ void load_entry(const float4* __restrict__ feat, uint32_t g, float4& f0, float4& f1,
+                                           float4& f2) {
   const float4* fg = feat + 3 * (size_t)g;
-  const float4 f0 = fg[0], f1 = fg[1], f2 = fg[2];
-  const float mlx = __fadd_rn(__fsub_rn(f0.x, ox), f0.z);
-  const float mly = __fadd_rn(__fsub_rn(f0.y, oy), f0.w);
-  sa = make_float4(mlx, mly, f1.x, f1.y);
-  sb = make_float4(f1.z, f1.w, f2.w, ex2_approx(-f1.w));  // .w = 1 / opacity
-  sc = make_float4(f2.x, f2.y, f2.z, 0.f);
-  mask = 0;
-  const float R2 = fminf(rp.qmax_s, f1.w - rp.log2_alpha_min);
-  if (R2 > 0.f && f1.x > 0.f && f1.z > 0.f) {
-    const float Rr = sqrtf(R2) * 1.0001f + 1e-4f;
-    const float inv0 = 1.f / f1.x, inv1 = 1.f / f1.z;
-    const float ex = Rr * inv0 + 1e-3f;
-    const float ey = Rr * sqrtf(f1.y * f1.y * inv0 * inv0 + inv1 * inv1) + 1e-3f;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const float x0 = (float)((w % WX) * 8) + 0.5f, y0 = (float)((w / WX) * 8) + 0.5f;
-      if (mlx + ex >= x0 && mlx - ex <= x0 + 7.f && mly + ey >= y0 && mly - ey <= y0 + 7.f) mask |= 1u << w;
-    }
-  }
+  f0 = __ldg(fg);
+  f1 = __ldg(fg + 1);
+  f2 = __ldg(fg + 2);
 }
 
-// Compact the batch entries whose mask has bit `w` into list[0..count).
-__device__ __forceinline__ int build_list(const uint32_t* s_mask, int cnt, int w, uint8_t* list) {
-  const int lane = threadIdx.x & 31;
-  int count = 0;
-  for (int base = 0; base < cnt; base += 32) {
-    const int j = base + lane;
-    const bool on = j < cnt && ((s_mask[j] >> w) & 1u);
-    const unsigned bal = __ballot_sync(kFull, on);
-    if (on) list[count + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
-    count += __popc(bal);
-  }
-  __syncwarp();
-  return count;
+// Converts a gathered record to tile-local coordinates and tests the splat's
+// support bounding box against the warp's 8 x 8 block [bx, bx + 8) x [by, by + 8).
+// The box holds every pixel the per-pixel test can accept: q' <= min(qmax,
+// log2 o - log2 alpha_min) is the ellipse (i0 dx)^2 + (i1 (dy - k dx))^2 <= R2,
+// with half-extents sqrt(R2) / i0 and sqrt(R2) sqrt(k^2 / i0^2 + 1 / i1^2);
+// the widening covers float32 rounding of the test.
+__device__ __forceinline__ bool make_entry(float4 f0, float4 f1, float4 f2, float ox, float oy, float bx, float by,
+                                           const RasterParams& rp, Entry& e) {
+  const float mlx = __fadd_rn(__fsub_rn(f0.x, ox), f0.z);
+  const float mly = __fadd_rn(__fsub_rn(f0.y, oy), f0.w);
+  e.a = make_float4(mlx, mly, f1.x, f1.y);
+  e.b = make_float4(f1.z, f1.w, f2.w, ex2_approx(-f1.w));
+  e.c = make_float4(f2.x, f2.y, f2.z, 0.f);
+  const float R2 = fminf(rp.qmax_s, f1.w - rp.log2_alpha_min);
+  if (!(R2 > 0.f && f1.x > 0.f && f1.z > 0.f)) return false;
+  const float Rr = sqrtf(R2) * 1.0001f + 1e-4f;
+  const float inv0 = __frcp_rn(f1.x), inv1 = __frcp_rn(f1.z);
+  const float ex = Rr * inv0 + 1e-3f;
+  const float ey = Rr * sqrtf(f1.y * f1.y * inv0 * inv0 + inv1 * inv1) + 1e-3f;
+  return mlx + ex >= bx + 0.5f && mlx - ex <= bx + 7.5f && mly + ey >= by + 0.5f && mly - ey <= by + 7.5f;
 }
 
 template <int TW, int TH, bool COUNT>
@@ -81,78 +69,82 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
                                                               unsigned long long* __restrict__ counters) {
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
-  __shared__ float4 s_a[kBatch];  // mu_local.x, mu_local.y, i0, k
-  __shared__ float4 s_b[kBatch];  // i1, log2o, z, 1/opacity
-  __shared__ float4 s_c[kBatch];  // r, g, b, -
-  __shared__ uint32_t s_mask[kBatch];
-  __shared__ uint8_t s_list[kThreads / 32][kBatch];
+  __shared__ Entry s_e[kThreads / 32][32];
   const int tile = blockIdx.x;
   const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lx = (warp % WX) * 8 + (lane & 7), ly0 = (warp / WX) * 8 + (lane >> 3), ly1 = ly0 + 4;
+  const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
+  const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
   const int px = tx * TW + lx, py0 = ty * TH + ly0, py1 = ty * TH + ly1;
   const bool in0 = px < rp.width && py0 < rp.height, in1 = px < rp.width && py1 < rp.height;
   const float plx = (float)lx + 0.5f, ply0 = (float)ly0 + 0.5f, ply1 = (float)ly1 + 0.5f;
-  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
+  const float ox = (float)(tx * TW), oy = (float)(ty * TH), bx = (float)bxi, by = (float)byi;
   const uint2 r = ranges[tile];
   const int n = (int)(r.y - r.x);
+  Entry* buf = s_e[warp];
 
   float T0 = 1.f, R0 = 0.f, G0 = 0.f, B0 = 0.f, D0 = 0.f;
   float T1 = 1.f, R1 = 0.f, G1 = 0.f, B1 = 0.f, D1 = 0.f;
   int last0 = 0, last1 = 0;
   uint32_t n_blend = 0, n_visit = 0;
   bool done0 = !in0, done1 = !in1;
-  for (int b = 0; b < n; b += kBatch) {
-    if (__syncthreads_count(done0 && done1) == kThreads) break;
-#pragma unroll
-    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
-      if (b + s < n) stage_entry<WX>(feat, ids[r.x + b + s], ox, oy, rp, s_a[s], s_b[s], s_c[s], s_mask[s]);
-    }
-    __syncthreads();
-    const int cnt = min(kBatch, n - b);
-    const int count = build_list(s_mask, cnt, warp, s_list[warp]);
-    for (int q = 0; q < count; ++q) {
-      if ((q & 7) == 0 && __all_sync(kFull, done0 && done1)) break;
-      const int j = s_list[warp][q];
-      const float4 a = s_a[j];
-      const float4 bb = s_b[j];
-      PixEval e;
+
+  // software pipeline: the records of the next 32 entries are in flight
+  float4 f0, f1, f2;
+  if (lane < n) load_entry(feat, ids[r.x + lane], f0, f1, f2);
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    if (__all_sync(kFull, done0 && done1)) break;
+    const bool have = c0 + lane < n;
+    const float4 h0 = f0, h1 = f1, h2 = f2;
+    if (c0 + 32 + lane < n) load_entry(feat, ids[r.x + c0 + 32 + lane], f0, f1, f2);
+    Entry e;
+    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e);
+    __syncwarp();
+    if (hit) buf[lane] = e;
+    unsigned bal = __ballot_sync(kFull, hit);
+    __syncwarp();
+    while (bal) {
+      const int j = __ffs(bal) - 1;
+      bal &= bal - 1;
+      const float4 a = buf[j].a;
+      const float4 bb = buf[j].b;
+      PixEval pe;
       if (!done0) {
         if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, plx, ply0, rp.qmax_s, rp.log2_alpha_min, e)) {
-          const float al = fminf(rp.alpha_max, e.araw);
+        if (eval_splat(a, bb.x, bb.y, plx, ply0, rp.qmax_s, rp.log2_alpha_min, pe)) {
+          const float al = fminf(rp.alpha_max, pe.araw);
           const float test_T = __fmul_rn(T0, __fsub_rn(1.f, al));
           if (test_T < rp.t_eps) {
             done0 = true;
           } else {
-            const float4 c = s_c[j];
+            const float4 c = buf[j].c;
             const float w = al * T0;
             R0 = fmaf(w, c.x, R0);
             G0 = fmaf(w, c.y, G0);
             B0 = fmaf(w, c.z, B0);
             D0 = fmaf(w, bb.z, D0);
             T0 = test_T;
-            last0 = b + j + 1;
+            last0 = c0 + j + 1;
             if (COUNT) ++n_blend;
           }
         }
       }
       if (!done1) {
         if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, plx, ply1, rp.qmax_s, rp.log2_alpha_min, e)) {
-          const float al = fminf(rp.alpha_max, e.araw);
+        if (eval_splat(a, bb.x, bb.y, plx, ply1, rp.qmax_s, rp.log2_alpha_min, pe)) {
+          const float al = fminf(rp.alpha_max, pe.araw);
           const float test_T = __fmul_rn(T1, __fsub_rn(1.f, al));
           if (test_T < rp.t_eps) {
             done1 = true;
           } else {
-            const float4 c = s_c[j];
+            const float4 c = buf[j].c;
             const float w = al * T1;
             R1 = fmaf(w, c.x, R1);
             G1 = fmaf(w, c.y, G1);
             B1 = fmaf(w, c.z, B1);
             D1 = fmaf(w, bb.z, D1);
             T1 = test_T;
-            last1 = b + j + 1;
+            last1 = c0 + j + 1;
             if (COUNT) ++n_blend;
           }
         }
@@ -198,11 +190,16 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
   }
 }
 
+// float offset of gradient value k (mu 2, factor 3, opacity, z | rgb 3) in the
+// 12-float record {mu_x, mu_y, i0, k} {i1, opacity, z, -} {r, g, b, -}
+__device__ __forceinline__ int rec_off(int k) { return k < 7 ? k : k + 1; }
+
 // Sum the 10 values v[0..9] over the warp with exchanges that halve the number
 // of values each lane carries (xor 16: 10 -> 5, xor 8: 5 -> 3, xor 4: 3 -> 2,
-// xor 2: 2 -> 1) and a final xor-1 step (12 shuffles instead of 50).  The
-// even lane l then holds the total of value vidx(l) and adds it to dst.
-__device__ __forceinline__ void warp_transpose_add10(float (&v)[10], float* dst) {
+// xor 2: 2 -> 1) and a final xor-1 step (12 shuffles instead of 50), then add
+// the totals to the record: even lanes hold distinct values, so this is one
+// warp-wide scalar atomic add.
+__device__ __forceinline__ void warp_reduce_add10(float (&v)[10], float* __restrict__ rec) {
   const int lane = threadIdx.x & 31;
   const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
   float u[5];
@@ -239,22 +236,21 @@ __device__ __forceinline__ void warp_transpose_add10(float (&v)[10], float* dst)
   // xor 16; lanes with b2 and (b3 or b1) hold the zero pads
   const int i3 = (b3 ? 3 : 0) + (b2 ? 2 : 0) + (b1 ? 1 : 0);
   const bool valid = !(b2 && (b3 || b1));
-  if (!(lane & 1) && valid) atomicAdd(&dst[(b4 ? 5 : 0) + i3], x);
+  if (!(lane & 1) && valid) atomicAdd(&rec[rec_off((b4 ? 5 : 0) + i3)], x);
 }
 
 // Back-to-front step of one pixel for one Gaussian: updates the pixel's
 // running transmittance T and "colour behind" U and adds the Gaussian's
-// gradient record (mu 2, factor 3, opacity, z, rgb 3) to v.
-__device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, const float4* s_c, int j, float plx,
-                                          float ply, const RasterParams& rp, float& T, float& U, float dC0, float dC1,
-                                          float dC2, float dD, float dA_T, float (&v)[10]) {
+// gradient values (mu 2, factor 3, opacity, z, rgb 3) to v.
+__device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, const float4& c, float plx, float ply,
+                                          const RasterParams& rp, float& T, float& U, float dC0, float dC1, float dC2,
+                                          float dD, float dA_T, float (&v)[10]) {
   PixEval e;
   if (!eval_splat(a, bb.x, bb.y, plx, ply, rp.qmax_s, rp.log2_alpha_min, e)) return false;
   const float al = fminf(rp.alpha_max, e.araw);
   const float inv1m = __frcp_rn(1.f - al);
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
   const float w = al * Ti;
-  const float4 c = s_c[j];
   v[7] += w * dC0;
   v[8] += w * dC1;
   v[9] += w * dC2;
@@ -285,27 +281,24 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
     RasterParams rp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
     const float4* __restrict__ feat, const float* __restrict__ T_final, const int32_t* __restrict__ last_in,
     const float* __restrict__ dLdc, const float* __restrict__ dLdd, const float* __restrict__ dLda,
-    float4* __restrict__ g2d) {
+    float* __restrict__ g2d) {
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
-  __shared__ float4 s_a[kBatch];
-  __shared__ float4 s_b[kBatch];  // i1, log2o, z, 1/opacity
-  __shared__ float4 s_c[kBatch];
-  __shared__ uint32_t s_mask[kBatch];
-  __shared__ uint32_t s_id[kBatch];
-  __shared__ uint8_t s_list[kThreads / 32][kBatch];
-  __shared__ float s_acc[kBatch][12];
-  __shared__ int s_maxlast;
+  __shared__ Entry s_e[kThreads / 32][32];
+  __shared__ uint32_t s_id[kThreads / 32][32];
   const int tile = blockIdx.x;
   const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lx = (warp % WX) * 8 + (lane & 7), ly0 = (warp / WX) * 8 + (lane >> 3), ly1 = ly0 + 4;
+  const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
+  const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
   const int px = tx * TW + lx, py0 = ty * TH + ly0, py1 = ty * TH + ly1;
   const bool in0 = px < rp.width && py0 < rp.height, in1 = px < rp.width && py1 < rp.height;
   const float plx = (float)lx + 0.5f, ply0 = (float)ly0 + 0.5f, ply1 = (float)ly1 + 0.5f;
-  const float ox = (float)(tx * TW), oy = (float)(ty * TH);
+  const float ox = (float)(tx * TW), oy = (float)(ty * TH), bx = (float)bxi, by = (float)byi;
   const uint2 r = ranges[tile];
   const size_t HW = (size_t)rp.width * rp.height;
+  Entry* buf = s_e[warp];
+  uint32_t* bid = s_id[warp];
 
   // per-pixel state (two pixels per thread)
   float T0 = 1.f, c00 = 0.f, c01 = 0.f, c02 = 0.f, d0 = 0.f, a0 = 0.f;
@@ -339,64 +332,56 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   int wmax = max(last0, last1);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, off));
-  if (threadIdx.x == 0) s_maxlast = 0;
-  __syncthreads();
-  if (lane == 0 && wmax > 0) atomicMax(&s_maxlast, wmax);
-  __syncthreads();
-  const int max_last = s_maxlast;
+  if (wmax == 0) return;
 
-  for (int hi = max_last; hi > 0; hi -= kBatch) {
-    const int lo = max(0, hi - kBatch);
-    const int cnt = hi - lo;
-    __syncthreads();
-#pragma unroll
-    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
-      if (s < cnt) {
-        const uint32_t g = ids[r.x + lo + s];
-        s_id[s] = g;
-        stage_entry<WX>(feat, g, ox, oy, rp, s_a[s], s_b[s], s_c[s], s_mask[s]);
-      }
+  // walk the list back to front in chunks of 32, the next chunk's records in flight
+  int c0 = ((wmax - 1) >> 5) << 5;
+  float4 f0, f1, f2;
+  uint32_t g = 0;
+  if (c0 + lane < wmax) {
+    g = ids[r.x + c0 + lane];
+    load_entry(feat, g, f0, f1, f2);
+  }
+  for (; c0 >= 0; c0 -= 32) {
+    const bool have = c0 + lane < wmax;
+    const float4 h0 = f0, h1 = f1, h2 = f2;
+    const uint32_t hg = g;
+    if (c0 >= 32) {
+      g = ids[r.x + c0 - 32 + lane];
+      load_entry(feat, g, f0, f1, f2);
     }
-    for (int k = threadIdx.x; k < kBatch * 12; k += kThreads) (&s_acc[0][0])[k] = 0.f;
-    __syncthreads();
-    const int count = build_list(s_mask, cnt, warp, s_list[warp]);
-    for (int q = count - 1; q >= 0; --q) {
-      const int j = s_list[warp][q];
-      const int idx = lo + j;
-      if (idx >= wmax) continue;  // behind every pixel's last contributor in this warp
-      const float4 a = s_a[j];
-      const float4 bb = s_b[j];
+    Entry e;
+    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e);
+    __syncwarp();
+    if (hit) {
+      buf[lane] = e;
+      bid[lane] = hg;
+    }
+    unsigned bal = __ballot_sync(kFull, hit);
+    __syncwarp();
+    while (bal) {
+      const int j = 31 - __clz(bal);
+      bal &= ~(1u << j);
+      const int idx = c0 + j;
+      const float4 a = buf[j].a;
+      const float4 bb = buf[j].b;
+      const float4 cc = buf[j].c;
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       bool contrib = false;
-      if (idx < last0) contrib |= bwd_pixel(a, bb, s_c, j, plx, ply0, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
-      if (idx < last1) contrib |= bwd_pixel(a, bb, s_c, j, plx, ply1, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+      if (idx < last0) contrib |= bwd_pixel(a, bb, cc, plx, ply0, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+      if (idx < last1) contrib |= bwd_pixel(a, bb, cc, plx, ply1, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;
+      float* rec = g2d + 12 * (size_t)bid[j];
       if (__popc(m) <= 2) {
         if (contrib) {
 #pragma unroll
-          for (int k = 0; k < 10; ++k) atomicAdd(&s_acc[j][k], v[k]);
+          for (int k = 0; k < 10; ++k) atomicAdd(&rec[rec_off(k)], v[k]);
         }
       } else {
-        warp_transpose_add10(v, s_acc[j]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = threadIdx.x; s < kBatch; s += kThreads) {
-      if (s < cnt) {
-        const float* acc = s_acc[s];
-        bool nz = false;
-#pragma unroll
-        for (int k = 0; k < 10; ++k) nz |= acc[k] != 0.f;
-        if (nz) {
-          float4* dst = g2d + 3 * (size_t)s_id[s];
-          atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
-          atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
-          atomicAdd(dst + 2, make_float4(acc[7], acc[8], acc[9], 0.f));
-        }
+        warp_reduce_add10(v, rec);
       }
     }
   }
@@ -451,13 +436,13 @@ void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t*
   RasterParams rp = make_params(a);
   if (a.tile_w == 16)
     raster_bwd_kernel<16, 16><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                      dL_ddepth, dL_dalpha, g2d);
+                                                      dL_ddepth, dL_dalpha, (float*)g2d);
   else if (a.tile_w == 8)
     raster_bwd_kernel<8, 32><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                     dL_ddepth, dL_dalpha, g2d);
+                                                     dL_ddepth, dL_dalpha, (float*)g2d);
   else
     raster_bwd_kernel<32, 8><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                     dL_ddepth, dL_dalpha, g2d);
+                                                     dL_ddepth, dL_dalpha, (float*)g2d);
 }
 
 }  // namespace gs

@@ -259,6 +259,18 @@ __global__ void export_keys_kernel(const uint32_t* __restrict__ tiles, const uin
   }
 }
 
+// one block per tile writes the keys of its range
+__global__ void export_keys_ranges_kernel(const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
+                                          const uint32_t* __restrict__ depth_key, uint64_t* __restrict__ keys,
+                                          uint32_t* __restrict__ ids_out) {
+  const uint2 r = ranges[blockIdx.x];
+  for (uint32_t i = r.x + threadIdx.x; i < r.y; i += blockDim.x) {
+    const uint32_t g = ids[i];
+    keys[i] = ((uint64_t)blockIdx.x << 32) | (uint64_t)depth_key[g];
+    ids_out[i] = g;
+  }
+}
+
 int sort_blocks(uint32_t n, int num_sms, int max_blocks) {
   // about four rounds of 256 items per block; at most four blocks per SM
   int g = (int)std::min<uint64_t>(((uint64_t)n + 1023) / 1024, (uint64_t)std::max(1, 4 * num_sms));
@@ -320,6 +332,13 @@ void launch_tile_ranges(const uint32_t* sorted_tiles, const uint32_t* n_dev, uin
   int g = (int)std::min<uint64_t>(((uint64_t)n_max + 255) / 256, (uint64_t)(8 * num_sms));
   tile_ranges_kernel<<<std::max(g, 1), 256, 0, s>>>(sorted_tiles, n_dev, n_max, ranges);
   if (launches) *launches += 1;
+}
+
+void launch_export_keys_ranges(const uint2* ranges, int n_tiles, const uint32_t* sorted_ids,
+                               const uint32_t* depth_key_by_id, uint32_t P, uint64_t* keys, uint32_t* ids,
+                               cudaStream_t s) {
+  if (P == 0 || n_tiles == 0) return;
+  export_keys_ranges_kernel<<<n_tiles, 128, 0, s>>>(ranges, sorted_ids, depth_key_by_id, keys, ids);
 }
 
 void launch_export_keys(const uint32_t* sorted_tiles, const uint32_t* sorted_ids, const uint32_t* depth_key_by_id,

@@ -1,0 +1,263 @@
+// Tile binning by counting scatter and per-tile sort (Sec. III-B.3: screen
+// tiles, Gaussians sorted by depth in each tile):
+//   1. count:   every (Gaussian, tile) pair of a Gaussian's tile rectangle adds
+//               one to its tile's counter,
+//   2. scan:    exclusive scan of the tile counters -> list offsets (and the
+//               total pair count and the longest list),
+//   3. scatter: every pair takes a slot of its tile's list with an atomic
+//               cursor and writes its Gaussian id,
+//   4. sort:    one CTA per tile sorts its list in shared memory by the 64-bit
+//               key (float32 depth bits << 32 | id), a bitonic network.
+// The per-tile keys are unique, so the result is exactly the (tile, depth, id)
+// order of a stable sort and does not depend on the scatter's atomic order.
+// Counting and scattering expand the rectangles warp-cooperatively, so a
+// Gaussian covering thousands of tiles is spread over the whole warp.
+#include "common.cuh"
+#include "internal.h"
+
+namespace gs {
+
+namespace {
+
+constexpr int kBinThreads = 256;
+constexpr int kBinWarps = kBinThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kSortThreads = 256;
+
+// Calls f(gaussian, tile, active) for every tile of every Gaussian's
+// rectangle.  A block expands 256 consecutive Gaussians at a time: a block
+// scan of their tile counts gives each Gaussian's first pair, and the block's
+// threads take consecutive pairs (owner found by binary search over the
+// prefix in shared memory), so one large splat is spread over the whole block
+// and large splats clustered in one region are averaged over 256 Gaussians.
+// `active` is the mask of lanes of the calling warp that call f together.
+template <class F>
+__device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__ rects,
+                                              const uint32_t* __restrict__ tiles, int tiles_x, F f) {
+  __shared__ uint32_t s_excl[kBinThreads];
+  __shared__ ushort4 s_rect[kBinThreads];
+  __shared__ uint32_t s_wsum[kBinWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = blockIdx.x * kBinThreads; base < n; base += gridDim.x * kBinThreads) {
+    const int g = base + threadIdx.x;
+    const uint32_t cnt = g < n ? tiles[g] : 0u;
+    const ushort4 r = g < n ? rects[g] : make_ushort4(0, 0, 0, 0);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    __syncthreads();  // previous round done with the shared arrays
+    if (lane == 31) s_wsum[w] = incl;
+    __syncthreads();
+    uint32_t wpre = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kBinWarps; ++k) {
+      const uint32_t sk = s_wsum[k];
+      wpre += k < w ? sk : 0u;
+      total += sk;
+    }
+    s_excl[threadIdx.x] = wpre + incl - cnt;
+    s_rect[threadIdx.x] = r;
+    __syncthreads();
+    for (uint32_t k0 = 0; k0 < total; k0 += kBinThreads) {
+      const uint32_t k = k0 + threadIdx.x;
+      const unsigned active = __ballot_sync(0xFFFFFFFFu, k < total);
+      if (k >= total) break;
+      int o = 0;
+#pragma unroll
+      for (int step = kBinThreads / 2; step > 0; step >>= 1)
+        if (s_excl[o + step] <= k) o += step;
+      const ushort4 ro = s_rect[o];
+      const uint32_t local = k - s_excl[o];
+      const uint32_t width = (uint32_t)(ro.z - ro.x);
+      const uint32_t ty = ro.y + local / width, tx = ro.x + local % width;
+      f(base + o, ty * (uint32_t)tiles_x + tx, active);
+    }
+  }
+}
+
+// Warp-aggregated atomic add of 1 per active lane to counter[t]: lanes with the
+// same t are grouped, the group leader adds the group size once, and each
+// lane gets old value + its rank in the group (neighbouring Gaussians tend to
+// share tiles, so plain per-lane atomics would serialise on one address).
+__device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter, uint32_t t, unsigned active) {
+  const unsigned peers = __match_any_sync(active, t);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&counter[t], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+__global__ void __launch_bounds__(kBinThreads) tile_count_kernel(int n, const ushort4* __restrict__ rects,
+                                                                 const uint32_t* __restrict__ tiles, int tiles_x,
+                                                                 uint32_t* __restrict__ counts) {
+  for_each_pair(n, rects, tiles, tiles_x, [&](int, uint32_t t, unsigned active) { warp_agg_inc(counts, t, active); });
+}
+
+// offsets = exclusive scan of counts (clamped to 32 bits), cursors = offsets;
+// stats[0] = total pairs, stats[1] = longest list; n_pairs = min(total, capacity)
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const uint32_t* __restrict__ counts,
+                                                                 uint32_t* __restrict__ offsets,
+                                                                 uint32_t* __restrict__ cursors, uint32_t capacity,
+                                                                 uint32_t* __restrict__ n_pairs,
+                                                                 unsigned long long* __restrict__ stats) {
+  __shared__ unsigned long long s[kScanThreads];
+  __shared__ uint32_t s_max[32];
+  const int per = (T + kScanThreads - 1) / kScanThreads;
+  const int beg = min(T, (int)threadIdx.x * per), end = min(T, beg + per);
+  unsigned long long sum = 0;
+  uint32_t mx = 0;
+  for (int i = beg; i < end; ++i) {
+    const uint32_t c = counts[i];
+    sum += c;
+    mx = max(mx, c);
+  }
+  s[threadIdx.x] = sum;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    const unsigned long long v = threadIdx.x >= (unsigned)off ? s[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    s[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = s[threadIdx.x] - sum;
+  for (int i = beg; i < end; ++i) {
+    const uint32_t o = (uint32_t)(run < 0xFFFFFFFFull ? run : 0xFFFFFFFFull);
+    offsets[i] = o;
+    cursors[i] = o;
+    run += counts[i];
+  }
+  if (threadIdx.x == 0) {
+    uint32_t m = 0;
+    for (int k = 0; k < kScanThreads / 32; ++k) m = max(m, s_max[k]);
+    const unsigned long long tot = s[kScanThreads - 1];
+    stats[0] = tot;
+    stats[1] = m;
+    *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
+  }
+}
+
+__global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(int n, const ushort4* __restrict__ rects,
+                                                                   const uint32_t* __restrict__ tiles, int tiles_x,
+                                                                   uint32_t* __restrict__ cursors,
+                                                                   uint32_t* __restrict__ ids, uint32_t capacity,
+                                                                   uint32_t* __restrict__ overflow) {
+  bool over = false;
+  for_each_pair(n, rects, tiles, tiles_x, [&](int g, uint32_t t, unsigned active) {
+    const uint32_t pos = warp_agg_inc(cursors, t, active);
+    if (pos < capacity)
+      ids[pos] = (uint32_t)g;
+    else
+      over = true;
+  });
+  if (over) atomicOr(overflow, 1u);
+}
+
+// One CTA per tile: bitonic sort of (depth bits << 32 | id) in shared memory.
+template <int CAP>
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t* __restrict__ offsets,
+                                                                 const uint32_t* __restrict__ counts,
+                                                                 uint32_t* __restrict__ ids,
+                                                                 const uint32_t* __restrict__ zkey,
+                                                                 uint2* __restrict__ ranges, uint32_t capacity,
+                                                                 uint32_t* __restrict__ overflow) {
+  __shared__ unsigned long long s[CAP];
+  const int t = blockIdx.x;
+  const uint32_t off = offsets[t], n = counts[t];
+  const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
+  if (threadIdx.x == 0) ranges[t] = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
+  if (n <= 1 || !fits) return;
+  if (n > (uint32_t)CAP) {
+    if (threadIdx.x == 0) {
+      atomicOr(overflow, 2u);
+      ranges[t] = make_uint2(0u, 0u);
+    }
+    return;
+  }
+  if (n <= 256) {
+    // short list: rank of each key = number of smaller keys (keys are unique)
+    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
+      const uint32_t g = ids[off + i];
+      s[i] = ((unsigned long long)zkey[g] << 32) | g;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
+      const unsigned long long key = s[i];
+      uint32_t rank = 0;
+      for (uint32_t j = 0; j < n; ++j) rank += s[j] < key ? 1u : 0u;
+      ids[off + rank] = (uint32_t)key;
+    }
+    return;
+  }
+  uint32_t m = 2;
+  while (m < n) m <<= 1;
+  for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
+    unsigned long long key = ~0ull;
+    if (i < n) {
+      const uint32_t g = ids[off + i];
+      key = ((unsigned long long)zkey[g] << 32) | g;
+    }
+    s[i] = key;
+  }
+  __syncthreads();
+  for (uint32_t k = 2; k <= m; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = s[i], b = s[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) ids[off + i] = (uint32_t)s[i];
+}
+
+int bin_grid(int n, int num_sms) {
+  const int blocks = (n + kBinThreads - 1) / kBinThreads;
+  return max(1, min(blocks, 16 * max(num_sms, 1)));
+}
+
+}  // namespace
+
+int tile_sort_capacity() { return kTileSortCap; }
+
+void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
+  cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
+  if (a.n > 0) {
+    tile_count_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a.n, a.rects, a.tiles, a.tiles_x, a.counts);
+    if (launches) *launches += 1;
+  }
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
+                                              a.stats);
+  if (launches) *launches += 1;
+}
+
+void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
+  if (a.n > 0) {
+    tile_scatter_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a.n, a.rects, a.tiles, a.tiles_x,
+                                                                          a.cursors, a.ids, a.capacity, a.overflow);
+    if (launches) *launches += 1;
+  }
+}
+
+void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
+  tile_sort_kernel<kTileSortCap><<<a.n_tiles, kSortThreads, 0, s>>>(a.offsets, a.counts, a.ids, a.zkey, a.ranges,
+                                                                    a.capacity, a.overflow);
+  if (launches) *launches += 1;
+}
+
+}  // namespace gs

@@ -152,6 +152,55 @@ class Trainer:
             abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
         return self.loss
 
+    def _step_device_counter(self, target_rgb, target_depth, stream=None):
+        # one iteration whose every argument is fixed: the Adam step comes from
+        # the context's device counter (step = 0), so it can be graph-captured
+        h = self.ctx.handle
+        m = self.model
+        self.forward(stream)
+        abi.gs_loss_l1(h, self.cam, self.color, self.depth, target_rgb, target_depth, self.w_color, self.w_depth,
+                       self.loss, self.dLdc, self.dLdd, stream)
+        abi.gs_render_bwd_adam(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, m.flat, m.m,
+                               m.v, self.acfg, 0, None, stream)
+
+    def capture(self, target_rgb: torch.Tensor, target_depth: torch.Tensor, pair_headroom: float = 1.5):
+        """Record one iteration into a CUDA graph (``replay`` runs it).
+
+        Switches the context to no-sync mode with the pair buffers reserved at
+        ``pair_headroom`` times the current pair count; the graph reads the
+        targets from ``target_rgb`` / ``target_depth`` (copy new frames into
+        them).  Runs one eager no-sync iteration first (a real step)."""
+        assert self.fused, "graph capture uses the fused backward + Adam"
+        h = self.ctx.handle
+        self.forward()
+        torch.cuda.synchronize()
+        pairs = abi.gs_get_stats(h)["n_pairs"]
+        H, W = self.cam.height, self.cam.width
+        abi.gs_ctx_reserve(h, self.model.n, H * W, int(pairs * pair_headroom) + 4096)
+        abi.gs_ctx_set_sync(h, False)
+        abi.gs_ctx_set_adam_step(h, self.step_count)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._step_device_counter(target_rgb, target_depth)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.step_count += 1
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._step_device_counter(target_rgb, target_depth)
+        return self.graph
+
+    def replay(self):
+        """One captured iteration; the loss stays on the device in ``self.loss``."""
+        self.graph.replay()
+        self.step_count += 1
+        return self.loss
+
+    def check_capacity(self):
+        """Raises GsError(GS_ERR_CAPACITY) if a no-sync pass dropped pairs."""
+        abi.gs_sync_status(self.ctx.handle)
+
 
 class _Render(torch.autograd.Function):
     @staticmethod

@@ -75,3 +75,19 @@ def test_edge_cases(ctx):
     np.testing.assert_array_equal(k1, rk)
     np.testing.assert_array_equal(i1, ri)
     np.testing.assert_array_equal(r1, rr)
+
+
+def test_long_tile_lists_take_the_radix_fallback(ctx):
+    """Tile lists longer than the per-tile shared-memory sort holds (4096)
+    switch the whole frame to the radix-sort binning; still bit-exact."""
+    rng = np.random.default_rng(77)
+    n = 6000
+    m = np.stack([rng.uniform(0, 64, n), rng.uniform(0, 48, n)], 1).astype(np.float32)
+    e = np.full((n, 2), 200.0, np.float32)  # every Gaussian covers all 12 tiles
+    z = (rng.integers(1, 50, n) * 0.1).astype(np.float32)
+    keys, ids, ranges = _run(ctx, m, e, z, 64, 48, 16, 16)
+    rk, ri, rr = binning.bin_tiles(m, e, z, 64, 48, 16, 16)
+    assert (rr[:, 1] - rr[:, 0]).max() > 4096
+    np.testing.assert_array_equal(keys, rk)
+    np.testing.assert_array_equal(ids, ri)
+    np.testing.assert_array_equal(ranges, rr)
