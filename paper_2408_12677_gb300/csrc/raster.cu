@@ -28,6 +28,17 @@ struct Entry {
   float4 a, b, c;
 };
 
+// Asynchronous copy of one 48 B record into shared memory (3 x 16 B cp.async).
+__device__ __forceinline__ void cp_record(float4* dst, const float4* __restrict__ feat, uint32_t g) {
+  const float4* src = feat + 3 * (size_t)g;
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 16u * k), "l"(src + k) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 __device__ __forceinline__ void load_entry(const float4* __restrict__ feat, uint32_t g, float4& f0, float4& f1,
                                            float4& f2) {
   const float4* fg = feat + 3 * (size_t)g;
@@ -277,7 +288,7 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
+__global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(
     RasterParams rp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
     const float4* __restrict__ feat, const float* __restrict__ T_final, const int32_t* __restrict__ last_in,
     const float* __restrict__ dLdc, const float* __restrict__ dLdd, const float* __restrict__ dLda,
@@ -286,6 +297,8 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
   __shared__ uint32_t s_id[kThreads / 32][32];
+  __shared__ __align__(16) float4 s_raw[kThreads / 32][2][32][3];
+  __shared__ uint32_t s_gid[kThreads / 32][2][32];
   const int tile = blockIdx.x;
   const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -334,28 +347,33 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
   for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, off));
   if (wmax == 0) return;
 
-  // walk the list back to front in chunks of 32, the next chunk's records in flight
+  // walk the list back to front in chunks of 32: chunk c in shared memory,
+  // chunk c - 32 in flight (cp.async), the ids of chunk c - 64 in a register
   int c0 = ((wmax - 1) >> 5) << 5;
-  float4 f0, f1, f2;
-  uint32_t g = 0;
+  int cur = 0;
   if (c0 + lane < wmax) {
-    g = ids[r.x + c0 + lane];
-    load_entry(feat, g, f0, f1, f2);
+    const uint32_t g = ids[r.x + c0 + lane];
+    s_gid[warp][0][lane] = g;
+    cp_record(s_raw[warp][0][lane], feat, g);
   }
-  for (; c0 >= 0; c0 -= 32) {
-    const bool have = c0 + lane < wmax;
-    const float4 h0 = f0, h1 = f1, h2 = f2;
-    const uint32_t hg = g;
+  cp_commit();
+  uint32_t g2 = c0 >= 32 ? ids[r.x + c0 - 32 + lane] : 0u;
+  for (; c0 >= 0; c0 -= 32, cur ^= 1) {
     if (c0 >= 32) {
-      g = ids[r.x + c0 - 32 + lane];
-      load_entry(feat, g, f0, f1, f2);
+      s_gid[warp][cur ^ 1][lane] = g2;
+      cp_record(s_raw[warp][cur ^ 1][lane], feat, g2);
     }
+    cp_commit();
+    if (c0 >= 64) g2 = ids[r.x + c0 - 64 + lane];
+    cp_wait_prev();
+    const bool have = c0 + lane < wmax;
     Entry e;
-    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e);
+    const float4* raw = s_raw[warp][cur][lane];
+    const bool hit = have && make_entry(raw[0], raw[1], raw[2], ox, oy, bx, by, rp, e);
     __syncwarp();
     if (hit) {
       buf[lane] = e;
-      bid[lane] = hg;
+      bid[lane] = s_gid[warp][cur][lane];
     }
     unsigned bal = __ballot_sync(kFull, hit);
     __syncwarp();
@@ -385,6 +403,7 @@ __global__ void __launch_bounds__(kThreads) raster_bwd_kernel(
       }
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 RasterParams make_params(const RasterArgs& a) {
