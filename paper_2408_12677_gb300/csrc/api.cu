@@ -45,6 +45,8 @@ struct gs_ctx {
   uint32_t* tcount = nullptr;   // per-tile pair counts
   uint32_t* toffset = nullptr;  // per-tile list offsets
   uint32_t* tcursor = nullptr;  // per-tile scatter cursors
+  uint32_t* bigq = nullptr;     // ids of Gaussians covering more than kBigTiles tiles
+  uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue
   unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
   long long* d_step = nullptr;               // device Adam step counter (step = 0 calls)
   int64_t cap_px = 0;
@@ -144,6 +146,7 @@ gs_status ensure_n(gs_ctx* c, int64_t n) {
   }
   GS_CUDA(c, regrow(&c->tiles, cap));
   GS_CUDA(c, regrow(&c->rects, cap));
+  GS_CUDA(c, regrow(&c->bigq, cap));
   GS_CUDA(c, regrow(&c->g2d, 3 * cap));
   GS_CUDA(c, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
   GS_CUDA(c, regrow(&c->pose_partials, 6 * ((int64_t)project_bwd_blocks((int)cap) + 1)));
@@ -362,6 +365,8 @@ gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t 
   tb.n_pairs = c->d_npairs;
   tb.stats = c->d_binstats;
   tb.overflow = c->d_overflow;
+  tb.big_queue = c->bigq;
+  tb.big_len = c->d_bigmeta;
   {
     StageTimer t(c, GS_STAGE_DUPLICATE, s);
     launch_tile_count_scan(tb, s, &c->launches);
@@ -441,6 +446,7 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_overflow, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bigmeta, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
   if (e == cudaSuccess) init_project_kernels();
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_evals, 2 * sizeof(unsigned long long));
@@ -481,6 +487,8 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->tcount);
   cudaFree(c->toffset);
   cudaFree(c->tcursor);
+  cudaFree(c->bigq);
+  cudaFree(c->d_bigmeta);
   cudaFree(c->d_binstats);
   cudaFree(c->d_step);
   cudaFree(c->T_final);
@@ -640,6 +648,9 @@ gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
   pa.tile_h = cfg->tile_h;
   pa.tiles_x = tiles_x;
   pa.tiles_y = tiles_y;
+  pa.big_queue = c->bigq;
+  pa.big_len = c->d_bigmeta;
+  GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
   {
     StageTimer t(c, GS_STAGE_PROJECT_FWD, s);
     launch_project_fwd(pa, c->feat, c->zkey, c->tiles, c->rects, s);
@@ -727,6 +738,8 @@ gs_status raster_backward(gs_ctx* c, const gs_camera* cam, const gs_raster_cfg* 
 ProjectArgs project_args(const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
                          const gs_raster_cfg* cfg, int tiles_x, int tiles_y) {
   ProjectArgs pa;
+  pa.big_queue = nullptr;
+  pa.big_len = nullptr;
   pa.n = (int)g->n;
   pa.means = g->means;
   pa.log_scales = g->log_scales;
@@ -913,8 +926,9 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
     return st;
   }
   c->have_state = false;
+  GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
   launch_bin_prepare((int)n, mean2d, extent, depth, tile_w, tile_h, tiles_x, tiles_y, c->zkey, c->tiles, c->rects,
-                     s);
+                     c->bigq, c->d_bigmeta, s);
   if (n > 0) c->launches += 1;
   st = bin_and_sort(c, (int)n, tiles_x, tiles_y, s);
   c->sync = was_sync;

@@ -13,7 +13,15 @@ struct CamView {
   float C[3];  // camera centre in the world frame, -R^T t
 };
 
+// Gaussians covering more than this many tiles are queued and expanded by
+// whole warps spread over the grid in the binning kernels instead of by the
+// block that owns them (large splats cluster, which would leave a few blocks
+// running long).
+constexpr uint32_t kBigTiles = 32;
+
 struct ProjectArgs {
+  uint32_t* big_queue;  // ids of Gaussians with more than kBigTiles tiles
+  uint32_t* big_len;    // queue length (zeroed before the launch)
   int n;
   const float *means, *log_scales, *quats, *logits, *sh;
   int sh_degree;
@@ -28,7 +36,7 @@ void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key,
 // binning-only front end: rects/keys from given mean2d / extent / depth
 void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
                         int tiles_x, int tiles_y, uint32_t* depth_key, uint32_t* tiles_touched, ushort4* rects,
-                        cudaStream_t s);
+                        uint32_t* big_queue, uint32_t* big_len, cudaStream_t s);
 // g2d [n, 12] -> parameter gradients (+=) and per-block pose partials
 int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales,
                        float* g_quats, float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s);
@@ -103,6 +111,8 @@ struct TileBinArgs {
   uint32_t* n_pairs;          // device: min(total, capacity)
   unsigned long long* stats;  // device: [0] total pairs, [1] longest list
   uint32_t* overflow;         // device flag: 1 = pairs over capacity, 2 = list over kTileSortCap
+  const uint32_t* big_queue;  // Gaussians with more than kBigTiles tiles
+  const uint32_t* big_len;
 };
 int tile_sort_capacity();
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches);

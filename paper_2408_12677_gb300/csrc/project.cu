@@ -148,9 +148,11 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(ProjectArgs a,
     tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x, a.tiles_y, x0, y0,
               x1, y1);
   }
-  tiles_touched[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  tiles_touched[i] = nt;
   rects[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
   depth_key[i] = __float_as_uint(z);
+  if (nt > kBigTiles) a.big_queue[atomicAdd(a.big_len, 1u)] = (uint32_t)i;
 
   // view-dependent colour
   float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
@@ -173,15 +175,18 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(ProjectArgs a,
 __global__ void bin_prepare_kernel(int n, const float* __restrict__ mean2d, const float* __restrict__ extent,
                                    const float* __restrict__ depth, float inv_tw, float inv_th, int tiles_x,
                                    int tiles_y, uint32_t* __restrict__ depth_key, uint32_t* __restrict__ tiles,
-                                   ushort4* __restrict__ rects) {
+                                   ushort4* __restrict__ rects, uint32_t* __restrict__ big_queue,
+                                   uint32_t* __restrict__ big_len) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int x0, y0, x1, y1;
   tile_rect(mean2d[2 * i], mean2d[2 * i + 1], extent[2 * i], extent[2 * i + 1], inv_tw, inv_th, tiles_x, tiles_y,
             x0, y0, x1, y1);
-  tiles[i] = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+  tiles[i] = nt;
   rects[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
   depth_key[i] = __float_as_uint(depth[i]);
+  if (nt > kBigTiles) big_queue[atomicAdd(big_len, 1u)] = (uint32_t)i;
 }
 
 constexpr int kBwdThreads = 128;
@@ -606,11 +611,11 @@ void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key,
 
 void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
                         int tiles_x, int tiles_y, uint32_t* depth_key, uint32_t* tiles_touched, ushort4* rects,
-                        cudaStream_t s) {
+                        uint32_t* big_queue, uint32_t* big_len, cudaStream_t s) {
   if (n <= 0) return;
   bin_prepare_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, mean2d, extent, depth, 1.f / (float)tile_w,
                                                      1.f / (float)tile_h, tiles_x, tiles_y, depth_key,
-                                                     tiles_touched, rects);
+                                                     tiles_touched, rects, big_queue, big_len);
 }
 
 int project_bwd_blocks(int n) { return n > 0 ? (n + kBwdThreads - 1) / kBwdThreads : 0; }

@@ -25,7 +25,9 @@ constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 256;
 
 // Calls f(gaussian, tile, active) for every tile of every Gaussian's
-// rectangle.  A block expands 256 consecutive Gaussians at a time: a block
+// rectangle.  Gaussians with more than kBigTiles tiles come from the queue
+// the projection built (see the end); the others are expanded by their
+// block, 256 consecutive Gaussians at a time: a block
 // scan of their tile counts gives each Gaussian's first pair, and the block's
 // threads take consecutive pairs (owner found by binary search over the
 // prefix in shared memory), so one large splat is spread over the whole block
@@ -33,14 +35,17 @@ constexpr int kSortThreads = 256;
 // `active` is the mask of lanes of the calling warp that call f together.
 template <class F>
 __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__ rects,
-                                              const uint32_t* __restrict__ tiles, int tiles_x, F f) {
+                                              const uint32_t* __restrict__ tiles, int tiles_x,
+                                              const uint32_t* __restrict__ big_queue,
+                                              const uint32_t* __restrict__ big_len, F f) {
   __shared__ uint32_t s_excl[kBinThreads];
   __shared__ ushort4 s_rect[kBinThreads];
   __shared__ uint32_t s_wsum[kBinWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int base = blockIdx.x * kBinThreads; base < n; base += gridDim.x * kBinThreads) {
     const int g = base + threadIdx.x;
-    const uint32_t cnt = g < n ? tiles[g] : 0u;
+    uint32_t cnt = g < n ? tiles[g] : 0u;
+    if (cnt > kBigTiles) cnt = 0;  // expanded from the queue below
     const ushort4 r = g < n ? rects[g] : make_ushort4(0, 0, 0, 0);
     uint32_t incl = cnt;
 #pragma unroll
@@ -76,6 +81,25 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
       f(base + o, ty * (uint32_t)tiles_x + tx, active);
     }
   }
+  // large splats: warp w of the grid expands queued Gaussians w, w + W, ...
+  // spreading each one's tiles over its lanes (no shared cursor: one address
+  // hit by every warp would serialise)
+  const uint32_t nbig = *big_len;
+  const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t item = gwarp; item < nbig; item += nwarps) {
+    const uint32_t g = big_queue[item];
+    const ushort4 ro = rects[g];
+    const uint32_t cnt = tiles[g];
+    const uint32_t width = (uint32_t)(ro.z - ro.x);
+    for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const unsigned active = __ballot_sync(0xFFFFFFFFu, k < cnt);
+      if (k >= cnt) break;
+      const uint32_t ty = ro.y + k / width, tx = ro.x + k % width;
+      f((int)g, ty * (uint32_t)tiles_x + tx, active);
+    }
+  }
 }
 
 // Warp-aggregated atomic add of 1 per active lane to counter[t]: lanes with the
@@ -92,10 +116,9 @@ __device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter,
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void __launch_bounds__(kBinThreads) tile_count_kernel(int n, const ushort4* __restrict__ rects,
-                                                                 const uint32_t* __restrict__ tiles, int tiles_x,
-                                                                 uint32_t* __restrict__ counts) {
-  for_each_pair(n, rects, tiles, tiles_x, [&](int, uint32_t t, unsigned active) { warp_agg_inc(counts, t, active); });
+__global__ void __launch_bounds__(kBinThreads) tile_count_kernel(TileBinArgs a) {
+  for_each_pair(a.n, a.rects, a.tiles, a.tiles_x, a.big_queue, a.big_len,
+                [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
 }
 
 // offsets = exclusive scan of counts (clamped to 32 bits), cursors = offsets;
@@ -144,20 +167,17 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
   }
 }
 
-__global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(int n, const ushort4* __restrict__ rects,
-                                                                   const uint32_t* __restrict__ tiles, int tiles_x,
-                                                                   uint32_t* __restrict__ cursors,
-                                                                   uint32_t* __restrict__ ids, uint32_t capacity,
-                                                                   uint32_t* __restrict__ overflow) {
+__global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(TileBinArgs a) {
   bool over = false;
-  for_each_pair(n, rects, tiles, tiles_x, [&](int g, uint32_t t, unsigned active) {
-    const uint32_t pos = warp_agg_inc(cursors, t, active);
-    if (pos < capacity)
-      ids[pos] = (uint32_t)g;
-    else
-      over = true;
-  });
-  if (over) atomicOr(overflow, 1u);
+  for_each_pair(a.n, a.rects, a.tiles, a.tiles_x, a.big_queue, a.big_len,
+                [&](int g, uint32_t t, unsigned active) {
+                  const uint32_t pos = warp_agg_inc(a.cursors, t, active);
+                  if (pos < a.capacity)
+                    a.ids[pos] = (uint32_t)g;
+                  else
+                    over = true;
+                });
+  if (over) atomicOr(a.overflow, 1u);
 }
 
 // One CTA per tile: bitonic sort of (depth bits << 32 | id) in shared memory.
@@ -181,19 +201,61 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
     }
     return;
   }
-  if (n <= 256) {
-    // short list: rank of each key = number of smaller keys (keys are unique)
-    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
-      const uint32_t g = ids[off + i];
-      s[i] = ((unsigned long long)zkey[g] << 32) | g;
+  if (n <= 2 * kSortThreads) {
+    // bitonic network in registers: thread t holds keys 2t and 2t + 1;
+    // partners within a warp are exchanged by shuffles, across warps through
+    // shared memory
+    uint32_t m = 2;
+    while (m < n) m <<= 1;
+    const uint32_t e0 = 2 * threadIdx.x;
+    unsigned long long x0 = ~0ull, x1 = ~0ull;
+    if (e0 < n) {
+      const uint32_t g = ids[off + e0];
+      x0 = ((unsigned long long)zkey[g] << 32) | g;
     }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) {
-      const unsigned long long key = s[i];
-      uint32_t rank = 0;
-      for (uint32_t j = 0; j < n; ++j) rank += s[j] < key ? 1u : 0u;
-      ids[off + rank] = (uint32_t)key;
+    if (e0 + 1 < n) {
+      const uint32_t g = ids[off + e0 + 1];
+      x1 = ((unsigned long long)zkey[g] << 32) | g;
     }
+    const bool live = e0 < m;  // threads beyond m only keep padding
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        if (j == 1) {
+          const bool up = (e0 & k) == 0;
+          if ((x0 > x1) == up) {
+            const unsigned long long tmp = x0;
+            x0 = x1;
+            x1 = tmp;
+          }
+        } else if (j <= 32) {
+          const int d = (int)(j >> 1);  // partner lane distance
+          const unsigned long long y0 = __shfl_xor_sync(0xFFFFFFFFu, x0, d);
+          const unsigned long long y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, d);
+          const bool lower = (e0 & j) == 0;   // this element is the lower index of the pair
+          const bool up = (e0 & k) == 0;      // ascending block
+          const bool keep_min = lower == up;
+          x0 = keep_min ? (x0 < y0 ? x0 : y0) : (x0 > y0 ? x0 : y0);
+          x1 = keep_min ? (x1 < y1 ? x1 : y1) : (x1 > y1 ? x1 : y1);
+        } else {
+          __syncthreads();
+          if (live) {
+            s[e0] = x0;
+            s[e0 + 1] = x1;
+          }
+          __syncthreads();
+          if (live) {
+            const unsigned long long y0 = s[e0 ^ j], y1 = s[(e0 + 1) ^ j];
+            const bool lower = (e0 & j) == 0;
+            const bool up = (e0 & k) == 0;
+            const bool keep_min = lower == up;
+            x0 = keep_min ? (x0 < y0 ? x0 : y0) : (x0 > y0 ? x0 : y0);
+            x1 = keep_min ? (x1 < y1 ? x1 : y1) : (x1 > y1 ? x1 : y1);
+          }
+        }
+      }
+    }
+    if (e0 < n) ids[off + e0] = (uint32_t)x0;
+    if (e0 + 1 < n) ids[off + e0 + 1] = (uint32_t)x1;
     return;
   }
   uint32_t m = 2;
@@ -238,7 +300,7 @@ int tile_sort_capacity() { return kTileSortCap; }
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
   if (a.n > 0) {
-    tile_count_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a.n, a.rects, a.tiles, a.tiles_x, a.counts);
+    tile_count_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
     if (launches) *launches += 1;
   }
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
@@ -248,8 +310,7 @@ void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launc
 
 void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   if (a.n > 0) {
-    tile_scatter_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a.n, a.rects, a.tiles, a.tiles_x,
-                                                                          a.cursors, a.ids, a.capacity, a.overflow);
+    tile_scatter_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
     if (launches) *launches += 1;
   }
 }
