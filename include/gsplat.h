@@ -136,8 +136,9 @@ gs_status gs_ctx_destroy(gs_ctx *ctx);
 /* Last error message of this context ("" if none).  Owned by the context. */
 const char *gs_last_error(const gs_ctx *ctx);
 
-/* Pre-size scratch for up to n Gaussians, width*height pixels and n_pairs
- * pairs (each 0 = leave as is), e.g. before capturing a CUDA graph. */
+/* Pre-size scratch for up to n_gaussians items (Gaussians times views in a
+ * batched call), n_pixels pixels (summed over the views) and n_pairs pairs
+ * (each 0 = leave as is), e.g. before capturing a CUDA graph. */
 gs_status gs_ctx_reserve(gs_ctx *ctx, int64_t n_gaussians, int64_t n_pixels, int64_t n_pairs);
 
 /* sync = 1 (default): the forward pass reads the pair count to the host and
@@ -221,6 +222,66 @@ gs_status gs_render_bwd_adam(gs_ctx *ctx, const gs_gaussians *g, const gs_camera
                              float *params, float *m, float *v, const gs_adam_cfg *adam, int64_t step,
                              float *dL_dpose, gs_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched multi-view form.  One call renders, differentiates or scores
+ * n_views in [1, GS_MAX_VIEWS] views of one Gaussian map, each with its own
+ * camera, pose and image size.  The paper runs its per-frame iterations one
+ * view at a time (Sec. III-B.3 optimises on the current frame, keyframes are
+ * revisited in later iterations); the batched calls compute the same
+ * quantities for all views in one pass over the map, with each kernel
+ * launched once for the whole batch (the tiles of all views form one grid).
+ * Per-view arguments are HOST arrays of length n_views: cams, views and the
+ * image pointer arrays (whose entries are device pointers to that view's
+ * images, sized by its camera).  The batched loss is the sum over views of
+ * the per-view loss of gs_loss_l1 (each normalised by its own pixel count),
+ * so its gradient w.r.t. the map is the sum of the per-view gradients, and a
+ * batched step applies one Adam update to that sum.  Limits: n_views * n <
+ * 2^31 and fewer than 2^31 pixels and tiles over the batch.
+ * ------------------------------------------------------------------------- */
+#define GS_MAX_VIEWS 16
+
+/* gs_render_fwd for n_views views.  color, depth, alpha: host arrays of
+ * n_views device pointers (each array nullable, each entry nullable).  The
+ * state for gs_render_bwd_batched / gs_render_bwd_adam_batched stays in the
+ * context as for gs_render_fwd. */
+gs_status gs_render_fwd_batched(gs_ctx *ctx, const gs_gaussians *g, int32_t n_views,
+                                const gs_camera *cams, const gs_viewmat *views, const gs_raster_cfg *cfg,
+                                float *const *color, float *const *depth, float *const *alpha,
+                                gs_stream_t stream);
+
+/* gs_render_bwd for the views of the most recent gs_render_fwd_batched (same
+ * g, n_views, cams, views, cfg; GS_ERR_STATE otherwise).  dL_dcolor,
+ * dL_ddepth: host arrays of n_views device pointers (required); dL_dalpha:
+ * nullable array, nullable entries.  The parameter gradients summed over the
+ * views are ADDED to grads.  dL_dpose (device float[n_views][6], nullable)
+ * receives += each view's pose-twist gradient. */
+gs_status gs_render_bwd_batched(gs_ctx *ctx, const gs_gaussians *g, int32_t n_views,
+                                const gs_camera *cams, const gs_viewmat *views, const gs_raster_cfg *cfg,
+                                const float *const *dL_dcolor, const float *const *dL_ddepth,
+                                const float *const *dL_dalpha, const gs_grads *grads, float *dL_dpose,
+                                gs_stream_t stream);
+
+/* gs_render_bwd_adam for a batch: the backward pass of the most recent
+ * gs_render_fwd_batched fused with ONE Adam step on the gradient summed over
+ * the views.  Same arguments and step / device-counter rules as
+ * gs_render_bwd_adam, per-view arrays as in gs_render_bwd_batched. */
+gs_status gs_render_bwd_adam_batched(gs_ctx *ctx, const gs_gaussians *g, int32_t n_views,
+                                     const gs_camera *cams, const gs_viewmat *views, const gs_raster_cfg *cfg,
+                                     const float *const *dL_dcolor, const float *const *dL_ddepth,
+                                     const float *const *dL_dalpha, float *params, float *m, float *v,
+                                     const gs_adam_cfg *adam, int64_t step, float *dL_dpose,
+                                     gs_stream_t stream);
+
+/* gs_loss_l1 summed over n_views views: loss (device float[1]) = sum over v of
+ * L_v, where L_v is gs_loss_l1's loss of view v; writes every view's
+ * dL/dcolor and dL/ddepth.  All image arguments are host arrays of n_views
+ * device pointers (none NULL). */
+gs_status gs_loss_l1_batched(gs_ctx *ctx, int32_t n_views, const gs_camera *cams,
+                             const float *const *color, const float *const *depth,
+                             const float *const *target_rgb, const float *const *target_depth,
+                             float w_color, float w_depth, float *loss, float *const *dL_dcolor,
+                             float *const *dL_ddepth, gs_stream_t stream);
+
 /* Photometric loss (Eq. 12) plus a depth term:
  *   L = w_color * mean over 3HW of |color - target_rgb|
  *     + w_depth * mean over pixels with target_depth > 0 of |depth - target_depth|.
@@ -280,7 +341,8 @@ gs_status gs_bin_tiles(gs_ctx *ctx, int64_t n, const float *mean2d, const float 
                        int64_t *n_pairs, gs_stream_t stream);
 
 /* Copy the last forward pass's projected per-Gaussian quantities to caller
- * buffers (each nullable): mean2d [n, 2] (high part of a double-float),
+ * buffers (each nullable), n = views x Gaussians items, item v * N + i being
+ * Gaussian i seen from view v: mean2d [n, 2] (high part of a double-float),
  * cov2d [n, 3] (a, b, c of the dilated 2D covariance [[a, b], [b, c]]),
  * depth [n], rgb [n, 3], opacity [n], tiles [n] (int32 tiles touched; 0 =
  * culled).  For parity checks of the projection step. */

@@ -315,6 +315,73 @@ def weighted_pixel_gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, pixe
     return grads, out
 
 
+# ----------------------------------------------------------------------------
+# several views of one map (batched multi-view form)
+# ----------------------------------------------------------------------------
+def multiview_gradients(params: dict, sh_degree: int, cams, poses, targets, rcfg=RasterCfg(), lcfg=LossCfg(),
+                        with_pose: bool = True):
+    """Objective of one batched iteration over V views of the same map:
+    L = sum over v of L_v, L_v the single-view loss of view v (Eq. 12 plus
+    the depth term, each normalised by its own pixel count).  The paper
+    optimises view by view (Sec. III-B.3); summing the per-view losses is the
+    reading under which one batched Adam step uses the gradients of all views
+    at once.  Returns L, its gradient w.r.t. every parameter array, the pose
+    twist gradient of every view [V, 6] and the per-view renders.
+    ``poses`` is a list of (R_cw, t_cw); ``targets`` a list of (rgb, depth)."""
+    P = to_tensors(params, requires_grad=True)
+    xis = []
+    L = torch.zeros((), dtype=DT)
+    outs = []
+    for cam, (R_cw, t_cw), (trgb, tdep) in zip(cams, poses, targets):
+        R = torch.as_tensor(np.asarray(R_cw), dtype=DT)
+        t = torch.as_tensor(np.asarray(t_cw), dtype=DT)
+        xi = torch.zeros(6, dtype=DT, requires_grad=True)
+        xis.append(xi)
+        if with_pose:
+            R, t = perturb_pose(R, t, xi)
+        Lv, out = render_loss(P, sh_degree, cam, R, t, trgb, tdep, rcfg, lcfg)
+        L = L + Lv
+        outs.append(out)
+    leaves = [P[k] for k in PARAM_NAMES] + (xis if with_pose else [])
+    g = torch.autograd.grad(L, leaves, allow_unused=True)
+    grads = {k: (gi if gi is not None else torch.zeros_like(P[k])) for k, gi in zip(PARAM_NAMES, g)}
+    if with_pose:
+        grads["pose"] = torch.stack([gi if gi is not None else torch.zeros(6, dtype=DT)
+                                     for gi in g[len(PARAM_NAMES):]])
+    return L.detach(), grads, outs
+
+
+def multiview_weighted_gradients(params: dict, sh_degree: int, cams, poses, w_color, w_depth, w_alpha=None,
+                                 rcfg=RasterCfg(), with_pose: bool = True, prefilter: bool = True):
+    """Gradient of sum over views v and pixels s of <w_color[v][:, s], C_v(u_s)>
+    + w_depth[v][s] D_v(u_s) + w_alpha[v][s] A_v(u_s) (full images; the
+    upstream gradients of a batched backward pass).  Pose gradients [V, 6]."""
+    P = to_tensors(params, requires_grad=True)
+    xis = []
+    obj = torch.zeros((), dtype=DT)
+    for v, (cam, (R_cw, t_cw)) in enumerate(zip(cams, poses)):
+        R = torch.as_tensor(np.asarray(R_cw), dtype=DT)
+        t = torch.as_tensor(np.asarray(t_cw), dtype=DT)
+        xi = torch.zeros(6, dtype=DT, requires_grad=True)
+        xis.append(xi)
+        if with_pose:
+            R, t = perturb_pose(R, t, xi)
+        jj, ii = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+        pix = np.stack([ii.ravel(), jj.ravel()], 1)
+        out = render(P, sh_degree, cam, R, t, rcfg, pixels=pix, prefilter=prefilter)
+        obj = obj + (out["color"] * torch.as_tensor(np.asarray(w_color[v]).reshape(3, -1), dtype=DT)).sum()
+        obj = obj + (out["depth"] * torch.as_tensor(np.asarray(w_depth[v]).reshape(-1), dtype=DT)).sum()
+        if w_alpha is not None and w_alpha[v] is not None:
+            obj = obj + (out["alpha"] * torch.as_tensor(np.asarray(w_alpha[v]).reshape(-1), dtype=DT)).sum()
+    leaves = [P[k] for k in PARAM_NAMES] + (xis if with_pose else [])
+    g = torch.autograd.grad(obj, leaves, allow_unused=True)
+    grads = {k: (gi if gi is not None else torch.zeros_like(P[k])) for k, gi in zip(PARAM_NAMES, g)}
+    if with_pose:
+        grads["pose"] = torch.stack([gi if gi is not None else torch.zeros(6, dtype=DT)
+                                     for gi in g[len(PARAM_NAMES):]])
+    return grads
+
+
 def gaussian_pixel_evals(out: dict) -> int:
     """E_alg: number of (pixel, Gaussian) pairs that were blended."""
     return int(out["n_contrib"].sum())
@@ -323,5 +390,6 @@ def gaussian_pixel_evals(out: dict) -> int:
 __all__ = [
     "RasterCfg", "LossCfg", "to_tensors", "quat_to_rotmat", "covariance_3d", "se3_exp", "perturb_pose",
     "project", "composite", "render", "loss_l1", "loss_image_grads", "render_loss", "gradients",
-    "weighted_pixel_gradients", "pixel_centers", "gaussian_pixel_evals",
+    "weighted_pixel_gradients", "pixel_centers", "gaussian_pixel_evals", "multiview_gradients",
+    "multiview_weighted_gradients",
 ]

@@ -21,6 +21,9 @@ STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ER
                 5: "GS_ERR_BOUNDS", 6: "GS_ERR_TIMEOUT", 7: "GS_ERR_OOM", 8: "GS_ERR_STATE"}
 
 
+GS_ERR_INVALID_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_OOM, GS_ERR_STATE = 1, 2, 3, 7, 8
+
+
 class GsError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
@@ -68,6 +71,7 @@ STAGES = ("project_fwd", "depth_sort", "duplicate", "pair_sort", "ranges", "rast
 
 
 P = C.c_void_p
+PP = C.POINTER(C.c_void_p)  # host array of device pointers
 EXPORTS = {
     "gs_ctx_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int64]),
     "gs_ctx_destroy": (C.c_int, [P]),
@@ -92,6 +96,16 @@ EXPORTS = {
                                C.POINTER(C.c_int64), P]),
     "gs_get_projection": (C.c_int, [P, P, P, P, P, P, P, P]),
     "gs_loss_l1_noalloc": (C.c_int, [C.POINTER(gs_camera), P, P, P, P, C.c_float, C.c_float, P, P, P, P]),
+    "gs_render_fwd_batched": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera),
+                                        C.POINTER(gs_viewmat), C.POINTER(gs_raster_cfg), PP, PP, PP, P]),
+    "gs_render_bwd_batched": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera),
+                                        C.POINTER(gs_viewmat), C.POINTER(gs_raster_cfg), PP, PP, PP,
+                                        C.POINTER(gs_grads), P, P]),
+    "gs_render_bwd_adam_batched": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera),
+                                             C.POINTER(gs_viewmat), C.POINTER(gs_raster_cfg), PP, PP, PP, P, P, P,
+                                             C.POINTER(gs_adam_cfg), C.c_int64, P, P]),
+    "gs_loss_l1_batched": (C.c_int, [P, C.c_int32, C.POINTER(gs_camera), PP, PP, PP, PP, C.c_float, C.c_float, P,
+                                     PP, PP, P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
     "gs_set_profiling": (C.c_int, [P, C.c_int]),
     "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -317,3 +331,65 @@ def gs_get_projection(ctx, mean2d=None, cov2d=None, depth=None, rgb=None, opacit
     st = load().gs_get_projection(ctx, _f32(mean2d, "mean2d"), _f32(cov2d, "cov2d"), _f32(depth, "depth"),
                                   _f32(rgb, "rgb"), _f32(opacity, "opacity"), _ptr(tiles), _stream(stream))
     _check(ctx, st, "gs_get_projection")
+
+
+# ---------------------------------------------------------------------------
+# batched multi-view entry points: per-view arguments are Python sequences
+# ---------------------------------------------------------------------------
+def _cams(cams):
+    arr = (gs_camera * len(cams))(*cams)
+    return arr
+
+
+def _views(views):
+    return (gs_viewmat * len(views))(*views)
+
+
+def _ptrs(tensors, name, n):
+    """Host array of n device pointers (None -> NULL array / entry)."""
+    if tensors is None:
+        return None
+    if len(tensors) != n:
+        raise ValueError(f"{name}: expected {n} entries")
+    return (C.c_void_p * n)(*[_f32(t, name) for t in tensors])
+
+
+def gs_render_fwd_batched(ctx, gaussians: gs_gaussians, cams, views, cfg: gs_raster_cfg, color=None, depth=None,
+                          alpha=None, stream=None):
+    V = len(cams)
+    st = load().gs_render_fwd_batched(ctx, C.byref(gaussians), V, _cams(cams), _views(views), C.byref(cfg),
+                                      _ptrs(color, "color", V), _ptrs(depth, "depth", V), _ptrs(alpha, "alpha", V),
+                                      _stream(stream))
+    _check(ctx, st, "gs_render_fwd_batched")
+
+
+def gs_render_bwd_batched(ctx, gaussians, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, grads: gs_grads,
+                          dL_dpose=None, stream=None):
+    V = len(cams)
+    st = load().gs_render_bwd_batched(ctx, C.byref(gaussians), V, _cams(cams), _views(views), C.byref(cfg),
+                                      _ptrs(dL_dcolor, "dL_dcolor", V), _ptrs(dL_ddepth, "dL_ddepth", V),
+                                      _ptrs(dL_dalpha, "dL_dalpha", V), C.byref(grads), _f32(dL_dpose, "dL_dpose"),
+                                      _stream(stream))
+    _check(ctx, st, "gs_render_bwd_batched")
+
+
+def gs_render_bwd_adam_batched(ctx, gaussians, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, params, m, v,
+                               adam: gs_adam_cfg, step: int, dL_dpose=None, stream=None):
+    V = len(cams)
+    st = load().gs_render_bwd_adam_batched(ctx, C.byref(gaussians), V, _cams(cams), _views(views), C.byref(cfg),
+                                           _ptrs(dL_dcolor, "dL_dcolor", V), _ptrs(dL_ddepth, "dL_ddepth", V),
+                                           _ptrs(dL_dalpha, "dL_dalpha", V), _f32(params, "params"), _f32(m, "m"),
+                                           _f32(v, "v"), C.byref(adam), int(step), _f32(dL_dpose, "dL_dpose"),
+                                           _stream(stream))
+    _check(ctx, st, "gs_render_bwd_adam_batched")
+
+
+def gs_loss_l1_batched(ctx, cams, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
+                       dL_ddepth, stream=None):
+    V = len(cams)
+    st = load().gs_loss_l1_batched(ctx, V, _cams(cams), _ptrs(color, "color", V), _ptrs(depth, "depth", V),
+                                   _ptrs(target_rgb, "target_rgb", V), _ptrs(target_depth, "target_depth", V),
+                                   float(w_color), float(w_depth), _f32(loss, "loss"),
+                                   _ptrs(dL_dcolor, "dL_dcolor", V), _ptrs(dL_ddepth, "dL_ddepth", V),
+                                   _stream(stream))
+    _check(ctx, st, "gs_loss_l1_batched")

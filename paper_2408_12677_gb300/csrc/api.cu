@@ -72,10 +72,15 @@ struct gs_ctx {
   // state of the last forward pass
   bool have_state = false;
   int64_t st_n = 0;
-  int st_w = 0, st_h = 0, st_tw = 0, st_th = 0, st_tx = 0, st_ty = 0;
+  int st_views = 0;
+  int st_w[kMaxViews] = {}, st_h[kMaxViews] = {};
+  int st_tw = 0, st_th = 0;
+  int64_t st_tiles = 0;
   int64_t st_pairs = 0;
   int st_pair_buf = 0;
   int st_sh = 0;
+  TileMap st_map{};
+  int64_t st_pix_base[kMaxViews] = {};
 };
 
 namespace {
@@ -149,7 +154,8 @@ gs_status ensure_n(gs_ctx* c, int64_t n) {
   GS_CUDA(c, regrow(&c->bigq, cap));
   GS_CUDA(c, regrow(&c->g2d, 3 * cap));
   GS_CUDA(c, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
-  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((int64_t)project_bwd_blocks((int)cap) + 1)));
+  // per (block, view) pose partials: blocks(n) * V <= blocks(V n) + V
+  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((int64_t)project_bwd_blocks((int)cap) + kMaxViews + 1)));
   c->cap_n = cap;
   c->have_state = false;
   return GS_OK;
@@ -189,7 +195,9 @@ gs_status ensure_px(gs_ctx* c, int64_t npx) {
   const int64_t cap = grow_target(npx, c->cap_px);
   GS_CUDA(c, regrow(&c->T_final, cap));
   GS_CUDA(c, regrow(&c->last, cap));
-  GS_CUDA(c, regrow(&c->loss_partials, 3 * (int64_t)loss_blocks((int)cap) + 4));
+  // per-block partials (blocks of every view: <= blocks(total) + views) and per-view scales
+  const int64_t lb = loss_blocks((int)std::min<int64_t>(cap, INT32_MAX - 4096));
+  GS_CUDA(c, regrow(&c->loss_partials, 3 * (lb + kMaxViews) + kMaxViews + 4));
   c->cap_px = cap;
   c->have_state = false;
   return GS_OK;
@@ -260,11 +268,11 @@ gs_status ensure_hist(gs_ctx* c) {
 }
 
 // Radix binning (used when a tile list is longer than the per-tile sort holds):
-// depth sort of n Gaussians (keys in zkey, ids implicit), duplication into
-// pairs, pair sort by tile, tile ranges.  On success c->st_pairs / st_pair_buf
-// describe the sorted pair list.
-gs_status bin_and_sort_radix(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
-  const int64_t T = (int64_t)tiles_x * tiles_y;
+// depth sort of the n items (keys in zkey, ids implicit), duplication into
+// pairs, pair sort by global tile, tile ranges.  On success c->st_pairs /
+// st_pair_buf describe the sorted pair list.
+gs_status bin_and_sort_radix(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
+  const int64_t T = (int64_t)map.tile_base[map.views];
   if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
   SortBuffers sb;
   sb.keys[0] = c->dkey[0];
@@ -285,7 +293,7 @@ gs_status bin_and_sort_radix(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStr
   da.sorted_ids = sorted_ids;
   da.tiles_touched = c->tiles;
   da.rects = c->rects;
-  da.tiles_x = tiles_x;
+  da.map = map;
   da.block_sums = c->dup_sums;
   da.n_pairs = c->d_npairs;
   da.n_pairs_full = c->d_npairs_full;
@@ -345,15 +353,15 @@ gs_status bin_and_sort_radix(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStr
 // Counting-scatter binning with per-tile sorts: count, scan (one host read of
 // the totals in sync mode), scatter, sort.  Falls back to the radix path when
 // some tile list is longer than the per-tile sort holds.
-gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t s) {
-  const int64_t T = (int64_t)tiles_x * tiles_y;
+gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
+  const int64_t T = (int64_t)map.tile_base[map.views];
   if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
   TileBinArgs tb;
   tb.n = n;
   tb.rects = c->rects;
   tb.tiles = c->tiles;
   tb.zkey = c->zkey;
-  tb.tiles_x = tiles_x;
+  tb.map = map;
   tb.n_tiles = (int)T;
   tb.num_sms = c->num_sms;
   tb.counts = c->tcount;
@@ -378,7 +386,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, int tiles_x, int tiles_y, cudaStream_t 
     GS_CUDA(c, cudaStreamSynchronize(s));
     P = (int64_t)c->h_pinned[0];
     const int64_t longest = (int64_t)c->h_pinned[1];
-    if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, tiles_x, tiles_y, s);
+    if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, map, s);
     gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
     if (st != GS_OK) return st;
     tb.capacity = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFF0ll);
@@ -558,7 +566,7 @@ gs_status gs_get_stats(gs_ctx* c, gs_stats* out) {
   out->n_pairs = c->st_pairs;
   out->pair_capacity = c->cap_p;
   out->kernel_launches = c->launches;
-  out->n_tiles = (int64_t)c->st_tx * c->st_ty;
+  out->n_tiles = c->st_tiles;
   out->evals_blended = 0;
   out->evals_tiled = 0;
   if (c->counting) {
@@ -608,46 +616,142 @@ gs_status gs_profile_read(gs_ctx* c, double* ms, int64_t* count) {
   return GS_OK;
 }
 
-gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                        const gs_raster_cfg* cfg, float* color, float* depth, float* alpha, gs_stream_t stream) {
-  if (!c) return GS_ERR_INVALID_ARG;
-  gs_status st;
-  if ((st = check_gauss(c, g)) != GS_OK || (st = check_cam(c, cam)) != GS_OK || (st = check_cfg(c, cfg)) != GS_OK)
-    return st;
-  if (!view) return fail(c, GS_ERR_INVALID_ARG, "viewmat is NULL");
-  const int tiles_x = (cam->width + cfg->tile_w - 1) / cfg->tile_w;
-  const int tiles_y = (cam->height + cfg->tile_h - 1) / cfg->tile_h;
-  if (tiles_x > 65535 || tiles_y > 65535) return fail(c, GS_ERR_INVALID_ARG, "too many tiles per axis");
-  cudaStream_t s = (cudaStream_t)stream;
-  GS_CUDA(c, cudaSetDevice(c->device));
-  const int n = (int)g->n;
-  const int64_t npx = (int64_t)cam->width * cam->height;
-  const int64_t T = (int64_t)tiles_x * tiles_y;
-  if (c->sync) {
-    if ((st = ensure_n(c, std::max(n, 1))) != GS_OK || (st = ensure_px(c, npx)) != GS_OK ||
-        (st = ensure_tiles(c, T)) != GS_OK)
-      return st;
-  } else if (n > c->cap_n || npx > c->cap_px || T > c->cap_t) {
-    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve Gaussians/pixels first (gs_ctx_reserve)");
-  }
-  c->have_state = false;
+}  // extern "C"
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Batched internals: every render entry point runs through these with
+// V >= 1 views of one Gaussian map (the single-view calls are V = 1).
+// ---------------------------------------------------------------------------
+
+struct ViewLayout {
+  int V = 0;
+  int64_t items = 0, pixels = 0, tiles = 0;
+  TileMap map{};
+  int tiles_y[kMaxViews] = {};
+  int64_t pix_base[kMaxViews] = {};
+};
+
+gs_status check_views(gs_ctx* c, int32_t V, const gs_camera* cams, const gs_viewmat* views) {
+  if (V < 1 || V > kMaxViews) return fail(c, GS_ERR_INVALID_ARG, "n_views must be in [1, 16]");
+  if (!cams || !views) return fail(c, GS_ERR_INVALID_ARG, "cameras / viewmats array is NULL");
+  for (int v = 0; v < V; ++v) {
+    gs_status st = check_cam(c, &cams[v]);
+    if (st != GS_OK) return st;
+  }
+  return GS_OK;
+}
+
+gs_status layout_views(gs_ctx* c, int64_t n, int V, const gs_camera* cams, const gs_raster_cfg* cfg, ViewLayout& L) {
+  L.V = V;
+  L.items = (int64_t)V * n;
+  if (L.items >= ((int64_t)1 << 31)) return fail(c, GS_ERR_INVALID_ARG, "views x Gaussians must be < 2^31");
+  L.map.views = V;
+  L.map.n_per_view = (int)n;
+  int64_t tiles = 0, pixels = 0;
+  for (int v = 0; v < V; ++v) {
+    const int tx = (cams[v].width + cfg->tile_w - 1) / cfg->tile_w;
+    const int ty = (cams[v].height + cfg->tile_h - 1) / cfg->tile_h;
+    if (tx > 65535 || ty > 65535) return fail(c, GS_ERR_INVALID_ARG, "too many tiles per axis");
+    L.map.tiles_x[v] = tx;
+    L.tiles_y[v] = ty;
+    L.map.tile_base[v] = (uint32_t)tiles;
+    L.pix_base[v] = pixels;
+    tiles += (int64_t)tx * ty;
+    pixels += (int64_t)cams[v].width * cams[v].height;
+  }
+  if (tiles >= ((int64_t)1 << 31) || pixels >= ((int64_t)1 << 31))
+    return fail(c, GS_ERR_INVALID_ARG, "a batch must have < 2^31 tiles and pixels");
+  for (int v = V; v <= kMaxViews; ++v) {
+    if (v < kMaxViews) L.map.tiles_x[v] = 1;
+    L.map.tile_base[v] = (uint32_t)tiles;
+  }
+  L.tiles = tiles;
+  L.pixels = pixels;
+  return GS_OK;
+}
+
+ProjectArgs project_args(const gs_gaussians* g, int V, const gs_camera* cams, const gs_viewmat* views,
+                         const gs_raster_cfg* cfg, const TileMap& map, const int* tiles_y) {
   ProjectArgs pa;
-  pa.n = n;
+  pa.big_queue = nullptr;
+  pa.big_len = nullptr;
+  pa.n = (int)g->n;
+  pa.views = V;
   pa.means = g->means;
   pa.log_scales = g->log_scales;
   pa.quats = g->quats;
   pa.logits = g->opacity_logits;
   pa.sh = g->sh;
   pa.sh_degree = g->sh_degree;
-  pa.cv = make_camview(cam, view);
   pa.near_z = cfg->near_z;
   pa.dilation = cfg->dilation;
   pa.alpha_min = cfg->alpha_min;
   pa.tile_w = cfg->tile_w;
   pa.tile_h = cfg->tile_h;
-  pa.tiles_x = tiles_x;
-  pa.tiles_y = tiles_y;
+  for (int v = 0; v < kMaxViews; ++v) {
+    if (v < V) {
+      pa.cv[v] = make_camview(&cams[v], &views[v]);
+      pa.tiles_x[v] = map.tiles_x[v];
+      pa.tiles_y[v] = tiles_y[v];
+    } else {
+      pa.cv[v] = CamView{};
+      pa.tiles_x[v] = pa.tiles_y[v] = 0;
+    }
+  }
+  return pa;
+}
+
+RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
+  RasterArgs ra;
+  ra.views = c->st_views;
+  ra.tile_w = cfg->tile_w;
+  ra.tile_h = cfg->tile_h;
+  ra.n_tiles = (uint32_t)c->st_tiles;
+  for (int k = 0; k < 3; ++k) ra.bg[k] = cfg->bg[k];
+  ra.alpha_max = cfg->alpha_max;
+  ra.alpha_min = cfg->alpha_min;
+  ra.t_eps = cfg->t_eps;
+  ra.ranges = c->ranges;
+  ra.ids = c->pv[c->st_pair_buf];
+  ra.feat = c->feat;
+  ra.order = nullptr;
+  for (int v = 0; v < kMaxViews; ++v) {
+    RasterView& rv = ra.v[v];
+    const bool live = v < c->st_views;
+    rv.width = live ? c->st_w[v] : 0;
+    rv.height = live ? c->st_h[v] : 0;
+    rv.tiles_x = c->st_map.tiles_x[v];
+    rv.tile_base = c->st_map.tile_base[v];
+    rv.pix_base = live ? c->st_pix_base[v] : 0;
+    rv.color = rv.depth = rv.alpha = nullptr;
+    rv.dLdc = rv.dLdd = rv.dLda = nullptr;
+  }
+  return ra;
+}
+
+gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
+                           const gs_viewmat* views, const gs_raster_cfg* cfg, float* const* color,
+                           float* const* depth, float* const* alpha, cudaStream_t s) {
+  gs_status st;
+  if ((st = check_gauss(c, g)) != GS_OK || (st = check_views(c, V, cams, views)) != GS_OK ||
+      (st = check_cfg(c, cfg)) != GS_OK)
+    return st;
+  ViewLayout L;
+  if ((st = layout_views(c, g->n, V, cams, cfg, L)) != GS_OK) return st;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  const int n_items = (int)L.items;
+  if (c->sync) {
+    if ((st = ensure_n(c, std::max(n_items, 1))) != GS_OK || (st = ensure_px(c, L.pixels)) != GS_OK ||
+        (st = ensure_tiles(c, L.tiles)) != GS_OK)
+      return st;
+  } else if (n_items > c->cap_n || L.pixels > c->cap_px || L.tiles > c->cap_t) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve items/pixels first (gs_ctx_reserve)");
+  }
+  c->have_state = false;
+
+  ProjectArgs pa = project_args(g, V, cams, views, cfg, L.map, L.tiles_y);
   pa.big_queue = c->bigq;
   pa.big_len = c->d_bigmeta;
   GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
@@ -655,107 +759,75 @@ gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
     StageTimer t(c, GS_STAGE_PROJECT_FWD, s);
     launch_project_fwd(pa, c->feat, c->zkey, c->tiles, c->rects, s);
   }
-  if (n > 0) c->launches += 1;
+  if (g->n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "project_fwd");
 
-  if ((st = bin_and_sort(c, n, tiles_x, tiles_y, s)) != GS_OK) return st;
+  if ((st = bin_and_sort(c, n_items, L.map, s)) != GS_OK) return st;
 
-  RasterArgs ra;
-  ra.width = cam->width;
-  ra.height = cam->height;
-  ra.tile_w = cfg->tile_w;
-  ra.tile_h = cfg->tile_h;
-  ra.tiles_x = tiles_x;
-  ra.tiles_y = tiles_y;
-  for (int k = 0; k < 3; ++k) ra.bg[k] = cfg->bg[k];
-  ra.alpha_max = cfg->alpha_max;
-  ra.alpha_min = cfg->alpha_min;
-  ra.t_eps = cfg->t_eps;
-  ra.ranges = c->ranges;
-  ra.ids = c->pv[c->st_pair_buf];
-  ra.feat = c->feat;
+  c->st_n = g->n;
+  c->st_views = V;
+  for (int v = 0; v < V; ++v) {
+    c->st_w[v] = cams[v].width;
+    c->st_h[v] = cams[v].height;
+    c->st_pix_base[v] = L.pix_base[v];
+  }
+  c->st_tw = cfg->tile_w;
+  c->st_th = cfg->tile_h;
+  c->st_tiles = L.tiles;
+  c->st_map = L.map;
+  c->st_sh = g->sh_degree;
+
+  RasterArgs ra = raster_args(c, cfg);
+  for (int v = 0; v < V; ++v) {
+    ra.v[v].color = color ? color[v] : nullptr;
+    ra.v[v].depth = depth ? depth[v] : nullptr;
+    ra.v[v].alpha = alpha ? alpha[v] : nullptr;
+  }
   {
     StageTimer t(c, GS_STAGE_RASTER_FWD, s);
-    launch_raster_fwd(ra, color, depth, alpha, c->T_final, c->last, c->counting ? c->d_evals : nullptr, s);
+    launch_raster_fwd(ra, c->T_final, c->last, c->counting ? c->d_evals : nullptr, s);
   }
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_fwd");
-
   c->have_state = true;
-  c->st_n = n;
-  c->st_w = cam->width;
-  c->st_h = cam->height;
-  c->st_tw = cfg->tile_w;
-  c->st_th = cfg->tile_h;
-  c->st_tx = tiles_x;
-  c->st_ty = tiles_y;
-  c->st_sh = g->sh_degree;
   return GS_OK;
 }
 
-namespace {
-
-gs_status check_bwd_common(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                           const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth) {
+gs_status check_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
+                          const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
+                          const float* const* dL_ddepth) {
   gs_status st;
-  if ((st = check_gauss(c, g)) != GS_OK || (st = check_cam(c, cam)) != GS_OK || (st = check_cfg(c, cfg)) != GS_OK)
+  if ((st = check_gauss(c, g)) != GS_OK || (st = check_views(c, V, cams, views)) != GS_OK ||
+      (st = check_cfg(c, cfg)) != GS_OK)
     return st;
-  if (!view) return fail(c, GS_ERR_INVALID_ARG, "viewmat is NULL");
   if (!dL_dcolor || !dL_ddepth) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
-  if (!c->have_state || c->st_n != g->n || c->st_w != cam->width || c->st_h != cam->height ||
-      c->st_tw != cfg->tile_w || c->st_th != cfg->tile_h || c->st_sh != g->sh_degree)
-    return fail(c, GS_ERR_STATE, "the backward pass needs the matching gs_render_fwd on this context");
+  for (int v = 0; v < V; ++v)
+    if (!dL_dcolor[v] || !dL_ddepth[v]) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
+  bool match = c->have_state && c->st_n == g->n && c->st_views == V && c->st_tw == cfg->tile_w &&
+               c->st_th == cfg->tile_h && c->st_sh == g->sh_degree;
+  for (int v = 0; match && v < V; ++v) match = c->st_w[v] == cams[v].width && c->st_h[v] == cams[v].height;
+  if (!match) return fail(c, GS_ERR_STATE, "the backward pass needs the matching forward pass on this context");
   return GS_OK;
 }
 
-// raster backward into the context's per-Gaussian gradient records
-gs_status raster_backward(gs_ctx* c, const gs_camera* cam, const gs_raster_cfg* cfg, const float* dL_dcolor,
-                          const float* dL_ddepth, const float* dL_dalpha, int n, cudaStream_t s) {
-  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)n, s));
-  RasterArgs ra;
-  ra.width = cam->width;
-  ra.height = cam->height;
-  ra.tile_w = cfg->tile_w;
-  ra.tile_h = cfg->tile_h;
-  ra.tiles_x = c->st_tx;
-  ra.tiles_y = c->st_ty;
-  for (int k = 0; k < 3; ++k) ra.bg[k] = cfg->bg[k];
-  ra.alpha_max = cfg->alpha_max;
-  ra.alpha_min = cfg->alpha_min;
-  ra.t_eps = cfg->t_eps;
-  ra.ranges = c->ranges;
-  ra.ids = c->pv[c->st_pair_buf];
-  ra.feat = c->feat;
+// raster backward into the context's per-item gradient records
+gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
+                          const float* const* dL_ddepth, const float* const* dL_dalpha, cudaStream_t s) {
+  const int64_t items = c->st_n * c->st_views;
+  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)items, s));
+  RasterArgs ra = raster_args(c, cfg);
+  for (int v = 0; v < c->st_views; ++v) {
+    ra.v[v].dLdc = dL_dcolor[v];
+    ra.v[v].dLdd = dL_ddepth[v];
+    ra.v[v].dLda = dL_dalpha ? dL_dalpha[v] : nullptr;
+  }
   {
     StageTimer t(c, GS_STAGE_RASTER_BWD, s);
-    launch_raster_bwd(ra, c->T_final, c->last, dL_dcolor, dL_ddepth, dL_dalpha, c->g2d, s);
+    launch_raster_bwd(ra, c->T_final, c->last, c->g2d, s);
   }
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_bwd");
   return GS_OK;
-}
-
-ProjectArgs project_args(const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                         const gs_raster_cfg* cfg, int tiles_x, int tiles_y) {
-  ProjectArgs pa;
-  pa.big_queue = nullptr;
-  pa.big_len = nullptr;
-  pa.n = (int)g->n;
-  pa.means = g->means;
-  pa.log_scales = g->log_scales;
-  pa.quats = g->quats;
-  pa.logits = g->opacity_logits;
-  pa.sh = g->sh;
-  pa.sh_degree = g->sh_degree;
-  pa.cv = make_camview(cam, view);
-  pa.near_z = cfg->near_z;
-  pa.dilation = cfg->dilation;
-  pa.alpha_min = cfg->alpha_min;
-  pa.tile_w = cfg->tile_w;
-  pa.tile_h = cfg->tile_h;
-  pa.tiles_x = tiles_x;
-  pa.tiles_y = tiles_y;
-  return pa;
 }
 
 gs_status check_adam(gs_ctx* c, const gs_adam_cfg* cfg, int64_t step, bool allow_device_step = false) {
@@ -789,26 +861,23 @@ AdamArgs adam_args(const gs_adam_cfg* cfg, int64_t step) {
   return ad;
 }
 
-}  // namespace
-
-gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                             const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
-                             const float* dL_dalpha, float* params, float* m, float* v, const gs_adam_cfg* adam,
-                             int64_t step, float* dL_dpose, gs_stream_t stream) {
-  if (!c) return GS_ERR_INVALID_ARG;
+gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
+                                const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
+                                const float* const* dL_ddepth, const float* const* dL_dalpha, float* params,
+                                float* m, float* v, const gs_adam_cfg* adam, int64_t step, float* dL_dpose,
+                                cudaStream_t s) {
   gs_status st;
-  if ((st = check_bwd_common(c, g, cam, view, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
+  if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
   const int64_t n = g->n;
   if (n > 0 && (!params || !m || !v)) return fail(c, GS_ERR_INVALID_ARG, "params, m and v are required");
   if (n > 0 && (g->means != params || g->log_scales != params + 3 * n || g->quats != params + 6 * n ||
                 g->opacity_logits != params + 10 * n || g->sh != params + 11 * n))
     return fail(c, GS_ERR_INVALID_ARG, "the Gaussian arrays must be the flat parameter buffer's blocks");
-  cudaStream_t s = (cudaStream_t)stream;
   GS_CUDA(c, cudaSetDevice(c->device));
   if (n == 0) return GS_OK;
-  if ((st = raster_backward(c, cam, cfg, dL_dcolor, dL_ddepth, dL_dalpha, (int)n, s)) != GS_OK) return st;
-  const ProjectArgs pa = project_args(g, cam, view, cfg, c->st_tx, c->st_ty);
+  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s)) != GS_OK) return st;
+  const ProjectArgs pa = project_args(g, V, cams, views, cfg, c->st_map, c->st_map.tiles_x);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
     AdamArgs ad = adam_args(adam, step);
@@ -817,10 +886,10 @@ gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* 
       c->launches += 1;
       ad.step_dev = c->d_step;
     }
-    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, c->pose_partials, s);
+    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, dL_dpose ? c->pose_partials : nullptr, s);
     c->launches += 1;
     if (dL_dpose) {
-      launch_pose_reduce(c->pose_partials, nb, dL_dpose, s);
+      launch_pose_reduce(c->pose_partials, nb, V, dL_dpose, s);
       c->launches += 1;
     }
   }
@@ -828,28 +897,26 @@ gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* 
   return GS_OK;
 }
 
-gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
-                        const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
-                        const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
-  if (!c) return GS_ERR_INVALID_ARG;
+gs_status render_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
+                           const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
+                           const float* const* dL_ddepth, const float* const* dL_dalpha, const gs_grads* grads,
+                           float* dL_dpose, cudaStream_t s) {
   gs_status st;
-  if ((st = check_bwd_common(c, g, cam, view, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
+  if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if (!grads) return fail(c, GS_ERR_INVALID_ARG, "grads is NULL");
   if (g->n > 0 && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh))
     return fail(c, GS_ERR_INVALID_ARG, "a gradient pointer is NULL");
-  cudaStream_t s = (cudaStream_t)stream;
   GS_CUDA(c, cudaSetDevice(c->device));
-  const int n = (int)g->n;
-  if (n == 0) return GS_OK;
-  if ((st = raster_backward(c, cam, cfg, dL_dcolor, dL_ddepth, dL_dalpha, n, s)) != GS_OK) return st;
-  const ProjectArgs pa = project_args(g, cam, view, cfg, c->st_tx, c->st_ty);
+  if (g->n == 0) return GS_OK;
+  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s)) != GS_OK) return st;
+  const ProjectArgs pa = project_args(g, V, cams, views, cfg, c->st_map, c->st_map.tiles_x);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
     const int nb = launch_project_bwd(pa, c->g2d, grads->means, grads->log_scales, grads->quats,
-                                      grads->opacity_logits, grads->sh, c->pose_partials, s);
+                                      grads->opacity_logits, grads->sh, dL_dpose ? c->pose_partials : nullptr, s);
     c->launches += 1;
     if (dL_dpose) {
-      launch_pose_reduce(c->pose_partials, nb, dL_dpose, s);
+      launch_pose_reduce(c->pose_partials, nb, V, dL_dpose, s);
       c->launches += 1;
     }
   }
@@ -857,29 +924,121 @@ gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
   return GS_OK;
 }
 
+gs_status loss_views(gs_ctx* c, int32_t V, const gs_camera* cams, const float* const* color,
+                     const float* const* depth, const float* const* target_rgb, const float* const* target_depth,
+                     float w_color, float w_depth, float* loss, float* const* dL_dcolor, float* const* dL_ddepth,
+                     cudaStream_t s) {
+  if (V < 1 || V > kMaxViews) return fail(c, GS_ERR_INVALID_ARG, "n_views must be in [1, 16]");
+  if (!cams) return fail(c, GS_ERR_INVALID_ARG, "cameras array is NULL");
+  if (!color || !depth || !target_rgb || !target_depth || !loss || !dL_dcolor || !dL_ddepth)
+    return fail(c, GS_ERR_INVALID_ARG, "loss: NULL pointer");
+  if (!std::isfinite(w_color) || !std::isfinite(w_depth)) return fail(c, GS_ERR_INVALID_ARG, "non-finite weight");
+  LossArgs la;
+  la.views = V;
+  la.w_color = w_color;
+  la.w_depth = w_depth;
+  la.loss = loss;
+  int64_t pixels = 0, blocks = 0;
+  for (int v = 0; v < V; ++v) {
+    gs_status st = check_cam(c, &cams[v]);
+    if (st != GS_OK) return st;
+    if (!color[v] || !depth[v] || !target_rgb[v] || !target_depth[v] || !dL_dcolor[v] || !dL_ddepth[v])
+      return fail(c, GS_ERR_INVALID_ARG, "loss: NULL image pointer");
+    const int64_t npx = (int64_t)cams[v].width * cams[v].height;
+    la.v[v] = LossView{(int)npx, (int)blocks, color[v], depth[v], target_rgb[v], target_depth[v], dL_dcolor[v],
+                       dL_ddepth[v]};
+    pixels += npx;
+    blocks += loss_blocks((int)npx);
+  }
+  if (pixels >= ((int64_t)1 << 31)) return fail(c, GS_ERR_INVALID_ARG, "a batch must have < 2^31 pixels");
+  la.n_blocks = (int)blocks;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  gs_status st;
+  if (c->sync) {
+    if ((st = ensure_px(c, pixels)) != GS_OK) return st;
+  } else if (pixels > c->cap_px) {
+    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve pixels first");
+  }
+  {
+    StageTimer t(c, GS_STAGE_LOSS, s);
+    launch_loss(la, c->loss_partials, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "loss");
+  return GS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, float* color, float* depth, float* alpha, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
+  return render_fwd_views(c, g, 1, cam, view, cfg, &color, &depth, &alpha, (cudaStream_t)stream);
+}
+
+gs_status gs_render_fwd_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
+                                const gs_viewmat* views, const gs_raster_cfg* cfg, float* const* color,
+                                float* const* depth, float* const* alpha, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  return render_fwd_views(c, g, n_views, cams, views, cfg, color, depth, alpha, (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                             const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
+                             const float* dL_dalpha, float* params, float* m, float* v, const gs_adam_cfg* adam,
+                             int64_t step, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
+  return render_bwd_adam_views(c, g, 1, cam, view, cfg, &dL_dcolor, &dL_ddepth, &dL_dalpha, params, m, v, adam, step,
+                               dL_dpose, (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd_adam_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
+                                     const gs_viewmat* views, const gs_raster_cfg* cfg,
+                                     const float* const* dL_dcolor, const float* const* dL_ddepth,
+                                     const float* const* dL_dalpha, float* params, float* m, float* v,
+                                     const gs_adam_cfg* adam, int64_t step, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  return render_bwd_adam_views(c, g, n_views, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, params, m, v, adam,
+                               step, dL_dpose, (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
+                        const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
+  return render_bwd_views(c, g, 1, cam, view, cfg, &dL_dcolor, &dL_ddepth, &dL_dalpha, grads, dL_dpose,
+                          (cudaStream_t)stream);
+}
+
+gs_status gs_render_bwd_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
+                                const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
+                                const float* const* dL_ddepth, const float* const* dL_dalpha,
+                                const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  return render_bwd_views(c, g, n_views, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, grads, dL_dpose,
+                          (cudaStream_t)stream);
+}
+
 gs_status gs_loss_l1(gs_ctx* c, const gs_camera* cam, const float* color, const float* depth,
                      const float* target_rgb, const float* target_depth, float w_color, float w_depth, float* loss,
                      float* dL_dcolor, float* dL_ddepth, gs_stream_t stream) {
   if (!c) return GS_ERR_INVALID_ARG;
-  gs_status st;
-  if ((st = check_cam(c, cam)) != GS_OK) return st;
-  if (!color || !depth || !target_rgb || !target_depth || !loss || !dL_dcolor || !dL_ddepth)
-    return fail(c, GS_ERR_INVALID_ARG, "gs_loss_l1: NULL pointer");
-  if (!std::isfinite(w_color) || !std::isfinite(w_depth)) return fail(c, GS_ERR_INVALID_ARG, "non-finite weight");
-  GS_CUDA(c, cudaSetDevice(c->device));
-  const int64_t npx = (int64_t)cam->width * cam->height;
-  if (c->sync) {
-    if ((st = ensure_px(c, npx)) != GS_OK) return st;
-  } else if (npx > c->cap_px) {
-    return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve pixels first");
-  }
-  {
-    StageTimer t(c, GS_STAGE_LOSS, (cudaStream_t)stream);
-    launch_loss(cam->height, cam->width, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
-                dL_ddepth, c->loss_partials, (cudaStream_t)stream, &c->launches);
-  }
-  GS_CHECK_LAUNCH(c, "loss");
-  return GS_OK;
+  if (!cam) return fail(c, GS_ERR_INVALID_ARG, "camera is NULL");
+  return loss_views(c, 1, cam, &color, &depth, &target_rgb, &target_depth, w_color, w_depth, loss, &dL_dcolor,
+                    &dL_ddepth, (cudaStream_t)stream);
+}
+
+gs_status gs_loss_l1_batched(gs_ctx* c, int32_t n_views, const gs_camera* cams, const float* const* color,
+                             const float* const* depth, const float* const* target_rgb,
+                             const float* const* target_depth, float w_color, float w_depth, float* loss,
+                             float* const* dL_dcolor, float* const* dL_ddepth, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  return loss_views(c, n_views, cams, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
+                    dL_ddepth, (cudaStream_t)stream);
 }
 
 gs_status gs_adam_step(gs_ctx* c, float* params, float* grads, float* m, float* v, int64_t n,
@@ -930,7 +1089,12 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
   launch_bin_prepare((int)n, mean2d, extent, depth, tile_w, tile_h, tiles_x, tiles_y, c->zkey, c->tiles, c->rects,
                      c->bigq, c->d_bigmeta, s);
   if (n > 0) c->launches += 1;
-  st = bin_and_sort(c, (int)n, tiles_x, tiles_y, s);
+  TileMap map{};
+  map.views = 1;
+  map.n_per_view = (int)n;
+  map.tiles_x[0] = tiles_x;
+  for (int v = 1; v <= kMaxViews; ++v) map.tile_base[v] = (uint32_t)T;
+  st = bin_and_sort(c, (int)n, map, s);
   c->sync = was_sync;
   if (st != GS_OK) return st;
   const int64_t P = c->st_pairs;
@@ -955,7 +1119,7 @@ gs_status gs_get_projection(gs_ctx* c, float* mean2d, float* cov2d, float* depth
   if (!c) return GS_ERR_INVALID_ARG;
   if (!c->have_state) return fail(c, GS_ERR_STATE, "no forward pass on this context");
   GS_CUDA(c, cudaSetDevice(c->device));
-  launch_export_projection((int)c->st_n, c->feat, c->tiles, mean2d, cov2d, depth, rgb, opacity, tiles,
+  launch_export_projection((int)(c->st_n * c->st_views), c->feat, c->tiles, mean2d, cov2d, depth, rgb, opacity, tiles,
                            (cudaStream_t)stream);
   if (c->st_n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "export projection");

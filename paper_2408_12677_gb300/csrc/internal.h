@@ -13,6 +13,20 @@ struct CamView {
   float C[3];  // camera centre in the world frame, -R^T t
 };
 
+// A call renders up to kMaxViews views of one Gaussian map.  Every per-item
+// array (projected features, depth keys, tile rectangles, gradient records)
+// holds V * n items, item i = v * n + g being Gaussian g seen from view v,
+// and the views' tiles are laid end to end: view v owns the global tiles
+// [tile_base[v], tile_base[v + 1]), row-major within the view.
+constexpr int kMaxViews = 16;
+
+struct TileMap {
+  int views;
+  int n_per_view;                     // n: Gaussians per view
+  int tiles_x[kMaxViews];
+  uint32_t tile_base[kMaxViews + 1];  // tile_base[views] = total tiles
+};
+
 // Gaussians covering more than this many tiles are queued and expanded by
 // whole warps spread over the grid in the binning kernels instead of by the
 // block that owns them (large splats cluster, which would leave a few blocks
@@ -20,14 +34,16 @@ struct CamView {
 constexpr uint32_t kBigTiles = 32;
 
 struct ProjectArgs {
-  uint32_t* big_queue;  // ids of Gaussians with more than kBigTiles tiles
+  uint32_t* big_queue;  // items with more than kBigTiles tiles
   uint32_t* big_len;    // queue length (zeroed before the launch)
-  int n;
+  int n;                // Gaussians
+  int views;
   const float *means, *log_scales, *quats, *logits, *sh;
   int sh_degree;
-  CamView cv;
   float near_z, dilation, alpha_min;
-  int tile_w, tile_h, tiles_x, tiles_y;
+  int tile_w, tile_h;
+  CamView cv[kMaxViews];
+  int tiles_x[kMaxViews], tiles_y[kMaxViews];
 };
 
 // projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
@@ -37,10 +53,12 @@ void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key,
 void launch_bin_prepare(int n, const float* mean2d, const float* extent, const float* depth, int tile_w, int tile_h,
                         int tiles_x, int tiles_y, uint32_t* depth_key, uint32_t* tiles_touched, ushort4* rects,
                         uint32_t* big_queue, uint32_t* big_len, cudaStream_t s);
-// g2d [n, 12] -> parameter gradients (+=) and per-block pose partials
+// g2d [V * n, 12] -> parameter gradients summed over the views (+=) and,
+// if pose_partials is non-null, per-block pose partials [blocks][V][6]
 int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales,
                        float* g_quats, float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s);
-void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s);
+// dL_dpose[v][k] += sum over blocks of partials[b][v][k]
+void launch_pose_reduce(const float* partials, int nblocks, int views, float* dL_dpose, cudaStream_t s);
 
 // Adam hyper-parameters as the kernels use them
 struct AdamArgs {
@@ -55,7 +73,8 @@ struct AdamArgs {
 void launch_step_increment(long long* step, cudaStream_t s);
 // set once per context: shared-memory limits of the fused kernel
 void init_project_kernels();
-// fused projection backward + Adam over the flat buffer (one view, one step)
+// fused projection backward + Adam over the flat buffer (gradients summed
+// over the views, one step)
 int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
                             const AdamArgs& ad, float* pose_partials, cudaStream_t s);
 int project_bwd_blocks(int n);
@@ -81,7 +100,7 @@ struct DupArgs {
   const uint32_t* sorted_ids;
   const uint32_t* tiles_touched;
   const ushort4* rects;
-  int tiles_x;
+  TileMap map;
   uint32_t* block_sums;  // scratch >= dup_blocks(n) + 1
   uint32_t* n_pairs;     // device total (clamped to capacity for the kernels)
   unsigned long long* n_pairs_full;  // device total before clamping
@@ -97,21 +116,22 @@ void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches);
 // counting-scatter binning with per-tile sorts (lists of at most kTileSortCap)
 constexpr int kTileSortCap = 4096;
 struct TileBinArgs {
-  int n;                      // Gaussians
-  const ushort4* rects;       // per Gaussian tile rectangle
-  const uint32_t* tiles;      // per Gaussian tile count
-  const uint32_t* zkey;       // per Gaussian float32 depth bits
-  int tiles_x, n_tiles, num_sms;
+  int n;                      // items (views x Gaussians)
+  const ushort4* rects;       // per item tile rectangle (view-local tile coordinates)
+  const uint32_t* tiles;      // per item tile count
+  const uint32_t* zkey;       // per item float32 depth bits
+  TileMap map;
+  int n_tiles, num_sms;
   uint32_t* counts;           // per tile
   uint32_t* offsets;          // per tile
   uint32_t* cursors;          // per tile
-  uint32_t* ids;              // per pair: Gaussian id (output, sorted per tile)
+  uint32_t* ids;              // per pair: item (output, sorted per tile)
   uint2* ranges;              // per tile (output)
   uint32_t capacity;          // pair slots in ids
   uint32_t* n_pairs;          // device: min(total, capacity)
   unsigned long long* stats;  // device: [0] total pairs, [1] longest list
   uint32_t* overflow;         // device flag: 1 = pairs over capacity, 2 = list over kTileSortCap
-  const uint32_t* big_queue;  // Gaussians with more than kBigTiles tiles
+  const uint32_t* big_queue;  // items with more than kBigTiles tiles
   const uint32_t* big_len;
 };
 int tile_sort_capacity();
@@ -122,26 +142,48 @@ void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
 void launch_tile_ranges(const uint32_t* sorted_tiles, const uint32_t* n_dev, uint32_t n_max, uint2* ranges,
                         int n_tiles, int num_sms, cudaStream_t s, int64_t* launches);
 
-// raster passes
+// raster passes: one CTA per global tile, visited in `order` when given
+// (the tile list sorted by descending list length) else in index order
+struct RasterView {
+  int width, height, tiles_x;
+  uint32_t tile_base;  // first global tile of the view
+  int64_t pix_base;    // first pixel of the view in the T_final / last buffers
+  float *color, *depth, *alpha;           // forward outputs (each nullable)
+  const float *dLdc, *dLdd, *dLda;        // backward inputs (dLda nullable)
+};
 struct RasterArgs {
-  int width, height, tile_w, tile_h, tiles_x, tiles_y;
+  int views, tile_w, tile_h;
+  uint32_t n_tiles;
   float bg[3];
   float alpha_max, alpha_min, t_eps;
   const uint2* ranges;
   const uint32_t* ids;
   const float4* feat;
+  const uint32_t* order;  // nullable
+  RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);
-void launch_raster_fwd(const RasterArgs& a, float* color, float* depth, float* alpha, float* T_final,
-                       int32_t* last, unsigned long long* counters, cudaStream_t s);
-void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, const float* dL_dcolor,
-                       const float* dL_ddepth, const float* dL_dalpha, float4* g2d, cudaStream_t s);
+void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsigned long long* counters,
+                       cudaStream_t s);
+void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s);
 
-// loss and optimiser
+// loss and optimiser: per view v, L_v = w_color mean |C - C^| + w_depth
+// mean over valid target depths |D - D^|; loss = sum over views of L_v
+struct LossView {
+  int npix;
+  int block_base;  // first partials block of the view
+  const float *color, *depth, *trgb, *tdep;
+  float *dLdc, *dLdd;
+};
+struct LossArgs {
+  int views, n_blocks;
+  float w_color, w_depth;
+  float* loss;
+  LossView v[kMaxViews];
+};
 int loss_blocks(int npix);
-void launch_loss(int H, int W, const float* color, const float* depth, const float* trgb, const float* tdep,
-                 float w_color, float w_depth, float* loss, float* dLdc, float* dLdd, float* partials,
-                 cudaStream_t s, int64_t* launches);
+// partials: >= 3 * n_blocks + kMaxViews floats
+void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* launches);
 void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],
                  float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero_grads,
                  cudaStream_t s);

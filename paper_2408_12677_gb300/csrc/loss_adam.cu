@@ -15,14 +15,31 @@ constexpr int kLossItems = 8;  // pixels per thread
 
 __device__ __forceinline__ float sgn(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
+// Block b of a batched launch belongs to the view v with
+// block_base[v] <= b < block_base[v + 1] and covers that view's pixels
+// [(b - block_base[v]) * kLossThreads * kLossItems, ...).
+__device__ __forceinline__ int loss_view_of(const LossArgs& a, int b) {
+  int v = 0;
+  for (int k = 1; k < a.views; ++k)
+    if (b >= a.v[k].block_base) v = k;
+  return v;
+}
+
 // Pass 1: per pixel |residuals| and sign gradients; per-block partial sums
 // (|colour residual| sum, |depth residual| sum over valid pixels, valid count).
-__global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(
-    int npix, const float* __restrict__ color, const float* __restrict__ depth, const float* __restrict__ trgb,
-    const float* __restrict__ tdep, float gscale_c, float* __restrict__ dLdc, float* __restrict__ dLdd,
-    float* __restrict__ partials) {
+__global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(const __grid_constant__ LossArgs a,
+                                                                     float* __restrict__ partials) {
+  const LossView& lv = a.v[loss_view_of(a, blockIdx.x)];
+  const int npix = lv.npix;
+  const float* __restrict__ color = lv.color;
+  const float* __restrict__ depth = lv.depth;
+  const float* __restrict__ trgb = lv.trgb;
+  const float* __restrict__ tdep = lv.tdep;
+  float* __restrict__ dLdc = lv.dLdc;
+  float* __restrict__ dLdd = lv.dLdd;
+  const float gscale_c = a.w_color / (3.f * (float)npix);
   float sc = 0.f, sd = 0.f, nv = 0.f;
-  const int base = blockIdx.x * kLossThreads * kLossItems + threadIdx.x;
+  const int base = (blockIdx.x - lv.block_base) * kLossThreads * kLossItems + threadIdx.x;
 #pragma unroll
   for (int j = 0; j < kLossItems; ++j) {
     const int p = base + j * kLossThreads;
@@ -60,42 +77,61 @@ __global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(
   }
 }
 
-// Pass 2 (one block of 256): fixed-order reduction of the partials -> loss and
-// the depth-gradient scale w_depth / n_valid (stored in scale[0]).  Each
-// thread sums a strided subset in order, then a fixed tree combines them, so
-// the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) loss_finalize_kernel(const float* __restrict__ partials, int nblocks, int npix,
-                                                            float w_color, float w_depth, float* __restrict__ loss,
+// Pass 2 (one block of 256): per view, a fixed-order reduction of its
+// partials -> L_v and the depth-gradient scale w_depth / n_valid (scale[v]);
+// loss = sum of L_v in view order.  Each thread sums a strided subset in
+// order, then a fixed tree combines them, so the result does not depend on
+// scheduling.
+__global__ void __launch_bounds__(256) loss_finalize_kernel(const __grid_constant__ LossArgs a,
+                                                            const float* __restrict__ partials,
                                                             float* __restrict__ scale) {
   __shared__ float red[3][256];
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  for (int b = threadIdx.x; b < nblocks; b += 256) {
-    a0 += partials[3 * b];
-    a1 += partials[3 * b + 1];
-    a2 += partials[3 * b + 2];
-  }
-  red[0][threadIdx.x] = a0;
-  red[1][threadIdx.x] = a1;
-  red[2][threadIdx.x] = a2;
-  __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + s];
-      red[1][threadIdx.x] += red[1][threadIdx.x + s];
-      red[2][threadIdx.x] += red[2][threadIdx.x + s];
+  float total = 0.f;
+  for (int v = 0; v < a.views; ++v) {
+    const int b0 = a.v[v].block_base;
+    const int b1 = v + 1 < a.views ? a.v[v + 1].block_base : a.n_blocks;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int b = b0 + threadIdx.x; b < b1; b += 256) {
+      a0 += partials[3 * b];
+      a1 += partials[3 * b + 1];
+      a2 += partials[3 * b + 2];
     }
+    __syncthreads();  // previous view done with red
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
     __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+      if ((int)threadIdx.x < s) {
+        red[0][threadIdx.x] += red[0][threadIdx.x + s];
+        red[1][threadIdx.x] += red[1][threadIdx.x + s];
+        red[2][threadIdx.x] += red[2][threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const float nv = red[2][0] > 0.f ? red[2][0] : 1.f;
+      total += a.w_color * red[0][0] / (3.f * (float)a.v[v].npix) + a.w_depth * red[1][0] / nv;
+      scale[v] = a.w_depth / nv;
+    }
   }
-  if (threadIdx.x == 0) {
-    const float nv = red[2][0] > 0.f ? red[2][0] : 1.f;
-    loss[0] = w_color * red[0][0] / (3.f * (float)npix) + w_depth * red[1][0] / nv;
-    scale[0] = w_depth / nv;
-  }
+  if (threadIdx.x == 0) a.loss[0] = total;
 }
 
-__global__ void scale_kernel(int n, float* __restrict__ x, const float* __restrict__ scale) {
-  const float s = scale[0];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] *= s;
+// Pass 3: dL/dD = scale[v] * sign, same block layout as pass 1
+__global__ void __launch_bounds__(kLossThreads) scale_kernel(const __grid_constant__ LossArgs a,
+                                                             const float* __restrict__ scale) {
+  const int v = loss_view_of(a, blockIdx.x);
+  const LossView& lv = a.v[v];
+  const float sv = scale[v];
+  float* __restrict__ dLdd = lv.dLdd;
+  const int base = (blockIdx.x - lv.block_base) * kLossThreads * kLossItems + threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < kLossItems; ++j) {
+    const int p = base + j * kLossThreads;
+    if (p >= lv.npix) break;
+    dLdd[p] *= sv;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -193,16 +229,12 @@ __global__ void export_projection_kernel(int n, const float4* __restrict__ feat,
 
 int loss_blocks(int npix) { return (npix + kLossThreads * kLossItems - 1) / (kLossThreads * kLossItems); }
 
-void launch_loss(int H, int W, const float* color, const float* depth, const float* trgb, const float* tdep,
-                 float w_color, float w_depth, float* loss, float* dLdc, float* dLdd, float* partials,
-                 cudaStream_t s, int64_t* launches) {
-  const int npix = H * W;
-  const int nb = loss_blocks(npix);
-  float* scale = partials + 3 * nb;
-  loss_partials_kernel<<<nb, kLossThreads, 0, s>>>(npix, color, depth, trgb, tdep, w_color / (3.f * (float)npix),
-                                                   dLdc, dLdd, partials);
-  loss_finalize_kernel<<<1, 256, 0, s>>>(partials, nb, npix, w_color, w_depth, loss, scale);
-  scale_kernel<<<std::min(1024, (npix + 255) / 256), 256, 0, s>>>(npix, dLdd, scale);
+void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* launches) {
+  if (a.n_blocks <= 0) return;
+  float* scale = partials + 3 * a.n_blocks;
+  loss_partials_kernel<<<a.n_blocks, kLossThreads, 0, s>>>(a, partials);
+  loss_finalize_kernel<<<1, 256, 0, s>>>(a, partials, scale);
+  scale_kernel<<<a.n_blocks, kLossThreads, 0, s>>>(a, scale);
   if (launches) *launches += 3;
 }
 

@@ -62,7 +62,13 @@ extern "C" gs_status gs_loss_l1_noalloc(const gs_camera* cam, const float* color
   if (dev < 0 || dev >= kMaxDevices) return GS_ERR_INVALID_ARG;
   float* scratch = nullptr;
   if (scratch_for(dev, &scratch) != cudaSuccess) return GS_ERR_CUDA;
-  gs::launch_loss(cam->height, cam->width, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
-                  dL_ddepth, scratch, (cudaStream_t)stream, nullptr);
+  gs::LossArgs la;
+  la.views = 1;
+  la.n_blocks = gs::loss_blocks((int)npix);
+  la.w_color = w_color;
+  la.w_depth = w_depth;
+  la.loss = loss;
+  la.v[0] = gs::LossView{(int)npix, 0, color, depth, target_rgb, target_depth, dL_dcolor, dL_ddepth};
+  gs::launch_loss(la, scratch, (cudaStream_t)stream, nullptr);
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

@@ -1,5 +1,7 @@
 // Projection of 3D Gaussians to 2D splats (Eq. 2-5) and its backward pass,
 // including the gradient w.r.t. the camera pose.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -90,8 +92,11 @@ __device__ __forceinline__ void geometry(const CamView& cv, float dilation, floa
 
 constexpr int kFwdThreads = 128;
 
+// One thread per Gaussian: its parameters are read once and projected into
+// every view of the batch (item v * n + i for view v).
 template <int D>
-__global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(ProjectArgs a, float4* __restrict__ feat,
+__global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_constant__ ProjectArgs a,
+                                                                  float4* __restrict__ feat,
                                                                   uint32_t* __restrict__ depth_key,
                                                                   uint32_t* __restrict__ tiles_touched,
                                                                   ushort4* __restrict__ rects) {
@@ -109,67 +114,71 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(ProjectArgs a,
   __syncthreads();
   const int i = base + threadIdx.x;
   if (i >= a.n) return;
-  const CamView& cv = a.cv;
   const float px = a.means[3 * i], py = a.means[3 * i + 1], pz = a.means[3 * i + 2];
-  // camera-space position and pixel mean in double-float (the float32 error of
-  // W p + t alone would move mu by ~1e-3 px at 1-2 m)
-  df Z = df_dot3_plus(cv.R[6], cv.R[7], cv.R[8], px, py, pz, cv.t[2]);
-  const float z = Z.hi;
-  if (!(z > a.near_z)) {
-    depth_key[i] = 0xFFFFFFFFu;
-    tiles_touched[i] = 0;
-    rects[i] = make_ushort4(0, 0, 0, 0);
-    feat[3 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    feat[3 * i + 1] = make_float4(0.f, 0.f, 0.f, -1e30f);
-    feat[3 * i + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return;
-  }
-  df X = df_dot3_plus(cv.R[0], cv.R[1], cv.R[2], px, py, pz, cv.t[0]);
-  df Y = df_dot3_plus(cv.R[3], cv.R[4], cv.R[5], px, py, pz, cv.t[1]);
-  df mux = df_add(df_mul_f(df_div(X, Z), cv.fx), df{cv.cx, 0.f});
-  df muy = df_add(df_mul_f(df_div(Y, Z), cv.fy), df{cv.cy, 0.f});
-
-  float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
-  float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
-  Geo g;
-  geometry(cv, a.dilation, px, py, pz, q4, ls, X.hi, Y.hi, z, g);
-
+  const float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
+  const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
   const float logit = a.logits[i];
   const float o = 1.f / (1.f + expf(-logit));
   const float log2o = log2f(o);
   // support of the blend test: q <= min(9, 2 ln(o / alpha_min)), widened a
   // little so that float32 rounding of the per-pixel test stays inside
-  float Q = fminf(9.f, 2.f * logf(o / a.alpha_min));
-  int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-  if (Q > 0.f && g.det > 0.f) {
-    float Qw = Q * 1.0001f + 1e-4f;
-    float ex = sqrtf(Qw * g.a) * 1.00001f + 1e-3f;
-    float ey = sqrtf(Qw * (g.b * g.b + g.det) / g.a) * 1.00001f + 1e-3f;
-    tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x, a.tiles_y, x0, y0,
-              x1, y1);
-  }
-  const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-  tiles_touched[i] = nt;
-  rects[i] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
-  depth_key[i] = __float_as_uint(z);
-  if (nt > kBigTiles) a.big_queue[atomicAdd(a.big_len, 1u)] = (uint32_t)i;
-
-  // view-dependent colour
-  float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
-  float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-  float Yb[16];
-  sh_basis(D, dx * inv, dy * inv, dz * inv, Yb);
+  const float Q = fminf(9.f, 2.f * logf(o / a.alpha_min));
   const float* shp = s_sh + threadIdx.x * RS;
-  float rgb[3] = {0.5f, 0.5f, 0.5f};
+
+  for (int v = 0; v < a.views; ++v) {
+    const CamView& cv = a.cv[v];
+    const size_t it = (size_t)v * a.n + i;
+    // camera-space position and pixel mean in double-float (the float32 error
+    // of W p + t alone would move mu by ~1e-3 px at 1-2 m)
+    df Z = df_dot3_plus(cv.R[6], cv.R[7], cv.R[8], px, py, pz, cv.t[2]);
+    const float z = Z.hi;
+    if (!(z > a.near_z)) {
+      depth_key[it] = 0xFFFFFFFFu;
+      tiles_touched[it] = 0;
+      rects[it] = make_ushort4(0, 0, 0, 0);
+      feat[3 * it] = make_float4(0.f, 0.f, 0.f, 0.f);
+      feat[3 * it + 1] = make_float4(0.f, 0.f, 0.f, -1e30f);
+      feat[3 * it + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    df X = df_dot3_plus(cv.R[0], cv.R[1], cv.R[2], px, py, pz, cv.t[0]);
+    df Y = df_dot3_plus(cv.R[3], cv.R[4], cv.R[5], px, py, pz, cv.t[1]);
+    df mux = df_add(df_mul_f(df_div(X, Z), cv.fx), df{cv.cx, 0.f});
+    df muy = df_add(df_mul_f(df_div(Y, Z), cv.fy), df{cv.cy, 0.f});
+
+    Geo g;
+    geometry(cv, a.dilation, px, py, pz, q4, ls, X.hi, Y.hi, z, g);
+
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (Q > 0.f && g.det > 0.f) {
+      float Qw = Q * 1.0001f + 1e-4f;
+      float ex = sqrtf(Qw * g.a) * 1.00001f + 1e-3f;
+      float ey = sqrtf(Qw * (g.b * g.b + g.det) / g.a) * 1.00001f + 1e-3f;
+      tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x[v], a.tiles_y[v], x0,
+                y0, x1, y1);
+    }
+    const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+    tiles_touched[it] = nt;
+    rects[it] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+    depth_key[it] = __float_as_uint(z);
+    if (nt > kBigTiles) a.big_queue[atomicAdd(a.big_len, 1u)] = (uint32_t)it;
+
+    // view-dependent colour
+    float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float Yb[16];
+    sh_basis(D, dx * inv, dy * inv, dz * inv, Yb);
+    float rgb[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    rgb[0] += Yb[k] * shp[3 * k];
-    rgb[1] += Yb[k] * shp[3 * k + 1];
-    rgb[2] += Yb[k] * shp[3 * k + 2];
+    for (int k = 0; k < K; ++k) {
+      rgb[0] += Yb[k] * shp[3 * k];
+      rgb[1] += Yb[k] * shp[3 * k + 1];
+      rgb[2] += Yb[k] * shp[3 * k + 2];
+    }
+    feat[3 * it] = make_float4(mux.hi, muy.hi, mux.lo, muy.lo);
+    feat[3 * it + 1] = make_float4(g.i0, g.k, g.i1, log2o);
+    feat[3 * it + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
   }
-  feat[3 * i] = make_float4(mux.hi, muy.hi, mux.lo, muy.lo);
-  feat[3 * i + 1] = make_float4(g.i0, g.k, g.i1, log2o);
-  feat[3 * i + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
 }
 
 __global__ void bin_prepare_kernel(int n, const float* __restrict__ mean2d, const float* __restrict__ extent,
@@ -354,10 +363,12 @@ __device__ __forceinline__ bool nonzero_record(const float4& G0, const float4& G
          (G1.z != 0.f) | (G2.x != 0.f) | (G2.y != 0.f) | (G2.z != 0.f);
 }
 
-// deterministic per-block partial sums of the pose gradient
-__device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float* __restrict__ pose_partials) {
+// deterministic per-block sum of the pose gradient into out[0..5]; every
+// thread of the block calls it
+__device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float* __restrict__ out) {
   __shared__ float red[kBwdThreads / 32][6];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // an earlier call is done reading red
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     float v = pose[k];
@@ -369,45 +380,72 @@ __device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float
   if (threadIdx.x < 6) {
     float s = 0.f;
     for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w][threadIdx.x];
-    pose_partials[6 * blockIdx.x + threadIdx.x] = s;
+    out[threadIdx.x] = s;
   }
 }
 
+// One thread per Gaussian: the gradient records of its items in every view
+// are turned into parameter gradients, summed over the views and added to
+// the gradient arrays.
 template <int D>
-__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(ProjectArgs a, const float4* __restrict__ g2d,
+__global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(const __grid_constant__ ProjectArgs a,
+                                                                  const float4* __restrict__ g2d,
                                                                   float* __restrict__ gm, float* __restrict__ gls,
                                                                   float* __restrict__ gq, float* __restrict__ glog,
                                                                   float* __restrict__ gsh,
                                                                   float* __restrict__ pose_partials) {
   constexpr int K = (D + 1) * (D + 1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (i < a.n) {
-    const float4 G0 = g2d[3 * (size_t)i], G1 = g2d[3 * (size_t)i + 1], G2 = g2d[3 * (size_t)i + 2];
-    if (nonzero_record(G0, G1, G2)) {
-      const float p[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
-      const float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
-      const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
-      GaussGrad<D> gg;
-      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, a.logits[i], a.sh + (size_t)i * K * 3, G0, G1, G2, gg);
-      glog[i] += gg.glogit;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        gm[3 * i + c] += gg.gm[c];
-        gls[3 * i + c] += gg.gls[c];
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) gq[4 * i + j] += gg.gq[j];
-      float* gshp = gsh + (size_t)i * K * 3;
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gshp[3 * k + c] += gg.Y[k] * gg.graw[c];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
+  const bool live = i < a.n;
+  float p[3] = {0.f, 0.f, 0.f}, q4[4] = {1.f, 0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f}, logit = 0.f;
+  if (live) {
+    for (int c = 0; c < 3; ++c) {
+      p[c] = a.means[3 * i + c];
+      ls[c] = a.log_scales[3 * i + c];
     }
+    for (int j = 0; j < 4; ++j) q4[j] = a.quats[4 * i + j];
+    logit = a.logits[i];
   }
-  block_pose_partial(pose, pose_partials);
+  float am[3] = {0.f, 0.f, 0.f}, als[3] = {0.f, 0.f, 0.f}, aq[4] = {0.f, 0.f, 0.f, 0.f}, alog = 0.f;
+  bool any = false;
+  for (int v = 0; v < a.views; ++v) {
+    float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (live) {
+      const size_t it = (size_t)v * a.n + i;
+      const float4 G0 = g2d[3 * it], G1 = g2d[3 * it + 1], G2 = g2d[3 * it + 2];
+      if (nonzero_record(G0, G1, G2)) {
+        any = true;
+        GaussGrad<D> gg;
+        gaussian_grad<D>(a.cv[v], a.dilation, p, q4, ls, logit, a.sh + (size_t)i * K * 3, G0, G1, G2, gg);
+        alog += gg.glogit;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          am[c] += gg.gm[c];
+          als[c] += gg.gls[c];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) aq[j] += gg.gq[j];
+        float* gshp = gsh + (size_t)i * K * 3;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) gshp[3 * k + c] += gg.Y[k] * gg.graw[c];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
+      }
+    }
+    if (pose_partials) block_pose_partial(pose, pose_partials + ((size_t)blockIdx.x * a.views + v) * 6);
+  }
+  if (live && any) {
+    glog[i] += alog;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      gm[3 * i + c] += am[c];
+      gls[3 * i + c] += als[c];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gq[4 * i + j] += aq[j];
+  }
 }
 
 // Bias corrections from the device step counter: 1 - beta^t = -expm1(t log beta),
@@ -428,16 +466,19 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 }
 
 // Backward of the projection fused with the Adam step, for one optimisation
-// iteration on one view.  A block owns 128 consecutive Gaussians:
+// iteration on a batch of views.  A block owns 128 consecutive Gaussians:
 //   1. its slices of the parameter array and of the two Adam moments (each
 //      slice contiguous in the flat layout) are copied to shared memory with
 //      cp.async, the parameters as a first group and the moments as a second,
 //      so the moment loads stay in flight during step 2;
-//   2. one thread per Gaussian turns its gradient record into parameter
-//      gradients, kept in shared memory (SH gradients in factored form
-//      Y_k * graw_c);
+//   2. one thread per Gaussian turns its gradient records (one per view)
+//      into parameter gradients summed over the views, kept in shared memory;
 //   3. coalesced sweeps apply Adam to every float and store p, m, v.
-// No gradient buffer is written or read.
+// No gradient buffer is written or read.  With one view the SH gradient is
+// kept in factored form (Y_k * graw_c) and the SH moments are staged too;
+// with several views the SH gradients are summed in shared memory rows and
+// the sweep reads the SH moments from global memory directly (coalesced),
+// which keeps the shared-memory footprint at three blocks per SM.
 constexpr int kFusedThreads = 128;
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
@@ -464,13 +505,25 @@ struct FusedSmem {
 };
 
 template <int D>
-__global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(ProjectArgs a,
+struct FusedSmemMulti {
+  static constexpr int K = (D + 1) * (D + 1);
+  static constexpr int NS = 3 * K;
+  static constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;
+  static constexpr int B = kFusedThreads;
+  float p[B * 11], m[B * 11], v[B * 11];
+  float g[B * 11];
+  float sp[B * RS];  // SH parameters, one row per Gaussian
+  float gs[B * RS];  // SH gradients summed over the views, same rows
+};
+
+template <int D, bool MULTI>
+__global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
                                                                          const float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
                                                                          float* __restrict__ pose_partials) {
   device_bias_corrections(ad);
-  using S = FusedSmem<D>;
+  using S = typename std::conditional<MULTI, FusedSmemMulti<D>, FusedSmem<D>>::type;
   constexpr int K = S::K, NS = S::NS, RS = S::RS, B = S::B;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S& sm = *reinterpret_cast<S*>(smem_raw);
@@ -498,9 +551,11 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(Project
       cp_async4(&sm.m[so[r] + e], M + g0[r] + e);
       cp_async4(&sm.v[so[r] + e], V + g0[r] + e);
     }
-  for (int e = t; e < cnt * NS; e += B) {
-    cp_async4(&sm.sm[e], M + gsh + e);
-    cp_async4(&sm.sv[e], V + gsh + e);
+  if constexpr (!MULTI) {
+    for (int e = t; e < cnt * NS; e += B) {
+      cp_async4(&sm.sm[e], M + gsh + e);
+      cp_async4(&sm.sv[e], V + gsh + e);
+    }
   }
   cp_async_commit();
   float4 G0 = make_float4(0.f, 0.f, 0.f, 0.f), G1 = G0, G2 = G0;
@@ -514,37 +569,68 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(Project
   __syncthreads();
 
   // 2. per-Gaussian gradients
-  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float pq[3], ls[3], q4[4];
   if (t < cnt) {
-    GaussGrad<D> gg;
-    if (nonzero_record(G0, G1, G2)) {
-      const float p[3] = {sm.p[3 * t], sm.p[3 * t + 1], sm.p[3 * t + 2]};
-      const float ls[3] = {sm.p[3 * B + 3 * t], sm.p[3 * B + 3 * t + 1], sm.p[3 * B + 3 * t + 2]};
-      const float q4[4] = {sm.p[6 * B + 4 * t], sm.p[6 * B + 4 * t + 1], sm.p[6 * B + 4 * t + 2],
-                           sm.p[6 * B + 4 * t + 3]};
-      gaussian_grad<D>(a.cv, a.dilation, p, q4, ls, sm.p[10 * B + t], sm.sp + t * RS, G0, G1, G2, gg);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) gg.gm[c] = gg.gls[c] = gg.graw[c] = 0.f;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) gg.gq[j] = 0.f;
-      gg.glogit = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) gg.Y[k] = 0.f;
+    for (int c = 0; c < 3; ++c) {
+      pq[c] = sm.p[3 * t + c];
+      ls[c] = sm.p[3 * B + 3 * t + c];
     }
+    for (int j = 0; j < 4; ++j) q4[j] = sm.p[6 * B + 4 * t + j];
+  }
+  float am[3] = {0.f, 0.f, 0.f}, als[3] = {0.f, 0.f, 0.f}, aq[4] = {0.f, 0.f, 0.f, 0.f}, alog = 0.f;
+  if constexpr (MULTI) {
+    if (t < cnt)
+      for (int e = 0; e < NS; ++e) sm.gs[t * RS + e] = 0.f;
+  }
+  for (int v = 0; v < a.views; ++v) {
+    float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (t < cnt) {
+      if (v > 0) {
+        const int64_t it = (int64_t)v * N + base + t;
+        G0 = g2d[3 * it];
+        G1 = g2d[3 * it + 1];
+        G2 = g2d[3 * it + 2];
+      }
+      GaussGrad<D> gg;
+      const bool nz = nonzero_record(G0, G1, G2);
+      if (nz) {
+        gaussian_grad<D>(a.cv[v], a.dilation, pq, q4, ls, sm.p[10 * B + t], sm.sp + t * RS, G0, G1, G2, gg);
+        alog += gg.glogit;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          am[c] += gg.gm[c];
+          als[c] += gg.gls[c];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) aq[j] += gg.gq[j];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pose[k] = gg.pose[k];
+      }
+      if constexpr (MULTI) {
+        if (nz) {
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm.gs[t * RS + 3 * k + c] += gg.Y[k] * gg.graw[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.graw[t][c] = nz ? gg.graw[c] : 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) sm.Y[t][k] = nz ? gg.Y[k] : 0.f;
+      }
+    }
+    if (pose_partials) block_pose_partial(pose, pose_partials + ((size_t)blockIdx.x * a.views + v) * 6);
+  }
+  if (t < cnt) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      sm.g[3 * t + c] = gg.gm[c];
-      sm.g[3 * B + 3 * t + c] = gg.gls[c];
-      sm.graw[t][c] = gg.graw[c];
+      sm.g[3 * t + c] = am[c];
+      sm.g[3 * B + 3 * t + c] = als[c];
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sm.g[6 * B + 4 * t + j] = gg.gq[j];
-    sm.g[10 * B + t] = gg.glogit;
-#pragma unroll
-    for (int k = 0; k < K; ++k) sm.Y[t][k] = gg.Y[k];
+    for (int j = 0; j < 4; ++j) sm.g[6 * B + 4 * t + j] = aq[j];
+    sm.g[10 * B + t] = alog;
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -566,32 +652,43 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(Project
   for (int e = t; e < cnt * NS; e += B) {
     const int gi = e / NS, rr = e - gi * NS;
     const int k = rr / 3, c = rr - 3 * k;
-    float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e];
-    adam_update(p, sm.Y[gi][k] * sm.graw[gi][c], m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
     const int64_t f = gsh + e;
+    float p = sm.sp[gi * RS + rr], m, v, g;
+    if constexpr (MULTI) {
+      m = M[f];
+      v = V[f];
+      g = sm.gs[gi * RS + rr];
+    } else {
+      m = sm.sm[e];
+      v = sm.sv[e];
+      g = sm.Y[gi][k] * sm.graw[gi][c];
+    }
+    adam_update(p, g, m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
     P[f] = p;
     M[f] = m;
     V[f] = v;
   }
-  block_pose_partial(pose, pose_partials);
 }
 
-__global__ void pose_reduce_kernel(const float* __restrict__ partials, int nblocks, float* __restrict__ out) {
+// one block per view: dL_dpose[v] += sum over blocks b of partials[b][v]
+__global__ void pose_reduce_kernel(const float* __restrict__ partials, int nblocks, int views,
+                                   float* __restrict__ out) {
   __shared__ float red[32][6];
+  const int v = blockIdx.x;
   float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
-    for (int k = 0; k < 6; ++k) acc[k] += partials[6 * b + k];
+    for (int k = 0; k < 6; ++k) acc[k] += partials[((size_t)b * views + v) * 6 + k];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < 6; ++k) {
-    float v = acc[k];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red[wid][k] = v;
+    float x = acc[k];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[wid][k] = x;
   }
   __syncthreads();
   if (threadIdx.x < 6) {
     float s = 0.f;
     for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w][threadIdx.x];
-    out[threadIdx.x] += s;
+    out[6 * v + threadIdx.x] += s;
   }
 }
 
@@ -638,34 +735,48 @@ int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* para
   static_assert(kFusedThreads == kBwdThreads, "pose partial buffer is sized for kBwdThreads blocks");
   const int nb = project_bwd_blocks(a.n);
   if (nb == 0) return 0;
-#define GS_FUSED(D_)                                                                                      \
-  project_bwd_adam_kernel<D_><<<nb, kFusedThreads, (int)sizeof(FusedSmem<D_>), s>>>(a, g2d, params, m, v, ad, \
-                                                                                   pose_partials)
-  switch (a.sh_degree) {
-    case 0: GS_FUSED(0); break;
-    case 1: GS_FUSED(1); break;
-    case 2: GS_FUSED(2); break;
-    default: GS_FUSED(3); break;
+#define GS_FUSED(D_, M_, S_)                                                                                  \
+  project_bwd_adam_kernel<D_, M_><<<nb, kFusedThreads, (int)sizeof(S_<D_>), s>>>(a, g2d, params, m, v, ad, \
+                                                                                 pose_partials)
+  if (a.views == 1) {
+    switch (a.sh_degree) {
+      case 0: GS_FUSED(0, false, FusedSmem); break;
+      case 1: GS_FUSED(1, false, FusedSmem); break;
+      case 2: GS_FUSED(2, false, FusedSmem); break;
+      default: GS_FUSED(3, false, FusedSmem); break;
+    }
+  } else {
+    switch (a.sh_degree) {
+      case 0: GS_FUSED(0, true, FusedSmemMulti); break;
+      case 1: GS_FUSED(1, true, FusedSmemMulti); break;
+      case 2: GS_FUSED(2, true, FusedSmemMulti); break;
+      default: GS_FUSED(3, true, FusedSmemMulti); break;
+    }
   }
 #undef GS_FUSED
   return nb;
 }
 
 void init_project_kernels() {
-  cudaFuncSetAttribute(project_bwd_adam_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(FusedSmem<0>));
-  cudaFuncSetAttribute(project_bwd_adam_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(FusedSmem<1>));
-  cudaFuncSetAttribute(project_bwd_adam_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(FusedSmem<2>));
-  cudaFuncSetAttribute(project_bwd_adam_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(FusedSmem<3>));
+#define GS_ATTR(D_, M_, S_)                                                                           \
+  cudaFuncSetAttribute(project_bwd_adam_kernel<D_, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                       (int)sizeof(S_<D_>))
+  GS_ATTR(0, false, FusedSmem);
+  GS_ATTR(1, false, FusedSmem);
+  GS_ATTR(2, false, FusedSmem);
+  GS_ATTR(3, false, FusedSmem);
+  GS_ATTR(0, true, FusedSmemMulti);
+  GS_ATTR(1, true, FusedSmemMulti);
+  GS_ATTR(2, true, FusedSmemMulti);
+  GS_ATTR(3, true, FusedSmemMulti);
+#undef GS_ATTR
 }
 
 void launch_step_increment(long long* step, cudaStream_t s) { step_increment_kernel<<<1, 1, 0, s>>>(step); }
 
-void launch_pose_reduce(const float* partials, int nblocks, float* dL_dpose, cudaStream_t s) {
-  pose_reduce_kernel<<<1, 256, 0, s>>>(partials, nblocks, dL_dpose);
+void launch_pose_reduce(const float* partials, int nblocks, int views, float* dL_dpose, cudaStream_t s) {
+  if (nblocks <= 0 || views <= 0) return;
+  pose_reduce_kernel<<<views, 256, 0, s>>>(partials, nblocks, views, dL_dpose);
 }
 
 }  // namespace gs

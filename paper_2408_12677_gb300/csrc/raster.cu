@@ -69,28 +69,45 @@ __device__ __forceinline__ bool make_entry(float4 f0, float4 f1, float4 f2, floa
   return mlx + ex >= bx + 0.5f && mlx - ex <= bx + 7.5f && mly + ey >= by + 0.5f && mly - ey <= by + 7.5f;
 }
 
+// Tile, view and pixel origin of the CTA: blockIdx.x indexes the tile visit
+// order (or the tiles directly), global tiles map to views by tile_base.
+struct TileJob {
+  int v;       // view
+  int ox, oy;  // pixel origin of the tile within the view
+  uint2 range;
+};
+template <int TW, int TH>
+__device__ __forceinline__ TileJob tile_job(const RasterArgs& a) {
+  const uint32_t tile = a.order ? a.order[blockIdx.x] : blockIdx.x;
+  int v = 0;
+  for (int k = 1; k < a.views; ++k)
+    if (tile >= a.v[k].tile_base) v = k;
+  const int lt = (int)(tile - a.v[v].tile_base);
+  const int tx = lt % a.v[v].tiles_x, ty = lt / a.v[v].tiles_x;
+  return TileJob{v, tx * TW, ty * TH, a.ranges[tile]};
+}
+
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, const uint2* __restrict__ ranges,
-                                                              const uint32_t* __restrict__ ids,
-                                                              const float4* __restrict__ feat,
-                                                              float* __restrict__ color, float* __restrict__ depth,
-                                                              float* __restrict__ alpha,
-                                                              float* __restrict__ T_final,
-                                                              int32_t* __restrict__ last_out,
+__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
+                                                              float* __restrict__ T_final_all,
+                                                              int32_t* __restrict__ last_all,
                                                               unsigned long long* __restrict__ counters) {
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
-  const int tile = blockIdx.x;
-  const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  const TileJob job = tile_job<TW, TH>(a);
+  const RasterView& vw = a.v[job.v];
+  const int width = vw.width, height = vw.height;
+  const uint32_t* __restrict__ ids = a.ids;
+  const float4* __restrict__ feat = a.feat;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
-  const int px = tx * TW + lx, py0 = ty * TH + ly0, py1 = ty * TH + ly1;
-  const bool in0 = px < rp.width && py0 < rp.height, in1 = px < rp.width && py1 < rp.height;
+  const int px = job.ox + lx, py0 = job.oy + ly0, py1 = job.oy + ly1;
+  const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
   const float plx = (float)lx + 0.5f, ply0 = (float)ly0 + 0.5f, ply1 = (float)ly1 + 0.5f;
-  const float ox = (float)(tx * TW), oy = (float)(ty * TH), bx = (float)bxi, by = (float)byi;
-  const uint2 r = ranges[tile];
+  const float ox = (float)job.ox, oy = (float)job.oy, bx = (float)bxi, by = (float)byi;
+  const uint2 r = job.range;
   const int n = (int)(r.y - r.x);
   Entry* buf = s_e[warp];
 
@@ -174,9 +191,14 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
       atomicAdd(&counters[1], vv);
     }
   }
-  const size_t HW = (size_t)rp.width * rp.height;
+  const size_t HW = (size_t)width * height;
+  float* __restrict__ color = vw.color;
+  float* __restrict__ depth = vw.depth;
+  float* __restrict__ alpha = vw.alpha;
+  float* __restrict__ T_final = T_final_all + vw.pix_base;
+  int32_t* __restrict__ last_out = last_all + vw.pix_base;
   if (in0) {
-    const size_t p = (size_t)py0 * rp.width + px;
+    const size_t p = (size_t)py0 * width + px;
     if (color) {
       color[p] = R0 + T0 * rp.bg[0];
       color[HW + p] = G0 + T0 * rp.bg[1];
@@ -188,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(RasterParams rp, c
     last_out[p] = last0;
   }
   if (in1) {
-    const size_t p = (size_t)py1 * rp.width + px;
+    const size_t p = (size_t)py1 * width + px;
     if (color) {
       color[p] = R1 + T1 * rp.bg[0];
       color[HW + p] = G1 + T1 * rp.bg[1];
@@ -288,28 +310,36 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
 }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(
-    RasterParams rp, const uint2* __restrict__ ranges, const uint32_t* __restrict__ ids,
-    const float4* __restrict__ feat, const float* __restrict__ T_final, const int32_t* __restrict__ last_in,
-    const float* __restrict__ dLdc, const float* __restrict__ dLdd, const float* __restrict__ dLda,
-    float* __restrict__ g2d) {
+__global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_constant__ RasterArgs a,
+                                                                 RasterParams rp,
+                                                                 const float* __restrict__ T_final_all,
+                                                                 const int32_t* __restrict__ last_all,
+                                                                 float* __restrict__ g2d) {
   constexpr int WX = TW / 8;
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
   __shared__ uint32_t s_id[kThreads / 32][32];
   __shared__ __align__(16) float4 s_raw[kThreads / 32][2][32][3];
   __shared__ uint32_t s_gid[kThreads / 32][2][32];
-  const int tile = blockIdx.x;
-  const int tx = tile % rp.tiles_x, ty = tile / rp.tiles_x;
+  const TileJob job = tile_job<TW, TH>(a);
+  const RasterView& vw = a.v[job.v];
+  const int width = vw.width, height = vw.height;
+  const uint32_t* __restrict__ ids = a.ids;
+  const float4* __restrict__ feat = a.feat;
+  const float* __restrict__ T_final = T_final_all + vw.pix_base;
+  const int32_t* __restrict__ last_in = last_all + vw.pix_base;
+  const float* __restrict__ dLdc = vw.dLdc;
+  const float* __restrict__ dLdd = vw.dLdd;
+  const float* __restrict__ dLda = vw.dLda;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
-  const int px = tx * TW + lx, py0 = ty * TH + ly0, py1 = ty * TH + ly1;
-  const bool in0 = px < rp.width && py0 < rp.height, in1 = px < rp.width && py1 < rp.height;
+  const int px = job.ox + lx, py0 = job.oy + ly0, py1 = job.oy + ly1;
+  const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
   const float plx = (float)lx + 0.5f, ply0 = (float)ly0 + 0.5f, ply1 = (float)ly1 + 0.5f;
-  const float ox = (float)(tx * TW), oy = (float)(ty * TH), bx = (float)bxi, by = (float)byi;
-  const uint2 r = ranges[tile];
-  const size_t HW = (size_t)rp.width * rp.height;
+  const float ox = (float)job.ox, oy = (float)job.oy, bx = (float)bxi, by = (float)byi;
+  const uint2 r = job.range;
+  const size_t HW = (size_t)width * height;
   Entry* buf = s_e[warp];
   uint32_t* bid = s_id[warp];
 
@@ -318,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(
   float T1 = 1.f, c10 = 0.f, c11 = 0.f, c12 = 0.f, d1 = 0.f, a1 = 0.f;
   int last0 = 0, last1 = 0;
   if (in0) {
-    const size_t p = (size_t)py0 * rp.width + px;
+    const size_t p = (size_t)py0 * width + px;
     T0 = T_final[p];
     last0 = last_in[p];
     c00 = dLdc[p];
@@ -328,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(
     a0 = dLda ? dLda[p] : 0.f;
   }
   if (in1) {
-    const size_t p = (size_t)py1 * rp.width + px;
+    const size_t p = (size_t)py1 * width + px;
     T1 = T_final[p];
     last1 = last_in[p];
     c10 = dLdc[p];
@@ -408,12 +438,10 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(
 
 RasterParams make_params(const RasterArgs& a) {
   RasterParams rp;
-  rp.width = a.width;
-  rp.height = a.height;
+  rp.width = rp.height = 0;  // per view, from the view table
   rp.tile_w = a.tile_w;
   rp.tile_h = a.tile_h;
-  rp.tiles_x = a.tiles_x;
-  rp.tiles_y = a.tiles_y;
+  rp.tiles_x = rp.tiles_y = 0;
   for (int c = 0; c < 3; ++c) rp.bg[c] = a.bg[c];
   rp.alpha_max = a.alpha_max;
   rp.log2_alpha_min = log2f(a.alpha_min);
@@ -428,14 +456,12 @@ bool raster_shape_supported(int tw, int th) {
   return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8);
 }
 
-void launch_raster_fwd(const RasterArgs& a, float* color, float* depth, float* alpha, float* T_final,
-                       int32_t* last, unsigned long long* counters, cudaStream_t s) {
-  const int nt = a.tiles_x * a.tiles_y;
+void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsigned long long* counters,
+                       cudaStream_t s) {
+  const int nt = (int)a.n_tiles;
   if (nt == 0) return;
   RasterParams rp = make_params(a);
-#define GS_FWD(TW_, TH_, C_)                                                                               \
-  raster_fwd_kernel<TW_, TH_, C_><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, color, depth, alpha, T_final, \
-                                                         last, counters)
+#define GS_FWD(TW_, TH_, C_) raster_fwd_kernel<TW_, TH_, C_><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters)
   if (counters) {
     if (a.tile_w == 16) GS_FWD(16, 16, true);
     else if (a.tile_w == 8) GS_FWD(8, 32, true);
@@ -448,20 +474,16 @@ void launch_raster_fwd(const RasterArgs& a, float* color, float* depth, float* a
 #undef GS_FWD
 }
 
-void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, const float* dL_dcolor,
-                       const float* dL_ddepth, const float* dL_dalpha, float4* g2d, cudaStream_t s) {
-  const int nt = a.tiles_x * a.tiles_y;
+void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s) {
+  const int nt = (int)a.n_tiles;
   if (nt == 0) return;
   RasterParams rp = make_params(a);
   if (a.tile_w == 16)
-    raster_bwd_kernel<16, 16><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                      dL_ddepth, dL_dalpha, (float*)g2d);
+    raster_bwd_kernel<16, 16><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
   else if (a.tile_w == 8)
-    raster_bwd_kernel<8, 32><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                     dL_ddepth, dL_dalpha, (float*)g2d);
+    raster_bwd_kernel<8, 32><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
   else
-    raster_bwd_kernel<32, 8><<<nt, kThreads, 0, s>>>(rp, a.ranges, a.ids, a.feat, T_final, last, dL_dcolor,
-                                                     dL_ddepth, dL_dalpha, (float*)g2d);
+    raster_bwd_kernel<32, 8><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
 }
 
 }  // namespace gs

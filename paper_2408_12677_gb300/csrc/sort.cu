@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(kScanThreads) dup_scan_kernel(uint32_t* __rest
 
 __global__ void __launch_bounds__(kDupThreads) dup_write_kernel(
     int n, const uint32_t* __restrict__ sorted_ids, const uint32_t* __restrict__ tiles,
-    const ushort4* __restrict__ rects, int tiles_x, const uint32_t* __restrict__ block_offsets,
-    uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals, uint32_t capacity, uint32_t* overflow) {
+    const ushort4* __restrict__ rects, const __grid_constant__ TileMap map,
+    const uint32_t* __restrict__ block_offsets, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
+    uint32_t capacity, uint32_t* overflow) {
   const int base = blockIdx.x * kDupChunk + threadIdx.x * kDupItems;
   uint32_t cnt[kDupItems];
   uint32_t id[kDupItems];
@@ -225,10 +226,13 @@ __global__ void __launch_bounds__(kDupThreads) dup_write_kernel(
   for (int j = 0; j < kDupItems; ++j) {
     if (cnt[j] == 0) continue;
     const ushort4 r = rects[id[j]];
+    const int v = map.views == 1 ? 0 : (int)(id[j] / (uint32_t)map.n_per_view);
+    const uint32_t tbase = map.tile_base[v];
+    const int tiles_x = map.tiles_x[v];
     for (int ty = r.y; ty < r.w; ++ty)
       for (int tx = r.x; tx < r.z; ++tx) {
         if (off < capacity) {
-          tile_keys[off] = (uint32_t)(ty * tiles_x + tx);
+          tile_keys[off] = tbase + (uint32_t)(ty * tiles_x + tx);
           vals[off] = id[j];
         } else {
           over = true;
@@ -320,7 +324,7 @@ void launch_dup_count_scan(const DupArgs& a, cudaStream_t s, int64_t* launches) 
 void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches) {
   const int nb = dup_blocks(a.n);
   if (nb == 0) return;
-  dup_write_kernel<<<nb, kDupThreads, 0, s>>>(a.n, a.sorted_ids, a.tiles_touched, a.rects, a.tiles_x,
+  dup_write_kernel<<<nb, kDupThreads, 0, s>>>(a.n, a.sorted_ids, a.tiles_touched, a.rects, a.map,
                                               a.block_sums, a.tile_keys, a.vals, a.capacity, a.overflow);
   if (launches) *launches += 1;
 }

@@ -24,22 +24,33 @@ constexpr int kBinWarps = kBinThreads / 32;
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 256;
 
-// Calls f(gaussian, tile, active) for every tile of every Gaussian's
-// rectangle.  Gaussians with more than kBigTiles tiles come from the queue
+// Global tile of tile (tx, ty) of the view that item `it` belongs to.
+struct ItemTiles {
+  uint32_t base, stride;  // tile_base[v], tiles_x[v]
+};
+__device__ __forceinline__ ItemTiles item_tiles(const TileMap& map, uint32_t it) {
+  if (map.views == 1) return ItemTiles{0u, (uint32_t)map.tiles_x[0]};
+  const int v = (int)(it / (uint32_t)map.n_per_view);
+  return ItemTiles{map.tile_base[v], (uint32_t)map.tiles_x[v]};
+}
+
+// Calls f(item, global tile, active) for every tile of every item's
+// rectangle.  Items with more than kBigTiles tiles come from the queue
 // the projection built (see the end); the others are expanded by their
-// block, 256 consecutive Gaussians at a time: a block
-// scan of their tile counts gives each Gaussian's first pair, and the block's
-// threads take consecutive pairs (owner found by binary search over the
-// prefix in shared memory), so one large splat is spread over the whole block
-// and large splats clustered in one region are averaged over 256 Gaussians.
+// block, 256 consecutive items at a time: a block scan of their tile counts
+// gives each item's first pair, and the block's threads take consecutive
+// pairs (owner found by binary search over the prefix in shared memory), so
+// one large splat is spread over the whole block and large splats clustered
+// in one region are averaged over 256 items.
 // `active` is the mask of lanes of the calling warp that call f together.
 template <class F>
 __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__ rects,
-                                              const uint32_t* __restrict__ tiles, int tiles_x,
+                                              const uint32_t* __restrict__ tiles, const TileMap& map,
                                               const uint32_t* __restrict__ big_queue,
                                               const uint32_t* __restrict__ big_len, F f) {
   __shared__ uint32_t s_excl[kBinThreads];
   __shared__ ushort4 s_rect[kBinThreads];
+  __shared__ ItemTiles s_map[kBinThreads];
   __shared__ uint32_t s_wsum[kBinWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int base = blockIdx.x * kBinThreads; base < n; base += gridDim.x * kBinThreads) {
@@ -65,6 +76,7 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
     }
     s_excl[threadIdx.x] = wpre + incl - cnt;
     s_rect[threadIdx.x] = r;
+    s_map[threadIdx.x] = item_tiles(map, (uint32_t)min(g, n - 1));
     __syncthreads();
     for (uint32_t k0 = 0; k0 < total; k0 += kBinThreads) {
       const uint32_t k = k0 + threadIdx.x;
@@ -75,13 +87,14 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
       for (int step = kBinThreads / 2; step > 0; step >>= 1)
         if (s_excl[o + step] <= k) o += step;
       const ushort4 ro = s_rect[o];
+      const ItemTiles mt = s_map[o];
       const uint32_t local = k - s_excl[o];
       const uint32_t width = (uint32_t)(ro.z - ro.x);
       const uint32_t ty = ro.y + local / width, tx = ro.x + local % width;
-      f(base + o, ty * (uint32_t)tiles_x + tx, active);
+      f(base + o, mt.base + ty * mt.stride + tx, active);
     }
   }
-  // large splats: warp w of the grid expands queued Gaussians w, w + W, ...
+  // large splats: warp w of the grid expands queued items w, w + W, ...
   // spreading each one's tiles over its lanes (no shared cursor: one address
   // hit by every warp would serialise)
   const uint32_t nbig = *big_len;
@@ -91,13 +104,14 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
     const uint32_t g = big_queue[item];
     const ushort4 ro = rects[g];
     const uint32_t cnt = tiles[g];
+    const ItemTiles mt = item_tiles(map, g);
     const uint32_t width = (uint32_t)(ro.z - ro.x);
     for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
       const uint32_t k = k0 + lane;
       const unsigned active = __ballot_sync(0xFFFFFFFFu, k < cnt);
       if (k >= cnt) break;
       const uint32_t ty = ro.y + k / width, tx = ro.x + k % width;
-      f((int)g, ty * (uint32_t)tiles_x + tx, active);
+      f((int)g, mt.base + ty * mt.stride + tx, active);
     }
   }
 }
@@ -116,8 +130,8 @@ __device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter,
   return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-__global__ void __launch_bounds__(kBinThreads) tile_count_kernel(TileBinArgs a) {
-  for_each_pair(a.n, a.rects, a.tiles, a.tiles_x, a.big_queue, a.big_len,
+__global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_constant__ TileBinArgs a) {
+  for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                 [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
 }
 
@@ -167,9 +181,9 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
   }
 }
 
-__global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(TileBinArgs a) {
+__global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_constant__ TileBinArgs a) {
   bool over = false;
-  for_each_pair(a.n, a.rects, a.tiles, a.tiles_x, a.big_queue, a.big_len,
+  for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                 [&](int g, uint32_t t, unsigned active) {
                   const uint32_t pos = warp_agg_inc(a.cursors, t, active);
                   if (pos < a.capacity)

@@ -7,6 +7,8 @@
 * ``Trainer``         one optimisation iteration of GSFusion's online
                       optimisation (Sec. III-B.3) through the ABI:
                       gs_render_fwd -> gs_loss_l1 -> gs_render_bwd -> gs_adam_step.
+* ``BatchedTrainer``  the same iteration over several views of one map in
+                      one batched pass (one Adam step on the summed loss).
 * ``render``          a torch.autograd.Function around gs_render_fwd /
                       gs_render_bwd (gradients for every parameter array and,
                       through a zero pose twist, the camera pose).
@@ -199,6 +201,114 @@ class Trainer:
 
     def check_capacity(self):
         """Raises GsError(GS_ERR_CAPACITY) if a no-sync pass dropped pairs."""
+        abi.gs_sync_status(self.ctx.handle)
+
+
+class BatchedTrainer:
+    """Several views, one map: one batched iteration per ``step``.
+
+    ``views`` is a list of (camera, R_cw, t_cw).  A step renders every view
+    (gs_render_fwd_batched), scores it (gs_loss_l1_batched: the sum of the
+    per-view losses) and runs the backward pass of all views fused with one
+    Adam step on the summed gradient (gs_render_bwd_adam_batched).
+    ``step_sequential`` computes the same iteration with the single-view
+    calls, one view at a time (gradients accumulated, then gs_adam_step)."""
+
+    def __init__(self, model: GaussianModel, views, raster_cfg=None, adam_cfg=None, w_color=0.8, w_depth=0.2,
+                 ctx: Context | None = None, device: int = 0):
+        self.model = model
+        self.ctx = ctx or Context(device)
+        self.cam_list = list(c for c, _, _ in views)
+        self.cams = [camera_struct(c) for c, _, _ in views]
+        self.vms = [abi.make_viewmat(R, t) for _, R, t in views]
+        self.rcfg = raster_cfg or abi.raster_cfg()
+        self.acfg = adam_cfg or abi.adam_cfg(zero_grads=1)
+        self.w_color, self.w_depth = float(w_color), float(w_depth)
+        dev = model.flat.device
+        self.color = [torch.empty((3, c.height, c.width), device=dev) for c in self.cam_list]
+        self.depth = [torch.empty((c.height, c.width), device=dev) for c in self.cam_list]
+        self.alpha = [torch.empty((c.height, c.width), device=dev) for c in self.cam_list]
+        self.dLdc = [torch.empty((3, c.height, c.width), device=dev) for c in self.cam_list]
+        self.dLdd = [torch.empty((c.height, c.width), device=dev) for c in self.cam_list]
+        self.loss = torch.zeros(1, device=dev)
+        self.loss_views = torch.zeros(len(views), device=dev)  # per-view losses of step_sequential
+        self.step_count = 0
+        self._g = model.gaussians()
+        self._gr = model.grads()
+
+    @property
+    def n_views(self) -> int:
+        return len(self.cams)
+
+    @property
+    def n_pixels(self) -> int:
+        return sum(c.width * c.height for c in self.cam_list)
+
+    def forward(self, stream=None):
+        abi.gs_render_fwd_batched(self.ctx.handle, self._g, self.cams, self.vms, self.rcfg, self.color, self.depth,
+                                  self.alpha, stream)
+
+    def _iteration(self, targets_rgb, targets_depth, step, stream=None):
+        h = self.ctx.handle
+        m = self.model
+        self.forward(stream)
+        abi.gs_loss_l1_batched(h, self.cams, self.color, self.depth, targets_rgb, targets_depth, self.w_color,
+                               self.w_depth, self.loss, self.dLdc, self.dLdd, stream)
+        abi.gs_render_bwd_adam_batched(h, self._g, self.cams, self.vms, self.rcfg, self.dLdc, self.dLdd, None, m.flat,
+                                       m.m, m.v, self.acfg, step, None, stream)
+
+    def step(self, targets_rgb, targets_depth, stream=None):
+        """One batched iteration; the summed loss stays on the device in ``self.loss``."""
+        self.step_count += 1
+        self._iteration(targets_rgb, targets_depth, self.step_count, stream)
+        return self.loss
+
+    def step_sequential(self, targets_rgb, targets_depth, stream=None):
+        """The same iteration view by view with the single-view calls: per view
+        gs_render_fwd, gs_loss_l1 and gs_render_bwd (gradients accumulate in
+        the model's gradient buffer), then one gs_adam_step, which clears it.
+        Returns the per-view losses (device [V]; their sum is the batched loss)."""
+        h = self.ctx.handle
+        m = self.model
+        for v in range(self.n_views):
+            abi.gs_render_fwd(h, self._g, self.cams[v], self.vms[v], self.rcfg, self.color[v], self.depth[v],
+                              self.alpha[v], stream)
+            abi.gs_loss_l1(h, self.cams[v], self.color[v], self.depth[v], targets_rgb[v], targets_depth[v],
+                           self.w_color, self.w_depth, self.loss_views[v:v + 1], self.dLdc[v], self.dLdd[v], stream)
+            abi.gs_render_bwd(h, self._g, self.cams[v], self.vms[v], self.rcfg, self.dLdc[v], self.dLdd[v], None,
+                              self._gr, None, stream)
+        self.step_count += 1
+        abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
+        return self.loss_views
+
+    def capture(self, targets_rgb, targets_depth, pair_headroom: float = 1.5):
+        """Record one batched iteration into a CUDA graph (``replay`` runs it),
+        as Trainer.capture does for one view."""
+        h = self.ctx.handle
+        self.forward()
+        torch.cuda.synchronize()
+        pairs = abi.gs_get_stats(h)["n_pairs"]
+        abi.gs_ctx_reserve(h, self.model.n * self.n_views, self.n_pixels, int(pairs * pair_headroom) + 4096)
+        abi.gs_ctx_set_sync(h, False)
+        abi.gs_ctx_set_adam_step(h, self.step_count)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._iteration(targets_rgb, targets_depth, 0)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.step_count += 1
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._iteration(targets_rgb, targets_depth, 0)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+        self.step_count += 1
+        return self.loss
+
+    def check_capacity(self):
         abi.gs_sync_status(self.ctx.handle)
 
 

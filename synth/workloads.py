@@ -93,6 +93,30 @@ def tiny_random(seed: int = 1000, n: int = 500, width: int = 64, height: int = 4
     return Workload("tiny_random", params, [View(cam, pose, trgb, tdep)])
 
 
+# three small views of uneven size around one cloud of random Gaussians
+TINY_MULTI_CAMS = ((64, 48, 60.0), (40, 24, 40.0), (72, 56, 70.0))
+TINY_MULTI_EYES = ((0.0, 0.0, 0.0), (0.3, -0.4, 0.15), (-0.2, 0.35, -0.2))
+TINY_MULTI_TARGET = (2.5, 0.0, 0.0)
+
+
+def tiny_multi_view(seed: int = 1004, n: int = 500, sh_degree: int = 0, sh_rest_std: float = 0.0,
+                    cams=TINY_MULTI_CAMS) -> Workload:
+    """Views of uneven resolution looking at one cloud of random Gaussians
+    (placed in the frustum of the first view, 1.5-3.5 m away); targets are
+    uniform random images as in tiny_random."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for k, (w, h, f) in enumerate(cams):
+        cam = Camera(f, f, w / 2.0, h / 2.0, w, h)
+        pose = look_at(np.asarray(TINY_MULTI_EYES[k % len(TINY_MULTI_EYES)]) * (1 + k // len(TINY_MULTI_EYES)),
+                       TINY_MULTI_TARGET)
+        views.append(View(cam, pose, rng.uniform(0, 1, (3, h, w)).astype(np.float32),
+                          rng.uniform(0.5, 4.0, (h, w)).astype(np.float32)))
+    params = random_gaussians(rng, n, views[0].cam, views[0].pose, sh_degree, z_range=(1.5, 3.5),
+                              sh_rest_std=sh_rest_std)
+    return Workload("tiny_multi_view", params, views)
+
+
 def _frame(room, cam, pose):
     rgb, depth = raycast(room, cam, pose)
     return rgb, depth
