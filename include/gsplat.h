@@ -282,6 +282,24 @@ gs_status gs_loss_l1_batched(gs_ctx *ctx, int32_t n_views, const gs_camera *cams
                              float w_color, float w_depth, float *loss, float *const *dL_dcolor,
                              float *const *dL_ddepth, gs_stream_t stream);
 
+/* Tile-shape autotuner (no counterpart in the paper, whose rasterizer uses
+ * one fixed tile size).  Times, for each of the GS_AUTOTUNE_CANDIDATES tile
+ * shapes 16x16, 8x32 and 32x8 (in that order), `reps` passes of everything
+ * the tile shape changes -- the batched forward pass (projection, binning,
+ * per-tile sort, compositing) and the raster backward pass -- on the given
+ * map and views (n_views >= 1; a single view is n_views = 1), and writes the
+ * fastest shape to cfg->tile_w / cfg->tile_h (the other cfg fields are used
+ * as given).  ms (host float[GS_AUTOTUNE_CANDIDATES], nullable) receives the
+ * milliseconds per pass of each candidate.  The result does not depend on the
+ * tile shape (a Gaussian takes part in a pixel by its own support rule), so
+ * only speed is compared.  Synchronises; the context's forward state is
+ * cleared (run gs_render_fwd again before a backward pass); the list entries a
+ * warp stages per round are fixed at 32 (one per lane) and not searched. */
+#define GS_AUTOTUNE_CANDIDATES 3
+gs_status gs_autotune(gs_ctx *ctx, const gs_gaussians *g, int32_t n_views, const gs_camera *cams,
+                      const gs_viewmat *views, gs_raster_cfg *cfg, int32_t reps, float *ms,
+                      gs_stream_t stream);
+
 /* Photometric loss (Eq. 12) plus a depth term:
  *   L = w_color * mean over 3HW of |color - target_rgb|
  *     + w_depth * mean over pixels with target_depth > 0 of |depth - target_depth|.
@@ -318,7 +336,9 @@ gs_status gs_loss_l1_noalloc(const gs_camera *cam, const float *color, const flo
  *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
  *   p -= lr_group * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
  * The paper optimises "using the gradient descent method" (Sec. III-B.3);
- * Adam is the optimiser used here.  step >= 1.  params, m, v updated in
+ * Adam is the optimiser used here.  step >= 1 is the Adam step; step = 0
+ * instead increments the context's device-side step counter and uses it
+ * (as gs_render_bwd_adam does; graph-capturable).  params, m, v updated in
  * place; grads read, and cleared to 0 when cfg->zero_grads is 1 (ready for
  * the next accumulating gs_render_bwd). */
 gs_status gs_adam_step(gs_ctx *ctx, float *params, float *grads, float *m, float *v,

@@ -106,6 +106,8 @@ EXPORTS = {
                                              C.POINTER(gs_adam_cfg), C.c_int64, P, P]),
     "gs_loss_l1_batched": (C.c_int, [P, C.c_int32, C.POINTER(gs_camera), PP, PP, PP, PP, C.c_float, C.c_float, P,
                                      PP, PP, P]),
+    "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                              C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
     "gs_set_profiling": (C.c_int, [P, C.c_int]),
     "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -393,3 +395,16 @@ def gs_loss_l1_batched(ctx, cams, color, depth, target_rgb, target_depth, w_colo
                                    _ptrs(dL_dcolor, "dL_dcolor", V), _ptrs(dL_ddepth, "dL_ddepth", V),
                                    _stream(stream))
     _check(ctx, st, "gs_loss_l1_batched")
+
+
+AUTOTUNE_SHAPES = ((16, 16), (8, 32), (32, 8))
+
+
+def gs_autotune(ctx, gaussians, cams, views, cfg: gs_raster_cfg, reps: int = 5, stream=None) -> list:
+    """Picks the fastest tile shape for these views into ``cfg`` (in place);
+    returns the milliseconds per pass of each candidate (AUTOTUNE_SHAPES)."""
+    ms = (C.c_float * len(AUTOTUNE_SHAPES))()
+    st = load().gs_autotune(ctx, C.byref(gaussians), len(cams), _cams(cams), _views(views), C.byref(cfg), int(reps),
+                            ms, _stream(stream))
+    _check(ctx, st, "gs_autotune")
+    return list(ms)

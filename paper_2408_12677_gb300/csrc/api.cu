@@ -53,6 +53,8 @@ struct gs_ctx {
   float* T_final = nullptr;
   int32_t* last = nullptr;
   float* loss_partials = nullptr;
+  float* tune_img = nullptr;  // zero image gradients for the autotuner
+  int64_t cap_tune = 0;
   // device scalars and their host mirror
   uint32_t* d_npairs = nullptr;
   unsigned long long* d_npairs_full = nullptr;
@@ -502,6 +504,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->T_final);
   cudaFree(c->last);
   cudaFree(c->loss_partials);
+  cudaFree(c->tune_img);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
   cudaFree(c->d_overflow);
@@ -1044,22 +1047,106 @@ gs_status gs_loss_l1_batched(gs_ctx* c, int32_t n_views, const gs_camera* cams, 
 gs_status gs_adam_step(gs_ctx* c, float* params, float* grads, float* m, float* v, int64_t n,
                        int32_t sh_degree, const gs_adam_cfg* cfg, int64_t step, gs_stream_t stream) {
   if (!c) return GS_ERR_INVALID_ARG;
-  if (!cfg || step < 1 || n < 0 || sh_degree < 0 || sh_degree > 3)
+  if (!cfg || step < 0 || n < 0 || sh_degree < 0 || sh_degree > 3)
     return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: bad cfg, step, n or sh_degree");
   if (n > 0 && (!params || !grads || !m || !v)) return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: NULL pointer");
   if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
     return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: betas must be in [0, 1), eps >= 0");
   GS_CUDA(c, cudaSetDevice(c->device));
-  const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
-  const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
+  cudaStream_t s = (cudaStream_t)stream;
   const float lr[6] = {cfg->lr_means, cfg->lr_log_scales, cfg->lr_quats, cfg->lr_opacity, cfg->lr_sh_dc, cfg->lr_sh_rest};
   {
-    StageTimer t(c, GS_STAGE_ADAM, (cudaStream_t)stream);
-    launch_adam(params, grads, m, v, n, sh_degree, lr, cfg->beta1, cfg->beta2, cfg->eps, (float)(1.0 / bc1),
-                (float)(1.0 / std::sqrt(bc2)), cfg->zero_grads != 0, (cudaStream_t)stream);
+    StageTimer t(c, GS_STAGE_ADAM, s);
+    if (step == 0) {  // device-side step counter (graph-capturable)
+      launch_step_increment(c->d_step, s);
+      c->launches += 1;
+      launch_adam(params, grads, m, v, n, sh_degree, lr, cfg->beta1, cfg->beta2, cfg->eps, 1.f, 1.f,
+                  cfg->zero_grads != 0, c->d_step, s);
+    } else {
+      const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)step);
+      const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)step);
+      launch_adam(params, grads, m, v, n, sh_degree, lr, cfg->beta1, cfg->beta2, cfg->eps, (float)(1.0 / bc1),
+                  (float)(1.0 / std::sqrt(bc2)), cfg->zero_grads != 0, nullptr, s);
+    }
   }
   if (n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "adam");
+  return GS_OK;
+}
+
+gs_status gs_autotune(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
+                      const gs_viewmat* views, gs_raster_cfg* cfg, int32_t reps, float* ms, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_gauss(c, g)) != GS_OK || (st = check_views(c, n_views, cams, views)) != GS_OK ||
+      (st = check_cfg(c, cfg)) != GS_OK)
+    return st;
+  if (reps < 1 || reps > 1000) return fail(c, GS_ERR_INVALID_ARG, "gs_autotune: reps must be in [1, 1000]");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t pixels = 0;
+  for (int v = 0; v < n_views; ++v) pixels += (int64_t)cams[v].width * cams[v].height;
+  if (4 * pixels > c->cap_tune) {  // dL/dcolor (3 planes) + dL/ddepth per view, all zero
+    GS_CUDA(c, cudaDeviceSynchronize());
+    GS_CUDA(c, regrow(&c->tune_img, 4 * pixels));
+    GS_CUDA(c, cudaMemset(c->tune_img, 0, sizeof(float) * 4 * (size_t)pixels));
+    c->cap_tune = 4 * pixels;
+  }
+  const float* dlc[kMaxViews];
+  const float* dld[kMaxViews];
+  int64_t off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const int64_t np = (int64_t)cams[v].width * cams[v].height;
+    dlc[v] = c->tune_img + off;
+    dld[v] = c->tune_img + off + 3 * np;
+    off += 4 * np;
+  }
+  static const int kShapes[GS_AUTOTUNE_CANDIDATES][2] = {{16, 16}, {8, 32}, {32, 8}};
+  const bool was_sync = c->sync;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GS_CUDA(c, cudaEventCreate(&e0));
+  GS_CUDA(c, cudaEventCreate(&e1));
+  float best = 0.f;
+  int best_k = -1;
+  st = GS_OK;
+  for (int k = 0; k < GS_AUTOTUNE_CANDIDATES && st == GS_OK; ++k) {
+    gs_raster_cfg cand = *cfg;
+    cand.tile_w = kShapes[k][0];
+    cand.tile_h = kShapes[k][1];
+    // untimed pass in sync mode sizes the buffers for this tile shape
+    c->sync = true;
+    st = render_fwd_views(c, g, n_views, cams, views, &cand, nullptr, nullptr, nullptr, s);
+    if (st == GS_OK) st = raster_backward(c, &cand, dlc, dld, nullptr, s);
+    if (st != GS_OK) break;
+    c->sync = false;  // timed passes: no host synchronisation, same inputs so the same pair count
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == GS_OK; ++r) {
+      st = render_fwd_views(c, g, n_views, cams, views, &cand, nullptr, nullptr, nullptr, s);
+      if (st == GS_OK) st = raster_backward(c, &cand, dlc, dld, nullptr, s);
+    }
+    cudaEventRecord(e1, s);
+    if (st != GS_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "gs_autotune timing");
+      break;
+    }
+    t /= (float)reps;
+    if (ms) ms[k] = t;
+    if (best_k < 0 || t < best) {
+      best = t;
+      best_k = k;
+    }
+  }
+  c->sync = was_sync;
+  c->have_state = false;  // the stored state is the last candidate's, not the chosen one
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != GS_OK) return st;
+  cfg->tile_w = kShapes[best_k][0];
+  cfg->tile_h = kShapes[best_k][1];
   return GS_OK;
 }
 

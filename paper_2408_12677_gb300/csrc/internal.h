@@ -184,9 +184,11 @@ struct LossArgs {
 int loss_blocks(int npix);
 // partials: >= 3 * n_blocks + kMaxViews floats
 void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* launches);
+// step_dev non-null: bias corrections from the device step counter instead
+// of step_size_scale / inv_sqrt_bc2
 void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],
                  float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero_grads,
-                 cudaStream_t s);
+                 const long long* step_dev, cudaStream_t s);
 
 // debug/introspection
 void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, float* mean2d, float* cov2d,

@@ -141,7 +141,18 @@ struct AdamGroups {
   int64_t e_means, e_scales, e_quats, e_opac;  // group ends (exclusive) in floats
   int sh_stride;                              // 3 K
   float lr[6];
+  const long long* step_dev;  // device step counter (bias corrections on the device) or null
+  float log_b1, log_b2;
 };
+
+// Bias corrections from the device step counter when there is one:
+// 1 - beta^t = -expm1(t log beta).
+__device__ __forceinline__ void device_steps(const AdamGroups& g, float& ss, float& isb2) {
+  if (!g.step_dev) return;
+  const float t = (float)*g.step_dev;
+  ss = 1.f / -expm1f(t * g.log_b1);
+  isb2 = rsqrtf(-expm1f(t * g.log_b2));
+}
 
 __device__ __forceinline__ float adam_lr(const AdamGroups& g, int64_t i) {
   if (i < g.e_means) return g.lr[0];
@@ -161,6 +172,7 @@ __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, 
 __global__ void __launch_bounds__(256) adam_kernel(int64_t total, float4* __restrict__ p4, float4* __restrict__ g4,
                                                    float4* __restrict__ m4, float4* __restrict__ v4, AdamGroups grp,
                                                    float b1, float b2, float eps, float ss, float isb2, bool zero) {
+  device_steps(grp, ss, isb2);
   const int64_t nvec = total >> 2;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nvec; q += (int64_t)gridDim.x * blockDim.x) {
     float4 p = p4[q], g = g4[q], m = m4[q], v = v4[q];
@@ -179,6 +191,7 @@ __global__ void __launch_bounds__(256) adam_kernel(int64_t total, float4* __rest
 __global__ void adam_tail_kernel(int64_t start, int64_t total, float* __restrict__ p, float* __restrict__ g,
                                  float* __restrict__ m, float* __restrict__ v, AdamGroups grp, float b1, float b2,
                                  float eps, float ss, float isb2, bool zero) {
+  device_steps(grp, ss, isb2);
   const int64_t i = start + threadIdx.x;
   if (i < total) {
     adam_one(p[i], g[i], m[i], v[i], adam_lr(grp, i), b1, b2, eps, ss, isb2);
@@ -189,6 +202,7 @@ __global__ void adam_tail_kernel(int64_t start, int64_t total, float* __restrict
 __global__ void adam_scalar_kernel(int64_t total, float* __restrict__ p, float* __restrict__ g,
                                    float* __restrict__ m, float* __restrict__ v, AdamGroups grp, float b1, float b2,
                                    float eps, float ss, float isb2, bool zero) {
+  device_steps(grp, ss, isb2);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     adam_one(p[i], g[i], m[i], v[i], adam_lr(grp, i), b1, b2, eps, ss, isb2);
     if (zero) g[i] = 0.f;
@@ -240,7 +254,7 @@ void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* la
 
 void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],
                  float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero,
-                 cudaStream_t s) {
+                 const long long* step_dev, cudaStream_t s) {
   const int K = (sh_degree + 1) * (sh_degree + 1);
   AdamGroups grp;
   grp.e_means = 3 * n_gauss;
@@ -249,6 +263,9 @@ void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh
   grp.e_opac = 11 * n_gauss;
   grp.sh_stride = 3 * K;
   for (int k = 0; k < 6; ++k) grp.lr[k] = lr[k];
+  grp.step_dev = step_dev;
+  grp.log_b1 = logf(beta1);
+  grp.log_b2 = logf(beta2);
   const int64_t total = n_gauss * (11 + 3 * K);
   if (total == 0) return;
   const bool aligned = ((((uintptr_t)p) | ((uintptr_t)g) | ((uintptr_t)m) | ((uintptr_t)v)) & 15) == 0;

@@ -165,6 +165,10 @@ class Trainer:
         abi.gs_render_bwd_adam(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, m.flat, m.m,
                                m.v, self.acfg, 0, None, stream)
 
+    def autotune(self, reps: int = 5) -> list:
+        """Pick the fastest tile shape for this view (gs_autotune)."""
+        return abi.gs_autotune(self.ctx.handle, self._g, [self.cam], [self.view], self.rcfg, reps)
+
     def capture(self, target_rgb: torch.Tensor, target_depth: torch.Tensor, pair_headroom: float = 1.5):
         """Record one iteration into a CUDA graph (``replay`` runs it).
 
@@ -280,6 +284,49 @@ class BatchedTrainer:
         self.step_count += 1
         abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, self.step_count, stream)
         return self.loss_views
+
+    def autotune(self, reps: int = 5) -> list:
+        """Pick the fastest tile shape for these views (gs_autotune); returns
+        the milliseconds per pass of each candidate shape."""
+        return abi.gs_autotune(self.ctx.handle, self._g, self.cams, self.vms, self.rcfg, reps)
+
+    def _sequential_device_counter(self, targets_rgb, targets_depth):
+        h = self.ctx.handle
+        m = self.model
+        for v in range(self.n_views):
+            abi.gs_render_fwd(h, self._g, self.cams[v], self.vms[v], self.rcfg, self.color[v], self.depth[v],
+                              self.alpha[v])
+            abi.gs_loss_l1(h, self.cams[v], self.color[v], self.depth[v], targets_rgb[v], targets_depth[v],
+                           self.w_color, self.w_depth, self.loss_views[v:v + 1], self.dLdc[v], self.dLdd[v])
+            abi.gs_render_bwd(h, self._g, self.cams[v], self.vms[v], self.rcfg, self.dLdc[v], self.dLdd[v], None,
+                              self._gr, None)
+        abi.gs_adam_step(h, m.flat, m.grad, m.m, m.v, m.n, m.sh_degree, self.acfg, 0)
+
+    def capture_sequential(self, targets_rgb, targets_depth, pair_headroom: float = 1.5):
+        """Record ``step_sequential`` (one view at a time, then one Adam step on
+        the device step counter) into a CUDA graph (``replay`` runs it): the
+        strongest form of the view-by-view comparison."""
+        h = self.ctx.handle
+        pairs = 0
+        for v in range(self.n_views):
+            abi.gs_render_fwd(h, self._g, self.cams[v], self.vms[v], self.rcfg)
+            torch.cuda.synchronize()
+            pairs = max(pairs, abi.gs_get_stats(h)["n_pairs"])
+        npx = max(c.width * c.height for c in self.cam_list)
+        abi.gs_ctx_reserve(h, self.model.n, npx, int(pairs * pair_headroom) + 4096)
+        abi.gs_ctx_set_sync(h, False)
+        abi.gs_ctx_set_adam_step(h, self.step_count)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._sequential_device_counter(targets_rgb, targets_depth)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.step_count += 1
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._sequential_device_counter(targets_rgb, targets_depth)
+        return self.graph
 
     def capture(self, targets_rgb, targets_depth, pair_headroom: float = 1.5):
         """Record one batched iteration into a CUDA graph (``replay`` runs it),

@@ -285,3 +285,39 @@ def test_batched_argument_checks(ctx):
                                   model.grads())
     assert e.value.status == abi.GS_ERR_STATE
     torch.cuda.synchronize()
+
+
+def test_autotune_picks_a_candidate_and_renders_the_same(ctx):
+    from paper_2408_12677_gb300 import abi
+    P, views = _mid_views(3)
+    model = to_gpu_model(P)
+    cams, vms = _structs(views)
+    cfg = abi.raster_cfg()
+    ms = abi.gs_autotune(ctx.handle, model.gaussians(), cams, vms, cfg, reps=2)
+    assert len(ms) == 3 and all(m > 0 for m in ms)
+    assert (cfg.tile_w, cfg.tile_h) in abi.AUTOTUNE_SHAPES
+    assert ms[abi.AUTOTUNE_SHAPES.index((cfg.tile_w, cfg.tile_h))] == min(ms)
+    # the tile shape changes the speed only: images of every candidate agree
+    ref = _batched_render(ctx, model, views)
+    for tw, th in abi.AUTOTUNE_SHAPES:
+        for (c0, d0, a0), (c1, d1, a1) in zip(ref, _batched_render(ctx, model, views, tile_w=tw, tile_h=th)):
+            assert np.abs(c0 - c1).max() <= 1e-5 and np.abs(d0 - d1).max() <= 1e-4 and np.abs(a0 - a1).max() <= 1e-5
+
+
+def test_adam_step_device_counter(ctx):
+    """gs_adam_step with step = 0 uses (and advances) the context's device step."""
+    from paper_2408_12677_gb300 import abi
+    P, _ = _mid_views(1)
+    ma, mb = to_gpu_model(P), to_gpu_model(P)
+    for mdl in (ma, mb):
+        mdl.grad.copy_(torch.linspace(-1e-3, 1e-3, mdl.grad.numel(), device="cuda"))
+    acfg = abi.adam_cfg(zero_grads=0)
+    abi.gs_ctx_set_adam_step(ctx.handle, 4)
+    abi.gs_adam_step(ctx.handle, ma.flat, ma.grad, ma.m, ma.v, ma.n, ma.sh_degree, acfg, 0)  # step 5
+    abi.gs_adam_step(ctx.handle, ma.flat, ma.grad, ma.m, ma.v, ma.n, ma.sh_degree, acfg, 0)  # step 6
+    abi.gs_adam_step(ctx.handle, mb.flat, mb.grad, mb.m, mb.v, mb.n, mb.sh_degree, acfg, 5)
+    abi.gs_adam_step(ctx.handle, mb.flat, mb.grad, mb.m, mb.v, mb.n, mb.sh_degree, acfg, 6)
+    torch.cuda.synchronize()
+    a, b = ma.flat.cpu().numpy(), mb.flat.cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-6, atol=1e-7 * np.abs(b).max())
+    abi.gs_ctx_set_adam_step(ctx.handle, 0)
