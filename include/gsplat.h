@@ -152,6 +152,19 @@ gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
  * Synchronises the device. */
 gs_status gs_ctx_set_adam_step(gs_ctx *ctx, int64_t step);
 
+/* on = 1 (default): the raster passes visit the tiles longest list first
+ * (tiles ordered by the binary length class of their lists, computed during
+ * binning), so the slowest tiles start early and the grid ends evenly; on = 0
+ * visits them in index order.  Results do not depend on the order.  Takes
+ * effect at the next forward pass. */
+gs_status gs_ctx_set_tile_order(gs_ctx *ctx, int on);
+
+/* on = 1 (default): each raster pass is one persistent launch of as many
+ * CTAs as the GPU holds at once, whose warps pull (tile, 8 x 8 pixel block)
+ * jobs from a device counter in the visit order above, for all views of a
+ * batch.  on = 0: one CTA per tile.  Results do not depend on it. */
+gs_status gs_ctx_set_persistent(gs_ctx *ctx, int on);
+
 /* Synchronise the stream, then report GS_ERR_CAPACITY if a no-sync forward
  * pass overflowed the pair buffers (and clear the flag). */
 gs_status gs_sync_status(gs_ctx *ctx, gs_stream_t stream);

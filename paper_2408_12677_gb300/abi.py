@@ -79,6 +79,8 @@ EXPORTS = {
     "gs_ctx_reserve": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
     "gs_ctx_set_sync": (C.c_int, [P, C.c_int]),
     "gs_ctx_set_adam_step": (C.c_int, [P, C.c_int64]),
+    "gs_ctx_set_tile_order": (C.c_int, [P, C.c_int]),
+    "gs_ctx_set_persistent": (C.c_int, [P, C.c_int]),
     "gs_sync_status": (C.c_int, [P, P]),
     "gs_get_stats": (C.c_int, [P, C.POINTER(gs_stats)]),
     "gs_raster_cfg_default": (C.c_int, [C.POINTER(gs_raster_cfg)]),
@@ -237,6 +239,14 @@ def gs_ctx_set_sync(ctx, sync: bool):
 
 def gs_ctx_set_adam_step(ctx, step: int):
     _check(ctx, load().gs_ctx_set_adam_step(ctx, int(step)), "gs_ctx_set_adam_step")
+
+
+def gs_ctx_set_tile_order(ctx, on: bool):
+    _check(ctx, load().gs_ctx_set_tile_order(ctx, int(bool(on))), "gs_ctx_set_tile_order")
+
+
+def gs_ctx_set_persistent(ctx, on: bool):
+    _check(ctx, load().gs_ctx_set_persistent(ctx, int(bool(on))), "gs_ctx_set_persistent")
 
 
 def gs_sync_status(ctx, stream=None):

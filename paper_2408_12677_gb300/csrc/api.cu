@@ -45,6 +45,7 @@ struct gs_ctx {
   uint32_t* tcount = nullptr;   // per-tile pair counts
   uint32_t* toffset = nullptr;  // per-tile list offsets
   uint32_t* tcursor = nullptr;  // per-tile scatter cursors
+  uint32_t* torder = nullptr;   // raster visit order of the tiles (longest lists first)
   uint32_t* bigq = nullptr;     // ids of Gaussians covering more than kBigTiles tiles
   uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue
   unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
@@ -80,6 +81,9 @@ struct gs_ctx {
   int64_t st_tiles = 0;
   int64_t st_pairs = 0;
   int st_pair_buf = 0;
+  bool st_ordered = false;  // torder holds the visit order of the last forward pass
+  bool order_tiles = true;  // compute and use the visit order
+  bool persistent = true;   // raster passes as persistent grids pulling (tile, quadrant) jobs
   int st_sh = 0;
   TileMap st_map{};
   int64_t st_pix_base[kMaxViews] = {};
@@ -186,6 +190,7 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   GS_CUDA(c, regrow(&c->tcount, cap));
   GS_CUDA(c, regrow(&c->toffset, cap));
   GS_CUDA(c, regrow(&c->tcursor, cap));
+  GS_CUDA(c, regrow(&c->torder, cap));
   c->cap_t = cap;
   c->have_state = false;
   return GS_OK;
@@ -377,6 +382,8 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
   tb.overflow = c->d_overflow;
   tb.big_queue = c->bigq;
   tb.big_len = c->d_bigmeta;
+  tb.order = c->order_tiles ? c->torder : nullptr;
+  c->st_ordered = false;
   {
     StageTimer t(c, GS_STAGE_DUPLICATE, s);
     launch_tile_count_scan(tb, s, &c->launches);
@@ -407,6 +414,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
   GS_CHECK_LAUNCH(c, "tile scatter/sort");
   c->st_pairs = P;
   c->st_pair_buf = 0;
+  c->st_ordered = tb.order != nullptr;
   return GS_OK;
 }
 
@@ -497,6 +505,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->tcount);
   cudaFree(c->toffset);
   cudaFree(c->tcursor);
+  cudaFree(c->torder);
   cudaFree(c->bigq);
   cudaFree(c->d_bigmeta);
   cudaFree(c->d_binstats);
@@ -544,6 +553,18 @@ gs_status gs_ctx_set_adam_step(gs_ctx* c, int64_t step) {
 gs_status gs_ctx_set_sync(gs_ctx* c, int sync) {
   if (!c) return GS_ERR_INVALID_ARG;
   c->sync = sync != 0;
+  return GS_OK;
+}
+
+gs_status gs_ctx_set_tile_order(gs_ctx* c, int on) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->order_tiles = on != 0;
+  return GS_OK;
+}
+
+gs_status gs_ctx_set_persistent(gs_ctx* c, int on) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  c->persistent = on != 0;
   return GS_OK;
 }
 
@@ -719,7 +740,9 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.ranges = c->ranges;
   ra.ids = c->pv[c->st_pair_buf];
   ra.feat = c->feat;
-  ra.order = nullptr;
+  ra.order = c->st_ordered ? c->torder : nullptr;
+  ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;
+  ra.num_sms = c->num_sms;
   for (int v = 0; v < kMaxViews; ++v) {
     RasterView& rv = ra.v[v];
     const bool live = v < c->st_views;

@@ -133,6 +133,7 @@ struct TileBinArgs {
   uint32_t* overflow;         // device flag: 1 = pairs over capacity, 2 = list over kTileSortCap
   const uint32_t* big_queue;  // items with more than kBigTiles tiles
   const uint32_t* big_len;
+  uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
 };
 int tile_sort_capacity();
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
@@ -160,6 +161,8 @@ struct RasterArgs {
   const uint32_t* ids;
   const float4* feat;
   const uint32_t* order;  // nullable
+  uint32_t* work;         // nullable: job counter of the persistent form (zeroed by the launcher)
+  int num_sms;
   RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);

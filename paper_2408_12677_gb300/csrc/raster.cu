@@ -12,6 +12,8 @@
 // Gaussian's gradient over the warp (per-lane atomics when at most two lanes
 // contribute, else a transposed shuffle reduction) and adds it to the
 // Gaussian's global record with one warp-wide atomic.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -69,16 +71,16 @@ __device__ __forceinline__ bool make_entry(float4 f0, float4 f1, float4 f2, floa
   return mlx + ex >= bx + 0.5f && mlx - ex <= bx + 7.5f && mly + ey >= by + 0.5f && mly - ey <= by + 7.5f;
 }
 
-// Tile, view and pixel origin of the CTA: blockIdx.x indexes the tile visit
-// order (or the tiles directly), global tiles map to views by tile_base.
+// Tile, view and pixel origin of visit k: k indexes the tile visit order (or
+// the tiles directly), global tiles map to views by tile_base.
 struct TileJob {
   int v;       // view
   int ox, oy;  // pixel origin of the tile within the view
   uint2 range;
 };
 template <int TW, int TH>
-__device__ __forceinline__ TileJob tile_job(const RasterArgs& a) {
-  const uint32_t tile = a.order ? a.order[blockIdx.x] : blockIdx.x;
+__device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
+  const uint32_t tile = a.order ? a.order[k] : k;
   int v = 0;
   for (int k = 1; k < a.views; ++k)
     if (tile >= a.v[k].tile_base) v = k;
@@ -87,21 +89,20 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a) {
   return TileJob{v, tx * TW, ty * TH, a.ranges[tile]};
 }
 
+// Forward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
+// visit k) by one warp; buf is the warp's shared staging buffer.
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
-                                                              float* __restrict__ T_final_all,
-                                                              int32_t* __restrict__ last_all,
-                                                              unsigned long long* __restrict__ counters) {
+__device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t k, int quad,
+                                        Entry* __restrict__ buf, float* __restrict__ T_final_all,
+                                        int32_t* __restrict__ last_all, unsigned long long* __restrict__ counters) {
   constexpr int WX = TW / 8;
-  static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
-  __shared__ Entry s_e[kThreads / 32][32];
-  const TileJob job = tile_job<TW, TH>(a);
+  const TileJob job = tile_job<TW, TH>(a, k);
   const RasterView& vw = a.v[job.v];
   const int width = vw.width, height = vw.height;
   const uint32_t* __restrict__ ids = a.ids;
   const float4* __restrict__ feat = a.feat;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
+  const int lane = threadIdx.x & 31;
+  const int bxi = (quad % WX) * 8, byi = (quad / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
   const int px = job.ox + lx, py0 = job.oy + ly0, py1 = job.oy + ly1;
   const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   const float ox = (float)job.ox, oy = (float)job.oy, bx = (float)bxi, by = (float)byi;
   const uint2 r = job.range;
   const int n = (int)(r.y - r.x);
-  Entry* buf = s_e[warp];
+  __syncwarp();  // the warp's previous job is done with buf
 
   float T0 = 1.f, R0 = 0.f, G0 = 0.f, B0 = 0.f, D0 = 0.f;
   float T1 = 1.f, R1 = 0.f, G1 = 0.f, B1 = 0.f, D1 = 0.f;
@@ -223,6 +224,39 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   }
 }
 
+// Pulls the next (tile visit, quadrant) job for the calling warp from the
+// device counter `work`: jobs 4k .. 4k + 3 are the four quadrants of visit
+// k, so warps take the tiles in visit order (longest lists first) and a warp
+// that finishes early takes new work instead of waiting for the other
+// quadrants of its tile.  Returns false when all jobs are taken.
+__device__ __forceinline__ bool next_job(uint32_t* __restrict__ work, uint32_t n_jobs, uint32_t& job) {
+  uint32_t j = 0;
+  if ((threadIdx.x & 31) == 0) j = atomicAdd(work, 1u);
+  job = __shfl_sync(kFull, j, 0);
+  return job < n_jobs;
+}
+
+// PERSIST = false: one CTA per tile visit, warp w on quadrant w.  Otherwise
+// a persistent grid whose warps pull jobs from `work` with next_job.
+template <int TW, int TH, bool COUNT, bool PERSIST>
+__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
+                                                              float* __restrict__ T_final_all,
+                                                              int32_t* __restrict__ last_all,
+                                                              unsigned long long* __restrict__ counters,
+                                                              uint32_t* __restrict__ work) {
+  static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
+  __shared__ Entry s_e[kThreads / 32][32];
+  const int warp = threadIdx.x >> 5;
+  if constexpr (!PERSIST) {
+    fwd_job<TW, TH, COUNT>(a, rp, blockIdx.x, warp, s_e[warp], T_final_all, last_all, counters);
+  } else {
+    const uint32_t n_jobs = 4u * a.n_tiles;
+    uint32_t job;
+    while (next_job(work, n_jobs, job))
+      fwd_job<TW, TH, COUNT>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], T_final_all, last_all, counters);
+  }
+}
+
 // float offset of gradient value k (mu 2, factor 3, opacity, z | rgb 3) in the
 // 12-float record {mu_x, mu_y, i0, k} {i1, opacity, z, -} {r, g, b, -}
 __device__ __forceinline__ int rec_off(int k) { return k < 7 ? k : k + 1; }
@@ -309,19 +343,16 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
   return true;
 }
 
+// Backward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
+// visit k) by one warp, with the warp's shared staging buffers.
 template <int TW, int TH>
-__global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_constant__ RasterArgs a,
-                                                                 RasterParams rp,
-                                                                 const float* __restrict__ T_final_all,
-                                                                 const int32_t* __restrict__ last_all,
-                                                                 float* __restrict__ g2d) {
+__device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t k, int quad,
+                                        Entry* __restrict__ buf, uint32_t* __restrict__ bid,
+                                        float4 (*__restrict__ s_raw)[32][3], uint32_t (*__restrict__ s_gid)[32],
+                                        const float* __restrict__ T_final_all,
+                                        const int32_t* __restrict__ last_all, float* __restrict__ g2d) {
   constexpr int WX = TW / 8;
-  static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
-  __shared__ Entry s_e[kThreads / 32][32];
-  __shared__ uint32_t s_id[kThreads / 32][32];
-  __shared__ __align__(16) float4 s_raw[kThreads / 32][2][32][3];
-  __shared__ uint32_t s_gid[kThreads / 32][2][32];
-  const TileJob job = tile_job<TW, TH>(a);
+  const TileJob job = tile_job<TW, TH>(a, k);
   const RasterView& vw = a.v[job.v];
   const int width = vw.width, height = vw.height;
   const uint32_t* __restrict__ ids = a.ids;
@@ -331,8 +362,8 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_co
   const float* __restrict__ dLdc = vw.dLdc;
   const float* __restrict__ dLdd = vw.dLdd;
   const float* __restrict__ dLda = vw.dLda;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bxi = (warp % WX) * 8, byi = (warp / WX) * 8;
+  const int lane = threadIdx.x & 31;
+  const int bxi = (quad % WX) * 8, byi = (quad / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
   const int px = job.ox + lx, py0 = job.oy + ly0, py1 = job.oy + ly1;
   const bool in0 = px < width && py0 < height, in1 = px < width && py1 < height;
@@ -340,8 +371,7 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_co
   const float ox = (float)job.ox, oy = (float)job.oy, bx = (float)bxi, by = (float)byi;
   const uint2 r = job.range;
   const size_t HW = (size_t)width * height;
-  Entry* buf = s_e[warp];
-  uint32_t* bid = s_id[warp];
+  __syncwarp();  // the warp's previous job is done with the buffers
 
   // per-pixel state (two pixels per thread)
   float T0 = 1.f, c00 = 0.f, c01 = 0.f, c02 = 0.f, d0 = 0.f, a0 = 0.f;
@@ -383,27 +413,27 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_co
   int cur = 0;
   if (c0 + lane < wmax) {
     const uint32_t g = ids[r.x + c0 + lane];
-    s_gid[warp][0][lane] = g;
-    cp_record(s_raw[warp][0][lane], feat, g);
+    s_gid[0][lane] = g;
+    cp_record(s_raw[0][lane], feat, g);
   }
   cp_commit();
   uint32_t g2 = c0 >= 32 ? ids[r.x + c0 - 32 + lane] : 0u;
   for (; c0 >= 0; c0 -= 32, cur ^= 1) {
     if (c0 >= 32) {
-      s_gid[warp][cur ^ 1][lane] = g2;
-      cp_record(s_raw[warp][cur ^ 1][lane], feat, g2);
+      s_gid[cur ^ 1][lane] = g2;
+      cp_record(s_raw[cur ^ 1][lane], feat, g2);
     }
     cp_commit();
     if (c0 >= 64) g2 = ids[r.x + c0 - 64 + lane];
     cp_wait_prev();
     const bool have = c0 + lane < wmax;
     Entry e;
-    const float4* raw = s_raw[warp][cur][lane];
+    const float4* raw = s_raw[cur][lane];
     const bool hit = have && make_entry(raw[0], raw[1], raw[2], ox, oy, bx, by, rp, e);
     __syncwarp();
     if (hit) {
       buf[lane] = e;
-      bid[lane] = s_gid[warp][cur][lane];
+      bid[lane] = s_gid[cur][lane];
     }
     unsigned bal = __ballot_sync(kFull, hit);
     __syncwarp();
@@ -436,6 +466,33 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_co
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// PERSIST = false: one CTA per tile visit, warp w on quadrant w.  Otherwise
+// a persistent grid whose warps pull jobs from `work` with next_job.
+template <int TW, int TH, bool PERSIST>
+__global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_constant__ RasterArgs a,
+                                                                 RasterParams rp,
+                                                                 const float* __restrict__ T_final_all,
+                                                                 const int32_t* __restrict__ last_all,
+                                                                 float* __restrict__ g2d,
+                                                                 uint32_t* __restrict__ work) {
+  static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
+  __shared__ Entry s_e[kThreads / 32][32];
+  __shared__ uint32_t s_id[kThreads / 32][32];
+  __shared__ __align__(16) float4 s_raw[kThreads / 32][2][32][3];
+  __shared__ uint32_t s_gid[kThreads / 32][2][32];
+  const int warp = threadIdx.x >> 5;
+  if constexpr (!PERSIST) {
+    bwd_job<TW, TH>(a, rp, blockIdx.x, warp, s_e[warp], s_id[warp], s_raw[warp], s_gid[warp], T_final_all,
+                    last_all, g2d);
+  } else {
+    const uint32_t n_jobs = 4u * a.n_tiles;
+    uint32_t job;
+    while (next_job(work, n_jobs, job))
+      bwd_job<TW, TH>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], s_id[warp], s_raw[warp], s_gid[warp],
+                      T_final_all, last_all, g2d);
+  }
+}
+
 RasterParams make_params(const RasterArgs& a) {
   RasterParams rp;
   rp.width = rp.height = 0;  // per view, from the view table
@@ -456,34 +513,72 @@ bool raster_shape_supported(int tw, int th) {
   return (tw == 16 && th == 16) || (tw == 8 && th == 32) || (tw == 32 && th == 8);
 }
 
+namespace {
+
+// Persistent grid: as many CTAs as fit on the GPU at once (occupancy of the
+// kernel x SMs; per_sm caches the occupancy query of one kernel), at most one
+// per tile visit.
+template <class K>
+int persistent_grid(K kernel, int& per_sm, int n_tiles, int num_sms) {
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm = b;
+  }
+  return std::max(1, std::min(n_tiles, per_sm * std::max(num_sms, 1)));
+}
+
+template <int TW, int TH, bool COUNT>
+void fwd_shape(const RasterArgs& a, const RasterParams& rp, float* T_final, int32_t* last,
+               unsigned long long* counters, cudaStream_t s) {
+  const int nt = (int)a.n_tiles;
+  if (a.work) {
+    static int per_sm = 0;
+    auto* k = raster_fwd_kernel<TW, TH, COUNT, true>;
+    k<<<persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s>>>(a, rp, T_final, last, counters, a.work);
+  } else {
+    raster_fwd_kernel<TW, TH, COUNT, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters, nullptr);
+  }
+}
+
+template <int TW, int TH>
+void bwd_shape(const RasterArgs& a, const RasterParams& rp, const float* T_final, const int32_t* last, float* g2d,
+               cudaStream_t s) {
+  const int nt = (int)a.n_tiles;
+  if (a.work) {
+    static int per_sm = 0;
+    auto* k = raster_bwd_kernel<TW, TH, true>;
+    k<<<persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s>>>(a, rp, T_final, last, g2d, a.work);
+  } else {
+    raster_bwd_kernel<TW, TH, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, g2d, nullptr);
+  }
+}
+
+}  // namespace
+
 void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsigned long long* counters,
                        cudaStream_t s) {
-  const int nt = (int)a.n_tiles;
-  if (nt == 0) return;
-  RasterParams rp = make_params(a);
-#define GS_FWD(TW_, TH_, C_) raster_fwd_kernel<TW_, TH_, C_><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters)
+  if (a.n_tiles == 0) return;
+  const RasterParams rp = make_params(a);
+  if (a.work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
   if (counters) {
-    if (a.tile_w == 16) GS_FWD(16, 16, true);
-    else if (a.tile_w == 8) GS_FWD(8, 32, true);
-    else GS_FWD(32, 8, true);
+    if (a.tile_w == 16) fwd_shape<16, 16, true>(a, rp, T_final, last, counters, s);
+    else if (a.tile_w == 8) fwd_shape<8, 32, true>(a, rp, T_final, last, counters, s);
+    else fwd_shape<32, 8, true>(a, rp, T_final, last, counters, s);
   } else {
-    if (a.tile_w == 16) GS_FWD(16, 16, false);
-    else if (a.tile_w == 8) GS_FWD(8, 32, false);
-    else GS_FWD(32, 8, false);
+    if (a.tile_w == 16) fwd_shape<16, 16, false>(a, rp, T_final, last, counters, s);
+    else if (a.tile_w == 8) fwd_shape<8, 32, false>(a, rp, T_final, last, counters, s);
+    else fwd_shape<32, 8, false>(a, rp, T_final, last, counters, s);
   }
-#undef GS_FWD
 }
 
 void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s) {
-  const int nt = (int)a.n_tiles;
-  if (nt == 0) return;
-  RasterParams rp = make_params(a);
-  if (a.tile_w == 16)
-    raster_bwd_kernel<16, 16><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
-  else if (a.tile_w == 8)
-    raster_bwd_kernel<8, 32><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
-  else
-    raster_bwd_kernel<32, 8><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, (float*)g2d);
+  if (a.n_tiles == 0) return;
+  const RasterParams rp = make_params(a);
+  if (a.work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
+  if (a.tile_w == 16) bwd_shape<16, 16>(a, rp, T_final, last, (float*)g2d, s);
+  else if (a.tile_w == 8) bwd_shape<8, 32>(a, rp, T_final, last, (float*)g2d, s);
+  else bwd_shape<32, 8>(a, rp, T_final, last, (float*)g2d, s);
 }
 
 }  // namespace gs

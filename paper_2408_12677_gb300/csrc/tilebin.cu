@@ -135,13 +135,21 @@ __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_co
                 [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
 }
 
+// Length class of a tile list for the visit order: 0 for an empty list,
+// else 1 + floor(log2(length)).
+__device__ __forceinline__ int length_class(uint32_t c) { return c ? 32 - __clz(c) : 0; }
+
 // offsets = exclusive scan of counts (clamped to 32 bits), cursors = offsets;
-// stats[0] = total pairs, stats[1] = longest list; n_pairs = min(total, capacity)
+// stats[0] = total pairs, stats[1] = longest list; n_pairs = min(total, capacity).
+// order (if non-null) = the tiles by descending length class, the order in
+// which the raster passes visit them (longest lists first, so that the
+// slowest tiles do not start last).
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const uint32_t* __restrict__ counts,
                                                                  uint32_t* __restrict__ offsets,
                                                                  uint32_t* __restrict__ cursors, uint32_t capacity,
                                                                  uint32_t* __restrict__ n_pairs,
-                                                                 unsigned long long* __restrict__ stats) {
+                                                                 unsigned long long* __restrict__ stats,
+                                                                 uint32_t* __restrict__ order) {
   __shared__ unsigned long long s[kScanThreads];
   __shared__ uint32_t s_max[32];
   const int per = (T + kScanThreads - 1) / kScanThreads;
@@ -178,6 +186,39 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
     stats[0] = tot;
     stats[1] = m;
     *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
+  }
+  if (!order) return;
+  // counting sort of the tiles by length class (33 classes), descending;
+  // lanes of a warp with the same class are aggregated into one atomic
+  __shared__ uint32_t s_cls[33];
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 33) s_cls[threadIdx.x] = 0;
+  __syncthreads();
+  for (int i0 = 0; i0 < T; i0 += kScanThreads) {
+    const int i = i0 + threadIdx.x;
+    const int c = i < T ? length_class(counts[i]) : 33;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
+    if (c < 33 && lane == __ffs(peers) - 1) atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int c = 32; c >= 0; --c) {
+      const uint32_t k = s_cls[c];
+      s_cls[c] = run;
+      run += k;
+    }
+  }
+  __syncthreads();
+  for (int i0 = 0; i0 < T; i0 += kScanThreads) {
+    const int i = i0 + threadIdx.x;
+    const int c = i < T ? length_class(counts[i]) : 33;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (c < 33 && lane == leader) base = atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (c < 33) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 
@@ -318,7 +359,7 @@ void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launc
     if (launches) *launches += 1;
   }
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
-                                              a.stats);
+                                              a.stats, a.order);
   if (launches) *launches += 1;
 }
 

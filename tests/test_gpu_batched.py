@@ -321,3 +321,29 @@ def test_adam_step_device_counter(ctx):
     a, b = ma.flat.cpu().numpy(), mb.flat.cpu().numpy()
     assert np.allclose(a, b, rtol=1e-6, atol=1e-7 * np.abs(b).max())
     abi.gs_ctx_set_adam_step(ctx.handle, 0)
+
+
+def test_tile_visit_order_and_persistent_grid_change_nothing(ctx):
+    """Longest-list-first tile order vs index order, persistent job-pulling
+    grid vs one CTA per tile: identical forward images, gradients equal up to
+    float32 atomics order."""
+    from paper_2408_12677_gb300 import abi
+    P, views = _mid_views(3)
+    rng = np.random.default_rng(21)
+    wc = [rng.standard_normal((3, v.cam.height, v.cam.width)).astype(np.float32) for v in views]
+    wd = [rng.standard_normal((v.cam.height, v.cam.width)).astype(np.float32) for v in views]
+    model = to_gpu_model(P)
+    out = []
+    for order, persistent in ((True, True), (False, False), (True, False), (False, True)):
+        abi.gs_ctx_set_tile_order(ctx.handle, order)
+        abi.gs_ctx_set_persistent(ctx.handle, persistent)
+        imgs = _batched_render(ctx, model, views)
+        out.append((imgs, _batched_backward(ctx, model, views, wc, wd, None)))
+    abi.gs_ctx_set_tile_order(ctx.handle, True)
+    abi.gs_ctx_set_persistent(ctx.handle, True)
+    for other in out[1:]:
+        for (c0, d0, a0), (c1, d1, a1) in zip(out[0][0], other[0]):
+            assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(a0, a1)
+        for k in NAMES:
+            g0, g1 = out[0][1][k], other[1][k]
+            compare(k, g0, g1, 1e-3, 1e-6 * np.abs(g1).max(), 1e-5, max(2, int(1e-3 * g1.size)))
