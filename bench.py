@@ -270,6 +270,27 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+def run_sequential(args, w, views, trgb, tdep, rcfg, timed, local_rank):
+    """The batched iteration run view by view with the single-view calls:
+    eager (one host read of the pair count per view) and graph-captured."""
+    import torch
+
+    from paper_2408_12677_gb300.torch_api import BatchedTrainer, Context, GaussianModel
+
+    dev = torch.device("cuda", local_rank)
+    ctx_s = Context(local_rank)
+    ts = BatchedTrainer(GaussianModel(w.params, device=dev), views, raster_cfg=rcfg, ctx=ctx_s)
+    for _ in range(args.warmup):
+        ts.step_sequential(trgb, tdep)
+    ms_s_eager = timed(lambda: ts.step_sequential(trgb, tdep), args.steps)
+    ts.capture_sequential(trgb, tdep)
+    for _ in range(args.warmup):
+        ts.replay()
+    ms_s = timed(ts.replay, args.steps)
+    ts.check_capacity()
+    return ms_s, ms_s_eager, float(ts.loss_views.sum())
+
+
 def run_multi_view(args, rank, world, local_rank):
     """Batched multi-view iteration: 8 views of uneven resolution (2 x 640x480,
     4 x 1200x680, 2 x 1752x1168) against one 500k-Gaussian map, one step =
@@ -348,20 +369,12 @@ def run_multi_view(args, rank, world, local_rank):
     ms_e2e = timed(e2e_step, args.steps)
     h2d = sum(x.numel() * 4 for x in h_rgb + h_dep)
 
-    # the same iteration view by view
-    ctx_s = Context(local_rank)
-    ts = BatchedTrainer(GaussianModel(w.params, device=dev), views, raster_cfg=tb.rcfg, ctx=ctx_s)
-    for _ in range(args.warmup):
-        ts.step_sequential(trgb, tdep)
-    ms_s_eager = timed(lambda: ts.step_sequential(trgb, tdep), args.steps)
-    ts.capture_sequential(trgb, tdep)
-    for _ in range(args.warmup):
-        ts.replay()
-    ms_s = timed(ts.replay, args.steps)
-    ts.check_capacity()
-    loss_s = float(ts.loss_views.sum())
-
-    ms_b, ms_s, ms_e2e = max_over_ranks([ms_b, ms_s, ms_e2e], world)
+    if args.no_compare:
+        ms_s = ms_s_eager = float("nan")
+        loss_s = None
+    else:
+        ms_s, ms_s_eager, loss_s = run_sequential(args, w, views, trgb, tdep, tb.rcfg, timed, local_rank)
+    ms_b, ms_e2e = max_over_ranks([ms_b, ms_e2e], world)
     per_stage = {k: {"ms_per_launch": (ms / c if c else 0.0), "launches": c} for k, (ms, c) in stages.items()}
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms = per_stage[dom]["ms_per_launch"]
@@ -385,7 +398,7 @@ def run_multi_view(args, rank, world, local_rank):
                    "timing": "CUDA graph replay per step", "l2": "no flush: per-step working set > 129 MB L2",
                    "host_generation_s": t_gen},
         "gaussian_pixel_evals_per_s": e_blend * it_s, "evals_blended_per_iter": e_blend,
-        "comparison": {
+        "comparison": None if args.no_compare else {
             "batched_graph_ms": ms_b / args.steps, "batched_eager_ms": ms_b_eager / args.steps,
             "sequential_graph_ms": ms_s / args.steps, "sequential_eager_ms": ms_s_eager / args.steps,
             "speedup_vs_sequential_graph": ms_s / ms_b, "speedup_vs_sequential_eager": ms_s_eager / ms_b,
@@ -516,6 +529,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view"],
                     help="multi_view: the batched 8-view iteration vs the same iteration view by view")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="multi_view: skip the view-by-view comparison arm (e.g. for a profiler capture)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -582,7 +582,8 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(const _
     if (t < cnt)
       for (int e = 0; e < NS; ++e) sm.gs[t * RS + e] = 0.f;
   }
-  for (int v = 0; v < a.views; ++v) {
+  const int n_views = MULTI ? a.views : 1;  // the one-view variant runs for one view only
+  for (int v = 0; v < n_views; ++v) {
     float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (t < cnt) {
       if (v > 0) {

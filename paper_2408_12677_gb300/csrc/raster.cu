@@ -25,7 +25,8 @@ constexpr int kThreads = 128;  // 4 independent warps per CTA, one 8 x 8 pixel b
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // One list entry in tile-local coordinates:
-//   sa = {mu_x, mu_y, i0, k}, sb = {i1, log2 opacity, z, 1/opacity}, sc = {r, g, b, -}
+//   a = {mu_x, mu_y, i0, k}, b = {i1, log2 opacity, z, 1/opacity},
+//   c = {r, g, b, mask of the warp block's halves the support box meets}
 struct Entry {
   float4 a, b, c;
 };
@@ -50,25 +51,35 @@ __device__ __forceinline__ void load_entry(const float4* __restrict__ feat, uint
 }
 
 // Converts a gathered record to tile-local coordinates and tests the splat's
-// support bounding box against the warp's 8 x 8 block [bx, bx + 8) x [by, by + 8).
-// The box holds every pixel the per-pixel test can accept: q' <= min(qmax,
-// log2 o - log2 alpha_min) is the ellipse (i0 dx)^2 + (i1 (dy - k dx))^2 <= R2,
-// with half-extents sqrt(R2) / i0 and sqrt(R2) sqrt(k^2 / i0^2 + 1 / i1^2);
-// the widening covers float32 rounding of the test.
-__device__ __forceinline__ bool make_entry(float4 f0, float4 f1, float4 f2, float ox, float oy, float bx, float by,
-                                           const RasterParams& rp, Entry& e) {
+// support bounding box against the two halves of the warp's 8 x 8 block:
+// rows [by, by + 4) (bit 0, the lanes' first pixels) and [by + 4, by + 8)
+// (bit 1, their second pixels), columns [bx, bx + 8).  The box holds every
+// pixel the per-pixel test can accept: q' <= min(qmax, log2 o - log2 alpha_min)
+// is the ellipse (i0 dx)^2 + (i1 (dy - k dx))^2 <= R2, with half-extents
+// sqrt(R2) / i0 and sqrt(R2) sqrt(k^2 / i0^2 + 1 / i1^2); the widening covers
+// float32 rounding of the test.  Returns the mask of halves hit (0 = none);
+// the mask is warp-uniform per entry, so a half it excludes costs the warp
+// nothing.
+__device__ __forceinline__ unsigned make_entry(float4 f0, float4 f1, float4 f2, float ox, float oy, float bx, float by,
+                                               const RasterParams& rp, Entry& e) {
   const float mlx = __fadd_rn(__fsub_rn(f0.x, ox), f0.z);
   const float mly = __fadd_rn(__fsub_rn(f0.y, oy), f0.w);
   e.a = make_float4(mlx, mly, f1.x, f1.y);
   e.b = make_float4(f1.z, f1.w, f2.w, ex2_approx(-f1.w));
-  e.c = make_float4(f2.x, f2.y, f2.z, 0.f);
   const float R2 = fminf(rp.qmax_s, f1.w - rp.log2_alpha_min);
-  if (!(R2 > 0.f && f1.x > 0.f && f1.z > 0.f)) return false;
-  const float Rr = sqrtf(R2) * 1.0001f + 1e-4f;
-  const float inv0 = __frcp_rn(f1.x), inv1 = __frcp_rn(f1.z);
-  const float ex = Rr * inv0 + 1e-3f;
-  const float ey = Rr * sqrtf(f1.y * f1.y * inv0 * inv0 + inv1 * inv1) + 1e-3f;
-  return mlx + ex >= bx + 0.5f && mlx - ex <= bx + 7.5f && mly + ey >= by + 0.5f && mly - ey <= by + 7.5f;
+  unsigned m = 0u;
+  if (R2 > 0.f && f1.x > 0.f && f1.z > 0.f) {
+    const float Rr = sqrtf(R2) * 1.0001f + 1e-4f;
+    const float inv0 = rcp_approx(f1.x), inv1 = rcp_approx(f1.z);
+    const float ex = Rr * inv0 + 1e-3f;
+    const float ey = Rr * sqrtf(f1.y * f1.y * inv0 * inv0 + inv1 * inv1) + 1e-3f;
+    if (mlx + ex >= bx + 0.5f && mlx - ex <= bx + 7.5f) {
+      const float y0 = mly - ey, y1 = mly + ey;
+      m = ((y1 >= by + 0.5f && y0 <= by + 3.5f) ? 1u : 0u) | ((y1 >= by + 4.5f && y0 <= by + 7.5f) ? 2u : 0u);
+    }
+  }
+  e.c = make_float4(f2.x, f2.y, f2.z, __uint_as_float(m));
+  return m;
 }
 
 // Tile, view and pixel origin of visit k: k indexes the tile visit order (or
@@ -127,7 +138,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
     const float4 h0 = f0, h1 = f1, h2 = f2;
     if (c0 + 32 + lane < n) load_entry(feat, ids[r.x + c0 + 32 + lane], f0, f1, f2);
     Entry e;
-    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e);
+    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e) != 0u;
     __syncwarp();
     if (hit) buf[lane] = e;
     unsigned bal = __ballot_sync(kFull, hit);
@@ -137,8 +148,10 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       bal &= bal - 1;
       const float4 a = buf[j].a;
       const float4 bb = buf[j].b;
+      const float4 c = buf[j].c;
+      const unsigned halves = __float_as_uint(c.w);
       PixEval pe;
-      if (!done0) {
+      if ((halves & 1u) && !done0) {
         if (COUNT) ++n_visit;
         if (eval_splat(a, bb.x, bb.y, plx, ply0, rp.qmax_s, rp.log2_alpha_min, pe)) {
           const float al = fminf(rp.alpha_max, pe.araw);
@@ -146,7 +159,6 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
           if (test_T < rp.t_eps) {
             done0 = true;
           } else {
-            const float4 c = buf[j].c;
             const float w = al * T0;
             R0 = fmaf(w, c.x, R0);
             G0 = fmaf(w, c.y, G0);
@@ -158,7 +170,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
           }
         }
       }
-      if (!done1) {
+      if ((halves & 2u) && !done1) {
         if (COUNT) ++n_visit;
         if (eval_splat(a, bb.x, bb.y, plx, ply1, rp.qmax_s, rp.log2_alpha_min, pe)) {
           const float al = fminf(rp.alpha_max, pe.araw);
@@ -166,7 +178,6 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
           if (test_T < rp.t_eps) {
             done1 = true;
           } else {
-            const float4 c = buf[j].c;
             const float w = al * T1;
             R1 = fmaf(w, c.x, R1);
             G1 = fmaf(w, c.y, G1);
@@ -315,7 +326,7 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
   PixEval e;
   if (!eval_splat(a, bb.x, bb.y, plx, ply, rp.qmax_s, rp.log2_alpha_min, e)) return false;
   const float al = fminf(rp.alpha_max, e.araw);
-  const float inv1m = __frcp_rn(1.f - al);
+  const float inv1m = rcp_approx(1.f - al);  // 1 - alpha in [0.01, 1)
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
   const float w = al * Ti;
   v[7] += w * dC0;
@@ -429,7 +440,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
     const bool have = c0 + lane < wmax;
     Entry e;
     const float4* raw = s_raw[cur][lane];
-    const bool hit = have && make_entry(raw[0], raw[1], raw[2], ox, oy, bx, by, rp, e);
+    const bool hit = have && make_entry(raw[0], raw[1], raw[2], ox, oy, bx, by, rp, e) != 0u;
     __syncwarp();
     if (hit) {
       buf[lane] = e;
@@ -447,9 +458,12 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
+      const unsigned halves = __float_as_uint(cc.w);
       bool contrib = false;
-      if (idx < last0) contrib |= bwd_pixel(a, bb, cc, plx, ply0, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
-      if (idx < last1) contrib |= bwd_pixel(a, bb, cc, plx, ply1, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+      if ((halves & 1u) && idx < last0)
+        contrib |= bwd_pixel(a, bb, cc, plx, ply0, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+      if ((halves & 2u) && idx < last1)
+        contrib |= bwd_pixel(a, bb, cc, plx, ply1, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;
       float* rec = g2d + 12 * (size_t)bid[j];
