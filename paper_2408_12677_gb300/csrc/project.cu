@@ -582,8 +582,7 @@ __global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(const _
     if (t < cnt)
       for (int e = 0; e < NS; ++e) sm.gs[t * RS + e] = 0.f;
   }
-  const int n_views = MULTI ? a.views : 1;  // the one-view variant runs for one view only
-  for (int v = 0; v < n_views; ++v) {
+  for (int v = 0; v < (MULTI ? a.views : 1); ++v) {  // the one-view variant runs for one view only
     float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (t < cnt) {
       if (v > 0) {
