@@ -413,6 +413,86 @@ def run_multi_view(args, rank, world, local_rank):
     }
 
 
+STREAM_SEEDING = {"var_thr": 0.035, "min_size": 2}  # about 50k Gaussians from the first 1200x680 frame
+
+
+def _stream_frame(args):
+    """Ray-cast frame k of the streaming sequence (worker process)."""
+    n_frames, k = args
+    from synth import workloads
+    return workloads.streaming(n_frames=n_frames).frame(k)
+
+
+def _stream_seed(rgb, depth, cam, pose, mask):
+    from synth.quadtree import seed_gaussians
+    return seed_gaussians(rgb, depth, cam, pose, 3, mask=mask, **STREAM_SEEDING)
+
+
+def run_streaming(args, rank, world, local_rank):
+    """Per-frame streaming optimisation at 1200x680: each frame seeds
+    Gaussians where the map's rendered alpha is below 0.5, then 10 batched
+    iterations over the frame and up to 4 random earlier keyframes.  The
+    frames are ray-cast on the host cores before the GPU starts (a spawn
+    process pool); value = optimisation iterations per second of GPU time
+    (CUDA events around each frame's iterations), e2e = frames per second of
+    the whole loop (render for the novelty mask, host seeding, upload,
+    iterations)."""
+    import multiprocessing as mp
+
+    t_gen = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        frames = pool.map(_stream_frame, [(args.frames, k) for k in range(args.frames)])
+    t_gen = time.perf_counter() - t_gen
+
+    import torch
+
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.streaming import StreamingOptimizer
+    from synth import workloads
+
+    torch.cuda.set_device(local_rank)
+    abi.load()
+    st = workloads.streaming(n_frames=args.frames)
+    opt = StreamingOptimizer(st.cam, 3, _stream_seed, iters=10, n_past=4, capacity=1 << 16, device=local_rank)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = opt.ctx.stats()["kernel_launches"]
+    t0 = time.perf_counter()
+    stats = [opt.process_frame(rgb, dep, st.poses[k]) for k, (rgb, dep) in enumerate(frames)]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = opt.ctx.stats()["kernel_launches"] - launches0
+    gpu_ms = sum(s.gpu_ms for s in stats)
+    iters = sum(len(s.views_per_iter) for s in stats)
+    views = sum(sum(s.views_per_iter) for s in stats)
+    gpu_ms, wall = max_over_ranks([gpu_ms, wall], world)
+    return {
+        "metric": METRIC, "value": world * iters / (gpu_ms * 1e-3), "unit": "it/s", "n_gpus": world,
+        "steps": iters, "warmup": 0, "ms_per_step": gpu_ms / iters, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"streaming: {args.frames} frames at 1200x680 (fx 600), novelty seeding where "
+                               "rendered alpha < 0.5, 10 batched iterations per frame over the frame and up to 4 "
+                               "random earlier keyframes, SH degree 3, fp32",
+                   "frames": args.frames, "seeding": STREAM_SEEDING, "host_generation_s": t_gen,
+                   "parallelism": f"replicas{world}", "timing": "CUDA events around each frame's iterations"},
+        "stream": {
+            "gaussians_first_frame": stats[0].n_gaussians, "gaussians_last_frame": stats[-1].n_gaussians,
+            "capacity_last": stats[-1].capacity, "keyframes": sum(s.keyframe for s in stats),
+            "views_per_iteration_mean": views / iters, "gpu_ms_per_frame": gpu_ms / len(stats),
+            "host_ms_per_frame": 1e3 * wall / len(stats), "loss_first": stats[0].loss, "loss_last": stats[-1].loss,
+            "new_per_frame": [s.new_gaussians for s in stats],
+        },
+        # e2e step = one frame: its RGB-D upload, the alpha read-back for the novelty mask, the new
+        # Gaussians' upload and one loss read
+        "e2e": {"value": world * len(stats) / wall, "unit": "frames/s",
+                "h2d_bytes_per_step": 16 * st.cam.width * st.cam.height
+                + int(sum(s.new_gaussians for s in stats) / len(stats)) * 4 * (11 + 48),
+                "d2h_bytes_per_step": 4 * st.cam.width * st.cam.height + 4},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+
 def max_over_ranks(values, world):
     """Element-wise maximum of per-rank timings (gloo/NCCL all-reduce)."""
     import torch
@@ -527,8 +607,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-pixels", type=int, default=12288)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view"],
+    ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view", "streaming"],
                     help="multi_view: the batched 8-view iteration vs the same iteration view by view")
+    ap.add_argument("--frames", type=int, default=40, help="streaming: frames of the sequence")
     ap.add_argument("--no-compare", action="store_true",
                     help="multi_view: skip the view-by-view comparison arm (e.g. for a profiler capture)")
     args = ap.parse_args()
@@ -542,8 +623,9 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    if args.workload == "multi_view":
-        out = run_multi_view(args, rank, world, local_rank)
+    if args.workload in ("multi_view", "streaming"):
+        run = run_multi_view if args.workload == "multi_view" else run_streaming
+        out = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(out))
         if world > 1:

@@ -1,0 +1,226 @@
+"""Per-frame streaming optimisation: GSFusion's online loop around the hot
+path (Sec. III-B.2-3).  For every incoming RGB-D frame:
+
+1. render the current map at the frame's pose (gs_render_fwd) and read the
+   alpha image back;
+2. seed new Gaussians only where the map does not cover the frame yet: the
+   caller's quadtree seeding function receives the mask alpha < 0.5 (the
+   novelty rule; the paper tests the TSDF voxel weight instead, Sec. III-B.2);
+3. append them to the map (capacity-doubling buffers, Adam moments of the
+   new Gaussians zero);
+4. keep the frame as a keyframe when it added more than 50 Gaussians
+   (Sec. IV-A.4);
+5. run ``iters`` optimisation iterations, each one batched over the current
+   frame and up to ``n_past`` random earlier keyframes (Sec. III-B.3 revisits
+   keyframes; one Adam step per iteration on the summed loss).
+
+The map lives in flat buffers of a fixed capacity: slots [0, n) hold the
+Gaussians, the others are inert (opacity logit and log-scales -30, so the
+projection gives them no tile and their gradient, hence their Adam update,
+is zero).  The kernels always run over the whole capacity, which only changes
+when the map doubles.  All per-Gaussian arithmetic runs in libgsplat; this
+module moves buffers and chooses views.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import abi
+from .torch_api import PARAM_NAMES, Context, GaussianModel, camera_struct, flat_sizes, n_sh
+
+INERT_LOGIT = -30.0
+INERT_LOG_SCALE = -30.0
+NOVELTY_ALPHA = 0.5
+KEYFRAME_MIN_NEW = 50
+
+
+def inert_params(n: int, sh_degree: int) -> dict:
+    """Host parameters of n inert slots."""
+    K = n_sh(sh_degree)
+    quats = np.zeros((n, 4), np.float32)
+    quats[:, 0] = 1.0
+    return {"means": np.zeros((n, 3), np.float32),
+            "log_scales": np.full((n, 3), INERT_LOG_SCALE, np.float32), "quats": quats,
+            "opacity_logits": np.full(n, INERT_LOGIT, np.float32), "sh": np.zeros((n, K, 3), np.float32),
+            "sh_degree": sh_degree}
+
+
+def novelty_mask(alpha: np.ndarray, thr: float = NOVELTY_ALPHA) -> np.ndarray:
+    """Pixels the map does not cover yet (rendered alpha below ``thr``)."""
+    return np.asarray(alpha) < thr
+
+
+def pick_views(rng: np.random.Generator, n_keyframes: int, current_is_keyframe: bool, n_past: int) -> list:
+    """Indices of the earlier keyframes an iteration optimises besides the
+    current frame: up to n_past distinct ones, drawn uniformly (the current
+    frame, if it became a keyframe, is the last one and is not drawn)."""
+    pool = n_keyframes - (1 if current_is_keyframe else 0)
+    if pool <= 0 or n_past <= 0:
+        return []
+    return sorted(rng.choice(pool, size=min(n_past, pool), replace=False).tolist())
+
+
+class GrowingMap:
+    """Gaussian map in capacity-doubling flat buffers (parameters, gradient,
+    Adam moments); ``n`` live slots, the rest inert."""
+
+    def __init__(self, sh_degree: int, capacity: int = 1 << 16, device: int = 0):
+        self.sh_degree = int(sh_degree)
+        self.device = device
+        self.n = 0
+        self.model = GaussianModel(inert_params(int(capacity), self.sh_degree), device=f"cuda:{device}")
+
+    @property
+    def capacity(self) -> int:
+        return self.model.n
+
+    def _grow(self, need: int):
+        cap = self.capacity
+        while cap < need:
+            cap *= 2
+        old = self.model
+        new = GaussianModel(inert_params(cap, self.sh_degree), device=f"cuda:{self.device}")
+        for name in PARAM_NAMES:  # copy the first old.n slots of every block
+            new.p[name][:old.n].copy_(old.p[name])
+        for src, dst in ((old.m, new.m), (old.v, new.v)):
+            so = do = 0
+            for size_old, size_new in zip(flat_sizes(old.n, self.sh_degree), flat_sizes(cap, self.sh_degree)):
+                dst[do:do + size_old].copy_(src[so:so + size_old])
+                so += size_old
+                do += size_new
+        self.model = new
+
+    def append(self, params: dict) -> int:
+        """Write k new Gaussians into slots [n, n + k) (moments zero)."""
+        k = int(np.asarray(params["means"]).shape[0])
+        if k == 0:
+            return 0
+        if self.n + k > self.capacity:
+            self._grow(self.n + k)
+        m = self.model
+        dev = m.flat.device
+        a, b = self.n, self.n + k
+        for name in PARAM_NAMES:
+            m.p[name][a:b].copy_(torch.as_tensor(np.asarray(params[name], np.float32), device=dev))
+        off = 0
+        for size in flat_sizes(m.n, self.sh_degree):  # zero the new slots' moments in every block
+            per = size // m.n
+            m.m[off + a * per:off + b * per].zero_()
+            m.v[off + a * per:off + b * per].zero_()
+            off += size
+        self.n = b
+        return k
+
+    def live_params(self) -> dict:
+        """Host copy of the live Gaussians' parameters."""
+        out = {k: v[:self.n].detach().cpu().numpy().copy() for k, v in self.model.p.items()}
+        out["sh_degree"] = self.sh_degree
+        return out
+
+
+@dataclasses.dataclass
+class Keyframe:
+    cam: object
+    view: abi.gs_viewmat
+    rgb: torch.Tensor    # [3, H, W] device
+    depth: torch.Tensor  # [H, W] device
+
+
+@dataclasses.dataclass
+class FrameStats:
+    index: int
+    new_gaussians: int
+    n_gaussians: int
+    capacity: int
+    keyframe: bool
+    views_per_iter: list
+    loss: float
+    gpu_ms: float        # CUDA-event time of the frame's optimisation iterations
+    host_ms: float       # wall time of the whole frame (render, seeding, upload, iterations)
+
+
+class StreamingOptimizer:
+    """The per-frame loop over one camera model (all frames share it)."""
+
+    def __init__(self, cam, sh_degree: int, seed_fn, iters: int = 10, n_past: int = 4, capacity: int = 1 << 16,
+                 raster_cfg=None, adam_cfg=None, w_color: float = 0.8, w_depth: float = 0.2, rng_seed: int = 0,
+                 device: int = 0, ctx: Context | None = None):
+        self.cam = cam
+        self.cam_s = camera_struct(cam)
+        self.seed_fn = seed_fn
+        self.iters, self.n_past = int(iters), int(n_past)
+        self.map = GrowingMap(sh_degree, capacity, device)
+        self.ctx = ctx or Context(device)
+        self.rcfg = raster_cfg or abi.raster_cfg()
+        self.acfg = adam_cfg or abi.adam_cfg(zero_grads=1)
+        self.w_color, self.w_depth = float(w_color), float(w_depth)
+        self.rng = np.random.default_rng(rng_seed)
+        self.keyframes: list[Keyframe] = []
+        self.step = 0
+        H, W = cam.height, cam.width
+        dev = torch.device("cuda", device)
+        slots = 1 + self.n_past
+        self.color = [torch.empty((3, H, W), device=dev) for _ in range(slots)]
+        self.depth = [torch.empty((H, W), device=dev) for _ in range(slots)]
+        self.alpha = [torch.empty((H, W), device=dev) for _ in range(slots)]
+        self.dLdc = [torch.empty((3, H, W), device=dev) for _ in range(slots)]
+        self.dLdd = [torch.empty((H, W), device=dev) for _ in range(slots)]
+        self.loss = torch.zeros(1, device=dev)
+        self.frame_index = 0
+
+    def render_alpha(self, view) -> np.ndarray:
+        """Alpha image of the current map at ``view`` (host array)."""
+        if self.map.n == 0:
+            return np.zeros((self.cam.height, self.cam.width), np.float32)
+        abi.gs_render_fwd(self.ctx.handle, self.map.model.gaussians(), self.cam_s, view, self.rcfg, None, None,
+                          self.alpha[0])
+        return self.alpha[0].cpu().numpy()
+
+    def iterate(self, views: list[Keyframe]):
+        """One batched optimisation iteration over ``views``."""
+        h = self.ctx.handle
+        m = self.map.model
+        g = m.gaussians()
+        V = len(views)
+        cams = [self.cam_s] * V
+        vms = [k.view for k in views]
+        abi.gs_render_fwd_batched(h, g, cams, vms, self.rcfg, self.color[:V], self.depth[:V], self.alpha[:V])
+        abi.gs_loss_l1_batched(h, cams, self.color[:V], self.depth[:V], [k.rgb for k in views],
+                               [k.depth for k in views], self.w_color, self.w_depth, self.loss, self.dLdc[:V],
+                               self.dLdd[:V])
+        self.step += 1
+        abi.gs_render_bwd_adam_batched(h, g, cams, vms, self.rcfg, self.dLdc[:V], self.dLdd[:V], None, m.flat, m.m,
+                                       m.v, self.acfg, self.step)
+
+    def process_frame(self, rgb: np.ndarray, depth: np.ndarray, pose) -> FrameStats:
+        """rgb [H, W, 3] in [0, 1], depth [H, W] (0 = invalid), pose: world-to-camera (R, t)."""
+        t0 = time.perf_counter()
+        view = abi.make_viewmat(pose.R, pose.t)
+        alpha = self.render_alpha(view)
+        new = self.seed_fn(rgb, depth, self.cam, pose, novelty_mask(alpha))
+        k = self.map.append(new)
+        dev = self.map.model.flat.device
+        cur = Keyframe(self.cam, view, torch.as_tensor(np.ascontiguousarray(np.transpose(rgb, (2, 0, 1)), np.float32),
+                                                        device=dev),
+                       torch.as_tensor(np.ascontiguousarray(depth, np.float32), device=dev))
+        is_key = k > KEYFRAME_MIN_NEW or not self.keyframes
+        if is_key:
+            self.keyframes.append(cur)
+        sizes = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(self.iters):
+            past = [self.keyframes[i] for i in pick_views(self.rng, len(self.keyframes), is_key, self.n_past)]
+            views = [cur] + past
+            sizes.append(len(views))
+            self.iterate(views)
+        ev1.record()
+        torch.cuda.synchronize()
+        stats = FrameStats(self.frame_index, k, self.map.n, self.map.capacity, is_key, sizes, float(self.loss.item()),
+                           ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
+        self.frame_index += 1
+        return stats

@@ -66,9 +66,11 @@ def quadtree_leaves(rgb: np.ndarray, var_thr: float = 0.01, max_size: int = 64, 
 
 
 def seed_gaussians(rgb: np.ndarray, depth: np.ndarray, cam: Camera, pose: Pose, sh_degree: int,
-                   var_thr: float = 0.01, max_size: int = 64):
-    """Quadtree-seed Gaussians from one RGB-D frame; returns a parameter dict."""
-    leaves = quadtree_leaves(rgb, var_thr, max_size)
+                   var_thr: float = 0.01, max_size: int = 64, min_size: int = 1, mask: np.ndarray | None = None):
+    """Quadtree-seed Gaussians from one RGB-D frame; returns a parameter dict.
+    ``mask`` [H, W] (optional): only leaves whose centre pixel is True are
+    seeded (the novelty rule of the per-frame loop)."""
+    leaves = quadtree_leaves(rgb, var_thr, max_size, min_size)
     x0, y0, w, h = leaves.T
     uc = x0 + w / 2.0
     vc = y0 + h / 2.0
@@ -76,6 +78,8 @@ def seed_gaussians(rgb: np.ndarray, depth: np.ndarray, cam: Camera, pose: Pose, 
     pj = np.minimum(np.floor(vc).astype(np.int64), cam.height - 1)
     z = depth[pj, pi].astype(np.float64)
     ok = z > 0
+    if mask is not None:
+        ok &= np.asarray(mask, bool)[pj, pi]
     uc, vc, z, w, h, pi, pj = uc[ok], vc[ok], z[ok], w[ok], h[ok], pi[ok], pj[ok]
     pc = np.stack([(uc - cam.cx) * z / cam.fx, (vc - cam.cy) * z / cam.fy, z], 1)
     pw = (pc - pose.t.astype(np.float64)[None]) @ pose.R.astype(np.float64)  # R^T (p_c - t)

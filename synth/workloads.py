@@ -243,3 +243,44 @@ RECIPES = {
     "scale_stress": scale_stress,
     "multi_view": multi_view,
 }
+
+
+# ----------------------------------------------------------------------------
+# streaming per-frame sequence
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Stream:
+    """A smooth camera trajectory through one synthetic room; ``frame(k)``
+    ray-casts frame k (RGB [H, W, 3] and depth [H, W], float32)."""
+    room: object
+    cam: Camera
+    poses: list
+
+    def frame(self, k: int):
+        return raycast(self.room, self.cam, self.poses[k])
+
+
+def stream_poses(n_frames: int, radius=(1.6, 1.1), height=0.25, sweep=np.pi):
+    """Eye on an ellipse around the room centre (half a turn over the
+    sequence by default), looking across the room (inwards, with a slow yaw
+    swing) and a slow pitch oscillation."""
+    poses, eyes = [], []
+    for k in range(n_frames):
+        s = k / max(n_frames - 1, 1)
+        a = sweep * s
+        eye = ROOM_CENTER + np.array([radius[0] * np.cos(a), radius[1] * np.sin(a), height * np.sin(2 * a) - 0.1])
+        yaw = a + np.pi + 0.5 * np.sin(3 * a)
+        pitch = -0.12 + 0.1 * np.sin(2 * np.pi * s)
+        poses.append(yaw_pitch_pose(eye, yaw, pitch))
+        eyes.append(eye)
+    return poses, eyes
+
+
+def streaming(seed: int = 1005, n_frames: int = 200, width: int = 1200, height: int = 680, f: float = 600.0) -> Stream:
+    """The per-frame streaming sequence: ``n_frames`` frames of a smooth
+    trajectory through a room generated with the trajectory kept clear of
+    boxes."""
+    poses, eyes = stream_poses(n_frames)
+    room = make_room(seed, keep_clear=eyes[:: max(1, n_frames // 40)] + [eyes[-1]])
+    cam = Camera(f, f, width / 2.0, height / 2.0, width, height)
+    return Stream(room, cam, poses)

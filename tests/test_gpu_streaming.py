@@ -1,0 +1,109 @@
+"""The per-frame streaming loop on the GPU: the map grows only where it does
+not cover a frame yet, doubles its capacity without disturbing live slots,
+keeps inert slots inert, and its batched gradients at checkpoints match the
+FP64 oracle (and central differences of the oracle loss, h = 1e-4)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import render as R
+from synth import workloads
+from synth.quadtree import seed_gaussians
+from tests._util import ensure_built
+from tests.test_gpu_grad import check_grad_arrays
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logits", "sh")
+DEG = 1
+
+
+def _seed(rgb, depth, cam, pose, mask):
+    return seed_gaussians(rgb, depth, cam, pose, DEG, var_thr=0.03, min_size=4, mask=mask)
+
+
+@pytest.fixture(scope="module")
+def run():
+    ensure_built()
+    from paper_2408_12677_gb300.streaming import StreamingOptimizer
+    st = workloads.streaming(n_frames=8, width=96, height=64, f=48.0)
+    frames = [st.frame(k) for k in range(6)]
+    opt = StreamingOptimizer(st.cam, DEG, _seed, iters=3, n_past=2, capacity=256, rng_seed=1)
+    stats = [opt.process_frame(rgb, dep, st.poses[k]) for k, (rgb, dep) in enumerate(frames)]
+    return st, frames, opt, stats
+
+
+def test_map_grows_where_uncovered_and_capacity_doubles(run):
+    st, frames, opt, stats = run
+    ns = [s.n_gaussians for s in stats]
+    assert ns[0] > 200 and all(b >= a for a, b in zip(ns, ns[1:]))
+    assert stats[-1].capacity > 256 and stats[-1].capacity >= ns[-1]
+    assert stats[0].keyframe and all(np.isfinite(s.loss) for s in stats)
+    # the last frame again: its pixels are covered now, so it seeds far fewer Gaussians
+    rgb, dep = frames[-1]
+    again = opt.process_frame(rgb, dep, st.poses[len(frames) - 1])
+    assert again.new_gaussians < 0.2 * stats[0].new_gaussians, (again.new_gaussians, stats[0].new_gaussians)
+    m = opt.map.model
+    n = opt.map.n
+    assert torch.isfinite(m.flat).all()
+    assert bool((m.p["opacity_logits"][n:] == -30.0).all()) and bool((m.p["log_scales"][n:] == -30.0).all())
+    from paper_2408_12677_gb300.torch_api import flat_sizes
+    off = 0
+    for size in flat_sizes(m.n, DEG):  # inert slots never get Adam state
+        per = size // m.n
+        assert float(m.m[off + n * per:off + size].abs().max()) == 0.0
+        assert float(m.v[off + n * per:off + size].abs().max()) == 0.0
+        off += size
+
+
+def test_checkpoint_gradients_match_oracle(run):
+    """The batched gradient of the current frame + two keyframes against the
+    FP64 oracle's multi-view gradient, on the live slots of the grown map."""
+    from paper_2408_12677_gb300 import abi
+    st, frames, opt, stats = run
+    views = [opt.keyframes[-1], opt.keyframes[0]] + ([opt.keyframes[1]] if len(opt.keyframes) > 2 else [])
+    h = opt.ctx.handle
+    m = opt.map.model
+    V = len(views)
+    cams = [opt.cam_s] * V
+    vms = [k.view for k in views]
+    abi.gs_render_fwd_batched(h, m.gaussians(), cams, vms, opt.rcfg, opt.color[:V], opt.depth[:V], opt.alpha[:V])
+    abi.gs_loss_l1_batched(h, cams, opt.color[:V], opt.depth[:V], [k.rgb for k in views], [k.depth for k in views],
+                           0.8, 0.2, opt.loss, opt.dLdc[:V], opt.dLdd[:V])
+    m.grad.zero_()
+    gp = torch.zeros((V, 6), device="cuda")
+    abi.gs_render_bwd_batched(h, m.gaussians(), cams, vms, opt.rcfg, opt.dLdc[:V], opt.dLdd[:V], None, m.grads(), gp)
+    torch.cuda.synchronize()
+    n = opt.map.n
+    g = {k: v[:n].detach().cpu().numpy().copy() for k, v in m.g.items()}
+    for k, v in m.g.items():
+        assert float(v[n:].abs().max()) == 0.0, k  # inert slots: exactly no gradient
+    g["pose"] = gp.cpu().numpy()
+    P = opt.map.live_params()
+    poses = [(np.array(k.view.R, np.float64).reshape(3, 3), np.array(k.view.t, np.float64)) for k in views]
+    targets = [(k.rgb.cpu().numpy(), k.depth.cpu().numpy()) for k in views]
+    L, og, _ = R.multiview_gradients(P, DEG, [st.cam] * V, poses, targets)
+    assert abs(float(opt.loss.item()) - float(L)) <= 1e-4 * float(L)
+    check_grad_arrays(g, og, max(2, int(0.004 * n)))
+
+    # central differences of the FP64 loss (h = 1e-4) at the largest gradient entries
+    Pd = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in P.items()}
+    checked = 0
+    for name in ("means", "log_scales", "opacity_logits", "sh"):
+        G = og[name].numpy().ravel()
+        for i in np.argsort(-np.abs(G))[:3]:
+            def f(hh):
+                Q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in Pd.items()}
+                Q[name].reshape(-1)[i] += hh
+                T = R.to_tensors(Q)
+                with torch.no_grad():
+                    return sum(float(R.render_loss(T, DEG, st.cam, Rm, tv, trgb, tdep)[0])
+                               for (Rm, tv), (trgb, tdep) in zip(poses, targets))
+            d1 = (f(1e-4) - f(-1e-4)) / 2e-4
+            d2 = (f(5e-5) - f(-5e-5)) / 1e-4
+            if abs(d1 - d2) > 1e-3 * max(abs(d1), abs(d2), 1e-9):
+                continue  # a kink (L1 sign, support edge) within h
+            gpu = g[name].ravel()[i]
+            assert abs(gpu - d1) <= 2e-3 * abs(d1) + 1e-6 * np.abs(G).max(), (name, i, gpu, d1)
+            checked += 1
+    assert checked >= 6
