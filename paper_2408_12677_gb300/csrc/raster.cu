@@ -22,6 +22,10 @@ namespace gs {
 namespace {
 
 constexpr int kThreads = 128;  // 4 independent warps per CTA, one 8 x 8 pixel block each
+// Backward pass: when at most this many lanes contribute to a Gaussian, they
+// add their values with per-lane atomics (10 issue slots) instead of the warp
+// reduction (about 40); the kernel is issue-bound, the L2 atomics are not.
+constexpr int kAtomicLanes = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // One list entry in tile-local coordinates:
@@ -467,7 +471,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;
       float* rec = g2d + 12 * (size_t)bid[j];
-      if (__popc(m) <= 2) {
+      if (__popc(m) <= kAtomicLanes) {
         if (contrib) {
 #pragma unroll
           for (int k = 0; k < 10; ++k) atomicAdd(&rec[rec_off(k)], v[k]);
