@@ -295,6 +295,35 @@ gs_status gs_loss_l1_batched(gs_ctx *ctx, int32_t n_views, const gs_camera *cams
                              float w_color, float w_depth, float *loss, float *const *dL_dcolor,
                              float *const *dL_ddepth, gs_stream_t stream);
 
+/* One optimisation iteration of the online optimisation (Sec. III-B.3) in
+ * one call: the forward pass with the loss of gs_loss_l1 (Eq. 12 plus the
+ * depth term) computed in the compositing epilogue, then the backward pass
+ * fused with the Adam step, as gs_render_bwd_adam.  The same result as
+ * gs_render_fwd + gs_loss_l1 + gs_render_bwd_adam (the same image
+ * gradients; the loss value is summed in another order), but the rendered
+ * images and the loss image gradients never go to caller memory: the
+ * context keeps the gradients.  target_rgb [3, H, W], target_depth [H, W]
+ * (0 = invalid); loss (device float[1]) receives L; params / m / v, adam and
+ * step as in gs_render_bwd_adam (step = 0: device step counter).  The
+ * forward state stays in the context as after gs_render_fwd. */
+gs_status gs_train_step(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam, const gs_viewmat *view,
+                        const gs_raster_cfg *cfg, const float *target_rgb, const float *target_depth,
+                        float w_color, float w_depth, float *loss, float *params, float *m, float *v,
+                        const gs_adam_cfg *adam, int64_t step, gs_stream_t stream);
+
+/* gs_train_step for a batch of views: loss = sum over views of L_v, one Adam
+ * step on the summed gradient (as gs_loss_l1_batched and
+ * gs_render_bwd_adam_batched).  target_rgb, target_depth: host arrays of
+ * n_views device pointers; color, depth, alpha: optional host arrays of
+ * n_views device pointers (each array and entry nullable) that receive the
+ * rendered images. */
+gs_status gs_train_step_batched(gs_ctx *ctx, const gs_gaussians *g, int32_t n_views, const gs_camera *cams,
+                                const gs_viewmat *views, const gs_raster_cfg *cfg,
+                                const float *const *target_rgb, const float *const *target_depth,
+                                float w_color, float w_depth, float *loss, float *params, float *m, float *v,
+                                const gs_adam_cfg *adam, int64_t step, float *const *color,
+                                float *const *depth, float *const *alpha, gs_stream_t stream);
+
 /* Tile-shape autotuner (no counterpart in the paper, whose rasterizer uses
  * one fixed tile size).  Times, for each of the GS_AUTOTUNE_CANDIDATES tile
  * shapes 16x16, 8x32 and 32x8 (in that order), `reps` passes of everything

@@ -108,6 +108,12 @@ EXPORTS = {
                                              C.POINTER(gs_adam_cfg), C.c_int64, P, P]),
     "gs_loss_l1_batched": (C.c_int, [P, C.c_int32, C.POINTER(gs_camera), PP, PP, PP, PP, C.c_float, C.c_float, P,
                                      PP, PP, P]),
+    "gs_train_step": (C.c_int, [P, C.POINTER(gs_gaussians), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                                C.POINTER(gs_raster_cfg), P, P, C.c_float, C.c_float, P, P, P, P,
+                                C.POINTER(gs_adam_cfg), C.c_int64, P]),
+    "gs_train_step_batched": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera),
+                                        C.POINTER(gs_viewmat), C.POINTER(gs_raster_cfg), PP, PP, C.c_float,
+                                        C.c_float, P, P, P, P, C.POINTER(gs_adam_cfg), C.c_int64, PP, PP, PP, P]),
     "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                               C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
@@ -418,3 +424,24 @@ def gs_autotune(ctx, gaussians, cams, views, cfg: gs_raster_cfg, reps: int = 5, 
                             ms, _stream(stream))
     _check(ctx, st, "gs_autotune")
     return list(ms)
+
+
+def gs_train_step(ctx, gaussians, cam, view, cfg, target_rgb, target_depth, w_color, w_depth, loss, params, m, v,
+                  adam: gs_adam_cfg, step: int, stream=None):
+    st = load().gs_train_step(ctx, C.byref(gaussians), C.byref(cam), C.byref(view), C.byref(cfg),
+                              _f32(target_rgb, "target_rgb"), _f32(target_depth, "target_depth"), float(w_color),
+                              float(w_depth), _f32(loss, "loss"), _f32(params, "params"), _f32(m, "m"), _f32(v, "v"),
+                              C.byref(adam), int(step), _stream(stream))
+    _check(ctx, st, "gs_train_step")
+
+
+def gs_train_step_batched(ctx, gaussians, cams, views, cfg, target_rgb, target_depth, w_color, w_depth, loss, params,
+                          m, v, adam: gs_adam_cfg, step: int, color=None, depth=None, alpha=None, stream=None):
+    V = len(cams)
+    st = load().gs_train_step_batched(ctx, C.byref(gaussians), V, _cams(cams), _views(views), C.byref(cfg),
+                                      _ptrs(target_rgb, "target_rgb", V), _ptrs(target_depth, "target_depth", V),
+                                      float(w_color), float(w_depth), _f32(loss, "loss"), _f32(params, "params"),
+                                      _f32(m, "m"), _f32(v, "v"), C.byref(adam), int(step),
+                                      _ptrs(color, "color", V), _ptrs(depth, "depth", V), _ptrs(alpha, "alpha", V),
+                                      _stream(stream))
+    _check(ctx, st, "gs_train_step_batched")

@@ -55,6 +55,9 @@ struct gs_ctx {
   int32_t* last = nullptr;
   float* loss_partials = nullptr;
   float* tune_img = nullptr;  // zero image gradients for the autotuner
+  float* dl_img = nullptr;    // per pixel: dL/dcolor (3 planes) and the depth residual sign (fused loss)
+  float* tile_loss = nullptr;  // per (tile, 8 x 8 block): fused-loss partial sums (3 floats)
+  float* d_dscale = nullptr;   // per view: depth-gradient scale of the fused loss
   int64_t cap_tune = 0;
   // device scalars and their host mirror
   uint32_t* d_npairs = nullptr;
@@ -191,6 +194,7 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   GS_CUDA(c, regrow(&c->toffset, cap));
   GS_CUDA(c, regrow(&c->tcursor, cap));
   GS_CUDA(c, regrow(&c->torder, cap));
+  GS_CUDA(c, regrow(&c->tile_loss, 12 * cap));
   c->cap_t = cap;
   c->have_state = false;
   return GS_OK;
@@ -202,6 +206,7 @@ gs_status ensure_px(gs_ctx* c, int64_t npx) {
   const int64_t cap = grow_target(npx, c->cap_px);
   GS_CUDA(c, regrow(&c->T_final, cap));
   GS_CUDA(c, regrow(&c->last, cap));
+  GS_CUDA(c, regrow(&c->dl_img, 4 * cap));
   // per-block partials (blocks of every view: <= blocks(total) + views) and per-view scales
   const int64_t lb = loss_blocks((int)std::min<int64_t>(cap, INT32_MAX - 4096));
   GS_CUDA(c, regrow(&c->loss_partials, 3 * (lb + kMaxViews) + kMaxViews + 4));
@@ -464,6 +469,7 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_overflow, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bigmeta, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
   if (e == cudaSuccess) init_project_kernels();
@@ -514,6 +520,9 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->last);
   cudaFree(c->loss_partials);
   cudaFree(c->tune_img);
+  cudaFree(c->dl_img);
+  cudaFree(c->tile_loss);
+  cudaFree(c->d_dscale);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
   cudaFree(c->d_overflow);
@@ -743,6 +752,9 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.order = c->st_ordered ? c->torder : nullptr;
   ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;
   ra.num_sms = c->num_sms;
+  ra.loss_partials = nullptr;
+  ra.w_color = 0.f;
+  ra.depth_scale = nullptr;
   for (int v = 0; v < kMaxViews; ++v) {
     RasterView& rv = ra.v[v];
     const bool live = v < c->st_views;
@@ -753,13 +765,24 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
     rv.pix_base = live ? c->st_pix_base[v] : 0;
     rv.color = rv.depth = rv.alpha = nullptr;
     rv.dLdc = rv.dLdd = rv.dLda = nullptr;
+    rv.trgb = rv.tdep = nullptr;
+    rv.loss_dc = rv.loss_dd = nullptr;
   }
   return ra;
 }
 
+// Fused loss of a training step: targets per view and the colour weight; the
+// image gradients go to the context's dl_img, the partial sums to tile_loss.
+struct FusedLoss {
+  const float* const* trgb;
+  const float* const* tdep;
+  float w_color;
+};
+
 gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
                            const gs_viewmat* views, const gs_raster_cfg* cfg, float* const* color,
-                           float* const* depth, float* const* alpha, cudaStream_t s) {
+                           float* const* depth, float* const* alpha, cudaStream_t s,
+                           const FusedLoss* fl = nullptr) {
   gs_status st;
   if ((st = check_gauss(c, g)) != GS_OK || (st = check_views(c, V, cams, views)) != GS_OK ||
       (st = check_cfg(c, cfg)) != GS_OK)
@@ -809,6 +832,17 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     ra.v[v].depth = depth ? depth[v] : nullptr;
     ra.v[v].alpha = alpha ? alpha[v] : nullptr;
   }
+  if (fl) {
+    ra.loss_partials = c->tile_loss;
+    ra.w_color = fl->w_color;
+    for (int v = 0; v < V; ++v) {
+      const int64_t np = (int64_t)cams[v].width * cams[v].height;
+      ra.v[v].trgb = fl->trgb[v];
+      ra.v[v].tdep = fl->tdep[v];
+      ra.v[v].loss_dc = c->dl_img + 4 * L.pix_base[v];
+      ra.v[v].loss_dd = c->dl_img + 4 * L.pix_base[v] + 3 * np;
+    }
+  }
   {
     StageTimer t(c, GS_STAGE_RASTER_FWD, s);
     launch_raster_fwd(ra, c->T_final, c->last, c->counting ? c->d_evals : nullptr, s);
@@ -838,10 +872,12 @@ gs_status check_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
 
 // raster backward into the context's per-item gradient records
 gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
-                          const float* const* dL_ddepth, const float* const* dL_dalpha, cudaStream_t s) {
+                          const float* const* dL_ddepth, const float* const* dL_dalpha, cudaStream_t s,
+                          const float* depth_scale = nullptr) {
   const int64_t items = c->st_n * c->st_views;
   GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)items, s));
   RasterArgs ra = raster_args(c, cfg);
+  ra.depth_scale = depth_scale;
   for (int v = 0; v < c->st_views; ++v) {
     ra.v[v].dLdc = dL_dcolor[v];
     ra.v[v].dLdd = dL_ddepth[v];
@@ -891,7 +927,7 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
                                 const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                                 const float* const* dL_ddepth, const float* const* dL_dalpha, float* params,
                                 float* m, float* v, const gs_adam_cfg* adam, int64_t step, float* dL_dpose,
-                                cudaStream_t s) {
+                                cudaStream_t s, const float* depth_scale = nullptr) {
   gs_status st;
   if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
@@ -902,7 +938,7 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
     return fail(c, GS_ERR_INVALID_ARG, "the Gaussian arrays must be the flat parameter buffer's blocks");
   GS_CUDA(c, cudaSetDevice(c->device));
   if (n == 0) return GS_OK;
-  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s)) != GS_OK) return st;
+  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s, depth_scale)) != GS_OK) return st;
   const ProjectArgs pa = project_args(g, V, cams, views, cfg, c->st_map, c->st_map.tiles_x);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
@@ -993,9 +1029,68 @@ gs_status loss_views(gs_ctx* c, int32_t V, const gs_camera* cams, const float* c
   return GS_OK;
 }
 
+// One optimisation iteration: forward pass with the loss fused into the
+// compositing epilogue, the loss finalised on the device (with the per-view
+// depth-gradient scales), then the backward pass fused with the Adam step,
+// reading the image gradients from the context.
+gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
+                           const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* target_rgb,
+                           const float* const* target_depth, float w_color, float w_depth, float* loss,
+                           float* params, float* m, float* v, const gs_adam_cfg* adam, int64_t step,
+                           float* const* color, float* const* depth, float* const* alpha, cudaStream_t s) {
+  if (V < 1 || V > kMaxViews) return fail(c, GS_ERR_INVALID_ARG, "n_views must be in [1, 16]");
+  if (!cams || !target_rgb || !target_depth || !loss)
+    return fail(c, GS_ERR_INVALID_ARG, "train step: NULL cameras, targets or loss");
+  for (int k = 0; k < V; ++k)
+    if (!target_rgb[k] || !target_depth[k]) return fail(c, GS_ERR_INVALID_ARG, "train step: NULL target image");
+  if (!std::isfinite(w_color) || !std::isfinite(w_depth)) return fail(c, GS_ERR_INVALID_ARG, "non-finite weight");
+  gs_status st;
+  if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
+  const FusedLoss fl{target_rgb, target_depth, w_color};
+  if ((st = render_fwd_views(c, g, V, cams, views, cfg, color, depth, alpha, s, &fl)) != GS_OK) return st;
+  RasterArgs ra = raster_args(c, cfg);
+  ra.loss_partials = c->tile_loss;
+  ra.w_color = w_color;
+  {
+    StageTimer t(c, GS_STAGE_LOSS, s);
+    launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "loss finalize");
+  const float* dlc[kMaxViews];
+  const float* dld[kMaxViews];
+  for (int k = 0; k < V; ++k) {
+    const int64_t np = (int64_t)cams[k].width * cams[k].height;
+    dlc[k] = c->dl_img + 4 * c->st_pix_base[k];
+    dld[k] = c->dl_img + 4 * c->st_pix_base[k] + 3 * np;
+  }
+  return render_bwd_adam_views(c, g, V, cams, views, cfg, dlc, dld, nullptr, params, m, v, adam, step, nullptr, s,
+                               c->d_dscale);
+}
+
 }  // namespace
 
 extern "C" {
+
+gs_status gs_train_step(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
+                        const gs_raster_cfg* cfg, const float* target_rgb, const float* target_depth,
+                        float w_color, float w_depth, float* loss, float* params, float* m, float* v,
+                        const gs_adam_cfg* adam, int64_t step, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
+  return train_step_views(c, g, 1, cam, view, cfg, &target_rgb, &target_depth, w_color, w_depth, loss, params, m, v,
+                          adam, step, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+gs_status gs_train_step_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
+                                const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* target_rgb,
+                                const float* const* target_depth, float w_color, float w_depth, float* loss,
+                                float* params, float* m, float* v, const gs_adam_cfg* adam, int64_t step,
+                                float* const* color, float* const* depth, float* const* alpha,
+                                gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  return train_step_views(c, g, n_views, cams, views, cfg, target_rgb, target_depth, w_color, w_depth, loss, params,
+                          m, v, adam, step, color, depth, alpha, (cudaStream_t)stream);
+}
 
 gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
                         const gs_raster_cfg* cfg, float* color, float* depth, float* alpha, gs_stream_t stream) {

@@ -151,6 +151,10 @@ struct RasterView {
   int64_t pix_base;    // first pixel of the view in the T_final / last buffers
   float *color, *depth, *alpha;           // forward outputs (each nullable)
   const float *dLdc, *dLdd, *dLda;        // backward inputs (dLda nullable)
+  // forward with the fused loss: targets in, image gradients out (dLdd
+  // unscaled: the sign of the depth residual, 0 where the target is invalid)
+  const float *trgb, *tdep;
+  float *loss_dc, *loss_dd;
 };
 struct RasterArgs {
   int views, tile_w, tile_h;
@@ -163,11 +167,25 @@ struct RasterArgs {
   const uint32_t* order;  // nullable
   uint32_t* work;         // nullable: job counter of the persistent form (zeroed by the launcher)
   int num_sms;
+  // fused loss (forward): per (tile, 8 x 8 block) partial sums {|colour
+  // residual|, |depth residual| over valid targets, valid count} at
+  // loss_partials[3 (4 tile + block) + i]; null = no loss
+  float* loss_partials;
+  float w_color;
+  // backward: dL/dD = dLdd * depth_scale[v] when non-null (the scale the
+  // fused loss finalises on the device)
+  const float* depth_scale;
   RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);
 void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsigned long long* counters,
                        cudaStream_t s);
+// loss from the forward pass's per-block partials: loss = sum over views of
+// w_color sum|rc| / (3 npix_v) + w_depth sum|rd| / nvalid_v; depth_scale[v] =
+// w_depth / nvalid_v (fixed summation order)
+// partials: scratch of >= 3 * (4 n_tiles / 2048 + views) floats
+void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss, float* depth_scale,
+                                float* partials, cudaStream_t s, int64_t* launches);
 void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s);
 
 // loss and optimiser: per view v, L_v = w_color mean |C - C^| + w_depth

@@ -134,6 +134,57 @@ __global__ void __launch_bounds__(kLossThreads) scale_kernel(const __grid_consta
   }
 }
 
+// Loss of the fused forward pass, phase 1: block b sums, in a fixed order,
+// the (tile, 8 x 8 block) partials [lo, lo + kTileLossChunk) of one view
+// into partials[3 b ..] (the layout of loss_partials_kernel's output, so
+// loss_finalize_kernel finishes the job).  View v owns blocks
+// [block_base[v], block_base[v + 1]) and job partials [4 tile_base[v], 4 tile_base[v + 1]).
+constexpr int kTileLossChunk = kLossThreads * kLossItems;
+
+struct TileLossArgs {
+  int views;
+  int block_base[kMaxViews + 1];
+  uint32_t job_base[kMaxViews + 1];
+  const float* jobs;
+};
+
+__global__ void __launch_bounds__(kLossThreads) loss_tiles_partial_kernel(const __grid_constant__ TileLossArgs t,
+                                                                          float* __restrict__ partials) {
+  int v = 0;
+  for (int k = 1; k < t.views; ++k)
+    if ((int)blockIdx.x >= t.block_base[k]) v = k;
+  const uint32_t lo = t.job_base[v] + (uint32_t)(blockIdx.x - t.block_base[v]) * kTileLossChunk;
+  const uint32_t hi = min(lo + (uint32_t)kTileLossChunk, t.job_base[v + 1]);
+  float sc = 0.f, sd = 0.f, nv = 0.f;
+#pragma unroll
+  for (int j = 0; j < kLossItems; ++j) {
+    const uint32_t i = lo + threadIdx.x + j * kLossThreads;
+    if (i < hi) {
+      sc += t.jobs[3 * (size_t)i];
+      sd += t.jobs[3 * (size_t)i + 1];
+      nv += t.jobs[3 * (size_t)i + 2];
+    }
+  }
+  __shared__ float red[3][kLossThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    sc += __shfl_xor_sync(0xFFFFFFFFu, sc, off);
+    sd += __shfl_xor_sync(0xFFFFFFFFu, sd, off);
+    nv += __shfl_xor_sync(0xFFFFFFFFu, nv, off);
+  }
+  if (lane == 0) {
+    red[0][wid] = sc;
+    red[1][wid] = sd;
+    red[2][wid] = nv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    float s = 0.f;
+    for (int w = 0; w < kLossThreads / 32; ++w) s += red[threadIdx.x][w];
+    partials[3 * blockIdx.x + threadIdx.x] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Adam
 // ---------------------------------------------------------------------------
@@ -250,6 +301,33 @@ void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* la
   loss_finalize_kernel<<<1, 256, 0, s>>>(a, partials, scale);
   scale_kernel<<<a.n_blocks, kLossThreads, 0, s>>>(a, scale);
   if (launches) *launches += 3;
+}
+
+void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss, float* depth_scale,
+                                float* partials, cudaStream_t s, int64_t* launches) {
+  TileLossArgs t;
+  LossArgs la;
+  t.views = la.views = a.views;
+  t.jobs = a.loss_partials;
+  la.w_color = a.w_color;
+  la.w_depth = w_depth;
+  la.loss = loss;
+  int blocks = 0;
+  for (int v = 0; v < a.views; ++v) {
+    const uint32_t j0 = 4 * a.v[v].tile_base;
+    const uint32_t j1 = 4 * (v + 1 < a.views ? a.v[v + 1].tile_base : a.n_tiles);
+    t.block_base[v] = blocks;
+    t.job_base[v] = j0;
+    t.job_base[v + 1] = j1;
+    la.v[v] = LossView{a.v[v].width * a.v[v].height, blocks, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    blocks += (int)((j1 - j0 + kTileLossChunk - 1) / kTileLossChunk);
+  }
+  t.block_base[a.views] = blocks;
+  la.n_blocks = blocks;
+  if (blocks == 0) return;
+  loss_tiles_partial_kernel<<<blocks, kLossThreads, 0, s>>>(t, partials);
+  loss_finalize_kernel<<<1, 256, 0, s>>>(la, partials, depth_scale);
+  if (launches) *launches += 2;
 }
 
 void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],

@@ -89,9 +89,10 @@ __device__ __forceinline__ unsigned make_entry(float4 f0, float4 f1, float4 f2, 
 // Tile, view and pixel origin of visit k: k indexes the tile visit order (or
 // the tiles directly), global tiles map to views by tile_base.
 struct TileJob {
-  int v;       // view
-  int ox, oy;  // pixel origin of the tile within the view
+  int v;          // view
+  int ox, oy;     // pixel origin of the tile within the view
   uint2 range;
+  uint32_t tile;  // global tile id
 };
 template <int TW, int TH>
 __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
@@ -101,12 +102,12 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
     if (tile >= a.v[k].tile_base) v = k;
   const int lt = (int)(tile - a.v[v].tile_base);
   const int tx = lt % a.v[v].tiles_x, ty = lt / a.v[v].tiles_x;
-  return TileJob{v, tx * TW, ty * TH, a.ranges[tile]};
+  return TileJob{v, tx * TW, ty * TH, a.ranges[tile], tile};
 }
 
 // Forward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
 // visit k) by one warp; buf is the warp's shared staging buffer.
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, bool LOSS>
 __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t k, int quad,
                                         Entry* __restrict__ buf, float* __restrict__ T_final_all,
                                         int32_t* __restrict__ last_all, unsigned long long* __restrict__ counters) {
@@ -237,6 +238,45 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
     T_final[p] = T1;
     last_out[p] = last1;
   }
+  if constexpr (LOSS) {
+    // L1 loss epilogue (Eq. 12 plus the depth term): the same residuals,
+    // signs and colour scale as the separate loss kernels, per-block sums
+    const float gscale_c = a.w_color / (3.f * (float)HW);
+    float sc = 0.f, sd = 0.f, nv = 0.f;
+    const float* __restrict__ trgb = vw.trgb;
+    const float* __restrict__ tdep = vw.tdep;
+    float* __restrict__ ldc = vw.loss_dc;
+    float* __restrict__ ldd = vw.loss_dd;
+    auto score = [&](size_t p, float T, float Rc, float Gc, float Bc, float D) {
+      const float col[3] = {Rc + T * rp.bg[0], Gc + T * rp.bg[1], Bc + T * rp.bg[2]};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float r = col[c] - trgb[(size_t)c * HW + p];
+        sc += fabsf(r);
+        ldc[(size_t)c * HW + p] = gscale_c * (float)((r > 0.f) - (r < 0.f));
+      }
+      const float td = tdep[p];
+      const bool valid = td > 0.f;
+      const float rd = D - td;
+      sd += valid ? fabsf(rd) : 0.f;
+      nv += valid ? 1.f : 0.f;
+      ldd[p] = valid ? (float)((rd > 0.f) - (rd < 0.f)) : 0.f;
+    };
+    if (in0) score((size_t)py0 * width + px, T0, R0, G0, B0, D0);
+    if (in1) score((size_t)py1 * width + px, T1, R1, G1, B1, D1);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sc += __shfl_xor_sync(kFull, sc, off);
+      sd += __shfl_xor_sync(kFull, sd, off);
+      nv += __shfl_xor_sync(kFull, nv, off);
+    }
+    if (lane == 0) {
+      float* part = a.loss_partials + 3 * (4 * (size_t)job.tile + quad);
+      part[0] = sc;
+      part[1] = sd;
+      part[2] = nv;
+    }
+  }
 }
 
 // Pulls the next (tile visit, quadrant) job for the calling warp from the
@@ -253,7 +293,7 @@ __device__ __forceinline__ bool next_job(uint32_t* __restrict__ work, uint32_t n
 
 // PERSIST = false: one CTA per tile visit, warp w on quadrant w.  Otherwise
 // a persistent grid whose warps pull jobs from `work` with next_job.
-template <int TW, int TH, bool COUNT, bool PERSIST>
+template <int TW, int TH, bool COUNT, bool LOSS, bool PERSIST>
 __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
                                                               float* __restrict__ T_final_all,
                                                               int32_t* __restrict__ last_all,
@@ -263,12 +303,12 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   __shared__ Entry s_e[kThreads / 32][32];
   const int warp = threadIdx.x >> 5;
   if constexpr (!PERSIST) {
-    fwd_job<TW, TH, COUNT>(a, rp, blockIdx.x, warp, s_e[warp], T_final_all, last_all, counters);
+    fwd_job<TW, TH, COUNT, LOSS>(a, rp, blockIdx.x, warp, s_e[warp], T_final_all, last_all, counters);
   } else {
     const uint32_t n_jobs = 4u * a.n_tiles;
     uint32_t job;
     while (next_job(work, n_jobs, job))
-      fwd_job<TW, TH, COUNT>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], T_final_all, last_all, counters);
+      fwd_job<TW, TH, COUNT, LOSS>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], T_final_all, last_all, counters);
   }
 }
 
@@ -377,6 +417,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
   const float* __restrict__ dLdc = vw.dLdc;
   const float* __restrict__ dLdd = vw.dLdd;
   const float* __restrict__ dLda = vw.dLda;
+  const float dscale = a.depth_scale ? a.depth_scale[job.v] : 1.f;
   const int lane = threadIdx.x & 31;
   const int bxi = (quad % WX) * 8, byi = (quad / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;
@@ -399,7 +440,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
     c00 = dLdc[p];
     c01 = dLdc[HW + p];
     c02 = dLdc[2 * HW + p];
-    d0 = dLdd[p];
+    d0 = dLdd[p] * dscale;
     a0 = dLda ? dLda[p] : 0.f;
   }
   if (in1) {
@@ -409,7 +450,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
     c10 = dLdc[p];
     c11 = dLdc[HW + p];
     c12 = dLdc[2 * HW + p];
-    d1 = dLdd[p];
+    d1 = dLdd[p] * dscale;
     a1 = dLda ? dLda[p] : 0.f;
   }
   // U = sum over Gaussians behind of w_j (c_j . dC + z_j dD) + T_final (bg . dC)
@@ -546,17 +587,25 @@ int persistent_grid(K kernel, int& per_sm, int n_tiles, int num_sms) {
   return std::max(1, std::min(n_tiles, per_sm * std::max(num_sms, 1)));
 }
 
-template <int TW, int TH, bool COUNT>
+template <int TW, int TH, bool COUNT, bool LOSS>
 void fwd_shape(const RasterArgs& a, const RasterParams& rp, float* T_final, int32_t* last,
                unsigned long long* counters, cudaStream_t s) {
   const int nt = (int)a.n_tiles;
   if (a.work) {
     static int per_sm = 0;
-    auto* k = raster_fwd_kernel<TW, TH, COUNT, true>;
+    auto* k = raster_fwd_kernel<TW, TH, COUNT, LOSS, true>;
     k<<<persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s>>>(a, rp, T_final, last, counters, a.work);
   } else {
-    raster_fwd_kernel<TW, TH, COUNT, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters, nullptr);
+    raster_fwd_kernel<TW, TH, COUNT, LOSS, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters, nullptr);
   }
+}
+
+template <bool COUNT, bool LOSS>
+void fwd_shapes(const RasterArgs& a, const RasterParams& rp, float* T_final, int32_t* last,
+                unsigned long long* counters, cudaStream_t s) {
+  if (a.tile_w == 16) fwd_shape<16, 16, COUNT, LOSS>(a, rp, T_final, last, counters, s);
+  else if (a.tile_w == 8) fwd_shape<8, 32, COUNT, LOSS>(a, rp, T_final, last, counters, s);
+  else fwd_shape<32, 8, COUNT, LOSS>(a, rp, T_final, last, counters, s);
 }
 
 template <int TW, int TH>
@@ -579,14 +628,13 @@ void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsig
   if (a.n_tiles == 0) return;
   const RasterParams rp = make_params(a);
   if (a.work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
+  const bool loss = a.loss_partials != nullptr;
   if (counters) {
-    if (a.tile_w == 16) fwd_shape<16, 16, true>(a, rp, T_final, last, counters, s);
-    else if (a.tile_w == 8) fwd_shape<8, 32, true>(a, rp, T_final, last, counters, s);
-    else fwd_shape<32, 8, true>(a, rp, T_final, last, counters, s);
+    if (loss) fwd_shapes<true, true>(a, rp, T_final, last, counters, s);
+    else fwd_shapes<true, false>(a, rp, T_final, last, counters, s);
   } else {
-    if (a.tile_w == 16) fwd_shape<16, 16, false>(a, rp, T_final, last, counters, s);
-    else if (a.tile_w == 8) fwd_shape<8, 32, false>(a, rp, T_final, last, counters, s);
-    else fwd_shape<32, 8, false>(a, rp, T_final, last, counters, s);
+    if (loss) fwd_shapes<false, true>(a, rp, T_final, last, counters, s);
+    else fwd_shapes<false, false>(a, rp, T_final, last, counters, s);
   }
 }
 

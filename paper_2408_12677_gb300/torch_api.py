@@ -106,13 +106,17 @@ class Context:
 class Trainer:
     """One view, one map: fwd + L1 loss + bwd + Adam per ``step``.
 
-    ``fused`` (default) runs the backward pass and the Adam step as
-    gs_render_bwd_adam (no gradient buffer); otherwise gs_render_bwd into the
-    model's gradient buffer followed by gs_adam_step (which clears it)."""
+    ``one_call`` (default) runs the whole iteration as gs_train_step (loss in
+    the compositing epilogue, backward fused with Adam; the rendered images
+    stay unwritten).  Otherwise ``fused`` runs gs_render_fwd + gs_loss_l1 +
+    gs_render_bwd_adam (no gradient buffer), or, with fused=False,
+    gs_render_bwd into the model's gradient buffer followed by gs_adam_step
+    (which clears it)."""
 
     def __init__(self, model: GaussianModel, cam, R, t, raster_cfg=None, adam_cfg=None, w_color=0.8, w_depth=0.2,
-                 ctx: Context | None = None, device: int = 0, fused: bool = True):
+                 ctx: Context | None = None, device: int = 0, fused: bool = True, one_call: bool = True):
         self.fused = fused
+        self.one_call = one_call and fused
         self.model = model
         self.ctx = ctx or Context(device)
         self.cam = camera_struct(cam)
@@ -140,11 +144,16 @@ class Trainer:
         """One iteration; the loss of the rendered image stays on the device in
         ``self.loss``.  Gradients are cleared by the Adam kernel."""
         h = self.ctx.handle
+        m = self.model
+        if self.one_call:
+            self.step_count += 1
+            abi.gs_train_step(h, self._g, self.cam, self.view, self.rcfg, target_rgb, target_depth, self.w_color,
+                              self.w_depth, self.loss, m.flat, m.m, m.v, self.acfg, self.step_count, stream)
+            return self.loss
         self.forward(stream)
         abi.gs_loss_l1(h, self.cam, self.color, self.depth, target_rgb, target_depth, self.w_color, self.w_depth,
                        self.loss, self.dLdc, self.dLdd, stream)
         self.step_count += 1
-        m = self.model
         if self.fused:
             abi.gs_render_bwd_adam(h, self._g, self.cam, self.view, self.rcfg, self.dLdc, self.dLdd, None, m.flat, m.m,
                                    m.v, self.acfg, self.step_count, None, stream)
@@ -159,6 +168,10 @@ class Trainer:
         # the context's device counter (step = 0), so it can be graph-captured
         h = self.ctx.handle
         m = self.model
+        if self.one_call:
+            abi.gs_train_step(h, self._g, self.cam, self.view, self.rcfg, target_rgb, target_depth, self.w_color,
+                              self.w_depth, self.loss, m.flat, m.m, m.v, self.acfg, 0, stream)
+            return
         self.forward(stream)
         abi.gs_loss_l1(h, self.cam, self.color, self.depth, target_rgb, target_depth, self.w_color, self.w_depth,
                        self.loss, self.dLdc, self.dLdd, stream)
@@ -219,7 +232,8 @@ class BatchedTrainer:
     calls, one view at a time (gradients accumulated, then gs_adam_step)."""
 
     def __init__(self, model: GaussianModel, views, raster_cfg=None, adam_cfg=None, w_color=0.8, w_depth=0.2,
-                 ctx: Context | None = None, device: int = 0):
+                 ctx: Context | None = None, device: int = 0, one_call: bool = True):
+        self.one_call = one_call
         self.model = model
         self.ctx = ctx or Context(device)
         self.cam_list = list(c for c, _, _ in views)
@@ -255,6 +269,11 @@ class BatchedTrainer:
     def _iteration(self, targets_rgb, targets_depth, step, stream=None):
         h = self.ctx.handle
         m = self.model
+        if self.one_call:  # gs_train_step_batched (the rendered images are written too)
+            abi.gs_train_step_batched(h, self._g, self.cams, self.vms, self.rcfg, targets_rgb, targets_depth,
+                                      self.w_color, self.w_depth, self.loss, m.flat, m.m, m.v, self.acfg, step,
+                                      self.color, self.depth, self.alpha, stream)
+            return
         self.forward(stream)
         abi.gs_loss_l1_batched(h, self.cams, self.color, self.depth, targets_rgb, targets_depth, self.w_color,
                                self.w_depth, self.loss, self.dLdc, self.dLdd, stream)
@@ -262,7 +281,9 @@ class BatchedTrainer:
                                        m.m, m.v, self.acfg, step, None, stream)
 
     def step(self, targets_rgb, targets_depth, stream=None):
-        """One batched iteration; the summed loss stays on the device in ``self.loss``."""
+        """One batched iteration; the summed loss stays on the device in ``self.loss``.
+        ``one_call`` (default) runs it as gs_train_step_batched, otherwise as
+        gs_render_fwd_batched + gs_loss_l1_batched + gs_render_bwd_adam_batched."""
         self.step_count += 1
         self._iteration(targets_rgb, targets_depth, self.step_count, stream)
         return self.loss

@@ -347,3 +347,37 @@ def test_tile_visit_order_and_persistent_grid_change_nothing(ctx):
         for k in NAMES:
             g0, g1 = out[0][1][k], other[1][k]
             compare(k, g0, g1, 1e-3, 1e-6 * np.abs(g1).max(), 1e-5, max(2, int(1e-3 * g1.size)))
+
+
+def test_train_step_batched_matches_three_calls(ctx):
+    from paper_2408_12677_gb300 import abi
+    P, views = _mid_views(3)
+    cams, vms = _structs(views)
+    rcfg, acfg = abi.raster_cfg(), abi.adam_cfg()
+    trgb = [_t(v.target_rgb) for v in views]
+    tdep = [_t(v.target_depth) for v in views]
+    A, B = to_gpu_model(P), to_gpu_model(P)
+    shp = [((3, v.cam.height, v.cam.width), (v.cam.height, v.cam.width)) for v in views]
+    col = [torch.empty(a, device="cuda") for a, _ in shp]
+    dep = [torch.empty(b, device="cuda") for _, b in shp]
+    dc = [torch.empty(a, device="cuda") for a, _ in shp]
+    dd = [torch.empty(b, device="cuda") for _, b in shp]
+    colB = [torch.empty(a, device="cuda") for a, _ in shp]
+    depB = [torch.empty(b, device="cuda") for _, b in shp]
+    la, lb = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    for step in (1, 2):
+        abi.gs_render_fwd_batched(ctx.handle, A.gaussians(), cams, vms, rcfg, col, dep, None)
+        abi.gs_loss_l1_batched(ctx.handle, cams, col, dep, trgb, tdep, 0.8, 0.2, la, dc, dd)
+        abi.gs_render_bwd_adam_batched(ctx.handle, A.gaussians(), cams, vms, rcfg, dc, dd, None, A.flat, A.m, A.v,
+                                       acfg, step)
+        abi.gs_train_step_batched(ctx.handle, B.gaussians(), cams, vms, rcfg, trgb, tdep, 0.8, 0.2, lb, B.flat, B.m,
+                                  B.v, acfg, step, colB, depB, None)
+        torch.cuda.synchronize()
+        if step == 1:  # same map: the rendered images are bit-identical
+            for x, y in zip(col + dep, colB + depB):
+                assert torch.equal(x, y)
+        assert abs(float(la.item()) - float(lb.item())) <= 1e-6 * abs(float(la.item()))
+        for name, x, y in (("p", A.flat, B.flat), ("m", A.m, B.m), ("v", A.v, B.v)):
+            xa, ya = x.cpu().numpy(), y.cpu().numpy()
+            bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
+            assert bad.sum() <= max(4, int(1e-4 * xa.size)), (name, step, int(bad.sum()))

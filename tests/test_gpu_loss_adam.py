@@ -112,3 +112,42 @@ def test_fused_backward_adam_matches_unfused(ctx, deg, seed):
             compare(name, ya, xa, 1e-5, 1e-6 * np.abs(xa).max() + 1e-12, 1e-5)
         compare("pose", pb.cpu().numpy(), pa.cpu().numpy(), 1e-5, 1e-6, 1e-5)
     assert float(B.grad.abs().max()) == 0.0  # the fused path never touches a gradient buffer
+
+
+@pytest.mark.parametrize("deg,seed", [(0, 3), (3, 4)])
+def test_train_step_matches_three_calls(ctx, deg, seed):
+    """gs_train_step (loss in the compositing epilogue, depth scale applied in
+    the backward pass) == gs_render_fwd + gs_loss_l1 + gs_render_bwd_adam over
+    three iterations: the same loss and the same parameters and moments up to
+    float32 atomics order."""
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import GaussianModel, camera_struct
+    from synth import workloads
+    from synth.scene import Camera, look_at
+    cam = Camera(80.0, 75.0, 40.0, 30.0, 84, 60)
+    pose = look_at([0.1, 0.2, -0.1], [0.7, 3.0, 0.2])
+    P = workloads.random_gaussians(np.random.default_rng(seed), 700, cam, pose, deg, log_scale_range=(-3.5, -1.5),
+                                   sh_rest_std=0.15)
+    rng = np.random.default_rng(seed + 10)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+    trgb = t(rng.uniform(0, 1, (3, 60, 84)))
+    tdep_np = rng.uniform(0.5, 4.0, (60, 84))
+    tdep_np[:7] = 0.0  # invalid target depth rows
+    tdep = t(tdep_np)
+    A, B = GaussianModel(P), GaussianModel(P)
+    camS, view, rcfg, acfg = camera_struct(cam), abi.make_viewmat(pose.R, pose.t), abi.raster_cfg(), abi.adam_cfg()
+    col, dep = torch.empty((3, 60, 84), device="cuda"), torch.empty((60, 84), device="cuda")
+    dc, dd = torch.empty_like(col), torch.empty_like(dep)
+    la, lb = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    for step in range(1, 4):
+        abi.gs_render_fwd(ctx.handle, A.gaussians(), camS, view, rcfg, col, dep, None)
+        abi.gs_loss_l1(ctx.handle, camS, col, dep, trgb, tdep, 0.8, 0.2, la, dc, dd)
+        abi.gs_render_bwd_adam(ctx.handle, A.gaussians(), camS, view, rcfg, dc, dd, None, A.flat, A.m, A.v, acfg, step)
+        abi.gs_train_step(ctx.handle, B.gaussians(), camS, view, rcfg, trgb, tdep, 0.8, 0.2, lb, B.flat, B.m, B.v,
+                          acfg, step)
+        torch.cuda.synchronize()
+        assert abs(float(la.item()) - float(lb.item())) <= 1e-6 * abs(float(la.item()))
+        for name, x, y in (("p", A.flat, B.flat), ("m", A.m, B.m), ("v", A.v, B.v)):
+            xa, ya = x.cpu().numpy(), y.cpu().numpy()
+            bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
+            assert bad.sum() <= max(2, int(1e-4 * xa.size)), (name, step, int(bad.sum()))
