@@ -203,18 +203,19 @@ struct PixEval {
   float dx, dy, t0, w, t1, araw;
 };
 
-__device__ __forceinline__ bool eval_splat(float4 a, float i1, float log2o, float plx, float ply, float qmax_s,
-                                           float log2_amin, PixEval& e) {
+// r2 = min(qmax_s, log2 o - log2 alpha_min), the support radius of the
+// splat in q' units: a pixel takes part iff q' <= r2 (inside the 3-sigma
+// ellipse and alpha = o 2^-q' >= alpha_min; one comparison for both tests).
+__device__ __forceinline__ bool eval_splat(float4 a, float i1, float log2o, float r2, float plx, float ply,
+                                           PixEval& e) {
   e.dx = __fsub_rn(plx, a.x);
   e.dy = __fsub_rn(ply, a.y);
   e.t0 = __fmul_rn(a.z, e.dx);
   e.w = __fmaf_rn(-a.w, e.dx, e.dy);
   e.t1 = __fmul_rn(i1, e.w);
-  float q = __fmaf_rn(e.t0, e.t0, __fmul_rn(e.t1, e.t1));
-  if (q > qmax_s) return false;
-  float ex = __fsub_rn(log2o, q);
-  if (ex < log2_amin) return false;
-  e.araw = ex2_approx(ex);
+  const float q = __fmaf_rn(e.t0, e.t0, __fmul_rn(e.t1, e.t1));
+  if (q > r2) return false;
+  e.araw = ex2_approx(__fsub_rn(log2o, q));
   return true;
 }
 

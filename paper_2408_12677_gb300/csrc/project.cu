@@ -200,9 +200,9 @@ __global__ void bin_prepare_kernel(int n, const float* __restrict__ mean2d, cons
 
 constexpr int kBwdThreads = 128;
 
-// Gradient of one Gaussian's parameters from its projected-feature gradient
-// record G0..G2 (mu 2, factor 3 | opacity, depth | rgb 3), plus its share of
-// the pose-twist gradient.  SH gradients are returned in factored form: the
+// Gradient of one Gaussian's parameters from its gradient record G0..G2
+// (the raster backward pass's six exponent / opacity sums, depth, rgb 3),
+// plus its share of the pose-twist gradient.  SH gradients are returned in factored form: the
 // gradient of coefficient (k, c) is Y[k] * graw[c].
 template <int D>
 struct GaussGrad {
@@ -221,11 +221,22 @@ __device__ __forceinline__ void gaussian_grad(const CamView& cv, float dilation,
   for (int r = 0; r < 3; ++r) pc[r] = cv.R[3 * r] * p[0] + cv.R[3 * r + 1] * p[1] + cv.R[3 * r + 2] * p[2] + cv.t[r];
   Geo g;
   geometry(cv, dilation, p[0], p[1], p[2], q4, ls, pc[0], pc[1], pc[2], g);
-  const float gmx = G0.x, gmy = G0.y, gi0 = G0.z, gk = G0.w, gi1 = G1.x, go = G1.y, gdep = G1.z;
+  // The raster backward pass leaves, per Gaussian, sums over its pixels of
+  // ga = dL/dalpha * alpha times {t0, t1, t0 dx, t1 dx, t1 w, 1}
+  // (q' = t0^2 + t1^2, t0 = i0 dx, t1 = i1 w, w = dy - k dx, dx = u - mu_x,
+  // dalpha/dq' = -ln2 alpha, dalpha/do = alpha / o): the gradients of the
+  // mean and the factored conic follow with the Gaussian's constants.
+  constexpr float kTwoLn2 = 2.f * kLn2;
+  const float gmx = kTwoLn2 * (g.i0 * G0.x - g.i1 * g.k * G0.y);
+  const float gmy = kTwoLn2 * g.i1 * G0.y;
+  const float gi0 = -kTwoLn2 * G0.z;
+  const float gk = kTwoLn2 * g.i1 * G0.w;
+  const float gi1 = -kTwoLn2 * G1.x;
+  const float gdep = G1.z;
 
-  // opacity
+  // opacity: dL/do = sum ga / o, d o / d logit = o (1 - o)
   const float o = 1.f / (1.f + expf(-logit));
-  out.glogit = go * o * (1.f - o);
+  out.glogit = G1.y * (1.f - o);
 
   // colour: SH coefficients and view direction
   float dv[3] = {p[0] - cv.C[0], p[1] - cv.C[1], p[2] - cv.C[2]};
@@ -517,7 +528,7 @@ struct FusedSmemMulti {
 };
 
 template <int D, bool MULTI>
-__global__ void __launch_bounds__(kFusedThreads) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
+__global__ void __launch_bounds__(kFusedThreads, MULTI ? 3 : 1) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
                                                                          const float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,

@@ -29,7 +29,7 @@ constexpr int kAtomicLanes = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // One list entry in tile-local coordinates:
-//   a = {mu_x, mu_y, i0, k}, b = {i1, log2 opacity, z, 1/opacity},
+//   a = {mu_x, mu_y, i0, k}, b = {i1, log2 opacity, z, support radius r2},
 //   c = {r, g, b, mask of the warp block's halves the support box meets}
 struct Entry {
   float4 a, b, c;
@@ -68,9 +68,9 @@ __device__ __forceinline__ unsigned make_entry(float4 f0, float4 f1, float4 f2, 
                                                const RasterParams& rp, Entry& e) {
   const float mlx = __fadd_rn(__fsub_rn(f0.x, ox), f0.z);
   const float mly = __fadd_rn(__fsub_rn(f0.y, oy), f0.w);
+  const float R2 = fminf(rp.qmax_s, __fsub_rn(f1.w, rp.log2_alpha_min));
   e.a = make_float4(mlx, mly, f1.x, f1.y);
-  e.b = make_float4(f1.z, f1.w, f2.w, ex2_approx(-f1.w));
-  const float R2 = fminf(rp.qmax_s, f1.w - rp.log2_alpha_min);
+  e.b = make_float4(f1.z, f1.w, f2.w, R2);
   unsigned m = 0u;
   if (R2 > 0.f && f1.x > 0.f && f1.z > 0.f) {
     const float Rr = sqrtf(R2) * 1.0001f + 1e-4f;
@@ -158,7 +158,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       PixEval pe;
       if ((halves & 1u) && !done0) {
         if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, plx, ply0, rp.qmax_s, rp.log2_alpha_min, pe)) {
+        if (eval_splat(a, bb.x, bb.y, bb.w, plx, ply0, pe)) {
           const float al = fminf(rp.alpha_max, pe.araw);
           const float test_T = __fmul_rn(T0, __fsub_rn(1.f, al));
           if (test_T < rp.t_eps) {
@@ -177,7 +177,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       }
       if ((halves & 2u) && !done1) {
         if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, plx, ply1, rp.qmax_s, rp.log2_alpha_min, pe)) {
+        if (eval_splat(a, bb.x, bb.y, bb.w, plx, ply1, pe)) {
           const float al = fminf(rp.alpha_max, pe.araw);
           const float test_T = __fmul_rn(T1, __fsub_rn(1.f, al));
           if (test_T < rp.t_eps) {
@@ -312,8 +312,8 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   }
 }
 
-// float offset of gradient value k (mu 2, factor 3, opacity, z | rgb 3) in the
-// 12-float record {mu_x, mu_y, i0, k} {i1, opacity, z, -} {r, g, b, -}
+// float offset of gradient value k (the six exponent / opacity sums, depth |
+// rgb 3) in the 12-float record {s0, s1, s2, s3} {s4, s5, depth, -} {r, g, b, -}
 __device__ __forceinline__ int rec_off(int k) { return k < 7 ? k : k + 1; }
 
 // Sum the 10 values v[0..9] over the warp with exchanges that halve the number
@@ -363,12 +363,18 @@ __device__ __forceinline__ void warp_reduce_add10(float (&v)[10], float* __restr
 
 // Back-to-front step of one pixel for one Gaussian: updates the pixel's
 // running transmittance T and "colour behind" U and adds the Gaussian's
-// gradient values (mu 2, factor 3, opacity, z, rgb 3) to v.
+// gradient sums to v.  With ga = dL/dalpha * alpha (unclamped alpha) the
+// exponent and opacity gradients are linear in
+//   v[0] = sum ga t0, v[1] = sum ga t1, v[2] = sum ga t0 dx,
+//   v[3] = sum ga t1 dx, v[4] = sum ga t1 w, v[5] = sum ga
+// (t0 = i0 dx, t1 = i1 w, w = dy - k dx): the Gaussian's constants (i0, i1,
+// k, ln 2, 1 / opacity) are applied once per Gaussian in the projection
+// backward pass.  v[6] = sum w dD (depth), v[7..9] = sum w dC (colour).
 __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, const float4& c, float plx, float ply,
                                           const RasterParams& rp, float& T, float& U, float dC0, float dC1, float dC2,
                                           float dD, float dA_T, float (&v)[10]) {
   PixEval e;
-  if (!eval_splat(a, bb.x, bb.y, plx, ply, rp.qmax_s, rp.log2_alpha_min, e)) return false;
+  if (!eval_splat(a, bb.x, bb.y, bb.w, plx, ply, e)) return false;
   const float al = fminf(rp.alpha_max, e.araw);
   const float inv1m = rcp_approx(1.f - al);  // 1 - alpha in [0.01, 1)
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
@@ -382,18 +388,15 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
   const float g_alpha = Ti * cdot - (U - dA_T) * inv1m;
   U = fmaf(w, cdot, U);
   T = Ti;
-  if (e.araw <= rp.alpha_max) {
-    v[5] += g_alpha * e.araw * bb.w;             // d alpha / d opacity = G = alpha / opacity
-    const float gq = -g_alpha * e.araw * kLn2;  // d alpha / d q' = -ln2 alpha
-    // q' = t0^2 + t1^2, t0 = i0 dx, t1 = i1 (dy - k dx), dx = plx - mu_x
-    const float two_t0 = 2.f * e.t0, two_t1 = 2.f * e.t1;
-    const float dq_ddx = two_t0 * a.z - two_t1 * bb.x * a.w;
-    const float dq_ddy = two_t1 * bb.x;
-    v[0] -= gq * dq_ddx;
-    v[1] -= gq * dq_ddy;
-    v[2] += gq * two_t0 * e.dx;
-    v[3] -= gq * two_t1 * bb.x * e.dx;
-    v[4] += gq * two_t1 * e.w;
+  if (e.araw <= rp.alpha_max) {  // the 0.99 clamp has zero gradient
+    const float ga = g_alpha * e.araw;
+    const float gt0 = ga * e.t0, gt1 = ga * e.t1;
+    v[0] += gt0;
+    v[1] += gt1;
+    v[2] = fmaf(gt0, e.dx, v[2]);
+    v[3] = fmaf(gt1, e.dx, v[3]);
+    v[4] = fmaf(gt1, e.w, v[4]);
+    v[5] += ga;
   }
   return true;
 }

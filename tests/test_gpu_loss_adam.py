@@ -110,7 +110,10 @@ def test_fused_backward_adam_matches_unfused(ctx, deg, seed):
         for name, x, y in (("p", A.flat, B.flat), ("m", A.m, B.m), ("v", A.v, B.v)):
             xa, ya = x.cpu().numpy(), y.cpu().numpy()
             compare(name, ya, xa, 1e-5, 1e-6 * np.abs(xa).max() + 1e-12, 1e-5)
-        compare("pose", pb.cpu().numpy(), pa.cpu().numpy(), 1e-5, 1e-6, 1e-5)
+        # the pose gradient sums every Gaussian's share: a component that cancels
+        # carries float32 atomics-order noise of ~1e-6 of the largest component
+        pan = pa.cpu().numpy()
+        compare("pose", pb.cpu().numpy(), pan, 1e-5, 1e-6 * np.abs(pan).max() + 1e-6, 1e-5)
     assert float(B.grad.abs().max()) == 0.0  # the fused path never touches a gradient buffer
 
 
