@@ -364,8 +364,10 @@ gs_status bin_and_sort_radix(gs_ctx* c, int n, const TileMap& map, cudaStream_t 
 
 // Counting-scatter binning with per-tile sorts: count, scan (one host read of
 // the totals in sync mode), scatter, sort.  Falls back to the radix path when
-// some tile list is longer than the per-tile sort holds.
-gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
+// some tile list is longer than the per-tile sort holds.  small_counted: the
+// projection already counted every item with at most kBigTiles tiles into
+// the (zeroed) tile counters.
+gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, bool small_counted) {
   const int64_t T = (int64_t)map.tile_base[map.views];
   if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
   TileBinArgs tb;
@@ -388,6 +390,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
   tb.big_queue = c->bigq;
   tb.big_len = c->d_bigmeta;
   tb.order = c->order_tiles ? c->torder : nullptr;
+  tb.small_counted = small_counted;
   c->st_ordered = false;
   {
     StageTimer t(c, GS_STAGE_DUPLICATE, s);
@@ -732,7 +735,9 @@ ProjectArgs project_args(const gs_gaussians* g, int V, const gs_camera* cams, co
       pa.cv[v] = CamView{};
       pa.tiles_x[v] = pa.tiles_y[v] = 0;
     }
+    pa.tile_base[v] = map.tile_base[v];
   }
+  pa.counts = nullptr;
   return pa;
 }
 
@@ -803,7 +808,9 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   ProjectArgs pa = project_args(g, V, cams, views, cfg, L.map, L.tiles_y);
   pa.big_queue = c->bigq;
   pa.big_len = c->d_bigmeta;
+  pa.counts = c->tcount;  // the projection counts the tiles of the small rectangles
   GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
+  GS_CUDA(c, cudaMemsetAsync(c->tcount, 0, sizeof(uint32_t) * (size_t)L.tiles, s));
   {
     StageTimer t(c, GS_STAGE_PROJECT_FWD, s);
     launch_project_fwd(pa, c->feat, c->zkey, c->tiles, c->rects, s);
@@ -811,7 +818,7 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   if (g->n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "project_fwd");
 
-  if ((st = bin_and_sort(c, n_items, L.map, s)) != GS_OK) return st;
+  if ((st = bin_and_sort(c, n_items, L.map, s, true)) != GS_OK) return st;
 
   c->st_n = g->n;
   c->st_views = V;
@@ -1299,7 +1306,7 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
   map.n_per_view = (int)n;
   map.tiles_x[0] = tiles_x;
   for (int v = 1; v <= kMaxViews; ++v) map.tile_base[v] = (uint32_t)T;
-  st = bin_and_sort(c, (int)n, map, s);
+  st = bin_and_sort(c, (int)n, map, s, false);
   c->sync = was_sync;
   if (st != GS_OK) return st;
   const int64_t P = c->st_pairs;

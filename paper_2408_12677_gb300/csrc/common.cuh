@@ -219,4 +219,18 @@ __device__ __forceinline__ bool eval_splat(float4 a, float i1, float log2o, floa
   return true;
 }
 
+// Warp-aggregated atomic add of 1 per active lane to counter[t]: lanes with the
+// same t are grouped, the group leader adds the group size once, and each
+// lane gets old value + its rank in the group (neighbouring Gaussians tend to
+// share tiles, so plain per-lane atomics would serialise on one address).
+__device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter, uint32_t t, unsigned active) {
+  const unsigned peers = __match_any_sync(active, t);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(&counter[t], (uint32_t)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
 }  // namespace gs

@@ -44,6 +44,9 @@ struct ProjectArgs {
   int tile_w, tile_h;
   CamView cv[kMaxViews];
   int tiles_x[kMaxViews], tiles_y[kMaxViews];
+  uint32_t tile_base[kMaxViews];  // first global tile of each view
+  uint32_t* counts;               // per global tile (zeroed, nullable): the projection counts the
+                                  // tiles of items with at most kBigTiles tiles
 };
 
 // projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
@@ -134,6 +137,7 @@ struct TileBinArgs {
   const uint32_t* big_queue;  // items with more than kBigTiles tiles
   const uint32_t* big_len;
   uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
+  bool small_counted;         // counts already hold every item with at most kBigTiles tiles (projection)
 };
 int tile_sort_capacity();
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches);

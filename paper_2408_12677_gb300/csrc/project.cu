@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   }
   __syncthreads();
   const int i = base + threadIdx.x;
+  const unsigned live = __ballot_sync(0xFFFFFFFFu, i < a.n);  // lanes that reach the counting loops
   if (i >= a.n) return;
   const float px = a.means[3 * i], py = a.means[3 * i + 1], pz = a.means[3 * i + 2];
   const float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   for (int v = 0; v < a.views; ++v) {
     const CamView& cv = a.cv[v];
     const size_t it = (size_t)v * a.n + i;
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     // camera-space position and pixel mean in double-float (the float32 error
     // of W p + t alone would move mu by ~1e-3 px at 1-2 m)
     df Z = df_dot3_plus(cv.R[6], cv.R[7], cv.R[8], px, py, pz, cv.t[2]);
@@ -139,45 +141,58 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
       feat[3 * it] = make_float4(0.f, 0.f, 0.f, 0.f);
       feat[3 * it + 1] = make_float4(0.f, 0.f, 0.f, -1e30f);
       feat[3 * it + 2] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    df X = df_dot3_plus(cv.R[0], cv.R[1], cv.R[2], px, py, pz, cv.t[0]);
-    df Y = df_dot3_plus(cv.R[3], cv.R[4], cv.R[5], px, py, pz, cv.t[1]);
-    df mux = df_add(df_mul_f(df_div(X, Z), cv.fx), df{cv.cx, 0.f});
-    df muy = df_add(df_mul_f(df_div(Y, Z), cv.fy), df{cv.cy, 0.f});
+    } else {
+      df X = df_dot3_plus(cv.R[0], cv.R[1], cv.R[2], px, py, pz, cv.t[0]);
+      df Y = df_dot3_plus(cv.R[3], cv.R[4], cv.R[5], px, py, pz, cv.t[1]);
+      df mux = df_add(df_mul_f(df_div(X, Z), cv.fx), df{cv.cx, 0.f});
+      df muy = df_add(df_mul_f(df_div(Y, Z), cv.fy), df{cv.cy, 0.f});
 
-    Geo g;
-    geometry(cv, a.dilation, px, py, pz, q4, ls, X.hi, Y.hi, z, g);
+      Geo g;
+      geometry(cv, a.dilation, px, py, pz, q4, ls, X.hi, Y.hi, z, g);
 
-    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-    if (Q > 0.f && g.det > 0.f) {
-      float Qw = Q * 1.0001f + 1e-4f;
-      float ex = sqrtf(Qw * g.a) * 1.00001f + 1e-3f;
-      float ey = sqrtf(Qw * (g.b * g.b + g.det) / g.a) * 1.00001f + 1e-3f;
-      tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x[v], a.tiles_y[v], x0,
-                y0, x1, y1);
-    }
-    const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
-    tiles_touched[it] = nt;
-    rects[it] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
-    depth_key[it] = __float_as_uint(z);
-    if (nt > kBigTiles) a.big_queue[atomicAdd(a.big_len, 1u)] = (uint32_t)it;
+      if (Q > 0.f && g.det > 0.f) {
+        float Qw = Q * 1.0001f + 1e-4f;
+        float ex = sqrtf(Qw * g.a) * 1.00001f + 1e-3f;
+        float ey = sqrtf(Qw * (g.b * g.b + g.det) / g.a) * 1.00001f + 1e-3f;
+        tile_rect(mux.hi, muy.hi, ex, ey, 1.f / (float)a.tile_w, 1.f / (float)a.tile_h, a.tiles_x[v], a.tiles_y[v],
+                  x0, y0, x1, y1);
+      }
+      const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+      tiles_touched[it] = nt;
+      rects[it] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
+      depth_key[it] = __float_as_uint(z);
+      if (nt > kBigTiles) a.big_queue[atomicAdd(a.big_len, 1u)] = (uint32_t)it;
 
-    // view-dependent colour
-    float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
-    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float Yb[16];
-    sh_basis(D, dx * inv, dy * inv, dz * inv, Yb);
-    float rgb[3] = {0.5f, 0.5f, 0.5f};
+      // view-dependent colour
+      float dx = px - cv.C[0], dy = py - cv.C[1], dz = pz - cv.C[2];
+      float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+      float Yb[16];
+      sh_basis(D, dx * inv, dy * inv, dz * inv, Yb);
+      float rgb[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      rgb[0] += Yb[k] * shp[3 * k];
-      rgb[1] += Yb[k] * shp[3 * k + 1];
-      rgb[2] += Yb[k] * shp[3 * k + 2];
+      for (int k = 0; k < K; ++k) {
+        rgb[0] += Yb[k] * shp[3 * k];
+        rgb[1] += Yb[k] * shp[3 * k + 1];
+        rgb[2] += Yb[k] * shp[3 * k + 2];
+      }
+      feat[3 * it] = make_float4(mux.hi, muy.hi, mux.lo, muy.lo);
+      feat[3 * it + 1] = make_float4(g.i0, g.k, g.i1, log2o);
+      feat[3 * it + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
     }
-    feat[3 * it] = make_float4(mux.hi, muy.hi, mux.lo, muy.lo);
-    feat[3 * it + 1] = make_float4(g.i0, g.k, g.i1, log2o);
-    feat[3 * it + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
+    // tile counts of the small rectangles (the binning expands the queued large ones)
+    if (a.counts) {
+      const uint32_t w = (uint32_t)(x1 - x0);
+      const uint32_t ns = w * (uint32_t)(y1 - y0) <= kBigTiles ? w * (uint32_t)(y1 - y0) : 0u;
+      const uint32_t rounds = __reduce_max_sync(live, ns);
+      for (uint32_t k = 0; k < rounds; ++k) {
+        const bool act = k < ns;
+        const unsigned am = __ballot_sync(live, act);
+        if (act) {
+          const uint32_t t = a.tile_base[v] + (uint32_t)(y0 + k / w) * (uint32_t)a.tiles_x[v] + (uint32_t)x0 + k % w;
+          warp_agg_inc(a.counts, t, am);
+        }
+      }
+    }
   }
 }
 

@@ -43,7 +43,7 @@ __device__ __forceinline__ ItemTiles item_tiles(const TileMap& map, uint32_t it)
 // one large splat is spread over the whole block and large splats clustered
 // in one region are averaged over 256 items.
 // `active` is the mask of lanes of the calling warp that call f together.
-template <class F>
+template <bool SMALL = true, class F>
 __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__ rects,
                                               const uint32_t* __restrict__ tiles, const TileMap& map,
                                               const uint32_t* __restrict__ big_queue,
@@ -53,7 +53,7 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
   __shared__ ItemTiles s_map[kBinThreads];
   __shared__ uint32_t s_wsum[kBinWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int base = blockIdx.x * kBinThreads; base < n; base += gridDim.x * kBinThreads) {
+  for (int base = blockIdx.x * kBinThreads; SMALL && base < n; base += gridDim.x * kBinThreads) {
     const int g = base + threadIdx.x;
     uint32_t cnt = g < n ? tiles[g] : 0u;
     if (cnt > kBigTiles) cnt = 0;  // expanded from the queue below
@@ -116,23 +116,12 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
   }
 }
 
-// Warp-aggregated atomic add of 1 per active lane to counter[t]: lanes with the
-// same t are grouped, the group leader adds the group size once, and each
-// lane gets old value + its rank in the group (neighbouring Gaussians tend to
-// share tiles, so plain per-lane atomics would serialise on one address).
-__device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter, uint32_t t, unsigned active) {
-  const unsigned peers = __match_any_sync(active, t);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&counter[t], (uint32_t)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  return base + __popc(peers & ((1u << lane) - 1u));
-}
-
+// SMALL = false: the projection already counted the items with at most
+// kBigTiles tiles; only the queued large ones are expanded here.
+template <bool SMALL>
 __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_constant__ TileBinArgs a) {
-  for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
-                [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
+  for_each_pair<SMALL>(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
+                       [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
 }
 
 // Length class of a tile list for the visit order: 0 for an empty list,
@@ -353,9 +342,12 @@ int bin_grid(int n, int num_sms) {
 int tile_sort_capacity() { return kTileSortCap; }
 
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
-  cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
+  if (!a.small_counted) cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
   if (a.n > 0) {
-    tile_count_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
+    if (a.small_counted)  // the large splats only: a grid of warps over the queue
+      tile_count_kernel<false><<<std::max(1, 2 * a.num_sms), kBinThreads, 0, s>>>(a);
+    else
+      tile_count_kernel<true><<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
     if (launches) *launches += 1;
   }
   tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
