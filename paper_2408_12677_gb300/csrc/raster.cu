@@ -105,6 +105,37 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
   return TileJob{v, tx * TW, ty * TH, a.ranges[tile], tile};
 }
 
+// Front-to-back step of one pixel for one list entry (Eq. 11 with the skip
+// and stop rules), without branches: a pixel that is done, outside the
+// support or would drop T below t_eps adds a weight of exactly 0.
+template <bool COUNT>
+__device__ __forceinline__ void blend_slot(const float4& a, const float4& bb, const float4& c, float plx, float ply,
+                                           const RasterParams& rp, int idx1, float& T, float& R, float& G, float& B,
+                                           float& D, int& last, bool& done, uint32_t& n_visit, uint32_t& n_blend) {
+  const float dx = __fsub_rn(plx, a.x);
+  const float dy = __fsub_rn(ply, a.y);
+  const float t0 = __fmul_rn(a.z, dx);
+  const float t1 = __fmul_rn(bb.x, __fmaf_rn(-a.w, dx, dy));
+  const float q = __fmaf_rn(t0, t0, __fmul_rn(t1, t1));
+  const bool pass = !done && q <= bb.w;
+  const float al = fminf(rp.alpha_max, ex2_approx(__fsub_rn(bb.y, q)));
+  const float test_T = __fmul_rn(T, __fsub_rn(1.f, al));
+  const bool stop = pass && test_T < rp.t_eps;
+  const bool add = pass && !stop;
+  const float w = add ? al * T : 0.f;
+  R = fmaf(w, c.x, R);
+  G = fmaf(w, c.y, G);
+  B = fmaf(w, c.z, B);
+  D = fmaf(w, bb.z, D);
+  T = add ? test_T : T;
+  last = add ? idx1 : last;
+  if (COUNT) {
+    n_visit += done ? 0u : 1u;
+    n_blend += add ? 1u : 0u;
+  }
+  done = done || stop;
+}
+
 // Forward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
 // visit k) by one warp; buf is the warp's shared staging buffer.
 template <int TW, int TH, bool COUNT, bool LOSS>
@@ -155,45 +186,12 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       const float4 bb = buf[j].b;
       const float4 c = buf[j].c;
       const unsigned halves = __float_as_uint(c.w);
-      PixEval pe;
-      if ((halves & 1u) && !done0) {
-        if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, bb.w, plx, ply0, pe)) {
-          const float al = fminf(rp.alpha_max, pe.araw);
-          const float test_T = __fmul_rn(T0, __fsub_rn(1.f, al));
-          if (test_T < rp.t_eps) {
-            done0 = true;
-          } else {
-            const float w = al * T0;
-            R0 = fmaf(w, c.x, R0);
-            G0 = fmaf(w, c.y, G0);
-            B0 = fmaf(w, c.z, B0);
-            D0 = fmaf(w, bb.z, D0);
-            T0 = test_T;
-            last0 = c0 + j + 1;
-            if (COUNT) ++n_blend;
-          }
-        }
-      }
-      if ((halves & 2u) && !done1) {
-        if (COUNT) ++n_visit;
-        if (eval_splat(a, bb.x, bb.y, bb.w, plx, ply1, pe)) {
-          const float al = fminf(rp.alpha_max, pe.araw);
-          const float test_T = __fmul_rn(T1, __fsub_rn(1.f, al));
-          if (test_T < rp.t_eps) {
-            done1 = true;
-          } else {
-            const float w = al * T1;
-            R1 = fmaf(w, c.x, R1);
-            G1 = fmaf(w, c.y, G1);
-            B1 = fmaf(w, c.z, B1);
-            D1 = fmaf(w, bb.z, D1);
-            T1 = test_T;
-            last1 = c0 + j + 1;
-            if (COUNT) ++n_blend;
-          }
-        }
-      }
+      // branch-free per pixel: every lane evaluates, predicates decide
+      // (a blend of weight 0 leaves R, G, B, D unchanged)
+      if (halves & 1u)
+        blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, T0, R0, G0, B0, D0, last0, done0, n_visit, n_blend);
+      if (halves & 2u)
+        blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, T1, R1, G1, B1, D1, last1, done1, n_visit, n_blend);
     }
   }
   if (COUNT) {
