@@ -199,25 +199,6 @@ __device__ __forceinline__ void tile_rect(float mx, float my, float ex, float ey
 // intrinsics (no contraction differences between the two call sites).
 // a = {mu_local_x, mu_local_y, i0, k}, i1, log2o
 // ---------------------------------------------------------------------------
-struct PixEval {
-  float dx, dy, t0, w, t1, araw;
-};
-
-// r2 = min(qmax_s, log2 o - log2 alpha_min), the support radius of the
-// splat in q' units: a pixel takes part iff q' <= r2 (inside the 3-sigma
-// ellipse and alpha = o 2^-q' >= alpha_min; one comparison for both tests).
-__device__ __forceinline__ bool eval_splat(float4 a, float i1, float log2o, float r2, float plx, float ply,
-                                           PixEval& e) {
-  e.dx = __fsub_rn(plx, a.x);
-  e.dy = __fsub_rn(ply, a.y);
-  e.t0 = __fmul_rn(a.z, e.dx);
-  e.w = __fmaf_rn(-a.w, e.dx, e.dy);
-  e.t1 = __fmul_rn(i1, e.w);
-  const float q = __fmaf_rn(e.t0, e.t0, __fmul_rn(e.t1, e.t1));
-  if (q > r2) return false;
-  e.araw = ex2_approx(__fsub_rn(log2o, q));
-  return true;
-}
 
 // Warp-aggregated atomic add of 1 per active lane to counter[t]: lanes with the
 // same t are grouped, the group leader adds the group size once, and each
