@@ -1,6 +1,6 @@
 // Shared device helpers of the GB300 Gaussian-splatting path: constants,
-// the projected-feature layout, double-float arithmetic, the real SH basis
-// and the per-pixel evaluation used by both raster passes.
+// the projected-feature layout, double-float arithmetic, the real SH basis,
+// hardware exp2 / reciprocal and the warp-aggregated counter increment.
 #pragma once
 
 #include <cstdint>
