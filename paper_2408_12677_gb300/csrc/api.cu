@@ -163,8 +163,9 @@ gs_status ensure_n(gs_ctx* c, int64_t n) {
   GS_CUDA(c, regrow(&c->bigq, cap));
   GS_CUDA(c, regrow(&c->g2d, 3 * cap));
   GS_CUDA(c, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
-  // per (block, view) pose partials: blocks(n) * V <= blocks(V n) + V
-  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((int64_t)project_bwd_blocks((int)cap) + kMaxViews + 1)));
+  // per (block, view) pose partials: blocks(n) * V <= blocks(V n) + V, for
+  // blocks of 64 or more Gaussians
+  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((cap + 31) / 32 + kMaxViews + 1)));
   c->cap_n = cap;
   c->have_state = false;
   return GS_OK;

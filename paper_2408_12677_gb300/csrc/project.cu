@@ -392,8 +392,8 @@ __device__ __forceinline__ bool nonzero_record(const float4& G0, const float4& G
 // deterministic per-block sum of the pose gradient into out[0..5]; every
 // thread of the block calls it
 __device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float* __restrict__ out) {
-  __shared__ float red[kBwdThreads / 32][6];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ float red[kBwdThreads / 32][6];  // blocks of up to kBwdThreads threads
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
   __syncthreads();  // an earlier call is done reading red
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
@@ -405,7 +405,7 @@ __device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float
   __syncthreads();
   if (threadIdx.x < 6) {
     float s = 0.f;
-    for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w][threadIdx.x];
+    for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
     out[threadIdx.x] = s;
   }
 }
@@ -505,7 +505,11 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // with several views the SH gradients are summed in shared memory rows and
 // the sweep reads the SH moments from global memory directly (coalesced),
 // which keeps the shared-memory footprint at three blocks per SM.
-constexpr int kFusedThreads = 128;
+// Gaussians (and threads) per block: 64 for one view (4 blocks of 53 KB per
+// SM, so that the staging, gradient and sweep phases of different blocks
+// overlap), 128 for several views
+template <bool MULTI>
+constexpr int fused_threads() { return MULTI ? 128 : 32; }
 
 __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -522,7 +526,7 @@ struct FusedSmem {
   static constexpr int K = (D + 1) * (D + 1);
   static constexpr int NS = 3 * K;
   static constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
-  static constexpr int B = kFusedThreads;
+  static constexpr int B = fused_threads<false>();
   float p[B * 11], m[B * 11], v[B * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
   float g[B * 11];                        // gradients, same layout
   float sp[B * RS], sm[B * NS], sv[B * NS];
@@ -535,7 +539,7 @@ struct FusedSmemMulti {
   static constexpr int K = (D + 1) * (D + 1);
   static constexpr int NS = 3 * K;
   static constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;
-  static constexpr int B = kFusedThreads;
+  static constexpr int B = fused_threads<true>();
   float p[B * 11], m[B * 11], v[B * 11];
   float g[B * 11];
   float sp[B * RS];  // SH parameters, one row per Gaussian
@@ -543,7 +547,7 @@ struct FusedSmemMulti {
 };
 
 template <int D, bool MULTI>
-__global__ void __launch_bounds__(kFusedThreads, MULTI ? 3 : 1) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
+__global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
                                                                          const float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
@@ -758,12 +762,12 @@ int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, 
 
 int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
                             const AdamArgs& ad, float* pose_partials, cudaStream_t s) {
-  static_assert(kFusedThreads == kBwdThreads, "pose partial buffer is sized for kBwdThreads blocks");
-  const int nb = project_bwd_blocks(a.n);
-  if (nb == 0) return 0;
+  if (a.n <= 0) return 0;
+  const int bt = a.views == 1 ? fused_threads<false>() : fused_threads<true>();
+  const int nb = (a.n + bt - 1) / bt;
 #define GS_FUSED(D_, M_, S_)                                                                                  \
-  project_bwd_adam_kernel<D_, M_><<<nb, kFusedThreads, (int)sizeof(S_<D_>), s>>>(a, g2d, params, m, v, ad, \
-                                                                                 pose_partials)
+  project_bwd_adam_kernel<D_, M_><<<nb, fused_threads<M_>(), (int)sizeof(S_<D_>), s>>>(a, g2d, params, m, v, ad, \
+                                                                                       pose_partials)
   if (a.views == 1) {
     switch (a.sh_degree) {
       case 0: GS_FUSED(0, false, FusedSmem); break;
