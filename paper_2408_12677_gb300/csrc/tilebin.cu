@@ -262,6 +262,11 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
       x1 = ((unsigned long long)zkey[g] << 32) | g;
     }
     const bool live = e0 < m;  // threads beyond m only keep padding
+    // Only the warps holding keys below m run the network (64 keys per
+    // warp); the others leave, and the shared-memory steps synchronise the
+    // remaining warps with a named barrier sized to them.
+    const uint32_t live_threads = m >= 64 ? m / 2 : 32u;
+    if (threadIdx.x >= live_threads) return;
     for (uint32_t k = 2; k <= m; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
         if (j == 1) {
@@ -281,12 +286,12 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
           x0 = keep_min ? (x0 < y0 ? x0 : y0) : (x0 > y0 ? x0 : y0);
           x1 = keep_min ? (x1 < y1 ? x1 : y1) : (x1 > y1 ? x1 : y1);
         } else {
-          __syncthreads();
+          asm volatile("bar.sync 1, %0;" ::"r"(live_threads) : "memory");
           if (live) {
             s[e0] = x0;
             s[e0 + 1] = x1;
           }
-          __syncthreads();
+          asm volatile("bar.sync 1, %0;" ::"r"(live_threads) : "memory");
           if (live) {
             const unsigned long long y0 = s[e0 ^ j], y1 = s[(e0 + 1) ^ j];
             const bool lower = (e0 & j) == 0;
