@@ -99,6 +99,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// sqrt(x) by the hardware approximation (PTX sqrt.approx, about 1 ulp).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One Adam update of one float, shared by every Adam kernel so that the
+// fused and the standalone updates agree bit for bit:
+//   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+//   p -= lr ss m / (sqrt(v) isb2 + eps),  ss = 1 / (1 - b1^t), isb2 = 1 / sqrt(1 - b2^t).
+// The square root and the division are the hardware approximations (within
+// 2 ulp; the denominator is at least eps, a normal number).
+__device__ __forceinline__ void adam_apply(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                           float eps, float ss, float isb2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * g * g;
+  p -= __fdividef(lr * ss * m, sqrt_approx(v) * isb2 + eps);
+}
+
 // 1 / x by the hardware reciprocal (PTX rcp.approx: relative error within
 // 2^-23 for normal x), one instruction instead of the IEEE-rounded
 // division sequence; used where x is a normal number far from overflow.

@@ -215,9 +215,7 @@ __device__ __forceinline__ float adam_lr(const AdamGroups& g, int64_t i) {
 
 __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, float b1, float b2,
                                          float eps, float ss, float isb2) {
-  m = b1 * m + (1.f - b1) * g;
-  v = b2 * v + (1.f - b2) * g * g;
-  p -= lr * ss * m / (sqrtf(v) * isb2 + eps);
+  adam_apply(p, g, m, v, lr, b1, b2, eps, ss, isb2);
 }
 
 __global__ void __launch_bounds__(256) adam_kernel(int64_t total, float4* __restrict__ p4, float4* __restrict__ g4,

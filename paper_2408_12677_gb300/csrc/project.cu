@@ -486,9 +486,7 @@ __device__ __forceinline__ void device_bias_corrections(AdamArgs& ad) {
 __global__ void step_increment_kernel(long long* step) { *step += 1; }
 
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& ad) {
-  m = ad.beta1 * m + (1.f - ad.beta1) * g;
-  v = ad.beta2 * v + (1.f - ad.beta2) * g * g;
-  p -= lr * ad.step_scale * m / (sqrtf(v) * ad.inv_sqrt_bc2 + ad.eps);
+  adam_apply(p, g, m, v, lr, ad.beta1, ad.beta2, ad.eps, ad.step_scale, ad.inv_sqrt_bc2);
 }
 
 // Backward of the projection fused with the Adam step, for one optimisation
@@ -679,24 +677,46 @@ __global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project
       V[f] = v;
     }
   }
-  for (int e = t; e < cnt * NS; e += B) {
-    const int gi = e / NS, rr = e - gi * NS;
-    const int k = rr / 3, c = rr - 3 * k;
-    const int64_t f = gsh + e;
-    float p = sm.sp[gi * RS + rr], m, v, g;
-    if constexpr (MULTI) {
-      m = M[f];
-      v = V[f];
-      g = sm.gs[gi * RS + rr];
-    } else {
-      m = sm.sm[e];
-      v = sm.sv[e];
-      g = sm.Y[gi][k] * sm.graw[gi][c];
+  if constexpr (!MULTI && B == 32) {
+    // one view, a warp per block: walk the SH rows, lane t on columns t, t + 32, ...
+    // (coalesced rows, and each lane's coefficient (k, c) fixed per column)
+#pragma unroll
+    for (int c0 = 0; c0 < NS; c0 += B) {
+      const int rr = c0 + t;
+      if (rr < NS) {
+        const int k = rr / 3, c = rr - 3 * k;
+        const float lr = k == 0 ? ad.lr[4] : ad.lr[5];
+        for (int gi = 0; gi < cnt; ++gi) {
+          const int e = gi * NS + rr;
+          float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e];
+          adam_update(p, sm.Y[gi][k] * sm.graw[gi][c], m, v, lr, ad);
+          const int64_t f = gsh + e;
+          P[f] = p;
+          M[f] = m;
+          V[f] = v;
+        }
+      }
     }
-    adam_update(p, g, m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
-    P[f] = p;
-    M[f] = m;
-    V[f] = v;
+  } else {
+    for (int e = t; e < cnt * NS; e += B) {
+      const int gi = e / NS, rr = e - gi * NS;
+      const int k = rr / 3, c = rr - 3 * k;
+      const int64_t f = gsh + e;
+      float p = sm.sp[gi * RS + rr], m, v, g;
+      if constexpr (MULTI) {
+        m = M[f];
+        v = V[f];
+        g = sm.gs[gi * RS + rr];
+      } else {
+        m = sm.sm[e];
+        v = sm.sv[e];
+        g = sm.Y[gi][k] * sm.graw[gi][c];
+      }
+      adam_update(p, g, m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
+      P[f] = p;
+      M[f] = m;
+      V[f] = v;
+    }
   }
 }
 
