@@ -90,6 +90,16 @@ __device__ __forceinline__ void geometry(const CamView& cv, float dilation, floa
   g.i1 = kS2 * sqrtf(g.a / g.det);
 }
 
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 constexpr int kFwdThreads = 128;
 
 // One thread per Gaussian: its parameters are read once and projected into
@@ -104,21 +114,38 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   constexpr int NS = 3 * K;
   constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
   __shared__ float s_sh[kFwdThreads * RS];
-  // the block's SH coefficients are contiguous: stage them with coalesced loads
+  __shared__ float s_p[kFwdThreads * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
+  // the block's slices of every parameter array are contiguous: stage them
+  // all at once with coalesced asynchronous copies
   const int base = blockIdx.x * kFwdThreads;
   const int cnt = min(kFwdThreads, a.n - base);
-  for (int e = threadIdx.x; e < cnt * NS; e += kFwdThreads) {
-    const int gi = e / NS;
-    s_sh[gi * RS + (e - gi * NS)] = __ldg(a.sh + (size_t)base * NS + e);
+  {
+    constexpr int B = kFwdThreads;
+    const float* src[4] = {a.means + 3 * (size_t)base, a.log_scales + 3 * (size_t)base, a.quats + 4 * (size_t)base,
+                           a.logits + (size_t)base};
+    const int so[4] = {0, 3 * B, 6 * B, 10 * B};
+    const int len[4] = {3 * cnt, 3 * cnt, 4 * cnt, cnt};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      for (int e = threadIdx.x; e < len[r]; e += B) cp_async4(&s_p[so[r] + e], src[r] + e);
+    for (int e = threadIdx.x; e < cnt * NS; e += B) {
+      const int gi = e / NS;
+      cp_async4(&s_sh[gi * RS + (e - gi * NS)], a.sh + (size_t)base * NS + e);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
   }
   __syncthreads();
   const int i = base + threadIdx.x;
   const unsigned live = __ballot_sync(0xFFFFFFFFu, i < a.n);  // lanes that reach the counting loops
   if (i >= a.n) return;
-  const float px = a.means[3 * i], py = a.means[3 * i + 1], pz = a.means[3 * i + 2];
-  const float q4[4] = {a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]};
-  const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
-  const float logit = a.logits[i];
+  const int t = threadIdx.x;
+  const float px = s_p[3 * t], py = s_p[3 * t + 1], pz = s_p[3 * t + 2];
+  const float ls[3] = {s_p[3 * kFwdThreads + 3 * t], s_p[3 * kFwdThreads + 3 * t + 1],
+                       s_p[3 * kFwdThreads + 3 * t + 2]};
+  const float q4[4] = {s_p[6 * kFwdThreads + 4 * t], s_p[6 * kFwdThreads + 4 * t + 1],
+                       s_p[6 * kFwdThreads + 4 * t + 2], s_p[6 * kFwdThreads + 4 * t + 3]};
+  const float logit = s_p[10 * kFwdThreads + t];
   const float o = 1.f / (1.f + expf(-logit));
   const float log2o = log2f(o);
   // support of the blend test: q <= min(9, 2 ln(o / alpha_min)), widened a
@@ -508,16 +535,6 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // overlap), 128 for several views
 template <bool MULTI>
 constexpr int fused_threads() { return MULTI ? 128 : 32; }
-
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 template <int D>
 struct FusedSmem {
