@@ -46,6 +46,7 @@ struct gs_ctx {
   uint32_t* toffset = nullptr;  // per-tile list offsets
   uint32_t* tcursor = nullptr;  // per-tile scatter cursors
   uint32_t* torder = nullptr;   // raster visit order of the tiles (longest lists first)
+  uint32_t* scan_aux = nullptr;  // multi-block tile scan scratch
   uint32_t* bigq = nullptr;     // ids of Gaussians covering more than kBigTiles tiles
   uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue
   unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
@@ -195,6 +196,7 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   GS_CUDA(c, regrow(&c->toffset, cap));
   GS_CUDA(c, regrow(&c->tcursor, cap));
   GS_CUDA(c, regrow(&c->torder, cap));
+  GS_CUDA(c, regrow(&c->scan_aux, tile_scan_aux_size(cap)));
   GS_CUDA(c, regrow(&c->tile_loss, 12 * cap));
   c->cap_t = cap;
   c->have_state = false;
@@ -392,6 +394,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
   tb.big_len = c->d_bigmeta;
   tb.order = c->order_tiles ? c->torder : nullptr;
   tb.small_counted = small_counted;
+  tb.scan_aux = c->scan_aux;
   c->st_ordered = false;
   {
     StageTimer t(c, GS_STAGE_DUPLICATE, s);
@@ -516,6 +519,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->toffset);
   cudaFree(c->tcursor);
   cudaFree(c->torder);
+  cudaFree(c->scan_aux);
   cudaFree(c->bigq);
   cudaFree(c->d_bigmeta);
   cudaFree(c->d_binstats);

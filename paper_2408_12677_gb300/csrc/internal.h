@@ -138,8 +138,10 @@ struct TileBinArgs {
   const uint32_t* big_len;
   uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
   bool small_counted;         // counts already hold every item with at most kBigTiles tiles (projection)
+  uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
 };
 int tile_sort_capacity();
+int64_t tile_scan_aux_size(int64_t n_tiles);
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
 void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches);
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches);

@@ -211,6 +211,157 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
   }
 }
 
+// Multi-block form of tile_scan_kernel for many tiles (batches of views):
+//   up:   block b sums the counts of its kScanTiles tiles, takes their
+//         maximum and the histogram of their length classes;
+//   mid:  one block: the total (stats, n_pairs), the longest list and the
+//         start of each length class in the visit order (descending);
+//   down: block b adds up the earlier blocks' sums and class histograms (in
+//         block order) for its bases, then writes offsets, cursors and the
+//         visit order of its tiles.
+// aux per block: {sum lo, sum hi, max, hist[33]}; aux_tail: class starts[33].
+constexpr int kScanTiles = 1024;
+constexpr int kScanAux = 36;
+
+__global__ void __launch_bounds__(256) tile_scan_up_kernel(int T, const uint32_t* __restrict__ counts,
+                                                           uint32_t* __restrict__ aux) {
+  __shared__ uint32_t s_hist[33];
+  __shared__ unsigned long long s_sum[8];
+  __shared__ uint32_t s_max[8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x < 33) s_hist[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long sum = 0;
+  uint32_t mx = 0;
+  const int i0 = blockIdx.x * kScanTiles;
+#pragma unroll
+  for (int j = 0; j < kScanTiles / 256; ++j) {
+    const int i = i0 + j * 256 + threadIdx.x;
+    const uint32_t c = i < T ? counts[i] : 0u;
+    sum += c;
+    mx = max(mx, c);
+    const int cls = i < T ? length_class(c) : 33;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, cls);
+    if (cls < 33 && lane == __ffs(peers) - 1) atomicAdd(&s_hist[cls], (uint32_t)__popc(peers));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+    mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+  }
+  if (lane == 0) {
+    s_sum[wid] = sum;
+    s_max[wid] = mx;
+  }
+  __syncthreads();
+  uint32_t* out = aux + (size_t)kScanAux * blockIdx.x;
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    uint32_t m = 0;
+    for (int w = 0; w < 8; ++w) {
+      t += s_sum[w];
+      m = max(m, s_max[w]);
+    }
+    out[0] = (uint32_t)t;
+    out[1] = (uint32_t)(t >> 32);
+    out[2] = m;
+  }
+  if (threadIdx.x < 33) out[3 + threadIdx.x] = s_hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(64) tile_scan_mid_kernel(int nb, const uint32_t* __restrict__ aux,
+                                                           uint32_t* __restrict__ aux_tail, uint32_t capacity,
+                                                           uint32_t* __restrict__ n_pairs,
+                                                           unsigned long long* __restrict__ stats) {
+  __shared__ uint32_t s_tot[33];
+  if (threadIdx.x < 33) {
+    uint32_t t = 0;
+    for (int b = 0; b < nb; ++b) t += aux[(size_t)kScanAux * b + 3 + threadIdx.x];
+    s_tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    uint32_t m = 0;
+    for (int b = 0; b < nb; ++b) {
+      const uint32_t* a = aux + (size_t)kScanAux * b;
+      tot += (unsigned long long)a[0] | ((unsigned long long)a[1] << 32);
+      m = max(m, a[2]);
+    }
+    stats[0] = tot;
+    stats[1] = m;
+    *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
+    uint32_t run = 0;
+    for (int c = 32; c >= 0; --c) {  // longest class first
+      aux_tail[c] = run;
+      run += s_tot[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) tile_scan_down_kernel(int T, const uint32_t* __restrict__ counts,
+                                                             const uint32_t* __restrict__ aux,
+                                                             const uint32_t* __restrict__ aux_tail,
+                                                             uint32_t* __restrict__ offsets,
+                                                             uint32_t* __restrict__ cursors,
+                                                             uint32_t* __restrict__ order) {
+  constexpr int PER = kScanTiles / 256;  // consecutive tiles per thread
+  __shared__ unsigned long long s_scan[256];
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_cls[33];
+  const int b = blockIdx.x, lane = threadIdx.x & 31;
+  if (threadIdx.x < 33) {  // start of this block's tiles within each length class
+    uint32_t o = aux_tail[threadIdx.x];
+    for (int k = 0; k < b; ++k) o += aux[(size_t)kScanAux * k + 3 + threadIdx.x];
+    s_cls[threadIdx.x] = o;
+  } else if (threadIdx.x == 64) {
+    unsigned long long o = 0;
+    for (int k = 0; k < b; ++k) {
+      const uint32_t* a = aux + (size_t)kScanAux * k;
+      o += (unsigned long long)a[0] | ((unsigned long long)a[1] << 32);
+    }
+    s_base = o;
+  }
+  const int i0 = b * kScanTiles + threadIdx.x * PER;
+  uint32_t c[PER];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    c[j] = i0 + j < T ? counts[i0 + j] : 0u;
+    sum += c[j];
+  }
+  s_scan[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 1; off < 256; off <<= 1) {
+    const unsigned long long v = threadIdx.x >= (unsigned)off ? s_scan[threadIdx.x - off] : 0ull;
+    __syncthreads();
+    s_scan[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = s_base + s_scan[threadIdx.x] - sum;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    if (i0 + j < T) {
+      const uint32_t o = (uint32_t)(run < 0xFFFFFFFFull ? run : 0xFFFFFFFFull);
+      offsets[i0 + j] = o;
+      cursors[i0 + j] = o;
+    }
+    run += c[j];
+  }
+  if (!order) return;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = i0 + j;
+    const int cls = i < T ? length_class(c[j]) : 33;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, cls);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (cls < 33 && lane == leader) base = atomicAdd(&s_cls[cls], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    if (cls < 33) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
+}
+
 __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_constant__ TileBinArgs a) {
   bool over = false;
   for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
@@ -346,6 +497,8 @@ int bin_grid(int n, int num_sms) {
 
 int tile_sort_capacity() { return kTileSortCap; }
 
+int64_t tile_scan_aux_size(int64_t n_tiles) { return (int64_t)kScanAux * ((n_tiles + kScanTiles - 1) / kScanTiles + 2); }
+
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   if (!a.small_counted) cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
   if (a.n > 0) {
@@ -355,9 +508,18 @@ void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launc
       tile_count_kernel<true><<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
     if (launches) *launches += 1;
   }
-  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
-                                              a.stats, a.order);
-  if (launches) *launches += 1;
+  if (a.n_tiles <= 4 * kScanThreads || !a.scan_aux) {  // one block is enough
+    tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
+                                                a.stats, a.order);
+    if (launches) *launches += 1;
+  } else {
+    const int nb = (a.n_tiles + kScanTiles - 1) / kScanTiles;
+    uint32_t* tail = a.scan_aux + (size_t)kScanAux * nb;
+    tile_scan_up_kernel<<<nb, 256, 0, s>>>(a.n_tiles, a.counts, a.scan_aux);
+    tile_scan_mid_kernel<<<1, 64, 0, s>>>(nb, a.scan_aux, tail, a.capacity, a.n_pairs, a.stats);
+    tile_scan_down_kernel<<<nb, 256, 0, s>>>(a.n_tiles, a.counts, a.scan_aux, tail, a.offsets, a.cursors, a.order);
+    if (launches) *launches += 3;
+  }
 }
 
 void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {

@@ -381,3 +381,30 @@ def test_train_step_batched_matches_three_calls(ctx):
             xa, ya = x.cpu().numpy(), y.cpu().numpy()
             bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
             assert bad.sum() <= max(4, int(1e-4 * xa.size)), (name, step, int(bad.sum()))
+
+
+def test_visit_order_with_many_tiles(ctx):
+    """Two 1200x680 views (6450 tiles: the multi-block binning scan builds the
+    visit order): the same images with and without the order and with a CTA
+    per tile, so the order is a permutation of all tiles."""
+    from paper_2408_12677_gb300 import abi
+    rng = np.random.default_rng(41)
+    views = []
+    for k, eye in enumerate(([0.0, 0.0, 0.0], [0.2, -0.3, 0.1])):
+        cam = Camera(600.0, 600.0, 600.0, 340.0, 1200, 680)
+        views.append(workloads.View(cam, look_at(eye, [2.5, 0.0, 0.0]), None, None))
+    P = workloads.random_gaussians(rng, 40000, views[0].cam, views[0].pose, 0, z_range=(1.5, 3.5),
+                                   log_scale_range=(-4.0, -2.0))
+    model = to_gpu_model(P)
+    out = []
+    for order, persistent in ((True, True), (False, True), (True, False)):
+        abi.gs_ctx_set_tile_order(ctx.handle, order)
+        abi.gs_ctx_set_persistent(ctx.handle, persistent)
+        out.append(_batched_render(ctx, model, views))
+    abi.gs_ctx_set_tile_order(ctx.handle, True)
+    abi.gs_ctx_set_persistent(ctx.handle, True)
+    assert ctx.stats()["n_tiles"] == 2 * 75 * 43
+    for other in out[1:]:
+        for (c0, d0, a0), (c1, d1, a1) in zip(out[0], other):
+            assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(a0, a1)
+    assert float(np.mean(out[0][0][2] > 0.1)) > 0.3  # the views see the cloud

@@ -45,7 +45,9 @@ def _case(rng, n, W, H, max_ext, ties=False):
 
 @pytest.mark.parametrize("tw,th", [(16, 16), (8, 32), (32, 8)])
 @pytest.mark.parametrize("W,H,n,max_ext,ties", [(64, 48, 500, 20.0, False), (100, 70, 3000, 12.0, True),
-                                                 (1200, 680, 60000, 40.0, False)])
+                                                 (1200, 680, 60000, 40.0, False),
+                                                 # more than 4096 tiles: the multi-block scan, a ragged last block
+                                                 (2600, 1950, 90000, 30.0, True)])
 def test_bitexact(ctx, tw, th, W, H, n, max_ext, ties):
     rng = np.random.default_rng(W * 7 + n + tw)
     m, e, z = _case(rng, n, W, H, max_ext, ties)
