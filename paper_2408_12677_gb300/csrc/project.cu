@@ -534,7 +534,7 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // SM, so that the staging, gradient and sweep phases of different blocks
 // overlap), 128 for several views
 template <bool MULTI>
-constexpr int fused_threads() { return MULTI ? 128 : 32; }
+constexpr int fused_threads() { return 32; }
 
 template <int D>
 struct FusedSmem {
@@ -559,10 +559,11 @@ struct FusedSmemMulti {
   float g[B * 11];
   float sp[B * RS];  // SH parameters, one row per Gaussian
   float gs[B * RS];  // SH gradients summed over the views, same rows
+  float sm[B * NS], sv[B * NS];  // SH moments
 };
 
 template <int D, bool MULTI>
-__global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
+__global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
                                                                          const float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
@@ -596,11 +597,9 @@ __global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project
       cp_async4(&sm.m[so[r] + e], M + g0[r] + e);
       cp_async4(&sm.v[so[r] + e], V + g0[r] + e);
     }
-  if constexpr (!MULTI) {
-    for (int e = t; e < cnt * NS; e += B) {
-      cp_async4(&sm.sm[e], M + gsh + e);
-      cp_async4(&sm.sv[e], V + gsh + e);
-    }
+  for (int e = t; e < cnt * NS; e += B) {
+    cp_async4(&sm.sm[e], M + gsh + e);
+    cp_async4(&sm.sv[e], V + gsh + e);
   }
   cp_async_commit();
   float4 G0 = make_float4(0.f, 0.f, 0.f, 0.f), G1 = G0, G2 = G0;
@@ -694,8 +693,8 @@ __global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project
       V[f] = v;
     }
   }
-  if constexpr (!MULTI && B == 32) {
-    // one view, a warp per block: walk the SH rows, lane t on columns t, t + 32, ...
+  if constexpr (B == 32) {
+    // a warp per block: walk the SH rows, lane t on columns t, t + 32, ...
     // (coalesced rows, and each lane's coefficient (k, c) fixed per column)
 #pragma unroll
     for (int c0 = 0; c0 < NS; c0 += B) {
@@ -706,7 +705,12 @@ __global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project
         for (int gi = 0; gi < cnt; ++gi) {
           const int e = gi * NS + rr;
           float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e];
-          adam_update(p, sm.Y[gi][k] * sm.graw[gi][c], m, v, lr, ad);
+          float g;
+          if constexpr (MULTI)
+            g = sm.gs[gi * RS + rr];
+          else
+            g = sm.Y[gi][k] * sm.graw[gi][c];
+          adam_update(p, g, m, v, lr, ad);
           const int64_t f = gsh + e;
           P[f] = p;
           M[f] = m;
@@ -719,16 +723,11 @@ __global__ void __launch_bounds__(fused_threads<MULTI>(), MULTI ? 3 : 1) project
       const int gi = e / NS, rr = e - gi * NS;
       const int k = rr / 3, c = rr - 3 * k;
       const int64_t f = gsh + e;
-      float p = sm.sp[gi * RS + rr], m, v, g;
-      if constexpr (MULTI) {
-        m = M[f];
-        v = V[f];
+      float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e], g;
+      if constexpr (MULTI)
         g = sm.gs[gi * RS + rr];
-      } else {
-        m = sm.sm[e];
-        v = sm.sv[e];
+      else
         g = sm.Y[gi][k] * sm.graw[gi][c];
-      }
       adam_update(p, g, m, v, k == 0 ? ad.lr[4] : ad.lr[5], ad);
       P[f] = p;
       M[f] = m;
