@@ -359,34 +359,42 @@ __device__ __forceinline__ void warp_reduce_add10(float (&v)[10], float* __restr
   if (!(lane & 1) && valid) atomicAdd(&rec[rec_off((b4 ? 5 : 0) + i3)], x);
 }
 
-// Back-to-front step of one pixel for one Gaussian: updates the pixel's
-// running transmittance T and "colour behind" U and adds the Gaussian's
-// gradient sums to v.  With ga = dL/dalpha * alpha (unclamped alpha) the
+// Back-to-front step of one pixel for one Gaussian (pixel_q, then bwd_body):
+// updates the pixel's running transmittance T and "colour behind" U and adds
+// the Gaussian's gradient sums to v.  With ga = dL/dalpha * alpha (unclamped alpha) the
 // exponent and opacity gradients are linear in
 //   v[0] = sum ga t0, v[1] = sum ga t1, v[2] = sum ga t0 dx,
 //   v[3] = sum ga t1 dx, v[4] = sum ga t1 w, v[5] = sum ga
 // (t0 = i0 dx, t1 = i1 w, w = dy - k dx): the Gaussian's constants (i0, i1,
 // k, ln 2, 1 / opacity) are applied once per Gaussian in the projection
 // backward pass.  v[6] = sum w dD (depth), v[7..9] = sum w dC (colour).
-__device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, const float4& c, float plx, float ply,
-                                          const RasterParams& rp, bool behind_last, float& T, float& U, float dC0,
-                                          float dC1, float dC2, float dD, float dA_T, float (&v)[10]) {
-  // every lane of the warp calls this together; lanes that do not take part
-  // (outside the support, or the entry is not in front of their last
-  // contributor) run the same instructions with weight 0
-  const float dx = __fsub_rn(plx, a.x);
+// Exponent of one pixel for one entry: q' = t0^2 + t1^2 and its parts.
+struct PixQ {
+  float dx, t0, wq, t1, q;
+  bool pass;  // inside the support and in front of the pixel's last contributor
+};
+__device__ __forceinline__ PixQ pixel_q(const float4& a, const float4& bb, float plx, float ply, bool behind_last) {
+  PixQ r;
+  r.dx = __fsub_rn(plx, a.x);
   const float dy = __fsub_rn(ply, a.y);
-  const float t0 = __fmul_rn(a.z, dx);
-  const float wq = __fmaf_rn(-a.w, dx, dy);
-  const float t1 = __fmul_rn(bb.x, wq);
-  const float q = __fmaf_rn(t0, t0, __fmul_rn(t1, t1));
-  const bool pass = behind_last && q <= bb.w;
-  if (!__any_sync(kFull, pass)) return false;
-  const float araw = ex2_approx(__fsub_rn(bb.y, q));
+  r.t0 = __fmul_rn(a.z, r.dx);
+  r.wq = __fmaf_rn(-a.w, r.dx, dy);
+  r.t1 = __fmul_rn(bb.x, r.wq);
+  r.q = __fmaf_rn(r.t0, r.t0, __fmul_rn(r.t1, r.t1));
+  r.pass = behind_last && r.q <= bb.w;
+  return r;
+}
+
+// The rest of the back-to-front step, without branches: a lane whose pixel
+// does not take part runs it with weight 0 and leaves T, U and v unchanged.
+__device__ __forceinline__ void bwd_body(const PixQ& e, const float4& bb, const float4& c, const RasterParams& rp,
+                                         float& T, float& U, float dC0, float dC1, float dC2, float dD, float dA_T,
+                                         float (&v)[10]) {
+  const float araw = ex2_approx(__fsub_rn(bb.y, e.q));
   const float al = fminf(rp.alpha_max, araw);
   const float inv1m = rcp_approx(1.f - al);  // 1 - alpha in [0.01, 1)
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
-  const float w = pass ? al * Ti : 0.f;
+  const float w = e.pass ? al * Ti : 0.f;
   v[7] = fmaf(w, dC0, v[7]);
   v[8] = fmaf(w, dC1, v[8]);
   v[9] = fmaf(w, dC2, v[9]);
@@ -395,16 +403,15 @@ __device__ __forceinline__ bool bwd_pixel(const float4& a, const float4& bb, con
   // d/d alpha_i: colour/depth T_i c_i - (sum behind)/(1 - alpha_i); alpha image + T_final/(1 - alpha_i)
   const float g_alpha = Ti * cdot - (U - dA_T) * inv1m;
   U = fmaf(w, cdot, U);
-  T = pass ? Ti : T;
-  const float ga = (pass && araw <= rp.alpha_max) ? g_alpha * araw : 0.f;  // the 0.99 clamp has zero gradient
-  const float gt0 = ga * t0, gt1 = ga * t1;
+  T = e.pass ? Ti : T;
+  const float ga = (e.pass && araw <= rp.alpha_max) ? g_alpha * araw : 0.f;  // the 0.99 clamp has zero gradient
+  const float gt0 = ga * e.t0, gt1 = ga * e.t1;
   v[0] += gt0;
   v[1] += gt1;
-  v[2] = fmaf(gt0, dx, v[2]);
-  v[3] = fmaf(gt1, dx, v[3]);
-  v[4] = fmaf(gt1, wq, v[4]);
+  v[2] = fmaf(gt0, e.dx, v[2]);
+  v[3] = fmaf(gt1, e.dx, v[3]);
+  v[4] = fmaf(gt1, e.wq, v[4]);
   v[5] += ga;
-  return pass;
 }
 
 // Backward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
@@ -513,11 +520,14 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       const unsigned halves = __float_as_uint(cc.w);
-      bool contrib = false;
-      if (halves & 1u)
-        contrib |= bwd_pixel(a, bb, cc, plx, ply0, rp, idx < last0, T0, U0, c00, c01, c02, d0, dAT0, v);
-      if (halves & 2u)
-        contrib |= bwd_pixel(a, bb, cc, plx, ply1, rp, idx < last1, T1, U1, c10, c11, c12, d1, dAT1, v);
+      // both pixel rows' exponents first, then the rows' steps as straight-line
+      // code (independent chains); skipped when no lane of the warp takes part
+      const PixQ e0 = pixel_q(a, bb, plx, ply0, (halves & 1u) && idx < last0);
+      const PixQ e1 = pixel_q(a, bb, plx, ply1, (halves & 2u) && idx < last1);
+      const bool contrib = e0.pass || e1.pass;
+      if (!__any_sync(kFull, contrib)) continue;
+      if (halves & 1u) bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+      if (halves & 2u) bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;
       float* rec = g2d + 12 * (size_t)bid[j];
