@@ -110,14 +110,15 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
 // support or would drop T below t_eps adds a weight of exactly 0.
 template <bool COUNT>
 __device__ __forceinline__ void blend_slot(const float4& a, const float4& bb, const float4& c, float plx, float ply,
-                                           const RasterParams& rp, int idx1, float& T, float& R, float& G, float& B,
-                                           float& D, int& last, bool& done, uint32_t& n_visit, uint32_t& n_blend) {
+                                           const RasterParams& rp, int idx1, bool on, float& T, float& R, float& G,
+                                           float& B, float& D, int& last, bool& done, uint32_t& n_visit,
+                                           uint32_t& n_blend) {
   const float dx = __fsub_rn(plx, a.x);
   const float dy = __fsub_rn(ply, a.y);
   const float t0 = __fmul_rn(a.z, dx);
   const float t1 = __fmul_rn(bb.x, __fmaf_rn(-a.w, dx, dy));
   const float q = __fmaf_rn(t0, t0, __fmul_rn(t1, t1));
-  const bool pass = !done && q <= bb.w;
+  const bool pass = on && !done && q <= bb.w;
   const float al = fminf(rp.alpha_max, ex2_approx(__fsub_rn(bb.y, q)));
   const float test_T = __fmul_rn(T, __fsub_rn(1.f, al));
   const bool stop = pass && test_T < rp.t_eps;
@@ -130,7 +131,7 @@ __device__ __forceinline__ void blend_slot(const float4& a, const float4& bb, co
   T = add ? test_T : T;
   last = add ? idx1 : last;
   if (COUNT) {
-    n_visit += done ? 0u : 1u;
+    n_visit += (on && !done) ? 1u : 0u;
     n_blend += add ? 1u : 0u;
   }
   done = done || stop;
@@ -188,10 +189,12 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       const unsigned halves = __float_as_uint(c.w);
       // branch-free per pixel: every lane evaluates, predicates decide
       // (a blend of weight 0 leaves R, G, B, D unchanged)
-      if (halves & 1u)
-        blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, T0, R0, G0, B0, D0, last0, done0, n_visit, n_blend);
-      if (halves & 2u)
-        blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, T1, R1, G1, B1, D1, last1, done1, n_visit, n_blend);
+      // both rows as straight-line code (independent chains; a row outside the
+      // support box runs with weight 0)
+      blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, halves & 1u, T0, R0, G0, B0, D0, last0, done0, n_visit,
+                        n_blend);
+      blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, halves & 2u, T1, R1, G1, B1, D1, last1, done1, n_visit,
+                        n_blend);
     }
   }
   if (COUNT) {
