@@ -181,20 +181,13 @@ class StreamingOptimizer:
         return self.alpha[0].cpu().numpy()
 
     def iterate(self, views: list[Keyframe]):
-        """One batched optimisation iteration over ``views``."""
-        h = self.ctx.handle
+        """One batched optimisation iteration over ``views`` (gs_train_step_batched)."""
         m = self.map.model
-        g = m.gaussians()
         V = len(views)
-        cams = [self.cam_s] * V
-        vms = [k.view for k in views]
-        abi.gs_render_fwd_batched(h, g, cams, vms, self.rcfg, self.color[:V], self.depth[:V], self.alpha[:V])
-        abi.gs_loss_l1_batched(h, cams, self.color[:V], self.depth[:V], [k.rgb for k in views],
-                               [k.depth for k in views], self.w_color, self.w_depth, self.loss, self.dLdc[:V],
-                               self.dLdd[:V])
         self.step += 1
-        abi.gs_render_bwd_adam_batched(h, g, cams, vms, self.rcfg, self.dLdc[:V], self.dLdd[:V], None, m.flat, m.m,
-                                       m.v, self.acfg, self.step)
+        abi.gs_train_step_batched(self.ctx.handle, m.gaussians(), [self.cam_s] * V, [k.view for k in views], self.rcfg,
+                                  [k.rgb for k in views], [k.depth for k in views], self.w_color, self.w_depth,
+                                  self.loss, m.flat, m.m, m.v, self.acfg, self.step)
 
     def process_frame(self, rgb: np.ndarray, depth: np.ndarray, pose) -> FrameStats:
         """rgb [H, W, 3] in [0, 1], depth [H, W] (0 = invalid), pose: world-to-camera (R, t)."""
@@ -224,3 +217,63 @@ class StreamingOptimizer:
                            ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
         self.frame_index += 1
         return stats
+
+
+@dataclasses.dataclass
+class GlobalStats:
+    epochs: int
+    keyframes: int
+    steps: int
+    view_iterations: int
+    gpu_ms: float
+    loss_first: float   # summed loss of the first batched step
+    loss_last: float    # summed loss of the last batched step
+
+    @property
+    def ms_per_view_iteration(self) -> float:
+        return self.gpu_ms / max(self.view_iterations, 1)
+
+
+def global_optimize(opt: StreamingOptimizer, epochs: int = 2, views_per_step: int = 16,
+                    rng_seed: int = 0) -> GlobalStats:
+    """Offline optimisation over the keyframe list after the sequence (the
+    paper's global optimisation, Sec. III-B.3 / IV): each epoch visits every
+    keyframe once in a random order, ``views_per_step`` keyframes per batched
+    iteration (gs_train_step_batched: the loss summed over them, one Adam
+    step)."""
+    rng = np.random.default_rng(rng_seed)
+    kfs = opt.keyframes
+    if not kfs:
+        return GlobalStats(0, 0, 0, 0, 0.0, float("nan"), float("nan"))
+    V = max(1, min(int(views_per_step), len(kfs), 16))
+    H, W = opt.cam.height, opt.cam.width
+    dev = opt.map.model.flat.device
+    extra = V - len(opt.color)
+    for _ in range(max(0, extra)):  # output slots for the larger batches
+        opt.color.append(torch.empty((3, H, W), device=dev))
+        opt.depth.append(torch.empty((H, W), device=dev))
+        opt.alpha.append(torch.empty((H, W), device=dev))
+        opt.dLdc.append(torch.empty((3, H, W), device=dev))
+        opt.dLdd.append(torch.empty((H, W), device=dev))
+    m = opt.map.model
+    g = m.gaussians()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = views = 0
+    first = None
+    ev0.record()
+    for _ in range(epochs):
+        perm = rng.permutation(len(kfs))
+        for s0 in range(0, len(kfs), V):
+            batch = [kfs[i] for i in perm[s0:s0 + V]]
+            n = len(batch)
+            opt.step += 1
+            abi.gs_train_step_batched(opt.ctx.handle, g, [opt.cam_s] * n, [k.view for k in batch], opt.rcfg,
+                                      [k.rgb for k in batch], [k.depth for k in batch], opt.w_color, opt.w_depth,
+                                      opt.loss, m.flat, m.m, m.v, opt.acfg, opt.step)
+            if first is None:
+                first = float(opt.loss.item())
+            steps += 1
+            views += n
+    ev1.record()
+    torch.cuda.synchronize()
+    return GlobalStats(epochs, len(kfs), steps, views, ev0.elapsed_time(ev1), first, float(opt.loss.item()))

@@ -107,3 +107,30 @@ def test_checkpoint_gradients_match_oracle(run):
             assert abs(gpu - d1) <= 2e-3 * abs(d1) + 1e-6 * np.abs(G).max(), (name, i, gpu, d1)
             checked += 1
     assert checked >= 6
+
+
+def test_global_optimisation_over_keyframes(run):
+    """The offline pass over the keyframe list: every keyframe visited once per
+    epoch in batches of up to 16 views, finite map, the summed loss of a
+    fixed batch decreases."""
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.streaming import global_optimize
+    st, frames, opt, stats = run
+    kfs = opt.keyframes
+    probe = kfs[: min(4, len(kfs))]
+
+    def probe_loss():
+        V = len(probe)
+        abi.gs_render_fwd_batched(opt.ctx.handle, opt.map.model.gaussians(), [opt.cam_s] * V, [k.view for k in probe],
+                                  opt.rcfg, opt.color[:V], opt.depth[:V], None)
+        abi.gs_loss_l1_batched(opt.ctx.handle, [opt.cam_s] * V, opt.color[:V], opt.depth[:V], [k.rgb for k in probe],
+                               [k.depth for k in probe], 0.8, 0.2, opt.loss, opt.dLdc[:V], opt.dLdd[:V])
+        return float(opt.loss.item())
+
+    before = probe_loss()
+    g = global_optimize(opt, epochs=3, views_per_step=3, rng_seed=2)
+    after = probe_loss()
+    assert g.keyframes == len(kfs) and g.view_iterations == 3 * len(kfs)
+    assert g.steps == 3 * -(-len(kfs) // 3)
+    assert torch.isfinite(opt.map.model.flat).all()
+    assert after < before, (before, after)
