@@ -18,9 +18,11 @@ Modules
 ``adam``     the Adam update with per-group learning rates (float64).
 ``binning``  the integer tile-binning rule: (tile, depth) keys, stable sort,
              per-tile ranges (numpy, bit-exact).
+``quadtree`` the per-frame seeding: contrast quadtree over the RGB frame and
+             the back-projection of its leaf centres (Eq. 10).
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` to
 something other than itself (closed forms, Monte Carlo, finite differences,
 library routines, brute force).  No function is "parity unpinned".
 """
-from . import adam, binning, render, sh  # noqa: F401
+from . import adam, binning, quadtree, render, sh  # noqa: F401
