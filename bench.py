@@ -476,7 +476,8 @@ def run_streaming(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     abi.load()
     st = workloads.streaming(n_frames=args.frames)
-    opt = StreamingOptimizer(st.cam, 3, _stream_seed, iters=10, n_past=4, capacity=1 << 16, device=local_rank)
+    opt = StreamingOptimizer(st.cam, 3, _stream_seed if args.host_seeding else None, iters=10, n_past=4,
+                             capacity=1 << 16, device=local_rank, seeding=STREAM_SEEDING)
     clocks = ClockSampler(local_rank)
     clocks.start()
     launches0 = opt.ctx.stats()["kernel_launches"]
@@ -498,7 +499,8 @@ def run_streaming(args, rank, world, local_rank):
         "config": {"workload": f"streaming: {args.frames} frames at 1200x680 (fx 600), novelty seeding where "
                                "rendered alpha < 0.5, 10 batched iterations per frame over the frame and up to 4 "
                                "random earlier keyframes, SH degree 3, fp32",
-                   "frames": args.frames, "seeding": STREAM_SEEDING, "host_generation_s": t_gen,
+                   "frames": args.frames, "seeding": STREAM_SEEDING,
+                   "seeding_on": "host" if args.host_seeding else "device", "host_generation_s": t_gen,
                    "parallelism": f"replicas{world}", "timing": "CUDA events around each frame's iterations"},
         "stream": {
             "gaussians_first_frame": stats[0].n_gaussians, "gaussians_last_frame": stats[-1].n_gaussians,
@@ -643,6 +645,8 @@ def main():
     ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view", "streaming"],
                     help="multi_view: the batched 8-view iteration vs the same iteration view by view")
     ap.add_argument("--frames", type=int, default=40, help="streaming: frames of the sequence")
+    ap.add_argument("--host-seeding", action="store_true",
+                    help="streaming: seed new Gaussians with the host quadtree instead of gs_seed_quadtree")
     ap.add_argument("--global-epochs", type=int, default=2,
                     help="streaming: passes of the offline optimisation over the keyframe list afterwards")
     ap.add_argument("--no-compare", action="store_true",

@@ -402,6 +402,41 @@ gs_status gs_bin_tiles(gs_ctx *ctx, int64_t n, const float *mean2d, const float 
                        uint64_t *keys, uint32_t *ids, uint32_t *ranges, int64_t pair_capacity,
                        int64_t *n_pairs, gs_stream_t stream);
 
+/* Per-frame seeding of new Gaussians (Sec. III-B.2, Eq. 10) on the device.
+ * The frame rgb [3, H, W] (values in [0, 1]) is covered by a grid of square
+ * root cells of max_size px (clipped at the border); a cell splits into its
+ * four (clipped, non-empty) quadrants while the mean over the three channels
+ * of the per-channel pixel variance exceeds var_thr (0.01: the paper's
+ * contrast threshold 0.1 read as a standard deviation), its side exceeds
+ * min_size and it holds more than one pixel; cells that do not split are
+ * leaves.  max_size and min_size are powers of two, 1 <= min <= max <= 4096.
+ *
+ * gs_quadtree_leaves writes the leaves as int32 (x0, y0, w, h) rows to
+ * `leaves` (device [capacity, 4], in no particular order) and their number to
+ * *n_leaves (host); GS_ERR_CAPACITY if they do not fit.  Synchronises. */
+gs_status gs_quadtree_leaves(gs_ctx *ctx, const float *rgb, int32_t width, int32_t height, float var_thr,
+                             int32_t max_size, int32_t min_size, int32_t *leaves, int64_t capacity,
+                             int64_t *n_leaves, gs_stream_t stream);
+
+/* gs_seed_quadtree: the quadtree of the frame (size from cam), then one new
+ * Gaussian per leaf whose centre pixel (min(floor(x0 + w/2), W - 1),
+ * min(floor(y0 + h/2), H - 1)) has depth > 0 and, if alpha (the rendered
+ * alpha image [H, W] of the current map, nullable) is given, alpha <
+ * alpha_thr (the novelty rule, 0.5).  Eq. 10 back-projects the leaf centre u
+ * with that depth z: p_w = R^T (((u_x - cx) z / fx, (u_y - cy) z / fy, z) - t);
+ * log-scales log(sqrt(w^2 + h^2) / 2 * z / fx) on all axes, quaternion
+ * (1, 0, 0, 0), opacity logit 0, SH DC (c - 0.5) / Y_00 from the pixel colour
+ * c, higher bands 0.  The parameters go to rows [0, k) of the caller's arrays
+ * (device, each with `capacity` rows in the layout of gs_gaussians, e.g. the
+ * free slots of a map), in no particular order; *n_seeded (host) = k.  If
+ * k > capacity only `capacity` rows are written and GS_ERR_CAPACITY is
+ * returned with *n_seeded = k.  Synchronises (twice). */
+gs_status gs_seed_quadtree(gs_ctx *ctx, const float *rgb, const float *depth, const float *alpha, float alpha_thr,
+                           const gs_camera *cam, const gs_viewmat *view, int32_t sh_degree, float var_thr,
+                           int32_t max_size, int32_t min_size, float *means, float *log_scales, float *quats,
+                           float *opacity_logits, float *sh, int64_t capacity, int64_t *n_seeded,
+                           gs_stream_t stream);
+
 /* Copy the last forward pass's projected per-Gaussian quantities to caller
  * buffers (each nullable), n = views x Gaussians items, item v * N + i being
  * Gaussian i seen from view v: mean2d [n, 2] (high part of a double-float),

@@ -114,6 +114,11 @@ EXPORTS = {
     "gs_train_step_batched": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera),
                                         C.POINTER(gs_viewmat), C.POINTER(gs_raster_cfg), PP, PP, C.c_float,
                                         C.c_float, P, P, P, P, C.POINTER(gs_adam_cfg), C.c_int64, PP, PP, PP, P]),
+    "gs_quadtree_leaves": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, C.c_int32, C.c_int32, P, C.c_int64,
+                                     C.POINTER(C.c_int64), P]),
+    "gs_seed_quadtree": (C.c_int, [P, P, P, P, C.c_float, C.POINTER(gs_camera), C.POINTER(gs_viewmat), C.c_int32,
+                                   C.c_float, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int64,
+                                   C.POINTER(C.c_int64), P]),
     "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                               C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
@@ -445,3 +450,33 @@ def gs_train_step_batched(ctx, gaussians, cams, views, cfg, target_rgb, target_d
                                       _ptrs(color, "color", V), _ptrs(depth, "depth", V), _ptrs(alpha, "alpha", V),
                                       _stream(stream))
     _check(ctx, st, "gs_train_step_batched")
+
+
+def gs_quadtree_leaves(ctx, rgb, var_thr=0.01, max_size=64, min_size=1, leaves=None, stream=None) -> int:
+    """Quadtree leaves of rgb [3, H, W] into ``leaves`` (int32 [cap, 4]);
+    returns their number (-needed - 1 if ``leaves`` is too small)."""
+    H, W = rgb.shape[1], rgb.shape[2]
+    cap = 0 if leaves is None else leaves.shape[0]
+    n = C.c_int64(0)
+    st = load().gs_quadtree_leaves(ctx, _f32(rgb, "rgb"), int(W), int(H), float(var_thr), int(max_size), int(min_size),
+                                   _ptr(leaves), int(cap), C.byref(n), _stream(stream))
+    if st == 3:
+        return -int(n.value) - 1
+    _check(ctx, st, "gs_quadtree_leaves")
+    return int(n.value)
+
+
+def gs_seed_quadtree(ctx, rgb, depth, alpha, alpha_thr, cam: gs_camera, view: gs_viewmat, sh_degree, var_thr,
+                     max_size, min_size, means, log_scales, quats, opacity_logits, sh, capacity, stream=None) -> int:
+    """Seeds new Gaussians into the given rows; returns how many (-needed - 1
+    if more than ``capacity``)."""
+    n = C.c_int64(0)
+    st = load().gs_seed_quadtree(ctx, _f32(rgb, "rgb"), _f32(depth, "depth"), _f32(alpha, "alpha"), float(alpha_thr),
+                                 C.byref(cam), C.byref(view), int(sh_degree), float(var_thr), int(max_size),
+                                 int(min_size), _f32(means, "means"), _f32(log_scales, "log_scales"),
+                                 _f32(quats, "quats"), _f32(opacity_logits, "opacity_logits"), _f32(sh, "sh"),
+                                 int(capacity), C.byref(n), _stream(stream))
+    if st == 3:
+        return -int(n.value) - 1
+    _check(ctx, st, "gs_seed_quadtree")
+    return int(n.value)

@@ -59,6 +59,11 @@ struct gs_ctx {
   float* dl_img = nullptr;    // per pixel: dL/dcolor (3 planes) and the depth residual sign (fused loss)
   float* tile_loss = nullptr;  // per (tile, 8 x 8 block): fused-loss partial sums (3 floats)
   float* d_dscale = nullptr;   // per view: depth-gradient scale of the fused loss
+  // per-frame seeding scratch
+  int64_t cap_qt = 0;
+  int2* qt_cells[2] = {nullptr, nullptr};
+  int4* qt_leaves = nullptr;
+  uint32_t* qt_counters = nullptr;
   int64_t cap_tune = 0;
   // device scalars and their host mirror
   uint32_t* d_npairs = nullptr;
@@ -531,6 +536,10 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->dl_img);
   cudaFree(c->tile_loss);
   cudaFree(c->d_dscale);
+  cudaFree(c->qt_cells[0]);
+  cudaFree(c->qt_cells[1]);
+  cudaFree(c->qt_leaves);
+  cudaFree(c->qt_counters);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
   cudaFree(c->d_overflow);
@@ -1277,6 +1286,98 @@ gs_status gs_autotune(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const g
   if (st != GS_OK) return st;
   cfg->tile_w = kShapes[best_k][0];
   cfg->tile_h = kShapes[best_k][1];
+  return GS_OK;
+}
+
+namespace {
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+gs_status qt_prepare(gs_ctx* c, int W, int H, int max_size, int min_size, float var_thr) {
+  if (W < 1 || H < 1 || (int64_t)W * H > ((int64_t)1 << 30))
+    return fail(c, GS_ERR_INVALID_ARG, "quadtree: image size out of range");
+  if (!pow2(max_size) || !pow2(min_size) || min_size > max_size || max_size > 4096)
+    return fail(c, GS_ERR_INVALID_ARG, "quadtree: cell sizes must be powers of two, 1 <= min <= max <= 4096");
+  if (!std::isfinite(var_thr) || var_thr < 0.f) return fail(c, GS_ERR_INVALID_ARG, "quadtree: bad threshold");
+  const int64_t need = quadtree_scratch_cells(W, H);
+  if (need > c->cap_qt) {
+    GS_CUDA(c, cudaDeviceSynchronize());
+    GS_CUDA(c, regrow(&c->qt_cells[0], need));
+    GS_CUDA(c, regrow(&c->qt_cells[1], need));
+    GS_CUDA(c, regrow(&c->qt_leaves, need));
+    if (!c->qt_counters) GS_CUDA(c, cudaMalloc((void**)&c->qt_counters, 32 * sizeof(uint32_t)));
+    c->cap_qt = need;
+  }
+  return GS_OK;
+}
+
+// quadtree over rgb [3, H, W]; returns the leaf count (host) after one synchronisation
+gs_status qt_run(gs_ctx* c, const float* rgb, int W, int H, int max_size, int min_size, float var_thr,
+                 uint32_t* n_leaves, cudaStream_t s) {
+  gs_status st = qt_prepare(c, W, H, max_size, min_size, var_thr);
+  if (st != GS_OK) return st;
+  c->launches += launch_quadtree(rgb, W, H, max_size, min_size, (double)var_thr, c->qt_cells[0], c->qt_cells[1],
+                                 c->qt_counters, c->qt_leaves, s);
+  GS_CHECK_LAUNCH(c, "quadtree");
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->qt_counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  *n_leaves = (uint32_t)(c->h_pinned[0] & 0xFFFFFFFFull);
+  return GS_OK;
+}
+
+}  // namespace
+
+gs_status gs_quadtree_leaves(gs_ctx* c, const float* rgb, int32_t width, int32_t height, float var_thr,
+                             int32_t max_size, int32_t min_size, int32_t* leaves, int64_t capacity, int64_t* n_leaves,
+                             gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!rgb || !n_leaves || capacity < 0) return fail(c, GS_ERR_INVALID_ARG, "gs_quadtree_leaves: bad arguments");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t nl = 0;
+  gs_status st = qt_run(c, rgb, width, height, max_size, min_size, var_thr, &nl, s);
+  if (st != GS_OK) return st;
+  *n_leaves = nl;
+  if ((int64_t)nl > capacity) return fail(c, GS_ERR_CAPACITY, "gs_quadtree_leaves: output capacity too small");
+  if (nl > 0) {
+    if (!leaves) return fail(c, GS_ERR_INVALID_ARG, "gs_quadtree_leaves: NULL output");
+    GS_CUDA(c, cudaMemcpyAsync(leaves, c->qt_leaves, sizeof(int4) * nl, cudaMemcpyDeviceToDevice, s));
+  }
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  return GS_OK;
+}
+
+gs_status gs_seed_quadtree(gs_ctx* c, const float* rgb, const float* depth, const float* alpha, float alpha_thr,
+                           const gs_camera* cam, const gs_viewmat* view, int32_t sh_degree, float var_thr,
+                           int32_t max_size, int32_t min_size, float* means, float* log_scales, float* quats,
+                           float* opacity_logits, float* sh, int64_t capacity, int64_t* n_seeded,
+                           gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_cam(c, cam)) != GS_OK) return st;
+  if (!view || !rgb || !depth || !n_seeded || capacity < 0 || sh_degree < 0 || sh_degree > 3)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_seed_quadtree: bad arguments");
+  if (capacity > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
+    return fail(c, GS_ERR_INVALID_ARG, "gs_seed_quadtree: NULL output array");
+  if (capacity > 0xFFFFFFF0ll) return fail(c, GS_ERR_INVALID_ARG, "gs_seed_quadtree: capacity too large");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t nl = 0;
+  if ((st = qt_run(c, rgb, cam->width, cam->height, max_size, min_size, var_thr, &nl, s)) != GS_OK) return st;
+  const double K4[4] = {cam->fx, cam->fy, cam->cx, cam->cy};
+  double R[9], t[3];
+  for (int k = 0; k < 9; ++k) R[k] = view->R[k];
+  for (int k = 0; k < 3; ++k) t[k] = view->t[k];
+  uint32_t* n_dev = c->qt_counters + 24;
+  launch_seed(rgb, depth, alpha, alpha_thr, cam->width, cam->height, K4, R, t, sh_degree, c->qt_leaves, nl, means,
+              log_scales, quats, opacity_logits, sh, (uint32_t)capacity, n_dev, s);
+  if (nl > 0) c->launches += 1;
+  GS_CHECK_LAUNCH(c, "seed");
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, n_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  const int64_t n = (int64_t)(c->h_pinned[0] & 0xFFFFFFFFull);
+  *n_seeded = n;
+  if (n > capacity) return fail(c, GS_ERR_CAPACITY, "gs_seed_quadtree: more new Gaussians than capacity");
   return GS_OK;
 }
 

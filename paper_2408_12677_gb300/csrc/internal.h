@@ -217,6 +217,17 @@ void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh
                  float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero_grads,
                  const long long* step_dev, cudaStream_t s);
 
+// per-frame seeding (quadtree + Eq. 10); counters: >= levels + 2 words;
+// cells_a / cells_b / leaves: quadtree_scratch_cells(W, H) entries each
+int64_t quadtree_scratch_cells(int W, int H);
+int launch_quadtree(const float* rgb, int W, int H, int max_size, int min_size, double var_thr, int2* cells_a,
+                    int2* cells_b, uint32_t* counters, int4* leaves, cudaStream_t s);
+// K4 = (fx, fy, cx, cy); R, t world-to-camera
+void launch_seed(const float* rgb, const float* depth, const float* alpha, float alpha_thr, int W, int H,
+                 const double K4[4], const double R[9], const double t[3], int sh_degree, const int4* leaves,
+                 uint32_t n_leaves, float* means, float* log_scales, float* quats, float* logits, float* sh,
+                 uint32_t capacity, uint32_t* n_seeded, cudaStream_t s);
+
 // debug/introspection
 void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, float* mean2d, float* cov2d,
                               float* depth, float* rgb, float* opacity, int32_t* tiles_out, cudaStream_t s);

@@ -3,9 +3,10 @@ path (Sec. III-B.2-3).  For every incoming RGB-D frame:
 
 1. render the current map at the frame's pose (gs_render_fwd) and read the
    alpha image back;
-2. seed new Gaussians only where the map does not cover the frame yet: the
-   caller's quadtree seeding function receives the mask alpha < 0.5 (the
-   novelty rule; the paper tests the TSDF voxel weight instead, Sec. III-B.2);
+2. seed new Gaussians only where the map does not cover the frame yet
+   (rendered alpha < 0.5 at the leaf centre: the novelty rule; the paper tests
+   the TSDF voxel weight instead, Sec. III-B.2), on the device
+   (gs_seed_quadtree) or through a host seeding function;
 3. append them to the map (capacity-doubling buffers, Adam moments of the
    new Gaussians zero);
 4. keep the frame as a keyframe when it added more than 50 Gaussians
@@ -146,12 +147,16 @@ class FrameStats:
 class StreamingOptimizer:
     """The per-frame loop over one camera model (all frames share it)."""
 
-    def __init__(self, cam, sh_degree: int, seed_fn, iters: int = 10, n_past: int = 4, capacity: int = 1 << 16,
+    def __init__(self, cam, sh_degree: int, seed_fn=None, iters: int = 10, n_past: int = 4, capacity: int = 1 << 16,
                  raster_cfg=None, adam_cfg=None, w_color: float = 0.8, w_depth: float = 0.2, rng_seed: int = 0,
-                 device: int = 0, ctx: Context | None = None):
+                 device: int = 0, ctx: Context | None = None, seeding=None):
+        """``seed_fn(rgb, depth, cam, pose, mask) -> params`` seeds on the host;
+        without it the frame is seeded on the device (gs_seed_quadtree) with
+        ``seeding`` = dict(var_thr, max_size, min_size)."""
         self.cam = cam
         self.cam_s = camera_struct(cam)
         self.seed_fn = seed_fn
+        self.seeding = {"var_thr": 0.01, "max_size": 64, "min_size": 1, **(seeding or {})}
         self.iters, self.n_past = int(iters), int(n_past)
         self.map = GrowingMap(sh_degree, capacity, device)
         self.ctx = ctx or Context(device)
@@ -189,17 +194,41 @@ class StreamingOptimizer:
                                   [k.rgb for k in views], [k.depth for k in views], self.w_color, self.w_depth,
                                   self.loss, m.flat, m.m, m.v, self.acfg, self.step)
 
+    def seed_on_device(self, cur: "Keyframe") -> int:
+        """Novelty seeding of the frame on the device (gs_seed_quadtree) into
+        the map's free slots, growing the map when they do not suffice."""
+        h = self.ctx.handle
+        alpha = None
+        if self.map.n > 0:
+            abi.gs_render_fwd(h, self.map.model.gaussians(), self.cam_s, cur.view, self.rcfg, None, None,
+                              self.alpha[0])
+            alpha = self.alpha[0]
+        sp = self.seeding
+        for _ in range(2):
+            m, n = self.map.model, self.map.n
+            k = abi.gs_seed_quadtree(h, cur.rgb, cur.depth, alpha, NOVELTY_ALPHA, self.cam_s, cur.view,
+                                     self.map.sh_degree, sp["var_thr"], sp["max_size"], sp["min_size"],
+                                     m.p["means"][n:], m.p["log_scales"][n:], m.p["quats"][n:],
+                                     m.p["opacity_logits"][n:], m.p["sh"][n:], m.n - n)
+            if k >= 0:
+                self.map.n += k
+                return k
+            self.map._grow(n - k - 1)  # -k - 1 = the number of new Gaussians
+        raise RuntimeError("seeding did not fit after growing the map")
+
     def process_frame(self, rgb: np.ndarray, depth: np.ndarray, pose) -> FrameStats:
         """rgb [H, W, 3] in [0, 1], depth [H, W] (0 = invalid), pose: world-to-camera (R, t)."""
         t0 = time.perf_counter()
         view = abi.make_viewmat(pose.R, pose.t)
-        alpha = self.render_alpha(view)
-        new = self.seed_fn(rgb, depth, self.cam, pose, novelty_mask(alpha))
-        k = self.map.append(new)
         dev = self.map.model.flat.device
         cur = Keyframe(self.cam, view, torch.as_tensor(np.ascontiguousarray(np.transpose(rgb, (2, 0, 1)), np.float32),
                                                         device=dev),
                        torch.as_tensor(np.ascontiguousarray(depth, np.float32), device=dev))
+        if self.seed_fn is None:
+            k = self.seed_on_device(cur)
+        else:
+            alpha = self.render_alpha(view)
+            k = self.map.append(self.seed_fn(rgb, depth, self.cam, pose, novelty_mask(alpha)))
         is_key = k > KEYFRAME_MIN_NEW or not self.keyframes
         if is_key:
             self.keyframes.append(cur)
