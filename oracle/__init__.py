@@ -20,9 +20,11 @@ Modules
              per-tile ranges (numpy, bit-exact).
 ``quadtree`` the per-frame seeding: contrast quadtree over the RGB frame and
              the back-projection of its leaf centres (Eq. 10).
+``tsdf``     the TSDF fusion (Eq. 6-9) over 8^3-voxel blocks and the
+             voxel-weight novelty check of the seeding.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py`` to
 something other than itself (closed forms, Monte Carlo, finite differences,
 library routines, brute force).  No function is "parity unpinned".
 """
-from . import adam, binning, quadtree, render, sh  # noqa: F401
+from . import adam, binning, quadtree, render, sh, tsdf  # noqa: F401
