@@ -437,6 +437,7 @@ def run_multi_view(args, rank, world, local_rank):
 
 
 STREAM_SEEDING = {"var_thr": 0.035, "min_size": 2}  # about 50k Gaussians from the first 1200x680 frame
+PAPER_SEEDING = {"var_thr": 0.01, "max_size": 64, "min_size": 1}  # quadtree threshold 0.1 (as a std), 1 px leaves
 
 
 def _stream_frame(args):
@@ -452,14 +453,14 @@ def _stream_seed(rgb, depth, cam, pose, mask):
 
 
 def run_streaming(args, rank, world, local_rank):
-    """Per-frame streaming optimisation at 1200x680: each frame seeds
-    Gaussians where the map's rendered alpha is below 0.5, then 10 batched
-    iterations over the frame and up to 4 random earlier keyframes.  The
-    frames are ray-cast on the host cores before the GPU starts (a spawn
+    """Per-frame streaming optimisation at 1200x680: each frame is fused into
+    the TSDF grid and seeds Gaussians where the voxel weight is 1 (or, with
+    --novelty alpha, where the map's rendered alpha is below 0.5), then 10
+    batched iterations over the frame and up to 4 random earlier keyframes.
+    The frames are ray-cast on the host cores before the GPU starts (a spawn
     process pool); value = optimisation iterations per second of GPU time
     (CUDA events around each frame's iterations), e2e = frames per second of
-    the whole loop (render for the novelty mask, host seeding, upload,
-    iterations)."""
+    the whole loop (fusion, seeding, uploads, iterations)."""
     import multiprocessing as mp
 
     t_gen = time.perf_counter()
@@ -476,8 +477,10 @@ def run_streaming(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     abi.load()
     st = workloads.streaming(n_frames=args.frames)
+    novelty = "alpha" if args.host_seeding else args.novelty
+    seeding = STREAM_SEEDING if novelty == "alpha" else PAPER_SEEDING
     opt = StreamingOptimizer(st.cam, 3, _stream_seed if args.host_seeding else None, iters=10, n_past=4,
-                             capacity=1 << 16, device=local_rank, seeding=STREAM_SEEDING)
+                             capacity=1 << 16, device=local_rank, seeding=seeding, novelty=novelty)
     clocks = ClockSampler(local_rank)
     clocks.start()
     launches0 = opt.ctx.stats()["kernel_launches"]
@@ -491,15 +494,19 @@ def run_streaming(args, rank, world, local_rank):
     gpu_ms = sum(s.gpu_ms for s in stats)
     iters = sum(len(s.views_per_iter) for s in stats)
     views = sum(sum(s.views_per_iter) for s in stats)
-    gpu_ms, wall = max_over_ranks([gpu_ms, wall], world)
+    tsdf_ms = sum(s.tsdf_ms for s in stats)
+    tsdf_updated = sum(s.tsdf_updated for s in stats)
+    gpu_ms, wall, tsdf_ms = max_over_ranks([gpu_ms, wall, tsdf_ms], world)
     return {
         "metric": METRIC, "value": world * iters / (gpu_ms * 1e-3), "unit": "it/s", "n_gpus": world,
         "steps": iters, "warmup": 0, "ms_per_step": gpu_ms / iters, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"streaming: {args.frames} frames at 1200x680 (fx 600), novelty seeding where "
-                               "rendered alpha < 0.5, 10 batched iterations per frame over the frame and up to 4 "
+        "config": {"workload": f"streaming: {args.frames} frames at 1200x680 (fx 600), "
+                               + ("TSDF fusion (1 cm voxels, eps 8 cm) and seeding where the voxel weight is 1"
+                                  if novelty == "tsdf" else "novelty seeding where rendered alpha < 0.5")
+                               + ", 10 batched iterations per frame over the frame and up to 4 "
                                "random earlier keyframes, SH degree 3, fp32",
-                   "frames": args.frames, "seeding": STREAM_SEEDING,
+                   "frames": args.frames, "seeding": seeding, "novelty": novelty,
                    "seeding_on": "host" if args.host_seeding else "device", "host_generation_s": t_gen,
                    "parallelism": f"replicas{world}", "timing": "CUDA events around each frame's iterations"},
         "stream": {
@@ -508,6 +515,14 @@ def run_streaming(args, rank, world, local_rank):
             "views_per_iteration_mean": views / iters, "gpu_ms_per_frame": gpu_ms / len(stats),
             "host_ms_per_frame": 1e3 * wall / len(stats), "loss_first": stats[0].loss, "loss_last": stats[-1].loss,
             "new_per_frame": [s.new_gaussians for s in stats],
+        },
+        # TSDF fusion (allocation + integration kernels, CUDA events): algorithmic bytes = 16 per updated
+        # voxel (float2 read + write) + 4 per depth pixel
+        "tsdf": None if novelty != "tsdf" else {
+            "ms_per_frame": tsdf_ms / len(stats), "blocks_last": stats[-1].tsdf_blocks,
+            "touched_per_frame": sum(s.tsdf_touched for s in stats) / len(stats),
+            "updated_voxels_per_frame": tsdf_updated / len(stats),
+            "achieved_gbs": (16 * tsdf_updated + 4 * st.cam.width * st.cam.height * len(stats)) / (tsdf_ms * 1e6),
         },
         # e2e step = one frame: its RGB-D upload, the alpha read-back for the novelty mask, the new
         # Gaussians' upload and one loss read
@@ -522,7 +537,7 @@ def run_streaming(args, rank, world, local_rank):
         "e2e": {"value": world * len(stats) / wall, "unit": "frames/s",
                 "h2d_bytes_per_step": 16 * st.cam.width * st.cam.height
                 + int(sum(s.new_gaussians for s in stats) / len(stats)) * 4 * (11 + 48),
-                "d2h_bytes_per_step": 4 * st.cam.width * st.cam.height + 4},
+                "d2h_bytes_per_step": (4 * st.cam.width * st.cam.height if novelty == "alpha" else 16 + 4) + 4 + 4},
         "gpu_launches": launches,
         "clocks": clk,
     }
@@ -645,6 +660,8 @@ def main():
     ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view", "streaming"],
                     help="multi_view: the batched 8-view iteration vs the same iteration view by view")
     ap.add_argument("--frames", type=int, default=40, help="streaming: frames of the sequence")
+    ap.add_argument("--novelty", choices=("tsdf", "alpha"), default="tsdf",
+                    help="streaming: seed where the TSDF voxel weight is 1 (the paper) or where rendered alpha < 0.5")
     ap.add_argument("--host-seeding", action="store_true",
                     help="streaming: seed new Gaussians with the host quadtree instead of gs_seed_quadtree")
     ap.add_argument("--global-epochs", type=int, default=2,

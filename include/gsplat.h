@@ -423,7 +423,8 @@ gs_status gs_quadtree_leaves(gs_ctx *ctx, const float *rgb, int32_t width, int32
  * min(floor(y0 + h/2), H - 1)) has depth > 0 and, if alpha (the rendered
  * alpha image [H, W] of the current map, nullable) is given, alpha <
  * alpha_thr (the novelty rule, 0.5).  Eq. 10 back-projects the leaf centre u
- * with that depth z: p_w = R^T (((u_x - cx) z / fx, (u_y - cy) z / fy, z) - t);
+ * with that depth z: p_w = R^T (((u_x - cx) z / fx, (u_y - cy) z / fy, z) - t)
+ * (float32, evaluated left to right, R^T's products summed in row order);
  * log-scales log(sqrt(w^2 + h^2) / 2 * z / fx) on all axes, quaternion
  * (1, 0, 0, 0), opacity logit 0, SH DC (c - 0.5) / Y_00 from the pixel colour
  * c, higher bands 0.  The parameters go to rows [0, k) of the caller's arrays
@@ -436,6 +437,94 @@ gs_status gs_seed_quadtree(gs_ctx *ctx, const float *rgb, const float *depth, co
                            int32_t max_size, int32_t min_size, float *means, float *log_scales, float *quats,
                            float *opacity_logits, float *sh, int64_t capacity, int64_t *n_seeded,
                            gs_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * TSDF fusion (Sec. III-B.1, Eq. 6-9) and the voxel-weight novelty check of
+ * the per-frame seeding (Sec. III-B.2).
+ *
+ * The grid is single resolution: voxels of side voxel_size in blocks of 8^3,
+ * found through an open-addressing hash table of table_size buckets over a
+ * pool of `capacity` block slots.  Every array is device memory owned by the
+ * caller and set once before the first call: keys all 0xFF bytes (free
+ * buckets), stamps 0, voxels 0, claims all 0xFF bytes, counters 0; slots and
+ * touched need no initial value.  Block (bx, by, bz), each coordinate in
+ * [-2^20, 2^20), has the key ((bx + 2^20) << 42) | ((by + 2^20) << 21) |
+ * (bz + 2^20); voxel (x, y, z) of the block (0..7 each) holds its tsdf and
+ * weight at voxels[2 (512 slot + x + 8 y + 64 z)] and [... + 1], and its
+ * centre is at (8 b + (x, y, z) + 0.5) voxel_size in the world frame.
+ * ------------------------------------------------------------------------- */
+#define GS_TSDF_BLOCK 8
+#define GS_TSDF_MAX_SAMPLES 16
+
+typedef struct {
+  uint64_t *keys;     /* [table_size] block keys; all-ones = free */
+  int32_t *slots;     /* [table_size] pool slot of each bucket's block */
+  uint32_t *stamps;   /* [table_size] id of the last frame that touched the bucket */
+  float *voxels;      /* [capacity, 512, 2] (tsdf, weight) */
+  uint32_t *claims;   /* [capacity, 512] seeding scratch, all 0xFFFFFFFF between calls */
+  uint32_t *touched;  /* [table_size / 2] buckets touched by the last allocation */
+  uint32_t *counters; /* [4]: slots handed out (may exceed capacity), buckets touched by the
+                         last allocation, failed inserts, voxels updated (accumulates) */
+  int64_t table_size; /* power of two in [2, 2^32] */
+  int64_t capacity;   /* pool slots in [1, 2^31 - 1] */
+  float voxel_size;   /* s (metres) */
+  float truncation;   /* eps (metres); at most GS_TSDF_MAX_SAMPLES band samples: eps <= 30 s */
+  float max_weight;   /* w_max >= 1 (Eq. 8) */
+  int32_t fusion;     /* 0: Eq. 9 as printed, the new tsdf weighted by w_k;
+                         1: weighted by 1 (KinectFusion's running average) */
+} gs_tsdf_grid;
+
+/* gs_tsdf_integrate: fuse the depth image [H, W] (camera z in metres, <= 0 =
+ * no measurement; size from cam) seen with the world-to-camera pose `view`.
+ * Allocation: the ray through every pixel centre (i + 0.5, j + 0.5) with
+ * depth D > 0 is sampled at camera depths D - eps + k 2 eps / n, k = 0..n,
+ * n = ceil(eps / 2s) (samples at z <= 0 dropped); each block holding a sample
+ * is inserted (a new key takes the next slot, counters[0]++) and listed once
+ * in `touched` (stamps[bucket] = frame).  Integration (Eq. 6-9), for every
+ * voxel of the touched blocks: p_c = R p_v + t; skipped if z <= 0, if the
+ * projection (fx x/z + cx, fy y/z + cy) is outside the image, if the depth
+ * at its pixel (floor of the projection) is not > 0, or if sdf = D - z <
+ * -eps; otherwise tsdf = clamp(sdf / eps, -1, 1), w_k = min(w_max, w_{k-1} +
+ * 1) and the average of `fusion`.  The block, pixel and update decisions are
+ * float32 with correctly rounded operations in the order written here.
+ * `frame` (>= 1) must differ from the previous call's.  The table must have
+ * room: with table_size >= 2 (blocks + W H (n + 1)) no insert can fail;
+ * failures are counted in counters[2] and their blocks skipped.  Blocks whose
+ * slot is >= capacity are skipped too: after the caller grows the pool,
+ * min_slot = the old capacity re-runs only the integration, over the last
+ * touched list, for the slots >= min_slot (same depth, camera and pose).
+ * min_slot = 0 runs both steps.  Asynchronous; gs_tsdf_counters reads the
+ * counters. */
+gs_status gs_tsdf_integrate(gs_ctx *ctx, const gs_tsdf_grid *grid, const float *depth, const gs_camera *cam,
+                            const gs_viewmat *view, uint32_t frame, int64_t min_slot, gs_stream_t stream);
+
+/* Synchronise the stream and copy the 4 counters to out (host).  Returns
+ * GS_ERR_CAPACITY if counters[0] > capacity (grow the pool, then
+ * gs_tsdf_integrate with min_slot) or counters[2] > 0 (table too small). */
+gs_status gs_tsdf_counters(gs_ctx *ctx, const gs_tsdf_grid *grid, int64_t *out, gs_stream_t stream);
+
+/* Insert every key of `from` into `to` (same pool: the slot of each key is
+ * kept; to's keys all free, to.table_size a power of two > from's count of
+ * keys).  Between frames only: the touched list refers to buckets of `from`. */
+gs_status gs_tsdf_rehash(gs_ctx *ctx, const gs_tsdf_grid *from, const gs_tsdf_grid *to, gs_stream_t stream);
+
+/* tsdf[i], weight[i] (each nullable) of the voxel holding world point
+ * points[i] (float [n, 3]; voxel floor(p / s), float32 division), 0 and 0 where its
+ * block is not allocated. */
+gs_status gs_tsdf_query(gs_ctx *ctx, const gs_tsdf_grid *grid, const float *points, int64_t n, float *tsdf,
+                        float *weight, gs_stream_t stream);
+
+/* gs_seed_tsdf: gs_seed_quadtree with the paper's novelty check instead of
+ * the rendered alpha.  After gs_tsdf_integrate of this frame, a leaf seeds
+ * iff the voxel holding its Eq. 10 point (p_w in float32, correctly rounded
+ * operations in the order of gs_seed_quadtree's formula, voxel floor(p_w /
+ * s) with a float32 division) has weight exactly 1, and at most one leaf
+ * seeds each voxel: the one with the smallest y0 W + x0.  Means are that
+ * p_w; the other parameters as in gs_seed_quadtree.  Synchronises (twice). */
+gs_status gs_seed_tsdf(gs_ctx *ctx, const float *rgb, const float *depth, const gs_tsdf_grid *grid,
+                       const gs_camera *cam, const gs_viewmat *view, int32_t sh_degree, float var_thr,
+                       int32_t max_size, int32_t min_size, float *means, float *log_scales, float *quats,
+                       float *opacity_logits, float *sh, int64_t capacity, int64_t *n_seeded, gs_stream_t stream);
 
 /* Copy the last forward pass's projected per-Gaussian quantities to caller
  * buffers (each nullable), n = views x Gaussians items, item v * N + i being

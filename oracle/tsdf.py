@@ -11,12 +11,13 @@ tsdf and weight of its voxels as float64 arrays indexed [z, y, x].  Voxel
 
 Definition followed, with the readings where the paper is silent:
 
-* Allocation (Sec. III-B.1): for every pixel (i, j) with depth D > 0, the ray
-  through the pixel centre (i + 0.5, j + 0.5) is sampled at the camera depths
-  z_k = D + c_k, c_k = -eps + k (2 eps / n), k = 0..n, n = ceil(eps / (2 s))
-  (sample spacing at most half a block along the depth; samples with z <= 0
-  are dropped); every block holding a sample is allocated and is "touched"
-  by the frame.  Only touched blocks are integrated.
+* Allocation (Sec. III-B.1): for every pixel (i, j) with a finite depth
+  D > 0, the ray through the pixel centre (i + 0.5, j + 0.5) is sampled at
+  the camera depths z_k = D + c_k, c_k = -eps + k (2 eps / n), k = 0..n,
+  n = ceil(eps / (2 s)) (sample spacing at most half a block along the
+  depth; samples with z <= 0 are dropped); every block holding a sample
+  (block coordinates in [-2^20, 2^20)) is allocated and is "touched" by the
+  frame.  Only touched blocks are integrated.
 * Integration (Eq. 6-9), for every voxel of a touched block: camera point
   p_c = R p_v + t of its centre (world-to-camera pose R, t); skipped if
   z <= 0, if pi(p_c) = (fx x/z + cx, fy y/z + cy) falls outside the image,
@@ -29,10 +30,11 @@ Definition followed, with the readings where the paper is silent:
   ``fusion="unit"`` instead weights the new measurement by 1, as in
   KinectFusion: (tsdf_{k-1} w_{k-1} + tsdf) / (w_{k-1} + 1).
 * The integer decisions (which block a sample falls in, which pixel a voxel
-  projects to, whether it is updated) are taken in float32 with a fixed order
-  of correctly rounded operations, the precision of the kernels: the same
-  decisions on both sides.  The tsdf values are float64.
-* Novelty (Sec. III-B.2): a quadtree leaf whose Eq. 10 point p_q (float64,
+  projects to, whether it is updated, which voxel p_q falls in) are taken in
+  float32 with a fixed order of correctly rounded operations, the precision
+  of the kernels: the same decisions on both sides.  The tsdf values are
+  float64.
+* Novelty (Sec. III-B.2): a quadtree leaf whose Eq. 10 point p_q (float32,
   fixed operation order) lies in a voxel of weight exactly 1 after this
   frame's integration is new; a voxel of a block that is not allocated
   counts as weight 0 (not new).  A voxel holds at most one Gaussian
@@ -73,8 +75,9 @@ def allocate(depth: np.ndarray, cam, R_cw, t_cw, voxel_size: float, eps: float) 
     R, t = _f32_pose(R_cw, t_cw)
     fx, fy, cx, cy = (F32(cam.fx), F32(cam.fy), F32(cam.cx), F32(cam.cy))
     bs = F32(F32(BLOCK) * F32(voxel_size))
-    jj, ii = np.nonzero(np.asarray(depth, F32) > F32(0))
-    D = np.asarray(depth, F32)[jj, ii]
+    dep = np.asarray(depth, F32)
+    jj, ii = np.nonzero((dep > F32(0)) & np.isfinite(dep))
+    D = dep[jj, ii]
     xn = ((ii.astype(F32) + F32(0.5)) - cx) / fx
     yn = ((jj.astype(F32) + F32(0.5)) - cy) / fy
     out = set()
@@ -84,10 +87,13 @@ def allocate(depth: np.ndarray, cam, R_cw, t_cw, voxel_size: float, eps: float) 
         pc = (xn[ok] * z[ok], yn[ok] * z[ok], z[ok])
         d = [pc[r] - t[r] for r in range(3)]
         blk = []
+        inside = np.ones(d[0].shape, bool)
         for a in range(3):
             pw = (R[0, a] * d[0] + R[1, a] * d[1]) + R[2, a] * d[2]
-            blk.append(np.floor(pw / bs).astype(np.int64))
-        out.update(zip(blk[0].tolist(), blk[1].tolist(), blk[2].tolist()))
+            f = np.floor(pw / bs)
+            inside &= np.abs(f) < 2 ** 20  # block coordinates in [-2^20, 2^20)
+            blk.append(np.where(inside, f, 0).astype(np.int64))
+        out.update(zip(blk[0][inside].tolist(), blk[1][inside].tolist(), blk[2][inside].tolist()))
     return out
 
 
@@ -157,23 +163,24 @@ def integrate(grid: dict, depth, cam, R_cw, t_cw, voxel_size: float = 0.01, eps:
 
 
 def leaf_points(depth, lv, cam, R_cw, t_cw):
-    """Eq. 10 world points (float64, fixed operation order) of the leaves with
-    depth > 0 at their centre pixel; returns (indices into lv, points [k, 3])."""
+    """Eq. 10 world points of the leaves with depth > 0 at their centre pixel,
+    in float32 with a fixed order of correctly rounded operations (the
+    precision the novelty decision is taken in); returns (indices into lv,
+    points [k, 3] as float64 holding the float32 values)."""
     H, W = depth.shape
     R, t = _f32_pose(R_cw, t_cw)
-    R64, t64 = R.astype(np.float64), t.astype(np.float64)
-    fx, fy, cx, cy = (float(F32(cam.fx)), float(F32(cam.fy)), float(F32(cam.cx)), float(F32(cam.cy)))
+    fx, fy, cx, cy = (F32(cam.fx), F32(cam.fy), F32(cam.cx), F32(cam.cy))
     idx, pts = [], []
     for n, (x0, y0, w, h) in enumerate(np.asarray(lv, np.int64)):
-        ux, uy = x0 + w / 2.0, y0 + h / 2.0
+        ux, uy = F32(x0 + w / 2.0), F32(y0 + h / 2.0)  # exact
         pi, pj = min(int(np.floor(ux)), W - 1), min(int(np.floor(uy)), H - 1)
-        z = float(F32(depth[pj, pi]))
-        if not z > 0.0:
+        z = F32(depth[pj, pi])
+        if not z > 0:
             continue
-        q = [((ux - cx) * z) / fx - t64[0], ((uy - cy) * z) / fy - t64[1], z - t64[2]]
-        pts.append([(R64[0, a] * q[0] + R64[1, a] * q[1]) + R64[2, a] * q[2] for a in range(3)])
+        q = [((ux - cx) * z) / fx - t[0], ((uy - cy) * z) / fy - t[1], z - t[2]]
+        pts.append([(R[0, a] * q[0] + R[1, a] * q[1]) + R[2, a] * q[2] for a in range(3)])
         idx.append(n)
-    return np.array(idx, np.int64), np.array(pts, np.float64).reshape(-1, 3)
+    return np.array(idx, np.int64), np.array(pts, np.float32).astype(np.float64).reshape(-1, 3)
 
 
 def voxel_weight(grid: dict, vox) -> float:
@@ -191,10 +198,10 @@ def novel_leaves(grid: dict, depth, lv, cam, R_cw, t_cw, voxel_size: float = 0.0
     of weight 1, at most one (smallest y0 W + x0) per voxel."""
     W = depth.shape[1]
     idx, pts = leaf_points(depth, lv, cam, R_cw, t_cw)
-    s = float(F32(voxel_size))
+    s = F32(voxel_size)
     best = {}
-    for n, p in zip(idx.tolist(), pts):
-        vox = tuple(int(np.floor(c / s)) for c in p)
+    for n, p in zip(idx.tolist(), pts.astype(np.float32)):
+        vox = tuple(int(np.floor(c / s)) for c in p)  # float32 division
         if voxel_weight(grid, vox) != 1.0:
             continue
         key = int(lv[n][1]) * W + int(lv[n][0])
@@ -209,4 +216,10 @@ def seed_tsdf(rgb, depth, grid: dict, cam, R_cw, t_cw, sh_degree: int, var_thr: 
     then Eq. 10 for the leaves that seed."""
     lv = _qt.leaves(np.asarray(rgb, np.float64), var_thr, max_size, min_size)
     sel = novel_leaves(grid, depth, lv, cam, R_cw, t_cw, voxel_size)
-    return _qt.seed(rgb, depth, lv[sel], cam, np.asarray(R_cw, np.float64), np.asarray(t_cw, np.float64), sh_degree)
+    out = _qt.seed(rgb, depth, lv[sel], cam, np.asarray(R_cw, np.float64), np.asarray(t_cw, np.float64), sh_degree)
+    # the means are the float32 points whose voxels were checked (Eq. 10's
+    # float64 value rounded through the float32 operations)
+    idx, pts = leaf_points(depth, lv[sel], cam, R_cw, t_cw)
+    assert len(idx) == len(sel)
+    out["means"] = pts
+    return out

@@ -66,6 +66,13 @@ class gs_stats(C.Structure):
                 ("n_tiles", C.c_int64), ("evals_blended", C.c_int64), ("evals_tiled", C.c_int64)]
 
 
+class gs_tsdf_grid(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("slots", C.c_void_p), ("stamps", C.c_void_p), ("voxels", C.c_void_p),
+                ("claims", C.c_void_p), ("touched", C.c_void_p), ("counters", C.c_void_p),
+                ("table_size", C.c_int64), ("capacity", C.c_int64), ("voxel_size", C.c_float),
+                ("truncation", C.c_float), ("max_weight", C.c_float), ("fusion", C.c_int32)]
+
+
 STAGES = ("project_fwd", "depth_sort", "duplicate", "pair_sort", "ranges", "raster_fwd", "loss", "raster_bwd",
           "project_bwd", "adam")
 
@@ -119,6 +126,14 @@ EXPORTS = {
     "gs_seed_quadtree": (C.c_int, [P, P, P, P, C.c_float, C.POINTER(gs_camera), C.POINTER(gs_viewmat), C.c_int32,
                                    C.c_float, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int64,
                                    C.POINTER(C.c_int64), P]),
+    "gs_tsdf_integrate": (C.c_int, [P, C.POINTER(gs_tsdf_grid), P, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                                    C.c_uint32, C.c_int64, P]),
+    "gs_tsdf_counters": (C.c_int, [P, C.POINTER(gs_tsdf_grid), C.POINTER(C.c_int64), P]),
+    "gs_tsdf_rehash": (C.c_int, [P, C.POINTER(gs_tsdf_grid), C.POINTER(gs_tsdf_grid), P]),
+    "gs_tsdf_query": (C.c_int, [P, C.POINTER(gs_tsdf_grid), P, C.c_int64, P, P, P]),
+    "gs_seed_tsdf": (C.c_int, [P, P, P, C.POINTER(gs_tsdf_grid), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
+                               C.c_int32, C.c_float, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int64,
+                               C.POINTER(C.c_int64), P]),
     "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                               C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
@@ -479,4 +494,46 @@ def gs_seed_quadtree(ctx, rgb, depth, alpha, alpha_thr, cam: gs_camera, view: gs
     if st == 3:
         return -int(n.value) - 1
     _check(ctx, st, "gs_seed_quadtree")
+    return int(n.value)
+
+
+def gs_tsdf_integrate(ctx, grid: gs_tsdf_grid, depth, cam: gs_camera, view: gs_viewmat, frame: int, min_slot: int = 0,
+                      stream=None):
+    _check(ctx, load().gs_tsdf_integrate(ctx, C.byref(grid), _f32(depth, "depth"), C.byref(cam), C.byref(view),
+                                         int(frame), int(min_slot), _stream(stream)), "gs_tsdf_integrate")
+
+
+def gs_tsdf_counters(ctx, grid: gs_tsdf_grid, stream=None):
+    """(counters [4], status): slots handed out, buckets touched, failed
+    inserts, voxels updated; status GS_ERR_CAPACITY (3) when the pool or the
+    table is too small."""
+    out = (C.c_int64 * 4)()
+    st = load().gs_tsdf_counters(ctx, C.byref(grid), out, _stream(stream))
+    if st not in (GS_OK, 3):
+        _check(ctx, st, "gs_tsdf_counters")
+    return [int(v) for v in out], st
+
+
+def gs_tsdf_rehash(ctx, src: gs_tsdf_grid, dst: gs_tsdf_grid, stream=None):
+    _check(ctx, load().gs_tsdf_rehash(ctx, C.byref(src), C.byref(dst), _stream(stream)), "gs_tsdf_rehash")
+
+
+def gs_tsdf_query(ctx, grid: gs_tsdf_grid, points, tsdf=None, weight=None, stream=None):
+    _check(ctx, load().gs_tsdf_query(ctx, C.byref(grid), _f32(points, "points"), int(points.shape[0]),
+                                     _f32(tsdf, "tsdf"), _f32(weight, "weight"), _stream(stream)), "gs_tsdf_query")
+
+
+def gs_seed_tsdf(ctx, rgb, depth, grid: gs_tsdf_grid, cam: gs_camera, view: gs_viewmat, sh_degree, var_thr, max_size,
+                 min_size, means, log_scales, quats, opacity_logits, sh, capacity, stream=None) -> int:
+    """Seeds new Gaussians (voxel-weight novelty) into the given rows; returns
+    how many (-needed - 1 if more than ``capacity``)."""
+    n = C.c_int64(0)
+    st = load().gs_seed_tsdf(ctx, _f32(rgb, "rgb"), _f32(depth, "depth"), C.byref(grid), C.byref(cam), C.byref(view),
+                             int(sh_degree), float(var_thr), int(max_size), int(min_size), _f32(means, "means"),
+                             _f32(log_scales, "log_scales"), _f32(quats, "quats"),
+                             _f32(opacity_logits, "opacity_logits"), _f32(sh, "sh"), int(capacity), C.byref(n),
+                             _stream(stream))
+    if st == 3:
+        return -int(n.value) - 1
+    _check(ctx, st, "gs_seed_tsdf")
     return int(n.value)

@@ -63,6 +63,7 @@ struct gs_ctx {
   int64_t cap_qt = 0;
   int2* qt_cells[2] = {nullptr, nullptr};
   int4* qt_leaves = nullptr;
+  int64_t* qt_claim = nullptr;  // per leaf: the voxel it bids for (TSDF seeding)
   uint32_t* qt_counters = nullptr;
   int64_t cap_tune = 0;
   // device scalars and their host mirror
@@ -539,6 +540,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->qt_cells[0]);
   cudaFree(c->qt_cells[1]);
   cudaFree(c->qt_leaves);
+  cudaFree(c->qt_claim);
   cudaFree(c->qt_counters);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
@@ -1305,6 +1307,7 @@ gs_status qt_prepare(gs_ctx* c, int W, int H, int max_size, int min_size, float 
     GS_CUDA(c, regrow(&c->qt_cells[0], need));
     GS_CUDA(c, regrow(&c->qt_cells[1], need));
     GS_CUDA(c, regrow(&c->qt_leaves, need));
+    GS_CUDA(c, regrow(&c->qt_claim, need));
     if (!c->qt_counters) GS_CUDA(c, cudaMalloc((void**)&c->qt_counters, 32 * sizeof(uint32_t)));
     c->cap_qt = need;
   }
@@ -1364,8 +1367,8 @@ gs_status gs_seed_quadtree(gs_ctx* c, const float* rgb, const float* depth, cons
   cudaStream_t s = (cudaStream_t)stream;
   uint32_t nl = 0;
   if ((st = qt_run(c, rgb, cam->width, cam->height, max_size, min_size, var_thr, &nl, s)) != GS_OK) return st;
-  const double K4[4] = {cam->fx, cam->fy, cam->cx, cam->cy};
-  double R[9], t[3];
+  const float K4[4] = {cam->fx, cam->fy, cam->cx, cam->cy};
+  float R[9], t[3];
   for (int k = 0; k < 9; ++k) R[k] = view->R[k];
   for (int k = 0; k < 3; ++k) t[k] = view->t[k];
   uint32_t* n_dev = c->qt_counters + 24;
@@ -1378,6 +1381,165 @@ gs_status gs_seed_quadtree(gs_ctx* c, const float* rgb, const float* depth, cons
   const int64_t n = (int64_t)(c->h_pinned[0] & 0xFFFFFFFFull);
   *n_seeded = n;
   if (n > capacity) return fail(c, GS_ERR_CAPACITY, "gs_seed_quadtree: more new Gaussians than capacity");
+  return GS_OK;
+}
+
+namespace {
+
+gs_status check_grid(gs_ctx* c, const gs_tsdf_grid* g) {
+  if (!g) return fail(c, GS_ERR_INVALID_ARG, "tsdf grid is NULL");
+  if (!g->keys || !g->slots || !g->stamps || !g->voxels || !g->claims || !g->touched || !g->counters)
+    return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: NULL array");
+  if (g->table_size < 2 || g->table_size > ((int64_t)1 << 32) || (g->table_size & (g->table_size - 1)))
+    return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: table_size must be a power of two in [2, 2^32]");
+  if (g->capacity < 1 || g->capacity > INT32_MAX) return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: bad capacity");
+  if (!finite_pos(g->voxel_size) || !finite_pos(g->truncation))
+    return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: voxel_size and truncation must be finite and > 0");
+  if ((double)g->truncation / (double)g->voxel_size > 1e6 ||
+      tsdf_band_steps(g->truncation, g->voxel_size) + 1 > GS_TSDF_MAX_SAMPLES)
+    return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: truncation too wide for the band samples (eps <= 30 s)");
+  if (!(g->max_weight >= 1.f) || !std::isfinite(g->max_weight))
+    return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: max_weight must be finite and >= 1");
+  if (g->fusion != 0 && g->fusion != 1) return fail(c, GS_ERR_INVALID_ARG, "tsdf grid: fusion must be 0 or 1");
+  return GS_OK;
+}
+
+TsdfGrid to_internal(const gs_tsdf_grid* g) {
+  TsdfGrid t;
+  t.keys = reinterpret_cast<unsigned long long*>(g->keys);
+  t.slots = g->slots;
+  t.stamps = g->stamps;
+  t.voxels = g->voxels;
+  t.claims = g->claims;
+  t.touched = g->touched;
+  t.counters = g->counters;
+  t.table_size = g->table_size;
+  t.capacity = g->capacity;
+  t.voxel_size = g->voxel_size;
+  t.truncation = g->truncation;
+  t.max_weight = g->max_weight;
+  t.fusion = g->fusion;
+  return t;
+}
+
+TsdfCamera tsdf_camera(const gs_camera* cam, const gs_viewmat* view) {
+  TsdfCamera t;
+  t.fx = cam->fx;
+  t.fy = cam->fy;
+  t.cx = cam->cx;
+  t.cy = cam->cy;
+  t.W = cam->width;
+  t.H = cam->height;
+  for (int k = 0; k < 9; ++k) t.R[k] = view->R[k];
+  for (int k = 0; k < 3; ++k) t.t[k] = view->t[k];
+  return t;
+}
+
+bool finite_view(const gs_viewmat* v) {
+  for (int k = 0; k < 9; ++k)
+    if (!std::isfinite(v->R[k])) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(v->t[k])) return false;
+  return true;
+}
+
+}  // namespace
+
+gs_status gs_tsdf_integrate(gs_ctx* c, const gs_tsdf_grid* grid, const float* depth, const gs_camera* cam,
+                            const gs_viewmat* view, uint32_t frame, int64_t min_slot, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_grid(c, grid)) != GS_OK || (st = check_cam(c, cam)) != GS_OK) return st;
+  if (!depth || !view || !finite_view(view) || frame == 0 || min_slot < 0 || min_slot > grid->capacity)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_tsdf_integrate: bad arguments");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const TsdfGrid g = to_internal(grid);
+  const TsdfCamera tc = tsdf_camera(cam, view);
+  if (min_slot == 0) {
+    GS_CUDA(c, cudaMemsetAsync(grid->counters + 1, 0, 2 * sizeof(uint32_t), s));
+    launch_tsdf_alloc(g, depth, tc, frame, s);
+    GS_CHECK_LAUNCH(c, "tsdf allocation");
+    c->launches += 1;
+  }
+  launch_tsdf_integrate(g, depth, tc, min_slot, c->num_sms, s);
+  GS_CHECK_LAUNCH(c, "tsdf integration");
+  c->launches += 1;
+  return GS_OK;
+}
+
+gs_status gs_tsdf_counters(gs_ctx* c, const gs_tsdf_grid* grid, int64_t* out, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_grid(c, grid)) != GS_OK) return st;
+  if (!out) return fail(c, GS_ERR_INVALID_ARG, "gs_tsdf_counters: NULL output");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, grid->counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  const uint32_t* h = reinterpret_cast<const uint32_t*>(c->h_pinned);
+  for (int k = 0; k < 4; ++k) out[k] = h[k];
+  if (out[2] > 0) return fail(c, GS_ERR_CAPACITY, "tsdf: hash table or touched list full (grow table_size)");
+  if (out[0] > grid->capacity) return fail(c, GS_ERR_CAPACITY, "tsdf: more blocks than pool slots (grow capacity)");
+  return GS_OK;
+}
+
+gs_status gs_tsdf_rehash(gs_ctx* c, const gs_tsdf_grid* from, const gs_tsdf_grid* to, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_grid(c, from)) != GS_OK || (st = check_grid(c, to)) != GS_OK) return st;
+  if (from->keys == to->keys || from->slots == to->slots)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_tsdf_rehash: the tables must not overlap");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  launch_tsdf_rehash(to_internal(from), to_internal(to), c->num_sms, (cudaStream_t)stream);
+  GS_CHECK_LAUNCH(c, "tsdf rehash");
+  c->launches += 1;
+  return GS_OK;
+}
+
+gs_status gs_tsdf_query(gs_ctx* c, const gs_tsdf_grid* grid, const float* points, int64_t n, float* tsdf,
+                        float* weight, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_grid(c, grid)) != GS_OK) return st;
+  if (n < 0 || (n > 0 && !points)) return fail(c, GS_ERR_INVALID_ARG, "gs_tsdf_query: bad arguments");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  launch_tsdf_query(to_internal(grid), points, n, tsdf, weight, (cudaStream_t)stream);
+  GS_CHECK_LAUNCH(c, "tsdf query");
+  if (n > 0) c->launches += 1;
+  return GS_OK;
+}
+
+gs_status gs_seed_tsdf(gs_ctx* c, const float* rgb, const float* depth, const gs_tsdf_grid* grid,
+                       const gs_camera* cam, const gs_viewmat* view, int32_t sh_degree, float var_thr,
+                       int32_t max_size, int32_t min_size, float* means, float* log_scales, float* quats,
+                       float* opacity_logits, float* sh, int64_t capacity, int64_t* n_seeded, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  gs_status st;
+  if ((st = check_cam(c, cam)) != GS_OK || (st = check_grid(c, grid)) != GS_OK) return st;
+  if (!view || !finite_view(view) || !rgb || !depth || !n_seeded || capacity < 0 || sh_degree < 0 || sh_degree > 3)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_seed_tsdf: bad arguments");
+  if (capacity > 0 && (!means || !log_scales || !quats || !opacity_logits || !sh))
+    return fail(c, GS_ERR_INVALID_ARG, "gs_seed_tsdf: NULL output array");
+  if (capacity > 0xFFFFFFF0ll) return fail(c, GS_ERR_INVALID_ARG, "gs_seed_tsdf: capacity too large");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t nl = 0;
+  if ((st = qt_run(c, rgb, cam->width, cam->height, max_size, min_size, var_thr, &nl, s)) != GS_OK) return st;
+  const float K4[4] = {cam->fx, cam->fy, cam->cx, cam->cy};
+  float R[9], t[3];
+  for (int k = 0; k < 9; ++k) R[k] = view->R[k];
+  for (int k = 0; k < 3; ++k) t[k] = view->t[k];
+  uint32_t* n_dev = c->qt_counters + 24;
+  launch_tsdf_seed(to_internal(grid), rgb, depth, cam->width, cam->height, K4, R, t, sh_degree, c->qt_leaves, nl,
+                   c->qt_claim, means, log_scales, quats, opacity_logits, sh, (uint32_t)capacity, n_dev, s);
+  if (nl > 0) c->launches += 2;
+  GS_CHECK_LAUNCH(c, "tsdf seed");
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, n_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  const int64_t n = (int64_t)(c->h_pinned[0] & 0xFFFFFFFFull);
+  *n_seeded = n;
+  if (n > capacity) return fail(c, GS_ERR_CAPACITY, "gs_seed_tsdf: more new Gaussians than capacity");
   return GS_OK;
 }
 

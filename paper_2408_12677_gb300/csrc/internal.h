@@ -217,6 +217,44 @@ void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh
                  float beta1, float beta2, float eps, float step_size_scale, float inv_sqrt_bc2, bool zero_grads,
                  const long long* step_dev, cudaStream_t s);
 
+// TSDF grid (Sec. III-B.1): hash table of 8^3-voxel blocks over a slot pool.
+// Mirrors gs_tsdf_grid; counters: [0] blocks (next slot), [1] buckets
+// touched by the last allocation, [2] insert / list failures, [3] voxels
+// updated.
+struct TsdfGrid {
+  unsigned long long* keys;  // [table_size], ~0 = free
+  int32_t* slots;            // [table_size]
+  uint32_t* stamps;          // [table_size] last frame that touched the bucket
+  float* voxels;             // [capacity][512] float2 (tsdf, weight)
+  uint32_t* claims;          // [capacity][512], ~0 between calls
+  uint32_t* touched;         // [table_size / 2] buckets
+  uint32_t* counters;        // [4]
+  int64_t table_size, capacity;
+  float voxel_size, truncation, max_weight;
+  int fusion;  // 0: Eq. 9 as printed, 1: unit measurement weight
+};
+
+struct TsdfCamera {
+  float fx, fy, cx, cy;
+  int W, H;
+  float R[9], t[3];  // world-to-camera, R row-major
+};
+
+constexpr int kTsdfMaxSamples = 16;  // band samples per ray
+int tsdf_band_steps(float eps, float s);
+int64_t tsdf_alloc_smem_bytes(float eps, float s);
+void launch_tsdf_alloc(const TsdfGrid& g, const float* depth, const TsdfCamera& c, uint32_t frame, cudaStream_t s);
+void launch_tsdf_integrate(const TsdfGrid& g, const float* depth, const TsdfCamera& c, int64_t min_slot,
+                           int num_sms, cudaStream_t s);
+void launch_tsdf_rehash(const TsdfGrid& from, const TsdfGrid& to, int num_sms, cudaStream_t s);
+void launch_tsdf_query(const TsdfGrid& g, const float* points, int64_t n, float* tsdf, float* weight,
+                       cudaStream_t s);
+// claim + seed kernels over the leaves; leaf_claim: n_leaves scratch words
+void launch_tsdf_seed(const TsdfGrid& g, const float* rgb, const float* depth, int W, int H, const float K4[4],
+                      const float R[9], const float t[3], int sh_degree, const int4* leaves, uint32_t n_leaves,
+                      int64_t* leaf_claim, float* means, float* log_scales, float* quats, float* logits, float* sh,
+                      uint32_t capacity, uint32_t* n_seeded, cudaStream_t s);
+
 // per-frame seeding (quadtree + Eq. 10); counters: >= levels + 2 words;
 // cells_a / cells_b / leaves: quadtree_scratch_cells(W, H) entries each
 int64_t quadtree_scratch_cells(int W, int H);
@@ -224,7 +262,7 @@ int launch_quadtree(const float* rgb, int W, int H, int max_size, int min_size, 
                     int2* cells_b, uint32_t* counters, int4* leaves, cudaStream_t s);
 // K4 = (fx, fy, cx, cy); R, t world-to-camera
 void launch_seed(const float* rgb, const float* depth, const float* alpha, float alpha_thr, int W, int H,
-                 const double K4[4], const double R[9], const double t[3], int sh_degree, const int4* leaves,
+                 const float K4[4], const float R[9], const float t[3], int sh_degree, const int4* leaves,
                  uint32_t n_leaves, float* means, float* log_scales, float* quats, float* logits, float* sh,
                  uint32_t capacity, uint32_t* n_seeded, cudaStream_t s);
 

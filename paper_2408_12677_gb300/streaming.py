@@ -1,12 +1,13 @@
 """Per-frame streaming optimisation: GSFusion's online loop around the hot
-path (Sec. III-B.2-3).  For every incoming RGB-D frame:
+path (Sec. III-B).  For every incoming RGB-D frame:
 
-1. render the current map at the frame's pose (gs_render_fwd) and read the
-   alpha image back;
-2. seed new Gaussians only where the map does not cover the frame yet
-   (rendered alpha < 0.5 at the leaf centre: the novelty rule; the paper tests
-   the TSDF voxel weight instead, Sec. III-B.2), on the device
-   (gs_seed_quadtree) or through a host seeding function;
+1. fuse the depth image into the TSDF grid (gs_tsdf_integrate, Eq. 6-9);
+2. seed new Gaussians at the quadtree leaves whose back-projected centre
+   falls in a voxel first seen by this frame (weight 1, at most one Gaussian
+   per voxel: gs_seed_tsdf, Sec. III-B.2).  ``novelty="alpha"`` instead
+   renders the current map at the frame's pose and seeds where its alpha is
+   below 0.5 (gs_seed_quadtree), and a host ``seed_fn`` seeds with that mask
+   on the CPU;
 3. append them to the map (capacity-doubling buffers, Adam moments of the
    new Gaussians zero);
 4. keep the frame as a keyframe when it added more than 50 Gaussians
@@ -19,8 +20,8 @@ The map lives in flat buffers of a fixed capacity: slots [0, n) hold the
 Gaussians, the others are inert (opacity logit and log-scales -30, so the
 projection gives them no tile and their gradient, hence their Adam update,
 is zero).  The kernels always run over the whole capacity, which only changes
-when the map doubles.  All per-Gaussian arithmetic runs in libgsplat; this
-module moves buffers and chooses views.
+when the map doubles.  All per-Gaussian and per-voxel arithmetic runs in
+libgsplat; this module moves buffers and chooses views.
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ import torch
 
 from . import abi
 from .torch_api import PARAM_NAMES, Context, GaussianModel, camera_struct, flat_sizes, n_sh
+from .tsdf import TSDFGrid
 
 INERT_LOGIT = -30.0
 INERT_LOG_SCALE = -30.0
@@ -141,7 +143,11 @@ class FrameStats:
     views_per_iter: list
     loss: float
     gpu_ms: float        # CUDA-event time of the frame's optimisation iterations
-    host_ms: float       # wall time of the whole frame (render, seeding, upload, iterations)
+    host_ms: float       # wall time of the whole frame (fusion, seeding, upload, iterations)
+    tsdf_ms: float = 0.0  # CUDA-event time of the frame's TSDF fusion (allocation + integration)
+    tsdf_blocks: int = 0  # allocated voxel blocks after the frame
+    tsdf_touched: int = 0  # blocks the frame allocated or updated
+    tsdf_updated: int = 0  # voxels the frame updated
 
 
 class StreamingOptimizer:
@@ -149,13 +155,19 @@ class StreamingOptimizer:
 
     def __init__(self, cam, sh_degree: int, seed_fn=None, iters: int = 10, n_past: int = 4, capacity: int = 1 << 16,
                  raster_cfg=None, adam_cfg=None, w_color: float = 0.8, w_depth: float = 0.2, rng_seed: int = 0,
-                 device: int = 0, ctx: Context | None = None, seeding=None):
-        """``seed_fn(rgb, depth, cam, pose, mask) -> params`` seeds on the host;
-        without it the frame is seeded on the device (gs_seed_quadtree) with
-        ``seeding`` = dict(var_thr, max_size, min_size)."""
+                 device: int = 0, ctx: Context | None = None, seeding=None, novelty: str = "tsdf", tsdf=None):
+        """``seed_fn(rgb, depth, cam, pose, mask) -> params`` seeds on the host
+        with the rendered-alpha mask; without it the frame is seeded on the
+        device with ``seeding`` = dict(var_thr, max_size, min_size) and the
+        ``novelty`` rule: "tsdf" (the voxel weights of the TSDF grid built
+        from ``tsdf`` = dict(voxel_size, truncation, max_weight, fusion)) or
+        "alpha" (rendered alpha < 0.5)."""
+        if novelty not in ("tsdf", "alpha"):
+            raise ValueError(f"novelty must be 'tsdf' or 'alpha', not {novelty!r}")
         self.cam = cam
         self.cam_s = camera_struct(cam)
         self.seed_fn = seed_fn
+        self.novelty = "alpha" if seed_fn is not None else novelty
         self.seeding = {"var_thr": 0.01, "max_size": 64, "min_size": 1, **(seeding or {})}
         self.iters, self.n_past = int(iters), int(n_past)
         self.map = GrowingMap(sh_degree, capacity, device)
@@ -176,6 +188,10 @@ class StreamingOptimizer:
         self.dLdd = [torch.empty((H, W), device=dev) for _ in range(slots)]
         self.loss = torch.zeros(1, device=dev)
         self.frame_index = 0
+        self.tsdf = None
+        if self.novelty == "tsdf":
+            self.tsdf = TSDFGrid(self.ctx, device=dev, **{"voxel_size": 0.01, "truncation": 0.08,
+                                                          "max_weight": 100.0, **(tsdf or {})})
 
     def render_alpha(self, view) -> np.ndarray:
         """Alpha image of the current map at ``view`` (host array)."""
@@ -195,21 +211,26 @@ class StreamingOptimizer:
                                   self.loss, m.flat, m.m, m.v, self.acfg, self.step)
 
     def seed_on_device(self, cur: "Keyframe") -> int:
-        """Novelty seeding of the frame on the device (gs_seed_quadtree) into
+        """Novelty seeding of the frame on the device (gs_seed_tsdf after the
+        frame's TSDF fusion, or gs_seed_quadtree with the rendered alpha) into
         the map's free slots, growing the map when they do not suffice."""
         h = self.ctx.handle
         alpha = None
-        if self.map.n > 0:
+        if self.novelty == "alpha" and self.map.n > 0:
             abi.gs_render_fwd(h, self.map.model.gaussians(), self.cam_s, cur.view, self.rcfg, None, None,
                               self.alpha[0])
             alpha = self.alpha[0]
         sp = self.seeding
         for _ in range(2):
             m, n = self.map.model, self.map.n
-            k = abi.gs_seed_quadtree(h, cur.rgb, cur.depth, alpha, NOVELTY_ALPHA, self.cam_s, cur.view,
-                                     self.map.sh_degree, sp["var_thr"], sp["max_size"], sp["min_size"],
-                                     m.p["means"][n:], m.p["log_scales"][n:], m.p["quats"][n:],
-                                     m.p["opacity_logits"][n:], m.p["sh"][n:], m.n - n)
+            rows = (m.p["means"][n:], m.p["log_scales"][n:], m.p["quats"][n:], m.p["opacity_logits"][n:],
+                    m.p["sh"][n:], m.n - n)
+            if self.novelty == "tsdf":
+                k = self.tsdf.seed(cur.rgb, cur.depth, self.cam_s, cur.view, self.map.sh_degree, sp["var_thr"],
+                                   sp["max_size"], sp["min_size"], *rows)
+            else:
+                k = abi.gs_seed_quadtree(h, cur.rgb, cur.depth, alpha, NOVELTY_ALPHA, self.cam_s, cur.view,
+                                         self.map.sh_degree, sp["var_thr"], sp["max_size"], sp["min_size"], *rows)
             if k >= 0:
                 self.map.n += k
                 return k
@@ -224,6 +245,9 @@ class StreamingOptimizer:
         cur = Keyframe(self.cam, view, torch.as_tensor(np.ascontiguousarray(np.transpose(rgb, (2, 0, 1)), np.float32),
                                                         device=dev),
                        torch.as_tensor(np.ascontiguousarray(depth, np.float32), device=dev))
+        fused = {}
+        if self.tsdf is not None:
+            fused = self.tsdf.integrate(cur.depth, self.cam_s, view)
         if self.seed_fn is None:
             k = self.seed_on_device(cur)
         else:
@@ -243,7 +267,8 @@ class StreamingOptimizer:
         ev1.record()
         torch.cuda.synchronize()
         stats = FrameStats(self.frame_index, k, self.map.n, self.map.capacity, is_key, sizes, float(self.loss.item()),
-                           ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0))
+                           ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t0), fused.get("ms", 0.0),
+                           fused.get("blocks", 0), fused.get("touched", 0), fused.get("updated", 0))
         self.frame_index += 1
         return stats
 

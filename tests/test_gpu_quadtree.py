@@ -118,13 +118,16 @@ def test_seeded_parameters_match_oracle(ctx):
     assert r == -k - 1 and float(small["means"][10:].abs().max()) == 0.0
 
 
-def test_streaming_with_device_seeding(ctx):
+@pytest.mark.parametrize("novelty", ["alpha", "tsdf"])
+def test_streaming_with_device_seeding(ctx, novelty):
     from paper_2408_12677_gb300.streaming import StreamingOptimizer
     st = workloads.streaming(n_frames=8, width=96, height=64, f=48.0)
     opt = StreamingOptimizer(st.cam, 1, None, iters=2, n_past=2, capacity=128, rng_seed=3,
-                             seeding=dict(var_thr=0.03, min_size=4))
+                             seeding=dict(var_thr=0.03, min_size=4), novelty=novelty)
     stats = [opt.process_frame(*st.frame(k), st.poses[k]) for k in range(4)]
     assert stats[0].n_gaussians > 100 and stats[-1].capacity >= stats[-1].n_gaussians > stats[0].n_gaussians
     again = opt.process_frame(*st.frame(3), st.poses[3])
     assert again.new_gaussians < 0.2 * stats[0].new_gaussians
+    if novelty == "tsdf":  # the repeated frame's own voxels all have weight >= 2 now
+        assert again.new_gaussians < 0.05 * stats[-1].n_gaussians and again.tsdf_touched > 0
     assert torch.isfinite(opt.map.model.flat).all()
