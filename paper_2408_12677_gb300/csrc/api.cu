@@ -64,6 +64,8 @@ struct gs_ctx {
   int2* qt_cells[2] = {nullptr, nullptr};
   int4* qt_leaves = nullptr;
   int64_t* qt_claim = nullptr;  // per leaf: the voxel it bids for (TSDF seeding)
+  double* qt_pyr = nullptr;     // quadtree sum pyramid
+  int64_t cap_pyr = 0;
   uint32_t* qt_counters = nullptr;
   int64_t cap_tune = 0;
   // device scalars and their host mirror
@@ -541,6 +543,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->qt_cells[1]);
   cudaFree(c->qt_leaves);
   cudaFree(c->qt_claim);
+  cudaFree(c->qt_pyr);
   cudaFree(c->qt_counters);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
@@ -1311,6 +1314,12 @@ gs_status qt_prepare(gs_ctx* c, int W, int H, int max_size, int min_size, float 
     if (!c->qt_counters) GS_CUDA(c, cudaMalloc((void**)&c->qt_counters, 32 * sizeof(uint32_t)));
     c->cap_qt = need;
   }
+  const int64_t need_pyr = quadtree_pyramid_doubles(W, H, max_size);
+  if (need_pyr > c->cap_pyr) {
+    GS_CUDA(c, cudaDeviceSynchronize());
+    GS_CUDA(c, regrow(&c->qt_pyr, need_pyr));
+    c->cap_pyr = need_pyr;
+  }
   return GS_OK;
 }
 
@@ -1320,7 +1329,7 @@ gs_status qt_run(gs_ctx* c, const float* rgb, int W, int H, int max_size, int mi
   gs_status st = qt_prepare(c, W, H, max_size, min_size, var_thr);
   if (st != GS_OK) return st;
   c->launches += launch_quadtree(rgb, W, H, max_size, min_size, (double)var_thr, c->qt_cells[0], c->qt_cells[1],
-                                 c->qt_counters, c->qt_leaves, s);
+                                 c->qt_counters, c->qt_leaves, c->qt_pyr, s);
   GS_CHECK_LAUNCH(c, "quadtree");
   GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->qt_counters, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(c, cudaStreamSynchronize(s));

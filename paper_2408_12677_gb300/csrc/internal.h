@@ -256,10 +256,13 @@ void launch_tsdf_seed(const TsdfGrid& g, const float* rgb, const float* depth, i
                       uint32_t capacity, uint32_t* n_seeded, cudaStream_t s);
 
 // per-frame seeding (quadtree + Eq. 10); counters: >= levels + 2 words;
-// cells_a / cells_b / leaves: quadtree_scratch_cells(W, H) entries each
+// cells_a / cells_b / leaves: quadtree_scratch_cells(W, H) entries each;
+// pyramid: quadtree_pyramid_doubles(W, H, max_size) doubles.  Returns the
+// number of kernels launched.
 int64_t quadtree_scratch_cells(int W, int H);
+int64_t quadtree_pyramid_doubles(int W, int H, int max_size);
 int launch_quadtree(const float* rgb, int W, int H, int max_size, int min_size, double var_thr, int2* cells_a,
-                    int2* cells_b, uint32_t* counters, int4* leaves, cudaStream_t s);
+                    int2* cells_b, uint32_t* counters, int4* leaves, double* pyramid, cudaStream_t s);
 // K4 = (fx, fy, cx, cy); R, t world-to-camera
 void launch_seed(const float* rgb, const float* depth, const float* alpha, float alpha_thr, int W, int H,
                  const float K4[4], const float R[9], const float t[3], int sh_degree, const int4* leaves,

@@ -23,6 +23,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "common.cuh"
 #include "internal.h"
 #include "seed.cuh"
 
@@ -300,13 +301,17 @@ __global__ void __launch_bounds__(256) tsdf_seed_kernel(const __grid_constant__ 
                                                         const int64_t* __restrict__ leaf_claim,
                                                         uint32_t* __restrict__ n_seeded) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_leaves) return;
-  const int64_t v = leaf_claim[i];
-  if (v < 0) return;
-  const int4 L = leaves[i];
-  if (g.claims[v] != (uint32_t)L.y * (uint32_t)a.W + (uint32_t)L.x) return;
+  const int64_t v = i < n_leaves ? leaf_claim[i] : -1;
+  int4 L = make_int4(0, 0, 1, 1);
+  bool wins = false;
+  if (v >= 0) {
+    L = leaves[i];
+    wins = g.claims[v] == (uint32_t)L.y * (uint32_t)a.W + (uint32_t)L.x;
+  }
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, wins);
+  if (!wins) return;
   g.claims[v] = 0xFFFFFFFFu;
-  const uint32_t k = atomicAdd(n_seeded, 1u);
+  const uint32_t k = warp_agg_inc(n_seeded, 0u, m);  // one atomic per warp
   if (k >= a.capacity) return;
   float ux, uy;
   const size_t pix = leaf_pixel(a, L, &ux, &uy);
