@@ -522,7 +522,8 @@ def run_streaming(args, rank, world, local_rank):
             "ms_per_frame": tsdf_ms / len(stats), "blocks_last": stats[-1].tsdf_blocks,
             "touched_per_frame": sum(s.tsdf_touched for s in stats) / len(stats),
             "updated_voxels_per_frame": tsdf_updated / len(stats),
-            "achieved_gbs": (16 * tsdf_updated + 4 * st.cam.width * st.cam.height * len(stats)) / (tsdf_ms * 1e6),
+            "roofline": tsdf_roofline(16 * tsdf_updated + 4 * st.cam.width * st.cam.height * len(stats), tsdf_ms,
+                                      len(stats)),
         },
         # e2e step = one frame: its RGB-D upload, the alpha read-back for the novelty mask, the new
         # Gaussians' upload and one loss read
@@ -541,6 +542,17 @@ def run_streaming(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+
+def tsdf_roofline(alg_bytes, ms, frames):
+    """HBM roofline of the TSDF fusion launches (allocation + integration),
+    timed with CUDA events around each frame's gs_tsdf_integrate; algorithmic
+    bytes: 16 per updated voxel (float2 read + write), 4 per depth pixel."""
+    peak, kind = load_peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9 if ms else 0.0
+    return {"kernel": "tsdf_alloc + tsdf_integrate", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": kind,
+            "alg_bytes_per_frame": alg_bytes / max(frames, 1)}
 
 
 def max_over_ranks(values, world):
