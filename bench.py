@@ -81,14 +81,27 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling every 50 ms and returns once the first sample is
+        in, so that the samples after it fall in the region timed next (the
+        first one is dropped)."""
+        self.skip = 0
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.perf_counter() + 3.0
+        while time.perf_counter() < t_end and self.proc.poll() is None:
+            with open(self.path) as f:
+                n = sum(1 for line in f if line.count(",") >= 8)
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -104,6 +117,7 @@ class ClockSampler:
             if len(f) >= 9:
                 rows.append(f)
         os.unlink(self.path)
+        rows = rows[self.skip:]  # taken before the timed region
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -589,18 +603,52 @@ def load_traffic(kernel):
 # ---------------------------------------------------------------------------
 # oracle timing (cpu_baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(w, n_pix, seed=0, adam_frac=1.0):
-    """Time the FP64 oracle on a bounded sample of one iteration: projection
-    of all Gaussians, forward + backward over n_pix random pixels (prefilter
-    mode) and the Adam update of a random adam_frac of the parameters; the
-    per-pixel and per-parameter parts are extrapolated to the full image and
-    parameter count.  Returns (seconds per iteration, description, threads)."""
+def oracle_projection(w):
+    """Times the oracle's projection of all Gaussians of the view, forward and
+    backward (autograd of the sum of its outputs), once; returns (seconds,
+    per-Gaussian 2D means and 3-sigma radii for selecting the Gaussians that
+    reach a pixel sample, the indices they belong to, the flat parameters and
+    their learning rates for the Adam sample)."""
+    import numpy as np
+    import torch
+
+    from oracle import render as R
+
+    v = w.views[0]
+    Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
+    t0 = time.perf_counter()
+    P = R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
+    out = R.project(P, w.sh_degree, v.cam, Rm, t)
+    total = sum(out[k].sum() for k in ("mean2d", "cov2d", "depth", "rgb", "opacity"))
+    torch.autograd.grad(total, [P[k] for k in R.PARAM_NAMES], allow_unused=True)
+    t_proj = time.perf_counter() - t0
+    cov = out["cov2d"].detach().numpy()
+    tr, det = cov[:, 0, 0] + cov[:, 1, 1], cov[:, 0, 0] * cov[:, 1, 1] - cov[:, 0, 1] ** 2
+    lam = 0.5 * tr + np.sqrt(np.maximum(0.25 * tr * tr - det, 0.0))
+    from oracle import adam as oadam
+    cfg = oadam.AdamCfg()
+    return (t_proj, out["mean2d"].detach().numpy(), 3.0 * np.sqrt(lam) + 1.0, out["idx"].numpy(),
+            oadam.flatten(w.params), oadam.lr_per_element(w.n, w.sh_degree, cfg))
+
+
+def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
+    """Time the FP64 oracle on a bounded sample of one iteration: forward +
+    backward over n_pix random pixels (prefilter mode) with the Gaussians
+    that reach them, and the Adam update of a random adam_frac of the
+    parameters.  The projection of all Gaussians (forward + backward, timed
+    once per run by oracle_projection, ``proj``) is added whole; the pixel
+    part (the sample's time less its Gaussians' share of the projection) is
+    extrapolated to the full image, the Adam part to every parameter.
+    Returns (seconds per iteration, description, threads, proj)."""
     import numpy as np
     import torch
 
     from oracle import adam as oadam
     from oracle import render as R
 
+    if proj is None:
+        proj = oracle_projection(w)
+    t_proj, mu, rad, idx, flat, lr_all = proj
     v = w.views[0]
     H, W = v.cam.height, v.cam.width
     rng = np.random.default_rng(seed)
@@ -608,29 +656,38 @@ def oracle_sample(w, n_pix, seed=0, adam_frac=1.0):
     wc = rng.standard_normal((3, n_pix))
     wd = rng.standard_normal(n_pix)
     Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
-    t0 = time.perf_counter()
-    P = R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
-    R.project(P, w.sh_degree, v.cam, Rm, t)
-    t_proj = time.perf_counter() - t0
+    # the Gaussians whose 3-sigma box holds a sampled pixel centre (the others
+    # cannot take part in those pixels)
+    occ = np.zeros((H + 1, W + 1), np.int64)  # summed-area table of the sampled pixels
+    np.add.at(occ, (pix[:, 1] + 1, pix[:, 0] + 1), 1)
+    occ = occ.cumsum(0).cumsum(1)
+    x0 = np.clip(np.ceil(mu[:, 0] - rad - 0.5), 0, W).astype(np.int64)
+    x1 = np.clip(np.floor(mu[:, 0] + rad - 0.5), -1, W - 1).astype(np.int64)
+    y0 = np.clip(np.ceil(mu[:, 1] - rad - 0.5), 0, H).astype(np.int64)
+    y1 = np.clip(np.floor(mu[:, 1] + rad - 0.5), -1, H - 1).astype(np.int64)
+    ok = (x1 >= x0) & (y1 >= y0)
+    x0, x1, y0, y1 = np.minimum(x0, W - 1), np.maximum(x1, 0), np.minimum(y0, H - 1), np.maximum(y1, 0)
+    hits = occ[y1 + 1, x1 + 1] - occ[y0, x1 + 1] - occ[y1 + 1, x0] + occ[y0, x0]
+    near = ok & (hits > 0)
+    sub = {k: np.asarray(w.params[k])[idx[near]] for k in R.PARAM_NAMES}
     t1 = time.perf_counter()
-    R.weighted_pixel_gradients(w.params, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
+    R.weighted_pixel_gradients(sub, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
     t_pix = time.perf_counter() - t1
     cfg = oadam.AdamCfg()
-    flat = oadam.flatten(w.params)
-    sel = rng.choice(flat.size, max(1, int(adam_frac * flat.size)), replace=False) if adam_frac < 1 else \
-        slice(None)
-    lr = oadam.lr_per_element(w.n, w.sh_degree, cfg)[sel]
-    p = flat[sel]
+    k = max(1, int(adam_frac * flat.size))
+    o = int(rng.integers(0, flat.size - k + 1))  # a random contiguous slice of the flat parameters
+    lr = lr_all[o:o + k]
+    p = flat[o:o + k].copy()
     t2 = time.perf_counter()
     oadam.adam_step(p, rng.standard_normal(p.size), np.zeros_like(p), np.zeros_like(p), 1, lr, cfg)
     t_adam = (time.perf_counter() - t2) / max(adam_frac, 1e-12)
-    per_pixel = max(t_pix - t_proj, 0.0) / n_pix
+    per_pixel = max(t_pix - t_proj * near.sum() / max(len(idx), 1), 0.0) / n_pix
     t_iter = t_proj + per_pixel * H * W + t_adam
-    desc = (f"oracle forward+backward at {n_pix} random pixels of the {W}x{H} view ({t_pix:.2f} s, including a "
-            f"{t_proj:.2f} s projection of all {w.n} Gaussians), per-pixel time extrapolated to {H * W} pixels; "
-            f"float64 Adam on {100 * adam_frac:.3g}% of the {flat.size} parameters extrapolated to all "
-            f"({t_adam:.2f} s)")
-    return t_iter, desc, torch.get_num_threads()
+    desc = (f"oracle forward+backward at {n_pix} random pixels of the {W}x{H} view with the {int(near.sum())} "
+            f"Gaussians reaching them ({t_pix:.3f} s), per-pixel time extrapolated to {H * W} pixels; projection "
+            f"of all {w.n} Gaussians, forward and backward, timed once per run ({t_proj:.2f} s); float64 Adam on "
+            f"{100 * adam_frac:.3g}% of the {flat.size} parameters extrapolated to all ({t_adam:.2f} s)")
+    return t_iter, desc, torch.get_num_threads(), proj
 
 
 def run_reference(args):
@@ -638,15 +695,18 @@ def run_reference(args):
     step is a bounded sample sized so the whole run takes about two minutes."""
     from synth import workloads
     w = workloads.single_view()
+    proj = oracle_projection(w)
     t_cal0 = time.perf_counter()
-    oracle_sample(w, 32, seed=12345, adam_frac=0.01)
+    oracle_sample(w, 32, seed=12345, adam_frac=0.01, proj=proj)
     t_cal = time.perf_counter() - t_cal0
     per_step = 120.0 / max(1, args.steps + args.warmup)
-    n_pix = int(max(16, min(args.ref_pixels, 32 * per_step / max(t_cal, 1e-3))))
+    # at least 256 pixels per step: the oracle call has a fixed cost that a
+    # smaller sample would spread over too few pixels
+    n_pix = int(max(256, min(args.ref_pixels, 32 * per_step / max(t_cal, 1e-3))))
     times = []
     desc, cores = "", 0
     for i in range(args.warmup + args.steps):
-        t_iter, desc, cores = oracle_sample(w, n_pix, seed=i, adam_frac=0.01)
+        t_iter, desc, cores, _ = oracle_sample(w, n_pix, seed=i, adam_frac=0.01, proj=proj)
         if i >= args.warmup:
             times.append(t_iter)
     value = 1.0 / statistics.mean(times)
@@ -664,7 +724,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-pixels", type=int, default=12288)
@@ -704,7 +764,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             from synth import workloads
-            t_iter, desc, cores = oracle_sample(workloads.single_view(), args.ref_pixels)
+            t_iter, desc, cores, _ = oracle_sample(workloads.single_view(), args.ref_pixels)
             out["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "it/s", "cores": cores, "kind": "oracle",
                                    "sample": desc}
         print(json.dumps(out))
