@@ -637,8 +637,9 @@ def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
     that reach them, and the Adam update of a random adam_frac of the
     parameters.  The projection of all Gaussians (forward + backward, timed
     once per run by oracle_projection, ``proj``) is added whole; the pixel
-    part (the sample's time less its Gaussians' share of the projection) is
-    extrapolated to the full image, the Adam part to every parameter.
+    part (the sample's time less the projection of its Gaussians, timed
+    alone) is extrapolated to the full image, the Adam part to every
+    parameter.
     Returns (seconds per iteration, description, threads, proj)."""
     import numpy as np
     import torch
@@ -673,6 +674,14 @@ def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
     t1 = time.perf_counter()
     R.weighted_pixel_gradients(sub, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
     t_pix = time.perf_counter() - t1
+    # the same Gaussians' projection alone (forward and backward), so the pixel
+    # part is the difference
+    t1 = time.perf_counter()
+    Ps = R.to_tensors({k: np.asarray(sub[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
+    outs = R.project(Ps, w.sh_degree, v.cam, Rm, t)
+    tot = sum(outs[k].sum() for k in ("mean2d", "cov2d", "depth", "rgb", "opacity"))
+    torch.autograd.grad(tot, [Ps[k] for k in R.PARAM_NAMES], allow_unused=True)
+    t_sub = time.perf_counter() - t1
     cfg = oadam.AdamCfg()
     k = max(1, int(adam_frac * flat.size))
     o = int(rng.integers(0, flat.size - k + 1))  # a random contiguous slice of the flat parameters
@@ -681,10 +690,11 @@ def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
     t2 = time.perf_counter()
     oadam.adam_step(p, rng.standard_normal(p.size), np.zeros_like(p), np.zeros_like(p), 1, lr, cfg)
     t_adam = (time.perf_counter() - t2) / max(adam_frac, 1e-12)
-    per_pixel = max(t_pix - t_proj * near.sum() / max(len(idx), 1), 0.0) / n_pix
+    per_pixel = max(t_pix - t_sub, 0.0) / n_pix
     t_iter = t_proj + per_pixel * H * W + t_adam
     desc = (f"oracle forward+backward at {n_pix} random pixels of the {W}x{H} view with the {int(near.sum())} "
-            f"Gaussians reaching them ({t_pix:.3f} s), per-pixel time extrapolated to {H * W} pixels; projection "
+            f"Gaussians reaching them ({t_pix:.3f} s, of which their projection {t_sub:.3f} s), per-pixel time "
+            f"extrapolated to {H * W} pixels; projection "
             f"of all {w.n} Gaussians, forward and backward, timed once per run ({t_proj:.2f} s); float64 Adam on "
             f"{100 * adam_frac:.3g}% of the {flat.size} parameters extrapolated to all ({t_adam:.2f} s)")
     return t_iter, desc, torch.get_num_threads(), proj
