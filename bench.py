@@ -177,6 +177,16 @@ def run_ours(args, rank, world, local_rank):
         tr.replay()
     torch.cuda.synchronize(dev)
 
+    # The map trains while it is timed (the iterations are the online
+    # optimisation, so its Gaussians and their pairs grow from step to step).
+    # The timed region, the per-stage run and the end-to-end run each start
+    # from this state (parameters, Adam moments and step restored), so all
+    # three measure the same K iterations.
+    snap = trainer_snapshot(tr)
+
+    def restore():
+        trainer_restore(tr, snap)
+
     # timed region: K graph replays, CUDA events on the launch stream
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -195,6 +205,7 @@ def run_ours(args, rank, world, local_rank):
 
     # per-stage device times: the same K iterations run eagerly (same kernels,
     # same no-sync mode) with the library's CUDA event pairs around each stage
+    restore()
     launches0 = ctx.stats()["kernel_launches"]
     abi.gs_set_profiling(ctx.handle, True)
     p0 = torch.cuda.Event(enable_timing=True)
@@ -209,46 +220,71 @@ def run_ours(args, rank, world, local_rank):
     launches = ctx.stats()["kernel_launches"] - launches0
 
     # end to end through the public API with host buffers: per step, H2D of
-    # that step's target RGB-D frame from pinned memory, one replay, D2H of
-    # the loss.  The targets are double-buffered (one captured graph per
-    # buffer): step k + 1's upload runs on a copy stream while step k
-    # computes, once step k - 1 (the last reader of that buffer) is done.
+    # that step's target RGB-D frame from pinned memory, the iteration and a
+    # D2H copy of the loss.  First choice: Trainer.capture_from_host, two
+    # graphs that each run one iteration on one target buffer while a forked
+    # branch uploads the next step's frame into the other (one launch call
+    # per step; the first frame is uploaded inside the timed region before
+    # the first replay).  Fallback if the copies cannot be captured: the same
+    # double buffering with a copy stream and events.
     h_rgb = torch.from_numpy(v.target_rgb).pin_memory()
     h_dep = torch.from_numpy(v.target_depth).pin_memory()
     h_loss = torch.empty(1).pin_memory()
+    restore()
     bufs = [(trgb, tdep), (trgb.clone(), tdep.clone())]
-    graphs = [tr.graph, tr.capture(*bufs[1])]
-    copy_stream = torch.cuda.Stream(dev)
-    ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    e2e_mode = "two captured graphs: iteration on one buffer + upload of the next frame into the other + D2H loss"
+    try:
+        g_h2h = tr.capture_from_host(h_rgb, h_dep, h_loss, bufs)
+        torch.cuda.synchronize(dev)
+    except Exception as exc:  # pragma: no cover - depends on the torch build
+        g_h2h = None
+        e2e_mode = f"double-buffered streams (graph capture of the copies failed: {type(exc).__name__})"
+    if g_h2h is not None:
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        t_host0 = time.perf_counter()
+        f0.record(stream)
+        bufs[0][0].copy_(h_rgb, non_blocking=True)
+        bufs[0][1].copy_(h_dep, non_blocking=True)
+        for k in range(args.steps):
+            g_h2h[k % 2].replay()
+            tr.step_count += 1
+        f1.record(stream)
+        barrier()
+    else:
+        graphs = [tr.graph, tr.capture(*bufs[1])]
+        copy_stream = torch.cuda.Stream(dev)
+        ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_done = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def upload(b):
-        bufs[b][0].copy_(h_rgb, non_blocking=True)
-        bufs[b][1].copy_(h_dep, non_blocking=True)
-        ev_copied[b].record(copy_stream)
+        def upload(b):
+            bufs[b][0].copy_(h_rgb, non_blocking=True)
+            bufs[b][1].copy_(h_dep, non_blocking=True)
+            ev_copied[b].record(copy_stream)
 
-    barrier()
-    f0 = torch.cuda.Event(enable_timing=True)
-    f1 = torch.cuda.Event(enable_timing=True)
-    t_host0 = time.perf_counter()
-    f0.record(stream)
-    copy_stream.wait_event(f0)
-    with torch.cuda.stream(copy_stream):
-        upload(0)
-    for k in range(args.steps):
-        b = k % 2
-        stream.wait_event(ev_copied[b])
-        graphs[b].replay()
-        tr.step_count += 1
-        h_loss.copy_(tr.loss, non_blocking=True)
-        ev_done[b].record(stream)
-        if k + 1 < args.steps:
-            with torch.cuda.stream(copy_stream):
-                if k >= 1:
-                    copy_stream.wait_event(ev_done[1 - b])  # step k - 1 read buffer 1 - b
-                upload(1 - b)
-    f1.record(stream)
-    barrier()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        t_host0 = time.perf_counter()
+        f0.record(stream)
+        copy_stream.wait_event(f0)
+        with torch.cuda.stream(copy_stream):
+            upload(0)
+        for k in range(args.steps):
+            b = k % 2
+            stream.wait_event(ev_copied[b])
+            graphs[b].replay()
+            tr.step_count += 1
+            h_loss.copy_(tr.loss, non_blocking=True)
+            ev_done[b].record(stream)
+            if k + 1 < args.steps:
+                with torch.cuda.stream(copy_stream):
+                    if k >= 1:
+                        copy_stream.wait_event(ev_done[1 - b])  # step k - 1 read buffer 1 - b
+                    upload(1 - b)
+        f1.record(stream)
+        barrier()
     e2e_ms = f0.elapsed_time(f1)
     e2e_host_s = time.perf_counter() - t_host0
     h2d = h_rgb.numel() * 4 + h_dep.numel() * 4
@@ -298,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "stages": per_stage,
         "e2e": {"value": whole_job_rate(args.steps, world, e2e_ms), "unit": "it/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": 4, "host_wall_s": e2e_host_s},
+                "d2h_bytes_per_step": 4, "host_wall_s": e2e_host_s, "mode": e2e_mode},
         "gpu_launches": launches,
         "eager_ms_per_step": ms_eager / args.steps,
         "clocks": clk,
@@ -307,9 +343,32 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
-def run_sequential(args, w, views, trgb, tdep, rcfg, timed, local_rank):
+def trainer_snapshot(tr):
+    """Parameters, Adam moments and step of a trainer (device copies)."""
+    m = tr.model
+    return [t.clone() for t in (m.flat, m.m, m.v)], tr.step_count
+
+
+def trainer_restore(tr, snap):
+    """Puts a trainer back to ``snap`` (also the context's device Adam step),
+    so that timed phases start from the same map."""
+    import torch
+
+    from paper_2408_12677_gb300 import abi
+    torch.cuda.synchronize()
+    m = tr.model
+    for dst, src in zip((m.flat, m.m, m.v), snap[0]):
+        dst.copy_(src)
+    tr.step_count = snap[1]
+    abi.gs_ctx_set_adam_step(tr.ctx.handle, snap[1])
+    torch.cuda.synchronize()
+
+
+def run_sequential(args, w, views, trgb, tdep, rcfg, timed, local_rank, snap=None):
     """The batched iteration run view by view with the single-view calls:
-    eager (one host read of the pair count per view) and graph-captured."""
+    eager (one host read of the pair count per view) and graph-captured; each
+    timed phase starts from ``snap`` (the batched run's map after its
+    warm-up) when given."""
     import torch
 
     from paper_2408_12677_gb300.torch_api import BatchedTrainer, Context, GaussianModel
@@ -319,10 +378,14 @@ def run_sequential(args, w, views, trgb, tdep, rcfg, timed, local_rank):
     ts = BatchedTrainer(GaussianModel(w.params, device=dev), views, raster_cfg=rcfg, ctx=ctx_s)
     for _ in range(args.warmup):
         ts.step_sequential(trgb, tdep)
+    if snap is not None:
+        trainer_restore(ts, snap)
     ms_s_eager = timed(lambda: ts.step_sequential(trgb, tdep), args.steps)
     ts.capture_sequential(trgb, tdep)
     for _ in range(args.warmup):
         ts.replay()
+    if snap is not None:
+        trainer_restore(ts, snap)
     ms_s = timed(ts.replay, args.steps)
     ts.check_capacity()
     return ms_s, ms_s_eager, float(ts.loss_views.sum())
@@ -376,16 +439,21 @@ def run_multi_view(args, rank, world, local_rank):
     st = ctx_b.stats()
     abi.gs_set_eval_counting(ctx_b.handle, False)
     pairs, e_blend = st["n_pairs"], st["evals_blended"]
+    # every timed phase (both forms) starts from this map: the map trains
+    # while it is timed, and its pairs grow with it
+    snap = trainer_snapshot(tb)
     ms_b_eager = timed(lambda: tb.step(trgb, tdep), args.steps)  # sync mode: one host read per call
     tb.capture(trgb, tdep)
     for _ in range(args.warmup):
         tb.replay()
+    trainer_restore(tb, snap)
     clocks = ClockSampler(local_rank)
     clocks.start()
     ms_b = timed(tb.replay, args.steps)
     clk = clocks.stop()
     tb.check_capacity()
     loss_b = float(tb.loss)
+    trainer_restore(tb, snap)
     launches0 = ctx_b.stats()["kernel_launches"]
     abi.gs_set_profiling(ctx_b.handle, True)
     timed(lambda: tb._iteration(trgb, tdep, 0), args.steps)
@@ -397,6 +465,8 @@ def run_multi_view(args, rank, world, local_rank):
     h_rgb = [torch.from_numpy(v.target_rgb).pin_memory() for v in w.views]
     h_dep = [torch.from_numpy(v.target_depth).pin_memory() for v in w.views]
     h_loss = torch.empty(1).pin_memory()
+
+    trainer_restore(tb, snap)
 
     def e2e_step():
         for k in range(len(views)):
@@ -410,7 +480,7 @@ def run_multi_view(args, rank, world, local_rank):
         ms_s = ms_s_eager = float("nan")
         loss_s = None
     else:
-        ms_s, ms_s_eager, loss_s = run_sequential(args, w, views, trgb, tdep, tb.rcfg, timed, local_rank)
+        ms_s, ms_s_eager, loss_s = run_sequential(args, w, views, trgb, tdep, tb.rcfg, timed, local_rank, snap)
     ms_b, ms_e2e = max_over_ranks([ms_b, ms_e2e], world)
     per_stage = {k: {"ms_per_launch": (ms / c if c else 0.0), "launches": c} for k, (ms, c) in stages.items()}
     dom = max(stages, key=lambda k: stages[k][0])

@@ -216,6 +216,37 @@ class Trainer:
         self.step_count += 1
         return self.loss
 
+    def capture_from_host(self, host_rgb: torch.Tensor, host_depth: torch.Tensor, host_loss: torch.Tensor,
+                          buffers) -> list:
+        """Record a double-buffered host-to-host loop as two CUDA graphs.
+        Graph b runs the iteration on the device targets buffers[b] = (rgb
+        [3, H, W], depth [H, W]) and copies the loss into pinned host_loss
+        [1], while a forked branch uploads the next frame from pinned host
+        memory (host_rgb, host_depth) into buffers[1 - b]; replaying graph 0,
+        1, 0, ... is one step each (the first frame is uploaded into
+        buffers[0] before the first replay; refill the host buffers between
+        replays once the previous replay has finished).  Call after
+        ``capture`` (no-sync mode, buffers reserved)."""
+        if not (host_rgb.is_pinned() and host_depth.is_pinned() and host_loss.is_pinned()):
+            raise ValueError("host buffers must be pinned")
+        side = torch.cuda.Stream()
+        graphs = []
+        for b in range(2):
+            cur_rgb, cur_dep = buffers[b]
+            nxt_rgb, nxt_dep = buffers[1 - b]
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                main = torch.cuda.current_stream()
+                side.wait_stream(main)
+                with torch.cuda.stream(side):
+                    nxt_rgb.copy_(host_rgb, non_blocking=True)
+                    nxt_dep.copy_(host_depth, non_blocking=True)
+                self._step_device_counter(cur_rgb, cur_dep)
+                host_loss.copy_(self.loss, non_blocking=True)
+                main.wait_stream(side)
+            graphs.append(g)
+        return graphs
+
     def check_capacity(self):
         """Raises GsError(GS_ERR_CAPACITY) if a no-sync pass dropped pairs."""
         abi.gs_sync_status(self.ctx.handle)
