@@ -349,12 +349,9 @@ int64_t tsdf_alloc_smem_bytes(float eps, float s) {
 void launch_tsdf_alloc(const TsdfGrid& g, const float* depth, const TsdfCamera& c, uint32_t frame, cudaStream_t s) {
   const Band band = make_band(g.truncation, g.voxel_size);
   const int set = set_entries(band.n);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tsdf_alloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(set_entries(kTsdfMaxSamples) * sizeof(unsigned long long)));
-    attr = true;
-  }
+  // per device and cheap: set on every launch
+  cudaFuncSetAttribute(tsdf_alloc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(set_entries(kTsdfMaxSamples) * sizeof(unsigned long long)));
   const dim3 grid((c.W + kAllocTile - 1) / kAllocTile, (c.H + kAllocTile - 1) / kAllocTile);
   tsdf_alloc_kernel<<<grid, kAllocThreads, set * sizeof(unsigned long long), s>>>(g, depth, c, band, frame, set);
 }
