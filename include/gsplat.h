@@ -54,7 +54,7 @@ typedef enum {
   GS_ERR_INVALID_ARG = 1, /* bad pointer, size or configuration; nothing enqueued */
   GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in gs_last_error) */
   GS_ERR_CAPACITY = 3,    /* (tile, Gaussian) pairs exceeded the reserved capacity in no-sync mode */
-  GS_ERR_NONFINITE = 4,   /* reserved: non-finite inputs detected */
+  GS_ERR_NONFINITE = 4,   /* non-finite values detected (gs_count_nonfinite) */
   GS_ERR_BOUNDS = 5,      /* reserved: device-side bounds check failed */
   GS_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait gave up */
   GS_ERR_OOM = 7,         /* cudaMalloc of context scratch failed */
@@ -525,6 +525,17 @@ gs_status gs_seed_tsdf(gs_ctx *ctx, const float *rgb, const float *depth, const 
                        const gs_camera *cam, const gs_viewmat *view, int32_t sh_degree, float var_thr,
                        int32_t max_size, int32_t min_size, float *means, float *log_scales, float *quats,
                        float *opacity_logits, float *sh, int64_t capacity, int64_t *n_seeded, gs_stream_t stream);
+
+/* Failure detection.  gs_count_nonfinite: *count (host) = the number of
+ * NaN / +-Inf floats in the device array x[0, n) (e.g. a map's flat
+ * parameters after a step); returns GS_ERR_NONFINITE if any.  Synchronises.
+ * gs_ctx_inject_alloc_failure: the after-th next growth of the context's
+ * scratch (1 = the next one; 0 disarms) fails with GS_ERR_OOM before any
+ * buffer is touched, so callers can test their recovery; the context stays
+ * usable (a real allocation failure part-way through a growth drops that
+ * scratch group, which the next call allocates again). */
+gs_status gs_count_nonfinite(gs_ctx *ctx, const float *x, int64_t n, int64_t *count, gs_stream_t stream);
+gs_status gs_ctx_inject_alloc_failure(gs_ctx *ctx, int32_t after);
 
 /* Copy the last forward pass's projected per-Gaussian quantities to caller
  * buffers (each nullable), n = views x Gaussians items, item v * N + i being

@@ -134,6 +134,8 @@ EXPORTS = {
     "gs_seed_tsdf": (C.c_int, [P, P, P, C.POINTER(gs_tsdf_grid), C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                                C.c_int32, C.c_float, C.c_int32, C.c_int32, P, P, P, P, P, C.c_int64,
                                C.POINTER(C.c_int64), P]),
+    "gs_count_nonfinite": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64), P]),
+    "gs_ctx_inject_alloc_failure": (C.c_int, [P, C.c_int32]),
     "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                               C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
@@ -537,3 +539,16 @@ def gs_seed_tsdf(ctx, rgb, depth, grid: gs_tsdf_grid, cam: gs_camera, view: gs_v
         return -int(n.value) - 1
     _check(ctx, st, "gs_seed_tsdf")
     return int(n.value)
+
+
+def gs_count_nonfinite(ctx, x, stream=None) -> int:
+    """Number of NaN / +-Inf values in the float32 device tensor x."""
+    n = C.c_int64(0)
+    st = load().gs_count_nonfinite(ctx, _f32(x, "x"), int(x.numel()), C.byref(n), _stream(stream))
+    if st not in (GS_OK, 4):
+        _check(ctx, st, "gs_count_nonfinite")
+    return int(n.value)
+
+
+def gs_ctx_inject_alloc_failure(ctx, after: int = 1):
+    _check(ctx, load().gs_ctx_inject_alloc_failure(ctx, int(after)), "gs_ctx_inject_alloc_failure")

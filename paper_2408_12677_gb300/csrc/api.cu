@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gsplat.h"
 #include "common.cuh"
 #include "internal.h"
@@ -20,6 +22,8 @@ struct gs_ctx {
   std::string err;
   bool sync = true;
   int64_t launches = 0;
+  int fail_alloc = 0;  // > 0: the fail_alloc-th next scratch growth fails (GS_ERR_OOM)
+  unsigned long long* d_count = nullptr;  // gs_count_nonfinite
 
   // per-Gaussian scratch
   int64_t cap_n = 0;
@@ -156,25 +160,49 @@ cudaError_t regrow(T** p, int64_t count) {
 
 int64_t grow_target(int64_t need, int64_t have) { return std::max<int64_t>(need + need / 4 + 1024, have); }
 
+// A scratch group that fails to grow mid-way has freed some of its old
+// buffers: its capacity drops to 0 so the next call allocates the whole
+// group again.
+#define GS_GROW(ctx, cap_field, call)       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) {                \
+      (ctx)->cap_field = 0;                 \
+      (ctx)->have_state = false;            \
+      return cuda_fail(ctx, e_, #call);     \
+    }                                       \
+  } while (0)
+
+// the failure injected by gs_ctx_inject_alloc_failure, checked before a
+// scratch group grows (the group keeps its current buffers)
+bool injected_alloc_failure(gs_ctx* c) { return c->fail_alloc > 0 && --c->fail_alloc == 0; }
+
+// RAII NVTX range around an ABI call (a no-op unless a profiler is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 gs_status ensure_n(gs_ctx* c, int64_t n) {
   if (n <= c->cap_n) return GS_OK;
+  if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
   const int64_t cap = grow_target(n, c->cap_n);
   GS_CUDA(c, cudaSetDevice(c->device));
   GS_CUDA(c, cudaDeviceSynchronize());
-  GS_CUDA(c, regrow(&c->feat, 3 * cap));
-  GS_CUDA(c, regrow(&c->zkey, cap));
+  GS_GROW(c, cap_n, regrow(&c->feat, 3 * cap));
+  GS_GROW(c, cap_n, regrow(&c->zkey, cap));
   for (int k = 0; k < 2; ++k) {
-    GS_CUDA(c, regrow(&c->dkey[k], cap));
-    GS_CUDA(c, regrow(&c->dval[k], cap));
+    GS_GROW(c, cap_n, regrow(&c->dkey[k], cap));
+    GS_GROW(c, cap_n, regrow(&c->dval[k], cap));
   }
-  GS_CUDA(c, regrow(&c->tiles, cap));
-  GS_CUDA(c, regrow(&c->rects, cap));
-  GS_CUDA(c, regrow(&c->bigq, cap));
-  GS_CUDA(c, regrow(&c->g2d, 3 * cap));
-  GS_CUDA(c, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
+  GS_GROW(c, cap_n, regrow(&c->tiles, cap));
+  GS_GROW(c, cap_n, regrow(&c->rects, cap));
+  GS_GROW(c, cap_n, regrow(&c->bigq, cap));
+  GS_GROW(c, cap_n, regrow(&c->g2d, 3 * cap));
+  GS_GROW(c, cap_n, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
   // per (block, view) pose partials: blocks(n) * V <= blocks(V n) + V, for
   // blocks of 64 or more Gaussians
-  GS_CUDA(c, regrow(&c->pose_partials, 6 * ((cap + 31) / 32 + kMaxViews + 1)));
+  GS_GROW(c, cap_n, regrow(&c->pose_partials, 6 * ((cap + 31) / 32 + kMaxViews + 1)));
   c->cap_n = cap;
   c->have_state = false;
   return GS_OK;
@@ -182,13 +210,14 @@ gs_status ensure_n(gs_ctx* c, int64_t n) {
 
 gs_status ensure_pairs(gs_ctx* c, int64_t p) {
   if (p <= c->cap_p) return GS_OK;
+  if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
   if (p > 0xFFFFFFF0ll) return fail(c, GS_ERR_CAPACITY, "more than 2^32 - 16 (tile, Gaussian) pairs");
   const int64_t cap = std::min<int64_t>(grow_target(p, c->cap_p), 0xFFFFFFF0ll);
   GS_CUDA(c, cudaSetDevice(c->device));
   GS_CUDA(c, cudaDeviceSynchronize());
   for (int k = 0; k < 2; ++k) {
-    GS_CUDA(c, regrow(&c->pk[k], cap));
-    GS_CUDA(c, regrow(&c->pv[k], cap));
+    GS_GROW(c, cap_p, regrow(&c->pk[k], cap));
+    GS_GROW(c, cap_p, regrow(&c->pv[k], cap));
   }
   c->cap_p = cap;
   c->have_state = false;
@@ -197,15 +226,16 @@ gs_status ensure_pairs(gs_ctx* c, int64_t p) {
 
 gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   if (t <= c->cap_t) return GS_OK;
+  if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
   GS_CUDA(c, cudaDeviceSynchronize());
   const int64_t cap = grow_target(t, c->cap_t);
-  GS_CUDA(c, regrow(&c->ranges, cap));
-  GS_CUDA(c, regrow(&c->tcount, cap));
-  GS_CUDA(c, regrow(&c->toffset, cap));
-  GS_CUDA(c, regrow(&c->tcursor, cap));
-  GS_CUDA(c, regrow(&c->torder, cap));
-  GS_CUDA(c, regrow(&c->scan_aux, tile_scan_aux_size(cap)));
-  GS_CUDA(c, regrow(&c->tile_loss, 12 * cap));
+  GS_GROW(c, cap_t, regrow(&c->ranges, cap));
+  GS_GROW(c, cap_t, regrow(&c->tcount, cap));
+  GS_GROW(c, cap_t, regrow(&c->toffset, cap));
+  GS_GROW(c, cap_t, regrow(&c->tcursor, cap));
+  GS_GROW(c, cap_t, regrow(&c->torder, cap));
+  GS_GROW(c, cap_t, regrow(&c->scan_aux, tile_scan_aux_size(cap)));
+  GS_GROW(c, cap_t, regrow(&c->tile_loss, 12 * cap));
   c->cap_t = cap;
   c->have_state = false;
   return GS_OK;
@@ -213,14 +243,15 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
 
 gs_status ensure_px(gs_ctx* c, int64_t npx) {
   if (npx <= c->cap_px) return GS_OK;
+  if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
   GS_CUDA(c, cudaDeviceSynchronize());
   const int64_t cap = grow_target(npx, c->cap_px);
-  GS_CUDA(c, regrow(&c->T_final, cap));
-  GS_CUDA(c, regrow(&c->last, cap));
-  GS_CUDA(c, regrow(&c->dl_img, 4 * cap));
+  GS_GROW(c, cap_px, regrow(&c->T_final, cap));
+  GS_GROW(c, cap_px, regrow(&c->last, cap));
+  GS_GROW(c, cap_px, regrow(&c->dl_img, 4 * cap));
   // per-block partials (blocks of every view: <= blocks(total) + views) and per-view scales
   const int64_t lb = loss_blocks((int)std::min<int64_t>(cap, INT32_MAX - 4096));
-  GS_CUDA(c, regrow(&c->loss_partials, 3 * (lb + kMaxViews) + kMaxViews + 4));
+  GS_GROW(c, cap_px, regrow(&c->loss_partials, 3 * (lb + kMaxViews) + kMaxViews + 4));
   c->cap_px = cap;
   c->have_state = false;
   return GS_OK;
@@ -544,6 +575,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->qt_leaves);
   cudaFree(c->qt_claim);
   cudaFree(c->qt_pyr);
+  cudaFree(c->d_count);
   cudaFree(c->qt_counters);
   cudaFree(c->d_npairs);
   cudaFree(c->d_npairs_full);
@@ -1101,6 +1133,7 @@ gs_status gs_train_step(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
                         const gs_raster_cfg* cfg, const float* target_rgb, const float* target_depth,
                         float w_color, float w_depth, float* loss, float* params, float* m, float* v,
                         const gs_adam_cfg* adam, int64_t step, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_train_step");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
   return train_step_views(c, g, 1, cam, view, cfg, &target_rgb, &target_depth, w_color, w_depth, loss, params, m, v,
@@ -1113,6 +1146,7 @@ gs_status gs_train_step_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_view
                                 float* params, float* m, float* v, const gs_adam_cfg* adam, int64_t step,
                                 float* const* color, float* const* depth, float* const* alpha,
                                 gs_stream_t stream) {
+  NvtxRange nvtx_("gs_train_step_batched");
   if (!c) return GS_ERR_INVALID_ARG;
   return train_step_views(c, g, n_views, cams, views, cfg, target_rgb, target_depth, w_color, w_depth, loss, params,
                           m, v, adam, step, color, depth, alpha, (cudaStream_t)stream);
@@ -1120,6 +1154,7 @@ gs_status gs_train_step_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_view
 
 gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
                         const gs_raster_cfg* cfg, float* color, float* depth, float* alpha, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_fwd");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
   return render_fwd_views(c, g, 1, cam, view, cfg, &color, &depth, &alpha, (cudaStream_t)stream);
@@ -1128,6 +1163,7 @@ gs_status gs_render_fwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, 
 gs_status gs_render_fwd_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
                                 const gs_viewmat* views, const gs_raster_cfg* cfg, float* const* color,
                                 float* const* depth, float* const* alpha, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_fwd_batched");
   if (!c) return GS_ERR_INVALID_ARG;
   return render_fwd_views(c, g, n_views, cams, views, cfg, color, depth, alpha, (cudaStream_t)stream);
 }
@@ -1136,6 +1172,7 @@ gs_status gs_render_bwd_adam(gs_ctx* c, const gs_gaussians* g, const gs_camera* 
                              const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
                              const float* dL_dalpha, float* params, float* m, float* v, const gs_adam_cfg* adam,
                              int64_t step, float* dL_dpose, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_bwd_adam");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
   return render_bwd_adam_views(c, g, 1, cam, view, cfg, &dL_dcolor, &dL_ddepth, &dL_dalpha, params, m, v, adam, step,
@@ -1147,6 +1184,7 @@ gs_status gs_render_bwd_adam_batched(gs_ctx* c, const gs_gaussians* g, int32_t n
                                      const float* const* dL_dcolor, const float* const* dL_ddepth,
                                      const float* const* dL_dalpha, float* params, float* m, float* v,
                                      const gs_adam_cfg* adam, int64_t step, float* dL_dpose, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_bwd_adam_batched");
   if (!c) return GS_ERR_INVALID_ARG;
   return render_bwd_adam_views(c, g, n_views, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, params, m, v, adam,
                                step, dL_dpose, (cudaStream_t)stream);
@@ -1155,6 +1193,7 @@ gs_status gs_render_bwd_adam_batched(gs_ctx* c, const gs_gaussians* g, int32_t n
 gs_status gs_render_bwd(gs_ctx* c, const gs_gaussians* g, const gs_camera* cam, const gs_viewmat* view,
                         const gs_raster_cfg* cfg, const float* dL_dcolor, const float* dL_ddepth,
                         const float* dL_dalpha, const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_bwd");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cam || !view) return fail(c, GS_ERR_INVALID_ARG, "camera / viewmat is NULL");
   return render_bwd_views(c, g, 1, cam, view, cfg, &dL_dcolor, &dL_ddepth, &dL_dalpha, grads, dL_dpose,
@@ -1165,6 +1204,7 @@ gs_status gs_render_bwd_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_view
                                 const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                                 const float* const* dL_ddepth, const float* const* dL_dalpha,
                                 const gs_grads* grads, float* dL_dpose, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_render_bwd_batched");
   if (!c) return GS_ERR_INVALID_ARG;
   return render_bwd_views(c, g, n_views, cams, views, cfg, dL_dcolor, dL_ddepth, dL_dalpha, grads, dL_dpose,
                           (cudaStream_t)stream);
@@ -1173,6 +1213,7 @@ gs_status gs_render_bwd_batched(gs_ctx* c, const gs_gaussians* g, int32_t n_view
 gs_status gs_loss_l1(gs_ctx* c, const gs_camera* cam, const float* color, const float* depth,
                      const float* target_rgb, const float* target_depth, float w_color, float w_depth, float* loss,
                      float* dL_dcolor, float* dL_ddepth, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_loss_l1");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cam) return fail(c, GS_ERR_INVALID_ARG, "camera is NULL");
   return loss_views(c, 1, cam, &color, &depth, &target_rgb, &target_depth, w_color, w_depth, loss, &dL_dcolor,
@@ -1183,6 +1224,7 @@ gs_status gs_loss_l1_batched(gs_ctx* c, int32_t n_views, const gs_camera* cams, 
                              const float* const* depth, const float* const* target_rgb,
                              const float* const* target_depth, float w_color, float w_depth, float* loss,
                              float* const* dL_dcolor, float* const* dL_ddepth, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_loss_l1_batched");
   if (!c) return GS_ERR_INVALID_ARG;
   return loss_views(c, n_views, cams, color, depth, target_rgb, target_depth, w_color, w_depth, loss, dL_dcolor,
                     dL_ddepth, (cudaStream_t)stream);
@@ -1190,6 +1232,7 @@ gs_status gs_loss_l1_batched(gs_ctx* c, int32_t n_views, const gs_camera* cams, 
 
 gs_status gs_adam_step(gs_ctx* c, float* params, float* grads, float* m, float* v, int64_t n,
                        int32_t sh_degree, const gs_adam_cfg* cfg, int64_t step, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_adam_step");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!cfg || step < 0 || n < 0 || sh_degree < 0 || sh_degree > 3)
     return fail(c, GS_ERR_INVALID_ARG, "gs_adam_step: bad cfg, step, n or sh_degree");
@@ -1220,6 +1263,7 @@ gs_status gs_adam_step(gs_ctx* c, float* params, float* grads, float* m, float* 
 
 gs_status gs_autotune(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const gs_camera* cams,
                       const gs_viewmat* views, gs_raster_cfg* cfg, int32_t reps, float* ms, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_autotune");
   if (!c) return GS_ERR_INVALID_ARG;
   gs_status st;
   if ((st = check_gauss(c, g)) != GS_OK || (st = check_views(c, n_views, cams, views)) != GS_OK ||
@@ -1342,6 +1386,7 @@ gs_status qt_run(gs_ctx* c, const float* rgb, int W, int H, int max_size, int mi
 gs_status gs_quadtree_leaves(gs_ctx* c, const float* rgb, int32_t width, int32_t height, float var_thr,
                              int32_t max_size, int32_t min_size, int32_t* leaves, int64_t capacity, int64_t* n_leaves,
                              gs_stream_t stream) {
+  NvtxRange nvtx_("gs_quadtree_leaves");
   if (!c) return GS_ERR_INVALID_ARG;
   if (!rgb || !n_leaves || capacity < 0) return fail(c, GS_ERR_INVALID_ARG, "gs_quadtree_leaves: bad arguments");
   GS_CUDA(c, cudaSetDevice(c->device));
@@ -1364,6 +1409,7 @@ gs_status gs_seed_quadtree(gs_ctx* c, const float* rgb, const float* depth, cons
                            int32_t max_size, int32_t min_size, float* means, float* log_scales, float* quats,
                            float* opacity_logits, float* sh, int64_t capacity, int64_t* n_seeded,
                            gs_stream_t stream) {
+  NvtxRange nvtx_("gs_seed_quadtree");
   if (!c) return GS_ERR_INVALID_ARG;
   gs_status st;
   if ((st = check_cam(c, cam)) != GS_OK) return st;
@@ -1456,6 +1502,7 @@ bool finite_view(const gs_viewmat* v) {
 
 gs_status gs_tsdf_integrate(gs_ctx* c, const gs_tsdf_grid* grid, const float* depth, const gs_camera* cam,
                             const gs_viewmat* view, uint32_t frame, int64_t min_slot, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_tsdf_integrate");
   if (!c) return GS_ERR_INVALID_ARG;
   gs_status st;
   if ((st = check_grid(c, grid)) != GS_OK || (st = check_cam(c, cam)) != GS_OK) return st;
@@ -1523,6 +1570,7 @@ gs_status gs_seed_tsdf(gs_ctx* c, const float* rgb, const float* depth, const gs
                        const gs_camera* cam, const gs_viewmat* view, int32_t sh_degree, float var_thr,
                        int32_t max_size, int32_t min_size, float* means, float* log_scales, float* quats,
                        float* opacity_logits, float* sh, int64_t capacity, int64_t* n_seeded, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_seed_tsdf");
   if (!c) return GS_ERR_INVALID_ARG;
   gs_status st;
   if ((st = check_cam(c, cam)) != GS_OK || (st = check_grid(c, grid)) != GS_OK) return st;
@@ -1555,6 +1603,7 @@ gs_status gs_seed_tsdf(gs_ctx* c, const float* rgb, const float* depth, const gs
 gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* extent, const float* depth,
                        int32_t width, int32_t height, int32_t tile_w, int32_t tile_h, uint64_t* keys, uint32_t* ids,
                        uint32_t* ranges, int64_t pair_capacity, int64_t* n_pairs, gs_stream_t stream) {
+  NvtxRange nvtx_("gs_bin_tiles");
   if (!c) return GS_ERR_INVALID_ARG;
   if (n < 0 || n >= ((int64_t)1 << 31) || width < 1 || height < 1 || !n_pairs || pair_capacity < 0)
     return fail(c, GS_ERR_INVALID_ARG, "gs_bin_tiles: bad sizes");
@@ -1612,6 +1661,29 @@ gs_status gs_get_projection(gs_ctx* c, float* mean2d, float* cov2d, float* depth
                            (cudaStream_t)stream);
   if (c->st_n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "export projection");
+  return GS_OK;
+}
+
+gs_status gs_ctx_inject_alloc_failure(gs_ctx* c, int32_t after) {
+  if (!c || after < 0) return GS_ERR_INVALID_ARG;
+  c->fail_alloc = after;
+  return GS_OK;
+}
+
+gs_status gs_count_nonfinite(gs_ctx* c, const float* x, int64_t n, int64_t* count, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  NvtxRange nvtx_("gs_count_nonfinite");
+  if (n < 0 || !count || (n > 0 && !x)) return fail(c, GS_ERR_INVALID_ARG, "gs_count_nonfinite: bad arguments");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  if (!c->d_count) GS_CUDA(c, cudaMalloc((void**)&c->d_count, sizeof(unsigned long long)));
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_count_nonfinite(x, n, c->d_count, c->num_sms, s);
+  if (n > 0) c->launches += 1;
+  GS_CHECK_LAUNCH(c, "count non-finite");
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaStreamSynchronize(s));
+  *count = (int64_t)c->h_pinned[0];
+  if (*count > 0) return fail(c, GS_ERR_NONFINITE, "non-finite values found");
   return GS_OK;
 }
 

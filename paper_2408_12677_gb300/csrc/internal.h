@@ -279,4 +279,7 @@ void launch_export_keys_ranges(const uint2* ranges, int n_tiles, const uint32_t*
                                const uint32_t* depth_key_by_id, uint32_t P, uint64_t* keys, uint32_t* ids,
                                cudaStream_t s);
 
+// out (device) = number of non-finite floats in x[0, n)
+void launch_count_nonfinite(const float* x, int64_t n, unsigned long long* out, int num_sms, cudaStream_t s);
+
 }  // namespace gs

@@ -369,4 +369,28 @@ void launch_export_projection(int n, const float4* feat, const uint32_t* tiles, 
                                                            tiles_out);
 }
 
+namespace {
+
+// non-finite floats (NaN, +-Inf) of x[0, n): per-thread counts, a warp sum,
+// one atomic per warp
+__global__ void __launch_bounds__(256) count_nonfinite_kernel(const float* __restrict__ x, int64_t n,
+                                                              unsigned long long* __restrict__ out) {
+  unsigned c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    c += isfinite(x[i]) ? 0u : 1u;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+}  // namespace
+
+void launch_count_nonfinite(const float* x, int64_t n, unsigned long long* out, int num_sms, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (n <= 0) return;
+  const int64_t want = (n + 255) / 256;
+  const int blocks = (int)std::min<int64_t>(want, 8 * (int64_t)std::max(num_sms, 1));
+  count_nonfinite_kernel<<<blocks, 256, 0, s>>>(x, n, out);
+}
+
 }  // namespace gs

@@ -26,6 +26,7 @@ libgsplat; this module moves buffers and chooses views.
 from __future__ import annotations
 
 import dataclasses
+import os
 import time
 
 import numpy as np
@@ -177,6 +178,7 @@ class StreamingOptimizer:
         self.w_color, self.w_depth = float(w_color), float(w_depth)
         self.rng = np.random.default_rng(rng_seed)
         self.keyframes: list[Keyframe] = []
+        self.keyframe_ids: list[int] = []  # position of each keyframe in the processed sequence
         self.step = 0
         H, W = cam.height, cam.width
         dev = torch.device("cuda", device)
@@ -256,6 +258,7 @@ class StreamingOptimizer:
         is_key = k > KEYFRAME_MIN_NEW or not self.keyframes
         if is_key:
             self.keyframes.append(cur)
+            self.keyframe_ids.append(self.frame_index)
         sizes = []
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
@@ -271,6 +274,63 @@ class StreamingOptimizer:
                            fused.get("blocks", 0), fused.get("touched", 0), fused.get("updated", 0))
         self.frame_index += 1
         return stats
+
+
+def save_stream(opt: "StreamingOptimizer", path: str) -> None:
+    """Checkpoint of the loop: the map with its Adam state (flat binary,
+    checkpoint.py) at ``path``, and at ``path + ".state.npz"`` the position in
+    the sequence, the keyframes' positions, the view sampler's state and the
+    TSDF grid."""
+    import json
+
+    from . import checkpoint
+    m = opt.map.model
+    torch.cuda.synchronize()
+    checkpoint.save_map(path, m.flat, m.m, m.v, m.n, opt.map.sh_degree, opt.step, opt.map.n)
+    meta = {"frame_index": opt.frame_index, "step": opt.step, "novelty": opt.novelty,
+            "rng": opt.rng.bit_generator.state}
+    arrays = {"meta": np.frombuffer(json.dumps(meta).encode(), np.uint8),
+              "keyframe_ids": np.asarray(opt.keyframe_ids, np.int64)}
+    if opt.tsdf is not None:
+        st = opt.tsdf.state()
+        arrays.update({f"tsdf_{k}": np.asarray(v) for k, v in st.items()})
+    tmp = f"{path}.state.tmp{os.getpid()}.npz"
+    np.savez(tmp, **arrays)
+    os.replace(tmp, path + ".state.npz")
+
+
+def load_stream(opt: "StreamingOptimizer", path: str, frames) -> None:
+    """Resumes ``opt`` (built with the same camera, SH degree and options)
+    from ``save_stream``'s files; ``frames(i) -> (rgb, depth, pose)`` gives
+    frame i of the sequence, for the keyframes' images."""
+    import json
+
+    from . import checkpoint
+    d = checkpoint.load_map(path)
+    if d["sh_degree"] != opt.map.sh_degree:
+        raise ValueError("checkpoint SH degree differs from the optimizer's")
+    st = np.load(path + ".state.npz")
+    meta = json.loads(bytes(st["meta"]).decode())
+    opt.map = GrowingMap(opt.map.sh_degree, d["n_slots"], opt.map.device)
+    m = opt.map.model
+    for dst, key in ((m.flat, "flat"), (m.m, "m"), (m.v, "v")):
+        dst.copy_(torch.from_numpy(d[key]).to(dst.device))
+    opt.map.n = d["n_live"]
+    opt.step = d["step"]
+    opt.frame_index = int(meta["frame_index"])
+    opt.rng.bit_generator.state = meta["rng"]
+    dev = m.flat.device
+    opt.keyframes, opt.keyframe_ids = [], []
+    for i in st["keyframe_ids"].tolist():
+        rgb, depth, pose = frames(int(i))
+        opt.keyframes.append(Keyframe(opt.cam, abi.make_viewmat(pose.R, pose.t),
+                                      torch.as_tensor(np.ascontiguousarray(np.transpose(rgb, (2, 0, 1)),
+                                                                           np.float32), device=dev),
+                                      torch.as_tensor(np.ascontiguousarray(depth, np.float32), device=dev)))
+        opt.keyframe_ids.append(int(i))
+    if opt.tsdf is not None:
+        opt.tsdf.load_state({k[5:]: st[k] for k in st.files if k.startswith("tsdf_")})
+    torch.cuda.synchronize()
 
 
 @dataclasses.dataclass

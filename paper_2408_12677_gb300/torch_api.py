@@ -82,6 +82,35 @@ def camera_struct(cam) -> abi.gs_camera:
     return abi.make_camera(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
 
 
+def save_trainer(tr, path: str) -> None:
+    """Checkpoint of a trainer's map, Adam moments and step (checkpoint.py)."""
+    from . import checkpoint
+    m = tr.model
+    torch.cuda.synchronize()
+    checkpoint.save_map(path, m.flat, m.m, m.v, m.n, m.sh_degree, tr.step_count)
+
+
+def nonfinite_params(tr) -> int:
+    """Number of NaN / +-Inf values among a trainer's parameters."""
+    return abi.gs_count_nonfinite(tr.ctx.handle, tr.model.flat)
+
+
+def load_trainer(tr, path: str) -> None:
+    """Resumes a trainer from ``save_trainer``'s file: the map must have the
+    same size and SH degree; the context's device Adam step is set too."""
+    from . import checkpoint
+    d = checkpoint.load_map(path)
+    m = tr.model
+    if d["n_slots"] != m.n or d["sh_degree"] != m.sh_degree:
+        raise ValueError(f"checkpoint holds {d['n_slots']} Gaussians of SH degree {d['sh_degree']}, "
+                         f"the trainer {m.n} of degree {m.sh_degree}")
+    for dst, key in ((m.flat, "flat"), (m.m, "m"), (m.v, "v")):
+        dst.copy_(torch.from_numpy(d[key]).to(dst.device))
+    tr.step_count = d["step"]
+    abi.gs_ctx_set_adam_step(tr.ctx.handle, d["step"])
+    torch.cuda.synchronize()
+
+
 class Context:
     """Owns one gs_ctx handle."""
 
@@ -251,6 +280,15 @@ class Trainer:
         """Raises GsError(GS_ERR_CAPACITY) if a no-sync pass dropped pairs."""
         abi.gs_sync_status(self.ctx.handle)
 
+    def save(self, path: str) -> None:
+        save_trainer(self, path)
+
+    def load(self, path: str) -> None:
+        load_trainer(self, path)
+
+    def nonfinite(self) -> int:
+        return nonfinite_params(self)
+
 
 class BatchedTrainer:
     """Several views, one map: one batched iteration per ``step``.
@@ -409,6 +447,15 @@ class BatchedTrainer:
 
     def check_capacity(self):
         abi.gs_sync_status(self.ctx.handle)
+
+    def save(self, path: str) -> None:
+        save_trainer(self, path)
+
+    def load(self, path: str) -> None:
+        load_trainer(self, path)
+
+    def nonfinite(self) -> int:
+        return nonfinite_params(self)
 
 
 class _Render(torch.autograd.Function):

@@ -136,6 +136,46 @@ class TSDFGrid:
         return abi.gs_seed_tsdf(self.ctx.handle, rgb, depth, self.struct(), cam, view, sh_degree, var_thr, max_size,
                                 min_size, means, log_scales, quats, opacity_logits, sh, capacity)
 
+    # -- checkpoint --------------------------------------------------------
+    def state(self) -> dict:
+        """Host copy of the grid for a checkpoint: the live (key, slot) pairs,
+        the voxels of the allocated slots, the frame counter and counters."""
+        torch.cuda.synchronize()
+        keys = self.keys.cpu().numpy()
+        live = np.nonzero(keys != -1)[0]
+        return {"keys": keys[live], "slots": self.slots.cpu().numpy()[live],
+                "voxels": self.voxels[:self.n_blocks].cpu().numpy(), "frame": self.frame,
+                "n_blocks": self.n_blocks, "updated": self.updated,
+                "params": [self.voxel_size, self.truncation, self.max_weight, self.fusion]}
+
+    def load_state(self, st: dict) -> None:
+        """Restores ``state()``: a table sized for the blocks, rebuilt on the
+        device from the saved (key, slot) pairs (gs_tsdf_rehash from a
+        compact table), and the voxels."""
+        n_blocks = int(st["n_blocks"])
+        self.voxel_size, self.truncation, self.max_weight, self.fusion = (float(st["params"][0]),
+                                                                          float(st["params"][1]),
+                                                                          float(st["params"][2]),
+                                                                          int(st["params"][3]))
+        self._new_pool(max(_pow2(max(n_blocks, 1)), self.capacity))
+        if n_blocks:
+            self.voxels[:n_blocks] = torch.as_tensor(np.asarray(st["voxels"], np.float32), device=self.device)
+        self.n_blocks, self.updated, self.frame = n_blocks, int(st["updated"]), int(st["frame"])
+        self._new_table(_pow2(max(2 * n_blocks, 1 << 16)))
+        keys = np.asarray(st["keys"], np.int64)
+        if keys.size:
+            size = _pow2(max(keys.size, 2))
+            src_keys = torch.full((size,), -1, dtype=torch.int64, device=self.device)
+            src_slots = torch.zeros(size, dtype=torch.int32, device=self.device)
+            src_keys[:keys.size] = torch.as_tensor(keys, device=self.device)
+            src_slots[:keys.size] = torch.as_tensor(np.asarray(st["slots"], np.int32), device=self.device)
+            src = self.struct()
+            src.keys, src.slots, src.table_size = src_keys.data_ptr(), src_slots.data_ptr(), size
+            abi.gs_tsdf_rehash(self.ctx.handle, src, self.struct())
+            torch.cuda.synchronize()
+        c = torch.tensor([n_blocks, 0, 0, self.updated], dtype=torch.int64).to(torch.int32)
+        self.counters.copy_(c.to(self.device))
+
     # -- read-out ----------------------------------------------------------
     def blocks(self) -> dict:
         """{(bx, by, bz): (tsdf [8, 8, 8], weight [8, 8, 8])} indexed [z, y, x]
