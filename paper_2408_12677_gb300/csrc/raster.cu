@@ -191,10 +191,19 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       // (a blend of weight 0 leaves R, G, B, D unchanged)
       // both rows as straight-line code (independent chains; a row outside the
       // support box runs with weight 0)
-      blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, halves & 1u, T0, R0, G0, B0, D0, last0, done0, n_visit,
-                        n_blend);
-      blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, halves & 2u, T1, R1, G1, B1, D1, last1, done1, n_visit,
-                        n_blend);
+      // a half the support box misses (warp-uniform) is skipped
+      if (halves == 3u) {
+        blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, true, T0, R0, G0, B0, D0, last0, done0, n_visit,
+                          n_blend);
+        blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, true, T1, R1, G1, B1, D1, last1, done1, n_visit,
+                          n_blend);
+      } else if (halves == 1u) {
+        blend_slot<COUNT>(a, bb, c, plx, ply0, rp, c0 + j + 1, true, T0, R0, G0, B0, D0, last0, done0, n_visit,
+                          n_blend);
+      } else {
+        blend_slot<COUNT>(a, bb, c, plx, ply1, rp, c0 + j + 1, true, T1, R1, G1, B1, D1, last1, done1, n_visit,
+                          n_blend);
+      }
     }
   }
   if (COUNT) {
