@@ -534,12 +534,26 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
       const unsigned halves = __float_as_uint(cc.w);
       // both pixel rows' exponents first, then the rows' steps as straight-line
       // code (independent chains); skipped when no lane of the warp takes part
-      const PixQ e0 = pixel_q(a, bb, plx, ply0, (halves & 1u) && idx < last0);
-      const PixQ e1 = pixel_q(a, bb, plx, ply1, (halves & 2u) && idx < last1);
-      const bool contrib = e0.pass || e1.pass;
-      if (!__any_sync(kFull, contrib)) continue;
-      if (halves & 1u) bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
-      if (halves & 2u) bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+      // a half the support box misses (warp-uniform) is skipped
+      bool contrib;
+      if (halves == 3u) {
+        const PixQ e0 = pixel_q(a, bb, plx, ply0, idx < last0);
+        const PixQ e1 = pixel_q(a, bb, plx, ply1, idx < last1);
+        contrib = e0.pass || e1.pass;
+        if (!__any_sync(kFull, contrib)) continue;
+        bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+        bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+      } else if (halves == 1u) {
+        const PixQ e0 = pixel_q(a, bb, plx, ply0, idx < last0);
+        contrib = e0.pass;
+        if (!__any_sync(kFull, contrib)) continue;
+        bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+      } else {
+        const PixQ e1 = pixel_q(a, bb, plx, ply1, idx < last1);
+        contrib = e1.pass;
+        if (!__any_sync(kFull, contrib)) continue;
+        bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+      }
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;
       float* rec = g2d + 12 * (size_t)bid[j];
