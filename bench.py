@@ -701,6 +701,23 @@ def oracle_projection(w):
             oadam.flatten(w.params), oadam.lr_per_element(w.n, w.sh_degree, cfg))
 
 
+def gaussians_near_pixels(mu, rad, pix, W, H):
+    """Mask of the Gaussians whose box mu +- rad holds the centre of one of
+    the pixels pix [k, 2] (x, y), through a summed-area table of the pixels."""
+    import numpy as np
+    occ = np.zeros((H + 1, W + 1), np.int64)
+    np.add.at(occ, (pix[:, 1] + 1, pix[:, 0] + 1), 1)
+    occ = occ.cumsum(0).cumsum(1)
+    x0 = np.clip(np.ceil(mu[:, 0] - rad - 0.5), 0, W).astype(np.int64)
+    x1 = np.clip(np.floor(mu[:, 0] + rad - 0.5), -1, W - 1).astype(np.int64)
+    y0 = np.clip(np.ceil(mu[:, 1] - rad - 0.5), 0, H).astype(np.int64)
+    y1 = np.clip(np.floor(mu[:, 1] + rad - 0.5), -1, H - 1).astype(np.int64)
+    ok = (x1 >= x0) & (y1 >= y0)
+    x0, x1, y0, y1 = np.minimum(x0, W - 1), np.maximum(x1, 0), np.minimum(y0, H - 1), np.maximum(y1, 0)
+    hits = occ[y1 + 1, x1 + 1] - occ[y0, x1 + 1] - occ[y1 + 1, x0] + occ[y0, x0]
+    return ok & (hits > 0)
+
+
 def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
     """Time the FP64 oracle on a bounded sample of one iteration: forward +
     backward over n_pix random pixels (prefilter mode) with the Gaussians
@@ -729,17 +746,7 @@ def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
     Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
     # the Gaussians whose 3-sigma box holds a sampled pixel centre (the others
     # cannot take part in those pixels)
-    occ = np.zeros((H + 1, W + 1), np.int64)  # summed-area table of the sampled pixels
-    np.add.at(occ, (pix[:, 1] + 1, pix[:, 0] + 1), 1)
-    occ = occ.cumsum(0).cumsum(1)
-    x0 = np.clip(np.ceil(mu[:, 0] - rad - 0.5), 0, W).astype(np.int64)
-    x1 = np.clip(np.floor(mu[:, 0] + rad - 0.5), -1, W - 1).astype(np.int64)
-    y0 = np.clip(np.ceil(mu[:, 1] - rad - 0.5), 0, H).astype(np.int64)
-    y1 = np.clip(np.floor(mu[:, 1] + rad - 0.5), -1, H - 1).astype(np.int64)
-    ok = (x1 >= x0) & (y1 >= y0)
-    x0, x1, y0, y1 = np.minimum(x0, W - 1), np.maximum(x1, 0), np.minimum(y0, H - 1), np.maximum(y1, 0)
-    hits = occ[y1 + 1, x1 + 1] - occ[y0, x1 + 1] - occ[y1 + 1, x0] + occ[y0, x0]
-    near = ok & (hits > 0)
+    near = gaussians_near_pixels(mu, rad, pix, W, H)
     sub = {k: np.asarray(w.params[k])[idx[near]] for k in R.PARAM_NAMES}
     t1 = time.perf_counter()
     R.weighted_pixel_gradients(sub, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
