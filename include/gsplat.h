@@ -2,7 +2,10 @@
  * gsplat.h -- C ABI of the GB300 (sm_103a) differentiable 3D Gaussian
  * splatting hot path of GSFusion (arXiv 2408.12677): the tile-based
  * rasterizer forward and backward pass and the Adam update of the Gaussian
- * parameters (Sec. III-B.3 "Online Optimization").
+ * parameters (Sec. III-B.3 "Online Optimization"), for one view or a batch
+ * of views, and the per-frame steps around it: TSDF fusion (Sec. III-B.1,
+ * Eq. 6-9), quadtree seeding with the voxel-weight or rendered-alpha
+ * novelty check (Sec. III-B.2, Eq. 10), and host-side failure detection.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
