@@ -24,6 +24,13 @@ def _pow2(n: int) -> int:
     return 1 << max(1, int(n - 1).bit_length())
 
 
+def band_samples(truncation: float, voxel_size: float) -> int:
+    """Samples per ray of the allocation (as gs_tsdf_integrate takes them):
+    n + 1 with n = ceil(eps / 2s), float32 eps and s."""
+    e, s = float(np.float32(truncation)), float(np.float32(voxel_size))
+    return max(1, math.ceil(e / (2.0 * s) - 1e-6)) + 1
+
+
 class TSDFGrid:
     """Single-resolution TSDF grid: voxels of ``voxel_size`` metres in blocks
     of 8^3, truncation ``truncation`` metres, weights capped at
@@ -67,7 +74,7 @@ class TSDFGrid:
 
     @property
     def band_samples(self) -> int:
-        return max(1, math.ceil(self.truncation / (2.0 * self.voxel_size) - 1e-6)) + 1
+        return band_samples(self.truncation, self.voxel_size)
 
     def reserve(self, n_pixels: int):
         """Grow the hash table so that a frame of ``n_pixels`` cannot fill it
