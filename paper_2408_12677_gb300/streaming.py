@@ -309,8 +309,11 @@ def load_stream(opt: "StreamingOptimizer", path: str, frames) -> None:
     d = checkpoint.load_map(path)
     if d["sh_degree"] != opt.map.sh_degree:
         raise ValueError("checkpoint SH degree differs from the optimizer's")
-    st = np.load(path + ".state.npz")
+    with np.load(path + ".state.npz") as f:
+        st = {k: f[k] for k in f.files}
     meta = json.loads(bytes(st["meta"]).decode())
+    if meta["novelty"] != opt.novelty:
+        raise ValueError(f"checkpoint of a {meta['novelty']!r} loop, the optimizer uses {opt.novelty!r}")
     opt.map = GrowingMap(opt.map.sh_degree, d["n_slots"], opt.map.device)
     m = opt.map.model
     for dst, key in ((m.flat, "flat"), (m.m, "m"), (m.v, "v")):
@@ -329,7 +332,7 @@ def load_stream(opt: "StreamingOptimizer", path: str, frames) -> None:
                                       torch.as_tensor(np.ascontiguousarray(depth, np.float32), device=dev)))
         opt.keyframe_ids.append(int(i))
     if opt.tsdf is not None:
-        opt.tsdf.load_state({k[5:]: st[k] for k in st.files if k.startswith("tsdf_")})
+        opt.tsdf.load_state({k[5:]: v for k, v in st.items() if k.startswith("tsdf_")})
     torch.cuda.synchronize()
 
 
