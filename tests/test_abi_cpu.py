@@ -78,3 +78,36 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    """Every struct the binding passes by pointer has the size and field
+    offsets a C compiler gives the header's declaration."""
+    import shutil
+    import subprocess
+    from paper_2408_12677_gb300 import abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [abi.gs_camera, abi.gs_viewmat, abi.gs_gaussians, abi.gs_grads, abi.gs_raster_cfg, abi.gs_adam_cfg,
+               abi.gs_stats, abi.gs_tsdf_grid]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsplat.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, key, value = line.split()
+        got[(name, key)] = int(value)
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "size")] == C.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
