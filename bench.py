@@ -591,6 +591,10 @@ def run_streaming(args, rank, world, local_rank):
                                + ", 10 batched iterations per frame over the frame and up to 4 "
                                "random earlier keyframes, SH degree 3, fp32",
                    "frames": args.frames, "seeding": seeding, "novelty": novelty,
+                   "tsdf_grid": None if opt.tsdf is None else {
+                       "voxel_size_m": opt.tsdf.voxel_size, "truncation_m": opt.tsdf.truncation,
+                       "max_weight": opt.tsdf.max_weight,
+                       "eq9": "as printed" if opt.tsdf.fusion == 0 else "unit measurement weight"},
                    "seeding_on": "host" if args.host_seeding else "device", "host_generation_s": t_gen,
                    "parallelism": f"replicas{world}", "timing": "CUDA events around each frame's iterations"},
         "stream": {
