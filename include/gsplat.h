@@ -207,8 +207,14 @@ gs_status gs_render_fwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam
                         const gs_viewmat *view, const gs_raster_cfg *cfg,
                         float *color, float *depth, float *alpha, gs_stream_t stream);
 
-/* Backward pass of the most recent gs_render_fwd on this context (same g,
- * cam, view, cfg; GS_ERR_STATE otherwise).  Walks every tile list back to
+/* Backward pass of the forward state the context holds: the most recent
+ * gs_render_fwd (or batched forward, or training step) on this context.  That
+ * state must have been computed from the same Gaussian arrays (the same five
+ * pointers, n and SH degree), byte-identical cameras, poses and raster
+ * configuration; anything else returns GS_ERR_STATE with nothing enqueued
+ * (e.g. two renders at two poses followed by the backward pass of the first).
+ * The parameter VALUES are not compared: changing them in place between the
+ * forward and the backward pass is the caller's error.  Walks every tile list back to
  * front from the stored last contributor, recomputing transmittance from the
  * stored final T.  dL_dcolor [3, H, W] and dL_ddepth [H, W] are required,
  * dL_dalpha [H, W] may be NULL.  Gradients w.r.t. every parameter array are
@@ -219,6 +225,12 @@ gs_status gs_render_bwd(gs_ctx *ctx, const gs_gaussians *g, const gs_camera *cam
                         const gs_viewmat *view, const gs_raster_cfg *cfg,
                         const float *dL_dcolor, const float *dL_ddepth, const float *dL_dalpha,
                         const gs_grads *grads, float *dL_dpose, gs_stream_t stream);
+
+/* Token of the forward state the context holds (0 = none): distinct for
+ * every forward pass on the context, so a caller that keeps the token of its
+ * own forward pass can tell whether the state is still its own before calling
+ * a backward pass (and re-run its forward pass if not). */
+gs_status gs_state_token(const gs_ctx *ctx, uint64_t *token);
 
 /* One single-view optimisation iteration's backward half (Sec. III-B.3:
  * each iteration optimises the map on one frame): the backward pass of the
@@ -539,6 +551,27 @@ gs_status gs_seed_tsdf(gs_ctx *ctx, const float *rgb, const float *depth, const 
  * scratch group, which the next call allocates again). */
 gs_status gs_count_nonfinite(gs_ctx *ctx, const float *x, int64_t n, int64_t *count, gs_stream_t stream);
 gs_status gs_ctx_inject_alloc_failure(gs_ctx *ctx, int32_t after);
+
+/* Measured issue rates of the two ALU pipes the raster passes run on (no
+ * counterpart in the paper: they are the denominators of the raster passes'
+ * ALU roofline).  On device `device`, a fully occupied grid runs eight
+ * independent chains per thread of FP32 FMA (iters x 128 per thread) and
+ * then of MUFU ex2.approx (iters / 4 x 128 per thread), each timed with CUDA
+ * events after a warm-up launch; one thread reads the SM cycle counter and
+ * the global timer around its loop, which gives the SM clock of the run.
+ * iters in [1, 2^24]; about 50 ms per probe at iters = 50000 on a GB300.
+ * Synchronises the device; allocates 36 bytes of device memory for the run. */
+typedef struct {
+  double fma_tflops;     /* 2 flop per FMA lane-instruction, whole GPU, TFLOP/s */
+  double ex2_gops;       /* ex2 lane-results per second, whole GPU, G/s */
+  double fma_sm_mhz;     /* SM clock during the FMA probe */
+  double ex2_sm_mhz;     /* SM clock during the ex2 probe */
+  double fma_per_sm_clk; /* FMA lane-instructions per SM per clock */
+  double ex2_per_sm_clk; /* ex2 lane-results per SM per clock */
+  double fma_ms, ex2_ms; /* event time of each timed launch */
+  int32_t num_sms;       /* multiprocessors of the device */
+} gs_alu_peaks;
+gs_status gs_measure_alu_peaks(int device, int32_t iters, gs_alu_peaks *out);
 
 /* Copy the last forward pass's projected per-Gaussian quantities to caller
  * buffers (each nullable), n = views x Gaussians items, item v * N + i being

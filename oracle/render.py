@@ -199,19 +199,40 @@ def pixel_centers(cam) -> torch.Tensor:
     return torch.stack([ii.flatten() + 0.5, jj.flatten() + 0.5], -1)
 
 
-def composite(proj: dict, U: torch.Tensor, cfg: RasterCfg = RasterCfg(), prefilter: bool = False,
-              chunk_elems: int = 1 << 21):
-    """Front-to-back compositing at pixel centres U [M, 2] (Eq. 11), no tiling."""
+def composite(proj: dict, U: torch.Tensor, cfg: RasterCfg = RasterCfg(), prefilter=False,
+              chunk_elems: int = 1 << 21, chunk_px: int = 256):
+    """Front-to-back compositing at pixel centres U [M, 2] (Eq. 11), no tiling.
+
+    ``prefilter``: False evaluates every Gaussian at every pixel; True drops,
+    per chunk of pixels, the Gaussians whose q exceeds 9 at every pixel of
+    the chunk; "bbox" takes the pixels ``chunk_px`` at a time (pass them
+    grouped by image region) and keeps the Gaussians whose q <= 9 ellipse's
+    bounding box, mu +- 3 sqrt(diag Sigma^), meets the chunk's bounding box
+    -- the others have q > 9 at every pixel of the chunk.  Dropped Gaussians
+    contribute exactly nothing, so all three give the same values."""
     o = proj["order"]
     mu, conic, opac = proj["mean2d"][o], proj["conic"][o], proj["opacity"][o]
     rgb, z = proj["rgb"][o], proj["depth"][o]
     n = mu.shape[0]
     M = U.shape[0]
     cols, deps, Ts, ns = [], [], [], []
-    step = max(1, chunk_elems // max(n, 1))
+    if prefilter == "bbox":
+        cov = proj["cov2d"][o].detach()
+        ext = torch.stack([torch.sqrt(cfg.q_max * cov[:, 0, 0]), torch.sqrt(cfg.q_max * cov[:, 1, 1])], -1)
+        ext = ext * (1 + 1e-9) + 1e-9
+        step = chunk_px
+    else:
+        step = max(1, chunk_elems // max(n, 1))
     for s in range(0, M, step):
         Uc = U[s:s + step]
-        if prefilter and n > 0:
+        if prefilter == "bbox" and n > 0:
+            with torch.no_grad():
+                lo, hi = Uc.min(0).values, Uc.max(0).values
+                m = mu.detach()
+                gap = torch.maximum(lo[None] - m, m - hi[None]).clamp(min=0.0)
+                use = torch.nonzero((gap <= ext).all(1)).flatten()
+            c, d, T, k = _composite_chunk(Uc, mu[use], conic[use], opac[use], rgb[use], z[use], cfg)
+        elif prefilter and n > 0:
             with torch.no_grad():
                 qc = _quad_form(Uc, mu.detach(), conic.detach())
                 use = torch.nonzero((qc <= cfg.q_max).any(0)).flatten()
@@ -225,8 +246,22 @@ def composite(proj: dict, U: torch.Tensor, cfg: RasterCfg = RasterCfg(), prefilt
     return torch.cat(cols), torch.cat(deps), torch.cat(Ts), torch.cat(ns)
 
 
+def tile_pixels(cam, tiles, tile_w: int = 16, tile_h: int = 16) -> np.ndarray:
+    """Integer (i, j) pixel coordinates [M, 2] of the listed tiles (tile
+    index = ty * tiles_x + tx), tile by tile, clipped to the image: pass them
+    with prefilter="bbox" and chunk_px = tile_w * tile_h."""
+    tx = -(-cam.width // tile_w)
+    out = []
+    for t in tiles:
+        x0, y0 = (int(t) % tx) * tile_w, (int(t) // tx) * tile_h
+        jj, ii = np.meshgrid(np.arange(y0, min(y0 + tile_h, cam.height)),
+                             np.arange(x0, min(x0 + tile_w, cam.width)), indexing="ij")
+        out.append(np.stack([ii.ravel(), jj.ravel()], 1))
+    return np.concatenate(out) if out else np.zeros((0, 2), np.int64)
+
+
 def render(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = RasterCfg(), pixels=None,
-           prefilter: bool = False) -> dict:
+           prefilter=False, chunk_px: int = 256) -> dict:
     """Render colour [3, M], depth [M], alpha [M] (M = H*W unless ``pixels``
     [M, 2] integer (i, j) coordinates are given).  Full images are reshaped to
     [3, H, W] / [H, W]."""
@@ -235,7 +270,7 @@ def render(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = RasterCfg(
         U = pixel_centers(cam)
     else:
         U = torch.as_tensor(np.asarray(pixels), dtype=DT) + 0.5
-    color, depth, T, ncon = composite(proj, U, cfg, prefilter)
+    color, depth, T, ncon = composite(proj, U, cfg, prefilter, chunk_px=chunk_px)
     out = {"color": color.T.contiguous(), "depth": depth, "alpha": 1.0 - T, "T_final": T, "n_contrib": ncon}
     if pixels is None:
         H, W = cam.height, cam.width
@@ -293,7 +328,8 @@ def gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, target_rgb, target_
 
 
 def weighted_pixel_gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, pixels, w_color, w_depth,
-                             w_alpha=None, rcfg=RasterCfg(), with_pose: bool = True, prefilter: bool = True):
+                             w_alpha=None, rcfg=RasterCfg(), with_pose: bool = True, prefilter=True,
+                             chunk_px: int = 256):
     """Gradient of sum_s <w_color[:, s], C(u_s)> + w_depth[s] D(u_s) + w_alpha[s] A(u_s)
     over the listed pixels only (a sparse upstream gradient)."""
     P = to_tensors(params, requires_grad=True)
@@ -302,7 +338,7 @@ def weighted_pixel_gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, pixe
     xi = torch.zeros(6, dtype=DT, requires_grad=True)
     if with_pose:
         R, t = perturb_pose(R, t, xi)
-    out = render(P, sh_degree, cam, R, t, rcfg, pixels=pixels, prefilter=prefilter)
+    out = render(P, sh_degree, cam, R, t, rcfg, pixels=pixels, prefilter=prefilter, chunk_px=chunk_px)
     obj = (out["color"] * torch.as_tensor(np.asarray(w_color), dtype=DT)).sum()
     obj = obj + (out["depth"] * torch.as_tensor(np.asarray(w_depth), dtype=DT)).sum()
     if w_alpha is not None:
@@ -382,6 +418,87 @@ def multiview_weighted_gradients(params: dict, sh_degree: int, cams, poses, w_co
     return grads
 
 
+# ----------------------------------------------------------------------------
+# distances to the decision thresholds (for the float32 / float64 flip audit)
+# ----------------------------------------------------------------------------
+MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99")
+
+
+def decision_margins(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = RasterCfg(), pixels=None,
+                     chunk_elems: int = 1 << 21) -> dict:
+    """Relative float64 distances of the compositing decisions (Eq. 11 with
+    the support, skip, stop and clamp rules) to their thresholds: for a
+    (pixel, Gaussian) pair near or inside the support, |q - 9| / 9, and where
+    q <= 9, |alpha - 1/255| / (1/255) and |alpha - 0.99| / 0.99 (alpha before
+    the clamp); for a pixel, |T (1 - alpha) - 1e-4| / 1e-4 over its active
+    Gaussians (those with q <= 9 and alpha >= 1/255).  A float32 evaluation
+    can take a decision the other way only where this distance is within its
+    rounding error.  Returns per pixel (M = H*W unless ``pixels`` [M, 2]):
+    ``pixel`` the smallest distance over its pairs and its stop test,
+    ``pixel_kind`` (index into MARGIN_KINDS), ``pixel_gid`` (the Gaussian);
+    per Gaussian (parameter index): ``gauss`` the smallest distance over the
+    pixels where it is active or near its support, counting each such
+    pixel's stop test too (a stop that flips changes the gradient of every
+    Gaussian the pixel reaches), and ``gauss_kind``."""
+    with torch.no_grad():
+        T = to_tensors(P)
+        proj = project(T, sh_degree, cam, torch.as_tensor(np.asarray(R_cw), dtype=DT),
+                       torch.as_tensor(np.asarray(t_cw), dtype=DT), cfg)
+        U = pixel_centers(cam) if pixels is None else torch.as_tensor(np.asarray(pixels), dtype=DT) + 0.5
+        o = proj["order"]
+        mu, conic, opac = proj["mean2d"][o], proj["conic"][o], proj["opacity"][o]
+        gid = proj["idx"][o]
+        n, M = mu.shape[0], U.shape[0]
+        N = P["means"].shape[0]
+        inf = torch.full((), float("inf"), dtype=DT)
+        pix = torch.full((M,), float("inf"), dtype=DT)
+        pix_kind = torch.zeros(M, dtype=torch.long)
+        pix_gid = torch.full((M,), -1, dtype=torch.long)
+        gm = torch.full((max(n, 1),), float("inf"), dtype=DT)
+        gk = torch.zeros(max(n, 1), dtype=torch.long)
+        step = max(1, chunk_elems // max(n, 1))
+        for s0 in range(0, M, step if n else M or 1):
+            if n == 0:
+                break
+            q = _quad_form(U[s0:s0 + step], mu, conic)
+            araw = opac[None, :] * torch.exp(-0.5 * q)
+            near = q <= cfg.q_max * (1 + 1e-3)
+            inside = q <= cfg.q_max
+            m_q = torch.where(near, torch.abs(q - cfg.q_max) / cfg.q_max, inf)
+            m_a = torch.where(inside, torch.abs(araw - cfg.alpha_min) / cfg.alpha_min, inf)
+            m_c = torch.where(inside, torch.abs(araw - cfg.alpha_max) / cfg.alpha_max, inf)
+            alpha = torch.clamp(araw, max=cfg.alpha_max)
+            active = inside & (alpha >= cfg.alpha_min)
+            a = torch.where(active, alpha, torch.zeros_like(alpha))
+            T_incl = torch.cumprod(1.0 - a, dim=1)
+            T_excl = torch.cat([torch.ones_like(T_incl[:, :1]), T_incl[:, :-1]], 1)
+            m_t = torch.where(active, torch.abs(T_excl * (1.0 - a) - cfg.t_eps) / cfg.t_eps, inf)
+            pair = torch.stack([m_q, m_a, m_t, m_c], 0)        # [4, chunk, n]
+            pair_min, pair_kind = pair.min(0)                 # [chunk, n]
+            stop_min = m_t.min(1).values                      # [chunk]
+            pm, pj = pair_min.min(1)                          # per pixel
+            pk = pair_kind.gather(1, pj[:, None])[:, 0]
+            sl = slice(s0, s0 + step)
+            pix[sl], pix_kind[sl], pix_gid[sl] = pm, pk, gid[pj]
+            # per Gaussian: its own pair decisions and the stop test of every
+            # pixel where it is active or near its support
+            touch = near | active
+            with_stop = torch.where(touch, torch.minimum(pair_min, stop_min[:, None]), inf)
+            kind_ws = torch.where(pair_min <= stop_min[:, None], pair_kind, torch.full_like(pair_kind, 2))
+            cm, ci = with_stop.min(0)
+            ck = kind_ws.gather(0, ci[None, :])[0]
+            better = cm < gm[:n]
+            gm[:n] = torch.where(better, cm, gm[:n])
+            gk[:n] = torch.where(better, ck, gk[:n])
+        gauss = torch.full((N,), float("inf"), dtype=DT)
+        gauss_kind = torch.zeros(N, dtype=torch.long)
+        if n:
+            gauss[gid] = gm[:n]
+            gauss_kind[gid] = gk[:n]
+    return {"pixel": pix.numpy(), "pixel_kind": pix_kind.numpy(), "pixel_gid": pix_gid.numpy(),
+            "gauss": gauss.numpy(), "gauss_kind": gauss_kind.numpy()}
+
+
 def gaussian_pixel_evals(out: dict) -> int:
     """E_alg: number of (pixel, Gaussian) pairs that were blended."""
     return int(out["n_contrib"].sum())
@@ -391,5 +508,5 @@ __all__ = [
     "RasterCfg", "LossCfg", "to_tensors", "quat_to_rotmat", "covariance_3d", "se3_exp", "perturb_pose",
     "project", "composite", "render", "loss_l1", "loss_image_grads", "render_loss", "gradients",
     "weighted_pixel_gradients", "pixel_centers", "gaussian_pixel_evals", "multiview_gradients",
-    "multiview_weighted_gradients",
+    "multiview_weighted_gradients", "decision_margins", "MARGIN_KINDS", "tile_pixels",
 ]

@@ -29,13 +29,18 @@ Definition followed, with the readings where the paper is silent:
   Eq. 9 as printed: tsdf_k = (tsdf_{k-1} w_{k-1} + tsdf w_k) / (w_{k-1} + w_k).
   ``fusion="unit"`` instead weights the new measurement by 1, as in
   KinectFusion: (tsdf_{k-1} w_{k-1} + tsdf) / (w_{k-1} + 1).
-* The integer decisions (which block a sample falls in, which pixel a voxel
-  projects to, whether it is updated, which voxel p_q falls in) are taken in
-  float32 with a fixed order of correctly rounded operations, the precision
-  of the kernels: the same decisions on both sides.  The tsdf values are
-  float64.
-* Novelty (Sec. III-B.2): a quadtree leaf whose Eq. 10 point p_q (float32,
-  fixed operation order) lies in a voxel of weight exactly 1 after this
+* Every quantity is evaluated in float64 on the float32 values the kernels
+  receive (depth image, pose, intrinsics, voxel size, truncation): the
+  integer decisions (the block of a sample, the pixel of a voxel, whether it
+  is updated, the voxel of p_q) are those of the exact arithmetic, up to
+  float64 rounding.  Where a float32 implementation may decide the other way
+  (a value within its rounding error of a boundary), the oracle reports how
+  far the float64 value lies from the boundary: ``allocation_samples`` gives
+  every sample's block coordinates as reals, every voxel keeps the smallest
+  distance of its projection to a pixel edge or the image border (pixels)
+  and of its sdf to -eps (metres) over the frames that reached it, and
+  ``leaf_points`` gives each Eq. 10 point's distance to a voxel face.
+* Novelty (Sec. III-B.2): a quadtree leaf whose Eq. 10 point p_q lies in a voxel of weight exactly 1 after this
   frame's integration is new; a voxel of a block that is not allocated
   counts as weight 0 (not new).  A voxel holds at most one Gaussian
   (Sec. IV-C.1): among the new leaves that fall in one voxel, the one whose
@@ -59,46 +64,73 @@ def n_band_steps(eps: float, voxel_size: float) -> int:
 
 
 def band_offsets(eps: float, voxel_size: float) -> np.ndarray:
-    """c_k = -eps + k 2 eps / n (computed in float64, stored as float32)."""
+    """c_k = -eps + k 2 eps / n, float64."""
     e = float(F32(eps))
     n = n_band_steps(eps, voxel_size)
-    return np.array([-e + k * (2.0 * e / n) for k in range(n + 1)], np.float64).astype(F32)
+    return np.array([-e + k * (2.0 * e / n) for k in range(n + 1)], np.float64)
 
 
-def _f32_pose(R, t):
-    return np.asarray(R, np.float64).astype(F32), np.asarray(t, np.float64).astype(F32)
+def _pose64(R, t):
+    """The pose as the kernels receive it (float32 values), in float64."""
+    return (np.asarray(R, np.float64).astype(F32).astype(np.float64),
+            np.asarray(t, np.float64).astype(F32).astype(np.float64))
+
+
+def _cam64(cam):
+    return tuple(float(F32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+
+
+def allocation_samples(depth: np.ndarray, cam, R_cw, t_cw, voxel_size: float, eps: float) -> np.ndarray:
+    """World coordinates, in block units (metres / (8 s)), of every band
+    sample of every pixel with depth > 0: float64 [M, 3]."""
+    R, t = _pose64(R_cw, t_cw)
+    fx, fy, cx, cy = _cam64(cam)
+    bs = BLOCK * float(F32(voxel_size))
+    dep = np.asarray(depth, F32)
+    jj, ii = np.nonzero((dep > F32(0)) & np.isfinite(dep))
+    D = dep[jj, ii].astype(np.float64)
+    xn = ((ii + 0.5) - cx) / fx
+    yn = ((jj + 0.5) - cy) / fy
+    out = []
+    for ck in band_offsets(eps, voxel_size):
+        z = D + ck
+        ok = z > 0
+        pc = np.stack([xn[ok] * z[ok], yn[ok] * z[ok], z[ok]], -1)
+        out.append(((pc - t) @ R) / bs)  # R^T (p_c - t), row form
+    return np.concatenate(out) if out else np.zeros((0, 3))
+
+
+def blocks_of(F: np.ndarray) -> set:
+    f = np.floor(F)
+    inside = (np.abs(f) < 2 ** 20).all(1)  # block coordinates in [-2^20, 2^20)
+    return set(map(tuple, f[inside].astype(np.int64).tolist()))
 
 
 def allocate(depth: np.ndarray, cam, R_cw, t_cw, voxel_size: float, eps: float) -> set:
-    """Blocks holding a band sample of some pixel's ray (float32 decisions)."""
-    H, W = depth.shape
-    R, t = _f32_pose(R_cw, t_cw)
-    fx, fy, cx, cy = (F32(cam.fx), F32(cam.fy), F32(cam.cx), F32(cam.cy))
-    bs = F32(F32(BLOCK) * F32(voxel_size))
-    dep = np.asarray(depth, F32)
-    jj, ii = np.nonzero((dep > F32(0)) & np.isfinite(dep))
-    D = dep[jj, ii]
-    xn = ((ii.astype(F32) + F32(0.5)) - cx) / fx
-    yn = ((jj.astype(F32) + F32(0.5)) - cy) / fy
-    out = set()
-    for ck in band_offsets(eps, voxel_size):
-        z = D + ck
-        ok = z > F32(0)
-        pc = (xn[ok] * z[ok], yn[ok] * z[ok], z[ok])
-        d = [pc[r] - t[r] for r in range(3)]
-        blk = []
-        inside = np.ones(d[0].shape, bool)
-        for a in range(3):
-            pw = (R[0, a] * d[0] + R[1, a] * d[1]) + R[2, a] * d[2]
-            f = np.floor(pw / bs)
-            inside &= np.abs(f) < 2 ** 20  # block coordinates in [-2^20, 2^20)
-            blk.append(np.where(inside, f, 0).astype(np.int64))
-        out.update(zip(blk[0][inside].tolist(), blk[1][inside].tolist(), blk[2][inside].tolist()))
-    return out
+    """Blocks holding a band sample of some pixel's ray."""
+    return blocks_of(allocation_samples(depth, cam, R_cw, t_cw, voxel_size, eps))
+
+
+def block_distance(F: np.ndarray, b) -> float:
+    """Smallest L-infinity distance (block units) from a sample to block b's
+    box [b, b + 1)^3; 0 if a sample lies in it."""
+    d = np.maximum(np.asarray(b, np.float64) - F, F - (np.asarray(b, np.float64) + 1.0))
+    return float(np.maximum(d, 0.0).max(1).min()) if len(F) else math.inf
+
+
+def block_depth(F: np.ndarray, b) -> float:
+    """How deep (block units, L-infinity) the deepest sample lies inside block
+    b: the distance it would have to move to leave it (0 if none is inside)."""
+    bb = np.asarray(b, np.float64)
+    m = np.minimum(F - bb, bb + 1.0 - F).min(1)
+    return float(m.max(initial=0.0))
 
 
 def new_block():
-    return [np.zeros((BLOCK,) * 3), np.zeros((BLOCK,) * 3)]
+    """tsdf, weight, smallest pixel-edge distance (px), smallest sdf + eps
+    distance (m) of the block's voxels, indexed [z, y, x]."""
+    return [np.zeros((BLOCK,) * 3), np.zeros((BLOCK,) * 3), np.full((BLOCK,) * 3, np.inf),
+            np.full((BLOCK,) * 3, np.inf)]
 
 
 def _local_grid():
@@ -113,32 +145,38 @@ def integrate_blocks(grid: dict, blocks, depth: np.ndarray, cam, R_cw, t_cw, vox
     if not blocks:
         return
     H, W = depth.shape
-    R, t = _f32_pose(R_cw, t_cw)
-    R64, t64 = R.astype(np.float64), t.astype(np.float64)
-    fx, fy, cx, cy = (F32(cam.fx), F32(cam.fy), F32(cam.cx), F32(cam.cy))
-    s = F32(voxel_size)
-    e32 = F32(eps)
-    e = float(e32)
+    R, t = _pose64(R_cw, t_cw)
+    fx, fy, cx, cy = _cam64(cam)
+    s = float(F32(voxel_size))
+    e = float(F32(eps))
     dep = np.asarray(depth, F32)
     lx, ly, lz = _local_grid()
     B = np.array(blocks, np.int64)  # [nb, 3]
-    g = [BLOCK * B[:, a:a + 1] + l[None, :] for a, l in enumerate((lx, ly, lz))]  # [nb, 512] each
-    pv = [(ga.astype(F32) + F32(0.5)) * s for ga in g]
-    pc = [((R[r, 0] * pv[0] + R[r, 1] * pv[1]) + R[r, 2] * pv[2]) + t[r] for r in range(3)]
+    pv = [(BLOCK * B[:, a:a + 1] + l[None, :] + 0.5) * s for a, l in enumerate((lx, ly, lz))]  # [nb, 512]
+    pc = [R[r, 0] * pv[0] + R[r, 1] * pv[1] + R[r, 2] * pv[2] + t[r] for r in range(3)]
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         u = fx * (pc[0] / pc[2]) + cx
         v = fy * (pc[1] / pc[2]) + cy
-    ok = (pc[2] > F32(0)) & (u >= F32(0)) & (u < F32(W)) & (v >= F32(0)) & (v < F32(H))
+    front = pc[2] > 0
+    ok = front & (u >= 0) & (u < W) & (v >= 0) & (v < H)
     pi = np.where(ok, np.floor(np.where(ok, u, 0)), 0).astype(np.int64)
     pj = np.where(ok, np.floor(np.where(ok, v, 0)), 0).astype(np.int64)
-    D32 = dep[pj, pi]
-    upd = ok & (D32 > F32(0)) & ((D32 - pc[2]) >= -e32)
-    pv64 = [(ga.astype(np.float64) + 0.5) * float(s) for ga in g]
-    z64 = R64[2, 0] * pv64[0] + R64[2, 1] * pv64[1] + R64[2, 2] * pv64[2] + t64[2]
-    sdf = D32.astype(np.float64) - z64
+    D = dep[pj, pi].astype(np.float64)
+    sdf = D - pc[2]
+    upd = ok & (D > 0) & (sdf >= -e)
     tsdf = np.where(sdf > 0, np.minimum(1.0, sdf / e), np.maximum(-1.0, sdf / e))
+    # distances to the decision boundaries (where a float32 evaluation may
+    # decide the other way): pixel edges and image border, sdf = -eps
+    with np.errstate(invalid="ignore"):
+        mpx = np.minimum(np.abs(u - np.round(u)), np.abs(v - np.round(v)))
+        mpx = np.minimum(mpx, np.minimum(np.minimum(np.abs(u), np.abs(u - W)), np.minimum(np.abs(v), np.abs(v - H))))
+    mpx = np.where(front, np.nan_to_num(mpx, nan=np.inf), np.inf)
+    msdf = np.where(ok & (D > 0), np.abs(sdf + e), np.inf)
+    msdf = np.minimum(msdf, np.abs(pc[2]))  # z = 0 (never near in practice)
     for n, b in enumerate(blocks):
         cell = grid.setdefault(b, new_block())
+        cell[2][lz, ly, lx] = np.minimum(cell[2][lz, ly, lx], mpx[n])
+        cell[3][lz, ly, lx] = np.minimum(cell[3][lz, ly, lx], msdf[n])
         m = upd[n]
         zi, yi, xi = lz[m], ly[m], lx[m]
         t_old = cell[0][zi, yi, xi]
@@ -163,51 +201,77 @@ def integrate(grid: dict, depth, cam, R_cw, t_cw, voxel_size: float = 0.01, eps:
 
 
 def leaf_points(depth, lv, cam, R_cw, t_cw):
-    """Eq. 10 world points of the leaves with depth > 0 at their centre pixel,
-    in float32 with a fixed order of correctly rounded operations (the
-    precision the novelty decision is taken in); returns (indices into lv,
-    points [k, 3] as float64 holding the float32 values)."""
+    """Eq. 10 world points of the leaves with depth > 0 at their centre pixel;
+    returns (indices into lv, points [k, 3] float64)."""
     H, W = depth.shape
-    R, t = _f32_pose(R_cw, t_cw)
-    fx, fy, cx, cy = (F32(cam.fx), F32(cam.fy), F32(cam.cx), F32(cam.cy))
-    idx, pts = [], []
-    for n, (x0, y0, w, h) in enumerate(np.asarray(lv, np.int64)):
-        ux, uy = F32(x0 + w / 2.0), F32(y0 + h / 2.0)  # exact
-        pi, pj = min(int(np.floor(ux)), W - 1), min(int(np.floor(uy)), H - 1)
-        z = F32(depth[pj, pi])
-        if not z > 0:
-            continue
-        q = [((ux - cx) * z) / fx - t[0], ((uy - cy) * z) / fy - t[1], z - t[2]]
-        pts.append([(R[0, a] * q[0] + R[1, a] * q[1]) + R[2, a] * q[2] for a in range(3)])
-        idx.append(n)
-    return np.array(idx, np.int64), np.array(pts, np.float32).astype(np.float64).reshape(-1, 3)
+    R, t = _pose64(R_cw, t_cw)
+    fx, fy, cx, cy = _cam64(cam)
+    lv = np.asarray(lv, np.int64).reshape(-1, 4)
+    ux = lv[:, 0] + lv[:, 2] / 2.0
+    uy = lv[:, 1] + lv[:, 3] / 2.0
+    pi = np.minimum(np.floor(ux).astype(np.int64), W - 1)
+    pj = np.minimum(np.floor(uy).astype(np.int64), H - 1)
+    z = np.asarray(depth, F32)[pj, pi].astype(np.float64) if len(lv) else np.zeros(0)
+    keep = np.nonzero(z > 0)[0]
+    z = z[keep]
+    q = np.stack([(ux[keep] - cx) * z / fx, (uy[keep] - cy) * z / fy, z], -1) - t
+    return keep.astype(np.int64), (q @ R).reshape(-1, 3)
+
+
+def voxel_of(points: np.ndarray, voxel_size: float):
+    """Voxel index of each point and the point's distance (m) to the nearest
+    voxel face (where a float32 evaluation may pick the neighbour)."""
+    s = float(F32(voxel_size))
+    f = np.asarray(points, np.float64) / s
+    vox = np.floor(f).astype(np.int64)
+    margin = (np.minimum(f - vox, vox + 1.0 - f).min(1) if len(f) else np.zeros(0)) * s
+    return vox, margin
 
 
 def voxel_weight(grid: dict, vox) -> float:
     """Weight of voxel ``vox`` (global integer coordinates); 0 if unallocated."""
+    return float(voxel_state(grid, vox)[1])
+
+
+def voxel_state(grid: dict, vox):
+    """(tsdf, weight, pixel margin, sdf margin) of voxel ``vox``; weight 0 and
+    infinite margins if its block is not allocated."""
     b = tuple(int(v) // BLOCK for v in vox)
     cell = grid.get(b)
     if cell is None:
-        return 0.0
+        return 0.0, 0.0, math.inf, math.inf
     lx, ly, lz = (int(v) - BLOCK * bb for v, bb in zip(vox, b))
-    return float(cell[1][lz, ly, lx])
+    return tuple(float(c[lz, ly, lx]) for c in cell)
+
+
+def novelty(grid: dict, depth, lv, cam, R_cw, t_cw, voxel_size: float = 0.01) -> dict:
+    """Per leaf with depth > 0 at its centre (``leaf``: indices into lv): its
+    Eq. 10 point, voxel, the voxel's weight, the point's distance to a voxel
+    face (m), the voxel's running pixel / sdf margins, and whether it seeds
+    (weight exactly 1 and the smallest y0 W + x0 of its voxel's new leaves)."""
+    W = depth.shape[1]
+    idx, pts = leaf_points(depth, lv, cam, R_cw, t_cw)
+    vox, vmargin = voxel_of(pts, voxel_size)
+    st = np.array([voxel_state(grid, v) for v in vox.tolist()], np.float64).reshape(-1, 4)
+    new = st[:, 1] == 1.0
+    best = {}
+    for k in np.nonzero(new)[0].tolist():
+        n = int(idx[k])
+        key = int(lv[n][1]) * W + int(lv[n][0])
+        v = tuple(vox[k].tolist())
+        if v not in best or key < best[v][0]:
+            best[v] = (key, k)
+    seeds = np.zeros(len(idx), bool)
+    seeds[[k for _, k in best.values()]] = True
+    return {"leaf": idx, "points": pts, "voxel": vox, "weight": st[:, 1], "voxel_margin": vmargin,
+            "px_margin": st[:, 2], "sdf_margin": st[:, 3], "seeds": seeds}
 
 
 def novel_leaves(grid: dict, depth, lv, cam, R_cw, t_cw, voxel_size: float = 0.01):
     """Indices into ``lv`` of the leaves that seed: Eq. 10 point in a voxel
     of weight 1, at most one (smallest y0 W + x0) per voxel."""
-    W = depth.shape[1]
-    idx, pts = leaf_points(depth, lv, cam, R_cw, t_cw)
-    s = F32(voxel_size)
-    best = {}
-    for n, p in zip(idx.tolist(), pts.astype(np.float32)):
-        vox = tuple(int(np.floor(c / s)) for c in p)  # float32 division
-        if voxel_weight(grid, vox) != 1.0:
-            continue
-        key = int(lv[n][1]) * W + int(lv[n][0])
-        if vox not in best or key < best[vox][0]:
-            best[vox] = (key, n)
-    return np.array(sorted(n for _, n in best.values()), np.int64)
+    r = novelty(grid, depth, lv, cam, R_cw, t_cw, voxel_size)
+    return np.sort(r["leaf"][r["seeds"]])
 
 
 def seed_tsdf(rgb, depth, grid: dict, cam, R_cw, t_cw, sh_degree: int, var_thr: float = 0.01, max_size: int = 64,
@@ -216,10 +280,5 @@ def seed_tsdf(rgb, depth, grid: dict, cam, R_cw, t_cw, sh_degree: int, var_thr: 
     then Eq. 10 for the leaves that seed."""
     lv = _qt.leaves(np.asarray(rgb, np.float64), var_thr, max_size, min_size)
     sel = novel_leaves(grid, depth, lv, cam, R_cw, t_cw, voxel_size)
-    out = _qt.seed(rgb, depth, lv[sel], cam, np.asarray(R_cw, np.float64), np.asarray(t_cw, np.float64), sh_degree)
-    # the means are the float32 points whose voxels were checked (Eq. 10's
-    # float64 value rounded through the float32 operations)
-    idx, pts = leaf_points(depth, lv[sel], cam, R_cw, t_cw)
-    assert len(idx) == len(sel)
-    out["means"] = pts
-    return out
+    R, t = _pose64(R_cw, t_cw)
+    return _qt.seed(rgb, depth, lv[sel], cam, R, t, sh_degree)

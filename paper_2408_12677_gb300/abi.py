@@ -66,6 +66,12 @@ class gs_stats(C.Structure):
                 ("n_tiles", C.c_int64), ("evals_blended", C.c_int64), ("evals_tiled", C.c_int64)]
 
 
+class gs_alu_peaks(C.Structure):
+    _fields_ = [("fma_tflops", C.c_double), ("ex2_gops", C.c_double), ("fma_sm_mhz", C.c_double),
+                ("ex2_sm_mhz", C.c_double), ("fma_per_sm_clk", C.c_double), ("ex2_per_sm_clk", C.c_double),
+                ("fma_ms", C.c_double), ("ex2_ms", C.c_double), ("num_sms", C.c_int32)]
+
+
 class gs_tsdf_grid(C.Structure):
     _fields_ = [("keys", C.c_void_p), ("slots", C.c_void_p), ("stamps", C.c_void_p), ("voxels", C.c_void_p),
                 ("claims", C.c_void_p), ("touched", C.c_void_p), ("counters", C.c_void_p),
@@ -141,6 +147,8 @@ EXPORTS = {
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
     "gs_set_profiling": (C.c_int, [P, C.c_int]),
     "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "gs_measure_alu_peaks": (C.c_int, [C.c_int, C.c_int32, C.POINTER(gs_alu_peaks)]),
+    "gs_state_token": (C.c_int, [P, C.POINTER(C.c_uint64)]),
 }
 
 _lib = None
@@ -552,3 +560,16 @@ def gs_count_nonfinite(ctx, x, stream=None) -> int:
 
 def gs_ctx_inject_alloc_failure(ctx, after: int = 1):
     _check(ctx, load().gs_ctx_inject_alloc_failure(ctx, int(after)), "gs_ctx_inject_alloc_failure")
+
+
+def gs_state_token(ctx) -> int:
+    """Token of the forward state the context holds (0 = none)."""
+    tok = C.c_uint64(0)
+    _check(ctx, load().gs_state_token(ctx, C.byref(tok)), "gs_state_token")
+    return int(tok.value)
+
+
+def gs_measure_alu_peaks(device: int = 0, iters: int = 50000) -> dict:
+    out = gs_alu_peaks()
+    _check(None, load().gs_measure_alu_peaks(int(device), int(iters), C.byref(out)), "gs_measure_alu_peaks")
+    return {name: getattr(out, name) for name, _ in gs_alu_peaks._fields_}

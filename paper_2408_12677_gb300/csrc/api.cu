@@ -16,6 +16,10 @@
 
 using namespace gs;
 
+// the forward state is matched by comparing these structs byte for byte
+static_assert(sizeof(gs_camera) == 24 && sizeof(gs_viewmat) == 48 && sizeof(gs_raster_cfg) == 44,
+              "ABI structs without padding");
+
 struct gs_ctx {
   int device = 0;
   int num_sms = 0;
@@ -88,8 +92,15 @@ struct gs_ctx {
   std::vector<Ev> evs;
   size_t ev_used = 0;
 
-  // state of the last forward pass
+  // state of the last forward pass: what it was computed from (the
+  // backward pass must be given the same) and its token
   bool have_state = false;
+  uint64_t serial = 0;       // forward passes started on this context
+  uint64_t state_token = 0;  // token of the held state (0 = none)
+  gs_gaussians st_g{};
+  gs_camera st_cam[kMaxViews] = {};
+  gs_viewmat st_view[kMaxViews] = {};
+  gs_raster_cfg st_cfg{};
   int64_t st_n = 0;
   int st_views = 0;
   int st_w[kMaxViews] = {}, st_h[kMaxViews] = {};
@@ -855,6 +866,8 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     return fail(c, GS_ERR_CAPACITY, "no-sync mode: reserve items/pixels first (gs_ctx_reserve)");
   }
   c->have_state = false;
+  c->state_token = 0;
+  c->serial += 1;
 
   ProjectArgs pa = project_args(g, V, cams, views, cfg, L.map, L.tiles_y);
   pa.big_queue = c->bigq;
@@ -907,6 +920,13 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   }
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_fwd");
+  c->st_g = *g;
+  for (int v = 0; v < V; ++v) {
+    c->st_cam[v] = cams[v];
+    c->st_view[v] = views[v];
+  }
+  c->st_cfg = *cfg;
+  c->state_token = c->serial;
   c->have_state = true;
   return GS_OK;
 }
@@ -921,10 +941,19 @@ gs_status check_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
   if (!dL_dcolor || !dL_ddepth) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
   for (int v = 0; v < V; ++v)
     if (!dL_dcolor[v] || !dL_ddepth[v]) return fail(c, GS_ERR_INVALID_ARG, "dL_dcolor and dL_ddepth are required");
-  bool match = c->have_state && c->st_n == g->n && c->st_views == V && c->st_tw == cfg->tile_w &&
-               c->st_th == cfg->tile_h && c->st_sh == g->sh_degree;
-  for (int v = 0; match && v < V; ++v) match = c->st_w[v] == cams[v].width && c->st_h[v] == cams[v].height;
-  if (!match) return fail(c, GS_ERR_STATE, "the backward pass needs the matching forward pass on this context");
+  if (!c->have_state) return fail(c, GS_ERR_STATE, "no forward state on this context (run the forward pass first)");
+  const gs_gaussians& h = c->st_g;
+  const bool same_map = h.means == g->means && h.log_scales == g->log_scales && h.quats == g->quats &&
+                        h.opacity_logits == g->opacity_logits && h.sh == g->sh && h.n == g->n &&
+                        h.sh_degree == g->sh_degree;
+  if (!same_map || c->st_views != V)
+    return fail(c, GS_ERR_STATE, "the held forward state is of other Gaussian arrays or another view count");
+  for (int v = 0; v < V; ++v)
+    if (std::memcmp(&c->st_cam[v], &cams[v], sizeof(gs_camera)) != 0 ||
+        std::memcmp(&c->st_view[v], &views[v], sizeof(gs_viewmat)) != 0)
+      return fail(c, GS_ERR_STATE, "the held forward state is of another camera or pose (view " + std::to_string(v) + ")");
+  if (std::memcmp(&c->st_cfg, cfg, sizeof(gs_raster_cfg)) != 0)
+    return fail(c, GS_ERR_STATE, "the held forward state is of another raster configuration");
   return GS_OK;
 }
 
@@ -1330,6 +1359,7 @@ gs_status gs_autotune(gs_ctx* c, const gs_gaussians* g, int32_t n_views, const g
   }
   c->sync = was_sync;
   c->have_state = false;  // the stored state is the last candidate's, not the chosen one
+  c->state_token = 0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != GS_OK) return st;
@@ -1661,6 +1691,12 @@ gs_status gs_get_projection(gs_ctx* c, float* mean2d, float* cov2d, float* depth
                            (cudaStream_t)stream);
   if (c->st_n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "export projection");
+  return GS_OK;
+}
+
+gs_status gs_state_token(const gs_ctx* c, uint64_t* token) {
+  if (!c || !token) return GS_ERR_INVALID_ARG;
+  *token = c->have_state ? c->state_token : 0;
   return GS_OK;
 }
 

@@ -470,6 +470,7 @@ class _Render(torch.autograd.Function):
         alpha = torch.empty((H, W), device=means.device)
         abi.gs_render_fwd(ctx.handle, g, cam, view, rcfg, color, depth, alpha)
         actx.meta = meta
+        actx.token = abi.gs_state_token(ctx.handle)
         actx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
         actx.pose_device = pose_xi.device if pose_xi is not None else None
         return color, depth, alpha
@@ -486,7 +487,20 @@ class _Render(torch.autograd.Function):
         gc = gc.contiguous() if gc is not None else torch.zeros((3, cam.height, cam.width), device=means.device)
         gd = gd.contiguous() if gd is not None else zero
         ga = ga.contiguous() if ga is not None else None
-        abi.gs_render_bwd(ctx.handle, g, cam, view, rcfg, gc, gd, ga, abi.make_grads(*grads), gp)
+        if abi.gs_state_token(ctx.handle) != actx.token:
+            # another forward pass ran on this context since (e.g. a second
+            # render of the same map at another pose): recompute this one's
+            # state from the saved inputs before differentiating it
+            abi.gs_render_fwd(ctx.handle, g, cam, view, rcfg, None, None, None)
+        try:
+            abi.gs_render_bwd(ctx.handle, g, cam, view, rcfg, gc, gd, ga, abi.make_grads(*grads), gp)
+        except abi.GsError as e:
+            if e.status != abi.GS_ERR_STATE:
+                raise
+            # inputs that were not contiguous were copied, so the arrays differ
+            # from the forward pass's: recompute the state from these copies
+            abi.gs_render_fwd(ctx.handle, g, cam, view, rcfg, None, None, None)
+            abi.gs_render_bwd(ctx.handle, g, cam, view, rcfg, gc, gd, ga, abi.make_grads(*grads), gp)
         pose_grad = gp.to(actx.pose_device) if actx.pose_device is not None else None
         return (*grads, pose_grad, None)
 

@@ -19,24 +19,72 @@ def ensure_built():
     return abi.load()
 
 
-def compare(name, got, ref, rtol, atol, norm_rtol, flip_budget=0, report=None):
+MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99")
+FLIP_EPS = 1e-4  # relative distance to a threshold within which float32 may decide the other way
+
+
+def compare(name, got, ref, rtol, atol, norm_rtol, flip_budget=0, report=None, margins=None, kinds=None,
+            flip_eps=FLIP_EPS):
     """Element-wise |got - ref| <= rtol |ref| + atol except for at most
-    ``flip_budget`` elements, and ||got - ref|| / ||ref|| <= norm_rtol."""
+    ``flip_budget`` elements ("flips"), and ||got - ref|| / ||ref|| <= norm_rtol.
+
+    With ``margins`` (one per element: the oracle's relative
+    float64 distance of the decisions behind the element to their thresholds,
+    ``kinds`` naming the nearest one), every element beyond the tolerance must
+    lie within ``flip_eps`` of a threshold -- a float32 / float64 decision
+    flip -- and each is listed in the report with its threshold and distance;
+    an element beyond the tolerance away from every threshold fails."""
     got = np.asarray(got, np.float64).ravel()
     ref = np.asarray(ref, np.float64).ravel()
     assert got.shape == ref.shape, (name, got.shape, ref.shape)
     assert np.isfinite(got).all(), f"{name}: non-finite values"
     err = np.abs(got - ref)
-    bad = err > rtol * np.abs(ref) + atol
+    tol = rtol * np.abs(ref) + atol
+    bad = err > tol
     nref = np.linalg.norm(ref)
     nrel = np.linalg.norm(got - ref) / nref if nref > 0 else np.linalg.norm(got - ref)
     info = {"name": name, "n": int(ref.size), "bad": int(bad.sum()), "max_err": float(err.max(initial=0.0)),
-            "norm_rel": float(nrel)}
+            "norm_rel": float(nrel), "budget": int(flip_budget), "flips": []}
+    unexplained = []
+    if bad.any():
+        idx = np.nonzero(bad)[0]
+        if margins is not None:
+            mg = np.asarray(margins, np.float64).ravel()
+            kd = None if kinds is None else np.asarray(kinds).ravel()
+            assert mg.size == ref.size and (kd is None or kd.size == ref.size), (name, mg.size, ref.size)
+            for i in idx.tolist():
+                rec = {"i": i, "got": float(got[i]), "ref": float(ref[i]), "err": float(err[i]),
+                       "tol": float(tol[i]), "margin": float(mg[i]),
+                       "kind": MARGIN_KINDS[int(kd[i])] if kd is not None else None}
+                info["flips"].append(rec)
+                if not mg[i] <= flip_eps:
+                    unexplained.append(rec)
+        else:
+            info["flips"] = [{"i": int(i), "got": float(got[i]), "ref": float(ref[i]), "err": float(err[i]),
+                              "tol": float(tol[i])} for i in idx.tolist()]
     if report is not None:
         report.append(info)
-    assert int(bad.sum()) <= flip_budget, f"{name}: {info} (budget {flip_budget}); worst idx {np.argsort(-err)[:5]}"
-    assert nrel <= norm_rtol, f"{name}: {info} (norm tolerance {norm_rtol})"
+    assert not unexplained, f"{name}: {len(unexplained)} elements beyond tolerance away from every threshold: " \
+                            f"{unexplained[:5]}"
+    assert int(bad.sum()) <= flip_budget, f"{name}: {info['bad']} flips (budget {flip_budget}): {info['flips'][:5]}"
+    assert nrel <= norm_rtol, f"{name}: norm rel {nrel:.3e} (tolerance {norm_rtol})"
     return info
+
+
+def margins_over_views(params, deg, cams, poses):
+    """Per-Gaussian decision margins (``R.decision_margins``) of several views
+    of one map: the smallest over the views."""
+    from oracle import render as R
+    out = None
+    for cam, (Rm, t) in zip(cams, poses):
+        m = R.decision_margins(params, deg, cam, np.asarray(Rm, np.float64), np.asarray(t, np.float64))
+        if out is None:
+            out = {"gauss": m["gauss"].copy(), "gauss_kind": m["gauss_kind"].copy()}
+        else:
+            better = m["gauss"] < out["gauss"]
+            out["gauss"][better] = m["gauss"][better]
+            out["gauss_kind"][better] = m["gauss_kind"][better]
+    return out
 
 
 def to_gpu_model(params):

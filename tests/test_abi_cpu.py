@@ -90,7 +90,7 @@ def test_struct_layouts_match_the_compiled_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = [abi.gs_camera, abi.gs_viewmat, abi.gs_gaussians, abi.gs_grads, abi.gs_raster_cfg, abi.gs_adam_cfg,
-               abi.gs_stats, abi.gs_tsdf_grid]
+               abi.gs_stats, abi.gs_tsdf_grid, abi.gs_alu_peaks]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gsplat.h"', "int main(void) {"]
     for st in structs:
         name = st.__name__

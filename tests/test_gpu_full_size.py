@@ -57,7 +57,8 @@ def test_sparse_upstream_gradient_matches_oracle(setup):
     og, _ = R.weighted_pixel_gradients(w.params, 3, v.cam, v.pose.R.astype(np.float64), v.pose.t.astype(np.float64),
                                        pix, wc.astype(np.float64), wd.astype(np.float64), None, prefilter=True)
     from tests.test_gpu_grad import check_grad_arrays
-    check_grad_arrays(g, og, 20)
+    check_grad_arrays(g, og, R.decision_margins(w.params, 3, v.cam, v.pose.R.astype(np.float64),
+                                                v.pose.t.astype(np.float64), pixels=pix))
 
 
 def test_training_iterations_reduce_loss(setup):

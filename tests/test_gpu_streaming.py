@@ -9,7 +9,7 @@ import torch
 from oracle import render as R
 from synth import workloads
 from synth.quadtree import seed_gaussians
-from tests._util import ensure_built
+from tests._util import ensure_built, margins_over_views
 from tests.test_gpu_grad import check_grad_arrays
 
 pytestmark = pytest.mark.gpu
@@ -82,9 +82,16 @@ def test_checkpoint_gradients_match_oracle(run):
     P = opt.map.live_params()
     poses = [(np.array(k.view.R, np.float64).reshape(3, 3), np.array(k.view.t, np.float64)) for k in views]
     targets = [(k.rgb.cpu().numpy(), k.depth.cpu().numpy()) for k in views]
-    L, og, _ = R.multiview_gradients(P, DEG, [st.cam] * V, poses, targets)
+    L, og_loss, _ = R.multiview_gradients(P, DEG, [st.cam] * V, poses, targets)
     assert abs(float(opt.loss.item()) - float(L)) <= 1e-4 * float(L)
-    check_grad_arrays(g, og, max(2, int(0.004 * n)))
+    # the backward pass against the oracle's, both driven by the image
+    # gradients the GPU loss wrote (so an L1 sign that flips at a residual
+    # near 0 does not enter the comparison; the loss is compared above)
+    wc = [x.cpu().numpy().astype(np.float64) for x in opt.dLdc[:V]]
+    wd = [x.cpu().numpy().astype(np.float64) for x in opt.dLdd[:V]]
+    og = R.multiview_weighted_gradients(P, DEG, [st.cam] * V, poses, wc, wd)
+    check_grad_arrays(g, og, margins_over_views(P, DEG, [st.cam] * V, poses))
+    og = og_loss  # central differences below are of the loss itself
 
     # central differences of the FP64 loss (h = 1e-4) at the largest gradient entries
     Pd = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in P.items()}

@@ -2,23 +2,29 @@
 gs_seed_tsdf) against the FP64 oracle (Sec. III-B.1, Eq. 6-9, and the
 voxel-weight novelty check of Sec. III-B.2).
 
-Block sets, touched lists, weights and the seeded leaves are integer results
-decided in the same float32 / float64 operation order on both sides:
-bit-exact.  tsdf values: |gpu - oracle| <= 1e-4.  The bound: the float32
-camera z of a voxel centre carries at most ~9 roundings of size ulp(10 m)/2
-= 4.8e-7 m for scenes within 10 m of the origin (4.3e-6 m), plus one in
-D - z; divided by eps = 0.08 m that is 5.5e-5, and the Eq. 9 average of
-values within that error stays within it."""
+The oracle takes the integer decisions (block of a band sample, pixel of a
+voxel, update, voxel of an Eq. 10 point) in float64, the kernels in float32.
+Touched block sets, weights and seeded leaves must agree except for flips:
+disagreements where the float64 value lies within float32 rounding of the
+deciding boundary (tests/_tsdf_flips.py gives the bounds), each logged with
+its float64 distance, their number bounded.  tsdf values: |gpu - oracle| <=
+1e-4: the float32 camera z of a voxel centre carries at most ~9 roundings
+of size ulp(10 m)/2 = 4.8e-7 m for scenes within 10 m of the origin
+(4.3e-6 m), plus one in D - z; divided by eps = 0.08 m that is 5.5e-5, and
+the Eq. 9 average of values within that error stays within it."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import tsdf as T
 from synth import workloads
+from tests import _tsdf_flips as FL
 from tests._util import ensure_built
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-4
+TOL = FL.TSDF_TOL
+S, EPS = 0.01, 0.08
+BS = 8 * float(np.float32(S))
 
 
 @pytest.fixture(scope="module")
@@ -54,49 +60,53 @@ def _touched(grid, n):
             for k in keys[idx].tolist()}
 
 
-def _compare(gpu_blocks, ref):
-    assert set(gpu_blocks) == set(ref)
-    gt = np.stack([gpu_blocks[b][0] for b in ref]).astype(np.float64)
-    gw = np.stack([gpu_blocks[b][1] for b in ref]).astype(np.float64)
-    rt = np.stack([ref[b][0] for b in ref])
-    rw = np.stack([ref[b][1] for b in ref])
-    assert np.array_equal(gw, rw)
-    err = np.abs(gt - rt)[rw > 0]
-    assert err.max() <= TOL, err.max()
-    assert (gt[rw == 0] == 0).all()
-    return int((rw > 0).sum())
+def _alloc(grid, c, depth, cam, pose, log, excused):
+    """The frame's touched blocks against the oracle's allocation (flips
+    logged and added to ``excused``); returns the oracle's block set."""
+    F = T.allocation_samples(depth, cam, pose.R, pose.t, S, EPS)
+    G = _touched(grid, c["touched"])
+    assert len(G) == c["touched"]
+    excused |= FL.check_alloc(G, F, BS, budget=max(2, len(G) // 50), log=log)
+    return T.blocks_of(F)
+
+
+def _compare(gpu_blocks, ref, excused, log):
+    n = FL.check_voxels(gpu_blocks, ref, excused, log)
+    print(FL.census(log))
+    return n
 
 
 @pytest.mark.parametrize("fusion", ["printed", "unit"])
 def test_integrate_matches_oracle(ctx, stream, fusion):
     grid = _grid(ctx, fusion=fusion, capacity=1 << 14, table_size=1 << 16)
-    ref = {}
+    ref, log, excused = {}, [], set()
     for k in (0, 4, 8, 8, 20):
         _, depth = stream.frame(k)
         cam, view = _structs(stream.cam, stream.poses[k])
         c = grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
-        want = T.integrate(ref, depth, stream.cam, stream.poses[k].R, stream.poses[k].t, fusion=fusion)
-        assert c["touched"] == len(want) and _touched(grid, c["touched"]) == want
-        assert c["blocks"] == len(ref)
-    n = _compare(grid.blocks(), ref)
+        want = _alloc(grid, c, depth, stream.cam, stream.poses[k], log, excused)
+        T.integrate_blocks(ref, sorted(want), depth, stream.cam, stream.poses[k].R, stream.poses[k].t, S, EPS,
+                           100.0, fusion)
+    n = _compare(grid.blocks(), ref, excused, log)
     assert n > 100_000
-    assert max(float(w.max()) for _, w in ref.values()) == 5.0  # some voxels are seen by all five frames
+    assert max(float(cell[1].max()) for cell in ref.values()) == 5.0  # some voxels are seen by all five frames
 
 
 def test_growth_rehash_and_pool_recovery(ctx, stream):
     """A tiny table and pool: every frame rehashes and overflows the pool;
     the recovery pass (min_slot) integrates exactly the skipped blocks."""
     grid = _grid(ctx, capacity=16, table_size=64)
-    ref = {}
+    ref, log, excused = {}, [], set()
     sizes = []
     for k in (0, 10, 30):
         _, depth = stream.frame(k)
         cam, view = _structs(stream.cam, stream.poses[k])
-        grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
-        T.integrate(ref, depth, stream.cam, stream.poses[k].R, stream.poses[k].t)
+        c = grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
+        want = _alloc(grid, c, depth, stream.cam, stream.poses[k], log, excused)
+        T.integrate_blocks(ref, sorted(want), depth, stream.cam, stream.poses[k].R, stream.poses[k].t, S, EPS, 100.0)
         sizes.append((grid.table_size, grid.capacity))
     assert sizes[0][0] > 64 and sizes[0][1] > 16
-    _compare(grid.blocks(), ref)
+    _compare(grid.blocks(), ref, excused, log)
 
 
 def test_query_and_edge_cases(ctx, stream):
@@ -104,9 +114,10 @@ def test_query_and_edge_cases(ctx, stream):
     grid = _grid(ctx)
     _, depth = stream.frame(5)
     cam, view = _structs(stream.cam, stream.poses[5])
-    ref = {}
-    grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
-    T.integrate(ref, depth, stream.cam, stream.poses[5].R, stream.poses[5].t)
+    ref, log, excused = {}, [], set()
+    c = grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
+    want = _alloc(grid, c, depth, stream.cam, stream.poses[5], log, excused)
+    T.integrate_blocks(ref, sorted(want), depth, stream.cam, stream.poses[5].R, stream.poses[5].t, S, EPS, 100.0)
     rng = np.random.default_rng(0)
     blocks = list(ref)
     pts = []
@@ -115,13 +126,23 @@ def test_query_and_edge_cases(ctx, stream):
         pts.append((8 * b + rng.uniform(0, 8, 3)) * 0.01)
     pts = np.concatenate([np.array(pts), rng.uniform(-3, 10, (200, 3))]).astype(np.float32)
     ts, ws = grid.query(torch.as_tensor(pts, device="cuda"))
-    for p, t, w in zip(pts.astype(np.float64), ts.cpu().numpy(), ws.cpu().numpy()):
-        vox = np.floor(p / np.float32(0.01)).astype(int)
-        assert w == T.voxel_weight(ref, vox)
+    vox_all, margin = T.voxel_of(pts.astype(np.float64), S)
+    checked = 0
+    for vox, m, t, w in zip(vox_all, margin, ts.cpu().numpy(), ws.cpu().numpy()):
+        rt, rw, mpx, msdf = T.voxel_state(ref, vox)
+        b = tuple(int(x) // 8 for x in vox)
+        # float32 may pick the neighbouring voxel (query), or have decided the
+        # voxel's update the other way (fusion): flips, logged
+        if m <= FL.TOL_M or mpx <= FL.TOL_PX or msdf <= FL.TOL_M or b in excused:
+            if w != rw or (rw > 0 and abs(t - rt) > TOL):
+                log.append(("query", tuple(vox.tolist()), float(w), rw, m, mpx, msdf))
+            continue
+        checked += 1
+        assert w == rw, (vox, w, rw, m, mpx, msdf)
         if w > 0:
-            b = tuple(vox // 8)
-            lx, ly, lz = vox - 8 * np.array(b)
-            assert abs(t - ref[b][0][lz, ly, lx]) <= TOL
+            assert abs(t - rt) <= TOL
+    print(FL.census(log))
+    assert checked > 550
     # an empty frame allocates and updates nothing
     before = grid.n_blocks
     c = grid.integrate(torch.zeros_like(torch.as_tensor(depth, device="cuda")), cam, view)
@@ -157,31 +178,32 @@ def _seed(grid, rgb, depth, cam, view, deg, thr, max_size, min_size, cap=1 << 15
 
 
 def test_seed_tsdf_matches_oracle(ctx, stream):
+    from oracle import quadtree as Q
     grid = _grid(ctx)
-    ref = {}
+    ref, log, excused = {}, [], set()
     deg, thr = 1, 0.01
     counts = []
     for k in (0, 6, 6):
         rgb, depth = stream.frame(k)
         pose = stream.poses[k]
         cam, view = _structs(stream.cam, pose)
-        grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
-        T.integrate(ref, depth, stream.cam, pose.R, pose.t)
+        c = grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
+        want_blocks = _alloc(grid, c, depth, stream.cam, pose, log, excused)
+        T.integrate_blocks(ref, sorted(want_blocks), depth, stream.cam, pose.R, pose.t, S, EPS, 100.0)
         n, out = _seed(grid, rgb, depth, cam, view, deg, thr, 16, 1)
-        want = T.seed_tsdf(rgb, depth, ref, stream.cam, pose.R, pose.t, deg, thr, 16, 1)
-        assert n == want["means"].shape[0]
+        lv = Q.leaves(np.asarray(rgb, np.float64), thr, 16, 1)
+        rep = T.novelty(ref, depth, lv, stream.cam, pose.R, pose.t, S)
         assert float(out["opacity_logits"][n]) == 9.0
         got = {k2: v[:n].cpu().numpy().astype(np.float64) for k2, v in out.items()}
-        # the kernel's means are the float32 rounding of the same float64
-        # points (same operation order): equal after rounding, so both sides
-        # sort identically
-        w32 = want["means"].astype(np.float32).astype(np.float64)
-        og, orf = np.lexsort(got["means"].T), np.lexsort(w32.T)
-        assert np.array_equal(got["means"][og], w32[orf])
-        assert np.allclose(got["log_scales"][og], want["log_scales"][orf], rtol=1e-6, atol=1e-6)
-        assert np.allclose(got["sh"][og], want["sh"][orf], rtol=1e-6, atol=1e-6)
+        gi, wi = FL.check_seeds(got["means"], rep, S, excused, log, budget=max(2, int(rep["seeds"].sum()) // 1000))
+        want = T.seed_tsdf(rgb, depth, ref, stream.cam, pose.R, pose.t, deg, thr, 16, 1)
+        # the oracle's seeds are the report's seeds in leaf order
+        order = np.searchsorted(np.sort(rep["leaf"][rep["seeds"]]), rep["leaf"][wi])
+        assert np.allclose(got["log_scales"][gi], want["log_scales"][order], rtol=1e-6, atol=1e-6)
+        assert np.allclose(got["sh"][gi], want["sh"][order], rtol=1e-6, atol=1e-6)
         assert (grid.claims == -1).all()  # every claim given back
         counts.append(n)
+    print(FL.census(log))
     # the repeated frame raises every voxel it updates to weight >= 2; what it
     # still seeds are leaves whose voxel it does not update (its centre falls
     # behind a depth edge) but an earlier frame updated once
@@ -203,45 +225,54 @@ def test_seed_tsdf_capacity(ctx, stream):
 
 def test_full_size_frames(ctx):
     """1200 x 680 frames of the streaming workload: the touched block sets
-    equal the oracle's allocation exactly, and a sample of blocks equals the
-    oracle's integration of those blocks over both frames."""
+    equal the oracle's allocation up to logged flips, and a sample of blocks
+    equals the oracle's integration of those blocks over both frames."""
     st = workloads.streaming(n_frames=200)
     grid = _grid(ctx, capacity=1 << 16, table_size=1 << 20)
     rng = np.random.default_rng(1)
-    ref = {}
+    ref, log, excused = {}, [], set()
     sample = None
     for k in (0, 3):
         _, depth = st.frame(k)
         pose = st.poses[k]
         cam, view = _structs(st.cam, pose)
         c = grid.integrate(torch.as_tensor(depth, device="cuda"), cam, view)
-        want = T.allocate(depth, st.cam, pose.R, pose.t, 0.01, 0.08)
-        assert c["touched"] == len(want) > 10_000
-        assert _touched(grid, c["touched"]) == want
+        want = _alloc(grid, c, depth, st.cam, pose, log, excused)
+        assert len(want) > 10_000
         if sample is None:
             blocks = sorted(want)
             sample = [blocks[i] for i in rng.choice(len(blocks), 300, replace=False)]
-        T.integrate_blocks(ref, [b for b in sample if b in want], depth, st.cam, pose.R, pose.t, 0.01, 0.08, 100.0)
+        T.integrate_blocks(ref, [b for b in sample if b in want], depth, st.cam, pose.R, pose.t, S, EPS, 100.0)
     got = grid.blocks()
-    _compare({b: got[b] for b in ref}, ref)
+    _compare({b: got[b] for b in ref if b in got}, ref, excused, log)
 
 
 def test_streaming_loop_seeds_like_the_oracle(ctx, stream):
     """The streaming loop (fusion, voxel-weight seeding, optimisation) seeds
-    per frame exactly the Gaussians the oracle's fusion + novelty check
-    gives for the same frames (the optimisation does not touch the grid)."""
+    per frame the Gaussians the oracle's fusion + novelty check gives for the
+    same frames (the optimisation does not touch the grid), up to seeds of
+    voxels whose decisions lie within float32 rounding of a boundary."""
+    from oracle import quadtree as Q
     from paper_2408_12677_gb300.streaming import StreamingOptimizer
     sp = dict(var_thr=0.02, max_size=32, min_size=2)
     opt = StreamingOptimizer(stream.cam, 1, None, iters=2, n_past=2, capacity=256, rng_seed=5, seeding=sp)
-    ref = {}
+    ref, log, excused = {}, [], set()
     for k in (0, 3, 7, 12, 12):
         rgb, depth = stream.frame(k)
         pose = stream.poses[k]
         s = opt.process_frame(rgb, depth, pose)
-        T.integrate(ref, depth, stream.cam, pose.R, pose.t)
-        want = T.seed_tsdf(rgb, depth, ref, stream.cam, pose.R, pose.t, 1, sp["var_thr"], sp["max_size"],
-                           sp["min_size"])
-        assert s.new_gaussians == want["means"].shape[0]
-        assert s.tsdf_blocks == len(ref)
+        want = _alloc(opt.tsdf, {"touched": s.tsdf_touched}, depth, stream.cam, pose, log, excused)
+        T.integrate_blocks(ref, sorted(want), depth, stream.cam, pose.R, pose.t, S, EPS, 100.0)
+        lv = Q.leaves(np.asarray(rgb, np.float64), sp["var_thr"], sp["max_size"], sp["min_size"])
+        rep = T.novelty(ref, depth, lv, stream.cam, pose.R, pose.t, S)
+        # the optimisation iterations have moved the seeded means since, so
+        # only the count is compared: it may differ by the flagged voxels
+        slack = len(FL.flagged_voxels(rep, S, excused))
+        n_want = int(rep["seeds"].sum())
+        if s.new_gaussians != n_want:
+            log.append(("seed count", k, s.new_gaussians, n_want, slack))
+        assert abs(s.new_gaussians - n_want) <= slack
+        assert abs(s.tsdf_blocks - len(ref)) <= len(excused)
+    print(FL.census(log))
     assert s.new_gaussians < 0.05 * opt.map.n and opt.map.n > 300
     assert torch.isfinite(opt.map.model.flat).all()

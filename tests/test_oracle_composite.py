@@ -187,3 +187,64 @@ def test_loss_closed_form():
     np.testing.assert_allclose(gd.numpy(), expect)
     _, gc0, _ = R.loss_image_grads(tgt, tdep, tgt, tdep)
     assert float(gc0.abs().max()) == 0.0  # sign(0) = 0
+
+
+def test_brute_equals_bbox_prefilter_on_tiles():
+    """The bounding-box selection per tile keeps every Gaussian with q <= 9 at
+    a pixel of the tile: same blend sets and values as brute force, over all
+    tiles of a ragged image in a permuted tile order."""
+    w = workloads.tiny_random(seed=16, n=500, sh_degree=1, sh_rest_std=0.1)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    full = _render(P, deg=1, prefilter=False)
+    tiles = np.random.default_rng(3).permutation(4 * 3)  # 64 x 48 in 16 x 16 tiles
+    pix = R.tile_pixels(CAM, tiles)
+    sub = _render(P, deg=1, pixels=pix, prefilter="bbox", chunk_px=256)
+    np.testing.assert_array_equal(sub["n_contrib"].numpy(), full["n_contrib"].numpy()[pix[:, 1], pix[:, 0]])
+    np.testing.assert_allclose(sub["color"].numpy(), full["color"].numpy()[:, pix[:, 1], pix[:, 0]], rtol=1e-13,
+                               atol=1e-15)
+    np.testing.assert_allclose(sub["alpha"].numpy(), full["alpha"].numpy()[pix[:, 1], pix[:, 0]], rtol=1e-13,
+                               atol=1e-15)
+    # a ragged tile at the image corner is clipped to the image
+    cam = Camera(60.0, 60.0, 32.0, 24.0, 70, 50)
+    p2 = R.tile_pixels(cam, [3 * 5 + 4])  # last tile of 5 x 4: 6 x 2 pixels
+    assert p2.shape == (12, 2) and p2[:, 0].min() == 64 and p2[:, 1].min() == 48
+
+
+def test_decision_margins_single_gaussian():
+    """One isotropic Gaussian: the q margin of a pixel is |q - 9| / 9 with q the
+    closed-form |u - mu|^2 / sigma^2, its alpha margins are the distances of
+    sigmoid(o) exp(-q/2) to 1/255 and 0.99, and a lone Gaussian never meets
+    the stop rule (T (1 - alpha) >= 0.01)."""
+    z, s, logit = 2.0, 0.02, 0.0
+    out = R.decision_margins(_scene([[0, 0, z]], [[np.log(s)] * 3], [logit], [[0.5, 0.5, 0.5]]), 0, CAM, *IDENT)
+    sig2 = (CAM.fx * s / z) ** 2 + 0.3
+    jj, ii = np.meshgrid(np.arange(48) + 0.5, np.arange(64) + 0.5, indexing="ij")
+    q = (((ii - 32.0) ** 2 + (jj - 24.0) ** 2) / sig2).ravel()
+    a = 0.5 * np.exp(-0.5 * q)
+    want = np.where(q <= 9 * (1 + 1e-3), np.abs(q - 9) / 9, np.inf)
+    want = np.minimum(want, np.where(q <= 9, np.abs(a - 1 / 255) * 255, np.inf))
+    want = np.minimum(want, np.where(q <= 9, np.abs(a - 0.99) / 0.99, np.inf))
+    want = np.minimum(want, np.where((q <= 9) & (a >= 1 / 255), np.abs((1 - a) - 1e-4) / 1e-4, np.inf))
+    np.testing.assert_allclose(out["pixel"], want, rtol=1e-9)
+    assert out["gauss"][0] == pytest.approx(want.min(), rel=1e-9)
+
+
+def test_decision_margins_stop_rule():
+    """Three opaque fronts (alpha = 0.99 each) over one pixel: before the
+    second, T = 0.01, so its stop test T (1 - alpha) = 1e-4 lies exactly on
+    the threshold (distance 0: a float32 evaluation may take it either way);
+    with the middle front half as opaque the nearest decision is the clamp of
+    the others instead."""
+    P = _scene([[0, 0, 1.0], [0, 0, 1.5], [0, 0, 2.0]], [[np.log(0.5)] * 3] * 3, [20.0] * 3, [[0.5] * 3] * 3)
+    out = R.decision_margins(P, 0, CAM, *IDENT, pixels=np.array([[32, 24]]))
+    assert out["pixel"][0] < 1e-12
+    assert R.MARGIN_KINDS[out["pixel_kind"][0]] == "T (1 - alpha) = 1e-4"
+    P["opacity_logits"][1] = 0.0  # alpha 0.5: the stop tests are now far (T (1 - alpha) = 0.005, 5e-5)
+    out = R.decision_margins(P, 0, CAM, *IDENT, pixels=np.array([[32, 24]]))
+    sigmoid20 = 1 / (1 + np.exp(-20.0))
+    want = []
+    for z in (1.0, 2.0):  # the two opaque fronts: q = |(0.5, 0.5)|^2 / sigma^2 at the pixel centre
+        q = 0.5 / ((CAM.fx * 0.5 / z) ** 2 + 0.3)
+        want.append(abs(sigmoid20 * np.exp(-0.5 * q) - 0.99) / 0.99)
+    assert out["pixel"][0] == pytest.approx(min(want), rel=1e-6)
+    assert R.MARGIN_KINDS[out["pixel_kind"][0]] == "alpha = 0.99"

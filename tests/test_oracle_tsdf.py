@@ -122,7 +122,7 @@ def test_frontal_plane_closed_form():
     bz = {b[2] for b in A}
     assert bz == set(range(int(np.floor((d - EPS) / BS)), int(np.floor((d + EPS) / BS)) + 1))
     checked = 0
-    for b, (ts, ws) in grid.items():
+    for b, (ts, ws, *_) in grid.items():
         for lz in range(8):
             for ly in range(8):
                 for lx in range(8):
@@ -157,7 +157,7 @@ def test_tilted_plane_general_pose():
     T.integrate(grid, depth, cam, R, t, S, EPS, 100.0)
     Tcw = _T_cw(R, t)
     upd = skipped = 0
-    for b, (ts, ws) in grid.items():
+    for b, (ts, ws, *_) in grid.items():
         lz, ly, lx = np.meshgrid(range(8), range(8), range(8), indexing="ij")
         g = np.stack([8 * b[0] + lx, 8 * b[1] + ly, 8 * b[2] + lz], -1).reshape(-1, 3)
         pc = (np.c_[(g + 0.5) * S32, np.ones(512)] @ Tcw.T)[:, :3]
