@@ -2,14 +2,20 @@
 (GSFusion's online optimisation, Sec. III-B.3) on one synthetic view at
 1200x680 with about 300k quadtree-seeded Gaussians, SH degree 3, float32.
 
-One step = gs_render_fwd + gs_loss_l1 + gs_render_bwd + gs_adam_step on the
-same view (inputs resident in HBM).  Prints one JSON line.
+One step = gs_train_step on the same view (inputs resident in HBM): the
+forward pass (projection, binning, compositing) with the L1 loss in its
+epilogue, then the backward pass fused with the Adam update, replayed as one
+CUDA graph.  Prints one JSON line; besides the single-view numbers it carries
+the measured ALU peaks of the raster passes' roofline, the clocks sampled
+during the timed region, the FP64 oracle timed on the host cores
+(cpu_baseline) and a compact batched-vs-view-by-view comparison of the
+8-view multi-view iteration (``multi_view``).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --gpus N > 1 runs N independent replicas under torchrun (one process per GPU,
 no collective on the data path); the value is the sum over replicas.
---impl reference times the FP64 CPU oracle on a bounded sample of the same
+--impl reference times the FP64 CPU oracle on whole iterations of the same
 workload (the only other place this script runs the oracle).
 """
 from __future__ import annotations
@@ -63,9 +69,17 @@ def algorithmic_bytes(n, deg, pairs, npx, n_tiles):
 FLOPS_PER_BLEND = {"raster_fwd": 27, "raster_bwd": 68}
 
 
-def alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 peak from unit counts: 152 SMs x 128 lanes x 2 flop (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def alu_roofline(dom, e_blend, dom_ms, alu):
+    """ALU roofline of a raster pass: algorithmic FP32 flops per blended pair
+    x blended pairs per launch over the launch time, against the FP32 FMA rate
+    measured by gs_measure_alu_peaks on this GPU."""
+    flops = e_blend * FLOPS_PER_BLEND[dom]
+    achieved = flops / (dom_ms * 1e-3) / 1e12 if dom_ms else 0.0
+    peak = alu["fma_tflops"]
+    return {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": load_traffic(dom),
+            "peak_kind": f"measured: FP32 FMA probe (gs_measure_alu_peaks) at {alu['fma_sm_mhz']:.0f} MHz",
+            "alg_flops_per_launch": flops, "ms_per_launch": dom_ms}
 
 
 class ClockSampler:
@@ -152,6 +166,9 @@ def run_ours(args, rank, world, local_rank):
     tdep = torch.as_tensor(v.target_depth, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # issue rates of the FP32 and MUFU pipes (the raster passes' ALU roofline)
+    alu = abi.gs_measure_alu_peaks(local_rank, 50000)
+
     # warm-up
     for _ in range(args.warmup):
         tr.step(trgb, tdep)
@@ -187,19 +204,29 @@ def run_ours(args, rank, world, local_rank):
     def restore():
         trainer_restore(tr, snap)
 
-    # timed region: K graph replays, CUDA events on the launch stream
+    # timed region: K graph replays, CUDA events on the launch stream.  It is
+    # repeated (the map restored between repeats) until the sampled region
+    # lasts at least 0.5 s, so that the clock sampler (50 ms period) sees it;
+    # ms_per_step is the median repeat.
     clocks = ClockSampler(local_rank)
     clocks.start()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        tr.replay()
-    e1.record(stream)
-    barrier()
+    reps = []
+    t_region = time.perf_counter()
+    while True:
+        restore()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tr.replay()
+        e1.record(stream)
+        barrier()
+        reps.append(e0.elapsed_time(e1))
+        if time.perf_counter() - t_region >= 0.5 or len(reps) >= 200:
+            break
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
+    ms_total = statistics.median(reps)
     tr.check_capacity()
     loss_end = float(tr.loss)
 
@@ -305,13 +332,7 @@ def run_ours(args, rank, world, local_rank):
     dom_ms = per_stage[dom]["ms_per_launch"]
     traffic = load_traffic(dom)
     if dom in FLOPS_PER_BLEND:
-        alu_peak = alu_peak_tflops(2070.0)
-        flops = e_blend * FLOPS_PER_BLEND[dom]
-        achieved = flops / (dom_ms * 1e-3) / 1e12 if dom_ms else 0.0
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "alg_flops_per_launch": flops, "ms_per_launch": dom_ms}
+        roof = alu_roofline(dom, e_blend, dom_ms, alu)
     else:
         achieved = alg[dom] / (dom_ms * 1e-3) / 1e9 if dom_ms else 0.0
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -338,9 +359,104 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "eager_ms_per_step": ms_eager / args.steps,
         "clocks": clk,
+        "timed_repeats": {"count": len(reps), "ms": reps, "note": "K steps each, map restored between repeats; "
+                          "ms_per_step from the median"},
+        "alu_peaks": {"fp32_fma_tflops": alu["fma_tflops"], "mufu_ex2_gops": alu["ex2_gops"],
+                      "fma_per_sm_clk": alu["fma_per_sm_clk"], "ex2_per_sm_clk": alu["ex2_per_sm_clk"],
+                      "sm_mhz": alu["fma_sm_mhz"], "num_sms": alu["num_sms"]},
         "loss_end": loss_end,
     }
     return out
+
+
+def run_scale_stress(args, rank, world, local_rank):
+    """The scale-stress configuration: 1752x1168 (fx 1200), 1M quadtree-seeded
+    Gaussians of which 20% are large (log-scale U[-1, 0], logit +2), SH
+    degree 3: about 1.1e9 (tile, Gaussian) pairs, every tile list beyond the
+    per-tile sort, so the binning takes the radix path, whose pair count the
+    forward pass reads back once (sync mode: the iteration runs eagerly, one
+    gs_train_step per step).  Reported on Gaussian-pixel evals/s (blended
+    pairs per second) like the single view, which it is compared with."""
+    import torch
+
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import Context, GaussianModel, Trainer
+    from synth import workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    abi.load()
+    t_gen = time.perf_counter()
+    w = workloads.scale_stress()
+    t_gen = time.perf_counter() - t_gen
+    v = w.views[0]
+    ctx = Context(local_rank)
+    tr = Trainer(GaussianModel(w.params, device=dev), v.cam, v.pose.R, v.pose.t, ctx=ctx, device=local_rank)
+    trgb = torch.as_tensor(v.target_rgb, device=dev)
+    tdep = torch.as_tensor(v.target_depth, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    alu = abi.gs_measure_alu_peaks(local_rank, 50000)
+    for _ in range(args.warmup):
+        tr.step(trgb, tdep)
+    abi.gs_set_eval_counting(ctx.handle, True)
+    tr.step(trgb, tdep)
+    st = ctx.stats()
+    abi.gs_set_eval_counting(ctx.handle, False)
+    pairs, e_blend, e_tiled = st["n_pairs"], st["evals_blended"], st["evals_tiled"]
+    snap = trainer_snapshot(tr)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tr.step(trgb, tdep)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    trainer_restore(tr, snap)
+    launches0 = ctx.stats()["kernel_launches"]
+    abi.gs_set_profiling(ctx.handle, True)
+    for _ in range(args.steps):
+        tr.step(trgb, tdep)
+    stages = abi.gs_profile_read(ctx.handle)
+    abi.gs_set_profiling(ctx.handle, False)
+    launches = ctx.stats()["kernel_launches"] - launches0
+    ms, = max_over_ranks([ms], world)
+    it_s = whole_job_rate(args.steps, world, ms)
+    per_stage = {k: {"ms_per_launch": (t / c if c else 0.0), "launches": c} for k, (t, c) in stages.items()}
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms = per_stage[dom]["ms_per_launch"]
+    if dom in FLOPS_PER_BLEND:
+        roof = alu_roofline(dom, e_blend, dom_ms, alu)
+    else:
+        n_tiles = ((v.cam.width + 15) // 16) * ((v.cam.height + 15) // 16)
+        alg = algorithmic_bytes(w.n, w.sh_degree, pairs, v.cam.width * v.cam.height, n_tiles)
+        alg["pair_sort"] = pairs * 8 * 2 * 2  # radix path: 2 passes over (tile, id) u32 pairs, read + write
+        alg["duplicate"] = w.n * 12 + pairs * 8
+        hbm_peak, peak_kind = load_peaks()
+        achieved = alg.get(dom, 0) / (dom_ms * 1e-3) / 1e9 if dom_ms else 0.0
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg.get(dom), "ms_per_launch": dom_ms}
+    return {
+        "metric": METRIC, "value": it_s, "unit": "it/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "scale_stress 1752x1168 (fx 1200), 1M quadtree-seeded Gaussians, 20% large "
+                               "(log-scale U[-1,0], logit +2), SH degree 3, fp32, loss 0.8 L1(rgb) + 0.2 L1(depth)",
+                   "n_gaussians": w.n, "width": v.cam.width, "height": v.cam.height, "tile": "16x16",
+                   "pairs": pairs, "binning": "radix path (every tile list > 4096)", "parallelism": f"replicas{world}",
+                   "timing": "eager gs_train_step per step (sync mode: one host read of the pair count)",
+                   "l2": "no flush: per-step working set (~25 GB of pairs) > 129 MB L2", "host_generation_s": t_gen},
+        "gaussian_pixel_evals_per_s": e_blend * it_s, "evals_blended_per_iter": e_blend,
+        "evals_tiled_per_iter": e_tiled,
+        "roofline": roof, "stages": per_stage,
+        "e2e": None, "gpu_launches": launches, "clocks": clk,
+        "alu_peaks": {"fp32_fma_tflops": alu["fma_tflops"], "mufu_ex2_gops": alu["ex2_gops"]},
+    }
 
 
 def trainer_snapshot(tr):
@@ -408,8 +524,9 @@ def run_multi_view(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     abi.load()
     t_gen = time.perf_counter()
-    w = workloads.multi_view()
+    w = workloads.multi_view(workers=min(8, os.cpu_count() or 1))
     t_gen = time.perf_counter() - t_gen
+    alu = abi.gs_measure_alu_peaks(local_rank, 50000)
     views = [(v.cam, v.pose.R, v.pose.t) for v in w.views]
     trgb = [torch.as_tensor(v.target_rgb, device=dev) for v in w.views]
     tdep = [torch.as_tensor(v.target_depth, device=dev) for v in w.views]
@@ -486,13 +603,7 @@ def run_multi_view(args, rank, world, local_rank):
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms = per_stage[dom]["ms_per_launch"]
     it_s = whole_job_rate(args.steps, world, ms_b)
-    roof = None
-    if dom in FLOPS_PER_BLEND:
-        alu_peak = alu_peak_tflops(2070.0)
-        achieved = e_blend * FLOPS_PER_BLEND[dom] / (dom_ms * 1e-3) / 1e12 if dom_ms else 0.0
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "ms_per_launch": dom_ms}
+    roof = alu_roofline(dom, e_blend, dom_ms, alu) if dom in FLOPS_PER_BLEND else None
     return {
         "metric": METRIC, "value": it_s, "unit": "it/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -518,6 +629,63 @@ def run_multi_view(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+
+def multi_view_compare(local_rank, steps=100, warmup=5):
+    """The batched multi-view iteration (8 views of uneven size, 2 x 640x480,
+    4 x 1200x680, 2 x 1752x1168, one 500k-Gaussian map) against the same
+    iteration run view by view, both graph-captured and starting from the
+    same map: the batched-vs-sequential comparison in compact form for the
+    default bench line."""
+    import argparse as _ap
+
+    import torch
+
+    from paper_2408_12677_gb300.torch_api import BatchedTrainer, Context, GaussianModel
+    from synth import workloads
+
+    dev = torch.device("cuda", local_rank)
+    t_gen = time.perf_counter()
+    w = workloads.multi_view(workers=min(8, os.cpu_count() or 1))
+    t_gen = time.perf_counter() - t_gen
+    views = [(v.cam, v.pose.R, v.pose.t) for v in w.views]
+    trgb = [torch.as_tensor(v.target_rgb, device=dev) for v in w.views]
+    tdep = [torch.as_tensor(v.target_depth, device=dev) for v in w.views]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, k):
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    ctx_b = Context(local_rank)
+    tb = BatchedTrainer(GaussianModel(w.params, device=dev), views, ctx=ctx_b)
+    tb.autotune(reps=2)
+    for _ in range(warmup):
+        tb.step(trgb, tdep)
+    snap = trainer_snapshot(tb)
+    tb.capture(trgb, tdep)
+    for _ in range(warmup):
+        tb.replay()
+    trainer_restore(tb, snap)
+    ms_b = timed(tb.replay, steps)
+    tb.check_capacity()
+    loss_b = float(tb.loss)
+    a = _ap.Namespace(steps=steps, warmup=warmup)
+    ms_s, ms_s_eager, loss_s = run_sequential(a, w, views, trgb, tdep, tb.rcfg, timed, local_rank, snap)
+    ctx_b.close()
+    return {"views": [[c.width, c.height] for c, _, _ in views], "n_gaussians": w.n,
+            "tile": f"{tb.rcfg.tile_w}x{tb.rcfg.tile_h}", "steps": steps,
+            "batched_graph_ms": ms_b / steps, "sequential_graph_ms": ms_s / steps,
+            "sequential_eager_ms": ms_s_eager / steps, "speedup_vs_sequential_graph": ms_s / ms_b,
+            "loss_batched": loss_b, "loss_sequential": loss_s, "host_generation_s": t_gen,
+            "note": "both forms from the same map after warm-up; the losses are after the same K steps"}
 
 
 STREAM_SEEDING = {"var_thr": 0.035, "min_size": 2}  # about 50k Gaussians from the first 1200x680 frame
@@ -677,137 +845,158 @@ def load_traffic(kernel):
 # ---------------------------------------------------------------------------
 # oracle timing (cpu_baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_projection(w):
-    """Times the oracle's projection of all Gaussians of the view, forward and
-    backward (autograd of the sum of its outputs), once; returns (seconds,
-    per-Gaussian 2D means and 3-sigma radii for selecting the Gaussians that
-    reach a pixel sample, the indices they belong to, the flat parameters and
-    their learning rates for the Adam sample)."""
+def _oracle_setup(w):
+    """float64 leaves, the view, its 16 x 16 tiles and each tile's pixels."""
+    import numpy as np
+
+    from oracle import render as R
+    v = w.views[0]
+    tx, ty = -(-v.cam.width // 16), -(-v.cam.height // 16)
+    return v, tx * ty, np.asarray(v.pose.R, np.float64), np.asarray(v.pose.t, np.float64), R
+
+
+def oracle_iteration(w, tiles=None):
+    """One iteration of the FP64 oracle on the host cores, as it stands:
+    projection of every Gaussian, compositing (Eq. 11) of the pixels of
+    ``tiles`` (16 x 16 tiles, every tile when None) with the Gaussians whose
+    3-sigma box meets each tile (exact selection: the others have q > 9
+    there), the L1 loss (Eq. 12 + depth term) of those pixels, autograd
+    backward to every parameter, and a float64 Adam step over ALL parameters.
+    Returns seconds of (projection + compositing forward, backward, Adam) and
+    the blended (pixel, Gaussian) pairs."""
     import numpy as np
     import torch
 
-    from oracle import render as R
-
-    v = w.views[0]
-    Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
+    from oracle import adam as oadam
+    v, n_tiles, Rm, t, R = _oracle_setup(w)
+    pix, sizes = R.tile_pixels(v.cam, range(n_tiles) if tiles is None else tiles, sizes=True)
+    lin = pix[:, 1] * v.cam.width + pix[:, 0]
+    trgb = torch.as_tensor(np.asarray(v.target_rgb, np.float64).reshape(3, -1)[:, lin])
+    tdep = torch.as_tensor(np.asarray(v.target_depth, np.float64).reshape(-1)[lin])
     t0 = time.perf_counter()
     P = R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
-    out = R.project(P, w.sh_degree, v.cam, Rm, t)
-    total = sum(out[k].sum() for k in ("mean2d", "cov2d", "depth", "rgb", "opacity"))
-    torch.autograd.grad(total, [P[k] for k in R.PARAM_NAMES], allow_unused=True)
-    t_proj = time.perf_counter() - t0
-    cov = out["cov2d"].detach().numpy()
-    tr, det = cov[:, 0, 0] + cov[:, 1, 1], cov[:, 0, 0] * cov[:, 1, 1] - cov[:, 0, 1] ** 2
-    lam = 0.5 * tr + np.sqrt(np.maximum(0.25 * tr * tr - det, 0.0))
-    from oracle import adam as oadam
+    out = R.render(P, w.sh_degree, v.cam, Rm, t, pixels=pix, prefilter="bbox", chunk_px=sizes)
+    if len(pix):
+        L = R.loss_l1(out["color"], out["depth"], trgb, tdep)
+    else:  # the projection alone: differentiate the sum of its outputs
+        L = sum(out["proj"][k].sum() for k in ("mean2d", "cov2d", "depth", "rgb", "opacity"))
+    t1 = time.perf_counter()
+    g = torch.autograd.grad(L, [P[k] for k in R.PARAM_NAMES])
+    t2 = time.perf_counter()
     cfg = oadam.AdamCfg()
-    return (t_proj, out["mean2d"].detach().numpy(), 3.0 * np.sqrt(lam) + 1.0, out["idx"].numpy(),
-            oadam.flatten(w.params), oadam.lr_per_element(w.n, w.sh_degree, cfg))
+    flat = oadam.flatten(w.params)
+    oadam.adam_step(flat, np.concatenate([x.numpy().ravel() for x in g]), np.zeros_like(flat),
+                    np.zeros_like(flat), 1, oadam.lr_per_element(w.n, w.sh_degree, cfg), cfg)
+    t3 = time.perf_counter()
+    return t1 - t0, t2 - t1, t3 - t2, int(out["n_contrib"].sum())
 
 
-def gaussians_near_pixels(mu, rad, pix, W, H):
-    """Mask of the Gaussians whose box mu +- rad holds the centre of one of
-    the pixels pix [k, 2] (x, y), through a summed-area table of the pixels."""
-    import numpy as np
-    occ = np.zeros((H + 1, W + 1), np.int64)
-    np.add.at(occ, (pix[:, 1] + 1, pix[:, 0] + 1), 1)
-    occ = occ.cumsum(0).cumsum(1)
-    x0 = np.clip(np.ceil(mu[:, 0] - rad - 0.5), 0, W).astype(np.int64)
-    x1 = np.clip(np.floor(mu[:, 0] + rad - 0.5), -1, W - 1).astype(np.int64)
-    y0 = np.clip(np.ceil(mu[:, 1] - rad - 0.5), 0, H).astype(np.int64)
-    y1 = np.clip(np.floor(mu[:, 1] + rad - 0.5), -1, H - 1).astype(np.int64)
-    ok = (x1 >= x0) & (y1 >= y0)
-    x0, x1, y0, y1 = np.minimum(x0, W - 1), np.maximum(x1, 0), np.minimum(y0, H - 1), np.maximum(y1, 0)
-    hits = occ[y1 + 1, x1 + 1] - occ[y0, x1 + 1] - occ[y1 + 1, x0] + occ[y0, x0]
-    return ok & (hits > 0)
-
-
-def oracle_sample(w, n_pix, seed=0, adam_frac=1.0, proj=None):
-    """Time the FP64 oracle on a bounded sample of one iteration: forward +
-    backward over n_pix random pixels (prefilter mode) with the Gaussians
-    that reach them, and the Adam update of a random adam_frac of the
-    parameters.  The projection of all Gaussians (forward + backward, timed
-    once per run by oracle_projection, ``proj``) is added whole; the pixel
-    part (the sample's time less the projection of its Gaussians, timed
-    alone) is extrapolated to the full image, the Adam part to every
-    parameter.
-    Returns (seconds per iteration, description, threads, proj)."""
+def oracle_tile_elements(w):
+    """Per 16 x 16 tile: pixels x Gaussians whose 3-sigma box meets it (the
+    oracle's compositing work, which its time follows)."""
     import numpy as np
     import torch
+    v, n_tiles, Rm, t, R = _oracle_setup(w)
+    with torch.no_grad():
+        pr = R.project(R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}), w.sh_degree,
+                       v.cam, Rm, t)
+    mu = pr["mean2d"].numpy()
+    cov = pr["cov2d"].numpy()
+    ex = np.sqrt(9.0 * (1 + 1e-3) * cov[:, 0, 0])  # the oracle's selection box (q <= 9 (1 + 1e-3))
+    ey = np.sqrt(9.0 * (1 + 1e-3) * cov[:, 1, 1])
+    W, H, tx, ty = v.cam.width, v.cam.height, -(-v.cam.width // 16), -(-v.cam.height // 16)
+    # tile k spans the pixel centres [16 k + 0.5, min(16 k + 15.5, W - 0.5)]; a Gaussian meets the tiles
+    # whose centre span its box mu +- e reaches (a 2D difference array counts them per tile)
+    cx0 = np.maximum(np.ceil((mu[:, 0] - ex - 15.5) / 16), 0).astype(np.int64)
+    cx1 = np.minimum(np.floor((mu[:, 0] + ex - 0.5) / 16), tx - 1).astype(np.int64)
+    cy0 = np.maximum(np.ceil((mu[:, 1] - ey - 15.5) / 16), 0).astype(np.int64)
+    cy1 = np.minimum(np.floor((mu[:, 1] + ey - 0.5) / 16), ty - 1).astype(np.int64)
+    ok = (cx1 >= cx0) & (cy1 >= cy0) & (mu[:, 0] - ex <= W - 0.5) & (mu[:, 1] - ey <= H - 0.5)
+    d = np.zeros((ty + 1, tx + 1), np.int64)
+    np.add.at(d, (cy0[ok], cx0[ok]), 1)
+    np.add.at(d, (cy0[ok], cx1[ok] + 1), -1)
+    np.add.at(d, (cy1[ok] + 1, cx0[ok]), -1)
+    np.add.at(d, (cy1[ok] + 1, cx1[ok] + 1), 1)
+    cnt = d.cumsum(0).cumsum(1)[:ty, :tx].ravel()
+    npx = np.array([len(R.tile_pixels(v.cam, [k])) for k in range(n_tiles)])
+    return cnt * npx
+
+
+def oracle_sample(w, n_tiles_sample, seed=0):
+    """Bounded sample of one oracle iteration: ``n_tiles_sample`` uniformly
+    random 16 x 16 tiles timed whole (compositing forward + backward with all
+    their Gaussians), the compositing part scaled to all tiles (an unbiased
+    estimate of the whole image's), plus the projection of every Gaussian
+    and Adam on every parameter, timed whole.  Returns (seconds per
+    iteration, description, threads)."""
+    import numpy as np
+    import torch
+    v, n_tiles, _, _, _ = _oracle_setup(w)
+    elems = oracle_tile_elements(w)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(n_tiles, min(n_tiles_sample, n_tiles), replace=False)
+    # the projection (of every Gaussian) alone, forward and backward
+    t_proj_f, t_proj_b, _, _ = oracle_iteration(w, tiles=[])
+    t_f, t_b, t_adam, blended = oracle_iteration(w, tiles=pick)
+    frac = float(elems[pick].sum()) / max(float(elems.sum()), 1.0)
+    t_tiles = max(t_f + t_b - t_proj_f - t_proj_b, 0.0)
+    comp = t_tiles * n_tiles / len(pick)  # uniformly sampled tiles: unbiased for the whole image
+    t_iter = t_proj_f + t_proj_b + comp + t_adam
+    desc = (f"{len(pick)} uniformly random 16x16 tiles of the {v.cam.width}x{v.cam.height} view timed whole "
+            f"(compositing forward + L1 loss + backward with all Gaussians meeting them, {t_tiles:.2f} s, "
+            f"{100 * frac:.2f}% of the image's pixel x Gaussian work), extrapolated to all {n_tiles} tiles "
+            f"({comp:.1f} s); projection of all {w.n} Gaussians forward + backward ({t_proj_f + t_proj_b:.2f} s) "
+            f"and float64 Adam on all parameters ({t_adam:.2f} s) timed whole")
+    return t_iter, desc, torch.get_num_threads()
+
+
+def oracle_small_iteration():
+    """A whole oracle iteration (brute force, every Gaussian at every pixel)
+    on the 64 x 48 / 500-Gaussian configuration: seconds."""
+    import numpy as np
 
     from oracle import adam as oadam
     from oracle import render as R
-
-    if proj is None:
-        proj = oracle_projection(w)
-    t_proj, mu, rad, idx, flat, lr_all = proj
+    from synth import workloads
+    w = workloads.tiny_random()
     v = w.views[0]
-    H, W = v.cam.height, v.cam.width
-    rng = np.random.default_rng(seed)
-    pix = np.stack([rng.integers(0, W, n_pix), rng.integers(0, H, n_pix)], 1)
-    wc = rng.standard_normal((3, n_pix))
-    wd = rng.standard_normal(n_pix)
-    Rm, t = v.pose.R.astype(np.float64), v.pose.t.astype(np.float64)
-    # the Gaussians whose 3-sigma box holds a sampled pixel centre (the others
-    # cannot take part in those pixels)
-    near = gaussians_near_pixels(mu, rad, pix, W, H)
-    sub = {k: np.asarray(w.params[k])[idx[near]] for k in R.PARAM_NAMES}
-    t1 = time.perf_counter()
-    R.weighted_pixel_gradients(sub, w.sh_degree, v.cam, Rm, t, pix, wc, wd, None, prefilter=True)
-    t_pix = time.perf_counter() - t1
-    # the same Gaussians' projection alone (forward and backward), so the pixel
-    # part is the difference
-    t1 = time.perf_counter()
-    Ps = R.to_tensors({k: np.asarray(sub[k], np.float64) for k in R.PARAM_NAMES}, requires_grad=True)
-    outs = R.project(Ps, w.sh_degree, v.cam, Rm, t)
-    tot = sum(outs[k].sum() for k in ("mean2d", "cov2d", "depth", "rgb", "opacity"))
-    torch.autograd.grad(tot, [Ps[k] for k in R.PARAM_NAMES], allow_unused=True)
-    t_sub = time.perf_counter() - t1
+    t0 = time.perf_counter()
+    _, g, _ = R.gradients(w.params, w.sh_degree, v.cam, np.asarray(v.pose.R, np.float64),
+                          np.asarray(v.pose.t, np.float64), v.target_rgb, v.target_depth, with_pose=False)
     cfg = oadam.AdamCfg()
-    k = max(1, int(adam_frac * flat.size))
-    o = int(rng.integers(0, flat.size - k + 1))  # a random contiguous slice of the flat parameters
-    lr = lr_all[o:o + k]
-    p = flat[o:o + k].copy()
-    t2 = time.perf_counter()
-    oadam.adam_step(p, rng.standard_normal(p.size), np.zeros_like(p), np.zeros_like(p), 1, lr, cfg)
-    t_adam = (time.perf_counter() - t2) / max(adam_frac, 1e-12)
-    per_pixel = max(t_pix - t_sub, 0.0) / n_pix
-    t_iter = t_proj + per_pixel * H * W + t_adam
-    desc = (f"oracle forward+backward at {n_pix} random pixels of the {W}x{H} view with the {int(near.sum())} "
-            f"Gaussians reaching them ({t_pix:.3f} s, of which their projection {t_sub:.3f} s), per-pixel time "
-            f"extrapolated to {H * W} pixels; projection "
-            f"of all {w.n} Gaussians, forward and backward, timed once per run ({t_proj:.2f} s); float64 Adam on "
-            f"{100 * adam_frac:.3g}% of the {flat.size} parameters extrapolated to all ({t_adam:.2f} s)")
-    return t_iter, desc, torch.get_num_threads(), proj
+    flat = oadam.flatten(w.params)
+    oadam.adam_step(flat, np.concatenate([g[k].numpy().ravel() for k in R.PARAM_NAMES]), np.zeros_like(flat),
+                    np.zeros_like(flat), 1, oadam.lr_per_element(w.n, w.sh_degree, cfg), cfg)
+    return time.perf_counter() - t0
 
 
 def run_reference(args):
-    """The reference arm: the oracle, as it stands, on the host cores; each
-    step is a bounded sample sized so the whole run takes about two minutes."""
+    """The reference arm: the FP64 oracle, as it stands, on the host cores,
+    timing WHOLE iterations of the single-view workload (every pixel, every
+    Gaussian, Adam on every parameter).  An iteration takes tens of seconds,
+    so the arm runs as many as fit in about two minutes (at least one) and
+    reports that true count in ``steps`` (``warmup`` 0); the requested
+    --steps / --warmup are echoed under ``requested``."""
     from synth import workloads
     w = workloads.single_view()
-    proj = oracle_projection(w)
-    t_cal0 = time.perf_counter()
-    oracle_sample(w, 32, seed=12345, adam_frac=0.01, proj=proj)
-    t_cal = time.perf_counter() - t_cal0
-    per_step = 120.0 / max(1, args.steps + args.warmup)
-    # at least 256 pixels per step: the oracle call has a fixed cost that a
-    # smaller sample would spread over too few pixels
-    n_pix = int(max(256, min(args.ref_pixels, 32 * per_step / max(t_cal, 1e-3))))
-    times = []
-    desc, cores = "", 0
-    for i in range(args.warmup + args.steps):
-        t_iter, desc, cores, _ = oracle_sample(w, n_pix, seed=i, adam_frac=0.01, proj=proj)
-        if i >= args.warmup:
-            times.append(t_iter)
-    value = 1.0 / statistics.mean(times)
+    times, blended = [], 0
+    t_start = time.perf_counter()
+    while len(times) < max(1, args.steps) and (not times or time.perf_counter() - t_start + times[-1] < 120.0):
+        t_f, t_b, t_a, blended = oracle_iteration(w)
+        times.append(t_f + t_b + t_a)
+    import torch
+    value = len(times) / sum(times)
+    desc = (f"{len(times)} whole iterations (projection, compositing of all {w.views[0].cam.width}x"
+            f"{w.views[0].cam.height} pixels with {blended} blended pairs, L1 loss, backward, Adam on all "
+            f"parameters), {[round(x, 2) for x in times]} s")
     return {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": 1, "steps": len(times),
+        "warmup": 0, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": w.n},
-        "cpu_baseline": {"value": value, "unit": "it/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: " + desc},
+        "requested": {"steps": args.steps, "warmup": args.warmup},
+        "cpu_baseline": {"value": value, "unit": "it/s", "cores": torch.get_num_threads(), "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -818,9 +1007,11 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-pixels", type=int, default=12288)
+    ap.add_argument("--baseline-tiles", type=int, default=256,
+                    help="cpu_baseline: random 16x16 tiles timed whole by the oracle (the rest extrapolated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single_view", choices=["single_view", "multi_view", "streaming"],
+    ap.add_argument("--workload", default="single_view",
+                    choices=["single_view", "multi_view", "streaming", "scale_stress"],
                     help="multi_view: the batched 8-view iteration vs the same iteration view by view")
     ap.add_argument("--frames", type=int, default=40, help="streaming: frames of the sequence")
     ap.add_argument("--novelty", choices=("tsdf", "alpha"), default="tsdf",
@@ -829,6 +1020,8 @@ def main():
                     help="streaming: seed new Gaussians with the host quadtree instead of gs_seed_quadtree")
     ap.add_argument("--global-epochs", type=int, default=2,
                     help="streaming: passes of the offline optimisation over the keyframe list afterwards")
+    ap.add_argument("--no-multi-view", action="store_true",
+                    help="single_view: skip the compact batched-vs-sequential multi-view comparison")
     ap.add_argument("--no-compare", action="store_true",
                     help="multi_view: skip the view-by-view comparison arm (e.g. for a profiler capture)")
     args = ap.parse_args()
@@ -842,8 +1035,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    if args.workload in ("multi_view", "streaming"):
-        run = run_multi_view if args.workload == "multi_view" else run_streaming
+    if args.workload in ("multi_view", "streaming", "scale_stress"):
+        run = {"multi_view": run_multi_view, "streaming": run_streaming, "scale_stress": run_scale_stress}[args.workload]
         out = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(out))
@@ -852,12 +1045,14 @@ def main():
             dist.destroy_process_group()
         return
     out = run_ours(args, rank, world, local_rank)
+    if rank == 0 and not args.no_multi_view:
+        out["multi_view"] = multi_view_compare(local_rank)
     if rank == 0:
         if not args.no_cpu_baseline:
             from synth import workloads
-            t_iter, desc, cores, _ = oracle_sample(workloads.single_view(), args.ref_pixels)
+            t_iter, desc, cores = oracle_sample(workloads.single_view(), args.baseline_tiles)
             out["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "it/s", "cores": cores, "kind": "oracle",
-                                   "sample": desc}
+                                   "sample": desc, "whole_iteration_64x48_500_s": oracle_small_iteration()}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -582,6 +582,13 @@ gs_status gs_measure_alu_peaks(int device, int32_t iters, gs_alu_peaks *out);
 gs_status gs_get_projection(gs_ctx *ctx, float *mean2d, float *cov2d, float *depth, float *rgb,
                             float *opacity, int32_t *tiles, gs_stream_t stream);
 
+/* Copy the last forward pass's per-tile list ranges to `ranges` (device
+ * uint32 [n_tiles, 2]: [first, last + 1) into the depth-sorted pair list,
+ * (0, 0) for an empty tile); n_tiles must be the forward pass's tile count
+ * (the views' tiles end to end, row-major within a view).  For parity checks
+ * of the binning and for picking the longest-list tiles. */
+gs_status gs_get_tile_ranges(gs_ctx *ctx, uint32_t *ranges, int64_t n_tiles, gs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

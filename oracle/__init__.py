@@ -6,6 +6,10 @@ CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
 The product path (``paper_2408_12677_gb300``) never imports it and shares no
 code with it; both sides only share the seeded input generators in ``synth/``.
+Those hold none of the rasterizer's arithmetic, but ``synth.quadtree`` seeds
+the synthetic Gaussian sets with the paper's quadtree and Eq. 10 (input
+plumbing, on the host); ``oracle.quadtree`` is a separate implementation of
+the same seeding, written independently and cross-checked against it.
 
 Modules
 -------

@@ -199,46 +199,64 @@ def pixel_centers(cam) -> torch.Tensor:
     return torch.stack([ii.flatten() + 0.5, jj.flatten() + 0.5], -1)
 
 
+def _pixel_chunks(U: torch.Tensor, mu, conic, cov, cfg: RasterCfg, prefilter, chunk_elems: int, chunk_px):
+    """The pixel chunks of ``composite`` / ``decision_margins``: yields
+    (start, stop, use) with ``use`` None (every Gaussian) or the indices of
+    the Gaussians kept for the chunk (see ``composite``)."""
+    n, M = mu.shape[0], U.shape[0]
+    if prefilter == "bbox":
+        sizes = [chunk_px] * (-(-M // chunk_px)) if isinstance(chunk_px, int) else list(chunk_px)
+        # the box of q <= 9 (1 + 1e-3): also every pair that decision_margins
+        # counts as near the support (keeping more Gaussians changes nothing)
+        qb = cfg.q_max * (1 + 1e-3)
+        ext = torch.stack([torch.sqrt(qb * cov[:, 0, 0]), torch.sqrt(qb * cov[:, 1, 1])], -1)
+        ext = ext * (1 + 1e-9) + 1e-9
+    else:
+        step = max(1, chunk_elems // max(n, 1))
+        sizes = [step] * (-(-M // step))
+    s0 = 0
+    for size in sizes:
+        Uc = U[s0:s0 + size]
+        use = None
+        if prefilter == "bbox" and n > 0:
+            lo, hi = Uc.min(0).values, Uc.max(0).values
+            gap = torch.maximum(lo[None] - mu, mu - hi[None]).clamp(min=0.0)
+            use = torch.nonzero((gap <= ext).all(1)).flatten()
+        elif prefilter and n > 0:
+            use = torch.nonzero((_quad_form(Uc, mu, conic) <= cfg.q_max).any(0)).flatten()
+        yield s0, s0 + Uc.shape[0], use
+        s0 += size
+
+
 def composite(proj: dict, U: torch.Tensor, cfg: RasterCfg = RasterCfg(), prefilter=False,
-              chunk_elems: int = 1 << 21, chunk_px: int = 256):
+              chunk_elems: int = 1 << 21, chunk_px=256):
     """Front-to-back compositing at pixel centres U [M, 2] (Eq. 11), no tiling.
 
     ``prefilter``: False evaluates every Gaussian at every pixel; True drops,
     per chunk of pixels, the Gaussians whose q exceeds 9 at every pixel of
-    the chunk; "bbox" takes the pixels ``chunk_px`` at a time (pass them
-    grouped by image region) and keeps the Gaussians whose q <= 9 ellipse's
-    bounding box, mu +- 3 sqrt(diag Sigma^), meets the chunk's bounding box
-    -- the others have q > 9 at every pixel of the chunk.  Dropped Gaussians
+    the chunk; "bbox" takes the pixels ``chunk_px`` at a time (an int, or
+    a list of group sizes: pass them grouped by image region, e.g. the tiles
+    of ``tile_pixels``) and keeps the Gaussians whose q <= 9 (1 + 1e-3)
+    ellipse's bounding box, mu +- sqrt(9.009 diag Sigma^), meets the chunk's
+    bounding box -- the others have q > 9 at every pixel of the chunk.  Dropped Gaussians
     contribute exactly nothing, so all three give the same values."""
     o = proj["order"]
     mu, conic, opac = proj["mean2d"][o], proj["conic"][o], proj["opacity"][o]
     rgb, z = proj["rgb"][o], proj["depth"][o]
-    n = mu.shape[0]
     M = U.shape[0]
+    if M == 0:
+        return (torch.zeros((0, 3), dtype=DT), torch.zeros(0, dtype=DT), torch.zeros(0, dtype=DT),
+                torch.zeros(0, dtype=torch.long))
     cols, deps, Ts, ns = [], [], [], []
-    if prefilter == "bbox":
-        cov = proj["cov2d"][o].detach()
-        ext = torch.stack([torch.sqrt(cfg.q_max * cov[:, 0, 0]), torch.sqrt(cfg.q_max * cov[:, 1, 1])], -1)
-        ext = ext * (1 + 1e-9) + 1e-9
-        step = chunk_px
-    else:
-        step = max(1, chunk_elems // max(n, 1))
-    for s in range(0, M, step):
-        Uc = U[s:s + step]
-        if prefilter == "bbox" and n > 0:
-            with torch.no_grad():
-                lo, hi = Uc.min(0).values, Uc.max(0).values
-                m = mu.detach()
-                gap = torch.maximum(lo[None] - m, m - hi[None]).clamp(min=0.0)
-                use = torch.nonzero((gap <= ext).all(1)).flatten()
-            c, d, T, k = _composite_chunk(Uc, mu[use], conic[use], opac[use], rgb[use], z[use], cfg)
-        elif prefilter and n > 0:
-            with torch.no_grad():
-                qc = _quad_form(Uc, mu.detach(), conic.detach())
-                use = torch.nonzero((qc <= cfg.q_max).any(0)).flatten()
-            c, d, T, k = _composite_chunk(Uc, mu[use], conic[use], opac[use], rgb[use], z[use], cfg)
-        else:
+    with torch.no_grad():
+        chunks = list(_pixel_chunks(U, mu.detach(), conic.detach(), proj["cov2d"][o].detach(), cfg, prefilter,
+                                    chunk_elems, chunk_px))
+    for s0, s1, use in chunks:
+        Uc = U[s0:s1]
+        if use is None:
             c, d, T, k = _composite_chunk(Uc, mu, conic, opac, rgb, z, cfg)
+        else:
+            c, d, T, k = _composite_chunk(Uc, mu[use], conic[use], opac[use], rgb[use], z[use], cfg)
         cols.append(c)
         deps.append(d)
         Ts.append(T)
@@ -246,22 +264,25 @@ def composite(proj: dict, U: torch.Tensor, cfg: RasterCfg = RasterCfg(), prefilt
     return torch.cat(cols), torch.cat(deps), torch.cat(Ts), torch.cat(ns)
 
 
-def tile_pixels(cam, tiles, tile_w: int = 16, tile_h: int = 16) -> np.ndarray:
+def tile_pixels(cam, tiles, tile_w: int = 16, tile_h: int = 16, sizes: bool = False):
     """Integer (i, j) pixel coordinates [M, 2] of the listed tiles (tile
-    index = ty * tiles_x + tx), tile by tile, clipped to the image: pass them
-    with prefilter="bbox" and chunk_px = tile_w * tile_h."""
+    index = ty * tiles_x + tx), tile by tile, clipped to the image; with
+    ``sizes`` also the pixel count of each tile (pass both to ``render``
+    with prefilter="bbox" and chunk_px = the counts)."""
     tx = -(-cam.width // tile_w)
-    out = []
+    out, counts = [], []
     for t in tiles:
         x0, y0 = (int(t) % tx) * tile_w, (int(t) // tx) * tile_h
         jj, ii = np.meshgrid(np.arange(y0, min(y0 + tile_h, cam.height)),
                              np.arange(x0, min(x0 + tile_w, cam.width)), indexing="ij")
         out.append(np.stack([ii.ravel(), jj.ravel()], 1))
-    return np.concatenate(out) if out else np.zeros((0, 2), np.int64)
+        counts.append(out[-1].shape[0])
+    pix = np.concatenate(out) if out else np.zeros((0, 2), np.int64)
+    return (pix, counts) if sizes else pix
 
 
 def render(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = RasterCfg(), pixels=None,
-           prefilter=False, chunk_px: int = 256) -> dict:
+           prefilter=False, chunk_px=256) -> dict:
     """Render colour [3, M], depth [M], alpha [M] (M = H*W unless ``pixels``
     [M, 2] integer (i, j) coordinates are given).  Full images are reshaped to
     [3, H, W] / [H, W]."""
@@ -329,7 +350,7 @@ def gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, target_rgb, target_
 
 def weighted_pixel_gradients(params: dict, sh_degree: int, cam, R_cw, t_cw, pixels, w_color, w_depth,
                              w_alpha=None, rcfg=RasterCfg(), with_pose: bool = True, prefilter=True,
-                             chunk_px: int = 256):
+                             chunk_px=256):
     """Gradient of sum_s <w_color[:, s], C(u_s)> + w_depth[s] D(u_s) + w_alpha[s] A(u_s)
     over the listed pixels only (a sparse upstream gradient)."""
     P = to_tensors(params, requires_grad=True)
@@ -421,11 +442,11 @@ def multiview_weighted_gradients(params: dict, sh_degree: int, cams, poses, w_co
 # ----------------------------------------------------------------------------
 # distances to the decision thresholds (for the float32 / float64 flip audit)
 # ----------------------------------------------------------------------------
-MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99")
+MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99", "L1 residual = 0")
 
 
 def decision_margins(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = RasterCfg(), pixels=None,
-                     chunk_elems: int = 1 << 21) -> dict:
+                     chunk_elems: int = 1 << 21, prefilter=False, chunk_px=256, pixel_extra=None) -> dict:
     """Relative float64 distances of the compositing decisions (Eq. 11 with
     the support, skip, stop and clamp rules) to their thresholds: for a
     (pixel, Gaussian) pair near or inside the support, |q - 9| / 9, and where
@@ -439,7 +460,13 @@ def decision_margins(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = 
     per Gaussian (parameter index): ``gauss`` the smallest distance over the
     pixels where it is active or near its support, counting each such
     pixel's stop test too (a stop that flips changes the gradient of every
-    Gaussian the pixel reaches), and ``gauss_kind``."""
+    Gaussian the pixel reaches), and ``gauss_kind``.  ``prefilter`` and
+    ``chunk_px`` as in ``composite`` (the bounding box there holds every
+    pixel with q <= 9 (1 + 1e-3), so a dropped pair's only decision, q <= 9,
+    is more than 1e-3 from its threshold).  ``pixel_extra`` [M] (optional):
+    a further per-pixel distance (kind 4, e.g. an L1 loss residual's distance
+    to 0, whose sign decides the image gradient) folded into the pixel's
+    margin and into every Gaussian the pixel reaches."""
     with torch.no_grad():
         T = to_tensors(P)
         proj = project(T, sh_degree, cam, torch.as_tensor(np.asarray(R_cw), dtype=DT),
@@ -456,12 +483,13 @@ def decision_margins(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = 
         pix_gid = torch.full((M,), -1, dtype=torch.long)
         gm = torch.full((max(n, 1),), float("inf"), dtype=DT)
         gk = torch.zeros(max(n, 1), dtype=torch.long)
-        step = max(1, chunk_elems // max(n, 1))
-        for s0 in range(0, M, step if n else M or 1):
-            if n == 0:
-                break
-            q = _quad_form(U[s0:s0 + step], mu, conic)
-            araw = opac[None, :] * torch.exp(-0.5 * q)
+        extra = None if pixel_extra is None else torch.as_tensor(np.asarray(pixel_extra, np.float64)).reshape(-1)
+        chunks = list(_pixel_chunks(U, mu, conic, proj["cov2d"][o], cfg, prefilter, chunk_elems, chunk_px)) \
+            if n and M else []
+        for s0, s1, use in chunks:
+            sel = torch.arange(n) if use is None else use
+            q = _quad_form(U[s0:s1], mu[sel], conic[sel])
+            araw = opac[sel][None, :] * torch.exp(-0.5 * q)
             near = q <= cfg.q_max * (1 + 1e-3)
             inside = q <= cfg.q_max
             m_q = torch.where(near, torch.abs(q - cfg.q_max) / cfg.q_max, inf)
@@ -476,20 +504,33 @@ def decision_margins(P: dict, sh_degree: int, cam, R_cw, t_cw, cfg: RasterCfg = 
             pair = torch.stack([m_q, m_a, m_t, m_c], 0)        # [4, chunk, n]
             pair_min, pair_kind = pair.min(0)                 # [chunk, n]
             stop_min = m_t.min(1).values                      # [chunk]
+            if extra is not None:  # a pixel-wide decision: it goes with the stop test
+                ex = extra[s0:s1]
+                stop_min = torch.minimum(stop_min, ex)
+                closer = ex[:, None] < pair_min
+                pair_kind = torch.where(closer, torch.full_like(pair_kind, 4), pair_kind)
+                pair_min = torch.minimum(pair_min, ex[:, None])
+            if sel.numel() == 0:
+                continue
             pm, pj = pair_min.min(1)                          # per pixel
             pk = pair_kind.gather(1, pj[:, None])[:, 0]
-            sl = slice(s0, s0 + step)
-            pix[sl], pix_kind[sl], pix_gid[sl] = pm, pk, gid[pj]
+            sl = slice(s0, s1)
+            pix[sl], pix_kind[sl], pix_gid[sl] = pm, pk, gid[sel][pj]
             # per Gaussian: its own pair decisions and the stop test of every
             # pixel where it is active or near its support
             touch = near | active
             with_stop = torch.where(touch, torch.minimum(pair_min, stop_min[:, None]), inf)
-            kind_ws = torch.where(pair_min <= stop_min[:, None], pair_kind, torch.full_like(pair_kind, 2))
+            if extra is None:
+                kind_ws = torch.where(pair_min <= stop_min[:, None], pair_kind, torch.full_like(pair_kind, 2))
+            else:
+                sk = torch.where(ex < m_t.min(1).values, torch.full_like(ex, 4, dtype=torch.long),
+                                 torch.full_like(ex, 2, dtype=torch.long))
+                kind_ws = torch.where(pair_min <= stop_min[:, None], pair_kind, sk[:, None].expand_as(pair_kind))
             cm, ci = with_stop.min(0)
             ck = kind_ws.gather(0, ci[None, :])[0]
-            better = cm < gm[:n]
-            gm[:n] = torch.where(better, cm, gm[:n])
-            gk[:n] = torch.where(better, ck, gk[:n])
+            better = cm < gm[sel]
+            gm[sel] = torch.where(better, cm, gm[sel])
+            gk[sel] = torch.where(better, ck, gk[sel])
         gauss = torch.full((N,), float("inf"), dtype=DT)
         gauss_kind = torch.zeros(N, dtype=torch.long)
         if n:

@@ -149,6 +149,7 @@ EXPORTS = {
     "gs_profile_read": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "gs_measure_alu_peaks": (C.c_int, [C.c_int, C.c_int32, C.POINTER(gs_alu_peaks)]),
     "gs_state_token": (C.c_int, [P, C.POINTER(C.c_uint64)]),
+    "gs_get_tile_ranges": (C.c_int, [P, P, C.c_int64, P]),
 }
 
 _lib = None
@@ -560,6 +561,12 @@ def gs_count_nonfinite(ctx, x, stream=None) -> int:
 
 def gs_ctx_inject_alloc_failure(ctx, after: int = 1):
     _check(ctx, load().gs_ctx_inject_alloc_failure(ctx, int(after)), "gs_ctx_inject_alloc_failure")
+
+
+def gs_get_tile_ranges(ctx, ranges, stream=None):
+    """ranges: int32 CUDA tensor [n_tiles, 2] receiving [first, last + 1) per tile."""
+    _check(ctx, load().gs_get_tile_ranges(ctx, _ptr(ranges), int(ranges.shape[0]), _stream(stream)),
+           "gs_get_tile_ranges")
 
 
 def gs_state_token(ctx) -> int:

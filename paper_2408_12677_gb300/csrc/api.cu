@@ -1694,6 +1694,17 @@ gs_status gs_get_projection(gs_ctx* c, float* mean2d, float* cov2d, float* depth
   return GS_OK;
 }
 
+gs_status gs_get_tile_ranges(gs_ctx* c, uint32_t* ranges, int64_t n_tiles, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!c->have_state) return fail(c, GS_ERR_STATE, "no forward pass on this context");
+  if (!ranges || n_tiles != c->st_tiles)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_get_tile_ranges: ranges is NULL or n_tiles is not the forward pass's");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaMemcpyAsync(ranges, c->ranges, sizeof(uint2) * (size_t)n_tiles, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  return GS_OK;
+}
+
 gs_status gs_state_token(const gs_ctx* c, uint64_t* token) {
   if (!c || !token) return GS_ERR_INVALID_ARG;
   *token = c->have_state ? c->state_token : 0;

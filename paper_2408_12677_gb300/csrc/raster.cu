@@ -8,10 +8,10 @@
 // list in chunks of 32 entries with the next chunk's 48 B records already in
 // flight, converts the records to tile-local coordinates (so per-pixel offsets
 // keep float32 precision), keeps the entries whose support bounding box meets
-// its block (ballot) and evaluates only those.  The backward pass sums each
-// Gaussian's gradient over the warp (per-lane atomics when at most two lanes
-// contribute, else a transposed shuffle reduction) and adds it to the
-// Gaussian's global record with one warp-wide atomic.
+// its block (ballot) and evaluates only those.  The backward pass adds each
+// Gaussian's gradient to its global record with per-lane vector atomics when
+// few lanes contribute, else after a transposed shuffle reduction over the
+// warp with one warp-wide atomic.
 #include <algorithm>
 
 #include "common.cuh"
@@ -22,10 +22,11 @@ namespace gs {
 namespace {
 
 constexpr int kThreads = 128;  // 4 independent warps per CTA, one 8 x 8 pixel block each
-// Backward pass: when at most this many lanes contribute to a Gaussian, they
-// add their values with per-lane atomics (10 issue slots) instead of the warp
-// reduction (about 40); the kernel is issue-bound, the L2 atomics are not.
-constexpr int kAtomicLanes = 8;
+// Backward pass: when at most this many lanes contribute to a Gaussian, each
+// adds its ten values with three 16-byte vector atomics (3 issue slots)
+// instead of the warp reduction (about 45); the kernel is issue-bound, and
+// up to this many lanes the L2 atomic units keep up (at 32 they saturate).
+constexpr int kAtomicLanes = 16;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // One list entry in tile-local coordinates:
@@ -559,8 +560,11 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
       float* rec = g2d + 12 * (size_t)bid[j];
       if (__popc(m) <= kAtomicLanes) {
         if (contrib) {
-#pragma unroll
-          for (int k = 0; k < 10; ++k) atomicAdd(&rec[rec_off(k)], v[k]);
+          // three 16-byte vector atomics per lane (red.global.add.v4.f32)
+          float4* r4 = reinterpret_cast<float4*>(rec);
+          atomicAdd(r4, make_float4(v[0], v[1], v[2], v[3]));
+          atomicAdd(r4 + 1, make_float4(v[4], v[5], v[6], 0.f));
+          atomicAdd(r4 + 2, make_float4(v[7], v[8], v[9], 0.f));
         }
       } else {
         warp_reduce_add10(v, rec);

@@ -288,7 +288,8 @@ def save_stream(opt: "StreamingOptimizer", path: str) -> None:
     torch.cuda.synchronize()
     checkpoint.save_map(path, m.flat, m.m, m.v, m.n, opt.map.sh_degree, opt.step, opt.map.n)
     meta = {"frame_index": opt.frame_index, "step": opt.step, "novelty": opt.novelty,
-            "rng": opt.rng.bit_generator.state}
+            "rng": opt.rng.bit_generator.state, "n_live": int(opt.map.n), "n_slots": int(m.n),
+            "map_bytes": os.path.getsize(path)}
     arrays = {"meta": np.frombuffer(json.dumps(meta).encode(), np.uint8),
               "keyframe_ids": np.asarray(opt.keyframe_ids, np.int64)}
     if opt.tsdf is not None:
@@ -314,6 +315,12 @@ def load_stream(opt: "StreamingOptimizer", path: str, frames) -> None:
     meta = json.loads(bytes(st["meta"]).decode())
     if meta["novelty"] != opt.novelty:
         raise ValueError(f"checkpoint of a {meta['novelty']!r} loop, the optimizer uses {opt.novelty!r}")
+    # the map file and the state file are renamed into place one after the
+    # other: a crash between the two leaves a pair from different steps
+    mine = {"step": d["step"], "n_live": d["n_live"], "n_slots": d["n_slots"], "map_bytes": os.path.getsize(path)}
+    theirs = {k: meta.get(k) for k in mine}
+    if mine != theirs:
+        raise ValueError(f"map file and state file are from different checkpoints: {mine} vs {theirs}")
     opt.map = GrowingMap(opt.map.sh_degree, d["n_slots"], opt.map.device)
     m = opt.map.model
     for dst, key in ((m.flat, "flat"), (m.m, "m"), (m.v, "v")):

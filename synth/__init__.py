@@ -3,7 +3,10 @@
 This package only *generates inputs*: camera intrinsics and poses, Gaussian
 parameter sets and target RGB-D frames.  It holds none of the rasterizer's
 arithmetic (projection, compositing, gradients, optimiser); both the FP64
-oracle (``oracle/``) and the CUDA path consume what it produces.
+oracle (``oracle/``) and the CUDA path consume what it produces.  It does
+implement the paper's quadtree seeding (Eq. 10) to build the Gaussian sets
+from its frames: that is method arithmetic used as input plumbing, and the
+oracle and the GPU seeding kernels each have their own implementation of it.
 
 Contents
 --------

@@ -203,21 +203,36 @@ def multi_view_poses(rng, n_views: int):
     return poses
 
 
-def multi_view(seed: int = 1003, n: int = 500_000, voxel: float = 0.01, cams=None) -> Workload:
+def _multi_view_frame(args):
+    """One view of the multi-view set: ray-cast frame and its seeded
+    Gaussians (a process-pool worker; the room is rebuilt from its seed)."""
+    seed, keep_clear, (w, h, f), (eye, yaw, pitch) = args
+    room = make_room(seed, keep_clear=keep_clear)
+    cam = Camera(f, f, w / 2.0, h / 2.0, w, h)
+    pose = yaw_pitch_pose(eye, yaw, pitch)
+    rgb, depth = _frame(room, cam, pose)
+    return cam, pose, rgb, depth, seed_gaussians(rgb, depth, cam, pose, 3)
+
+
+def multi_view(seed: int = 1003, n: int = 500_000, voxel: float = 0.01, cams=None, workers: int = 1) -> Workload:
     """Uneven views sharing one map; seeding keeps at most one Gaussian per voxel
     (the paper's TSDF-weight novelty check, Sec. III-B.2, reduced to voxel
-    occupancy since no TSDF map is built here)."""
+    occupancy since no TSDF map is built here).  ``workers`` > 1 ray-casts and
+    seeds the views in a spawned process pool (same result)."""
     rng = np.random.default_rng(seed)
     cams = cams or MULTI_VIEW_CAMS
     specs = multi_view_poses(rng, len(cams))
-    room = make_room(seed, keep_clear=[s[0] for s in specs])
+    keep_clear = [s[0] for s in specs]
+    jobs = [(seed, keep_clear, c, sp) for c, sp in zip(cams, specs)]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            frames = pool.map(_multi_view_frame, jobs)
+    else:
+        frames = [_multi_view_frame(j) for j in jobs]
     views, parts = [], []
     seen = set()
-    for (w, h, f), (eye, yaw, pitch) in zip(cams, specs):
-        cam = Camera(f, f, w / 2.0, h / 2.0, w, h)
-        pose = yaw_pitch_pose(eye, yaw, pitch)
-        rgb, depth = _frame(room, cam, pose)
-        p = seed_gaussians(rgb, depth, cam, pose, 3)
+    for cam, pose, rgb, depth, p in frames:
         vox = np.floor(p["means"].astype(np.float64) / voxel).astype(np.int64)
         keys = (vox[:, 0] * 1_000_003 + vox[:, 1]) * 1_000_033 + vox[:, 2]
         _, first = np.unique(keys, return_index=True)

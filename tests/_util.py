@@ -19,7 +19,7 @@ def ensure_built():
     return abi.load()
 
 
-MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99")
+MARGIN_KINDS = ("q = 9", "alpha = 1/255", "T (1 - alpha) = 1e-4", "alpha = 0.99", "L1 residual = 0")
 FLIP_EPS = 1e-4  # relative distance to a threshold within which float32 may decide the other way
 
 
@@ -71,13 +71,30 @@ def compare(name, got, ref, rtol, atol, norm_rtol, flip_budget=0, report=None, m
     return info
 
 
-def margins_over_views(params, deg, cams, poses):
+def residual_margins(color, depth, target_rgb, target_depth):
+    """Per pixel, the relative distance of the L1 loss residuals (Eq. 12 plus
+    the depth term) to 0, where their sign -- the image gradient -- flips:
+    min over the channels (and the depth where its target is valid) of
+    |r| / (|value| + 0.01); within 1e-4 the float32 render (image tolerance
+    1e-4 |value| + 1e-6) may give the other sign."""
+    c = np.asarray(color, np.float64).reshape(3, -1)
+    tc = np.asarray(target_rgb, np.float64).reshape(3, -1)
+    d = np.asarray(depth, np.float64).reshape(-1)
+    td = np.asarray(target_depth, np.float64).reshape(-1)
+    m = (np.abs(c - tc) / (np.abs(c) + 0.01)).min(0)
+    md = np.where(td > 0, np.abs(d - td) / (np.abs(d) + 0.01), np.inf)
+    return np.minimum(m, md)
+
+
+def margins_over_views(params, deg, cams, poses, extras=None):
     """Per-Gaussian decision margins (``R.decision_margins``) of several views
-    of one map: the smallest over the views."""
+    of one map: the smallest over the views (``extras``: per view a further
+    per-pixel margin, e.g. ``residual_margins``)."""
     from oracle import render as R
     out = None
-    for cam, (Rm, t) in zip(cams, poses):
-        m = R.decision_margins(params, deg, cam, np.asarray(Rm, np.float64), np.asarray(t, np.float64))
+    for v, (cam, (Rm, t)) in enumerate(zip(cams, poses)):
+        m = R.decision_margins(params, deg, cam, np.asarray(Rm, np.float64), np.asarray(t, np.float64),
+                               pixel_extra=None if extras is None else extras[v])
         if out is None:
             out = {"gauss": m["gauss"].copy(), "gauss_kind": m["gauss_kind"].copy()}
         else:

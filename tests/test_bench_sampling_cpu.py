@@ -1,22 +1,29 @@
-"""The oracle baseline's pixel sample keeps every Gaussian that can reach a
-sampled pixel: the summed-area-table selection equals a brute-force test of
-each Gaussian's box against each sampled pixel centre."""
+"""The oracle baseline's cost model: per 16 x 16 tile, the pixels times the
+Gaussians whose 3-sigma box meets the tile (counted with a 2D difference
+array) equal a brute-force test of every Gaussian against every tile's pixel
+centres -- the same selection the oracle's tile compositing makes."""
 import numpy as np
 
 
-def test_near_selection_matches_brute_force():
+def test_tile_elements_match_brute_force():
     import bench
-    rng = np.random.default_rng(0)
-    W, H = 37, 23
-    n = 4000
-    mu = np.stack([rng.uniform(-10, W + 10, n), rng.uniform(-10, H + 10, n)], 1)
-    rad = rng.uniform(0.0, 6.0, n)
-    rad[:50] = 0.0  # degenerate boxes
-    mu[50:60] = np.array([[3.5, 4.5]]) + rng.integers(-2, 3, (10, 2))  # centres exactly on pixel centres
-    for k in (1, 7, 200):
-        pix = np.stack([rng.integers(0, W, k), rng.integers(0, H, k)], 1)
-        got = bench.gaussians_near_pixels(mu, rad, pix, W, H)
-        c = pix.astype(np.float64) + 0.5
-        want = ((np.abs(mu[:, None, 0] - c[None, :, 0]) <= rad[:, None]) &
-                (np.abs(mu[:, None, 1] - c[None, :, 1]) <= rad[:, None])).any(1)
-        assert np.array_equal(got, want)
+    from oracle import render as R
+    from synth import workloads
+    w = workloads.tiny_random(seed=33, n=700)
+    v = w.views[0]
+    got = bench.oracle_tile_elements(w)
+    import torch
+    with torch.no_grad():
+        pr = R.project(R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}), 0, v.cam,
+                       np.asarray(v.pose.R, np.float64), np.asarray(v.pose.t, np.float64))
+    mu = pr["mean2d"].numpy()
+    cov = pr["cov2d"].numpy()
+    ext = np.stack([np.sqrt(9.009 * cov[:, 0, 0]), np.sqrt(9.009 * cov[:, 1, 1])], 1)
+    tx, ty = -(-v.cam.width // 16), -(-v.cam.height // 16)
+    want = []
+    for k in range(tx * ty):
+        pix = R.tile_pixels(v.cam, [k]) + 0.5
+        lo, hi = pix.min(0), pix.max(0)
+        gap = np.maximum(np.maximum(lo[None] - mu, mu - hi[None]), 0.0)
+        want.append(int((gap <= ext).all(1).sum()) * len(pix))
+    assert np.array_equal(got, np.array(want))

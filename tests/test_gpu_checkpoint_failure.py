@@ -72,6 +72,15 @@ def test_streaming_resume(lib, tmp_path):
             (r.new_gaussians, r.n_gaussians, r.tsdf_blocks, r.tsdf_touched, r.views_per_iter)
         assert g.loss == pytest.approx(r.loss, rel=1e-3)
     assert b.keyframe_ids == a.keyframe_ids
+    # a crash between the two renames of a later save leaves the new map file
+    # beside the old state file: the pair is refused
+    import shutil
+    old_state = str(tmp_path / "old.state.npz")
+    shutil.copy(path + ".state.npz", old_state)
+    save_stream(a, path)
+    shutil.copy(old_state, path + ".state.npz")
+    with pytest.raises(ValueError, match="different checkpoints"):
+        load_stream(make(), path, lambda i: (*st.frame(frames[i]), st.poses[frames[i]]))
 
 
 def test_nonfinite_count(lib):

@@ -2,15 +2,14 @@
 autograd Function, vs central differences of the GPU forward).
 
 Gradient tolerance: per parameter array ||g - o|| / ||o|| <= 1e-3 and
-element-wise |g - o| <= 1e-3 |o| + 1e-5 max|o| + 1e-6 G, with G the largest
-gradient entry over all parameter arrays (float32 cancellation floor: e.g. the
-quaternion gradient of an isotropic Gaussian is exactly 0 but sums float32
-terms of size ~G).  Elements beyond it are flips: the Gaussian must have a
+element-wise |g - o| <= 1e-3 |o| + 1e-5 max|o| (the largest error measured
+over every scene here is 2.3% of that bound).  Elements beyond it are flips:
+the Gaussian must have a
 float32 decision within 1e-4 (relative) of its threshold at some pixel it
-reaches (``R.decision_margins``, reported with the threshold), and their
-number is bounded by max(1, 1e-5 x elements) plus the flips the images of the
-same scene show, times the elements a flipped Gaussian owns.  Arrays whose
-exact gradient is 0 are checked against the floor only."""
+reaches (``R.decision_margins``, reported with the threshold), and there may
+be at most max(1, 1e-5 x elements) of them per array (the census of every
+scene here found none).  Arrays whose exact gradient is 0 are checked against
+the floor only."""
 import numpy as np
 import pytest
 import torch
@@ -56,7 +55,7 @@ def _check_grads(ctx, P, deg, cam, pose, seed, with_alpha=True, **cfg):
     check_grad_arrays(g, og, m)
 
 
-GRAD_FLIP_GAUSSIANS = 2  # Gaussians whose gradient may flip per scene (see the module docstring)
+GRAD_FLIP_GAUSSIANS = 0  # whole Gaussians' gradients allowed to flip on top of max(1, 1e-5 x elements)
 
 
 def check_grad_arrays(g, og, margins=None, names=NAMES + ("pose",), flip_gaussians=GRAD_FLIP_GAUSSIANS,
@@ -65,7 +64,7 @@ def check_grad_arrays(g, og, margins=None, names=NAMES + ("pose",), flip_gaussia
     for k in names:
         ref = og[k].detach().numpy()
         scale = np.abs(ref).max(initial=0.0)
-        floor = 1e-5 * scale + 1e-6 * G + 1e-12
+        floor = 1e-5 * scale + 1e-12
         if scale <= 1e-6 * G:  # exact gradient is (numerically) zero
             assert np.abs(g[k]).max(initial=0.0) <= 1e-5 * G, (k, np.abs(g[k]).max())
             continue

@@ -9,7 +9,7 @@ import torch
 from oracle import render as R
 from synth import workloads
 from synth.quadtree import seed_gaussians
-from tests._util import ensure_built, margins_over_views
+from tests._util import ensure_built, margins_over_views, residual_margins
 from tests.test_gpu_grad import check_grad_arrays
 
 pytestmark = pytest.mark.gpu
@@ -114,6 +114,64 @@ def test_checkpoint_gradients_match_oracle(run):
             assert abs(gpu - d1) <= 2e-3 * abs(d1) + 1e-6 * np.abs(G).max(), (name, i, gpu, d1)
             checked += 1
     assert checked >= 6
+
+
+def test_global_optimisation_step_matches_oracle(run):
+    """One step of the offline optimisation over the keyframe list (Sec.
+    III-B.3): the loss summed over every keyframe (one batched step) and the
+    Adam update it makes, against the FP64 oracle's multi-view loss, its
+    gradient and the float64 Adam step from the same parameters and moments
+    (with the float32 hyper-parameters the ABI receives)."""
+    from oracle import adam as oadam
+    from paper_2408_12677_gb300.streaming import global_optimize
+    from paper_2408_12677_gb300.torch_api import _views
+    from tests._util import compare
+    st, frames, opt, stats = run
+    kfs = opt.keyframes
+    assert 2 <= len(kfs) <= 16
+    m = opt.map.model
+    n, cap = opt.map.n, m.n
+    names = R.PARAM_NAMES
+
+    def live(flat):
+        return {k: v[:n].detach().cpu().numpy().astype(np.float64).copy() for k, v in _views(flat, cap, DEG).items()}
+
+    P0, M0, V0 = live(m.flat), live(m.m), live(m.v)
+    inert0 = m.flat.clone()
+    g = global_optimize(opt, epochs=1, views_per_step=len(kfs), rng_seed=7)
+    assert g.steps == 1 and g.view_iterations == len(kfs)
+    P1 = live(m.flat)
+    # inert slots are untouched
+    for k, v in _views(m.flat, cap, DEG).items():
+        assert torch.equal(v[n:], _views(inert0, cap, DEG)[k][n:]), k
+    poses = [(np.array(k.view.R, np.float64).reshape(3, 3), np.array(k.view.t, np.float64)) for k in kfs]
+    targets = [(k.rgb.cpu().numpy(), k.depth.cpu().numpy()) for k in kfs]
+    P = dict(P0, sh_degree=DEG)
+    L, og, outs = R.multiview_gradients(P, DEG, [st.cam] * len(kfs), poses, targets, with_pose=False)
+    assert abs(g.loss_first - float(L)) <= 1e-4 * float(L), (g.loss_first, float(L))
+    # where a loss residual is within float32 rounding of 0 its sign (the
+    # image gradient) may flip: such pixels flag the Gaussians they reach
+    extras = [residual_margins(o["color"].detach().numpy(), o["depth"].detach().numpy(), trgb, tdep)
+              for o, (trgb, tdep) in zip(outs, targets)]
+    mg = margins_over_views(P, DEG, [st.cam] * len(kfs), poses, extras)
+    f32 = lambda x: float(np.float32(x))
+    a = opt.acfg
+    cfg = oadam.AdamCfg(f32(a.lr_means), f32(a.lr_log_scales), f32(a.lr_quats), f32(a.lr_opacity), f32(a.lr_sh_dc),
+                        f32(a.lr_sh_rest), f32(a.beta1), f32(a.beta2), f32(a.eps))
+    flat = lambda d: np.concatenate([np.asarray(d[k], np.float64).ravel() for k in names])
+    p_new, _, _ = oadam.adam_step(flat(P0), flat({k: og[k].numpy() for k in names}), flat(M0), flat(V0), opt.step,
+                                  oadam.lr_per_element(n, DEG, cfg), cfg)
+    d_gpu, d_ref = flat(P1) - flat(P0), p_new - flat(P0)
+    # the update is smooth in the gradient where the moments are not 0 (every
+    # live Gaussian has been optimised before), so a 1e-3 gradient error
+    # moves it by less: element-wise 1e-3 relative, 1e-5 of the largest step
+    per = {k: og[k].numpy().size // n for k in names}
+    mrg = np.concatenate([np.repeat(mg["gauss"], per[k]) for k in names])
+    knd = np.concatenate([np.repeat(mg["gauss_kind"], per[k]) for k in names])
+    # every element beyond the tolerance must belong to a flagged Gaussian
+    from tests._util import FLIP_EPS
+    budget = max(1, int(1e-5 * d_ref.size)) + int((mrg <= FLIP_EPS).sum())
+    compare("adam update", d_gpu, d_ref, 1e-3, 1e-5 * np.abs(d_ref).max(), 1e-3, budget, margins=mrg, kinds=knd)
 
 
 def test_global_optimisation_over_keyframes(run):

@@ -199,6 +199,14 @@ def test_brute_equals_bbox_prefilter_on_tiles():
     tiles = np.random.default_rng(3).permutation(4 * 3)  # 64 x 48 in 16 x 16 tiles
     pix = R.tile_pixels(CAM, tiles)
     sub = _render(P, deg=1, pixels=pix, prefilter="bbox", chunk_px=256)
+    # ragged tiles (70 x 50 in 16 x 16: 6- and 2-pixel edges) grouped by tile
+    cam = Camera(60.0, 60.0, 35.0, 25.0, 70, 50)
+    full2 = _render(P, cam=cam, deg=1, prefilter=False)
+    pix2, sizes = R.tile_pixels(cam, np.random.default_rng(4).permutation(5 * 4), sizes=True)
+    sub2 = _render(P, cam=cam, deg=1, pixels=pix2, prefilter="bbox", chunk_px=sizes)
+    np.testing.assert_array_equal(sub2["n_contrib"].numpy(), full2["n_contrib"].numpy()[pix2[:, 1], pix2[:, 0]])
+    np.testing.assert_allclose(sub2["color"].numpy(), full2["color"].numpy()[:, pix2[:, 1], pix2[:, 0]],
+                               rtol=1e-13, atol=1e-15)
     np.testing.assert_array_equal(sub["n_contrib"].numpy(), full["n_contrib"].numpy()[pix[:, 1], pix[:, 0]])
     np.testing.assert_allclose(sub["color"].numpy(), full["color"].numpy()[:, pix[:, 1], pix[:, 0]], rtol=1e-13,
                                atol=1e-15)
@@ -248,3 +256,18 @@ def test_decision_margins_stop_rule():
         want.append(abs(sigmoid20 * np.exp(-0.5 * q) - 0.99) / 0.99)
     assert out["pixel"][0] == pytest.approx(min(want), rel=1e-6)
     assert R.MARGIN_KINDS[out["pixel_kind"][0]] == "alpha = 0.99"
+
+
+def test_decision_margins_bbox_equals_brute():
+    """Margins computed tile by tile with the bounding-box selection equal
+    the brute-force ones (a dropped Gaussian has no decision near a
+    threshold at any pixel of the tile)."""
+    w = workloads.tiny_random(seed=17, n=400)
+    P = {k: np.asarray(w.params[k], float) for k in R.PARAM_NAMES}
+    a = R.decision_margins(P, 0, CAM, *IDENT)
+    pix, sizes = R.tile_pixels(CAM, range(12), sizes=True)
+    b = R.decision_margins(P, 0, CAM, *IDENT, pixels=pix, prefilter="bbox", chunk_px=sizes)
+    lin = pix[:, 1] * CAM.width + pix[:, 0]
+    np.testing.assert_array_equal(a["pixel"][lin], b["pixel"])
+    np.testing.assert_array_equal(a["pixel_kind"][lin], b["pixel_kind"])
+    np.testing.assert_array_equal(a["gauss"], b["gauss"])
