@@ -459,6 +459,30 @@ def run_scale_stress(args, rank, world, local_rank):
     }
 
 
+def run_profile_driver(args, local_rank):
+    """``--profile-iterations N``: N eager gs_train_step iterations of the
+    single-view workload (the bench's kernels and launch configuration, no
+    graph, no timing loop), for profiler captures of single launches."""
+    import torch
+
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import Context, GaussianModel, Trainer
+    from synth import workloads
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    abi.load()
+    w = workloads.single_view()
+    v = w.views[0]
+    tr = Trainer(GaussianModel(w.params, device=dev), v.cam, v.pose.R, v.pose.t, ctx=Context(local_rank),
+                 device=local_rank)
+    trgb = torch.as_tensor(v.target_rgb, device=dev)
+    tdep = torch.as_tensor(v.target_depth, device=dev)
+    for _ in range(args.profile_iterations):
+        tr.step(trgb, tdep)
+    torch.cuda.synchronize(dev)
+    return {"profile_iterations": args.profile_iterations, "loss": float(tr.loss)}
+
+
 def trainer_snapshot(tr):
     """Parameters, Adam moments and step of a trainer (device copies)."""
     m = tr.model
@@ -1022,6 +1046,8 @@ def main():
                     help="streaming: passes of the offline optimisation over the keyframe list afterwards")
     ap.add_argument("--no-multi-view", action="store_true",
                     help="single_view: skip the compact batched-vs-sequential multi-view comparison")
+    ap.add_argument("--profile-iterations", type=int, default=0,
+                    help="run this many eager single-view iterations and exit (a short driver for ncu captures)")
     ap.add_argument("--no-compare", action="store_true",
                     help="multi_view: skip the view-by-view comparison arm (e.g. for a profiler capture)")
     args = ap.parse_args()
@@ -1031,6 +1057,9 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)))
+        return
+    if args.profile_iterations > 0:
+        print(json.dumps(run_profile_driver(args, local_rank)))
         return
     if world > 1:
         import torch.distributed as dist

@@ -86,7 +86,7 @@ typedef struct {
 
 typedef struct {
   int32_t tile_w, tile_h; /* 16x16, 8x32 or 32x8 */
-  int32_t batch;          /* Gaussians staged in shared memory per step: 256 */
+  int32_t batch;          /* list entries a warp stages per round (one per lane): 32, the only value */
   float bg[3];            /* background colour added with the final transmittance */
   float near_z;           /* cull Gaussians with camera z <= near_z (0.2) */
   float alpha_max;        /* opacity clamp (0.99) */
@@ -189,7 +189,7 @@ gs_status gs_set_eval_counting(gs_ctx *ctx, int counting);
 gs_status gs_set_profiling(gs_ctx *ctx, int profiling);
 gs_status gs_profile_read(gs_ctx *ctx, double *ms, int64_t *count);
 
-/* Default configurations (host structs): 16x16 tiles, batch 256, bg 0,
+/* Default configurations (host structs): 16x16 tiles, batch 32, bg 0,
  * near 0.2, alpha in [1/255, 0.99], T_eps 1e-4, dilation 0.3; Adam
  * beta = (0.9, 0.999), eps 1e-15, lr means 1.6e-4, log-scales 5e-3,
  * quats 1e-3, opacity 5e-2, SH DC 2.5e-3, SH rest 1.25e-4, zero_grads 0. */

@@ -56,7 +56,10 @@ struct gs_ctx {
   uint32_t* torder = nullptr;   // raster visit order of the tiles (longest lists first)
   uint32_t* scan_aux = nullptr;  // multi-block tile scan scratch
   uint32_t* bigq = nullptr;     // ids of Gaussians covering more than kBigTiles tiles
-  uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue
+  uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue, [1] raster job counter, [2] unused,
+                                  // [3] ticket of the fused-loss reduction (0 between launches)
+  bool counts_zero = false;       // the tile counters and the large-splat queue length are 0 (the per-tile
+                                  // sort, the last binning kernel, zeroes them)
   unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
   long long* d_step = nullptr;               // device Adam step counter (step = 0 calls)
   int64_t cap_px = 0;
@@ -242,6 +245,7 @@ gs_status ensure_tiles(gs_ctx* c, int64_t t) {
   const int64_t cap = grow_target(t, c->cap_t);
   GS_GROW(c, cap_t, regrow(&c->ranges, cap));
   GS_GROW(c, cap_t, regrow(&c->tcount, cap));
+  c->counts_zero = false;
   GS_GROW(c, cap_t, regrow(&c->toffset, cap));
   GS_GROW(c, cap_t, regrow(&c->tcursor, cap));
   GS_GROW(c, cap_t, regrow(&c->torder, cap));
@@ -290,7 +294,7 @@ gs_status check_cfg(gs_ctx* c, const gs_raster_cfg* cfg) {
   if (!cfg) return fail(c, GS_ERR_INVALID_ARG, "raster cfg is NULL");
   if (!raster_shape_supported(cfg->tile_w, cfg->tile_h))
     return fail(c, GS_ERR_INVALID_ARG, "tile shape must be 16x16, 8x32 or 32x8");
-  if (cfg->batch != 256) return fail(c, GS_ERR_INVALID_ARG, "batch must be 256");
+  if (cfg->batch != 32) return fail(c, GS_ERR_INVALID_ARG, "batch (list entries per warp round) must be 32");
   if (!(cfg->alpha_max > 0.f && cfg->alpha_max < 1.f) || !(cfg->alpha_min > 0.f && cfg->alpha_min < cfg->alpha_max) ||
       !(cfg->t_eps > 0.f && cfg->t_eps < 1.f) || !(cfg->dilation >= 0.f) || !std::isfinite(cfg->near_z))
     return fail(c, GS_ERR_INVALID_ARG, "raster thresholds out of range");
@@ -325,7 +329,7 @@ CamView make_camview(const gs_camera* cam, const gs_viewmat* v) {
 }
 
 gs_status ensure_hist(gs_ctx* c) {
-  const int want = 4 * std::max(c->num_sms, 1);
+  const int want = 8 * std::max(c->num_sms, 1);
   if (c->hist && c->hist_blocks >= want) return GS_OK;
   GS_CUDA(c, regrow(&c->hist, (int64_t)256 * (want + 1)));
   c->hist_blocks = want;
@@ -474,6 +478,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
     launch_tile_sort(tb, s, &c->launches);
   }
   GS_CHECK_LAUNCH(c, "tile scatter/sort");
+  c->counts_zero = true;
   c->st_pairs = P;
   c->st_pair_buf = 0;
   c->st_ordered = tb.order != nullptr;
@@ -488,7 +493,7 @@ gs_status gs_raster_cfg_default(gs_raster_cfg* cfg) {
   if (!cfg) return GS_ERR_INVALID_ARG;
   cfg->tile_w = 16;
   cfg->tile_h = 16;
-  cfg->batch = 256;
+  cfg->batch = 32;
   cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
   cfg->near_z = 0.2f;
   cfg->alpha_max = 0.99f;
@@ -528,6 +533,7 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bigmeta, 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_bigmeta, 0, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
   if (e == cudaSuccess) init_project_kernels();
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_evals, 2 * sizeof(unsigned long long));
@@ -873,8 +879,13 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   pa.big_queue = c->bigq;
   pa.big_len = c->d_bigmeta;
   pa.counts = c->tcount;  // the projection counts the tiles of the small rectangles
-  GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
-  GS_CUDA(c, cudaMemsetAsync(c->tcount, 0, sizeof(uint32_t) * (size_t)L.tiles, s));
+  if (!c->counts_zero) {  // else the last per-tile sort left them zero
+    // every counter of the allocation, so that a later pass over more tiles
+    // also starts from zeros
+    GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
+    GS_CUDA(c, cudaMemsetAsync(c->tcount, 0, sizeof(uint32_t) * (size_t)c->cap_t, s));
+  }
+  c->counts_zero = false;
   {
     StageTimer t(c, GS_STAGE_PROJECT_FWD, s);
     launch_project_fwd(pa, c->feat, c->zkey, c->tiles, c->rects, s);
@@ -1014,7 +1025,7 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
                                 const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                                 const float* const* dL_ddepth, const float* const* dL_dalpha, float* params,
                                 float* m, float* v, const gs_adam_cfg* adam, int64_t step, float* dL_dpose,
-                                cudaStream_t s, const float* depth_scale = nullptr) {
+                                cudaStream_t s, const float* depth_scale = nullptr, bool step_advanced = false) {
   gs_status st;
   if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
@@ -1031,8 +1042,10 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
     AdamArgs ad = adam_args(adam, step);
     if (step == 0) {
-      launch_step_increment(c->d_step, s);
-      c->launches += 1;
+      if (!step_advanced) {  // (the training step's loss launch has advanced it)
+        launch_step_increment(c->d_step, s);
+        c->launches += 1;
+      }
       ad.step_dev = c->d_step;
     }
     const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, dL_dpose ? c->pose_partials : nullptr, s);
@@ -1139,8 +1152,10 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   ra.loss_partials = c->tile_loss;
   ra.w_color = w_color;
   {
+    // the device step counter (step = 0) is advanced by the loss launch
     StageTimer t(c, GS_STAGE_LOSS, s);
-    launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, s, &c->launches);
+    launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, c->d_bigmeta + 3,
+                               step == 0 ? c->d_step : nullptr, s, &c->launches);
   }
   GS_CHECK_LAUNCH(c, "loss finalize");
   const float* dlc[kMaxViews];
@@ -1151,7 +1166,7 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     dld[k] = c->dl_img + 4 * c->st_pix_base[k] + 3 * np;
   }
   return render_bwd_adam_views(c, g, V, cams, views, cfg, dlc, dld, nullptr, params, m, v, adam, step, nullptr, s,
-                               c->d_dscale);
+                               c->d_dscale, /*step_advanced=*/true);
 }
 
 }  // namespace
@@ -1654,6 +1669,9 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
   }
   c->have_state = false;
   GS_CUDA(c, cudaMemsetAsync(c->d_bigmeta, 0, sizeof(uint32_t), s));
+  // the count kernel zeroes the T counters it uses; the others stay as they were
+  const bool counters_were_zero = c->counts_zero;
+  c->counts_zero = false;
   launch_bin_prepare((int)n, mean2d, extent, depth, tile_w, tile_h, tiles_x, tiles_y, c->zkey, c->tiles, c->rects,
                      c->bigq, c->d_bigmeta, s);
   if (n > 0) c->launches += 1;
@@ -1663,6 +1681,7 @@ gs_status gs_bin_tiles(gs_ctx* c, int64_t n, const float* mean2d, const float* e
   map.tiles_x[0] = tiles_x;
   for (int v = 1; v <= kMaxViews; ++v) map.tile_base[v] = (uint32_t)T;
   st = bin_and_sort(c, (int)n, map, s, false);
+  c->counts_zero = c->counts_zero && counters_were_zero;
   c->sync = was_sync;
   if (st != GS_OK) return st;
   const int64_t P = c->st_pairs;

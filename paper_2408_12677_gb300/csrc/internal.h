@@ -135,7 +135,7 @@ struct TileBinArgs {
   unsigned long long* stats;  // device: [0] total pairs, [1] longest list
   uint32_t* overflow;         // device flag: 1 = pairs over capacity, 2 = list over kTileSortCap
   const uint32_t* big_queue;  // items with more than kBigTiles tiles
-  const uint32_t* big_len;
+  const uint32_t* big_len;    // queue length (the per-tile sort zeroes it, and the counts, when done)
   uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
   bool small_counted;         // counts already hold every item with at most kBigTiles tiles (projection)
   uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
@@ -171,7 +171,7 @@ struct RasterArgs {
   const uint32_t* ids;
   const float4* feat;
   const uint32_t* order;  // nullable
-  uint32_t* work;         // nullable: job counter of the persistent form (zeroed by the launcher)
+  uint32_t* work;         // nullable: job counter of the persistent form, zeroed by the launcher
   int num_sms;
   // fused loss (forward): per (tile, 8 x 8 block) partial sums {|colour
   // residual|, |depth residual| over valid targets, valid count} at
@@ -189,9 +189,13 @@ void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsig
 // loss from the forward pass's per-block partials: loss = sum over views of
 // w_color sum|rc| / (3 npix_v) + w_depth sum|rd| / nvalid_v; depth_scale[v] =
 // w_depth / nvalid_v (fixed summation order)
-// partials: scratch of >= 3 * (4 n_tiles / 2048 + views) floats
+// partials: scratch of >= 3 * (4 n_tiles / 2048 + views) floats; ticket: a
+// device word that is 0 between launches (one launch; its last block
+// finalises and resets it); step (nullable): the device Adam step counter,
+// advanced by one after the loss is final
 void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss, float* depth_scale,
-                                float* partials, cudaStream_t s, int64_t* launches);
+                                float* partials, uint32_t* ticket, long long* step, cudaStream_t s,
+                                int64_t* launches);
 void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s);
 
 // loss and optimiser: per view v, L_v = w_color mean |C - C^| + w_depth

@@ -82,9 +82,9 @@ __global__ void __launch_bounds__(kLossThreads) loss_partials_kernel(const __gri
 // loss = sum of L_v in view order.  Each thread sums a strided subset in
 // order, then a fixed tree combines them, so the result does not depend on
 // scheduling.
-__global__ void __launch_bounds__(256) loss_finalize_kernel(const __grid_constant__ LossArgs a,
-                                                            const float* __restrict__ partials,
-                                                            float* __restrict__ scale) {
+// The finalize step by one block of 256 threads (every thread calls it).
+__device__ __forceinline__ void loss_finalize_block(const LossArgs& a, const float* __restrict__ partials,
+                                                    float* __restrict__ scale) {
   __shared__ float red[3][256];
   float total = 0.f;
   for (int v = 0; v < a.views; ++v) {
@@ -118,6 +118,12 @@ __global__ void __launch_bounds__(256) loss_finalize_kernel(const __grid_constan
   if (threadIdx.x == 0) a.loss[0] = total;
 }
 
+__global__ void __launch_bounds__(256) loss_finalize_kernel(const __grid_constant__ LossArgs a,
+                                                            const float* __restrict__ partials,
+                                                            float* __restrict__ scale) {
+  loss_finalize_block(a, partials, scale);
+}
+
 // Pass 3: dL/dD = scale[v] * sign, same block layout as pass 1
 __global__ void __launch_bounds__(kLossThreads) scale_kernel(const __grid_constant__ LossArgs a,
                                                              const float* __restrict__ scale) {
@@ -148,8 +154,18 @@ struct TileLossArgs {
   const float* jobs;
 };
 
-__global__ void __launch_bounds__(kLossThreads) loss_tiles_partial_kernel(const __grid_constant__ TileLossArgs t,
-                                                                          float* __restrict__ partials) {
+// One launch: every block sums its chunk of the per-(tile, block) partials;
+// the last block to finish (a ticket counter, reset by that block) then
+// finalises the loss and the depth scales over all blocks' partials in block
+// order (so the result does not depend on which block is last), and, given
+// `step`, advances the device Adam step counter of the training step.
+static_assert(kLossThreads == 256, "the finalize step is written for 256 threads");
+__global__ void __launch_bounds__(kLossThreads) loss_tiles_kernel(const __grid_constant__ TileLossArgs t,
+                                                                  const __grid_constant__ LossArgs la,
+                                                                  float* __restrict__ partials,
+                                                                  float* __restrict__ scale,
+                                                                  uint32_t* __restrict__ ticket,
+                                                                  long long* __restrict__ step) {
   int v = 0;
   for (int k = 1; k < t.views; ++k)
     if ((int)blockIdx.x >= t.block_base[k]) v = k;
@@ -182,6 +198,20 @@ __global__ void __launch_bounds__(kLossThreads) loss_tiles_partial_kernel(const 
     float s = 0.f;
     for (int w = 0; w < kLossThreads / 32; ++w) s += red[threadIdx.x][w];
     partials[3 * blockIdx.x + threadIdx.x] = s;
+  }
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partials are visible before its ticket
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  loss_finalize_block(la, partials, scale);
+  if (threadIdx.x == 0) {
+    *ticket = 0u;
+    if (step) *step += 1;
   }
 }
 
@@ -302,7 +332,8 @@ void launch_loss(const LossArgs& a, float* partials, cudaStream_t s, int64_t* la
 }
 
 void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss, float* depth_scale,
-                                float* partials, cudaStream_t s, int64_t* launches) {
+                                float* partials, uint32_t* ticket, long long* step, cudaStream_t s,
+                                int64_t* launches) {
   TileLossArgs t;
   LossArgs la;
   t.views = la.views = a.views;
@@ -322,10 +353,12 @@ void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss,
   }
   t.block_base[a.views] = blocks;
   la.n_blocks = blocks;
-  if (blocks == 0) return;
-  loss_tiles_partial_kernel<<<blocks, kLossThreads, 0, s>>>(t, partials);
-  loss_finalize_kernel<<<1, 256, 0, s>>>(la, partials, depth_scale);
-  if (launches) *launches += 2;
+  if (blocks == 0) {
+    if (step) launch_step_increment(step, s);
+    return;
+  }
+  loss_tiles_kernel<<<blocks, kLossThreads, 0, s>>>(t, la, partials, depth_scale, ticket, step);
+  if (launches) *launches += 1;
 }
 
 void launch_adam(float* p, float* g, float* m, float* v, int64_t n_gauss, int sh_degree, const float lr[6],

@@ -43,7 +43,15 @@ __global__ void __launch_bounds__(kSortThreads) radix_upsweep(const uint32_t* __
   const uint64_t beg64 = (uint64_t)blockIdx.x * chunk;
   const uint32_t beg = (uint32_t)(beg64 < n ? beg64 : (uint64_t)n);
   const uint32_t end = (uint32_t)(beg64 + chunk < n ? beg64 + chunk : (uint64_t)n);
-  for (uint32_t i = beg + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+  // lanes with the same digit add their count with one shared atomic (keys
+  // in a run share the high digits: per-lane atomics would serialise)
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t base = beg; base < end; base += kSortThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t d = i < end ? (keys[i] >> shift) & mask : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
   __syncthreads();
   ghist[threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
 }
@@ -204,11 +212,19 @@ __global__ void __launch_bounds__(kScanThreads) dup_scan_kernel(uint32_t* __rest
   }
 }
 
+// Writes the pairs of the block's kDupChunk consecutive (depth-sorted) items
+// at the offsets of the scan.  The block's pairs are spread over all its
+// threads -- pair k of the block goes to thread k mod 256, its item found by
+// a binary search over the block's exclusive prefix in shared memory -- so a
+// Gaussian covering thousands of tiles does not serialise one thread, and
+// consecutive threads write consecutive slots.
 __global__ void __launch_bounds__(kDupThreads) dup_write_kernel(
     int n, const uint32_t* __restrict__ sorted_ids, const uint32_t* __restrict__ tiles,
     const ushort4* __restrict__ rects, const __grid_constant__ TileMap map,
     const uint32_t* __restrict__ block_offsets, uint32_t* __restrict__ tile_keys, uint32_t* __restrict__ vals,
     uint32_t capacity, uint32_t* overflow) {
+  __shared__ uint32_t s_excl[kDupChunk];
+  __shared__ uint32_t s_id[kDupChunk];
   const int base = blockIdx.x * kDupChunk + threadIdx.x * kDupItems;
   uint32_t cnt[kDupItems];
   uint32_t id[kDupItems];
@@ -220,25 +236,36 @@ __global__ void __launch_bounds__(kDupThreads) dup_write_kernel(
     s += cnt[j];
   }
   uint32_t total;
-  uint64_t off = (uint64_t)block_offsets[blockIdx.x] + block_exclusive_scan(s, &total);
-  bool over = false;
+  uint32_t run = block_exclusive_scan(s, &total);
 #pragma unroll
   for (int j = 0; j < kDupItems; ++j) {
-    if (cnt[j] == 0) continue;
-    const ushort4 r = rects[id[j]];
-    const int v = map.views == 1 ? 0 : (int)(id[j] / (uint32_t)map.n_per_view);
-    const uint32_t tbase = map.tile_base[v];
-    const int tiles_x = map.tiles_x[v];
-    for (int ty = r.y; ty < r.w; ++ty)
-      for (int tx = r.x; tx < r.z; ++tx) {
-        if (off < capacity) {
-          tile_keys[off] = tbase + (uint32_t)(ty * tiles_x + tx);
-          vals[off] = id[j];
-        } else {
-          over = true;
-        }
-        ++off;
-      }
+    s_excl[threadIdx.x * kDupItems + j] = run;
+    s_id[threadIdx.x * kDupItems + j] = id[j];
+    run += cnt[j];
+  }
+  __syncthreads();
+  const uint64_t off0 = (uint64_t)block_offsets[blockIdx.x];
+  bool over = false;
+  for (uint32_t k = threadIdx.x; k < total; k += kDupThreads) {
+    // the item owning pair k: the last o with s_excl[o] <= k (items with no
+    // pairs share their successor's prefix and are never the last such o)
+    int o = 0;
+#pragma unroll
+    for (int step = kDupChunk / 2; step > 0; step >>= 1)
+      if (s_excl[o + step] <= k) o += step;
+    const uint32_t g = s_id[o];
+    const ushort4 r = rects[g];
+    const uint32_t local = k - s_excl[o];
+    const uint32_t width = (uint32_t)(r.z - r.x);
+    const uint32_t ty = r.y + local / width, tx = r.x + local % width;
+    const int v = map.views == 1 ? 0 : (int)(g / (uint32_t)map.n_per_view);
+    const uint64_t off = off0 + k;
+    if (off < capacity) {
+      tile_keys[off] = map.tile_base[v] + ty * (uint32_t)map.tiles_x[v] + tx;
+      vals[off] = g;
+    } else {
+      over = true;
+    }
   }
   if (over) atomicOr(overflow, 1u);
 }
@@ -276,8 +303,9 @@ __global__ void export_keys_ranges_kernel(const uint2* __restrict__ ranges, cons
 }
 
 int sort_blocks(uint32_t n, int num_sms, int max_blocks) {
-  // about four rounds of 256 items per block; at most four blocks per SM
-  int g = (int)std::min<uint64_t>(((uint64_t)n + 1023) / 1024, (uint64_t)std::max(1, 4 * num_sms));
+  // at least four rounds of 256 items per block; at most eight blocks per SM
+  // (one resident wave of 2048 threads per SM)
+  int g = (int)std::min<uint64_t>(((uint64_t)n + 1023) / 1024, (uint64_t)std::max(1, 8 * num_sms));
   return std::max(1, std::min(g, max_blocks));
 }
 

@@ -376,16 +376,24 @@ __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_
 }
 
 // One CTA per tile: bitonic sort of (depth bits << 32 | id) in shared memory.
+// The last binning kernel: it also zeroes its tile's counter (and block 0
+// the large-splat queue length), leaving both zero for the next forward pass.
 template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t* __restrict__ offsets,
-                                                                 const uint32_t* __restrict__ counts,
+                                                                 uint32_t* __restrict__ counts,
                                                                  uint32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ zkey,
                                                                  uint2* __restrict__ ranges, uint32_t capacity,
-                                                                 uint32_t* __restrict__ overflow) {
+                                                                 uint32_t* __restrict__ overflow,
+                                                                 uint32_t* __restrict__ big_len) {
   __shared__ unsigned long long s[CAP];
   const int t = blockIdx.x;
   const uint32_t off = offsets[t], n = counts[t];
+  __syncthreads();  // every thread has read counts[t]
+  if (threadIdx.x == 0) {
+    counts[t] = 0u;
+    if (t == 0) *big_len = 0u;
+  }
   const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
   if (threadIdx.x == 0) ranges[t] = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
   if (n <= 1 || !fits) return;
@@ -531,7 +539,8 @@ void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches
 
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   tile_sort_kernel<kTileSortCap><<<a.n_tiles, kSortThreads, 0, s>>>(a.offsets, a.counts, a.ids, a.zkey, a.ranges,
-                                                                    a.capacity, a.overflow);
+                                                                    a.capacity, a.overflow,
+                                                                    const_cast<uint32_t*>(a.big_len));
   if (launches) *launches += 1;
 }
 

@@ -109,11 +109,13 @@ def flagged_voxels(rep: dict, voxel_size: float, excused_blocks: set) -> set:
 
 
 def check_seeds(got_means: np.ndarray, rep: dict, voxel_size: float, excused_blocks: set, log: list,
-                budget: int):
+                budget: int | None = None):
     """Seeded means of the GPU (float32 rows, any order) against the oracle's
     novelty report: every oracle seed has a GPU mean within TOL_M and vice
-    versa, except seeds of flagged voxels (``flagged_voxels``).  Returns
-    (matched GPU rows, matched oracle leaves' report rows)."""
+    versa, except seeds of flagged voxels (``flagged_voxels``), at most
+    ``budget`` of them (default: the number of flagged voxels, a flip being
+    possible only there).  Returns (matched GPU rows, matched oracle leaves'
+    report rows)."""
     from scipy.spatial import cKDTree
     s = float(np.float32(voxel_size))
     flagged = flagged_voxels(rep, voxel_size, excused_blocks)
@@ -146,6 +148,7 @@ def check_seeds(got_means: np.ndarray, rep: dict, voxel_size: float, excused_blo
         (log.append(("seed",) + rec) if want_vox[k] in flagged else far.append(rec))
     assert not far, f"{len(far)} seed mismatches away from any decision boundary: {far[:5]}"
     n_flips = len(unmatched_got) + len(unmatched_want)
+    budget = len(flagged) if budget is None else budget
     assert n_flips <= budget, f"{n_flips} seed flips (budget {budget})"
     return np.array(gi, np.int64), seed_rows[np.array(wi, np.int64)] if wi else np.zeros(0, np.int64)
 

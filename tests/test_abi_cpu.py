@@ -46,7 +46,7 @@ def test_defaults_and_null_handling():
     lib = ensure_built()
     from paper_2408_12677_gb300 import abi
     c = abi.raster_cfg()
-    assert (c.tile_w, c.tile_h, c.batch) == (16, 16, 256)
+    assert (c.tile_w, c.tile_h, c.batch) == (16, 16, 32)
     assert abs(c.alpha_min - 1 / 255) < 1e-9 and abs(c.alpha_max - 0.99) < 1e-7
     assert abs(c.t_eps - 1e-4) < 1e-10 and abs(c.dilation - 0.3) < 1e-7 and abs(c.near_z - 0.2) < 1e-7
     a = abi.adam_cfg()
