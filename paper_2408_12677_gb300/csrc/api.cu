@@ -56,10 +56,13 @@ struct gs_ctx {
   uint32_t* torder = nullptr;   // raster visit order of the tiles (longest lists first)
   uint32_t* scan_aux = nullptr;  // multi-block tile scan scratch
   uint32_t* bigq = nullptr;     // ids of Gaussians covering more than kBigTiles tiles
-  uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue, [1] raster job counter, [2] unused,
-                                  // [3] ticket of the fused-loss reduction (0 between launches)
+  uint32_t* d_bigmeta = nullptr;  // [0] length of the large-splat queue, [1] / [2] forward / backward raster
+                                  // job counters, [3] ticket of the fused-loss reduction (0 between launches)
   bool counts_zero = false;       // the tile counters and the large-splat queue length are 0 (the per-tile
                                   // sort, the last binning kernel, zeroes them)
+  bool fwd_work_zero = false;     // the forward / backward raster job counters are 0 (the per-tile sort zeroes
+  bool bwd_work_zero = false;     // both; a raster launch uses its counter up)
+  bool g2d_zero = false;          // the gradient records are all 0 (their consumers clear what they read)
   unsigned long long* d_binstats = nullptr;  // [0] total pairs, [1] longest tile list
   long long* d_step = nullptr;               // device Adam step counter (step = 0 calls)
   int64_t cap_px = 0;
@@ -213,6 +216,7 @@ gs_status ensure_n(gs_ctx* c, int64_t n) {
   GS_GROW(c, cap_n, regrow(&c->rects, cap));
   GS_GROW(c, cap_n, regrow(&c->bigq, cap));
   GS_GROW(c, cap_n, regrow(&c->g2d, 3 * cap));
+  c->g2d_zero = false;
   GS_GROW(c, cap_n, regrow(&c->dup_sums, (int64_t)dup_blocks((int)cap) + 1));
   // per (block, view) pose partials: blocks(n) * V <= blocks(V n) + V, for
   // blocks of 64 or more Gaussians
@@ -473,12 +477,14 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
     StageTimer t(c, GS_STAGE_DUPLICATE, s);
     launch_tile_scatter(tb, s, &c->launches);
   }
+  tb.raster_work = c->persistent ? c->d_bigmeta + 1 : nullptr;
   {
     StageTimer t(c, GS_STAGE_PAIR_SORT, s);
     launch_tile_sort(tb, s, &c->launches);
   }
   GS_CHECK_LAUNCH(c, "tile scatter/sort");
   c->counts_zero = true;
+  if (tb.raster_work) c->fwd_work_zero = c->bwd_work_zero = true;
   c->st_pairs = P;
   c->st_pair_buf = 0;
   c->st_ordered = tb.order != nullptr;
@@ -823,7 +829,8 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.ids = c->pv[c->st_pair_buf];
   ra.feat = c->feat;
   ra.order = c->st_ordered ? c->torder : nullptr;
-  ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;
+  ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;  // the forward counter; the backward pass uses [2]
+  ra.zero_work = true;
   ra.num_sms = c->num_sms;
   ra.loss_partials = nullptr;
   ra.w_color = 0.f;
@@ -925,10 +932,12 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
       ra.v[v].loss_dd = c->dl_img + 4 * L.pix_base[v] + 3 * np;
     }
   }
+  ra.zero_work = !c->fwd_work_zero;
   {
     StageTimer t(c, GS_STAGE_RASTER_FWD, s);
     launch_raster_fwd(ra, c->T_final, c->last, c->counting ? c->d_evals : nullptr, s);
   }
+  c->fwd_work_zero = false;
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_fwd");
   c->st_g = *g;
@@ -972,19 +981,24 @@ gs_status check_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
 gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                           const float* const* dL_ddepth, const float* const* dL_dalpha, cudaStream_t s,
                           const float* depth_scale = nullptr) {
-  const int64_t items = c->st_n * c->st_views;
-  GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)items, s));
+  // the records are zero unless a backward pass ran without its consumer (or
+  // the buffer is new): then clear the whole buffer once
+  if (!c->g2d_zero) GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)c->cap_n, s));
   RasterArgs ra = raster_args(c, cfg);
+  if (ra.work) ra.work = c->d_bigmeta + 2;
+  ra.zero_work = !c->bwd_work_zero;
   ra.depth_scale = depth_scale;
   for (int v = 0; v < c->st_views; ++v) {
     ra.v[v].dLdc = dL_dcolor[v];
     ra.v[v].dLdd = dL_ddepth[v];
     ra.v[v].dLda = dL_dalpha ? dL_dalpha[v] : nullptr;
   }
+  c->g2d_zero = false;  // until a consumer has read (and cleared) the records
   {
     StageTimer t(c, GS_STAGE_RASTER_BWD, s);
     launch_raster_bwd(ra, c->T_final, c->last, c->g2d, s);
   }
+  c->bwd_work_zero = false;
   c->launches += 1;
   GS_CHECK_LAUNCH(c, "raster_bwd");
   return GS_OK;
@@ -1056,6 +1070,7 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
     }
   }
   GS_CHECK_LAUNCH(c, "project_bwd_adam");
+  c->g2d_zero = true;  // the consumer clears the records it reads
   return GS_OK;
 }
 
@@ -1083,6 +1098,7 @@ gs_status render_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     }
   }
   GS_CHECK_LAUNCH(c, "project_bwd");
+  c->g2d_zero = true;  // the consumer clears the records it reads
   return GS_OK;
 }
 

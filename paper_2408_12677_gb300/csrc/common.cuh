@@ -4,6 +4,8 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 namespace gs {
@@ -232,6 +234,40 @@ __device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter,
   if (lane == leader) base = atomicAdd(&counter[t], (uint32_t)__popc(peers));
   base = __shfl_sync(peers, base, leader);
   return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of an iteration form one chain
+// on one stream; launched with launch_pdl, a kernel's CTAs may be scheduled
+// while the previous kernel drains its last CTAs (and, in a CUDA graph, the
+// launch gap between them shrinks).  Every chained kernel starts with
+// pdl_wait(), which returns once the previous kernel has completed and its
+// memory is visible (a no-op for a kernel launched without the attribute),
+// and then calls pdl_trigger(), which allows the next kernel to be scheduled
+// as soon as SMs free up.  Nothing before pdl_wait() touches memory, so the
+// results are those of plain stream order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" :::); }
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_trigger();
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 }  // namespace gs

@@ -58,7 +58,7 @@ void launch_bin_prepare(int n, const float* mean2d, const float* extent, const f
                         uint32_t* big_queue, uint32_t* big_len, cudaStream_t s);
 // g2d [V * n, 12] -> parameter gradients summed over the views (+=) and,
 // if pose_partials is non-null, per-block pose partials [blocks][V][6]
-int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales,
+int launch_project_bwd(const ProjectArgs& a, float4* g2d, float* g_means, float* g_log_scales,
                        float* g_quats, float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s);
 // dL_dpose[v][k] += sum over blocks of partials[b][v][k]
 void launch_pose_reduce(const float* partials, int nblocks, int views, float* dL_dpose, cudaStream_t s);
@@ -78,7 +78,7 @@ void launch_step_increment(long long* step, cudaStream_t s);
 void init_project_kernels();
 // fused projection backward + Adam over the flat buffer (gradients summed
 // over the views, one step)
-int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
+int launch_project_bwd_adam(const ProjectArgs& a, float4* g2d, float* params, float* m, float* v,
                             const AdamArgs& ad, float* pose_partials, cudaStream_t s);
 int project_bwd_blocks(int n);
 
@@ -139,6 +139,7 @@ struct TileBinArgs {
   uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
   bool small_counted;         // counts already hold every item with at most kBigTiles tiles (projection)
   uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
+  uint32_t* raster_work = nullptr;  // nullable: the forward and backward raster job counters, zeroed by the sort
 };
 int tile_sort_capacity();
 int64_t tile_scan_aux_size(int64_t n_tiles);
@@ -171,7 +172,8 @@ struct RasterArgs {
   const uint32_t* ids;
   const float4* feat;
   const uint32_t* order;  // nullable
-  uint32_t* work;         // nullable: job counter of the persistent form, zeroed by the launcher
+  uint32_t* work;         // nullable: job counter of the persistent form
+  bool zero_work;         // the launcher zeroes *work first (it is not known to be 0)
   int num_sms;
   // fused loss (forward): per (tile, 8 x 8 block) partial sums {|colour
   // residual|, |depth residual| over valid targets, valid count} at

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kLossThreads) loss_tiles_kernel(const __grid_c
                                                                   float* __restrict__ scale,
                                                                   uint32_t* __restrict__ ticket,
                                                                   long long* __restrict__ step) {
+  pdl_enter();
   int v = 0;
   for (int k = 1; k < t.views; ++k)
     if ((int)blockIdx.x >= t.block_base[k]) v = k;
@@ -357,7 +358,7 @@ void launch_loss_tiles_finalize(const RasterArgs& a, float w_depth, float* loss,
     if (step) launch_step_increment(step, s);
     return;
   }
-  loss_tiles_kernel<<<blocks, kLossThreads, 0, s>>>(t, la, partials, depth_scale, ticket, step);
+  launch_pdl(loss_tiles_kernel, blocks, kLossThreads, 0, s, t, la, partials, depth_scale, ticket, step);
   if (launches) *launches += 1;
 }
 

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   constexpr int NS = 3 * K;
   constexpr int RS = (NS % 2 == 0) ? NS + 1 : NS;  // odd row stride: conflict-free per-thread rows
   __shared__ float s_sh[kFwdThreads * RS];
+  pdl_enter();
   __shared__ float s_p[kFwdThreads * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
   // the block's slices of every parameter array are contiguous: stage them
   // all at once with coalesced asynchronous copies
@@ -416,6 +417,15 @@ __device__ __forceinline__ bool nonzero_record(const float4& G0, const float4& G
          (G1.z != 0.f) | (G2.x != 0.f) | (G2.y != 0.f) | (G2.z != 0.f);
 }
 
+// The consumer of a gradient record leaves it zero for the next backward
+// pass (the raster backward pass only adds to records).
+__device__ __forceinline__ void zero_record(float4* rec) {
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  rec[0] = z;
+  rec[1] = z;
+  rec[2] = z;
+}
+
 // deterministic per-block sum of the pose gradient into out[0..5]; every
 // thread of the block calls it
 __device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float* __restrict__ out) {
@@ -442,11 +452,12 @@ __device__ __forceinline__ void block_pose_partial(const float (&pose)[6], float
 // the gradient arrays.
 template <int D>
 __global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(const __grid_constant__ ProjectArgs a,
-                                                                  const float4* __restrict__ g2d,
+                                                                  float4* __restrict__ g2d,
                                                                   float* __restrict__ gm, float* __restrict__ gls,
                                                                   float* __restrict__ gq, float* __restrict__ glog,
                                                                   float* __restrict__ gsh,
                                                                   float* __restrict__ pose_partials) {
+  pdl_enter();
   constexpr int K = (D + 1) * (D + 1);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = i < a.n;
@@ -467,6 +478,7 @@ __global__ void __launch_bounds__(kBwdThreads) project_bwd_kernel(const __grid_c
       const size_t it = (size_t)v * a.n + i;
       const float4 G0 = g2d[3 * it], G1 = g2d[3 * it + 1], G2 = g2d[3 * it + 2];
       if (nonzero_record(G0, G1, G2)) {
+        zero_record(g2d + 3 * it);
         any = true;
         GaussGrad<D> gg;
         gaussian_grad<D>(a.cv[v], a.dilation, p, q4, ls, logit, a.sh + (size_t)i * K * 3, G0, G1, G2, gg);
@@ -510,7 +522,10 @@ __device__ __forceinline__ void device_bias_corrections(AdamArgs& ad) {
   ad.inv_sqrt_bc2 = rsqrtf(-expm1f(t * ad.log_beta2));
 }
 
-__global__ void step_increment_kernel(long long* step) { *step += 1; }
+__global__ void step_increment_kernel(long long* step) {
+  pdl_enter();
+  *step += 1;
+}
 
 __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, const AdamArgs& ad) {
   adam_apply(p, g, m, v, lr, ad.beta1, ad.beta2, ad.eps, ad.step_scale, ad.inv_sqrt_bc2);
@@ -564,10 +579,11 @@ struct FusedSmemMulti {
 
 template <int D, bool MULTI>
 __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
-                                                                         const float4* __restrict__ g2d,
+                                                                         float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
                                                                          float* __restrict__ pose_partials) {
+  pdl_enter();
   device_bias_corrections(ad);
   using S = typename std::conditional<MULTI, FusedSmemMulti<D>, FusedSmem<D>>::type;
   constexpr int K = S::K, NS = S::NS, RS = S::RS, B = S::B;
@@ -608,6 +624,7 @@ __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kerne
     G0 = g2d[3 * i];
     G1 = g2d[3 * i + 1];
     G2 = g2d[3 * i + 2];
+    if (nonzero_record(G0, G1, G2)) zero_record(g2d + 3 * i);
   }
   cp_async_wait<1>();
   __syncthreads();
@@ -634,6 +651,7 @@ __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kerne
         G0 = g2d[3 * it];
         G1 = g2d[3 * it + 1];
         G2 = g2d[3 * it + 2];
+        if (nonzero_record(G0, G1, G2)) zero_record(g2d + 3 * it);
       }
       GaussGrad<D> gg;
       const bool nz = nonzero_record(G0, G1, G2);
@@ -765,10 +783,10 @@ void launch_project_fwd(const ProjectArgs& a, float4* feat, uint32_t* depth_key,
   if (a.n <= 0) return;
   const int nb = (a.n + kFwdThreads - 1) / kFwdThreads;
   switch (a.sh_degree) {
-    case 0: project_fwd_kernel<0><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
-    case 1: project_fwd_kernel<1><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
-    case 2: project_fwd_kernel<2><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
-    default: project_fwd_kernel<3><<<nb, kFwdThreads, 0, s>>>(a, feat, depth_key, tiles_touched, rects); break;
+    case 0: launch_pdl(project_fwd_kernel<0>, nb, kFwdThreads, 0, s, a, feat, depth_key, tiles_touched, rects); break;
+    case 1: launch_pdl(project_fwd_kernel<1>, nb, kFwdThreads, 0, s, a, feat, depth_key, tiles_touched, rects); break;
+    case 2: launch_pdl(project_fwd_kernel<2>, nb, kFwdThreads, 0, s, a, feat, depth_key, tiles_touched, rects); break;
+    default: launch_pdl(project_fwd_kernel<3>, nb, kFwdThreads, 0, s, a, feat, depth_key, tiles_touched, rects); break;
   }
 }
 
@@ -783,27 +801,27 @@ void launch_bin_prepare(int n, const float* mean2d, const float* extent, const f
 
 int project_bwd_blocks(int n) { return n > 0 ? (n + kBwdThreads - 1) / kBwdThreads : 0; }
 
-int launch_project_bwd(const ProjectArgs& a, const float4* g2d, float* g_means, float* g_log_scales, float* g_quats,
+int launch_project_bwd(const ProjectArgs& a, float4* g2d, float* g_means, float* g_log_scales, float* g_quats,
                        float* g_logits, float* g_sh, float* pose_partials, cudaStream_t s) {
   const int nb = project_bwd_blocks(a.n);
   if (nb == 0) return 0;
   switch (a.sh_degree) {
-    case 0: project_bwd_kernel<0><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
-    case 1: project_bwd_kernel<1><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
-    case 2: project_bwd_kernel<2><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
-    default: project_bwd_kernel<3><<<nb, kBwdThreads, 0, s>>>(a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    case 0: launch_pdl(project_bwd_kernel<0>, nb, kBwdThreads, 0, s, a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    case 1: launch_pdl(project_bwd_kernel<1>, nb, kBwdThreads, 0, s, a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    case 2: launch_pdl(project_bwd_kernel<2>, nb, kBwdThreads, 0, s, a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
+    default: launch_pdl(project_bwd_kernel<3>, nb, kBwdThreads, 0, s, a, g2d, g_means, g_log_scales, g_quats, g_logits, g_sh, pose_partials); break;
   }
   return nb;
 }
 
-int launch_project_bwd_adam(const ProjectArgs& a, const float4* g2d, float* params, float* m, float* v,
+int launch_project_bwd_adam(const ProjectArgs& a, float4* g2d, float* params, float* m, float* v,
                             const AdamArgs& ad, float* pose_partials, cudaStream_t s) {
   if (a.n <= 0) return 0;
   const int bt = a.views == 1 ? fused_threads<false>() : fused_threads<true>();
   const int nb = (a.n + bt - 1) / bt;
 #define GS_FUSED(D_, M_, S_)                                                                                  \
-  project_bwd_adam_kernel<D_, M_><<<nb, fused_threads<M_>(), (int)sizeof(S_<D_>), s>>>(a, g2d, params, m, v, ad, \
-                                                                                       pose_partials)
+  launch_pdl(project_bwd_adam_kernel<D_, M_>, nb, fused_threads<M_>(), sizeof(S_<D_>), s, a, g2d, params, m, v, ad, \
+             pose_partials)
   if (a.views == 1) {
     switch (a.sh_degree) {
       case 0: GS_FUSED(0, false, FusedSmem); break;
@@ -838,7 +856,7 @@ void init_project_kernels() {
 #undef GS_ATTR
 }
 
-void launch_step_increment(long long* step, cudaStream_t s) { step_increment_kernel<<<1, 1, 0, s>>>(step); }
+void launch_step_increment(long long* step, cudaStream_t s) { launch_pdl(step_increment_kernel, 1, 1, 0, s, step); }
 
 void launch_pose_reduce(const float* partials, int nblocks, int views, float* dL_dpose, cudaStream_t s) {
   if (nblocks <= 0 || views <= 0) return;

@@ -150,16 +150,8 @@ __device__ __forceinline__ f2x f2_pack(float lo, float hi) {
   return r;
 }
 __device__ __forceinline__ f2x f2_bcast(float x) { return f2_pack(x, x); }
-__device__ __forceinline__ float f2_lo(f2x r) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-  return a;
-}
-__device__ __forceinline__ float f2_hi(f2x r) {
-  float a, b;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-  return b;
-}
+__device__ __forceinline__ float f2_lo(f2x r) { return __uint_as_float((unsigned)(r & 0xFFFFFFFFull)); }
+__device__ __forceinline__ float f2_hi(f2x r) { return __uint_as_float((unsigned)(r >> 32)); }
 __device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
   f2x d;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -384,6 +376,7 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
                                                               int32_t* __restrict__ last_all,
                                                               unsigned long long* __restrict__ counters,
                                                               uint32_t* __restrict__ work) {
+  pdl_enter();
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
   const int warp = threadIdx.x >> 5;
@@ -657,6 +650,7 @@ __global__ void __launch_bounds__(kThreads, 6) raster_bwd_kernel(const __grid_co
                                                                  const int32_t* __restrict__ last_all,
                                                                  float* __restrict__ g2d,
                                                                  uint32_t* __restrict__ work) {
+  pdl_enter();
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
   __shared__ uint32_t s_id[kThreads / 32][32];
@@ -717,9 +711,10 @@ void fwd_shape(const RasterArgs& a, const RasterParams& rp, float* T_final, int3
   if (a.work) {
     static int per_sm = 0;
     auto* k = raster_fwd_kernel<TW, TH, COUNT, LOSS, true>;
-    k<<<persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s>>>(a, rp, T_final, last, counters, a.work);
+    launch_pdl(k, persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s, a, rp, T_final, last, counters, a.work);
   } else {
-    raster_fwd_kernel<TW, TH, COUNT, LOSS, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, counters, nullptr);
+    launch_pdl(raster_fwd_kernel<TW, TH, COUNT, LOSS, false>, nt, kThreads, 0, s, a, rp, T_final, last, counters,
+               (uint32_t*)nullptr);
   }
 }
 
@@ -738,9 +733,9 @@ void bwd_shape(const RasterArgs& a, const RasterParams& rp, const float* T_final
   if (a.work) {
     static int per_sm = 0;
     auto* k = raster_bwd_kernel<TW, TH, true>;
-    k<<<persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s>>>(a, rp, T_final, last, g2d, a.work);
+    launch_pdl(k, persistent_grid(k, per_sm, nt, a.num_sms), kThreads, 0, s, a, rp, T_final, last, g2d, a.work);
   } else {
-    raster_bwd_kernel<TW, TH, false><<<nt, kThreads, 0, s>>>(a, rp, T_final, last, g2d, nullptr);
+    launch_pdl(raster_bwd_kernel<TW, TH, false>, nt, kThreads, 0, s, a, rp, T_final, last, g2d, (uint32_t*)nullptr);
   }
 }
 
@@ -750,7 +745,7 @@ void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsig
                        cudaStream_t s) {
   if (a.n_tiles == 0) return;
   const RasterParams rp = make_params(a);
-  if (a.work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
+  if (a.work && a.zero_work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
   const bool loss = a.loss_partials != nullptr;
   if (counters) {
     if (loss) fwd_shapes<true, true>(a, rp, T_final, last, counters, s);
@@ -764,7 +759,7 @@ void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsig
 void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t* last, float4* g2d, cudaStream_t s) {
   if (a.n_tiles == 0) return;
   const RasterParams rp = make_params(a);
-  if (a.work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
+  if (a.work && a.zero_work) cudaMemsetAsync(a.work, 0, sizeof(uint32_t), s);
   if (a.tile_w == 16) bwd_shape<16, 16>(a, rp, T_final, last, (float*)g2d, s);
   else if (a.tile_w == 8) bwd_shape<8, 32>(a, rp, T_final, last, (float*)g2d, s);
   else bwd_shape<32, 8>(a, rp, T_final, last, (float*)g2d, s);

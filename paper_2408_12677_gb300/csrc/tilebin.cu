@@ -120,6 +120,7 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
 // kBigTiles tiles; only the queued large ones are expanded here.
 template <bool SMALL>
 __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_constant__ TileBinArgs a) {
+  pdl_enter();
   for_each_pair<SMALL>(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                        [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
 }
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
                                                                  uint32_t* __restrict__ n_pairs,
                                                                  unsigned long long* __restrict__ stats,
                                                                  uint32_t* __restrict__ order) {
+  pdl_enter();
   __shared__ unsigned long long s[kScanThreads];
   __shared__ uint32_t s_max[32];
   const int per = (T + kScanThreads - 1) / kScanThreads;
@@ -225,6 +227,7 @@ constexpr int kScanAux = 36;
 
 __global__ void __launch_bounds__(256) tile_scan_up_kernel(int T, const uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ aux) {
+  pdl_enter();
   __shared__ uint32_t s_hist[33];
   __shared__ unsigned long long s_sum[8];
   __shared__ uint32_t s_max[8];
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(64) tile_scan_mid_kernel(int nb, const uint32_
                                                            uint32_t* __restrict__ aux_tail, uint32_t capacity,
                                                            uint32_t* __restrict__ n_pairs,
                                                            unsigned long long* __restrict__ stats) {
+  pdl_enter();
   __shared__ uint32_t s_tot[33];
   if (threadIdx.x < 33) {
     uint32_t t = 0;
@@ -305,6 +309,7 @@ __global__ void __launch_bounds__(256) tile_scan_down_kernel(int T, const uint32
                                                              uint32_t* __restrict__ offsets,
                                                              uint32_t* __restrict__ cursors,
                                                              uint32_t* __restrict__ order) {
+  pdl_enter();
   constexpr int PER = kScanTiles / 256;  // consecutive tiles per thread
   __shared__ unsigned long long s_scan[256];
   __shared__ unsigned long long s_base;
@@ -363,6 +368,7 @@ __global__ void __launch_bounds__(256) tile_scan_down_kernel(int T, const uint32
 }
 
 __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_constant__ TileBinArgs a) {
+  pdl_enter();
   bool over = false;
   for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                 [&](int g, uint32_t t, unsigned active) {
@@ -377,7 +383,8 @@ __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_
 
 // One CTA per tile: bitonic sort of (depth bits << 32 | id) in shared memory.
 // The last binning kernel: it also zeroes its tile's counter (and block 0
-// the large-splat queue length), leaving both zero for the next forward pass.
+// the large-splat queue length, and the two raster job counters when given),
+// leaving them zero for the next passes.
 template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t* __restrict__ offsets,
                                                                  uint32_t* __restrict__ counts,
@@ -385,14 +392,19 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
                                                                  const uint32_t* __restrict__ zkey,
                                                                  uint2* __restrict__ ranges, uint32_t capacity,
                                                                  uint32_t* __restrict__ overflow,
-                                                                 uint32_t* __restrict__ big_len) {
+                                                                 uint32_t* __restrict__ big_len,
+                                                                 uint32_t* __restrict__ raster_work) {
+  pdl_enter();
   __shared__ unsigned long long s[CAP];
   const int t = blockIdx.x;
   const uint32_t off = offsets[t], n = counts[t];
   __syncthreads();  // every thread has read counts[t]
   if (threadIdx.x == 0) {
     counts[t] = 0u;
-    if (t == 0) *big_len = 0u;
+    if (t == 0) {
+      *big_len = 0u;
+      if (raster_work) raster_work[0] = raster_work[1] = 0u;  // the raster passes' job counters
+    }
   }
   const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
   if (threadIdx.x == 0) ranges[t] = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
@@ -511,36 +523,36 @@ void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launc
   if (!a.small_counted) cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
   if (a.n > 0) {
     if (a.small_counted)  // the large splats only: a grid of warps over the queue
-      tile_count_kernel<false><<<std::max(1, 2 * a.num_sms), kBinThreads, 0, s>>>(a);
+      launch_pdl(tile_count_kernel<false>, std::max(1, 2 * a.num_sms), kBinThreads, 0, s, a);
     else
-      tile_count_kernel<true><<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
+      launch_pdl(tile_count_kernel<true>, bin_grid(a.n, a.num_sms), kBinThreads, 0, s, a);
     if (launches) *launches += 1;
   }
   if (a.n_tiles <= 4 * kScanThreads || !a.scan_aux) {  // one block is enough
-    tile_scan_kernel<<<1, kScanThreads, 0, s>>>(a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity, a.n_pairs,
-                                                a.stats, a.order);
+    launch_pdl(tile_scan_kernel, 1, kScanThreads, 0, s, a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity,
+               a.n_pairs, a.stats, a.order);
     if (launches) *launches += 1;
   } else {
     const int nb = (a.n_tiles + kScanTiles - 1) / kScanTiles;
     uint32_t* tail = a.scan_aux + (size_t)kScanAux * nb;
-    tile_scan_up_kernel<<<nb, 256, 0, s>>>(a.n_tiles, a.counts, a.scan_aux);
-    tile_scan_mid_kernel<<<1, 64, 0, s>>>(nb, a.scan_aux, tail, a.capacity, a.n_pairs, a.stats);
-    tile_scan_down_kernel<<<nb, 256, 0, s>>>(a.n_tiles, a.counts, a.scan_aux, tail, a.offsets, a.cursors, a.order);
+    launch_pdl(tile_scan_up_kernel, nb, 256, 0, s, a.n_tiles, a.counts, a.scan_aux);
+    launch_pdl(tile_scan_mid_kernel, 1, 64, 0, s, nb, a.scan_aux, tail, a.capacity, a.n_pairs, a.stats);
+    launch_pdl(tile_scan_down_kernel, nb, 256, 0, s, a.n_tiles, a.counts, a.scan_aux, tail, a.offsets, a.cursors,
+               a.order);
     if (launches) *launches += 3;
   }
 }
 
 void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   if (a.n > 0) {
-    tile_scatter_kernel<<<bin_grid(a.n, a.num_sms), kBinThreads, 0, s>>>(a);
+    launch_pdl(tile_scatter_kernel, bin_grid(a.n, a.num_sms), kBinThreads, 0, s, a);
     if (launches) *launches += 1;
   }
 }
 
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
-  tile_sort_kernel<kTileSortCap><<<a.n_tiles, kSortThreads, 0, s>>>(a.offsets, a.counts, a.ids, a.zkey, a.ranges,
-                                                                    a.capacity, a.overflow,
-                                                                    const_cast<uint32_t*>(a.big_len));
+  launch_pdl(tile_sort_kernel<kTileSortCap>, a.n_tiles, kSortThreads, 0, s, a.offsets, a.counts, a.ids, a.zkey,
+             a.ranges, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len), a.raster_work);
   if (launches) *launches += 1;
 }
 
