@@ -58,7 +58,7 @@ typedef enum {
   GS_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in gs_last_error) */
   GS_ERR_CAPACITY = 3,    /* (tile, Gaussian) pairs exceeded the reserved capacity in no-sync mode */
   GS_ERR_NONFINITE = 4,   /* non-finite values detected (gs_count_nonfinite) */
-  GS_ERR_BOUNDS = 5,      /* reserved: device-side bounds check failed */
+  GS_ERR_BOUNDS = 5,      /* the bounds-checked build met an out-of-bounds index (gs_sync_status) */
   GS_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait gave up */
   GS_ERR_OOM = 7,         /* cudaMalloc of context scratch failed */
   GS_ERR_STATE = 8        /* gs_render_bwd without a matching gs_render_fwd on this context */
@@ -168,8 +168,10 @@ gs_status gs_ctx_set_tile_order(gs_ctx *ctx, int on);
  * batch.  on = 0: one CTA per tile.  Results do not depend on it. */
 gs_status gs_ctx_set_persistent(gs_ctx *ctx, int on);
 
-/* Synchronise the stream, then report GS_ERR_CAPACITY if a no-sync forward
- * pass overflowed the pair buffers (and clear the flag). */
+/* Synchronise the stream, then report GS_ERR_BOUNDS if the bounds-checked
+ * build met an out-of-bounds index since the last call (see
+ * gs_bounds_checked), else GS_ERR_CAPACITY if a no-sync forward pass
+ * overflowed the pair buffers; clears the flag it reports. */
 gs_status gs_sync_status(gs_ctx *ctx, gs_stream_t stream);
 
 /* Counters of this context (host struct).  The two eval counters live on the
@@ -551,6 +553,23 @@ gs_status gs_seed_tsdf(gs_ctx *ctx, const float *rgb, const float *depth, const 
  * scratch group, which the next call allocates again). */
 gs_status gs_count_nonfinite(gs_ctx *ctx, const float *x, int64_t n, int64_t *count, gs_stream_t stream);
 gs_status gs_ctx_inject_alloc_failure(gs_ctx *ctx, int32_t after);
+
+/* Bounds-checked build (libgsplat_checked.so, compiled with GS_CHECKED; no
+ * counterpart in the paper: the stand-in for a race / memory checker).  Its
+ * kernels check every index they read from memory (list ids against the
+ * projected records, tile ranges against the pair buffer, tile numbers
+ * against the grid, ids against the items in the per-tile sort) before using
+ * it; a violation sets the context's bounds word and the access is skipped or
+ * redirected to a valid dummy (never a trap), and the next gs_sync_status
+ * returns GS_ERR_BOUNDS and clears the word.  The word's address is bound
+ * per library at context creation (the newest context's word collects the
+ * violations of all contexts of the process).  Results are otherwise those
+ * of the normal build.  gs_bounds_checked: 1 in the checked build, 0 in the
+ * normal one (no device access).  gs_ctx_inject_bounds_fault: sets the bounds
+ * word from the host, as a violation would, so callers can test the
+ * reporting path without a device fault; synchronises. */
+int gs_bounds_checked(void);
+gs_status gs_ctx_inject_bounds_fault(gs_ctx *ctx);
 
 /* Measured issue rates of the two ALU pipes the raster passes run on (no
  * counterpart in the paper: they are the denominators of the raster passes'

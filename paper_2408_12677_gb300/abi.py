@@ -15,6 +15,7 @@ import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgsplat.so")
+CHECKED_LIB_PATH = os.path.join(HERE, "libgsplat_checked.so")  # bounds-checked build (gs_bounds_checked)
 
 GS_OK = 0
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_NONFINITE",
@@ -142,6 +143,8 @@ EXPORTS = {
                                C.POINTER(C.c_int64), P]),
     "gs_count_nonfinite": (C.c_int, [P, P, C.c_int64, C.POINTER(C.c_int64), P]),
     "gs_ctx_inject_alloc_failure": (C.c_int, [P, C.c_int32]),
+    "gs_bounds_checked": (C.c_int, []),
+    "gs_ctx_inject_bounds_fault": (C.c_int, [P]),
     "gs_autotune": (C.c_int, [P, C.POINTER(gs_gaussians), C.c_int32, C.POINTER(gs_camera), C.POINTER(gs_viewmat),
                               C.POINTER(gs_raster_cfg), C.c_int32, C.POINTER(C.c_float), P]),
     "gs_set_eval_counting": (C.c_int, [P, C.c_int]),
@@ -561,6 +564,15 @@ def gs_count_nonfinite(ctx, x, stream=None) -> int:
 
 def gs_ctx_inject_alloc_failure(ctx, after: int = 1):
     _check(ctx, load().gs_ctx_inject_alloc_failure(ctx, int(after)), "gs_ctx_inject_alloc_failure")
+
+
+def gs_bounds_checked() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().gs_bounds_checked())
+
+
+def gs_ctx_inject_bounds_fault(ctx):
+    _check(ctx, load().gs_ctx_inject_bounds_fault(ctx), "gs_ctx_inject_bounds_fault")
 
 
 def gs_get_tile_ranges(ctx, ranges, stream=None):

@@ -86,6 +86,7 @@ struct gs_ctx {
   uint32_t* d_npairs = nullptr;
   unsigned long long* d_npairs_full = nullptr;
   uint32_t* d_overflow = nullptr;
+  uint32_t* d_bounds = nullptr;  // set by the checked build's kernels on an out-of-bounds index
   unsigned long long* h_pinned = nullptr;
   // eval counters (blended, visited) and per-stage event profiling
   bool counting = false;
@@ -545,6 +546,10 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_evals, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(c->d_overflow, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bounds, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_bounds, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = raster_bind_bounds(c->d_bounds);
+  if (e == cudaSuccess) e = tilebin_bind_bounds(c->d_bounds);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_pinned, 4 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     gs_ctx_destroy(c);
@@ -584,6 +589,7 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->scan_aux);
   cudaFree(c->bigq);
   cudaFree(c->d_bigmeta);
+  cudaFree(c->d_bounds);
   cudaFree(c->d_binstats);
   cudaFree(c->d_step);
   cudaFree(c->T_final);
@@ -660,7 +666,14 @@ gs_status gs_sync_status(gs_ctx* c, gs_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   GS_CUDA(c, cudaMemcpyAsync(c->h_pinned + 1, c->d_overflow, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(c, cudaMemcpyAsync(c->h_pinned + 2, c->d_npairs_full, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(c, cudaMemcpyAsync(c->h_pinned + 3, c->d_bounds, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(c, cudaStreamSynchronize(s));
+  if ((uint32_t)(c->h_pinned[3] & 0xFFFFFFFFull)) {
+    GS_CUDA(c, cudaMemsetAsync(c->d_bounds, 0, sizeof(uint32_t), s));
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    c->have_state = false;
+    return fail(c, GS_ERR_BOUNDS, "an index was out of bounds (bounds-checked build); the results since are invalid");
+  }
   const uint32_t ov = (uint32_t)(c->h_pinned[1] & 0xFFFFFFFFull);
   if (ov) {
     GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
@@ -828,6 +841,8 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.ranges = c->ranges;
   ra.ids = c->pv[c->st_pair_buf];
   ra.feat = c->feat;
+  ra.n_ids = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFFFll);
+  ra.n_items = (uint32_t)(c->st_n * c->st_views);
   ra.order = c->st_ordered ? c->torder : nullptr;
   ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;  // the forward counter; the backward pass uses [2]
   ra.zero_work = true;
@@ -1743,6 +1758,21 @@ gs_status gs_get_tile_ranges(gs_ctx* c, uint32_t* ranges, int64_t n_tiles, gs_st
 gs_status gs_state_token(const gs_ctx* c, uint64_t* token) {
   if (!c || !token) return GS_ERR_INVALID_ARG;
   *token = c->have_state ? c->state_token : 0;
+  return GS_OK;
+}
+
+int gs_bounds_checked(void) {
+#ifdef GS_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+gs_status gs_ctx_inject_bounds_fault(gs_ctx* c) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaMemset(c->d_bounds, 0xFF, sizeof(uint32_t)));
   return GS_OK;
 }
 

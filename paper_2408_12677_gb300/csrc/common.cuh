@@ -237,6 +237,36 @@ __device__ __forceinline__ uint32_t warp_agg_inc(uint32_t* __restrict__ counter,
 }
 
 // ---------------------------------------------------------------------------
+// Bounds-checked build (compiled with -DGS_CHECKED into libgsplat_checked.so):
+// every index read from memory (list ids, tile ranges, tile numbers computed
+// from rectangles, record ids) is checked before it is used; a violation
+// sets the context's bounds word (gs_sync_status reports GS_ERR_BOUNDS) and
+// the access is skipped or redirected to a valid dummy, never trapped.  The
+// normal build compiles the checks away.  Each translation unit has its own
+// copy of the word's address, bound by bind_bounds_word().
+// ---------------------------------------------------------------------------
+#ifdef GS_CHECKED
+static __device__ uint32_t* gs_bounds_word = nullptr;
+#endif
+__device__ __forceinline__ bool in_bounds(bool ok) {
+#ifdef GS_CHECKED
+  if (!ok && gs_bounds_word) atomicOr(gs_bounds_word, 1u);
+  return ok;
+#else
+  (void)ok;
+  return true;
+#endif
+}
+static inline cudaError_t bind_bounds_word(uint32_t* word) {
+#ifdef GS_CHECKED
+  return cudaMemcpyToSymbol(gs_bounds_word, &word, sizeof(word));
+#else
+  (void)word;
+  return cudaSuccess;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of an iteration form one chain
 // on one stream; launched with launch_pdl, a kernel's CTAs may be scheduled
 // while the previous kernel drains its last CTAs (and, in a CUDA graph, the

@@ -171,6 +171,7 @@ struct RasterArgs {
   const uint2* ranges;
   const uint32_t* ids;
   const float4* feat;
+  uint32_t n_ids, n_items;  // entries of ids, records of feat (bounds of the checked build)
   const uint32_t* order;  // nullable
   uint32_t* work;         // nullable: job counter of the persistent form
   bool zero_work;         // the launcher zeroes *work first (it is not known to be 0)
@@ -186,6 +187,10 @@ struct RasterArgs {
   RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);
+// bounds-checked build: point the translation unit's kernels at the
+// context's bounds word (no-op in the normal build)
+cudaError_t raster_bind_bounds(uint32_t* word);
+cudaError_t tilebin_bind_bounds(uint32_t* word);
 void launch_raster_fwd(const RasterArgs& a, float* T_final, int32_t* last, unsigned long long* counters,
                        cudaStream_t s);
 // loss from the forward pass's per-block partials: loss = sum over views of

@@ -36,6 +36,12 @@ struct Entry {
   float4 a, b, c;
 };
 
+// A list entry's item id; the checked build redirects an id beyond the
+// records to record 0 (and reports it), the normal build passes it through.
+__device__ __forceinline__ uint32_t checked_id(uint32_t g, uint32_t n_items) {
+  return in_bounds(g < n_items) ? g : 0u;
+}
+
 // Asynchronous copy of one 48 B record into shared memory (3 x 16 B cp.async).
 __device__ __forceinline__ void cp_record(float4* dst, const float4* __restrict__ feat, uint32_t g) {
   const float4* src = feat + 3 * (size_t)g;
@@ -103,7 +109,9 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
     if (tile >= a.v[k].tile_base) v = k;
   const int lt = (int)(tile - a.v[v].tile_base);
   const int tx = lt % a.v[v].tiles_x, ty = lt / a.v[v].tiles_x;
-  return TileJob{v, tx * TW, ty * TH, a.ranges[tile], tile};
+  uint2 r = a.ranges[tile];
+  if (!in_bounds(r.x <= r.y && r.y <= a.n_ids)) r = make_uint2(0u, 0u);  // checked build: an empty list
+  return TileJob{v, tx * TW, ty * TH, r, tile};
 }
 
 // Front-to-back step of one pixel for one list entry (Eq. 11 with the skip
@@ -200,12 +208,12 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
 
   // software pipeline: the records of the next 32 entries are in flight
   float4 f0, f1, f2;
-  if (lane < n) load_entry(feat, ids[r.x + lane], f0, f1, f2);
+  if (lane < n) load_entry(feat, checked_id(ids[r.x + lane], a.n_items), f0, f1, f2);
   for (int c0 = 0; c0 < n; c0 += 32) {
     if (__all_sync(kFull, done0 && done1)) break;
     const bool have = c0 + lane < n;
     const float4 h0 = f0, h1 = f1, h2 = f2;
-    if (c0 + 32 + lane < n) load_entry(feat, ids[r.x + c0 + 32 + lane], f0, f1, f2);
+    if (c0 + 32 + lane < n) load_entry(feat, checked_id(ids[r.x + c0 + 32 + lane], a.n_items), f0, f1, f2);
     Entry e;
     const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e) != 0u;
     __syncwarp();
@@ -564,19 +572,19 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
   int c0 = ((wmax - 1) >> 5) << 5;
   int cur = 0;
   if (c0 + lane < wmax) {
-    const uint32_t g = ids[r.x + c0 + lane];
+    const uint32_t g = checked_id(ids[r.x + c0 + lane], a.n_items);
     s_gid[0][lane] = g;
     cp_record(s_raw[0][lane], feat, g);
   }
   cp_commit();
-  uint32_t g2 = c0 >= 32 ? ids[r.x + c0 - 32 + lane] : 0u;
+  uint32_t g2 = c0 >= 32 ? checked_id(ids[r.x + c0 - 32 + lane], a.n_items) : 0u;
   for (; c0 >= 0; c0 -= 32, cur ^= 1) {
     if (c0 >= 32) {
       s_gid[cur ^ 1][lane] = g2;
       cp_record(s_raw[cur ^ 1][lane], feat, g2);
     }
     cp_commit();
-    if (c0 >= 64) g2 = ids[r.x + c0 - 64 + lane];
+    if (c0 >= 64) g2 = checked_id(ids[r.x + c0 - 64 + lane], a.n_items);
     cp_wait_prev();
     const bool have = c0 + lane < wmax;
     Entry e;
@@ -764,5 +772,7 @@ void launch_raster_bwd(const RasterArgs& a, const float* T_final, const int32_t*
   else if (a.tile_w == 8) bwd_shape<8, 32>(a, rp, T_final, last, (float*)g2d, s);
   else bwd_shape<32, 8>(a, rp, T_final, last, (float*)g2d, s);
 }
+
+cudaError_t raster_bind_bounds(uint32_t* word) { return bind_bounds_word(word); }
 
 }  // namespace gs

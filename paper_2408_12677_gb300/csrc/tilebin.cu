@@ -122,7 +122,10 @@ template <bool SMALL>
 __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_constant__ TileBinArgs a) {
   pdl_enter();
   for_each_pair<SMALL>(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
-                       [&](int, uint32_t t, unsigned active) { warp_agg_inc(a.counts, t, active); });
+                       [&](int, uint32_t t, unsigned active) {
+                         // (the checked build counts a tile beyond the grid into tile 0, reported)
+                         warp_agg_inc(a.counts, in_bounds(t < (uint32_t)a.n_tiles) ? t : 0u, active);
+                       });
 }
 
 // Length class of a tile list for the visit order: 0 for an empty list,
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_
   bool over = false;
   for_each_pair(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                 [&](int g, uint32_t t, unsigned active) {
-                  const uint32_t pos = warp_agg_inc(a.cursors, t, active);
+                  const uint32_t pos = warp_agg_inc(a.cursors, in_bounds(t < (uint32_t)a.n_tiles) ? t : 0u, active);
                   if (pos < a.capacity)
                     a.ids[pos] = (uint32_t)g;
                   else
@@ -393,7 +396,8 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
                                                                  uint2* __restrict__ ranges, uint32_t capacity,
                                                                  uint32_t* __restrict__ overflow,
                                                                  uint32_t* __restrict__ big_len,
-                                                                 uint32_t* __restrict__ raster_work) {
+                                                                 uint32_t* __restrict__ raster_work,
+                                                                 uint32_t n_items) {
   pdl_enter();
   __shared__ unsigned long long s[CAP];
   const int t = blockIdx.x;
@@ -426,11 +430,11 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
     unsigned long long x0 = ~0ull, x1 = ~0ull;
     if (e0 < n) {
       const uint32_t g = ids[off + e0];
-      x0 = ((unsigned long long)zkey[g] << 32) | g;
+      x0 = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
     }
     if (e0 + 1 < n) {
       const uint32_t g = ids[off + e0 + 1];
-      x1 = ((unsigned long long)zkey[g] << 32) | g;
+      x1 = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
     }
     const bool live = e0 < m;  // threads beyond m only keep padding
     // Only the warps holding keys below m run the network (64 keys per
@@ -484,7 +488,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
     unsigned long long key = ~0ull;
     if (i < n) {
       const uint32_t g = ids[off + i];
-      key = ((unsigned long long)zkey[g] << 32) | g;
+      key = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
     }
     s[i] = key;
   }
@@ -552,8 +556,10 @@ void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches
 
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   launch_pdl(tile_sort_kernel<kTileSortCap>, a.n_tiles, kSortThreads, 0, s, a.offsets, a.counts, a.ids, a.zkey,
-             a.ranges, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len), a.raster_work);
+             a.ranges, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n);
   if (launches) *launches += 1;
 }
+
+cudaError_t tilebin_bind_bounds(uint32_t* word) { return bind_bounds_word(word); }
 
 }  // namespace gs

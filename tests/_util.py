@@ -14,7 +14,7 @@ _lock = threading.Lock()
 def ensure_built():
     from paper_2408_12677_gb300 import abi, build
     with _lock:
-        if not os.path.exists(abi.LIB_PATH):
+        if not (os.path.exists(abi.LIB_PATH) and os.path.exists(abi.CHECKED_LIB_PATH)):
             build.build()
     return abi.load()
 
@@ -24,9 +24,12 @@ FLIP_EPS = 1e-4  # relative distance to a threshold within which float32 may dec
 
 
 def compare(name, got, ref, rtol, atol, norm_rtol, flip_budget=0, report=None, margins=None, kinds=None,
-            flip_eps=FLIP_EPS):
+            flip_eps=FLIP_EPS, groups=None):
     """Element-wise |got - ref| <= rtol |ref| + atol except for at most
     ``flip_budget`` elements ("flips"), and ||got - ref|| / ||ref|| <= norm_rtol.
+    With ``groups`` (one id per element) the budget counts distinct groups
+    among the flips instead of elements: one flipped decision of a Gaussian
+    moves all of that Gaussian's gradient elements.
 
     With ``margins`` (one per element: the oracle's relative
     float64 distance of the decisions behind the element to their thresholds,
@@ -66,7 +69,9 @@ def compare(name, got, ref, rtol, atol, norm_rtol, flip_budget=0, report=None, m
         report.append(info)
     assert not unexplained, f"{name}: {len(unexplained)} elements beyond tolerance away from every threshold: " \
                             f"{unexplained[:5]}"
-    assert int(bad.sum()) <= flip_budget, f"{name}: {info['bad']} flips (budget {flip_budget}): {info['flips'][:5]}"
+    n_flips = int(bad.sum()) if groups is None else int(np.unique(np.asarray(groups).ravel()[bad]).size)
+    info["flipped_groups"] = None if groups is None else n_flips
+    assert n_flips <= flip_budget, f"{name}: {info['bad']} flips (budget {flip_budget}): {info['flips'][:5]}"
     assert nrel <= norm_rtol, f"{name}: norm rel {nrel:.3e} (tolerance {norm_rtol})"
     return info
 

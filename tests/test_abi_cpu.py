@@ -33,6 +33,19 @@ def test_library_exports_every_declared_symbol():
     assert set(_declared()) <= set(abi.EXPORTS), "binding lacks a declared entry point"
 
 
+def test_checked_build_exports_the_same_boundary():
+    """libgsplat_checked.so (GS_CHECKED) declares itself and exports every
+    entry point too; the normal library says it is not the checked one."""
+    ensure_built()
+    from paper_2408_12677_gb300 import abi
+    checked = C.CDLL(abi.CHECKED_LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(checked, n)]
+    assert not missing, missing
+    checked.gs_bounds_checked.restype = C.c_int
+    assert checked.gs_bounds_checked() == 1
+    assert abi.gs_bounds_checked() is False
+
+
 def test_struct_layouts_match_header_sizes():
     from paper_2408_12677_gb300 import abi
     assert C.sizeof(abi.gs_camera) == 24

@@ -69,10 +69,17 @@ def check_grad_arrays(g, og, margins=None, names=NAMES + ("pose",), flip_gaussia
             assert np.abs(g[k]).max(initial=0.0) <= 1e-5 * G, (k, np.abs(g[k]).max())
             continue
         mk = {}
-        per = ref.size // max(ref.shape[0], 1)
+        n_g = max(ref.shape[0], 1)
+        per = ref.size // n_g
         if margins is not None and k != "pose":
-            mk = dict(margins=np.repeat(margins["gauss"], per), kinds=np.repeat(margins["gauss_kind"], per))
-        budget = 0 if k == "pose" else max(1, int(1e-5 * ref.size)) + flip_gaussians * per
+            # flips are decisions of single Gaussians (within flip_eps of a
+            # threshold): the budget counts flipped Gaussians, each of which
+            # moves up to `per` elements
+            mk = dict(margins=np.repeat(margins["gauss"], per), kinds=np.repeat(margins["gauss_kind"], per),
+                      groups=np.repeat(np.arange(n_g), per))
+            budget = max(1, int(1e-5 * n_g)) + flip_gaussians
+        else:
+            budget = 0 if k == "pose" else max(1, int(1e-5 * ref.size)) + flip_gaussians * per
         compare(k, g[k], ref, 1e-3, floor, 1e-3, budget, report, **mk)
 
 
