@@ -6,8 +6,9 @@
 //               total pair count and the longest list),
 //   3. scatter: every pair takes a slot of its tile's list with an atomic
 //               cursor and writes its Gaussian id,
-//   4. sort:    one CTA per tile sorts its list in shared memory by the 64-bit
-//               key (float32 depth bits << 32 | id), a bitonic network.
+//   4. sort:    each tile's list is sorted by the 64-bit key (float32 depth
+//               bits << 32 | id) with a bitonic network: by one warp in
+//               registers up to 512 entries, by a CTA in shared memory beyond.
 // The per-tile keys are unique, so the result is exactly the (tile, depth, id)
 // order of a stable sort and does not depend on the scatter's atomic order.
 // Counting and scattering expand the rectangles warp-cooperatively, so a
@@ -23,6 +24,8 @@ constexpr int kBinThreads = 256;
 constexpr int kBinWarps = kBinThreads / 32;
 constexpr int kScanThreads = 1024;
 constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;  // tiles per CTA of the per-tile sort
+constexpr int kWarpSortMax = 512;              // lists up to this length are sorted by one warp
 
 // Global tile of tile (tx, ty) of the view that item `it` belongs to.
 struct ItemTiles {
@@ -384,132 +387,157 @@ __global__ void __launch_bounds__(kBinThreads) tile_scatter_kernel(const __grid_
   if (over) atomicOr(a.overflow, 1u);
 }
 
-// One CTA per tile: bitonic sort of (depth bits << 32 | id) in shared memory.
-// The last binning kernel: it also zeroes its tile's counter (and block 0
-// the large-splat queue length, and the two raster job counters when given),
-// leaving them zero for the next passes.
+// Bitonic network over the 32 KEYS keys of one warp, sorted ascending.
+// Blocked layout: lane l holds elements KEYS l .. KEYS l + KEYS - 1, so the
+// compare-exchanges of partner distance j < KEYS stay inside a lane (no
+// shuffle) and only the log2(32) largest distances of each merge level cross
+// lanes.  Element e is the lower index of its pair when (e & j) == 0 and its
+// block ascends when (e & k) == 0.
+template <int KEYS>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&x)[KEYS], int lane) {
+  constexpr int M = 32 * KEYS;
+#pragma unroll
+  for (int k = 2; k <= M; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < KEYS) {
+#pragma unroll
+        for (int i = 0; i < KEYS; ++i) {
+          if ((i & j) == 0) {
+            const int p = i | j;
+            // (e & k) for e = KEYS lane + i: i's bit when k < KEYS, else the lane's
+            const bool up = k < KEYS ? ((i & k) == 0) : (((lane * KEYS) & k) == 0);
+            const unsigned long long a = x[i], b = x[p];
+            const bool sw = (a > b) == up;
+            x[i] = sw ? b : a;
+            x[p] = sw ? a : b;
+          }
+        }
+      } else {
+        const int d = j / KEYS;  // partner lane distance
+        const bool keep_min = ((lane & d) == 0) == (((lane * KEYS) & k) == 0);
+#pragma unroll
+        for (int i = 0; i < KEYS; ++i) {
+          const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, x[i], d);
+          x[i] = ((x[i] < y) == keep_min) ? x[i] : y;
+        }
+      }
+    }
+  }
+}
+
+// One warp sorts the list of n <= 32 KEYS ids at ids[off ..] by the key
+// (depth bits << 32 | id), padded with all-ones keys to 32 KEYS.
+template <int KEYS>
+__device__ __forceinline__ void warp_sort_list(uint32_t* __restrict__ ids, const uint32_t* __restrict__ zkey,
+                                               uint32_t off, uint32_t n, uint32_t n_items, int lane) {
+  unsigned long long x[KEYS];
+#pragma unroll
+  for (int i = 0; i < KEYS; ++i) {
+    const uint32_t e = (uint32_t)(lane * KEYS + i);
+    x[i] = ~0ull;
+    if (e < n) {
+      const uint32_t g = ids[off + e];
+      x[i] = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
+    }
+  }
+  warp_bitonic<KEYS>(x, lane);
+#pragma unroll
+  for (int i = 0; i < KEYS; ++i) {
+    const uint32_t e = (uint32_t)(lane * KEYS + i);
+    if (e < n) ids[off + e] = (uint32_t)x[i];
+  }
+}
+
+// Per-tile sort of the lists by the 64-bit key (depth bits << 32 | id).  A
+// CTA takes kSortWarps consecutive tiles, one warp each: lists of up to
+// kWarpSortMax entries are sorted by that warp in registers (warp_bitonic,
+// no barriers); longer ones (up to CAP) are queued in the CTA and then
+// sorted one after the other by the whole CTA with a bitonic network in
+// shared memory.  The last binning kernel: it also zeroes each tile's counter
+// (and block 0 the large-splat queue length, and the two raster job counters
+// when given), leaving them zero for the next passes.
 template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t* __restrict__ offsets,
                                                                  uint32_t* __restrict__ counts,
                                                                  uint32_t* __restrict__ ids,
                                                                  const uint32_t* __restrict__ zkey,
-                                                                 uint2* __restrict__ ranges, uint32_t capacity,
-                                                                 uint32_t* __restrict__ overflow,
+                                                                 uint2* __restrict__ ranges, uint32_t n_tiles,
+                                                                 uint32_t capacity, uint32_t* __restrict__ overflow,
                                                                  uint32_t* __restrict__ big_len,
                                                                  uint32_t* __restrict__ raster_work,
                                                                  uint32_t n_items) {
   pdl_enter();
   __shared__ unsigned long long s[CAP];
-  const int t = blockIdx.x;
-  const uint32_t off = offsets[t], n = counts[t];
-  __syncthreads();  // every thread has read counts[t]
+  __shared__ uint2 s_long[kSortWarps];  // (offset, length) of the CTA's lists longer than kWarpSortMax
+  __shared__ uint32_t s_nlong;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    counts[t] = 0u;
-    if (t == 0) {
+    s_nlong = 0u;
+    if (blockIdx.x == 0) {
       *big_len = 0u;
       if (raster_work) raster_work[0] = raster_work[1] = 0u;  // the raster passes' job counters
     }
   }
-  const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
-  if (threadIdx.x == 0) ranges[t] = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
-  if (n <= 1 || !fits) return;
-  if (n > (uint32_t)CAP) {
-    if (threadIdx.x == 0) {
-      atomicOr(overflow, 2u);
-      ranges[t] = make_uint2(0u, 0u);
-    }
-    return;
-  }
-  if (n <= 2 * kSortThreads) {
-    // bitonic network in registers: thread t holds keys 2t and 2t + 1;
-    // partners within a warp are exchanged by shuffles, across warps through
-    // shared memory
-    uint32_t m = 2;
-    while (m < n) m <<= 1;
-    const uint32_t e0 = 2 * threadIdx.x;
-    unsigned long long x0 = ~0ull, x1 = ~0ull;
-    if (e0 < n) {
-      const uint32_t g = ids[off + e0];
-      x0 = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
-    }
-    if (e0 + 1 < n) {
-      const uint32_t g = ids[off + e0 + 1];
-      x1 = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
-    }
-    const bool live = e0 < m;  // threads beyond m only keep padding
-    // Only the warps holding keys below m run the network (64 keys per
-    // warp); the others leave, and the shared-memory steps synchronise the
-    // remaining warps with a named barrier sized to them.
-    const uint32_t live_threads = m >= 64 ? m / 2 : 32u;
-    if (threadIdx.x >= live_threads) return;
-    for (uint32_t k = 2; k <= m; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        if (j == 1) {
-          const bool up = (e0 & k) == 0;
-          if ((x0 > x1) == up) {
-            const unsigned long long tmp = x0;
-            x0 = x1;
-            x1 = tmp;
-          }
-        } else if (j <= 32) {
-          const int d = (int)(j >> 1);  // partner lane distance
-          const unsigned long long y0 = __shfl_xor_sync(0xFFFFFFFFu, x0, d);
-          const unsigned long long y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, d);
-          const bool lower = (e0 & j) == 0;   // this element is the lower index of the pair
-          const bool up = (e0 & k) == 0;      // ascending block
-          const bool keep_min = lower == up;
-          x0 = keep_min ? (x0 < y0 ? x0 : y0) : (x0 > y0 ? x0 : y0);
-          x1 = keep_min ? (x1 < y1 ? x1 : y1) : (x1 > y1 ? x1 : y1);
-        } else {
-          asm volatile("bar.sync 1, %0;" ::"r"(live_threads) : "memory");
-          if (live) {
-            s[e0] = x0;
-            s[e0 + 1] = x1;
-          }
-          asm volatile("bar.sync 1, %0;" ::"r"(live_threads) : "memory");
-          if (live) {
-            const unsigned long long y0 = s[e0 ^ j], y1 = s[(e0 + 1) ^ j];
-            const bool lower = (e0 & j) == 0;
-            const bool up = (e0 & k) == 0;
-            const bool keep_min = lower == up;
-            x0 = keep_min ? (x0 < y0 ? x0 : y0) : (x0 > y0 ? x0 : y0);
-            x1 = keep_min ? (x1 < y1 ? x1 : y1) : (x1 > y1 ? x1 : y1);
-          }
-        }
+  __syncthreads();
+  const uint32_t t = blockIdx.x * kSortWarps + warp;
+  if (t < n_tiles) {
+    const uint32_t off = offsets[t], n = counts[t];
+    __syncwarp();  // every lane has read counts[t]
+    const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
+    if (lane == 0) {
+      counts[t] = 0u;
+      uint2 rg = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
+      if (fits && n > (uint32_t)CAP) {
+        atomicOr(overflow, 2u);
+        rg = make_uint2(0u, 0u);
+      } else if (fits && n > (uint32_t)kWarpSortMax) {
+        s_long[atomicAdd(&s_nlong, 1u)] = make_uint2(off, n);
       }
+      ranges[t] = rg;
     }
-    if (e0 < n) ids[off + e0] = (uint32_t)x0;
-    if (e0 + 1 < n) ids[off + e0 + 1] = (uint32_t)x1;
-    return;
-  }
-  uint32_t m = 2;
-  while (m < n) m <<= 1;
-  for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
-    unsigned long long key = ~0ull;
-    if (i < n) {
-      const uint32_t g = ids[off + i];
-      key = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
+    if (fits && n > 1 && n <= (uint32_t)kWarpSortMax) {
+      if (n <= 32) warp_sort_list<1>(ids, zkey, off, n, n_items, lane);
+      else if (n <= 64) warp_sort_list<2>(ids, zkey, off, n, n_items, lane);
+      else if (n <= 128) warp_sort_list<4>(ids, zkey, off, n, n_items, lane);
+      else if (n <= 256) warp_sort_list<8>(ids, zkey, off, n, n_items, lane);
+      else warp_sort_list<16>(ids, zkey, off, n, n_items, lane);
     }
-    s[i] = key;
   }
   __syncthreads();
-  for (uint32_t k = 2; k <= m; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
-        const uint32_t ixj = i ^ j;
-        if (ixj > i) {
-          const unsigned long long a = s[i], b = s[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s[i] = b;
-            s[ixj] = a;
+  const uint32_t n_long = s_nlong;
+  for (uint32_t q = 0; q < n_long; ++q) {
+    const uint32_t off = s_long[q].x, n = s_long[q].y;
+    uint32_t m = 2;
+    while (m < n) m <<= 1;
+    for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
+      unsigned long long key = ~0ull;
+      if (i < n) {
+        const uint32_t g = ids[off + i];
+        key = in_bounds(g < n_items) ? ((unsigned long long)zkey[g] << 32) | g : ~0ull;
+      }
+      s[i] = key;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = threadIdx.x; i < m; i += kSortThreads) {
+          const uint32_t ixj = i ^ j;
+          if (ixj > i) {
+            const unsigned long long a = s[i], b = s[ixj];
+            const bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              s[i] = b;
+              s[ixj] = a;
+            }
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
+    for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) ids[off + i] = (uint32_t)s[i];
+    __syncthreads();  // s is reused by the next long list
   }
-  for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) ids[off + i] = (uint32_t)s[i];
 }
 
 int bin_grid(int n, int num_sms) {
@@ -555,8 +583,10 @@ void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches
 }
 
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
-  launch_pdl(tile_sort_kernel<kTileSortCap>, a.n_tiles, kSortThreads, 0, s, a.offsets, a.counts, a.ids, a.zkey,
-             a.ranges, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n);
+  const int grid = (a.n_tiles + kSortWarps - 1) / kSortWarps;
+  launch_pdl(tile_sort_kernel<kTileSortCap>, grid, kSortThreads, 0, s, a.offsets, a.counts, a.ids, a.zkey,
+             a.ranges, (uint32_t)a.n_tiles, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len),
+             a.raster_work, (uint32_t)a.n);
   if (launches) *launches += 1;
 }
 

@@ -93,3 +93,25 @@ def test_long_tile_lists_take_the_radix_fallback(ctx):
     np.testing.assert_array_equal(keys, rk)
     np.testing.assert_array_equal(ids, ri)
     np.testing.assert_array_equal(ranges, rr)
+
+
+@pytest.mark.parametrize("L", [2, 3, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 1000, 4096])
+def test_list_lengths_of_every_sort_path(ctx, L):
+    """Lists of exactly L entries in tile 0 and L // 2 + 1 in tile 1 of a
+    two-tile image: every register width of the per-warp sort (up to 32,
+    64, 128, 256, 512 entries), the CTA-wide sort beyond 512 and its limit
+    of 4096; depths drawn from few values so that ties are broken by id."""
+    rng = np.random.default_rng(L)
+    n0, n1 = L, L // 2 + 1
+    m = np.concatenate([np.stack([rng.uniform(2, 14, n0), rng.uniform(2, 14, n0)], 1),
+                        np.stack([rng.uniform(18, 30, n1), rng.uniform(2, 14, n1)], 1)]).astype(np.float32)
+    e = np.full((n0 + n1, 2), 1.5, np.float32)  # stays inside its tile
+    z = (rng.integers(1, 9, n0 + n1) * 0.5).astype(np.float32)
+    perm = rng.permutation(n0 + n1)  # ids of the two tiles interleaved
+    m, e, z = m[perm], e[perm], z[perm]
+    keys, ids, ranges = _run(ctx, m, e, z, 32, 16, 16, 16)
+    rk, ri, rr = binning.bin_tiles(m, e, z, 32, 16, 16, 16)
+    assert (rr[:, 1] - rr[:, 0]).tolist() == [n0, n1]
+    np.testing.assert_array_equal(keys, rk)
+    np.testing.assert_array_equal(ids, ri)
+    np.testing.assert_array_equal(ranges, rr)
