@@ -102,6 +102,86 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int kFwdThreads = 128;
 
+// 16-byte asynchronous copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+// Stages len floats from src (4-byte aligned, sh = (address / 4) mod 4) to
+// dst[sh .. sh + len): 4-byte copies up to the first 16-byte boundary and
+// after the last, 16-byte copies in between (dst 16-byte aligned).
+__device__ __forceinline__ void stage_slice16(float* dst, const float* src, int len, int sh, int t, int nthreads) {
+  const int head = min((4 - sh) & 3, len);
+  const int nvec = (len - head) >> 2;
+  const int tail0 = head + 4 * nvec;
+  if (t < head) cp_async4(dst + sh + t, src + t);
+  for (int c = t; c < nvec; c += nthreads) cp_async16(dst + sh + head + 4 * c, src + head + 4 * c);
+  if (t < len - tail0) cp_async4(dst + sh + tail0 + t, src + tail0 + t);
+}
+
+// tiles a block's shared counters cover (the bounding box of its rectangles)
+constexpr int kCountBox = 1024;
+
+// Adds the tiles of the block's rectangles [x0, x1) x [y0, y1) of one view
+// (those of at most kBigTiles tiles: ns = their tile count, 0 for the others
+// and for threads without an item) to the global per-tile counters.  When
+// the block's rectangles lie in a box of at most kCountBox tiles they are
+// counted in shared memory (s_cnt) first and each touched tile's counter
+// gets one atomic add; otherwise each (item, tile) pair adds 1 directly.
+// Called by every thread of the block (it synchronises the block).
+__device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts, uint32_t tile_base, int tiles_x,
+                                                  int x0, int y0, int x1, int y1, uint32_t ns,
+                                                  uint32_t* __restrict__ s_cnt, int* __restrict__ s_box) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int W = kFwdThreads / 32;
+  unsigned bx0 = ns ? (unsigned)x0 : 0xFFFFu, by0 = ns ? (unsigned)y0 : 0xFFFFu;
+  unsigned bx1 = ns ? (unsigned)x1 : 0u, by1 = ns ? (unsigned)y1 : 0u;
+  bx0 = __reduce_min_sync(0xFFFFFFFFu, bx0);
+  by0 = __reduce_min_sync(0xFFFFFFFFu, by0);
+  bx1 = __reduce_max_sync(0xFFFFFFFFu, bx1);
+  by1 = __reduce_max_sync(0xFFFFFFFFu, by1);
+  if (lane == 0) {
+    s_box[4 * warp] = (int)bx0;
+    s_box[4 * warp + 1] = (int)by0;
+    s_box[4 * warp + 2] = (int)bx1;
+    s_box[4 * warp + 3] = (int)by1;
+  }
+  __syncthreads();  // also: every thread is done with what s_cnt held before
+  int X0 = s_box[0], Y0 = s_box[1], X1 = s_box[2], Y1 = s_box[3];
+#pragma unroll
+  for (int w = 1; w < W; ++w) {
+    X0 = min(X0, s_box[4 * w]);
+    Y0 = min(Y0, s_box[4 * w + 1]);
+    X1 = max(X1, s_box[4 * w + 2]);
+    Y1 = max(Y1, s_box[4 * w + 3]);
+  }
+  const int bw = X1 - X0, bh = Y1 - Y0;
+  const int w = x1 - x0;
+  if (bw <= 0 || bh <= 0 || bw * bh > kCountBox) {  // block-uniform
+    for (uint32_t k = 0; k < ns; ++k)
+      atomicAdd(&counts[tile_base + (uint32_t)(y0 + (int)k / w) * (uint32_t)tiles_x + (uint32_t)(x0 + (int)k % w)], 1u);
+    __syncthreads();  // s_box is read before the next call rewrites it
+    return;
+  }
+  const int area = bw * bh;
+  for (int c = threadIdx.x; c < area; c += kFwdThreads) s_cnt[c] = 0u;
+  __syncthreads();
+  int tx = x0, ty = y0;
+  for (uint32_t k = 0; k < ns; ++k) {
+    atomicAdd(&s_cnt[(ty - Y0) * bw + (tx - X0)], 1u);
+    if (++tx == x1) {
+      tx = x0;
+      ++ty;
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < area; c += kFwdThreads) {
+    const uint32_t v = s_cnt[c];
+    if (v) atomicAdd(&counts[tile_base + (uint32_t)(Y0 + c / bw) * (uint32_t)tiles_x + (uint32_t)(X0 + c % bw)], v);
+  }
+  __syncthreads();  // s_cnt and s_box are reused by the next view
+}
+
 // One thread per Gaussian: its parameters are read once and projected into
 // every view of the batch (item v * n + i for view v).
 template <int D>
@@ -138,9 +218,11 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   }
   __syncthreads();
   const int i = base + threadIdx.x;
-  const unsigned live = __ballot_sync(0xFFFFFFFFu, i < a.n);  // lanes that reach the counting loops
-  if (i >= a.n) return;
-  const int t = threadIdx.x;
+  const bool valid = i < a.n;  // threads without an item stay for the block's tile counting
+  __shared__ int s_box[4 * (kFwdThreads / 32)];
+  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(s_p);  // s_p is in registers before it is reused
+  static_assert(kFwdThreads * 11 >= kCountBox, "the counters fit in the staging buffer");
+  const int t = valid ? threadIdx.x : 0;
   const float px = s_p[3 * t], py = s_p[3 * t + 1], pz = s_p[3 * t + 2];
   const float ls[3] = {s_p[3 * kFwdThreads + 3 * t], s_p[3 * kFwdThreads + 3 * t + 1],
                        s_p[3 * kFwdThreads + 3 * t + 2]};
@@ -158,6 +240,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
     const CamView& cv = a.cv[v];
     const size_t it = (size_t)v * a.n + i;
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (valid) {
     // camera-space position and pixel mean in double-float (the float32 error
     // of W p + t alone would move mu by ~1e-3 px at 1-2 m)
     df Z = df_dot3_plus(cv.R[6], cv.R[7], cv.R[8], px, py, pz, cv.t[2]);
@@ -207,19 +290,12 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
       feat[3 * it + 1] = make_float4(g.i0, g.k, g.i1, log2o);
       feat[3 * it + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
     }
+    }
     // tile counts of the small rectangles (the binning expands the queued large ones)
     if (a.counts) {
-      const uint32_t w = (uint32_t)(x1 - x0);
-      const uint32_t ns = w * (uint32_t)(y1 - y0) <= kBigTiles ? w * (uint32_t)(y1 - y0) : 0u;
-      const uint32_t rounds = __reduce_max_sync(live, ns);
-      for (uint32_t k = 0; k < rounds; ++k) {
-        const bool act = k < ns;
-        const unsigned am = __ballot_sync(live, act);
-        if (act) {
-          const uint32_t t = a.tile_base[v] + (uint32_t)(y0 + k / w) * (uint32_t)a.tiles_x[v] + (uint32_t)x0 + k % w;
-          warp_agg_inc(a.counts, t, am);
-        }
-      }
+      const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
+      block_count_tiles(a.counts, a.tile_base[v], a.tiles_x[v], x0, y0, x1, y1, nt <= kBigTiles ? nt : 0u, s_cnt,
+                        s_box);
     }
   }
 }
@@ -559,7 +635,7 @@ struct FusedSmem {
   static constexpr int B = fused_threads<false>();
   float p[B * 11], m[B * 11], v[B * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
   float g[B * 11];                        // gradients, same layout
-  float sp[B * RS], sm[B * NS], sv[B * NS];
+  float sp[B * RS], sm[B * NS + 4], sv[B * NS + 4];  // SH moments at their slice's offset within 16 B
   float Y[B][K + 1];
   float graw[B][4];
 };
@@ -574,7 +650,7 @@ struct FusedSmemMulti {
   float g[B * 11];
   float sp[B * RS];  // SH parameters, one row per Gaussian
   float gs[B * RS];  // SH gradients summed over the views, same rows
-  float sm[B * NS], sv[B * NS];  // SH moments
+  float sm[B * NS + 4], sv[B * NS + 4];  // SH moments
 };
 
 template <int D, bool MULTI>
@@ -613,10 +689,11 @@ __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kerne
       cp_async4(&sm.m[so[r] + e], M + g0[r] + e);
       cp_async4(&sm.v[so[r] + e], V + g0[r] + e);
     }
-  for (int e = t; e < cnt * NS; e += B) {
-    cp_async4(&sm.sm[e], M + gsh + e);
-    cp_async4(&sm.sv[e], V + gsh + e);
-  }
+  // SH moments: 16-byte copies over the 16-byte aligned interior of each
+  // slice, staged at the slice's own offset within 16 bytes (shM, shV)
+  const int shM = (int)(((uintptr_t)(M + gsh) >> 2) & 3u), shV = (int)(((uintptr_t)(V + gsh) >> 2) & 3u);
+  stage_slice16(sm.sm, M + gsh, cnt * NS, shM, t, B);
+  stage_slice16(sm.sv, V + gsh, cnt * NS, shV, t, B);
   cp_async_commit();
   float4 G0 = make_float4(0.f, 0.f, 0.f, 0.f), G1 = G0, G2 = G0;
   if (t < cnt) {
@@ -722,7 +799,7 @@ __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kerne
         const float lr = k == 0 ? ad.lr[4] : ad.lr[5];
         for (int gi = 0; gi < cnt; ++gi) {
           const int e = gi * NS + rr;
-          float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e];
+          float p = sm.sp[gi * RS + rr], m = sm.sm[shM + e], v = sm.sv[shV + e];
           float g;
           if constexpr (MULTI)
             g = sm.gs[gi * RS + rr];
@@ -741,7 +818,7 @@ __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kerne
       const int gi = e / NS, rr = e - gi * NS;
       const int k = rr / 3, c = rr - 3 * k;
       const int64_t f = gsh + e;
-      float p = sm.sp[gi * RS + rr], m = sm.sm[e], v = sm.sv[e], g;
+      float p = sm.sp[gi * RS + rr], m = sm.sm[shM + e], v = sm.sv[shV + e], g;
       if constexpr (MULTI)
         g = sm.gs[gi * RS + rr];
       else
