@@ -475,6 +475,10 @@ __device__ __forceinline__ PixQ pixel_q(const float4& a, const float4& bb, float
 
 // The rest of the back-to-front step, without branches: a lane whose pixel
 // does not take part runs it with weight 0 and leaves T, U and v unchanged.
+// FIRST: the entry's first pixel row of the lane writes the ten sums instead
+// of adding to them (no zeroing of v per entry; a zero term may then be
+// stored as -0, which adds like +0).
+template <bool FIRST>
 __device__ __forceinline__ void bwd_body(const PixQ& e, const float4& bb, const float4& c, const RasterParams& rp,
                                          float& T, float& U, float dC0, float dC1, float dC2, float dD, float dA_T,
                                          float (&v)[10]) {
@@ -483,10 +487,10 @@ __device__ __forceinline__ void bwd_body(const PixQ& e, const float4& bb, const 
   const float inv1m = rcp_approx(1.f - al);  // 1 - alpha in [0.01, 1)
   const float Ti = T * inv1m;  // transmittance in front of this Gaussian
   const float w = e.pass ? al * Ti : 0.f;
-  v[7] = fmaf(w, dC0, v[7]);
-  v[8] = fmaf(w, dC1, v[8]);
-  v[9] = fmaf(w, dC2, v[9]);
-  v[6] = fmaf(w, dD, v[6]);
+  v[7] = FIRST ? w * dC0 : fmaf(w, dC0, v[7]);
+  v[8] = FIRST ? w * dC1 : fmaf(w, dC1, v[8]);
+  v[9] = FIRST ? w * dC2 : fmaf(w, dC2, v[9]);
+  v[6] = FIRST ? w * dD : fmaf(w, dD, v[6]);
   const float cdot = c.x * dC0 + c.y * dC1 + c.z * dC2 + bb.z * dD;
   // d/d alpha_i: colour/depth T_i c_i - (sum behind)/(1 - alpha_i); alpha image + T_final/(1 - alpha_i)
   const float g_alpha = Ti * cdot - (U - dA_T) * inv1m;
@@ -494,12 +498,12 @@ __device__ __forceinline__ void bwd_body(const PixQ& e, const float4& bb, const 
   T = e.pass ? Ti : T;
   const float ga = (e.pass && araw <= rp.alpha_max) ? g_alpha * araw : 0.f;  // the 0.99 clamp has zero gradient
   const float gt0 = ga * e.t0, gt1 = ga * e.t1;
-  v[0] += gt0;
-  v[1] += gt1;
-  v[2] = fmaf(gt0, e.dx, v[2]);
-  v[3] = fmaf(gt1, e.dx, v[3]);
-  v[4] = fmaf(gt1, e.wq, v[4]);
-  v[5] += ga;
+  v[0] = FIRST ? gt0 : v[0] + gt0;
+  v[1] = FIRST ? gt1 : v[1] + gt1;
+  v[2] = FIRST ? gt0 * e.dx : fmaf(gt0, e.dx, v[2]);
+  v[3] = FIRST ? gt1 * e.dx : fmaf(gt1, e.dx, v[3]);
+  v[4] = FIRST ? gt1 * e.wq : fmaf(gt1, e.wq, v[4]);
+  v[5] = FIRST ? ga : v[5] + ga;
 }
 
 // Backward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
@@ -604,9 +608,7 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
       const float4 a = buf[j].a;
       const float4 bb = buf[j].b;
       const float4 cc = buf[j].c;
-      float v[10];
-#pragma unroll
-      for (int k = 0; k < 10; ++k) v[k] = 0.f;
+      float v[10];  // written by the first row's step
       const unsigned halves = __float_as_uint(cc.w);
       // both pixel rows' exponents first, then the rows' steps as straight-line
       // code (independent chains); skipped when no lane of the warp takes part
@@ -617,18 +619,18 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
         const PixQ e1 = pixel_q(a, bb, plx, ply1, idx < last1);
         contrib = e0.pass || e1.pass;
         if (!__any_sync(kFull, contrib)) continue;
-        bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
-        bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+        bwd_body<true>(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+        bwd_body<false>(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
       } else if (halves == 1u) {
         const PixQ e0 = pixel_q(a, bb, plx, ply0, idx < last0);
         contrib = e0.pass;
         if (!__any_sync(kFull, contrib)) continue;
-        bwd_body(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
+        bwd_body<true>(e0, bb, cc, rp, T0, U0, c00, c01, c02, d0, dAT0, v);
       } else {
         const PixQ e1 = pixel_q(a, bb, plx, ply1, idx < last1);
         contrib = e1.pass;
         if (!__any_sync(kFull, contrib)) continue;
-        bwd_body(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
+        bwd_body<true>(e1, bb, cc, rp, T1, U1, c10, c11, c12, d1, dAT1, v);
       }
       const unsigned m = __ballot_sync(kFull, contrib);
       if (m == 0) continue;

@@ -131,9 +131,47 @@ __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_co
                        });
 }
 
-// Length class of a tile list for the visit order: 0 for an empty list,
-// else 1 + floor(log2(length)).
-__device__ __forceinline__ int length_class(uint32_t c) { return c ? 32 - __clz(c) : 0; }
+// Length class of a tile list for the visit order, four per octave: 0 for
+// an empty list, else 4 floor(log2 c) + (the two bits after c's leading one)
+// + 1, so classes grow with the length and tiles within 19% of each other's
+// length share one.  kLenClasses classes (kLenClasses is also the "no tile"
+// sentinel).
+constexpr int kLenClasses = 129;
+__device__ __forceinline__ int length_class(uint32_t c) {
+  if (!c) return 0;
+  const int lead = 31 - __clz(c);
+  const int frac = lead >= 2 ? (int)((c >> (lead - 2)) & 3u) : (int)((c << (2 - lead)) & 3u);
+  return 4 * lead + frac + 1;
+}
+
+// Turns the class counts cls[0 .. kLenClasses) into the first visit position
+// of each class, longest class first (cls[c] = sum of the counts of the
+// classes above c); run by one warp.
+__device__ __forceinline__ void class_starts_desc(uint32_t* cls) {
+  constexpr int PER = (kLenClasses + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  // lane l takes classes kLenClasses - 1 - (PER l .. PER l + PER - 1)
+  uint32_t v[PER], sum = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int c = kLenClasses - 1 - (PER * lane + j);
+    v[j] = c >= 0 ? cls[c] : 0u;
+    sum += v[j];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  uint32_t run = incl - sum;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int c = kLenClasses - 1 - (PER * lane + j);
+    if (c >= 0) cls[c] = run;
+    run += v[j];
+  }
+}
 
 // offsets = exclusive scan of counts (clamped to 32 bits), cursors = offsets;
 // stats[0] = total pairs, stats[1] = longest list; n_pairs = min(total, capacity).
@@ -185,37 +223,30 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
     *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
   }
   if (!order) return;
-  // counting sort of the tiles by length class (33 classes), descending;
-  // lanes of a warp with the same class are aggregated into one atomic
-  __shared__ uint32_t s_cls[33];
+  // counting sort of the tiles by length class, descending; lanes of a warp
+  // with the same class are aggregated into one atomic
+  __shared__ uint32_t s_cls[kLenClasses];
   const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 33) s_cls[threadIdx.x] = 0;
+  if (threadIdx.x < kLenClasses) s_cls[threadIdx.x] = 0;
   __syncthreads();
   for (int i0 = 0; i0 < T; i0 += kScanThreads) {
     const int i = i0 + threadIdx.x;
-    const int c = i < T ? length_class(counts[i]) : 33;
+    const int c = i < T ? length_class(counts[i]) : kLenClasses;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
-    if (c < 33 && lane == __ffs(peers) - 1) atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
+    if (c < kLenClasses && lane == __ffs(peers) - 1) atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t run = 0;
-    for (int c = 32; c >= 0; --c) {
-      const uint32_t k = s_cls[c];
-      s_cls[c] = run;
-      run += k;
-    }
-  }
+  if (threadIdx.x < 32) class_starts_desc(s_cls);
   __syncthreads();
   for (int i0 = 0; i0 < T; i0 += kScanThreads) {
     const int i = i0 + threadIdx.x;
-    const int c = i < T ? length_class(counts[i]) : 33;
+    const int c = i < T ? length_class(counts[i]) : kLenClasses;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, c);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (c < 33 && lane == leader) base = atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
+    if (c < kLenClasses && lane == leader) base = atomicAdd(&s_cls[c], (uint32_t)__popc(peers));
     base = __shfl_sync(peers, base, leader);
-    if (c < 33) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+    if (c < kLenClasses) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 
@@ -227,18 +258,18 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(int T, const ui
 //   down: block b adds up the earlier blocks' sums and class histograms (in
 //         block order) for its bases, then writes offsets, cursors and the
 //         visit order of its tiles.
-// aux per block: {sum lo, sum hi, max, hist[33]}; aux_tail: class starts[33].
+// aux per block: {sum lo, sum hi, max, hist[kLenClasses]}; aux_tail: class starts[kLenClasses].
 constexpr int kScanTiles = 1024;
-constexpr int kScanAux = 36;
+constexpr int kScanAux = 3 + kLenClasses;
 
 __global__ void __launch_bounds__(256) tile_scan_up_kernel(int T, const uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ aux) {
   pdl_enter();
-  __shared__ uint32_t s_hist[33];
+  __shared__ uint32_t s_hist[kLenClasses];
   __shared__ unsigned long long s_sum[8];
   __shared__ uint32_t s_max[8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x < 33) s_hist[threadIdx.x] = 0;
+  if (threadIdx.x < kLenClasses) s_hist[threadIdx.x] = 0;
   __syncthreads();
   unsigned long long sum = 0;
   uint32_t mx = 0;
@@ -249,9 +280,9 @@ __global__ void __launch_bounds__(256) tile_scan_up_kernel(int T, const uint32_t
     const uint32_t c = i < T ? counts[i] : 0u;
     sum += c;
     mx = max(mx, c);
-    const int cls = i < T ? length_class(c) : 33;
+    const int cls = i < T ? length_class(c) : kLenClasses;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, cls);
-    if (cls < 33 && lane == __ffs(peers) - 1) atomicAdd(&s_hist[cls], (uint32_t)__popc(peers));
+    if (cls < kLenClasses && lane == __ffs(peers) - 1) atomicAdd(&s_hist[cls], (uint32_t)__popc(peers));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -275,7 +306,7 @@ __global__ void __launch_bounds__(256) tile_scan_up_kernel(int T, const uint32_t
     out[1] = (uint32_t)(t >> 32);
     out[2] = m;
   }
-  if (threadIdx.x < 33) out[3 + threadIdx.x] = s_hist[threadIdx.x];
+  if (threadIdx.x < kLenClasses) out[3 + threadIdx.x] = s_hist[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(64) tile_scan_mid_kernel(int nb, const uint32_t* __restrict__ aux,
@@ -283,11 +314,11 @@ __global__ void __launch_bounds__(64) tile_scan_mid_kernel(int nb, const uint32_
                                                            uint32_t* __restrict__ n_pairs,
                                                            unsigned long long* __restrict__ stats) {
   pdl_enter();
-  __shared__ uint32_t s_tot[33];
-  if (threadIdx.x < 33) {
+  __shared__ uint32_t s_tot[kLenClasses];
+  for (int c = threadIdx.x; c < kLenClasses; c += blockDim.x) {
     uint32_t t = 0;
-    for (int b = 0; b < nb; ++b) t += aux[(size_t)kScanAux * b + 3 + threadIdx.x];
-    s_tot[threadIdx.x] = t;
+    for (int b = 0; b < nb; ++b) t += aux[(size_t)kScanAux * b + 3 + c];
+    s_tot[c] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -301,11 +332,11 @@ __global__ void __launch_bounds__(64) tile_scan_mid_kernel(int nb, const uint32_
     stats[0] = tot;
     stats[1] = m;
     *n_pairs = (uint32_t)(tot < (unsigned long long)capacity ? tot : (unsigned long long)capacity);
-    uint32_t run = 0;
-    for (int c = 32; c >= 0; --c) {  // longest class first
-      aux_tail[c] = run;
-      run += s_tot[c];
-    }
+  }
+  if (threadIdx.x < 32) {  // longest class first
+    class_starts_desc(s_tot);
+    __syncwarp();
+    for (int c = threadIdx.x; c < kLenClasses; c += 32) aux_tail[c] = s_tot[c];
   }
 }
 
@@ -319,13 +350,14 @@ __global__ void __launch_bounds__(256) tile_scan_down_kernel(int T, const uint32
   constexpr int PER = kScanTiles / 256;  // consecutive tiles per thread
   __shared__ unsigned long long s_scan[256];
   __shared__ unsigned long long s_base;
-  __shared__ uint32_t s_cls[33];
+  __shared__ uint32_t s_cls[kLenClasses];
   const int b = blockIdx.x, lane = threadIdx.x & 31;
-  if (threadIdx.x < 33) {  // start of this block's tiles within each length class
+  static_assert(kLenClasses < 255, "thread 255 sums the bases");
+  if (threadIdx.x < kLenClasses) {  // start of this block's tiles within each length class
     uint32_t o = aux_tail[threadIdx.x];
     for (int k = 0; k < b; ++k) o += aux[(size_t)kScanAux * k + 3 + threadIdx.x];
     s_cls[threadIdx.x] = o;
-  } else if (threadIdx.x == 64) {
+  } else if (threadIdx.x == 255) {
     unsigned long long o = 0;
     for (int k = 0; k < b; ++k) {
       const uint32_t* a = aux + (size_t)kScanAux * k;
@@ -363,13 +395,13 @@ __global__ void __launch_bounds__(256) tile_scan_down_kernel(int T, const uint32
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int i = i0 + j;
-    const int cls = i < T ? length_class(c[j]) : 33;
+    const int cls = i < T ? length_class(c[j]) : kLenClasses;
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, cls);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
-    if (cls < 33 && lane == leader) base = atomicAdd(&s_cls[cls], (uint32_t)__popc(peers));
+    if (cls < kLenClasses && lane == leader) base = atomicAdd(&s_cls[cls], (uint32_t)__popc(peers));
     base = __shfl_sync(peers, base, leader);
-    if (cls < 33) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
+    if (cls < kLenClasses) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
   }
 }
 
