@@ -915,63 +915,17 @@ def oracle_iteration(w, tiles=None):
     return t1 - t0, t2 - t1, t3 - t2, int(out["n_contrib"].sum())
 
 
-def oracle_tile_elements(w):
-    """Per 16 x 16 tile: pixels x Gaussians whose 3-sigma box meets it (the
-    oracle's compositing work, which its time follows)."""
-    import numpy as np
+def oracle_whole_iteration(w):
+    """One whole iteration of the oracle on the single-view workload (every
+    pixel, every Gaussian, Adam on every parameter), the same procedure as
+    the reference arm's steps.  Returns (seconds, description, threads)."""
     import torch
-    v, n_tiles, Rm, t, R = _oracle_setup(w)
-    with torch.no_grad():
-        pr = R.project(R.to_tensors({k: np.asarray(w.params[k], np.float64) for k in R.PARAM_NAMES}), w.sh_degree,
-                       v.cam, Rm, t)
-    mu = pr["mean2d"].numpy()
-    cov = pr["cov2d"].numpy()
-    ex = np.sqrt(9.0 * (1 + 1e-3) * cov[:, 0, 0])  # the oracle's selection box (q <= 9 (1 + 1e-3))
-    ey = np.sqrt(9.0 * (1 + 1e-3) * cov[:, 1, 1])
-    W, H, tx, ty = v.cam.width, v.cam.height, -(-v.cam.width // 16), -(-v.cam.height // 16)
-    # tile k spans the pixel centres [16 k + 0.5, min(16 k + 15.5, W - 0.5)]; a Gaussian meets the tiles
-    # whose centre span its box mu +- e reaches (a 2D difference array counts them per tile)
-    cx0 = np.maximum(np.ceil((mu[:, 0] - ex - 15.5) / 16), 0).astype(np.int64)
-    cx1 = np.minimum(np.floor((mu[:, 0] + ex - 0.5) / 16), tx - 1).astype(np.int64)
-    cy0 = np.maximum(np.ceil((mu[:, 1] - ey - 15.5) / 16), 0).astype(np.int64)
-    cy1 = np.minimum(np.floor((mu[:, 1] + ey - 0.5) / 16), ty - 1).astype(np.int64)
-    ok = (cx1 >= cx0) & (cy1 >= cy0) & (mu[:, 0] - ex <= W - 0.5) & (mu[:, 1] - ey <= H - 0.5)
-    d = np.zeros((ty + 1, tx + 1), np.int64)
-    np.add.at(d, (cy0[ok], cx0[ok]), 1)
-    np.add.at(d, (cy0[ok], cx1[ok] + 1), -1)
-    np.add.at(d, (cy1[ok] + 1, cx0[ok]), -1)
-    np.add.at(d, (cy1[ok] + 1, cx1[ok] + 1), 1)
-    cnt = d.cumsum(0).cumsum(1)[:ty, :tx].ravel()
-    npx = np.array([len(R.tile_pixels(v.cam, [k])) for k in range(n_tiles)])
-    return cnt * npx
-
-
-def oracle_sample(w, n_tiles_sample, seed=0):
-    """Bounded sample of one oracle iteration: ``n_tiles_sample`` uniformly
-    random 16 x 16 tiles timed whole (compositing forward + backward with all
-    their Gaussians), the compositing part scaled to all tiles (an unbiased
-    estimate of the whole image's), plus the projection of every Gaussian
-    and Adam on every parameter, timed whole.  Returns (seconds per
-    iteration, description, threads)."""
-    import numpy as np
-    import torch
-    v, n_tiles, _, _, _ = _oracle_setup(w)
-    elems = oracle_tile_elements(w)
-    rng = np.random.default_rng(seed)
-    pick = rng.choice(n_tiles, min(n_tiles_sample, n_tiles), replace=False)
-    # the projection (of every Gaussian) alone, forward and backward
-    t_proj_f, t_proj_b, _, _ = oracle_iteration(w, tiles=[])
-    t_f, t_b, t_adam, blended = oracle_iteration(w, tiles=pick)
-    frac = float(elems[pick].sum()) / max(float(elems.sum()), 1.0)
-    t_tiles = max(t_f + t_b - t_proj_f - t_proj_b, 0.0)
-    comp = t_tiles * n_tiles / len(pick)  # uniformly sampled tiles: unbiased for the whole image
-    t_iter = t_proj_f + t_proj_b + comp + t_adam
-    desc = (f"{len(pick)} uniformly random 16x16 tiles of the {v.cam.width}x{v.cam.height} view timed whole "
-            f"(compositing forward + L1 loss + backward with all Gaussians meeting them, {t_tiles:.2f} s, "
-            f"{100 * frac:.2f}% of the image's pixel x Gaussian work), extrapolated to all {n_tiles} tiles "
-            f"({comp:.1f} s); projection of all {w.n} Gaussians forward + backward ({t_proj_f + t_proj_b:.2f} s) "
-            f"and float64 Adam on all parameters ({t_adam:.2f} s) timed whole")
-    return t_iter, desc, torch.get_num_threads()
+    t_f, t_b, t_a, blended = oracle_iteration(w)
+    v = w.views[0]
+    desc = (f"one whole iteration: projection and compositing of all {v.cam.width}x{v.cam.height} pixels "
+            f"({blended} blended pairs) {t_f:.2f} s, L1 loss and backward {t_b:.2f} s, float64 Adam on all "
+            f"parameters {t_a:.2f} s")
+    return t_f + t_b + t_a, desc, torch.get_num_threads()
 
 
 def oracle_small_iteration():
@@ -1031,8 +985,6 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--baseline-tiles", type=int, default=256,
-                    help="cpu_baseline: random 16x16 tiles timed whole by the oracle (the rest extrapolated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="single_view",
                     choices=["single_view", "multi_view", "streaming", "scale_stress"],
@@ -1079,7 +1031,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             from synth import workloads
-            t_iter, desc, cores = oracle_sample(workloads.single_view(), args.baseline_tiles)
+            t_iter, desc, cores = oracle_whole_iteration(workloads.single_view())
             out["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": "it/s", "cores": cores, "kind": "oracle",
                                    "sample": desc, "whole_iteration_64x48_500_s": oracle_small_iteration()}
         print(json.dumps(out))
