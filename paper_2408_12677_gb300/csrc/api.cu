@@ -73,6 +73,11 @@ struct gs_ctx {
   float* dl_img = nullptr;    // per pixel: dL/dcolor (3 planes) and the depth residual sign (fused loss)
   float* tile_loss = nullptr;  // per (tile, 8 x 8 block): fused-loss partial sums (3 floats)
   float* d_dscale = nullptr;   // per view: depth-gradient scale of the fused loss
+  uint32_t* d_nvalid = nullptr;  // per view: target depths > 0 seen by the fused-loss forward pass
+  // the training step's loss reduction runs on a side stream beside the
+  // backward pass (fork and join events on the caller's stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // per-frame seeding scratch
   int64_t cap_qt = 0;
   int2* qt_cells[2] = {nullptr, nullptr};
@@ -426,10 +431,10 @@ gs_status bin_and_sort_radix(gs_ctx* c, int n, const TileMap& map, cudaStream_t 
 
 // Counting-scatter binning with per-tile sorts: count, scan (one host read of
 // the totals in sync mode), scatter, sort.  Falls back to the radix path when
-// some tile list is longer than the per-tile sort holds.  small_counted: the
-// projection already counted every item with at most kBigTiles tiles into
-// the (zeroed) tile counters.
-gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, bool small_counted) {
+// some tile list is longer than the per-tile sort holds.  counted: the
+// projection already added every item's tiles to the (zeroed) tile
+// counters.
+gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, bool counted) {
   const int64_t T = (int64_t)map.tile_base[map.views];
   if (c->sync) GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
   TileBinArgs tb;
@@ -452,7 +457,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
   tb.big_queue = c->bigq;
   tb.big_len = c->d_bigmeta;
   tb.order = c->order_tiles ? c->torder : nullptr;
-  tb.small_counted = small_counted;
+  tb.counted = counted;
   tb.scan_aux = c->scan_aux;
   c->st_ordered = false;
   {
@@ -539,6 +544,11 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_nvalid, kMaxViews * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_nvalid, 0, kMaxViews * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bigmeta, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_bigmeta, 0, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
@@ -599,6 +609,10 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->dl_img);
   cudaFree(c->tile_loss);
   cudaFree(c->d_dscale);
+  cudaFree(c->d_nvalid);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->qt_cells[0]);
   cudaFree(c->qt_cells[1]);
   cudaFree(c->qt_leaves);
@@ -850,6 +864,8 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.loss_partials = nullptr;
   ra.w_color = 0.f;
   ra.depth_scale = nullptr;
+  ra.nvalid = nullptr;
+  ra.w_depth = 0.f;
   for (int v = 0; v < kMaxViews; ++v) {
     RasterView& rv = ra.v[v];
     const bool live = v < c->st_views;
@@ -900,7 +916,8 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   ProjectArgs pa = project_args(g, V, cams, views, cfg, L.map, L.tiles_y);
   pa.big_queue = c->bigq;
   pa.big_len = c->d_bigmeta;
-  pa.counts = c->tcount;  // the projection counts the tiles of the small rectangles
+  pa.counts = c->tcount;  // the projection counts every rectangle's tiles
+  pa.nvalid = fl ? c->d_nvalid : nullptr;  // zeroed by the projection for the fused loss's count
   if (!c->counts_zero) {  // else the last per-tile sort left them zero
     // every counter of the allocation, so that a later pass over more tiles
     // also starts from zeros
@@ -938,6 +955,7 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   }
   if (fl) {
     ra.loss_partials = c->tile_loss;
+    ra.nvalid = c->d_nvalid;
     ra.w_color = fl->w_color;
     for (int v = 0; v < V; ++v) {
       const int64_t np = (int64_t)cams[v].width * cams[v].height;
@@ -995,7 +1013,7 @@ gs_status check_bwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_
 // raster backward into the context's per-item gradient records
 gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                           const float* const* dL_ddepth, const float* const* dL_dalpha, cudaStream_t s,
-                          const float* depth_scale = nullptr) {
+                          const float* depth_scale = nullptr, const float* nvalid_w_depth = nullptr) {
   // the records are zero unless a backward pass ran without its consumer (or
   // the buffer is new): then clear the whole buffer once
   if (!c->g2d_zero) GS_CUDA(c, cudaMemsetAsync(c->g2d, 0, sizeof(float4) * 3 * (size_t)c->cap_n, s));
@@ -1003,6 +1021,10 @@ gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* cons
   if (ra.work) ra.work = c->d_bigmeta + 2;
   ra.zero_work = !c->bwd_work_zero;
   ra.depth_scale = depth_scale;
+  if (nvalid_w_depth) {  // the fused loss: dL/dD scale w_depth / (valid target depths) per view
+    ra.nvalid = c->d_nvalid;
+    ra.w_depth = *nvalid_w_depth;
+  }
   for (int v = 0; v < c->st_views; ++v) {
     ra.v[v].dLdc = dL_dcolor[v];
     ra.v[v].dLdd = dL_ddepth[v];
@@ -1054,7 +1076,8 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
                                 const gs_viewmat* views, const gs_raster_cfg* cfg, const float* const* dL_dcolor,
                                 const float* const* dL_ddepth, const float* const* dL_dalpha, float* params,
                                 float* m, float* v, const gs_adam_cfg* adam, int64_t step, float* dL_dpose,
-                                cudaStream_t s, const float* depth_scale = nullptr, bool step_advanced = false) {
+                                cudaStream_t s, const float* depth_scale = nullptr, bool step_advanced = false,
+                                const float* nvalid_w_depth = nullptr, cudaEvent_t before_adam = nullptr) {
   gs_status st;
   if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
@@ -1065,7 +1088,11 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
     return fail(c, GS_ERR_INVALID_ARG, "the Gaussian arrays must be the flat parameter buffer's blocks");
   GS_CUDA(c, cudaSetDevice(c->device));
   if (n == 0) return GS_OK;
-  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s, depth_scale)) != GS_OK) return st;
+  st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s, depth_scale, nvalid_w_depth);
+  // the work the Adam update waits for on another stream (the loss reduction
+  // that advances the device step) joins here, also when the backward failed
+  if (before_adam) GS_CUDA(c, cudaStreamWaitEvent(s, before_adam, 0));
+  if (st != GS_OK) return st;
   const ProjectArgs pa = project_args(g, V, cams, views, cfg, c->st_map, c->st_map.tiles_x);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
@@ -1182,13 +1209,23 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   RasterArgs ra = raster_args(c, cfg);
   ra.loss_partials = c->tile_loss;
   ra.w_color = w_color;
+  // The loss reduction (which also advances the device step counter when
+  // step = 0) runs on the side stream, beside the backward pass: the
+  // backward pass takes its depth scale from the forward pass's count of
+  // valid target depths, and only the Adam update waits for the reduction.
+  GS_CUDA(c, cudaEventRecord(c->ev_fork, s));
+  GS_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
   {
-    // the device step counter (step = 0) is advanced by the loss launch
-    StageTimer t(c, GS_STAGE_LOSS, s);
+    StageTimer t(c, GS_STAGE_LOSS, c->side);
     launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, c->d_bigmeta + 3,
-                               step == 0 ? c->d_step : nullptr, s, &c->launches);
+                               step == 0 ? c->d_step : nullptr, c->side, &c->launches);
   }
-  GS_CHECK_LAUNCH(c, "loss finalize");
+  const cudaError_t le = cudaGetLastError();
+  GS_CUDA(c, cudaEventRecord(c->ev_join, c->side));
+  if (le != cudaSuccess) {
+    GS_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    return cuda_fail(c, le, "loss finalize");
+  }
   const float* dlc[kMaxViews];
   const float* dld[kMaxViews];
   for (int k = 0; k < V; ++k) {
@@ -1197,7 +1234,7 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     dld[k] = c->dl_img + 4 * c->st_pix_base[k] + 3 * np;
   }
   return render_bwd_adam_views(c, g, V, cams, views, cfg, dlc, dld, nullptr, params, m, v, adam, step, nullptr, s,
-                               c->d_dscale, /*step_advanced=*/true);
+                               nullptr, /*step_advanced=*/true, &w_depth, c->ev_join);
 }
 
 }  // namespace

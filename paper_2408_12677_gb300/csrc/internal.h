@@ -45,8 +45,9 @@ struct ProjectArgs {
   CamView cv[kMaxViews];
   int tiles_x[kMaxViews], tiles_y[kMaxViews];
   uint32_t tile_base[kMaxViews];  // first global tile of each view
-  uint32_t* counts;               // per global tile (zeroed, nullable): the projection counts the
-                                  // tiles of items with at most kBigTiles tiles
+  uint32_t* counts;               // per global tile (zeroed, nullable): the projection adds every
+                                  // item's tiles
+  uint32_t* nvalid = nullptr;     // per view (nullable): zeroed by the projection (block 0)
 };
 
 // projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
@@ -137,7 +138,7 @@ struct TileBinArgs {
   const uint32_t* big_queue;  // items with more than kBigTiles tiles
   const uint32_t* big_len;    // queue length (the per-tile sort zeroes it, and the counts, when done)
   uint32_t* order;            // per tile (output, nullable): visit order, longest lists first
-  bool small_counted;         // counts already hold every item with at most kBigTiles tiles (projection)
+  bool counted;               // counts already hold every item's tiles (the projection counted them)
   uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
   uint32_t* raster_work = nullptr;  // nullable: the forward and backward raster job counters, zeroed by the sort
 };
@@ -184,6 +185,12 @@ struct RasterArgs {
   // backward: dL/dD = dLdd * depth_scale[v] when non-null (the scale the
   // fused loss finalises on the device)
   const float* depth_scale;
+  // fused loss: the forward pass adds each warp block's count of valid
+  // target depths to nvalid[v] (exact integers); given to the backward pass,
+  // dL/dD = dLdd * w_depth / max(nvalid[v], 1), the same scale the loss
+  // reduction computes (it takes precedence over depth_scale)
+  uint32_t* nvalid;
+  float w_depth;
   RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);

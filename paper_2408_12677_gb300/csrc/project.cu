@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   __shared__ float s_sh[kFwdThreads * RS];
   pdl_enter();
   __shared__ float s_p[kFwdThreads * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
+  if (a.nvalid && blockIdx.x == 0 && threadIdx.x < (unsigned)a.views) a.nvalid[threadIdx.x] = 0u;
   // the block's slices of every parameter array are contiguous: stage them
   // all at once with coalesced asynchronous copies
   const int base = blockIdx.x * kFwdThreads;
@@ -291,11 +292,24 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
       feat[3 * it + 2] = make_float4(fmaxf(rgb[0], 0.f), fmaxf(rgb[1], 0.f), fmaxf(rgb[2], 0.f), z);
     }
     }
-    // tile counts of the small rectangles (the binning expands the queued large ones)
+    // tile counts: the small rectangles per block in shared memory, each
+    // large one (queued above for the scatter) by its whole warp
     if (a.counts) {
       const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
       block_count_tiles(a.counts, a.tile_base[v], a.tiles_x[v], x0, y0, x1, y1, nt <= kBigTiles ? nt : 0u, s_cnt,
                         s_box);
+      unsigned big = __ballot_sync(0xFFFFFFFFu, nt > kBigTiles);
+      const int lane = threadIdx.x & 31;
+      while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t bx = (uint32_t)__shfl_sync(0xFFFFFFFFu, x0, src);
+        const uint32_t by = (uint32_t)__shfl_sync(0xFFFFFFFFu, y0, src);
+        const uint32_t bw = (uint32_t)__shfl_sync(0xFFFFFFFFu, x1 - x0, src);
+        const uint32_t bn = __shfl_sync(0xFFFFFFFFu, nt, src);
+        for (uint32_t k = lane; k < bn; k += 32)
+          atomicAdd(&a.counts[a.tile_base[v] + (by + k / bw) * (uint32_t)a.tiles_x[v] + bx + k % bw], 1u);
+      }
     }
   }
 }

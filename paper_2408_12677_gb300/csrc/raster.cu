@@ -360,6 +360,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       part[0] = sc;
       part[1] = sd;
       part[2] = nv;
+      if (a.nvalid) atomicAdd(&a.nvalid[job.v], (uint32_t)nv);  // an integer: exact in any order
     }
   }
 }
@@ -525,7 +526,8 @@ __device__ __forceinline__ void bwd_job(const RasterArgs& a, const RasterParams&
   const float* __restrict__ dLdc = vw.dLdc;
   const float* __restrict__ dLdd = vw.dLdd;
   const float* __restrict__ dLda = vw.dLda;
-  const float dscale = a.depth_scale ? a.depth_scale[job.v] : 1.f;
+  const float dscale = a.nvalid ? a.w_depth / (float)max(a.nvalid[job.v], 1u)
+                                : (a.depth_scale ? a.depth_scale[job.v] : 1.f);
   const int lane = threadIdx.x & 31;
   const int bxi = (quad % WX) * 8, byi = (quad / WX) * 8;
   const int lx = bxi + (lane & 7), ly0 = byi + (lane >> 3), ly1 = ly0 + 4;

@@ -119,12 +119,11 @@ __device__ __forceinline__ void for_each_pair(int n, const ushort4* __restrict__
   }
 }
 
-// SMALL = false: the projection already counted the items with at most
-// kBigTiles tiles; only the queued large ones are expanded here.
-template <bool SMALL>
+// Every (item, tile) pair adds one to its tile's counter (when the
+// projection has not counted them itself, as for gs_bin_tiles).
 __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_constant__ TileBinArgs a) {
   pdl_enter();
-  for_each_pair<SMALL>(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
+  for_each_pair<true>(a.n, a.rects, a.tiles, a.map, a.big_queue, a.big_len,
                        [&](int, uint32_t t, unsigned active) {
                          // (the checked build counts a tile beyond the grid into tile 0, reported)
                          warp_agg_inc(a.counts, in_bounds(t < (uint32_t)a.n_tiles) ? t : 0u, active);
@@ -584,13 +583,12 @@ int tile_sort_capacity() { return kTileSortCap; }
 int64_t tile_scan_aux_size(int64_t n_tiles) { return (int64_t)kScanAux * ((n_tiles + kScanTiles - 1) / kScanTiles + 2); }
 
 void launch_tile_count_scan(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
-  if (!a.small_counted) cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
-  if (a.n > 0) {
-    if (a.small_counted)  // the large splats only: a grid of warps over the queue
-      launch_pdl(tile_count_kernel<false>, std::max(1, 2 * a.num_sms), kBinThreads, 0, s, a);
-    else
-      launch_pdl(tile_count_kernel<true>, bin_grid(a.n, a.num_sms), kBinThreads, 0, s, a);
-    if (launches) *launches += 1;
+  if (!a.counted) {
+    cudaMemsetAsync(a.counts, 0, sizeof(uint32_t) * (size_t)a.n_tiles, s);
+    if (a.n > 0) {
+      launch_pdl(tile_count_kernel, bin_grid(a.n, a.num_sms), kBinThreads, 0, s, a);
+      if (launches) *launches += 1;
+    }
   }
   if (a.n_tiles <= 4 * kScanThreads || !a.scan_aux) {  // one block is enough
     launch_pdl(tile_scan_kernel, 1, kScanThreads, 0, s, a.n_tiles, a.counts, a.offsets, a.cursors, a.capacity,
