@@ -121,6 +121,22 @@ struct gs_ctx {
   int64_t st_pairs = 0;
   int st_pair_buf = 0;
   bool st_ordered = false;  // torder holds the visit order of the last forward pass
+  // Graph-mode (no-sync) binning into per-tile buckets: the projection writes
+  // each pair straight into its tile's bucket (kBucketCap entries), the
+  // per-tile sort sorts the buckets in place, files every tile under its
+  // length class (cls_count / cls_tiles) and turns the classes into the
+  // raster passes' visit order (torder), so the scan and the scatter drop
+  // out of the iteration.  Used in
+  // no-sync mode once a sync-mode pass has seen every list at most half a
+  // bucket long (bucket_ok); a bucket overflow clears bucket_ok (reported as
+  // GS_ERR_CAPACITY).
+  uint32_t* bids = nullptr;       // cap_bt * kBucketCap
+  uint32_t* cls_count = nullptr;  // kLenClasses
+  uint32_t* cls_tiles = nullptr;  // kLenClasses * cap_bt
+  uint32_t* d_sort_ticket = nullptr;  // 0 between launches of the bucket-mode sort
+  int64_t cap_bt = 0;
+  bool bucket_ok = false;
+  bool st_buckets = false;        // the last forward pass binned into the buckets
   bool order_tiles = true;  // compute and use the visit order
   bool persistent = true;   // raster passes as persistent grids pulling (tile, quadrant) jobs
   int st_sh = 0;
@@ -245,6 +261,19 @@ gs_status ensure_pairs(gs_ctx* c, int64_t p) {
   }
   c->cap_p = cap;
   c->have_state = false;
+  return GS_OK;
+}
+
+// Bucket storage for t tiles (see bids); synchronises when it grows.
+gs_status ensure_buckets(gs_ctx* c, int64_t t) {
+  if (t <= c->cap_bt) return GS_OK;
+  if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
+  GS_CUDA(c, cudaDeviceSynchronize());
+  const int64_t cap = grow_target(t, c->cap_bt);
+  GS_GROW(c, cap_bt, regrow(&c->bids, cap * (int64_t)kBucketCap));
+  GS_GROW(c, cap_bt, regrow(&c->cls_tiles, cap * (int64_t)kLenClasses));
+  if (!c->cls_count) GS_GROW(c, cap_bt, regrow(&c->cls_count, (int64_t)kLenClasses));
+  c->cap_bt = cap;
   return GS_OK;
 }
 
@@ -426,6 +455,53 @@ gs_status bin_and_sort_radix(gs_ctx* c, int n, const TileMap& map, cudaStream_t 
   GS_CHECK_LAUNCH(c, "pair sort / ranges");
   c->st_pairs = c->sync ? P : -1;
   c->st_pair_buf = pcur;
+  c->st_buckets = false;
+  return GS_OK;
+}
+
+// Graph-mode binning into the per-tile buckets the projection filled: one
+// per-tile sort, which also files the tiles under their length classes.
+gs_status bin_buckets(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
+  TileBinArgs tb;
+  tb.n = n;
+  tb.rects = c->rects;
+  tb.tiles = c->tiles;
+  tb.zkey = c->zkey;
+  tb.map = map;
+  tb.n_tiles = (int)map.tile_base[map.views];
+  tb.num_sms = c->num_sms;
+  tb.counts = c->tcount;
+  tb.offsets = nullptr;
+  tb.cursors = nullptr;
+  tb.ids = nullptr;
+  tb.ranges = c->ranges;
+  tb.capacity = 0;
+  tb.n_pairs = c->d_npairs;
+  tb.stats = c->d_binstats;
+  tb.overflow = c->d_overflow;
+  tb.big_queue = c->bigq;
+  tb.big_len = c->d_bigmeta;
+  tb.order = nullptr;
+  tb.counted = true;
+  tb.scan_aux = nullptr;
+  tb.raster_work = c->persistent ? c->d_bigmeta + 1 : nullptr;
+  tb.bucket_ids = c->bids;
+  tb.cls_count = c->cls_count;
+  tb.cls_tiles = c->cls_tiles;
+  tb.cls_stride = (uint32_t)c->cap_bt;
+  tb.sort_ticket = c->d_sort_ticket;
+  tb.order = c->torder;  // written by the sort's last CTA
+  {
+    StageTimer t(c, GS_STAGE_PAIR_SORT, s);
+    launch_tile_sort(tb, s, &c->launches);
+  }
+  GS_CHECK_LAUNCH(c, "tile sort (buckets)");
+  c->counts_zero = true;
+  if (tb.raster_work) c->fwd_work_zero = c->bwd_work_zero = true;
+  c->st_pairs = -1;
+  c->st_pair_buf = 0;
+  c->st_ordered = true;
+  c->st_buckets = true;
   return GS_OK;
 }
 
@@ -471,6 +547,9 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
     GS_CUDA(c, cudaStreamSynchronize(s));
     P = (int64_t)c->h_pinned[0];
     const int64_t longest = (int64_t)c->h_pinned[1];
+    // graph-mode passes may bin into buckets when every list fits half of one
+    c->bucket_ok = longest <= (int64_t)kBucketCap / 2 && T * (int64_t)kBucketCap < ((int64_t)1 << 32) &&
+                   ensure_buckets(c, T) == GS_OK;
     if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, map, s);
     gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
     if (st != GS_OK) return st;
@@ -494,6 +573,7 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
   c->st_pairs = P;
   c->st_pair_buf = 0;
   c->st_ordered = tb.order != nullptr;
+  c->st_buckets = false;
   return GS_OK;
 }
 
@@ -544,6 +624,8 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sort_ticket, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_sort_ticket, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_nvalid, kMaxViews * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_nvalid, 0, kMaxViews * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
@@ -610,6 +692,10 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->tile_loss);
   cudaFree(c->d_dscale);
   cudaFree(c->d_nvalid);
+  cudaFree(c->bids);
+  cudaFree(c->cls_count);
+  cudaFree(c->cls_tiles);
+  cudaFree(c->d_sort_ticket);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->side) cudaStreamDestroy(c->side);
@@ -689,6 +775,14 @@ gs_status gs_sync_status(gs_ctx* c, gs_stream_t stream) {
     return fail(c, GS_ERR_BOUNDS, "an index was out of bounds (bounds-checked build); the results since are invalid");
   }
   const uint32_t ov = (uint32_t)(c->h_pinned[1] & 0xFFFFFFFFull);
+  if (ov & 4u) {  // a tile bucket overflowed: graph-mode passes go back to the counting-scatter binning
+    GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
+    GS_CUDA(c, cudaStreamSynchronize(s));
+    c->have_state = false;
+    c->bucket_ok = false;
+    return fail(c, GS_ERR_CAPACITY, "a tile list outgrew its bucket (" + std::to_string(kBucketCap) +
+                                        " entries) in graph-mode binning; recapture to bin by counting and scatter");
+  }
   if (ov) {
     GS_CUDA(c, cudaMemsetAsync(c->d_overflow, 0, sizeof(uint32_t), s));
     GS_CUDA(c, cudaStreamSynchronize(s));
@@ -853,9 +947,9 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.alpha_min = cfg->alpha_min;
   ra.t_eps = cfg->t_eps;
   ra.ranges = c->ranges;
-  ra.ids = c->pv[c->st_pair_buf];
+  ra.ids = c->st_buckets ? c->bids : c->pv[c->st_pair_buf];
   ra.feat = c->feat;
-  ra.n_ids = (uint32_t)std::min<int64_t>(c->cap_p, 0xFFFFFFFFll);
+  ra.n_ids = (uint32_t)std::min<int64_t>(c->st_buckets ? c->cap_bt * (int64_t)kBucketCap : c->cap_p, 0xFFFFFFFFll);
   ra.n_items = (uint32_t)(c->st_n * c->st_views);
   ra.order = c->st_ordered ? c->torder : nullptr;
   ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;  // the forward counter; the backward pass uses [2]
@@ -918,6 +1012,12 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   pa.big_len = c->d_bigmeta;
   pa.counts = c->tcount;  // the projection counts every rectangle's tiles
   pa.nvalid = fl ? c->d_nvalid : nullptr;  // zeroed by the projection for the fused loss's count
+  const bool buckets = !c->sync && c->bucket_ok && (int64_t)L.tiles <= c->cap_bt;
+  if (buckets) {  // and writes every pair into its tile's bucket
+    pa.bucket_ids = c->bids;
+    pa.overflow = c->d_overflow;
+    pa.cls_count = c->cls_count;
+  }
   if (!c->counts_zero) {  // else the last per-tile sort left them zero
     // every counter of the allocation, so that a later pass over more tiles
     // also starts from zeros
@@ -932,7 +1032,8 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   if (g->n > 0) c->launches += 1;
   GS_CHECK_LAUNCH(c, "project_fwd");
 
-  if ((st = bin_and_sort(c, n_items, L.map, s, true)) != GS_OK) return st;
+  if ((st = buckets ? bin_buckets(c, n_items, L.map, s) : bin_and_sort(c, n_items, L.map, s, true)) != GS_OK)
+    return st;
 
   c->st_n = g->n;
   c->st_views = V;

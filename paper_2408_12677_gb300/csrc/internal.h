@@ -48,6 +48,14 @@ struct ProjectArgs {
   uint32_t* counts;               // per global tile (zeroed, nullable): the projection adds every
                                   // item's tiles
   uint32_t* nvalid = nullptr;     // per view (nullable): zeroed by the projection (block 0)
+  // per-tile buckets (nullable; graph-mode binning): every (item, tile) pair
+  // is written straight to bucket_ids[tile * kBucketCap + slot], slot taken
+  // from the tile's counter (a pair beyond the capacity sets bit 4 of
+  // *overflow instead); block 0 zeroes the length-class counters the
+  // per-tile sort then fills
+  uint32_t* bucket_ids = nullptr;
+  uint32_t* overflow = nullptr;
+  uint32_t* cls_count = nullptr;
 };
 
 // projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
@@ -119,6 +127,11 @@ void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches);
 
 // counting-scatter binning with per-tile sorts (lists of at most kTileSortCap)
 constexpr int kTileSortCap = 4096;
+// graph-mode binning: entries of a tile's bucket (the projection writes the
+// pairs straight into per-tile buckets, no scan and no scatter)
+constexpr uint32_t kBucketCap = 1024;
+// length classes of the raster passes' visit order (four per octave)
+constexpr int kLenClasses = 129;
 struct TileBinArgs {
   int n;                      // items (views x Gaussians)
   const ushort4* rects;       // per item tile rectangle (view-local tile coordinates)
@@ -141,6 +154,17 @@ struct TileBinArgs {
   bool counted;               // counts already hold every item's tiles (the projection counted them)
   uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
   uint32_t* raster_work = nullptr;  // nullable: the forward and backward raster job counters, zeroed by the sort
+  // bucket mode (nullable): the lists are the projection's per-tile buckets
+  // (bucket_ids, tile t's list at t * kBucketCap, its length in counts[t]);
+  // the sort files each tile under its length class (class 0: empty),
+  // cls_tiles[c * cls_stride + i] for i < cls_count[c], and its last CTA
+  // (sort_ticket: a word that is 0 between launches) turns the classes into
+  // the visit order (longest class first) in `order`
+  uint32_t* bucket_ids = nullptr;
+  uint32_t* cls_count = nullptr;
+  uint32_t* cls_tiles = nullptr;
+  uint32_t cls_stride = 0;
+  uint32_t* sort_ticket = nullptr;
 };
 int tile_sort_capacity();
 int64_t tile_scan_aux_size(int64_t n_tiles);

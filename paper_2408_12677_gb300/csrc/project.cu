@@ -122,16 +122,31 @@ __device__ __forceinline__ void stage_slice16(float* dst, const float* src, int 
 // tiles a block's shared counters cover (the bounding box of its rectangles)
 constexpr int kCountBox = 1024;
 
+// Bucket mode: takes slot `slot` of tile t's bucket for item `item` (a slot
+// beyond the bucket's capacity sets bit 4 of *overflow instead).
+__device__ __forceinline__ void bucket_put(uint32_t* __restrict__ bids, uint32_t* __restrict__ overflow, uint32_t t,
+                                           uint32_t slot, uint32_t item) {
+  if (slot < kBucketCap)
+    bids[(size_t)t * kBucketCap + slot] = item;
+  else
+    atomicOr(overflow, 4u);
+}
+
 // Adds the tiles of the block's rectangles [x0, x1) x [y0, y1) of one view
 // (those of at most kBigTiles tiles: ns = their tile count, 0 for the others
 // and for threads without an item) to the global per-tile counters.  When
 // the block's rectangles lie in a box of at most kCountBox tiles they are
 // counted in shared memory (s_cnt) first and each touched tile's counter
 // gets one atomic add; otherwise each (item, tile) pair adds 1 directly.
+// Bucket mode (bids non-null): the same counting reserves each touched
+// tile's run of slots (the atomic returns its start), then every pair takes
+// the next slot of its tile's run and writes `item` there.
 // Called by every thread of the block (it synchronises the block).
 __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts, uint32_t tile_base, int tiles_x,
                                                   int x0, int y0, int x1, int y1, uint32_t ns,
-                                                  uint32_t* __restrict__ s_cnt, int* __restrict__ s_box) {
+                                                  uint32_t* __restrict__ s_cnt, int* __restrict__ s_box,
+                                                  uint32_t* __restrict__ bids, uint32_t* __restrict__ overflow,
+                                                  uint32_t item) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int W = kFwdThreads / 32;
   unsigned bx0 = ns ? (unsigned)x0 : 0xFFFFu, by0 = ns ? (unsigned)y0 : 0xFFFFu;
@@ -158,8 +173,13 @@ __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts,
   const int bw = X1 - X0, bh = Y1 - Y0;
   const int w = x1 - x0;
   if (bw <= 0 || bh <= 0 || bw * bh > kCountBox) {  // block-uniform
-    for (uint32_t k = 0; k < ns; ++k)
-      atomicAdd(&counts[tile_base + (uint32_t)(y0 + (int)k / w) * (uint32_t)tiles_x + (uint32_t)(x0 + (int)k % w)], 1u);
+    for (uint32_t k = 0; k < ns; ++k) {
+      const uint32_t t = tile_base + (uint32_t)(y0 + (int)k / w) * (uint32_t)tiles_x + (uint32_t)(x0 + (int)k % w);
+      if (bids)
+        bucket_put(bids, overflow, t, atomicAdd(&counts[t], 1u), item);
+      else
+        atomicAdd(&counts[t], 1u);
+    }
     __syncthreads();  // s_box is read before the next call rewrites it
     return;
   }
@@ -177,7 +197,26 @@ __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts,
   __syncthreads();
   for (int c = threadIdx.x; c < area; c += kFwdThreads) {
     const uint32_t v = s_cnt[c];
-    if (v) atomicAdd(&counts[tile_base + (uint32_t)(Y0 + c / bw) * (uint32_t)tiles_x + (uint32_t)(X0 + c % bw)], v);
+    if (v) {
+      uint32_t* cnt = &counts[tile_base + (uint32_t)(Y0 + c / bw) * (uint32_t)tiles_x + (uint32_t)(X0 + c % bw)];
+      if (bids)
+        s_cnt[c] = atomicAdd(cnt, v);  // the start of the block's run in the tile's bucket
+      else
+        atomicAdd(cnt, v);
+    }
+  }
+  __syncthreads();
+  if (bids) {
+    tx = x0;
+    ty = y0;
+    for (uint32_t k = 0; k < ns; ++k) {
+      bucket_put(bids, overflow, tile_base + (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx,
+                 atomicAdd(&s_cnt[(ty - Y0) * bw + (tx - X0)], 1u), item);
+      if (++tx == x1) {
+        tx = x0;
+        ++ty;
+      }
+    }
   }
   __syncthreads();  // s_cnt and s_box are reused by the next view
 }
@@ -196,7 +235,11 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
   __shared__ float s_sh[kFwdThreads * RS];
   pdl_enter();
   __shared__ float s_p[kFwdThreads * 11];  // means (3B) | log-scales (3B) | quats (4B) | logits (B)
-  if (a.nvalid && blockIdx.x == 0 && threadIdx.x < (unsigned)a.views) a.nvalid[threadIdx.x] = 0u;
+  if (blockIdx.x == 0) {  // per-pass counters the later kernels accumulate into
+    if (a.nvalid && threadIdx.x < (unsigned)a.views) a.nvalid[threadIdx.x] = 0u;
+    if (a.cls_count)
+      for (int c = threadIdx.x; c < kLenClasses; c += kFwdThreads) a.cls_count[c] = 0u;
+  }
   // the block's slices of every parameter array are contiguous: stage them
   // all at once with coalesced asynchronous copies
   const int base = blockIdx.x * kFwdThreads;
@@ -297,7 +340,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
     if (a.counts) {
       const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
       block_count_tiles(a.counts, a.tile_base[v], a.tiles_x[v], x0, y0, x1, y1, nt <= kBigTiles ? nt : 0u, s_cnt,
-                        s_box);
+                        s_box, a.bucket_ids, a.overflow, (uint32_t)it);
       unsigned big = __ballot_sync(0xFFFFFFFFu, nt > kBigTiles);
       const int lane = threadIdx.x & 31;
       while (big) {
@@ -307,8 +350,14 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
         const uint32_t by = (uint32_t)__shfl_sync(0xFFFFFFFFu, y0, src);
         const uint32_t bw = (uint32_t)__shfl_sync(0xFFFFFFFFu, x1 - x0, src);
         const uint32_t bn = __shfl_sync(0xFFFFFFFFu, nt, src);
-        for (uint32_t k = lane; k < bn; k += 32)
-          atomicAdd(&a.counts[a.tile_base[v] + (by + k / bw) * (uint32_t)a.tiles_x[v] + bx + k % bw], 1u);
+        const uint32_t bit = (uint32_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)it, src);
+        for (uint32_t k = lane; k < bn; k += 32) {
+          const uint32_t t = a.tile_base[v] + (by + k / bw) * (uint32_t)a.tiles_x[v] + bx + k % bw;
+          if (a.bucket_ids)
+            bucket_put(a.bucket_ids, a.overflow, t, atomicAdd(&a.counts[t], 1u), bit);
+          else
+            atomicAdd(&a.counts[t], 1u);
+        }
       }
     }
   }

@@ -177,10 +177,12 @@ __device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
 }
 
 // Forward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
-// visit k) by one warp; buf is the warp's shared staging buffer.
+// visit k) by one warp; buf is the warp's shared staging buffer, s_raw the
+// two shared slots per lane that its Gaussians' records land in (cp.async).
 template <int TW, int TH, bool COUNT, bool LOSS>
 __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t k, int quad,
-                                        Entry* __restrict__ buf, float* __restrict__ T_final_all,
+                                        Entry* __restrict__ buf, float4 (*__restrict__ s_raw)[32][3],
+                                        float* __restrict__ T_final_all,
                                         int32_t* __restrict__ last_all, unsigned long long* __restrict__ counters) {
   constexpr int WX = TW / 8;
   const TileJob job = tile_job<TW, TH>(a, k);
@@ -206,16 +208,22 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
   bool done0 = !in0, done1 = !in1;
   const f2x PLY = f2_pack(ply0, ply1), ONE2 = f2_pack(1.f, 1.f);
 
-  // software pipeline: the records of the next 32 entries are in flight
-  float4 f0, f1, f2;
-  if (lane < n) load_entry(feat, checked_id(ids[r.x + lane], a.n_items), f0, f1, f2);
-  for (int c0 = 0; c0 < n; c0 += 32) {
+  // software pipeline: chunk c's records in shared memory, chunk c + 32's in
+  // flight (cp.async), the ids of chunk c + 64 in a register
+  int cur = 0;
+  if (lane < n) cp_record(s_raw[0][lane], feat, checked_id(ids[r.x + lane], a.n_items));
+  cp_commit();
+  uint32_t g2 = 32 + lane < n ? checked_id(ids[r.x + 32 + lane], a.n_items) : 0u;
+  for (int c0 = 0; c0 < n; c0 += 32, cur ^= 1) {
     if (__all_sync(kFull, done0 && done1)) break;
+    if (c0 + 32 + lane < n) cp_record(s_raw[cur ^ 1][lane], feat, g2);
+    cp_commit();
+    if (c0 + 64 + lane < n) g2 = checked_id(ids[r.x + c0 + 64 + lane], a.n_items);
+    cp_wait_prev();
     const bool have = c0 + lane < n;
-    const float4 h0 = f0, h1 = f1, h2 = f2;
-    if (c0 + 32 + lane < n) load_entry(feat, checked_id(ids[r.x + c0 + 32 + lane], a.n_items), f0, f1, f2);
     Entry e;
-    const bool hit = have && make_entry(h0, h1, h2, ox, oy, bx, by, rp, e) != 0u;
+    const float4* raw = s_raw[cur][lane];
+    const bool hit = have && make_entry(raw[0], raw[1], raw[2], ox, oy, bx, by, rp, e) != 0u;
     __syncwarp();
     if (hit) buf[lane] = e;
     unsigned bal = __ballot_sync(kFull, hit);
@@ -281,6 +289,7 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       }
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   if (COUNT) {
     unsigned long long vb = n_blend, vv = n_visit;
 #pragma unroll
@@ -388,14 +397,16 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   pdl_enter();
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
+  __shared__ __align__(16) float4 s_rawf[kThreads / 32][2][32][3];
   const int warp = threadIdx.x >> 5;
   if constexpr (!PERSIST) {
-    fwd_job<TW, TH, COUNT, LOSS>(a, rp, blockIdx.x, warp, s_e[warp], T_final_all, last_all, counters);
+    fwd_job<TW, TH, COUNT, LOSS>(a, rp, blockIdx.x, warp, s_e[warp], s_rawf[warp], T_final_all, last_all, counters);
   } else {
     const uint32_t n_jobs = 4u * a.n_tiles;
     uint32_t job;
     while (next_job(work, n_jobs, job))
-      fwd_job<TW, TH, COUNT, LOSS>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], T_final_all, last_all, counters);
+      fwd_job<TW, TH, COUNT, LOSS>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], s_rawf[warp], T_final_all,
+                                   last_all, counters);
   }
 }
 

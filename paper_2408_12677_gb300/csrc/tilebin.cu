@@ -134,8 +134,7 @@ __global__ void __launch_bounds__(kBinThreads) tile_count_kernel(const __grid_co
 // an empty list, else 4 floor(log2 c) + (the two bits after c's leading one)
 // + 1, so classes grow with the length and tiles within 19% of each other's
 // length share one.  kLenClasses classes (kLenClasses is also the "no tile"
-// sentinel).
-constexpr int kLenClasses = 129;
+// sentinel; the raster passes' bucket-mode visit order uses the same classes).
 __device__ __forceinline__ int length_class(uint32_t c) {
   if (!c) return 0;
   const int lead = 31 - __clz(c);
@@ -497,8 +496,13 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
                                                                  uint32_t capacity, uint32_t* __restrict__ overflow,
                                                                  uint32_t* __restrict__ big_len,
                                                                  uint32_t* __restrict__ raster_work,
-                                                                 uint32_t n_items) {
+                                                                 uint32_t n_items, uint32_t* __restrict__ cls_count,
+                                                                 uint32_t* __restrict__ cls_tiles,
+                                                                 uint32_t cls_stride,
+                                                                 uint32_t* __restrict__ sort_ticket,
+                                                                 uint32_t* __restrict__ order) {
   pdl_enter();
+  const bool buckets = cls_count != nullptr;  // the lists are per-tile buckets (see TileBinArgs)
   __shared__ unsigned long long s[CAP];
   __shared__ uint2 s_long[kSortWarps];  // (offset, length) of the CTA's lists longer than kWarpSortMax
   __shared__ uint32_t s_nlong;
@@ -513,11 +517,17 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
   __syncthreads();
   const uint32_t t = blockIdx.x * kSortWarps + warp;
   if (t < n_tiles) {
-    const uint32_t off = offsets[t], n = counts[t];
+    uint32_t n = counts[t];
+    const uint32_t off = buckets ? t * kBucketCap : offsets[t];
     __syncwarp();  // every lane has read counts[t]
-    const bool fits = (unsigned long long)off + n <= (unsigned long long)capacity;
+    if (buckets && n > kBucketCap) n = kBucketCap;  // its bucket overflowed (flagged by the projection)
+    const bool fits = buckets || (unsigned long long)off + n <= (unsigned long long)capacity;
     if (lane == 0) {
       counts[t] = 0u;
+      if (buckets) {  // file the tile under its length class (empty ones too: their pixels are composited)
+        const int c = length_class(n);
+        cls_tiles[(size_t)c * cls_stride + atomicAdd(&cls_count[c], 1u)] = t;
+      }
       uint2 rg = (n && fits) ? make_uint2(off, off + n) : make_uint2(0u, 0u);
       if (fits && n > (uint32_t)CAP) {
         atomicOr(overflow, 2u);
@@ -569,6 +579,38 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
     for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) ids[off + i] = (uint32_t)s[i];
     __syncthreads();  // s is reused by the next long list
   }
+  if (!buckets) return;
+  // bucket mode: the last CTA to finish turns the length classes into the
+  // raster passes' visit order (longest class first)
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's class entries are visible before its ticket
+    s_last = atomicAdd(sort_ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  uint32_t* e = reinterpret_cast<uint32_t*>(s);  // e[c]: tiles of class c or longer; e[kLenClasses] = 0
+  if (threadIdx.x < 32) {
+    for (int c = threadIdx.x; c < kLenClasses; c += 32) e[c] = __ldcg(&cls_count[c]);
+    __syncwarp();
+    class_starts_desc(e);  // e[c] = tiles of the classes above c
+    __syncwarp();
+    for (int c = threadIdx.x; c < kLenClasses; c += 32) e[c] += __ldcg(&cls_count[c]);
+    if (threadIdx.x == 0) e[kLenClasses] = 0u;
+  }
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < n_tiles; k += kSortThreads) {
+    int lo = 0, hi = kLenClasses - 1;  // the largest class c with e[c] > k
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (e[mid] > k) lo = mid;
+      else hi = mid - 1;
+    }
+    order[k] = __ldcg(&cls_tiles[(size_t)lo * cls_stride + (k - e[lo + 1])]);
+  }
+  if (threadIdx.x == 0) *sort_ticket = 0u;
 }
 
 int bin_grid(int n, int num_sms) {
@@ -614,9 +656,11 @@ void launch_tile_scatter(const TileBinArgs& a, cudaStream_t s, int64_t* launches
 
 void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   const int grid = (a.n_tiles + kSortWarps - 1) / kSortWarps;
-  launch_pdl(tile_sort_kernel<kTileSortCap>, grid, kSortThreads, 0, s, a.offsets, a.counts, a.ids, a.zkey,
-             a.ranges, (uint32_t)a.n_tiles, a.capacity, a.overflow, const_cast<uint32_t*>(a.big_len),
-             a.raster_work, (uint32_t)a.n);
+  const bool buckets = a.bucket_ids != nullptr;
+  launch_pdl(tile_sort_kernel<kTileSortCap>, grid, kSortThreads, 0, s, a.offsets, a.counts,
+             buckets ? a.bucket_ids : a.ids, a.zkey, a.ranges, (uint32_t)a.n_tiles, a.capacity, a.overflow,
+             const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n, buckets ? a.cls_count : nullptr,
+             a.cls_tiles, a.cls_stride, a.sort_ticket, a.order);
   if (launches) *launches += 1;
 }
 
