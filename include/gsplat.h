@@ -156,8 +156,9 @@ gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
 gs_status gs_ctx_set_adam_step(gs_ctx *ctx, int64_t step);
 
 /* on = 1 (default): the raster passes visit the tiles longest list first
- * (tiles ordered by the binary length class of their lists, computed during
- * binning), so the slowest tiles start early and the grid ends evenly; on = 0
+ * (tiles ordered by the length class of their lists, four classes per octave
+ * of the length, computed during binning), so the slowest tiles start early
+ * and the grid ends evenly; on = 0
  * visits them in index order.  Results do not depend on the order.  Takes
  * effect at the next forward pass. */
 gs_status gs_ctx_set_tile_order(gs_ctx *ctx, int on);
@@ -607,6 +608,15 @@ gs_status gs_get_projection(gs_ctx *ctx, float *mean2d, float *cov2d, float *dep
  * (the views' tiles end to end, row-major within a view).  For parity checks
  * of the binning and for picking the longest-list tiles. */
 gs_status gs_get_tile_ranges(gs_ctx *ctx, uint32_t *ranges, int64_t n_tiles, gs_stream_t stream);
+
+/* Copy the raster visit order of the last forward pass to `order` (device
+ * uint32 [n_tiles], a permutation of the tiles numbered as in
+ * gs_get_tile_ranges, their length classes non-increasing: class 0 for an
+ * empty list, else 4 floor(log2 len) + the two bits after len's leading one
+ * + 1); n_tiles must be the forward pass's tile count.  GS_ERR_STATE when
+ * that pass visited the tiles in index order (gs_ctx_set_tile_order(0), or
+ * the radix binning of very long lists).  For checks of the binning. */
+gs_status gs_get_tile_order(gs_ctx *ctx, uint32_t *order, int64_t n_tiles, gs_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -153,6 +153,7 @@ EXPORTS = {
     "gs_measure_alu_peaks": (C.c_int, [C.c_int, C.c_int32, C.POINTER(gs_alu_peaks)]),
     "gs_state_token": (C.c_int, [P, C.POINTER(C.c_uint64)]),
     "gs_get_tile_ranges": (C.c_int, [P, P, C.c_int64, P]),
+    "gs_get_tile_order": (C.c_int, [P, P, C.c_int64, P]),
 }
 
 _lib = None
@@ -579,6 +580,12 @@ def gs_get_tile_ranges(ctx, ranges, stream=None):
     """ranges: int32 CUDA tensor [n_tiles, 2] receiving [first, last + 1) per tile."""
     _check(ctx, load().gs_get_tile_ranges(ctx, _ptr(ranges), int(ranges.shape[0]), _stream(stream)),
            "gs_get_tile_ranges")
+
+
+def gs_get_tile_order(ctx, order, stream=None):
+    """order: int32 CUDA tensor [n_tiles] receiving the raster visit order."""
+    _check(ctx, load().gs_get_tile_order(ctx, _ptr(order), int(order.shape[0]), _stream(stream)),
+           "gs_get_tile_order")
 
 
 def gs_state_token(ctx) -> int:

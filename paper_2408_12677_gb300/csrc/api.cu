@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -127,14 +128,17 @@ struct gs_ctx {
   // length class (cls_count / cls_tiles) and turns the classes into the
   // raster passes' visit order (torder), so the scan and the scatter drop
   // out of the iteration.  Used in
-  // no-sync mode once a sync-mode pass has seen every list at most half a
-  // bucket long (bucket_ok); a bucket overflow clears bucket_ok (reported as
+  // no-sync mode while every sync-mode pass of the context has seen every
+  // list at most half a bucket long (longest_seen, bucket_ok: a context that
+  // renders several views or maps must not take one view's short lists for
+  // another's); a bucket overflow clears bucket_ok for good (reported as
   // GS_ERR_CAPACITY).
   uint32_t* bids = nullptr;       // cap_bt * kBucketCap
   uint32_t* cls_count = nullptr;  // kLenClasses
   uint32_t* cls_tiles = nullptr;  // kLenClasses * cap_bt
   uint32_t* d_sort_ticket = nullptr;  // 0 between launches of the bucket-mode sort
   int64_t cap_bt = 0;
+  int64_t longest_seen = 0;
   bool bucket_ok = false;
   bool st_buckets = false;        // the last forward pass binned into the buckets
   bool order_tiles = true;  // compute and use the visit order
@@ -547,9 +551,11 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
     GS_CUDA(c, cudaStreamSynchronize(s));
     P = (int64_t)c->h_pinned[0];
     const int64_t longest = (int64_t)c->h_pinned[1];
-    // graph-mode passes may bin into buckets when every list fits half of one
-    c->bucket_ok = longest <= (int64_t)kBucketCap / 2 && T * (int64_t)kBucketCap < ((int64_t)1 << 32) &&
-                   ensure_buckets(c, T) == GS_OK;
+    // graph-mode passes may bin into buckets while every list any sync pass
+    // has seen fits half of one
+    c->longest_seen = std::max(c->longest_seen, longest);
+    c->bucket_ok = c->longest_seen <= (int64_t)kBucketCap / 2 && T * (int64_t)kBucketCap < ((int64_t)1 << 32) &&
+                   ensure_buckets(c, T) == GS_OK && c->cap_bt * (int64_t)kLenClasses < ((int64_t)1 << 32);
     if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, map, s);
     gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
     if (st != GS_OK) return st;
@@ -780,6 +786,7 @@ gs_status gs_sync_status(gs_ctx* c, gs_stream_t stream) {
     GS_CUDA(c, cudaStreamSynchronize(s));
     c->have_state = false;
     c->bucket_ok = false;
+    c->longest_seen = std::numeric_limits<int64_t>::max();
     return fail(c, GS_ERR_CAPACITY, "a tile list outgrew its bucket (" + std::to_string(kBucketCap) +
                                         " entries) in graph-mode binning; recapture to bin by counting and scatter");
   }
@@ -1889,6 +1896,18 @@ gs_status gs_get_tile_ranges(gs_ctx* c, uint32_t* ranges, int64_t n_tiles, gs_st
     return fail(c, GS_ERR_INVALID_ARG, "gs_get_tile_ranges: ranges is NULL or n_tiles is not the forward pass's");
   GS_CUDA(c, cudaSetDevice(c->device));
   GS_CUDA(c, cudaMemcpyAsync(ranges, c->ranges, sizeof(uint2) * (size_t)n_tiles, cudaMemcpyDeviceToDevice,
+                             (cudaStream_t)stream));
+  return GS_OK;
+}
+
+gs_status gs_get_tile_order(gs_ctx* c, uint32_t* order, int64_t n_tiles, gs_stream_t stream) {
+  if (!c) return GS_ERR_INVALID_ARG;
+  if (!c->have_state) return fail(c, GS_ERR_STATE, "no forward pass on this context");
+  if (!c->st_ordered) return fail(c, GS_ERR_STATE, "the last forward pass visited the tiles in index order");
+  if (!order || n_tiles != c->st_tiles)
+    return fail(c, GS_ERR_INVALID_ARG, "gs_get_tile_order: order is NULL or n_tiles is not the forward pass's");
+  GS_CUDA(c, cudaSetDevice(c->device));
+  GS_CUDA(c, cudaMemcpyAsync(order, c->torder, sizeof(uint32_t) * (size_t)n_tiles, cudaMemcpyDeviceToDevice,
                              (cudaStream_t)stream));
   return GS_OK;
 }

@@ -591,24 +591,55 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // One CTA does this part alone, so it is written as few dependent global
+  // round trips as possible: one for the class counts, one per 4096 tiles
+  // for the class lists.
   uint32_t* e = reinterpret_cast<uint32_t*>(s);  // e[c]: tiles of class c or longer; e[kLenClasses] = 0
   if (threadIdx.x < 32) {
-    for (int c = threadIdx.x; c < kLenClasses; c += 32) e[c] = __ldcg(&cls_count[c]);
+    constexpr int PER = (kLenClasses + 31) / 32;
+    uint32_t cnt[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int c = threadIdx.x + 32 * i;
+      cnt[i] = c < kLenClasses ? __ldcg(&cls_count[c]) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+      if (threadIdx.x + 32 * i < kLenClasses) e[threadIdx.x + 32 * i] = cnt[i];
     __syncwarp();
     class_starts_desc(e);  // e[c] = tiles of the classes above c
     __syncwarp();
-    for (int c = threadIdx.x; c < kLenClasses; c += 32) e[c] += __ldcg(&cls_count[c]);
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+      if (threadIdx.x + 32 * i < kLenClasses) e[threadIdx.x + 32 * i] += cnt[i];
     if (threadIdx.x == 0) e[kLenClasses] = 0u;
   }
   __syncthreads();
-  for (uint32_t k = threadIdx.x; k < n_tiles; k += kSortThreads) {
-    int lo = 0, hi = kLenClasses - 1;  // the largest class c with e[c] > k
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (e[mid] > k) lo = mid;
-      else hi = mid - 1;
+  // kOrderIlp visits per thread and round, their searches unrolled and their
+  // loads in flight together
+  constexpr int kOrderIlp = 16;
+  for (uint32_t k0 = 0; k0 < n_tiles; k0 += kSortThreads * kOrderIlp) {
+    uint32_t src[kOrderIlp];  // < kLenClasses x cls_stride, which the host keeps below 2^32
+#pragma unroll
+    for (int i = 0; i < kOrderIlp; ++i) {
+      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
+      int c = 0;  // the largest class c with e[c] > k (e is non-increasing, e[0] = n_tiles)
+#pragma unroll
+      for (int step = 128; step > 0; step >>= 1)
+        if (c + step < kLenClasses && e[c + step] > k) c += step;
+      src[i] = (uint32_t)c * cls_stride + (k - e[c + 1]);
     }
-    order[k] = __ldcg(&cls_tiles[(size_t)lo * cls_stride + (k - e[lo + 1])]);
+    uint32_t v[kOrderIlp];
+#pragma unroll
+    for (int i = 0; i < kOrderIlp; ++i) {
+      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
+      v[i] = k < n_tiles ? __ldcg(&cls_tiles[src[i]]) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kOrderIlp; ++i) {
+      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
+      if (k < n_tiles) order[k] = v[i];
+    }
   }
   if (threadIdx.x == 0) *sort_ticket = 0u;
 }

@@ -43,6 +43,35 @@ def _longest(ctx, cam, tile=16):
     return int((r[:, 1] - r[:, 0]).max())
 
 
+def _length_class(n):
+    """Four classes per octave of the list length (0 for an empty list)."""
+    n = np.asarray(n, np.int64)
+    lead = np.where(n > 0, np.floor(np.log2(np.maximum(n, 1))).astype(np.int64), 0)
+    frac = np.where(lead >= 2, (n >> np.maximum(lead - 2, 0)) & 3, (n << np.maximum(2 - lead, 0)) & 3)
+    return np.where(n > 0, 4 * lead + frac + 1, 0)
+
+
+def check_visit_order(ctx, n_tiles):
+    """The raster visit order of the last forward pass is a permutation of
+    the tiles with non-increasing length classes."""
+    from paper_2408_12677_gb300 import abi
+    r = torch.empty((n_tiles, 2), dtype=torch.int32, device="cuda")
+    o = torch.empty(n_tiles, dtype=torch.int32, device="cuda")
+    abi.gs_get_tile_ranges(ctx.handle, r)
+    abi.gs_get_tile_order(ctx.handle, o)
+    torch.cuda.synchronize()
+    r = r.cpu().numpy().view(np.uint32).astype(np.int64)
+    o = o.cpu().numpy().view(np.uint32).astype(np.int64)
+    np.testing.assert_array_equal(np.sort(o), np.arange(n_tiles))
+    cls = _length_class(r[o, 1] - r[o, 0])
+    assert (np.diff(cls) <= 0).all()
+
+
+def test_length_classes():
+    assert _length_class([0, 1, 2, 3, 4, 5, 6, 7, 8, 451, 512, 1024]).tolist() == [
+        0, 1, 5, 7, 9, 10, 11, 12, 13, 4 * 8 + 3 + 1, 4 * 9 + 1, 4 * 10 + 1]
+
+
 def _no_sync(ctx, n, npx, pairs):
     from paper_2408_12677_gb300 import abi
     abi.gs_ctx_reserve(ctx.handle, n, npx, pairs)
@@ -63,6 +92,8 @@ def test_bucket_binning_renders_the_same_images_and_gradients():
     model = to_gpu_model(P)
     n_sync, ref = _launches_of_render(ctx, model, cam, pose)  # counting-scatter binning
     assert 0 < _longest(ctx, cam) <= 512
+    T = -(-cam.width // 16) * -(-cam.height // 16)
+    check_visit_order(ctx, T)
     rng = np.random.default_rng(5)
     H, W = cam.height, cam.width
     wc = rng.standard_normal((3, H, W)).astype(np.float32)
@@ -72,6 +103,7 @@ def test_bucket_binning_renders_the_same_images_and_gradients():
     _no_sync(ctx, P["means"].shape[0], H * W, 2_000_000)
     n_bucket, got = _launches_of_render(ctx, model, cam, pose)
     assert n_bucket < n_sync  # no count, scan or scatter launch
+    check_visit_order(ctx, T)
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
     g = gpu_backward(ctx, model, cam, pose, wc, wd, wa)
@@ -100,6 +132,7 @@ def test_bucket_binning_of_lists_longer_than_a_warp_sorts():
     abi.gs_sync_status(ctx.handle)
     longest = _longest(ctx, cam)
     assert 512 < longest <= 1024, longest
+    check_visit_order(ctx, -(-cam.width // 16) * -(-cam.height // 16))
     ref_ctx = _ctx()
     ref = gpu_render(ref_ctx, to_gpu_model(big), cam, pose)  # sync mode: counting-scatter binning
     for a, b in zip(got, ref):
@@ -143,10 +176,33 @@ def test_bucket_binning_of_a_batch_of_views():
     npx = sum(v.cam.width * v.cam.height for v in w.views)
     _no_sync(ctx, w.n * len(w.views), npx, 1_000_000)
     got = _batched_render(ctx, model, w.views)
+    check_visit_order(ctx, sum(-(-v.cam.width // 16) * -(-v.cam.height // 16) for v in w.views))
     for (a0, a1, a2), (b0, b1, b2) in zip(got, ref):
         np.testing.assert_array_equal(a0, b0)
         np.testing.assert_array_equal(a1, b1)
         np.testing.assert_array_equal(a2, b2)
     from paper_2408_12677_gb300 import abi
     abi.gs_sync_status(ctx.handle)
+    ctx.close()
+
+
+def test_bucket_binning_stays_off_after_any_long_list():
+    """A context that renders a map with long lists and then one with short
+    lists in sync mode must not bin the first into buckets in no-sync mode:
+    bucket binning needs every list any sync pass saw to fit half a bucket."""
+    from paper_2408_12677_gb300 import abi
+    P, cam, pose = _scene(seed=6, n=20000, log_scale_range=(-5.0, -3.5))
+    big = dict(P)
+    big["log_scales"] = (np.asarray(P["log_scales"]) + 1.5).astype(np.float32)  # lists of 1025-4096
+    ctx = _ctx()
+    small_model, big_model = to_gpu_model(P), to_gpu_model(big)
+    ref = gpu_render(ctx, big_model, cam, pose)
+    assert _longest(ctx, cam) > 1024
+    gpu_render(ctx, small_model, cam, pose)
+    assert _longest(ctx, cam) <= 512
+    _no_sync(ctx, P["means"].shape[0], cam.width * cam.height, 8_000_000)
+    got = gpu_render(ctx, big_model, cam, pose)
+    abi.gs_sync_status(ctx.handle)  # counting-scatter binning: no bucket overflow
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
     ctx.close()

@@ -17,6 +17,7 @@ from oracle import render as R
 from synth import workloads
 from tests._util import compare, ensure_built, oracle_params, to_gpu_model
 from tests.test_gpu_batched import _batched_backward, _batched_render
+from tests.test_gpu_buckets import check_visit_order
 from tests.test_gpu_grad import NAMES, check_grad_arrays
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +52,7 @@ def test_multi_view_whole_tiles_forward_and_backward(setup):
     grid = [(-(-v.cam.width // TILE), -(-v.cam.height // TILE)) for v in w.views]
     base = np.concatenate([[0], np.cumsum([tx * ty for tx, ty in grid])])
     lens = _tile_lengths(ctx, int(base[-1]))
+    check_visit_order(ctx, int(base[-1]))
     P = oracle_params(w.params)
     rng = np.random.default_rng(11)
     wc, wd, wa, sel = [], [], [], []
