@@ -147,7 +147,13 @@ gs_status gs_ctx_reserve(gs_ctx *ctx, int64_t n_gaussians, int64_t n_pixels, int
 /* sync = 1 (default): the forward pass reads the pair count to the host and
  * grows buffers.  sync = 0: no host synchronisation inside the forward pass
  * (stream-capturable); pairs beyond the reserved capacity are dropped and
- * the next gs_render_fwd / gs_sync_status reports GS_ERR_CAPACITY. */
+ * the next gs_render_fwd / gs_sync_status reports GS_ERR_CAPACITY.  While
+ * every tile list that the context's sync-mode passes have seen is at most
+ * 512 entries long, sync = 0 passes bin into fixed per-tile buckets of 1024
+ * entries written by the projection (no scan or scatter launch; the same
+ * lists and images); a list that outgrows its bucket is reported by
+ * gs_sync_status as GS_ERR_CAPACITY, after which the context bins by
+ * counting and scatter (a captured graph has to be recaptured). */
 gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
 
 /* Set the context's device-side Adam step counter (used by
@@ -172,7 +178,8 @@ gs_status gs_ctx_set_persistent(gs_ctx *ctx, int on);
 /* Synchronise the stream, then report GS_ERR_BOUNDS if the bounds-checked
  * build met an out-of-bounds index since the last call (see
  * gs_bounds_checked), else GS_ERR_CAPACITY if a no-sync forward pass
- * overflowed the pair buffers; clears the flag it reports. */
+ * overflowed the pair buffers or a tile bucket (see gs_ctx_set_sync);
+ * clears the flag it reports. */
 gs_status gs_sync_status(gs_ctx *ctx, gs_stream_t stream);
 
 /* Counters of this context (host struct).  The two eval counters live on the

@@ -124,10 +124,10 @@ struct gs_ctx {
   bool st_ordered = false;  // torder holds the visit order of the last forward pass
   // Graph-mode (no-sync) binning into per-tile buckets: the projection writes
   // each pair straight into its tile's bucket (kBucketCap entries), the
-  // per-tile sort sorts the buckets in place, files every tile under its
-  // length class (cls_count / cls_tiles) and turns the classes into the
-  // raster passes' visit order (torder), so the scan and the scatter drop
-  // out of the iteration.  Used in
+  // per-tile sort sorts the buckets in place and files every tile under its
+  // length class (cls_count / cls_tiles); the forward raster pass takes its
+  // visit order from the classes and records it in torder for the backward
+  // pass, so the scan and the scatter drop out of the iteration.  Used in
   // no-sync mode while every sync-mode pass of the context has seen every
   // list at most half a bucket long (longest_seen, bucket_ok: a context that
   // renders several views or maps must not take one view's short lists for
@@ -136,7 +136,6 @@ struct gs_ctx {
   uint32_t* bids = nullptr;       // cap_bt * kBucketCap
   uint32_t* cls_count = nullptr;  // kLenClasses
   uint32_t* cls_tiles = nullptr;  // kLenClasses * cap_bt
-  uint32_t* d_sort_ticket = nullptr;  // 0 between launches of the bucket-mode sort
   int64_t cap_bt = 0;
   int64_t longest_seen = 0;
   bool bucket_ok = false;
@@ -493,8 +492,6 @@ gs_status bin_buckets(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
   tb.cls_count = c->cls_count;
   tb.cls_tiles = c->cls_tiles;
   tb.cls_stride = (uint32_t)c->cap_bt;
-  tb.sort_ticket = c->d_sort_ticket;
-  tb.order = c->torder;  // written by the sort's last CTA
   {
     StageTimer t(c, GS_STAGE_PAIR_SORT, s);
     launch_tile_sort(tb, s, &c->launches);
@@ -630,8 +627,6 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_binstats, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_step, sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sort_ticket, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMemset(c->d_sort_ticket, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_nvalid, kMaxViews * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_nvalid, 0, kMaxViews * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
@@ -701,7 +696,6 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->bids);
   cudaFree(c->cls_count);
   cudaFree(c->cls_tiles);
-  cudaFree(c->d_sort_ticket);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->side) cudaStreamDestroy(c->side);
@@ -967,6 +961,10 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.depth_scale = nullptr;
   ra.nvalid = nullptr;
   ra.w_depth = 0.f;
+  ra.cls_count = nullptr;
+  ra.cls_tiles = nullptr;
+  ra.cls_stride = 0;
+  ra.order_out = nullptr;
   for (int v = 0; v < kMaxViews; ++v) {
     RasterView& rv = ra.v[v];
     const bool live = v < c->st_views;
@@ -1072,6 +1070,13 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
       ra.v[v].loss_dc = c->dl_img + 4 * L.pix_base[v];
       ra.v[v].loss_dd = c->dl_img + 4 * L.pix_base[v] + 3 * np;
     }
+  }
+  if (c->st_buckets) {  // visit order from the sort's class lists, recorded for the backward pass
+    ra.order = nullptr;
+    ra.cls_count = c->cls_count;
+    ra.cls_tiles = c->cls_tiles;
+    ra.cls_stride = (uint32_t)c->cap_bt;
+    ra.order_out = c->torder;
   }
   ra.zero_work = !c->fwd_work_zero;
   {

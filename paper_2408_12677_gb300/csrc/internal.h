@@ -132,6 +132,35 @@ constexpr int kTileSortCap = 4096;
 constexpr uint32_t kBucketCap = 1024;
 // length classes of the raster passes' visit order (four per octave)
 constexpr int kLenClasses = 129;
+
+// Turns the class counts cls[0 .. kLenClasses) into the first visit position
+// of each class, longest class first (cls[c] = sum of the counts of the
+// classes above c); run by one warp.
+__device__ __forceinline__ void class_starts_desc(uint32_t* cls) {
+  constexpr int PER = (kLenClasses + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  // lane l takes classes kLenClasses - 1 - (PER l .. PER l + PER - 1)
+  uint32_t v[PER], sum = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int c = kLenClasses - 1 - (PER * lane + j);
+    v[j] = c >= 0 ? cls[c] : 0u;
+    sum += v[j];
+  }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl += y;
+  }
+  uint32_t run = incl - sum;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int c = kLenClasses - 1 - (PER * lane + j);
+    if (c >= 0) cls[c] = run;
+    run += v[j];
+  }
+}
 struct TileBinArgs {
   int n;                      // items (views x Gaussians)
   const ushort4* rects;       // per item tile rectangle (view-local tile coordinates)
@@ -157,14 +186,12 @@ struct TileBinArgs {
   // bucket mode (nullable): the lists are the projection's per-tile buckets
   // (bucket_ids, tile t's list at t * kBucketCap, its length in counts[t]);
   // the sort files each tile under its length class (class 0: empty),
-  // cls_tiles[c * cls_stride + i] for i < cls_count[c], and its last CTA
-  // (sort_ticket: a word that is 0 between launches) turns the classes into
-  // the visit order (longest class first) in `order`
+  // cls_tiles[c * cls_stride + i] for i < cls_count[c], from which the
+  // forward raster pass takes its visit order (see RasterArgs)
   uint32_t* bucket_ids = nullptr;
   uint32_t* cls_count = nullptr;
   uint32_t* cls_tiles = nullptr;
   uint32_t cls_stride = 0;
-  uint32_t* sort_ticket = nullptr;
 };
 int tile_sort_capacity();
 int64_t tile_scan_aux_size(int64_t n_tiles);
@@ -215,6 +242,15 @@ struct RasterArgs {
   // reduction computes (it takes precedence over depth_scale)
   uint32_t* nvalid;
   float w_depth;
+  // bucket-mode visit order (forward pass, nullable): the tiles of length
+  // class c are cls_tiles[c * cls_stride + i] for i < cls_count[c]; visit k
+  // takes the longest classes first (each CTA turns the class counts into
+  // class starts once), and the warp that takes block 0 of visit k writes
+  // its tile to order_out[k], the flat order the backward pass reads
+  const uint32_t* cls_count;
+  const uint32_t* cls_tiles;
+  uint32_t cls_stride;
+  uint32_t* order_out;
   RasterView v[kMaxViews];
 };
 bool raster_shape_supported(int tw, int th);

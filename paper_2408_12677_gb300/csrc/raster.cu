@@ -102,8 +102,7 @@ struct TileJob {
   uint32_t tile;  // global tile id
 };
 template <int TW, int TH>
-__device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
-  const uint32_t tile = a.order ? a.order[k] : k;
+__device__ __forceinline__ TileJob tile_job_of(const RasterArgs& a, uint32_t tile) {
   int v = 0;
   for (int k = 1; k < a.views; ++k)
     if (tile >= a.v[k].tile_base) v = k;
@@ -112,6 +111,48 @@ __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
   uint2 r = a.ranges[tile];
   if (!in_bounds(r.x <= r.y && r.y <= a.n_ids)) r = make_uint2(0u, 0u);  // checked build: an empty list
   return TileJob{v, tx * TW, ty * TH, r, tile};
+}
+template <int TW, int TH>
+__device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
+  return tile_job_of<TW, TH>(a, a.order ? a.order[k] : k);
+}
+
+// Bucket mode: loads the class counts into s_start (kLenClasses + 1 words)
+// as s_start[c] = tiles of class c or longer (s_start[kLenClasses] = 0);
+// called by every thread of the CTA (it synchronises the CTA).
+__device__ __forceinline__ void load_class_starts(const RasterArgs& a, uint32_t* __restrict__ s_start) {
+  if (threadIdx.x < 32) {
+    constexpr int PER = (kLenClasses + 31) / 32;
+    uint32_t cnt[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int c = (int)threadIdx.x + 32 * i;
+      cnt[i] = c < kLenClasses ? a.cls_count[c] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+      if ((int)threadIdx.x + 32 * i < kLenClasses) s_start[threadIdx.x + 32 * i] = cnt[i];
+    __syncwarp();
+    class_starts_desc(s_start);  // s_start[c] = tiles of the classes above c
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+      if ((int)threadIdx.x + 32 * i < kLenClasses) s_start[threadIdx.x + 32 * i] += cnt[i];
+    if (threadIdx.x == 0) s_start[kLenClasses] = 0u;
+  }
+  __syncthreads();
+}
+
+// Bucket mode: the tile of visit k, the (k - tiles of longer classes)-th of
+// its class, c the largest class with s_start[c] > k (s_start is
+// non-increasing and s_start[0] is the tile count, which exceeds k).
+__device__ __forceinline__ uint32_t class_visit_tile(const RasterArgs& a, const uint32_t* __restrict__ s_start,
+                                                     uint32_t k) {
+  int c = 0;
+#pragma unroll
+  for (int step = 128; step > 0; step >>= 1)
+    if (c + step < kLenClasses && s_start[c + step] > k) c += step;
+  return a.cls_tiles[(size_t)c * a.cls_stride + (k - s_start[c + 1])];
 }
 
 // Front-to-back step of one pixel for one list entry (Eq. 11 with the skip
@@ -176,16 +217,16 @@ __device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
   return d;
 }
 
-// Forward pass of one 8 x 8 pixel block (quadrant `quad` of the tile of
-// visit k) by one warp; buf is the warp's shared staging buffer, s_raw the
+// Forward pass of one 8 x 8 pixel block (quadrant `quad` of global tile
+// `tile`) by one warp; buf is the warp's shared staging buffer, s_raw the
 // two shared slots per lane that its Gaussians' records land in (cp.async).
 template <int TW, int TH, bool COUNT, bool LOSS>
-__device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t k, int quad,
+__device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams& rp, uint32_t tile, int quad,
                                         Entry* __restrict__ buf, float4 (*__restrict__ s_raw)[32][3],
                                         float* __restrict__ T_final_all,
                                         int32_t* __restrict__ last_all, unsigned long long* __restrict__ counters) {
   constexpr int WX = TW / 8;
-  const TileJob job = tile_job<TW, TH>(a, k);
+  const TileJob job = tile_job_of<TW, TH>(a, tile);
   const RasterView& vw = a.v[job.v];
   const int width = vw.width, height = vw.height;
   const uint32_t* __restrict__ ids = a.ids;
@@ -386,10 +427,21 @@ __device__ __forceinline__ bool next_job(uint32_t* __restrict__ work, uint32_t n
   return job < n_jobs;
 }
 
+// The tile of forward visit k: from the class lists in bucket mode (the warp
+// on block 0 of the visit also records it in the flat order the backward
+// pass reads), else from the flat order, else tile k.
+__device__ __forceinline__ uint32_t fwd_visit_tile(const RasterArgs& a, const uint32_t* __restrict__ s_start,
+                                                   uint32_t k, int quad) {
+  if (!a.cls_count) return a.order ? a.order[k] : k;
+  const uint32_t tile = class_visit_tile(a, s_start, k);
+  if (quad == 0 && (threadIdx.x & 31) == 0) a.order_out[k] = tile;
+  return tile;
+}
+
 // PERSIST = false: one CTA per tile visit, warp w on quadrant w.  Otherwise
 // a persistent grid whose warps pull jobs from `work` with next_job.
 template <int TW, int TH, bool COUNT, bool LOSS, bool PERSIST>
-__global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
+__global__ void __launch_bounds__(kThreads, 7) raster_fwd_kernel(const __grid_constant__ RasterArgs a, RasterParams rp,
                                                               float* __restrict__ T_final_all,
                                                               int32_t* __restrict__ last_all,
                                                               unsigned long long* __restrict__ counters,
@@ -398,15 +450,20 @@ __global__ void __launch_bounds__(kThreads) raster_fwd_kernel(const __grid_const
   static_assert((TW / 8) * (TH / 8) == kThreads / 32, "four 8x8 warp blocks per tile");
   __shared__ Entry s_e[kThreads / 32][32];
   __shared__ __align__(16) float4 s_rawf[kThreads / 32][2][32][3];
+  __shared__ uint32_t s_start[kLenClasses + 1];  // bucket mode: tiles of class c or longer
   const int warp = threadIdx.x >> 5;
+  if (a.cls_count) load_class_starts(a, s_start);  // CTA-uniform
   if constexpr (!PERSIST) {
-    fwd_job<TW, TH, COUNT, LOSS>(a, rp, blockIdx.x, warp, s_e[warp], s_rawf[warp], T_final_all, last_all, counters);
+    fwd_job<TW, TH, COUNT, LOSS>(a, rp, fwd_visit_tile(a, s_start, blockIdx.x, warp), warp, s_e[warp], s_rawf[warp],
+                                 T_final_all, last_all, counters);
   } else {
     const uint32_t n_jobs = 4u * a.n_tiles;
     uint32_t job;
-    while (next_job(work, n_jobs, job))
-      fwd_job<TW, TH, COUNT, LOSS>(a, rp, job >> 2, (int)(job & 3u), s_e[warp], s_rawf[warp], T_final_all,
-                                   last_all, counters);
+    while (next_job(work, n_jobs, job)) {
+      const int quad = (int)(job & 3u);
+      fwd_job<TW, TH, COUNT, LOSS>(a, rp, fwd_visit_tile(a, s_start, job >> 2, quad), quad, s_e[warp], s_rawf[warp],
+                                   T_final_all, last_all, counters);
+    }
   }
 }
 

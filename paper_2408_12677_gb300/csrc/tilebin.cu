@@ -142,35 +142,6 @@ __device__ __forceinline__ int length_class(uint32_t c) {
   return 4 * lead + frac + 1;
 }
 
-// Turns the class counts cls[0 .. kLenClasses) into the first visit position
-// of each class, longest class first (cls[c] = sum of the counts of the
-// classes above c); run by one warp.
-__device__ __forceinline__ void class_starts_desc(uint32_t* cls) {
-  constexpr int PER = (kLenClasses + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  // lane l takes classes kLenClasses - 1 - (PER l .. PER l + PER - 1)
-  uint32_t v[PER], sum = 0;
-#pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    const int c = kLenClasses - 1 - (PER * lane + j);
-    v[j] = c >= 0 ? cls[c] : 0u;
-    sum += v[j];
-  }
-  uint32_t incl = sum;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-    if (lane >= off) incl += y;
-  }
-  uint32_t run = incl - sum;
-#pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    const int c = kLenClasses - 1 - (PER * lane + j);
-    if (c >= 0) cls[c] = run;
-    run += v[j];
-  }
-}
-
 // offsets = exclusive scan of counts (clamped to 32 bits), cursors = offsets;
 // stats[0] = total pairs, stats[1] = longest list; n_pairs = min(total, capacity).
 // order (if non-null) = the tiles by descending length class, the order in
@@ -486,7 +457,8 @@ __device__ __forceinline__ void warp_sort_list(uint32_t* __restrict__ ids, const
 // sorted one after the other by the whole CTA with a bitonic network in
 // shared memory.  The last binning kernel: it also zeroes each tile's counter
 // (and block 0 the large-splat queue length, and the two raster job counters
-// when given), leaving them zero for the next passes.
+// when given), leaving them zero for the next passes.  In bucket mode each
+// warp also files its tile under its length class (see TileBinArgs).
 template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t* __restrict__ offsets,
                                                                  uint32_t* __restrict__ counts,
@@ -498,9 +470,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
                                                                  uint32_t* __restrict__ raster_work,
                                                                  uint32_t n_items, uint32_t* __restrict__ cls_count,
                                                                  uint32_t* __restrict__ cls_tiles,
-                                                                 uint32_t cls_stride,
-                                                                 uint32_t* __restrict__ sort_ticket,
-                                                                 uint32_t* __restrict__ order) {
+                                                                 uint32_t cls_stride) {
   pdl_enter();
   const bool buckets = cls_count != nullptr;  // the lists are per-tile buckets (see TileBinArgs)
   __shared__ unsigned long long s[CAP];
@@ -579,69 +549,6 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
     for (uint32_t i = threadIdx.x; i < n; i += kSortThreads) ids[off + i] = (uint32_t)s[i];
     __syncthreads();  // s is reused by the next long list
   }
-  if (!buckets) return;
-  // bucket mode: the last CTA to finish turns the length classes into the
-  // raster passes' visit order (longest class first)
-  __shared__ bool s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();  // this CTA's class entries are visible before its ticket
-    s_last = atomicAdd(sort_ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  // One CTA does this part alone, so it is written as few dependent global
-  // round trips as possible: one for the class counts, one per 4096 tiles
-  // for the class lists.
-  uint32_t* e = reinterpret_cast<uint32_t*>(s);  // e[c]: tiles of class c or longer; e[kLenClasses] = 0
-  if (threadIdx.x < 32) {
-    constexpr int PER = (kLenClasses + 31) / 32;
-    uint32_t cnt[PER];
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-      const int c = threadIdx.x + 32 * i;
-      cnt[i] = c < kLenClasses ? __ldcg(&cls_count[c]) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < PER; ++i)
-      if (threadIdx.x + 32 * i < kLenClasses) e[threadIdx.x + 32 * i] = cnt[i];
-    __syncwarp();
-    class_starts_desc(e);  // e[c] = tiles of the classes above c
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < PER; ++i)
-      if (threadIdx.x + 32 * i < kLenClasses) e[threadIdx.x + 32 * i] += cnt[i];
-    if (threadIdx.x == 0) e[kLenClasses] = 0u;
-  }
-  __syncthreads();
-  // kOrderIlp visits per thread and round, their searches unrolled and their
-  // loads in flight together
-  constexpr int kOrderIlp = 16;
-  for (uint32_t k0 = 0; k0 < n_tiles; k0 += kSortThreads * kOrderIlp) {
-    uint32_t src[kOrderIlp];  // < kLenClasses x cls_stride, which the host keeps below 2^32
-#pragma unroll
-    for (int i = 0; i < kOrderIlp; ++i) {
-      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
-      int c = 0;  // the largest class c with e[c] > k (e is non-increasing, e[0] = n_tiles)
-#pragma unroll
-      for (int step = 128; step > 0; step >>= 1)
-        if (c + step < kLenClasses && e[c + step] > k) c += step;
-      src[i] = (uint32_t)c * cls_stride + (k - e[c + 1]);
-    }
-    uint32_t v[kOrderIlp];
-#pragma unroll
-    for (int i = 0; i < kOrderIlp; ++i) {
-      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
-      v[i] = k < n_tiles ? __ldcg(&cls_tiles[src[i]]) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < kOrderIlp; ++i) {
-      const uint32_t k = k0 + (uint32_t)(i * kSortThreads) + threadIdx.x;
-      if (k < n_tiles) order[k] = v[i];
-    }
-  }
-  if (threadIdx.x == 0) *sort_ticket = 0u;
 }
 
 int bin_grid(int n, int num_sms) {
@@ -691,7 +598,7 @@ void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   launch_pdl(tile_sort_kernel<kTileSortCap>, grid, kSortThreads, 0, s, a.offsets, a.counts,
              buckets ? a.bucket_ids : a.ids, a.zkey, a.ranges, (uint32_t)a.n_tiles, a.capacity, a.overflow,
              const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n, buckets ? a.cls_count : nullptr,
-             a.cls_tiles, a.cls_stride, a.sort_ticket, a.order);
+             a.cls_tiles, a.cls_stride);
   if (launches) *launches += 1;
 }
 
