@@ -671,7 +671,8 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 }
 
 // Backward of the projection fused with the Adam step, for one optimisation
-// iteration on a batch of views.  A block owns 128 consecutive Gaussians:
+// iteration on a batch of views.  A block (one warp) owns 32 consecutive
+// Gaussians:
 //   1. its slices of the parameter array and of the two Adam moments (each
 //      slice contiguous in the flat layout) are copied to shared memory with
 //      cp.async, the parameters as a first group and the moments as a second,
@@ -682,11 +683,9 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // No gradient buffer is written or read.  With one view the SH gradient is
 // kept in factored form (Y_k * graw_c) and the SH moments are staged too;
 // with several views the SH gradients are summed in shared memory rows and
-// the sweep reads the SH moments from global memory directly (coalesced),
-// which keeps the shared-memory footprint at three blocks per SM.
-// Gaussians (and threads) per block: 64 for one view (4 blocks of 53 KB per
-// SM, so that the staging, gradient and sweep phases of different blocks
-// overlap), 128 for several views
+// the SH moments are staged as well, beside the summed rows.  Blocks of one
+// warp (27 KB for one view, 8 blocks per SM) let the staging, gradient and
+// sweep phases of different blocks overlap.
 template <bool MULTI>
 constexpr int fused_threads() { return 32; }
 
