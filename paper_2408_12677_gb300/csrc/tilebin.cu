@@ -23,7 +23,7 @@ namespace {
 constexpr int kBinThreads = 256;
 constexpr int kBinWarps = kBinThreads / 32;
 constexpr int kScanThreads = 1024;
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 128;
 constexpr int kSortWarps = kSortThreads / 32;  // tiles per CTA of the per-tile sort
 constexpr int kWarpSortMax = 512;              // lists up to this length are sorted by one warp
 

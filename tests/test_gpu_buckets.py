@@ -206,3 +206,48 @@ def test_bucket_binning_stays_off_after_any_long_list():
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
     ctx.close()
+
+
+@pytest.mark.parametrize("which", ["single_view", "multi_view"])
+def test_bucket_binning_at_full_size(which):
+    """The bench's workloads (1200x680 with ~300k Gaussians; 8 views of
+    640x480 to 1752x1168, 7.97M pixels, 500k Gaussians): a no-sync pass
+    (bucket binning when every list of the sync pass fits half a bucket)
+    renders every pixel as the sync-mode pass does, bit for bit, and its
+    visit order is a permutation of the tiles, longest class first."""
+    import os
+    from paper_2408_12677_gb300 import abi
+    if which == "single_view":
+        w = workloads.single_view()
+    else:
+        w = workloads.multi_view(workers=min(8, os.cpu_count() or 1))
+    ctx = _ctx()
+    model = to_gpu_model(w.params)
+    T = sum(-(-v.cam.width // 16) * -(-v.cam.height // 16) for v in w.views)
+    b0 = ctx.stats()["kernel_launches"]
+    ref = _batched_render(ctx, model, w.views)
+    n_sync = ctx.stats()["kernel_launches"] - b0
+    longest = _longest_of(ctx, T)
+    _no_sync(ctx, w.n * len(w.views), sum(v.cam.width * v.cam.height for v in w.views),
+             int(abi.gs_get_stats(ctx.handle)["n_pairs"] * 1.5) + 4096)
+    b1 = ctx.stats()["kernel_launches"]
+    got = _batched_render(ctx, model, w.views)
+    n_no_sync = ctx.stats()["kernel_launches"] - b1
+    abi.gs_sync_status(ctx.handle)
+    check_visit_order(ctx, T)
+    if longest <= 512:  # bucket binning engaged: no count, scan or scatter launch
+        assert n_no_sync < n_sync
+    for (a0, a1, a2), (b0, b1, b2) in zip(got, ref):
+        np.testing.assert_array_equal(a0, b0)
+        np.testing.assert_array_equal(a1, b1)
+        np.testing.assert_array_equal(a2, b2)
+    ctx.close()
+
+
+def _longest_of(ctx, n_tiles):
+    from paper_2408_12677_gb300 import abi
+    r = torch.empty((n_tiles, 2), dtype=torch.int32, device="cuda")
+    abi.gs_get_tile_ranges(ctx.handle, r)
+    torch.cuda.synchronize()
+    r = r.cpu().numpy().view(np.uint32).astype(np.int64)
+    return int((r[:, 1] - r[:, 0]).max())
