@@ -44,10 +44,6 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# stages launched on the context's side stream by gs_train_step
-SIDE_STAGES = ("loss",)
-
-
 # ---------------------------------------------------------------------------
 # algorithmic traffic and work per launch
 # ---------------------------------------------------------------------------
@@ -328,17 +324,10 @@ def run_ours(args, rank, world, local_rank):
     alg = algorithmic_bytes(w.n, w.sh_degree, pairs, npx, n_tiles)
     per_stage = {k: {"ms_per_launch": (ms / c if c else 0.0), "launches": c, "share": None}
                  for k, (ms, c) in stages.items()}
-    # gs_train_step runs the loss reduction on the context's side stream,
-    # beside the backward raster pass: its event interval includes the wait
-    # for SMs that pass holds, so it is left out of the shares
-    main = {k: v for k, v in stages.items() if k not in SIDE_STAGES}
-    tot_stage = sum(ms for ms, _ in main.values())
-    for k, (ms, c) in main.items():
+    tot_stage = sum(ms for ms, _ in stages.values())
+    for k, (ms, c) in stages.items():
         per_stage[k]["share"] = ms / tot_stage if tot_stage else None
-    for k in SIDE_STAGES:
-        if k in per_stage:
-            per_stage[k]["stream"] = "side (beside raster_bwd; interval includes waiting for its SMs)"
-    dom = max(main, key=lambda k: main[k][0])
+    dom = max(stages, key=lambda k: stages[k][0])
     hbm_peak, peak_kind = load_peaks()
     dom_ms = per_stage[dom]["ms_per_launch"]
     traffic = load_traffic(dom)

@@ -75,10 +75,6 @@ struct gs_ctx {
   float* tile_loss = nullptr;  // per (tile, 8 x 8 block): fused-loss partial sums (3 floats)
   float* d_dscale = nullptr;   // per view: depth-gradient scale of the fused loss
   uint32_t* d_nvalid = nullptr;  // per view: target depths > 0 seen by the fused-loss forward pass
-  // the training step's loss reduction runs on a side stream beside the
-  // backward pass (fork and join events on the caller's stream)
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // per-frame seeding scratch
   int64_t cap_qt = 0;
   int2* qt_cells[2] = {nullptr, nullptr};
@@ -629,9 +625,6 @@ gs_status gs_ctx_create(gs_ctx** out, int device, int64_t pair_capacity) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_dscale, kMaxViews * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_nvalid, kMaxViews * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_nvalid, 0, kMaxViews * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_bigmeta, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_bigmeta, 0, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(c->d_step, 0, sizeof(long long));
@@ -696,9 +689,6 @@ gs_status gs_ctx_destroy(gs_ctx* c) {
   cudaFree(c->bids);
   cudaFree(c->cls_count);
   cudaFree(c->cls_tiles);
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->side) cudaStreamDestroy(c->side);
   cudaFree(c->qt_cells[0]);
   cudaFree(c->qt_cells[1]);
   cudaFree(c->qt_leaves);
@@ -987,6 +977,7 @@ struct FusedLoss {
   const float* const* trgb;
   const float* const* tdep;
   float w_color;
+  long long* step;  // nullable: the device Adam step, advanced by the projection
 };
 
 gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs_camera* cams,
@@ -1017,6 +1008,7 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   pa.big_len = c->d_bigmeta;
   pa.counts = c->tcount;  // the projection counts every rectangle's tiles
   pa.nvalid = fl ? c->d_nvalid : nullptr;  // zeroed by the projection for the fused loss's count
+  pa.step_inc = fl ? fl->step : nullptr;
   const bool buckets = !c->sync && c->bucket_ok && (int64_t)L.tiles <= c->cap_bt;
   if (buckets) {  // and writes every pair into its tile's bucket
     pa.bucket_ids = c->bids;
@@ -1154,6 +1146,13 @@ gs_status raster_backward(gs_ctx* c, const gs_raster_cfg* cfg, const float* cons
   return GS_OK;
 }
 
+// The training step's loss, reduced by the fused backward + Adam kernel
+// (LossFoldArgs): the caller's loss word and the weights.
+struct LossFold {
+  float* loss;
+  float w_color, w_depth;
+};
+
 gs_status check_adam(gs_ctx* c, const gs_adam_cfg* cfg, int64_t step, bool allow_device_step = false) {
   if (!cfg || step < (allow_device_step ? 0 : 1)) return fail(c, GS_ERR_INVALID_ARG, "Adam: bad cfg or step");
   if (!(cfg->beta1 >= 0.f && cfg->beta1 < 1.f && cfg->beta2 >= 0.f && cfg->beta2 < 1.f && cfg->eps >= 0.f))
@@ -1190,7 +1189,8 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
                                 const float* const* dL_ddepth, const float* const* dL_dalpha, float* params,
                                 float* m, float* v, const gs_adam_cfg* adam, int64_t step, float* dL_dpose,
                                 cudaStream_t s, const float* depth_scale = nullptr, bool step_advanced = false,
-                                const float* nvalid_w_depth = nullptr, cudaEvent_t before_adam = nullptr) {
+                                const float* nvalid_w_depth = nullptr, const LossFold* lf = nullptr) {
+  // lf: the training step's loss, reduced by the fused kernel's first blocks
   gs_status st;
   if ((st = check_bwd_views(c, g, V, cams, views, cfg, dL_dcolor, dL_ddepth)) != GS_OK) return st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
@@ -1201,23 +1201,43 @@ gs_status render_bwd_adam_views(gs_ctx* c, const gs_gaussians* g, int32_t V, con
     return fail(c, GS_ERR_INVALID_ARG, "the Gaussian arrays must be the flat parameter buffer's blocks");
   GS_CUDA(c, cudaSetDevice(c->device));
   if (n == 0) return GS_OK;
-  st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s, depth_scale, nvalid_w_depth);
-  // the work the Adam update waits for on another stream (the loss reduction
-  // that advances the device step) joins here, also when the backward failed
-  if (before_adam) GS_CUDA(c, cudaStreamWaitEvent(s, before_adam, 0));
-  if (st != GS_OK) return st;
+  if ((st = raster_backward(c, cfg, dL_dcolor, dL_ddepth, dL_dalpha, s, depth_scale, nvalid_w_depth)) != GS_OK)
+    return st;
   const ProjectArgs pa = project_args(g, V, cams, views, cfg, c->st_map, c->st_map.tiles_x);
   {
     StageTimer t(c, GS_STAGE_PROJECT_BWD, s);
     AdamArgs ad = adam_args(adam, step);
     if (step == 0) {
-      if (!step_advanced) {  // (the training step's loss launch has advanced it)
+      if (!step_advanced) {  // (the training step's projection has advanced it)
         launch_step_increment(c->d_step, s);
         c->launches += 1;
       }
       ad.step_dev = c->d_step;
     }
-    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, dL_dpose ? c->pose_partials : nullptr, s);
+    LossFoldArgs L{};
+    if (lf) {  // the forward pass's loss partials (per tile and 8 x 8 block)
+      L.partials = c->tile_loss;
+      L.blk = c->loss_partials;
+      L.out = lf->loss;
+      L.scale = c->d_dscale;
+      L.ticket = c->d_bigmeta + 3;
+      L.w_color = lf->w_color;
+      L.w_depth = lf->w_depth;
+      L.views = c->st_views;
+      int blocks = 0;
+      for (int k = 0; k < c->st_views; ++k) {
+        const int64_t t1 = k + 1 < c->st_views ? (int64_t)c->st_map.tile_base[k + 1] : c->st_tiles;
+        L.block_base[k] = blocks;
+        L.job_base[k] = 4u * c->st_map.tile_base[k];
+        L.job_base[k + 1] = (uint32_t)(4 * t1);
+        L.npix[k] = (float)c->st_w[k] * (float)c->st_h[k];
+        blocks += (int)((4 * (t1 - (int64_t)c->st_map.tile_base[k]) + kLossChunk - 1) / kLossChunk);
+      }
+      L.block_base[c->st_views] = blocks;
+      L.blocks = blocks;
+    }
+    const int nb = launch_project_bwd_adam(pa, c->g2d, params, m, v, ad, dL_dpose ? c->pose_partials : nullptr, s,
+                                           lf ? &L : nullptr);
     c->launches += 1;
     if (dL_dpose) {
       launch_pose_reduce(c->pose_partials, nb, V, dL_dpose, s);
@@ -1317,28 +1337,26 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   if (!std::isfinite(w_color) || !std::isfinite(w_depth)) return fail(c, GS_ERR_INVALID_ARG, "non-finite weight");
   gs_status st;
   if ((st = check_adam(c, adam, step, true)) != GS_OK) return st;
-  const FusedLoss fl{target_rgb, target_depth, w_color};
+  // The device step counter (step = 0) is advanced by the projection, and
+  // the loss is reduced by the fused backward + Adam kernel's first blocks
+  // before their own work: the backward raster pass takes its depth scale
+  // from the forward pass's count of valid target depths, so only the
+  // reported loss needs the reduction.  Without Gaussians neither kernel
+  // runs, and one kernel reduces the loss and advances the step.
+  const FusedLoss fl{target_rgb, target_depth, w_color, step == 0 && g->n > 0 ? c->d_step : nullptr};
   if ((st = render_fwd_views(c, g, V, cams, views, cfg, color, depth, alpha, s, &fl)) != GS_OK) return st;
-  RasterArgs ra = raster_args(c, cfg);
-  ra.loss_partials = c->tile_loss;
-  ra.w_color = w_color;
-  // The loss reduction (which also advances the device step counter when
-  // step = 0) runs on the side stream, beside the backward pass: the
-  // backward pass takes its depth scale from the forward pass's count of
-  // valid target depths, and only the Adam update waits for the reduction.
-  GS_CUDA(c, cudaEventRecord(c->ev_fork, s));
-  GS_CUDA(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-  {
-    StageTimer t(c, GS_STAGE_LOSS, c->side);
-    launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, c->d_bigmeta + 3,
-                               step == 0 ? c->d_step : nullptr, c->side, &c->launches);
+  if (g->n == 0) {
+    RasterArgs ra = raster_args(c, cfg);
+    ra.loss_partials = c->tile_loss;
+    ra.w_color = w_color;
+    {
+      StageTimer t(c, GS_STAGE_LOSS, s);
+      launch_loss_tiles_finalize(ra, w_depth, loss, c->d_dscale, c->loss_partials, c->d_bigmeta + 3,
+                                 step == 0 ? c->d_step : nullptr, s, &c->launches);
+    }
+    GS_CHECK_LAUNCH(c, "loss finalize");
   }
-  const cudaError_t le = cudaGetLastError();
-  GS_CUDA(c, cudaEventRecord(c->ev_join, c->side));
-  if (le != cudaSuccess) {
-    GS_CUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
-    return cuda_fail(c, le, "loss finalize");
-  }
+  const LossFold lf{loss, w_color, w_depth};
   const float* dlc[kMaxViews];
   const float* dld[kMaxViews];
   for (int k = 0; k < V; ++k) {
@@ -1347,7 +1365,7 @@ gs_status train_step_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
     dld[k] = c->dl_img + 4 * c->st_pix_base[k] + 3 * np;
   }
   return render_bwd_adam_views(c, g, V, cams, views, cfg, dlc, dld, nullptr, params, m, v, adam, step, nullptr, s,
-                               nullptr, /*step_advanced=*/true, &w_depth, c->ev_join);
+                               nullptr, /*step_advanced=*/true, &w_depth, &lf);
 }
 
 }  // namespace

@@ -56,6 +56,9 @@ struct ProjectArgs {
   uint32_t* bucket_ids = nullptr;
   uint32_t* overflow = nullptr;
   uint32_t* cls_count = nullptr;
+  // training step (nullable): block 0 advances the device Adam step that
+  // the iteration's fused backward + Adam reads
+  long long* step_inc = nullptr;
 };
 
 // projection (Eq. 2-5) -> features, depth keys, tile rects, tile counts
@@ -81,6 +84,27 @@ struct AdamArgs {
   const long long* step_dev;  // device step counter (bias corrections computed on the device), or null
   float log_beta1, log_beta2;  // log(beta) for the device-side bias corrections
 };
+// The training step's loss reduction, done by the fused backward + Adam
+// kernel's first blocks before their own work (out nullable): reduction
+// block b (of `blocks`; view v's from block_base[v]) sums kLossChunk
+// consecutive (tile, 8 x 8 block) partials {|colour residual|, |depth
+// residual| over valid targets, valid count} of one view, starting at
+// job_base[v] + (b - block_base[v]) kLossChunk, into blk[3 b + k] in a fixed
+// order; the block completing the last one (ticket: 0 between launches)
+// sums them per view into *out and the depth scales scale[v].
+struct LossFoldArgs {
+  const float* partials;
+  float* blk;
+  float* out;
+  float* scale;
+  uint32_t* ticket;
+  float w_color, w_depth;
+  int views, blocks;
+  int block_base[kMaxViews + 1];
+  uint32_t job_base[kMaxViews + 1];
+  float npix[kMaxViews];
+};
+constexpr int kLossChunk = 2048;
 // device step counter: *step += 1
 void launch_step_increment(long long* step, cudaStream_t s);
 // set once per context: shared-memory limits of the fused kernel
@@ -88,7 +112,8 @@ void init_project_kernels();
 // fused projection backward + Adam over the flat buffer (gradients summed
 // over the views, one step)
 int launch_project_bwd_adam(const ProjectArgs& a, float4* g2d, float* params, float* m, float* v,
-                            const AdamArgs& ad, float* pose_partials, cudaStream_t s);
+                            const AdamArgs& ad, float* pose_partials, cudaStream_t s,
+                            const LossFoldArgs* loss = nullptr);
 int project_bwd_blocks(int n);
 
 // Stable radix sort of (u32 key, u32 value) pairs on the low `bits` bits.

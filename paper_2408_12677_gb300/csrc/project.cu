@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
     if (a.nvalid && threadIdx.x < (unsigned)a.views) a.nvalid[threadIdx.x] = 0u;
     if (a.cls_count)
       for (int c = threadIdx.x; c < kLenClasses; c += kFwdThreads) a.cls_count[c] = 0u;
+    if (a.step_inc && threadIdx.x == 0) *a.step_inc += 1;
   }
   // the block's slices of every parameter array are contiguous: stage them
   // all at once with coalesced asynchronous copies
@@ -688,6 +689,8 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
 // sweep phases of different blocks overlap.
 template <bool MULTI>
 constexpr int fused_threads() { return 32; }
+static_assert(fused_threads<false>() == 32 && fused_threads<true>() == 32,
+              "the fused loss reduction takes one warp per block");
 
 template <int D>
 struct FusedSmem {
@@ -715,13 +718,75 @@ struct FusedSmemMulti {
   float sm[B * NS + 4], sv[B * NS + 4];  // SH moments
 };
 
+// The training step's loss reduction (see LossFoldArgs), by one warp per
+// reduction block: kLossChunk / 32 partials per lane in a fixed order, then
+// over the warp; the warp completing the last block sums the blocks per
+// view (per lane, then over the warp).  Warp-uniform.
+__device__ __forceinline__ void fused_loss_reduce(const LossFoldArgs& L) {
+  const int lane = threadIdx.x & 31;
+  for (int lb = blockIdx.x; lb < L.blocks; lb += gridDim.x) {
+    int v = 0;
+    for (int k = 1; k < L.views; ++k)
+      if (lb >= L.block_base[k]) v = k;
+    const uint32_t lo = L.job_base[v] + (uint32_t)(lb - L.block_base[v]) * kLossChunk;
+    const uint32_t hi = min(lo + (uint32_t)kLossChunk, L.job_base[v + 1]);
+    float sc = 0.f, sd = 0.f, nv = 0.f;
+#pragma unroll 8
+    for (uint32_t i = lo + lane; i < hi; i += 32) {
+      sc += L.partials[3 * (size_t)i];
+      sd += L.partials[3 * (size_t)i + 1];
+      nv += L.partials[3 * (size_t)i + 2];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sc += __shfl_xor_sync(0xFFFFFFFFu, sc, off);
+      sd += __shfl_xor_sync(0xFFFFFFFFu, sd, off);
+      nv += __shfl_xor_sync(0xFFFFFFFFu, nv, off);
+    }
+    uint32_t last = 0u;
+    if (lane == 0) {
+      L.blk[3 * lb] = sc;
+      L.blk[3 * lb + 1] = sd;
+      L.blk[3 * lb + 2] = nv;
+      __threadfence();  // this block's sums are visible before its ticket
+      last = atomicAdd(L.ticket, 1u) == (uint32_t)L.blocks - 1u ? 1u : 0u;
+    }
+    if (!__shfl_sync(0xFFFFFFFFu, last, 0)) continue;
+    __threadfence();
+    float total = 0.f;
+    for (int w = 0; w < L.views; ++w) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+      for (int b = L.block_base[w] + lane; b < L.block_base[w + 1]; b += 32) {
+        s0 += __ldcg(&L.blk[3 * b]);
+        s1 += __ldcg(&L.blk[3 * b + 1]);
+        s2 += __ldcg(&L.blk[3 * b + 2]);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, off);
+        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, off);
+        s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, off);
+      }
+      const float nvw = s2 > 0.f ? s2 : 1.f;
+      total += L.w_color * s0 / (3.f * L.npix[w]) + L.w_depth * s1 / nvw;
+      if (lane == 0) L.scale[w] = L.w_depth / nvw;
+    }
+    if (lane == 0) {
+      *L.out = total;
+      *L.ticket = 0u;
+    }
+  }
+}
+
 template <int D, bool MULTI>
 __global__ void __launch_bounds__(fused_threads<MULTI>()) project_bwd_adam_kernel(const __grid_constant__ ProjectArgs a,
                                                                          float4* __restrict__ g2d,
                                                                          float* __restrict__ P, float* __restrict__ M,
                                                                          float* __restrict__ V, AdamArgs ad,
-                                                                         float* __restrict__ pose_partials) {
+                                                                         float* __restrict__ pose_partials,
+                                                                         const __grid_constant__ LossFoldArgs L) {
   pdl_enter();
+  if (L.out && threadIdx.x < 32) fused_loss_reduce(L);  // blocks of one warp: the whole block
   device_bias_corrections(ad);
   using S = typename std::conditional<MULTI, FusedSmemMulti<D>, FusedSmem<D>>::type;
   constexpr int K = S::K, NS = S::NS, RS = S::RS, B = S::B;
@@ -954,13 +1019,15 @@ int launch_project_bwd(const ProjectArgs& a, float4* g2d, float* g_means, float*
 }
 
 int launch_project_bwd_adam(const ProjectArgs& a, float4* g2d, float* params, float* m, float* v,
-                            const AdamArgs& ad, float* pose_partials, cudaStream_t s) {
+                            const AdamArgs& ad, float* pose_partials, cudaStream_t s, const LossFoldArgs* loss) {
   if (a.n <= 0) return 0;
   const int bt = a.views == 1 ? fused_threads<false>() : fused_threads<true>();
   const int nb = (a.n + bt - 1) / bt;
+  LossFoldArgs L{};
+  if (loss) L = *loss;
 #define GS_FUSED(D_, M_, S_)                                                                                  \
   launch_pdl(project_bwd_adam_kernel<D_, M_>, nb, fused_threads<M_>(), sizeof(S_<D_>), s, a, g2d, params, m, v, ad, \
-             pose_partials)
+             pose_partials, L)
   if (a.views == 1) {
     switch (a.sh_degree) {
       case 0: GS_FUSED(0, false, FusedSmem); break;
