@@ -108,13 +108,13 @@ __device__ __forceinline__ TileJob tile_job_of(const RasterArgs& a, uint32_t til
     if (tile >= a.v[k].tile_base) v = k;
   const int lt = (int)(tile - a.v[v].tile_base);
   const int tx = lt % a.v[v].tiles_x, ty = lt / a.v[v].tiles_x;
-  uint2 r = a.ranges[tile];
+  uint2 r = __ldg(&a.ranges[tile]);
   if (!in_bounds(r.x <= r.y && r.y <= a.n_ids)) r = make_uint2(0u, 0u);  // checked build: an empty list
   return TileJob{v, tx * TW, ty * TH, r, tile};
 }
 template <int TW, int TH>
 __device__ __forceinline__ TileJob tile_job(const RasterArgs& a, uint32_t k) {
-  return tile_job_of<TW, TH>(a, a.order ? a.order[k] : k);
+  return tile_job_of<TW, TH>(a, a.order ? __ldg(&a.order[k]) : k);
 }
 
 // Bucket mode: loads the class counts into s_start (kLenClasses + 1 words)
@@ -127,7 +127,7 @@ __device__ __forceinline__ void load_class_starts(const RasterArgs& a, uint32_t*
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int c = (int)threadIdx.x + 32 * i;
-      cnt[i] = c < kLenClasses ? a.cls_count[c] : 0u;
+      cnt[i] = c < kLenClasses ? __ldg(&a.cls_count[c]) : 0u;
     }
 #pragma unroll
     for (int i = 0; i < PER; ++i)
@@ -152,7 +152,7 @@ __device__ __forceinline__ uint32_t class_visit_tile(const RasterArgs& a, const 
 #pragma unroll
   for (int step = 128; step > 0; step >>= 1)
     if (c + step < kLenClasses && s_start[c + step] > k) c += step;
-  return a.cls_tiles[(size_t)c * a.cls_stride + (k - s_start[c + 1])];
+  return __ldg(&a.cls_tiles[(size_t)c * a.cls_stride + (k - s_start[c + 1])]);
 }
 
 // Front-to-back step of one pixel for one list entry (Eq. 11 with the skip
@@ -252,14 +252,14 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
   // software pipeline: chunk c's records in shared memory, chunk c + 32's in
   // flight (cp.async), the ids of chunk c + 64 in a register
   int cur = 0;
-  if (lane < n) cp_record(s_raw[0][lane], feat, checked_id(ids[r.x + lane], a.n_items));
+  if (lane < n) cp_record(s_raw[0][lane], feat, checked_id(__ldg(&ids[r.x + lane]), a.n_items));
   cp_commit();
-  uint32_t g2 = 32 + lane < n ? checked_id(ids[r.x + 32 + lane], a.n_items) : 0u;
+  uint32_t g2 = 32 + lane < n ? checked_id(__ldg(&ids[r.x + 32 + lane]), a.n_items) : 0u;
   for (int c0 = 0; c0 < n; c0 += 32, cur ^= 1) {
     if (__all_sync(kFull, done0 && done1)) break;
     if (c0 + 32 + lane < n) cp_record(s_raw[cur ^ 1][lane], feat, g2);
     cp_commit();
-    if (c0 + 64 + lane < n) g2 = checked_id(ids[r.x + c0 + 64 + lane], a.n_items);
+    if (c0 + 64 + lane < n) g2 = checked_id(__ldg(&ids[r.x + c0 + 64 + lane]), a.n_items);
     cp_wait_prev();
     const bool have = c0 + lane < n;
     Entry e;
@@ -386,11 +386,11 @@ __device__ __forceinline__ void fwd_job(const RasterArgs& a, const RasterParams&
       const float col[3] = {Rc + T * rp.bg[0], Gc + T * rp.bg[1], Bc + T * rp.bg[2]};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float r = col[c] - trgb[(size_t)c * HW + p];
+        const float r = col[c] - __ldg(&trgb[(size_t)c * HW + p]);
         sc += fabsf(r);
         ldc[(size_t)c * HW + p] = gscale_c * (float)((r > 0.f) - (r < 0.f));
       }
-      const float td = tdep[p];
+      const float td = __ldg(&tdep[p]);
       const bool valid = td > 0.f;
       const float rd = D - td;
       sd += valid ? fabsf(rd) : 0.f;
