@@ -154,3 +154,60 @@ def test_train_step_matches_three_calls(ctx, deg, seed):
             xa, ya = x.cpu().numpy(), y.cpu().numpy()
             bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
             assert bad.sum() <= max(2, int(1e-4 * xa.size)), (name, step, int(bad.sum()))
+
+
+def test_train_step_device_step_and_empty_map(ctx):
+    """gs_train_step with step = 0 takes the Adam step from the context's
+    device counter, which the projection advances once per call: three such
+    calls from counter 0 give the parameters, moments and losses of explicit
+    steps 1, 2, 3.  With no Gaussians the loss is still reduced (of the
+    background image) and the counter still advances."""
+    from paper_2408_12677_gb300 import abi
+    from paper_2408_12677_gb300.torch_api import GaussianModel, camera_struct
+    from synth import workloads
+    from synth.scene import Camera, look_at
+    cam = Camera(80.0, 75.0, 40.0, 30.0, 84, 60)
+    pose = look_at([0.1, 0.2, -0.1], [0.7, 3.0, 0.2])
+    P = workloads.random_gaussians(np.random.default_rng(8), 600, cam, pose, 1, log_scale_range=(-3.5, -1.5),
+                                   sh_rest_std=0.15)
+    rng = np.random.default_rng(9)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda")
+    trgb = t(rng.uniform(0, 1, (3, 60, 84)))
+    tdep = t(rng.uniform(0.5, 4.0, (60, 84)))
+    A, B = GaussianModel(P), GaussianModel(P)
+    camS, view, rcfg, acfg = camera_struct(cam), abi.make_viewmat(pose.R, pose.t), abi.raster_cfg(), abi.adam_cfg()
+    la, lb = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    abi.gs_ctx_set_adam_step(ctx.handle, 0)
+    for step in range(1, 4):
+        abi.gs_train_step(ctx.handle, A.gaussians(), camS, view, rcfg, trgb, tdep, 0.8, 0.2, la, A.flat, A.m, A.v,
+                          acfg, step)
+        abi.gs_train_step(ctx.handle, B.gaussians(), camS, view, rcfg, trgb, tdep, 0.8, 0.2, lb, B.flat, B.m, B.v,
+                          acfg, 0)
+        torch.cuda.synchronize()
+        assert abs(float(la.item()) - float(lb.item())) <= 1e-6 * abs(float(la.item()))
+        for name, x, y in (("p", A.flat, B.flat), ("m", A.m, B.m), ("v", A.v, B.v)):
+            xa, ya = x.cpu().numpy(), y.cpu().numpy()
+            bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
+            assert bad.sum() <= max(2, int(1e-4 * xa.size)), (name, step, int(bad.sum()))
+    # an empty map: the loss of the background image, and the counter moves on to 4
+    empty = {"means": np.zeros((0, 3), np.float32), "log_scales": np.zeros((0, 3), np.float32),
+             "quats": np.zeros((0, 4), np.float32), "opacity_logits": np.zeros(0, np.float32),
+             "sh": np.zeros((0, 4, 3), np.float32), "sh_degree": 1}
+    E = GaussianModel(empty)
+    le = torch.full((1,), -1.0, device="cuda")
+    abi.gs_train_step(ctx.handle, E.gaussians(), camS, view, abi.raster_cfg(bg=(0.25, 0.5, 0.75)), trgb, tdep, 0.8,
+                      0.2, le, E.flat, E.m, E.v, acfg, 0)
+    torch.cuda.synchronize()
+    bg = np.array([0.25, 0.5, 0.75], np.float64)[:, None, None]
+    want = 0.8 * np.abs(bg - trgb.cpu().numpy().astype(np.float64)).mean() + \
+        0.2 * np.abs(tdep.cpu().numpy().astype(np.float64)).mean()  # rendered depth 0, every target valid
+    assert abs(float(le.item()) - want) <= 1e-5 * want
+    # the fourth device step: one more step = 0 call equals explicit step 5 after a step-4 call
+    abi.gs_train_step(ctx.handle, A.gaussians(), camS, view, rcfg, trgb, tdep, 0.8, 0.2, la, A.flat, A.m, A.v,
+                      acfg, 5)
+    abi.gs_train_step(ctx.handle, B.gaussians(), camS, view, rcfg, trgb, tdep, 0.8, 0.2, lb, B.flat, B.m, B.v,
+                      acfg, 0)
+    torch.cuda.synchronize()
+    xa, ya = A.flat.cpu().numpy(), B.flat.cpu().numpy()
+    bad = np.abs(xa - ya) > 1e-5 * np.abs(xa) + 1e-6 * np.abs(xa).max() + 1e-12
+    assert bad.sum() <= max(2, int(1e-4 * xa.size))
