@@ -149,11 +149,12 @@ gs_status gs_ctx_reserve(gs_ctx *ctx, int64_t n_gaussians, int64_t n_pixels, int
  * (stream-capturable); pairs beyond the reserved capacity are dropped and
  * the next gs_render_fwd / gs_sync_status reports GS_ERR_CAPACITY.  While
  * every tile list that the context's sync-mode passes have seen is at most
- * 512 entries long, sync = 0 passes bin into fixed per-tile buckets of 1024
- * entries written by the projection (no scan or scatter launch; the same
- * lists and images); a list that outgrows its bucket is reported by
- * gs_sync_status as GS_ERR_CAPACITY, after which the context bins by
- * counting and scatter (a captured graph has to be recaptured). */
+ * 2048 entries long, sync = 0 passes bin into per-tile buckets written by
+ * the projection (no scan or scatter launch; the same lists and images),
+ * each bucket twice as long as the longest list seen, rounded up to a
+ * power of two from 1024 to 4096; a list that outgrows its bucket is
+ * reported by gs_sync_status as GS_ERR_CAPACITY, after which the context
+ * bins by counting and scatter (a captured graph has to be recaptured). */
 gs_status gs_ctx_set_sync(gs_ctx *ctx, int sync);
 
 /* Set the context's device-side Adam step counter (used by

@@ -119,7 +119,7 @@ struct gs_ctx {
   int st_pair_buf = 0;
   bool st_ordered = false;  // torder holds the visit order of the last forward pass
   // Graph-mode (no-sync) binning into per-tile buckets: the projection writes
-  // each pair straight into its tile's bucket (kBucketCap entries), the
+  // each pair straight into its tile's bucket (bucket_cap entries), the
   // per-tile sort sorts the buckets in place and files every tile under its
   // length class (cls_count / cls_tiles); the forward raster pass takes its
   // visit order from the classes and records it in torder for the backward
@@ -129,7 +129,9 @@ struct gs_ctx {
   // renders several views or maps must not take one view's short lists for
   // another's); a bucket overflow clears bucket_ok for good (reported as
   // GS_ERR_CAPACITY).
-  uint32_t* bids = nullptr;       // cap_bt * kBucketCap
+  uint32_t* bids = nullptr;       // bids_words >= cap_bt * bucket_cap
+  int64_t bids_words = 0;
+  uint32_t bucket_cap = 0;        // entries per tile bucket: a power of two in [kBucketCapMin, kBucketCapMax]
   uint32_t* cls_count = nullptr;  // kLenClasses
   uint32_t* cls_tiles = nullptr;  // kLenClasses * cap_bt
   int64_t cap_bt = 0;
@@ -263,16 +265,23 @@ gs_status ensure_pairs(gs_ctx* c, int64_t p) {
   return GS_OK;
 }
 
-// Bucket storage for t tiles (see bids); synchronises when it grows.
-gs_status ensure_buckets(gs_ctx* c, int64_t t) {
-  if (t <= c->cap_bt) return GS_OK;
+// Bucket storage for t tiles of `entries` each (see bids); synchronises
+// when it grows.
+gs_status ensure_buckets(gs_ctx* c, int64_t t, uint32_t entries) {
+  const int64_t tiles = t <= c->cap_bt ? c->cap_bt : grow_target(t, c->cap_bt);
+  if (tiles == c->cap_bt && tiles * (int64_t)entries <= c->bids_words) {
+    c->bucket_cap = entries;
+    return GS_OK;
+  }
   if (injected_alloc_failure(c)) return fail(c, GS_ERR_OOM, "injected allocation failure");
   GS_CUDA(c, cudaDeviceSynchronize());
-  const int64_t cap = grow_target(t, c->cap_bt);
-  GS_GROW(c, cap_bt, regrow(&c->bids, cap * (int64_t)kBucketCap));
-  GS_GROW(c, cap_bt, regrow(&c->cls_tiles, cap * (int64_t)kLenClasses));
+  c->bids_words = 0;
+  GS_GROW(c, cap_bt, regrow(&c->bids, tiles * (int64_t)entries));
+  c->bids_words = tiles * (int64_t)entries;
+  if (tiles != c->cap_bt) GS_GROW(c, cap_bt, regrow(&c->cls_tiles, tiles * (int64_t)kLenClasses));
   if (!c->cls_count) GS_GROW(c, cap_bt, regrow(&c->cls_count, (int64_t)kLenClasses));
-  c->cap_bt = cap;
+  c->cap_bt = tiles;
+  c->bucket_cap = entries;
   return GS_OK;
 }
 
@@ -485,6 +494,7 @@ gs_status bin_buckets(gs_ctx* c, int n, const TileMap& map, cudaStream_t s) {
   tb.scan_aux = nullptr;
   tb.raster_work = c->persistent ? c->d_bigmeta + 1 : nullptr;
   tb.bucket_ids = c->bids;
+  tb.bucket_cap = c->bucket_cap;
   tb.cls_count = c->cls_count;
   tb.cls_tiles = c->cls_tiles;
   tb.cls_stride = (uint32_t)c->cap_bt;
@@ -545,10 +555,14 @@ gs_status bin_and_sort(gs_ctx* c, int n, const TileMap& map, cudaStream_t s, boo
     P = (int64_t)c->h_pinned[0];
     const int64_t longest = (int64_t)c->h_pinned[1];
     // graph-mode passes may bin into buckets while every list any sync pass
-    // has seen fits half of one
+    // has seen fits half of one; a bucket holds twice the longest of them,
+    // rounded up to a power of two (at least kBucketCapMin)
     c->longest_seen = std::max(c->longest_seen, longest);
-    c->bucket_ok = c->longest_seen <= (int64_t)kBucketCap / 2 && T * (int64_t)kBucketCap < ((int64_t)1 << 32) &&
-                   ensure_buckets(c, T) == GS_OK && c->cap_bt * (int64_t)kLenClasses < ((int64_t)1 << 32);
+    int64_t entries = kBucketCapMin;
+    while (entries < 2 * c->longest_seen && entries < (int64_t)kBucketCapMax) entries *= 2;
+    c->bucket_ok = c->longest_seen <= entries / 2 && T * entries < ((int64_t)1 << 32) &&
+                   ensure_buckets(c, T, (uint32_t)entries) == GS_OK &&
+                   c->cap_bt * (int64_t)kLenClasses < ((int64_t)1 << 32);
     if (longest > tile_sort_capacity()) return bin_and_sort_radix(c, n, map, s);
     gs_status st = ensure_pairs(c, std::max<int64_t>(P, 1));
     if (st != GS_OK) return st;
@@ -771,7 +785,7 @@ gs_status gs_sync_status(gs_ctx* c, gs_stream_t stream) {
     c->have_state = false;
     c->bucket_ok = false;
     c->longest_seen = std::numeric_limits<int64_t>::max();
-    return fail(c, GS_ERR_CAPACITY, "a tile list outgrew its bucket (" + std::to_string(kBucketCap) +
+    return fail(c, GS_ERR_CAPACITY, "a tile list outgrew its bucket (" + std::to_string(c->bucket_cap) +
                                         " entries) in graph-mode binning; recapture to bin by counting and scatter");
   }
   if (ov) {
@@ -940,7 +954,7 @@ RasterArgs raster_args(gs_ctx* c, const gs_raster_cfg* cfg) {
   ra.ranges = c->ranges;
   ra.ids = c->st_buckets ? c->bids : c->pv[c->st_pair_buf];
   ra.feat = c->feat;
-  ra.n_ids = (uint32_t)std::min<int64_t>(c->st_buckets ? c->cap_bt * (int64_t)kBucketCap : c->cap_p, 0xFFFFFFFFll);
+  ra.n_ids = (uint32_t)std::min<int64_t>(c->st_buckets ? c->cap_bt * (int64_t)c->bucket_cap : c->cap_p, 0xFFFFFFFFll);
   ra.n_items = (uint32_t)(c->st_n * c->st_views);
   ra.order = c->st_ordered ? c->torder : nullptr;
   ra.work = c->persistent ? c->d_bigmeta + 1 : nullptr;  // the forward counter; the backward pass uses [2]
@@ -1012,6 +1026,7 @@ gs_status render_fwd_views(gs_ctx* c, const gs_gaussians* g, int32_t V, const gs
   const bool buckets = !c->sync && c->bucket_ok && (int64_t)L.tiles <= c->cap_bt;
   if (buckets) {  // and writes every pair into its tile's bucket
     pa.bucket_ids = c->bids;
+    pa.bucket_cap = c->bucket_cap;
     pa.overflow = c->d_overflow;
     pa.cls_count = c->cls_count;
   }

@@ -49,11 +49,12 @@ struct ProjectArgs {
                                   // item's tiles
   uint32_t* nvalid = nullptr;     // per view (nullable): zeroed by the projection (block 0)
   // per-tile buckets (nullable; graph-mode binning): every (item, tile) pair
-  // is written straight to bucket_ids[tile * kBucketCap + slot], slot taken
+  // is written straight to bucket_ids[tile * bucket_cap + slot], slot taken
   // from the tile's counter (a pair beyond the capacity sets bit 4 of
   // *overflow instead); block 0 zeroes the length-class counters the
   // per-tile sort then fills
   uint32_t* bucket_ids = nullptr;
+  uint32_t bucket_cap = 0;
   uint32_t* overflow = nullptr;
   uint32_t* cls_count = nullptr;
   // training step (nullable): block 0 advances the device Adam step that
@@ -153,8 +154,12 @@ void launch_dup_write(const DupArgs& a, cudaStream_t s, int64_t* launches);
 // counting-scatter binning with per-tile sorts (lists of at most kTileSortCap)
 constexpr int kTileSortCap = 4096;
 // graph-mode binning: entries of a tile's bucket (the projection writes the
-// pairs straight into per-tile buckets, no scan and no scatter)
-constexpr uint32_t kBucketCap = 1024;
+// pairs straight into per-tile buckets, no scan and no scatter), a power of
+// two from kBucketCapMin to kBucketCapMax (the per-tile sort's limit) chosen
+// per context
+constexpr uint32_t kBucketCapMin = 1024;
+constexpr uint32_t kBucketCapMax = 4096;
+static_assert(kBucketCapMax <= (uint32_t)kTileSortCap, "a full bucket is sorted by the per-tile sort");
 // length classes of the raster passes' visit order (four per octave)
 constexpr int kLenClasses = 129;
 
@@ -209,11 +214,12 @@ struct TileBinArgs {
   uint32_t* scan_aux;         // scratch of tile_scan_aux_size(n_tiles) words for the multi-block scan
   uint32_t* raster_work = nullptr;  // nullable: the forward and backward raster job counters, zeroed by the sort
   // bucket mode (nullable): the lists are the projection's per-tile buckets
-  // (bucket_ids, tile t's list at t * kBucketCap, its length in counts[t]);
+  // (bucket_ids, tile t's list at t * bucket_cap, its length in counts[t]);
   // the sort files each tile under its length class (class 0: empty),
   // cls_tiles[c * cls_stride + i] for i < cls_count[c], from which the
   // forward raster pass takes its visit order (see RasterArgs)
   uint32_t* bucket_ids = nullptr;
+  uint32_t bucket_cap = 0;
   uint32_t* cls_count = nullptr;
   uint32_t* cls_tiles = nullptr;
   uint32_t cls_stride = 0;

@@ -124,10 +124,10 @@ constexpr int kCountBox = 1024;
 
 // Bucket mode: takes slot `slot` of tile t's bucket for item `item` (a slot
 // beyond the bucket's capacity sets bit 4 of *overflow instead).
-__device__ __forceinline__ void bucket_put(uint32_t* __restrict__ bids, uint32_t* __restrict__ overflow, uint32_t t,
-                                           uint32_t slot, uint32_t item) {
-  if (slot < kBucketCap)
-    bids[(size_t)t * kBucketCap + slot] = item;
+__device__ __forceinline__ void bucket_put(uint32_t* __restrict__ bids, uint32_t cap, uint32_t* __restrict__ overflow,
+                                           uint32_t t, uint32_t slot, uint32_t item) {
+  if (slot < cap)
+    bids[(size_t)t * cap + slot] = item;
   else
     atomicOr(overflow, 4u);
 }
@@ -145,8 +145,8 @@ __device__ __forceinline__ void bucket_put(uint32_t* __restrict__ bids, uint32_t
 __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts, uint32_t tile_base, int tiles_x,
                                                   int x0, int y0, int x1, int y1, uint32_t ns,
                                                   uint32_t* __restrict__ s_cnt, int* __restrict__ s_box,
-                                                  uint32_t* __restrict__ bids, uint32_t* __restrict__ overflow,
-                                                  uint32_t item) {
+                                                  uint32_t* __restrict__ bids, uint32_t cap,
+                                                  uint32_t* __restrict__ overflow, uint32_t item) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int W = kFwdThreads / 32;
   unsigned bx0 = ns ? (unsigned)x0 : 0xFFFFu, by0 = ns ? (unsigned)y0 : 0xFFFFu;
@@ -176,7 +176,7 @@ __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts,
     for (uint32_t k = 0; k < ns; ++k) {
       const uint32_t t = tile_base + (uint32_t)(y0 + (int)k / w) * (uint32_t)tiles_x + (uint32_t)(x0 + (int)k % w);
       if (bids)
-        bucket_put(bids, overflow, t, atomicAdd(&counts[t], 1u), item);
+        bucket_put(bids, cap, overflow, t, atomicAdd(&counts[t], 1u), item);
       else
         atomicAdd(&counts[t], 1u);
     }
@@ -210,7 +210,7 @@ __device__ __forceinline__ void block_count_tiles(uint32_t* __restrict__ counts,
     tx = x0;
     ty = y0;
     for (uint32_t k = 0; k < ns; ++k) {
-      bucket_put(bids, overflow, tile_base + (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx,
+      bucket_put(bids, cap, overflow, tile_base + (uint32_t)ty * (uint32_t)tiles_x + (uint32_t)tx,
                  atomicAdd(&s_cnt[(ty - Y0) * bw + (tx - X0)], 1u), item);
       if (++tx == x1) {
         tx = x0;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
     if (a.counts) {
       const uint32_t nt = (uint32_t)(x1 - x0) * (uint32_t)(y1 - y0);
       block_count_tiles(a.counts, a.tile_base[v], a.tiles_x[v], x0, y0, x1, y1, nt <= kBigTiles ? nt : 0u, s_cnt,
-                        s_box, a.bucket_ids, a.overflow, (uint32_t)it);
+                        s_box, a.bucket_ids, a.bucket_cap, a.overflow, (uint32_t)it);
       unsigned big = __ballot_sync(0xFFFFFFFFu, nt > kBigTiles);
       const int lane = threadIdx.x & 31;
       while (big) {
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kFwdThreads) project_fwd_kernel(const __grid_c
         for (uint32_t k = lane; k < bn; k += 32) {
           const uint32_t t = a.tile_base[v] + (by + k / bw) * (uint32_t)a.tiles_x[v] + bx + k % bw;
           if (a.bucket_ids)
-            bucket_put(a.bucket_ids, a.overflow, t, atomicAdd(&a.counts[t], 1u), bit);
+            bucket_put(a.bucket_ids, a.bucket_cap, a.overflow, t, atomicAdd(&a.counts[t], 1u), bit);
           else
             atomicAdd(&a.counts[t], 1u);
         }

@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
                                                                  uint32_t capacity, uint32_t* __restrict__ overflow,
                                                                  uint32_t* __restrict__ big_len,
                                                                  uint32_t* __restrict__ raster_work,
-                                                                 uint32_t n_items, uint32_t* __restrict__ cls_count,
+                                                                 uint32_t n_items, uint32_t bucket_cap,
+                                                                 uint32_t* __restrict__ cls_count,
                                                                  uint32_t* __restrict__ cls_tiles,
                                                                  uint32_t cls_stride) {
   pdl_enter();
@@ -488,9 +489,9 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
   const uint32_t t = blockIdx.x * kSortWarps + warp;
   if (t < n_tiles) {
     uint32_t n = counts[t];
-    const uint32_t off = buckets ? t * kBucketCap : offsets[t];
+    const uint32_t off = buckets ? t * bucket_cap : offsets[t];
     __syncwarp();  // every lane has read counts[t]
-    if (buckets && n > kBucketCap) n = kBucketCap;  // its bucket overflowed (flagged by the projection)
+    if (buckets && n > bucket_cap) n = bucket_cap;  // its bucket overflowed (flagged by the projection)
     const bool fits = buckets || (unsigned long long)off + n <= (unsigned long long)capacity;
     if (lane == 0) {
       counts[t] = 0u;
@@ -597,7 +598,8 @@ void launch_tile_sort(const TileBinArgs& a, cudaStream_t s, int64_t* launches) {
   const bool buckets = a.bucket_ids != nullptr;
   launch_pdl(tile_sort_kernel<kTileSortCap>, grid, kSortThreads, 0, s, a.offsets, a.counts,
              buckets ? a.bucket_ids : a.ids, a.zkey, a.ranges, (uint32_t)a.n_tiles, a.capacity, a.overflow,
-             const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n, buckets ? a.cls_count : nullptr,
+             const_cast<uint32_t*>(a.big_len), a.raster_work, (uint32_t)a.n, a.bucket_cap,
+             buckets ? a.cls_count : nullptr,
              a.cls_tiles, a.cls_stride);
   if (launches) *launches += 1;
 }

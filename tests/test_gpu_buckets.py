@@ -1,11 +1,12 @@
-"""Graph-mode (no-sync) binning into per-tile buckets: once a sync-mode pass
-has seen every tile list at most half a bucket long, no-sync passes let the
-projection write every (tile, Gaussian) pair straight into its tile's
-bucket and skip the scan and the scatter.  The per-tile lists, and with them
-every image, are the same as the counting-scatter binning's bit for bit;
-the gradients agree up to the order of the float32 atomics.  Lists that grow
-past 512 entries take the sort's block-wide path; a list past the bucket's
-1024 entries is reported as GS_ERR_CAPACITY and the context goes back to
+"""Graph-mode (no-sync) binning into per-tile buckets: while the sync-mode
+passes have seen every tile list at most 2048 entries long, no-sync passes
+let the projection write every (tile, Gaussian) pair straight into its
+tile's bucket (twice the longest list seen, rounded up to a power of two
+from 1024 to 4096) and skip the scan and the scatter.  The per-tile lists,
+and with them every image, are the same as the counting-scatter binning's
+bit for bit; the gradients agree up to the order of the float32 atomics.
+Lists that grow past 512 entries take the sort's block-wide path; a list
+past its bucket is reported as GS_ERR_CAPACITY and the context goes back to
 the counting-scatter binning."""
 import numpy as np
 import pytest
@@ -186,10 +187,11 @@ def test_bucket_binning_of_a_batch_of_views():
     ctx.close()
 
 
-def test_bucket_binning_stays_off_after_any_long_list():
+def test_bucket_size_follows_the_longest_list_any_sync_pass_saw():
     """A context that renders a map with long lists and then one with short
-    lists in sync mode must not bin the first into buckets in no-sync mode:
-    bucket binning needs every list any sync pass saw to fit half a bucket."""
+    lists in sync mode sizes its buckets from the long ones (or bins by
+    counting): the no-sync pass of the first map overflows nothing and
+    renders its sync-mode images."""
     from paper_2408_12677_gb300 import abi
     P, cam, pose = _scene(seed=6, n=20000, log_scale_range=(-5.0, -3.5))
     big = dict(P)
@@ -202,7 +204,7 @@ def test_bucket_binning_stays_off_after_any_long_list():
     assert _longest(ctx, cam) <= 512
     _no_sync(ctx, P["means"].shape[0], cam.width * cam.height, 8_000_000)
     got = gpu_render(ctx, big_model, cam, pose)
-    abi.gs_sync_status(ctx.handle)  # counting-scatter binning: no bucket overflow
+    abi.gs_sync_status(ctx.handle)  # no bucket overflow
     for a, b in zip(got, ref):
         np.testing.assert_array_equal(a, b)
     ctx.close()
@@ -212,7 +214,7 @@ def test_bucket_binning_stays_off_after_any_long_list():
 def test_bucket_binning_at_full_size(which):
     """The bench's workloads (1200x680 with ~300k Gaussians; 8 views of
     640x480 to 1752x1168, 7.97M pixels, 500k Gaussians): a no-sync pass
-    (bucket binning when every list of the sync pass fits half a bucket)
+    (bucket binning when every list of the sync pass is at most 2048 long)
     renders every pixel as the sync-mode pass does, bit for bit, and its
     visit order is a permutation of the tiles, longest class first."""
     import os
@@ -235,7 +237,7 @@ def test_bucket_binning_at_full_size(which):
     n_no_sync = ctx.stats()["kernel_launches"] - b1
     abi.gs_sync_status(ctx.handle)
     check_visit_order(ctx, T)
-    if longest <= 512:  # bucket binning engaged: no count, scan or scatter launch
+    if longest <= 2048:  # bucket binning engaged: no count, scan or scatter launch
         assert n_no_sync < n_sync
     for (a0, a1, a2), (b0, b1, b2) in zip(got, ref):
         np.testing.assert_array_equal(a0, b0)
