@@ -509,10 +509,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint32_t*
       ranges[t] = rg;
     }
     if (fits && n > 1 && n <= (uint32_t)kWarpSortMax) {
-      if (n <= 32) warp_sort_list<1>(ids, zkey, off, n, n_items, lane);
-      else if (n <= 64) warp_sort_list<2>(ids, zkey, off, n, n_items, lane);
-      else if (n <= 128) warp_sort_list<4>(ids, zkey, off, n, n_items, lane);
-      else if (n <= 256) warp_sort_list<8>(ids, zkey, off, n, n_items, lane);
+      if (n <= 256) warp_sort_list<8>(ids, zkey, off, n, n_items, lane);
       else warp_sort_list<16>(ids, zkey, off, n, n_items, lane);
     }
   }

@@ -98,9 +98,10 @@ def test_long_tile_lists_take_the_radix_fallback(ctx):
 @pytest.mark.parametrize("L", [2, 3, 31, 32, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 1000, 4096])
 def test_list_lengths_of_every_sort_path(ctx, L):
     """Lists of exactly L entries in tile 0 and L // 2 + 1 in tile 1 of a
-    two-tile image: every register width of the per-warp sort (up to 32,
-    64, 128, 256, 512 entries), the CTA-wide sort beyond 512 and its limit
-    of 4096; depths drawn from few values so that ties are broken by id."""
+    two-tile image: both register widths of the per-warp sort (up to 256
+    and 512 entries, short lists padded), the CTA-wide sort beyond 512 and
+    its limit of 4096; depths drawn from few values so that ties are broken
+    by id."""
     rng = np.random.default_rng(L)
     n0, n1 = L, L // 2 + 1
     m = np.concatenate([np.stack([rng.uniform(2, 14, n0), rng.uniform(2, 14, n0)], 1),
