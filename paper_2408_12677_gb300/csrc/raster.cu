@@ -53,14 +53,6 @@ __device__ __forceinline__ void cp_record(float4* dst, const float4* __restrict_
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__device__ __forceinline__ void load_entry(const float4* __restrict__ feat, uint32_t g, float4& f0, float4& f1,
-                                           float4& f2) {
-  const float4* fg = feat + 3 * (size_t)g;
-  f0 = __ldg(fg);
-  f1 = __ldg(fg + 1);
-  f2 = __ldg(fg + 2);
-}
-
 // Converts a gathered record to tile-local coordinates and tests the splat's
 // support bounding box against the two halves of the warp's 8 x 8 block:
 // rows [by, by + 4) (bit 0, the lanes' first pixels) and [by + 4, by + 8)
